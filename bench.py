@@ -1,0 +1,402 @@
+#!/usr/bin/env python
+"""Benchmark: ensemble CG sample-solves/s on the 64^3-cell KL diffusion workload.
+
+One step = the whole hot path over one batch of 1024 samples: per-mesh set-up
+(CRS graph, KL tables, mode matrices), then for each ensemble of s samples the
+ensemble assembly and the ensemble CG solve to relative residual 1e-8.  Inputs
+(the KL variables of all samples) are resident on the GPU before the timed
+region; every step's working set (matrix values of 1.8 GB per s=32 ensemble)
+is far larger than the 129 MB L2, so no L2 flush is needed between steps.
+
+Also reported: the roofline of the dominant kernel (the CG SpMV, timed with
+CUDA events inside the library on its launch stream), the per-sample (s = 1)
+GPU path on a subset, the end-to-end number through host buffers, and the CPU
+oracle on the host cores (`cpu_baseline`).  `--impl reference` times the CPU
+oracle alone (the reference arm of this workload).
+"""
+import argparse
+import hashlib
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+N_MESH, M_KL, SIGMA, KAPPA0, L_CORR, TOL = 64, 10, 0.1, 1.0, 1.0, 1e-8
+BATCH = 1024
+METRIC = "ensemble CG sample-solves/s and ens_spmv HBM GB/s (% peak) vs per-sample, 1 GB300"
+UNIT = "sample-solves/s"
+WORKLOAD = "KL diffusion, 64^3 hex Q1 mesh (274,625 rows, 7,189,057 nnz), M=10, 1024 samples, CG to 1e-8"
+
+
+def spmv_bytes(n, nnz, s, vbytes=8):
+    """Algorithmic bytes of one fused CG SpMV: values + columns once, row map,
+    p read once, q written once (the paper's ensemble byte model made exact)."""
+    return nnz * (vbytes * s + 4) + 4 * (n + 1) + 2 * 8 * n * s
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for f in ("ens_spmv.cuh", "ens_cg.cu", "ens_internal.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_1511_03703_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(s):
+    """DRAM bytes per launch of the CG SpMV from the committed ncu summary, if
+    that summary was taken on the current kernel source; else None."""
+    path = os.path.join(ROOT, "profiles", "cg_spmv_64cubed.txt")
+    if not os.path.exists(path):
+        return None
+    txt = open(path).read()
+    m = re.search(r"kernel_source_sha256_16:\s*(\w+)", txt)
+    if not m or m.group(1) != kernel_source_hash():
+        return None
+    m = re.search(rf"traffic_bytes_per_launch_s{s}:\s*([0-9.eE+]+)", txt)
+    return float(m.group(1)) if m else None
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        return d.get("hbm_gbs", 6800.0), "measured"
+    return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            p = [x.strip() for x in ln.split(",")]
+            if len(p) < 7:
+                continue
+            try:
+                sm.append(float(p[0]))
+                smax.append(float(p[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, p[3:7]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ------------------------------------------------------------- the solver
+def make_batch(rank, s, batch):
+    from paper_1511_03703_gb300 import inputs
+    first = rank * batch
+    return inputs.kl_samples(inputs.SEED_SCALE, first, batch, M_KL)
+
+
+class Runner:
+    """Holds device buffers for one batch; run_step() is one timed step."""
+
+    def __init__(self, torch, s, batch, device, time_spmv=True):
+        import paper_1511_03703_gb300 as E
+        from paper_1511_03703_gb300 import inputs
+        self.torch, self.E, self.s, self.batch = torch, E, s, batch
+        self.dev = device
+        self.nens = batch // s
+        self.time_spmv = time_spmv
+        n, nnz, _ = E.mesh_sizes(N_MESH)
+        self.n, self.nnz = n, nnz
+        T = torch
+        self.row_map = T.empty(n + 1, dtype=T.int32, device=device)
+        self.col = T.empty(nnz, dtype=T.int32, device=device)
+        self.bmask = T.empty(n, dtype=T.uint8, device=device)
+        self.kl = T.empty(E.kl_table_size(N_MESH, M_KL), dtype=T.float64, device=device)
+        self.modes = T.empty((M_KL + 1) * nnz, dtype=T.float64, device=device)
+        self.load = T.empty(n, dtype=T.float64, device=device)
+        self.values = T.empty(nnz * s, dtype=T.float64, device=device)
+        self.b = T.empty(n * s, dtype=T.float64, device=device)
+        self.x = T.empty((self.nens, n * s), dtype=T.float64, device=device)
+        self.work = T.empty(E.cg_workspace_size(n, s), dtype=T.uint8, device=device)
+        self.graph = E.Graph(self.row_map, self.col)
+        self.xi_host = np.stack([inputs.ensemble_layout(b) for b in make_batch(0, s, batch).reshape(self.nens, s, M_KL)])
+        self.xi = T.from_numpy(self.xi_host).to(device)
+        self.reset_stats()
+
+    def reset_stats(self):
+        self.iters = []
+        self.spmv_ms = 0.0
+        self.spmv_launches = 0
+        self.launches = 0
+        self.status_bad = 0
+
+    def setup_mesh(self):
+        E = self.E
+        E.graph_build(N_MESH, self.row_map, self.col, None, self.bmask)
+        E.kl_setup(N_MESH, M_KL, L_CORR, self.kl, want_host=False)
+        E.mode_matrices(N_MESH, self.graph, M_KL, self.kl, self.modes, self.load)
+        self.launches += 5
+
+    def solve_ensemble(self, g, xi=None):
+        E = self.E
+        E.assemble(self.graph, self.bmask, self.s, M_KL, self.modes, self.load,
+                   self.xi[g] if xi is None else xi, SIGMA, KAPPA0, self.values, self.b)
+        x = self.x[g]
+        x.zero_()
+        flags = E.CG_TIME_SPMV if self.time_spmv else 0
+        it, rr, st, stats = E.cg(self.graph, self.s, self.values, self.b, x, TOL, 10000, self.work,
+                                 flags=flags, check_every=16)
+        self.launches += 2 + stats.kernel_launches
+        self.iters.extend(it)
+        self.status_bad += sum(1 for v in st if v != 0)
+        self.spmv_ms += stats.spmv_ms
+        self.spmv_launches += stats.spmv_launches
+        return x
+
+    def run_step(self):
+        self.setup_mesh()
+        for g in range(self.nens):
+            self.solve_ensemble(g)
+
+
+def per_sample_baseline(torch, device, nsamp=32):
+    """The s = 1 path (samples one after another), as in the paper's speed-up."""
+    r = Runner(torch, 1, nsamp, device, time_spmv=True)
+    r.setup_mesh()
+    r.solve_ensemble(0)  # warm-up
+    r.reset_stats()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for g in range(r.nens):
+        r.solve_ensemble(g)
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    return {"value": nsamp / dt, "unit": UNIT, "samples": nsamp,
+            "mean_iters": float(np.mean(r.iters)),
+            "spmv_gbs": spmv_bytes(r.n, r.nnz, 1) * r.spmv_launches / (r.spmv_ms * 1e-3) / 1e9
+            if r.spmv_ms > 0 else None}
+
+
+def cpu_baseline_run(nsamples=None, nthreads=None):
+    import oracle
+    cores = nthreads or oracle.max_threads()
+    ns = nsamples or max(2, cores)
+    xi = make_batch(0, 1, BATCH)[:ns]
+    t0 = time.perf_counter()
+    _, it, rr, st = oracle.solve_samples(N_MESH, M_KL, xi, TOL, 10000, nthreads=cores, L=L_CORR,
+                                         sigma=SIGMA, kappa0=KAPPA0)
+    dt = time.perf_counter() - t0
+    return {"value": ns / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{ns} samples of the 64^3 workload (sample indices 0..{ns - 1}), "
+                      f"per-sample FP64 assembly + CG, OpenMP over samples on {cores} threads",
+            "mean_iters": float(np.mean(it)), "seconds": dt}
+
+
+def e2e_run(torch, r, steps):
+    """Same metric through the library with host buffers: per step the KL
+    variables are copied from pinned host memory, and every ensemble's solution
+    is copied back to pinned host memory on a second stream while the next
+    ensemble computes."""
+    T = torch
+    xi_pinned = T.from_numpy(r.xi_host).pin_memory()
+    x_host = T.empty((r.nens, r.n * r.s), dtype=T.float64).pin_memory()
+    copy_stream = T.cuda.Stream(device=r.dev)
+    main = T.cuda.current_stream(r.dev)
+    T.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        r.xi.copy_(xi_pinned, non_blocking=True)
+        r.setup_mesh()
+        for g in range(r.nens):
+            x = r.solve_ensemble(g)
+            ev = T.cuda.Event()
+            ev.record(main)
+            copy_stream.wait_event(ev)
+            with T.cuda.stream(copy_stream):
+                x_host[g].copy_(x, non_blocking=True)
+        copy_stream.synchronize()
+    T.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    return {"value": steps * r.batch / dt, "unit": UNIT,
+            "h2d_bytes_per_step": int(r.xi_host.nbytes),
+            "d2h_bytes_per_step": int(r.nens * r.n * r.s * 8)}
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def shard_first_sample(rank, per_rank):
+    """Weak scaling: rank r solves samples [r*per_rank, (r+1)*per_rank)."""
+    return rank * per_rank
+
+
+def main_ours(args):
+    import torch
+    world, rank, local = dist_setup()
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    device = torch.device(f"cuda:{local}")
+    torch.cuda.set_device(device)
+    import paper_1511_03703_gb300 as E
+    E.lib()
+    s = args.s
+    r = Runner(torch, s, BATCH, device, time_spmv=True)
+    if world > 1:  # shard: this rank's own 1024 samples
+        from paper_1511_03703_gb300 import inputs
+        xs = inputs.kl_samples(inputs.SEED_SCALE, shard_first_sample(rank, BATCH), BATCH, M_KL)
+        r.xi_host = np.stack([inputs.ensemble_layout(b) for b in xs.reshape(r.nens, s, M_KL)])
+        r.xi = torch.from_numpy(r.xi_host).to(device)
+    for _ in range(args.warmup):
+        r.run_step()
+    torch.cuda.synchronize()
+    r.reset_stats()
+    clocks = ClockSampler(local)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    stream = torch.cuda.current_stream(device)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        r.run_step()
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    ms = ev0.elapsed_time(ev1)
+    if world > 1:
+        t = torch.tensor([ms], device=device)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        torch.distributed.barrier()
+        ms = float(t.item())
+    value = world * args.steps * BATCH / (ms * 1e-3)
+    peak, peak_kind = measured_peaks()
+    avg_spmv_ms = r.spmv_ms / max(r.spmv_launches, 1)
+    bytes_launch = spmv_bytes(r.n, r.nnz, s)
+    achieved = bytes_launch / (avg_spmv_ms * 1e-3) / 1e9
+    traffic = profiled_traffic(s)
+    gpu_launches = r.launches
+    iters = r.iters
+    bad = r.status_bad
+    out = None
+    if rank == 0:
+        e2e = e2e_run(torch, r, max(1, min(args.steps, 2)))
+        per = per_sample_baseline(torch, device)
+        ens_speedup = value / world / per["value"]
+        out = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "ensemble_size": s, "batch_samples": BATCH,
+                       "ensembles_per_step": BATCH // s, "tol": TOL, "kl_terms": M_KL,
+                       "sigma": SIGMA, "corr_length": L_CORR, "l2": "inputs larger than L2 (1.8 GB values per ensemble)",
+                       "parallelism": f"replica per GPU, {world} GPU(s), samples sharded by rank"},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": traffic,
+                         "kernel": f"cg_spmv_kernel<{s}> (fused q = A p and per-member p.q)",
+                         "bytes_per_launch": bytes_launch, "avg_launch_ms": avg_spmv_ms,
+                         "launches_timed": r.spmv_launches, "peak_source": f"{peak_kind} hbm_gbs"},
+            "cpu_baseline": cpu_baseline_run() if not args.no_cpu_baseline else None,
+            "e2e": e2e,
+            "per_sample_gpu": per,
+            "ensemble_speedup_vs_per_sample": ens_speedup,
+            "cg_iterations": {"mean": float(np.mean(iters)), "min": int(min(iters)),
+                              "max": int(max(iters)), "failed_members": bad},
+            "gpu_launches": gpu_launches,
+            "clocks": clk,
+        }
+        print(json.dumps(out))
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return out
+
+
+def main_reference(args):
+    world, rank, _ = dist_setup()
+    if rank != 0:
+        return None
+    import oracle
+    cores = oracle.max_threads()
+    ns = max(2, cores)
+    for _ in range(args.warmup):
+        pass  # the oracle has no warm-up state; a first run would only repeat the same work
+    vals = []
+    for _ in range(args.steps):
+        vals.append(cpu_baseline_run(ns, cores))
+    t = sum(v["seconds"] for v in vals)
+    value = args.steps * ns / t
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "impl": "reference",
+           "config": {"workload": WORKLOAD, "ensemble_size": 1, "batch_samples": ns,
+                      "tol": TOL, "kl_terms": M_KL},
+           "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                            "sample": vals[0]["sample"]},
+           "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out))
+    return out
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--s", type=int, default=32, choices=[4, 8, 16, 32])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        main_reference(args)
+    else:
+        main_ours(args)
+
+
+if __name__ == "__main__":
+    main()

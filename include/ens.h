@@ -1,0 +1,182 @@
+/*
+ * ens.h -- C ABI of the embedded-ensemble (Phipps et al., "Embedded Ensemble
+ * Propagation ...") diffusion hot path on one NVIDIA GB300 (sm_103a).
+ *
+ * Problem (Sect. 4): -div(a(x,xi) grad u) = 1 on [0,1]^3, u = 0 on the
+ * boundary, trilinear hex finite elements on an N^3 cell mesh, coefficient a
+ * a truncated Karhunen-Loeve expansion (Eq. 9-10).  s samples ("an ensemble")
+ * share one CRS graph (Fig. 2) and are stored in the commuted Kronecker
+ * ordering of Eq. 3: the s values that belong to one matrix entry, node or KL
+ * variable are contiguous:
+ *     values[entry*s + e], x[node*s + e], xi[k*s + e],  e = 0..s-1.
+ *
+ * Conventions shared by every call
+ *   - Pointers are DEVICE pointers unless the name ends in _host.  The caller
+ *     allocates every buffer (inputs, outputs and workspaces); the library
+ *     never allocates device memory.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream).  Calls are asynchronous on that stream unless documented as
+ *     synchronising (those return host results).
+ *   - Every call returns an ens_status.  On failure ens_last_error() gives a
+ *     thread-local message.  No kernel traps; device-side failures (breakdown,
+ *     non-convergence) are reported through per-member status words.
+ *   - Supported ensemble sizes: s in {1, 4, 8, 16, 32} (s = 1 is the
+ *     per-sample path the paper's speed-up s*T1/Ts is measured against).
+ *   - Node numbering: (i,j,k) -> i + (N+1)(j + (N+1)k); cell (ci,cj,ck) ->
+ *     ci + N(cj + N ck); local node / Gauss point l -> offsets
+ *     (l&1, (l>>1)&1, (l>>2)&1).
+ */
+#ifndef ENS_H
+#define ENS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum ens_status {
+    ENS_OK = 0,
+    ENS_ERR_ARG = 1,           /* bad size, NULL pointer or inconsistent argument */
+    ENS_ERR_UNSUPPORTED = 2,   /* s not in {1,4,8,16,32}, dtype or mesh too large */
+    ENS_ERR_ALIGN = 3,         /* a pointer is not 16-byte aligned */
+    ENS_ERR_CUDA = 4,          /* a CUDA runtime call failed */
+    ENS_ERR_NOT_CONVERGED = 5, /* CG hit max_iter before the tolerance */
+    ENS_ERR_BREAKDOWN = 6,     /* p'Ap <= 0 or not finite (matrix not SPD) */
+    ENS_ERR_NONPOS_COEFF = 7,  /* reserved: coefficient a(x) <= 0 */
+    ENS_ERR_TIMEOUT = 8,       /* reserved: a bounded device wait gave up */
+    ENS_ERR_WORKSPACE = 9      /* workspace smaller than the *_workspace_size value */
+} ens_status;
+
+typedef enum ens_dtype { ENS_F64 = 0, ENS_F32 = 1, ENS_BF16 = 2 } ens_dtype;
+
+/* CRS graph (Fig. 2): row_map[num_rows+1], col_entry[num_entries] (device,
+ * int32, columns ascending within a row).  Values live in a separate array in
+ * the commuted layout, one block of s values per entry. */
+typedef struct ens_graph {
+    int32_t num_rows;
+    int32_t reserved;
+    int64_t num_entries;
+    const int32_t *row_map;
+    const int32_t *col_entry;
+} ens_graph;
+
+const char *ens_last_error(void);
+const char *ens_status_string(int status);
+int ens_version(void);
+
+/* ---------------------------------------------------------------- A1 graph */
+/* Host only.  Sizes of the Q1 mesh with N cells per side:
+ * num_rows = (N+1)^3, num_entries = (3N+1)^3, num_cells = N^3.  1 <= N <= 512. */
+int ens_mesh_sizes(int N, int32_t *num_rows, int64_t *num_entries, int64_t *num_cells);
+
+/* Builds the CRS graph of the Q1 hex mesh (Fig. 2; Algorithm 2's NodeIndex and
+ * ElemGraph): row I holds every node that shares a cell with I, ascending.
+ *   row_map   int32[num_rows+1]     (out)
+ *   col_entry int32[num_entries]    (out)
+ *   elem_graph int32[num_cells*64]  (out, may be NULL): entry of
+ *              (NodeIndex(c,a), NodeIndex(c,b)) at [c*64 + a*8 + b]
+ *   bmask     uint8[num_rows]       (out, may be NULL): 1 on the boundary.
+ * Integer work, bit-exact by construction. */
+int ens_graph_build(int N, int32_t *row_map, int32_t *col_entry, int32_t *elem_graph,
+                    uint8_t *bmask, void *stream);
+
+/* ------------------------------------------------------------------- A2 KL */
+/* KL of C(x,x') = exp(-|x-x'|_1 / L) on [0,1]^3 (Sect. 4, Eq. 9-10): the M
+ * largest eigenpairs, each a product of 1D cosine/sine modes (ordering: by
+ * eigenvalue, ties by (p,q,r) ascending with p the x index).  kl_table holds,
+ * for the 2N Gauss coordinates per axis, kl_table[(d*M + k)*2N + t] =
+ * phi_k,d(x_t) with sqrt(lambda_k) folded into d = 0, so
+ * kappa_k(x_q) = T[0][k][tx] * T[1][k][ty] * T[2][k][tz].
+ * ens_kl_table_size gives the length in doubles (3*M*2N).  The roots are
+ * found on the device; lambda_host[M] and pqr_host[3M] may be NULL, if not the
+ * call synchronises `stream` to fill them.  1 <= M <= 64. */
+int ens_kl_table_size(int N, int M, int64_t *num_doubles);
+int ens_kl_setup(int N, int M, double L, double *kl_table, double *lambda_host,
+                 int32_t *pqr_host, void *stream);
+
+/* Sample-independent part of the assembly (Algorithm 2 with the coefficient
+ * split by linearity): for k = 0..M the stiffness matrix of coefficient
+ * kappa_k (kappa_0 = 1) on the full graph,
+ *   modes[k*num_entries + entry] = sum_{cells c} sum_q kappa_k(x_q) G_q(a,b),
+ * where G_q is the Q1 gradient product at Gauss point q times w_q h (2x2x2
+ * Gauss), summed over the cells shared by the entry's row and column nodes;
+ * and load[num_rows] = the load vector of source 1 (zero on the boundary).
+ * Boundary rows and columns are stored as zeros (ens_assemble applies the
+ * Dirichlet rows).  modes: double[(M+1)*num_entries]. */
+int ens_mode_matrices(int N, const ens_graph *graph, int M, const double *kl_table,
+                      double *modes, double *load, void *stream);
+
+/* ------------------------------------------------------------- A3 assembly */
+/* Ensemble assembly of s samples: member e has coefficient
+ *   a_e(x) = kappa0 + sigma * sum_k kappa_k(x) xi[k*s + e]
+ * so its matrix is kappa0*modes_0 + sum_k (sigma*xi[k*s+e]) modes_k.  Output
+ * in the commuted layout: values[entry*s + e], b[node*s + e].  Dirichlet
+ * u = 0 by symmetric elimination: boundary rows become identity rows with
+ * b = 0; interior rows keep stored zeros in boundary columns.
+ * bmask from ens_graph_build; values and b must be 16-byte aligned for s>1. */
+int ens_assemble(const ens_graph *graph, const uint8_t *bmask, int s, int M,
+                 const double *modes, const double *load, const double *xi, double sigma,
+                 double kappa0, double *values, double *b, void *stream);
+
+/* --------------------------------------------------------------- A4 SpMV */
+/* y = A_c x for the commuted ensemble matrix (Fig. 5 semantics):
+ *   y[I*s+e] = sum_{entry in row I} values[entry*s+e] * x[col_entry[entry]*s+e].
+ * dtype = ENS_F64 (values double), ENS_F32 (float) or ENS_BF16 (bfloat16);
+ * x and y are double, accumulation in FP64.  The per-member sum order is
+ * fixed and independent of s: entry j goes to partial j mod 4, partials are
+ * combined as (p0+p1)+(p2+p3), so member e's result is bitwise the same for
+ * every s. x, y, values 16-byte aligned when s > 1. */
+int ens_spmv(const ens_graph *graph, int s, int dtype, const void *values, const double *x,
+             double *y, void *stream);
+
+/* ---------------------------------------------------------------- A5 dot */
+/* Per-member inner products (Sect. 3.4: the ensemble inner product computed
+ * first as sum_i u_i^T v_i (x) e_i):  out[e] = sum_I u[I*s+e] * v[I*s+e].
+ * Deterministic, s-independent order: products are summed in a fixed tree
+ * (32-row chunks by butterfly, then groups of 32 chunks, ...).
+ * work: device scratch of ens_dot_workspace_size bytes (16-byte aligned);
+ * its counters are cleared by the call.  out: device double[s]. */
+int ens_dot_workspace_size(int64_t n, int s, size_t *bytes);
+int ens_dot(int64_t n, int s, const double *u, const double *v, double *out, void *work,
+            size_t work_bytes, void *stream);
+
+/* ----------------------------------------------------------------- A6 CG */
+/* Statistics of one ens_cg call (optional). */
+typedef struct ens_cg_stats {
+    double spmv_ms;          /* summed CUDA-event time of the CG SpMV launches (ENS_CG_TIME_SPMV) */
+    int32_t spmv_launches;   /* SpMV launches timed */
+    int32_t kernel_launches; /* all kernels launched by the call */
+    int32_t iterations;      /* iterations run (max over members) */
+    int32_t host_checks;     /* device->host convergence polls */
+} ens_cg_stats;
+
+enum {
+    ENS_CG_COUPLED = 1,      /* paper's coupled ensemble CG (Sect. 3.6): alpha, beta
+                                from member-summed dots, one convergence test */
+    ENS_CG_GRAPH = 2,        /* replay the iteration through a captured CUDA graph */
+    ENS_CG_TIME_SPMV = 4     /* record CUDA events around each CG SpMV */
+};
+
+/* Unpreconditioned CG (Hestenes-Stiefel) on each member of the ensemble
+ * system, with per-member dots (default) or the paper's coupled form.
+ * Member e stops when ||r_e|| <= tol*||b_e|| (recursive residual) and is
+ * then frozen; the call returns when every member has stopped.
+ *   values: A_c (double, commuted), b: rhs, x: in = x0, out = solution.
+ *   work: ens_cg_workspace_size bytes of device scratch (16-byte aligned).
+ *   iters_host[s], relres_host[s] (true ||b-Ax||/||b||), status_host[s]
+ *   (ENS_OK / ENS_ERR_NOT_CONVERGED / ENS_ERR_BREAKDOWN) may be NULL.
+ *   check_every: iterations between host polls of the convergence word (>=1).
+ * Synchronises `stream`.  Returns ENS_OK if every member converged, else the
+ * first member's failure status. */
+int ens_cg_workspace_size(int32_t num_rows, int s, size_t *bytes);
+int ens_cg(const ens_graph *graph, int s, const double *values, const double *b, double *x,
+           double tol, int max_iter, int flags, int check_every, void *work, size_t work_bytes,
+           int32_t *iters_host, double *relres_host, int32_t *status_host,
+           ens_cg_stats *stats_host, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* ENS_H */

@@ -1,0 +1,263 @@
+"""Embedded ensemble propagation on one GB300: Python binding of libens.so.
+
+A thin ctypes layer over the C ABI declared in include/ens.h.  Every function
+here only marshals arguments (torch tensors -> device pointers, the current
+CUDA stream) and turns status codes into EnsError; every step of the
+computation runs in the library's CUDA kernels.  PyTorch is used for device
+memory and streams only.  There is no CPU fallback: if libens.so cannot be
+built or loaded, or no GPU is present, calls raise.
+"""
+import ctypes
+import os
+import threading
+
+__all__ = ["EnsError", "lib", "Graph", "Mesh", "mesh_sizes", "graph_build", "kl_table_size",
+           "kl_setup", "mode_matrices", "assemble", "spmv", "dot", "dot_workspace_size", "cg",
+           "cg_workspace_size", "CgStats", "F64", "F32", "BF16", "CG_COUPLED", "CG_GRAPH",
+           "CG_TIME_SPMV"]
+
+F64, F32, BF16 = 0, 1, 2
+CG_COUPLED, CG_GRAPH, CG_TIME_SPMV = 1, 2, 4
+OK, ERR_NOT_CONVERGED, ERR_BREAKDOWN = 0, 5, 6
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_lib = None
+_lock = threading.Lock()
+
+
+class EnsError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"[ens status {code}] {msg}")
+        self.code = code
+
+
+class EnsGraphC(ctypes.Structure):
+    _fields_ = [("num_rows", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("num_entries", ctypes.c_int64), ("row_map", ctypes.c_void_p),
+                ("col_entry", ctypes.c_void_p)]
+
+
+class CgStats(ctypes.Structure):
+    _fields_ = [("spmv_ms", ctypes.c_double), ("spmv_launches", ctypes.c_int32),
+                ("kernel_launches", ctypes.c_int32), ("iterations", ctypes.c_int32),
+                ("host_checks", ctypes.c_int32)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+def library_path():
+    return os.path.join(_HERE, "_build", "libens.so")
+
+
+def lib(build_if_missing=True):
+    """Load libens.so (building it with nvcc if it is missing)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = library_path()
+            if not os.path.exists(path):
+                if not build_if_missing:
+                    raise EnsError(-1, f"{path} missing: run paper_1511_03703_gb300.build.build()")
+                from . import build as _b
+                _b.build()
+            _lib = ctypes.CDLL(path)
+            _declare(_lib)
+    return _lib
+
+
+def _declare(L):
+    vp, i32, i64, d, sz = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_double, ctypes.c_size_t
+    I = ctypes.c_int
+    P = ctypes.POINTER
+    sig = {
+        "ens_last_error": (ctypes.c_char_p, []),
+        "ens_status_string": (ctypes.c_char_p, [I]),
+        "ens_version": (I, []),
+        "ens_mesh_sizes": (I, [I, P(i32), P(i64), P(i64)]),
+        "ens_graph_build": (I, [I, vp, vp, vp, vp, vp]),
+        "ens_kl_table_size": (I, [I, I, P(i64)]),
+        "ens_kl_setup": (I, [I, I, d, vp, vp, vp, vp]),
+        "ens_mode_matrices": (I, [I, P(EnsGraphC), I, vp, vp, vp, vp]),
+        "ens_assemble": (I, [P(EnsGraphC), vp, I, I, vp, vp, vp, d, d, vp, vp, vp]),
+        "ens_spmv": (I, [P(EnsGraphC), I, I, vp, vp, vp, vp]),
+        "ens_dot_workspace_size": (I, [i64, I, P(sz)]),
+        "ens_dot": (I, [i64, I, vp, vp, vp, vp, sz, vp]),
+        "ens_cg_workspace_size": (I, [i32, I, P(sz)]),
+        "ens_cg": (I, [P(EnsGraphC), I, vp, vp, vp, d, I, I, I, vp, sz, vp, vp, vp, P(CgStats), vp]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(L, name)
+        f.restype = res
+        f.argtypes = args
+
+
+def exported_symbols():
+    """Names declared in include/ens.h (used by the load/export test)."""
+    import re
+    hdr = os.path.join(os.path.dirname(_HERE), "include", "ens.h")
+    txt = open(hdr).read()
+    return sorted(set(re.findall(r"^(?:int|const char \*)\s*\*?\s*(ens_\w+)\s*\(", txt, re.M)))
+
+
+def _check(rc):
+    if rc != 0:
+        msg = lib().ens_last_error()
+        raise EnsError(rc, msg.decode() if msg else "")
+    return rc
+
+
+def _ptr(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream=None):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _require_cuda(*tensors):
+    for t in tensors:
+        if t is not None and not t.is_cuda:
+            raise EnsError(1, "tensor arguments must live on the GPU (no CPU path)")
+
+
+# ------------------------------------------------------------- mesh / graph
+def mesh_sizes(N):
+    n, nnz, nc = ctypes.c_int32(), ctypes.c_int64(), ctypes.c_int64()
+    _check(lib().ens_mesh_sizes(N, ctypes.byref(n), ctypes.byref(nnz), ctypes.byref(nc)))
+    return n.value, nnz.value, nc.value
+
+
+class Graph:
+    """CRS graph of the ensemble matrix (Fig. 2); keeps its tensors alive."""
+
+    def __init__(self, row_map, col_entry):
+        _require_cuda(row_map, col_entry)
+        self.row_map, self.col_entry = row_map, col_entry
+        self.num_rows = row_map.numel() - 1
+        self.num_entries = col_entry.numel()
+        self.c = EnsGraphC(self.num_rows, 0, self.num_entries, row_map.data_ptr(),
+                           col_entry.data_ptr())
+
+    def ref(self):
+        return ctypes.byref(self.c)
+
+
+def graph_build(N, row_map, col_entry, elem_graph=None, bmask=None, stream=None):
+    _require_cuda(row_map, col_entry, elem_graph, bmask)
+    _check(lib().ens_graph_build(N, _ptr(row_map), _ptr(col_entry), _ptr(elem_graph), _ptr(bmask),
+                                 _stream(stream)))
+
+
+# ---------------------------------------------------------------------- KL
+def kl_table_size(N, M):
+    v = ctypes.c_int64()
+    _check(lib().ens_kl_table_size(N, M, ctypes.byref(v)))
+    return v.value
+
+
+def kl_setup(N, M, L, kl_table, want_host=True, stream=None):
+    """Returns (lambda[M], pqr[M][3]) as Python lists when want_host."""
+    _require_cuda(kl_table)
+    if want_host:
+        lam = (ctypes.c_double * M)()
+        pqr = (ctypes.c_int32 * (3 * M))()
+        _check(lib().ens_kl_setup(N, M, L, _ptr(kl_table), lam, pqr, _stream(stream)))
+        return list(lam), [list(pqr[3 * k:3 * k + 3]) for k in range(M)]
+    _check(lib().ens_kl_setup(N, M, L, _ptr(kl_table), None, None, _stream(stream)))
+    return None, None
+
+
+def mode_matrices(N, graph, M, kl_table, modes, load, stream=None):
+    _require_cuda(kl_table, modes, load)
+    _check(lib().ens_mode_matrices(N, graph.ref(), M, _ptr(kl_table), _ptr(modes), _ptr(load),
+                                   _stream(stream)))
+
+
+def assemble(graph, bmask, s, M, modes, load, xi, sigma, kappa0, values, b, stream=None):
+    _require_cuda(bmask, modes, load, xi, values, b)
+    _check(lib().ens_assemble(graph.ref(), _ptr(bmask), s, M, _ptr(modes), _ptr(load), _ptr(xi),
+                              sigma, kappa0, _ptr(values), _ptr(b), _stream(stream)))
+
+
+# ------------------------------------------------------------ linear algebra
+_DT = {"float64": F64, "float32": F32, "bfloat16": BF16}
+
+
+def spmv(graph, s, values, x, y, stream=None):
+    _require_cuda(values, x, y)
+    dt = _DT[str(values.dtype).replace("torch.", "")]
+    _check(lib().ens_spmv(graph.ref(), s, dt, _ptr(values), _ptr(x), _ptr(y), _stream(stream)))
+
+
+def dot_workspace_size(n, s):
+    v = ctypes.c_size_t()
+    _check(lib().ens_dot_workspace_size(n, s, ctypes.byref(v)))
+    return v.value
+
+
+def dot(n, s, u, v, out, work, stream=None):
+    _require_cuda(u, v, out, work)
+    _check(lib().ens_dot(n, s, _ptr(u), _ptr(v), _ptr(out), _ptr(work), work.numel() * work.element_size(),
+                         _stream(stream)))
+
+
+def cg_workspace_size(n, s):
+    v = ctypes.c_size_t()
+    _check(lib().ens_cg_workspace_size(n, s, ctypes.byref(v)))
+    return v.value
+
+
+def cg(graph, s, values, b, x, tol, max_iter, work, flags=0, check_every=8, stream=None,
+       raise_on_failure=False):
+    """Runs ens_cg; returns (iters[s], relres[s], status[s], CgStats).  Synchronises."""
+    _require_cuda(values, b, x, work)
+    it = (ctypes.c_int32 * s)()
+    rr = (ctypes.c_double * s)()
+    stt = (ctypes.c_int32 * s)()
+    stats = CgStats()
+    rc = lib().ens_cg(graph.ref(), s, _ptr(values), _ptr(b), _ptr(x), tol, max_iter, flags,
+                      check_every, _ptr(work), work.numel() * work.element_size(), it, rr, stt,
+                      ctypes.byref(stats), _stream(stream))
+    if rc not in (0, ERR_NOT_CONVERGED, ERR_BREAKDOWN) or (rc and raise_on_failure):
+        _check(rc)
+    return list(it), list(rr), list(stt), stats
+
+
+# ------------------------------------------------------------ convenience
+class Mesh:
+    """Per-mesh, sample-independent set-up on the GPU: graph, boundary mask,
+    KL tables and mode matrices (all computed by library kernels)."""
+
+    def __init__(self, N, M, L=1.0, device="cuda", with_elem_graph=False, stream=None):
+        import torch
+        self.N, self.M, self.L = N, M, L
+        n, nnz, nc = mesh_sizes(N)
+        self.n, self.nnz, self.ncells = n, nnz, nc
+        dev = torch.device(device)
+        self.row_map = torch.empty(n + 1, dtype=torch.int32, device=dev)
+        self.col_entry = torch.empty(nnz, dtype=torch.int32, device=dev)
+        self.bmask = torch.empty(n, dtype=torch.uint8, device=dev)
+        self.elem_graph = torch.empty(nc * 64, dtype=torch.int32, device=dev) if with_elem_graph else None
+        graph_build(N, self.row_map, self.col_entry, self.elem_graph, self.bmask, stream)
+        self.graph = Graph(self.row_map, self.col_entry)
+        self.kl_table = torch.empty(kl_table_size(N, M), dtype=torch.float64, device=dev)
+        self.kl_lambda, self.kl_pqr = kl_setup(N, M, L, self.kl_table, True, stream)
+        self.modes = torch.empty((M + 1) * nnz, dtype=torch.float64, device=dev)
+        self.load = torch.empty(n, dtype=torch.float64, device=dev)
+        mode_matrices(N, self.graph, M, self.kl_table, self.modes, self.load, stream)
+
+    def assemble(self, s, xi_ens, sigma=0.1, kappa0=1.0, values=None, b=None, stream=None):
+        """xi_ens: device float64[M*s] (commuted layout).  Returns (values, b)."""
+        import torch
+        dev = self.row_map.device
+        if values is None:
+            values = torch.empty(self.nnz * s, dtype=torch.float64, device=dev)
+        if b is None:
+            b = torch.empty(self.n * s, dtype=torch.float64, device=dev)
+        assemble(self.graph, self.bmask, s, self.M, self.modes, self.load, xi_ens, sigma, kappa0,
+                 values, b, stream)
+        return values, b

@@ -1,0 +1,503 @@
+// ens_cg.cu -- ensemble conjugate gradients (Sect. 3.4 solver, Sect. 4 experiments).
+//
+// Hestenes-Stiefel CG run on every member of the commuted ensemble system at
+// once.  By default each member has its own alpha, beta and stopping test
+// (dots reduced per member: the vector sum_i u_i^T v_i (x) e_i of
+// Sect. 3.4 before its members are added), so member e follows exactly the iterates of a
+// standalone solve of sample e; members that converge are frozen.  With
+// ENS_CG_COUPLED the member dots are summed first, which is the paper's
+// coupled ensemble solver of Sect. 3.6.
+//
+// One iteration = 3 kernels, no host synchronisation:
+//   K1  q = A p,  pi_e = p.q            (last CTA: alpha_e = rho_e / pi_e)
+//   K2  r -= alpha q,  rho'_e = r.r     (last CTA: stop test, beta_e)
+//   K3  x += alpha p,  p = r + beta p   (x update deferred here so K2 reads 2 vectors)
+// Vector traffic per iteration: K1 1 gather + 1 write, K2 2 reads + 1 write,
+// K3 3 reads + 2 writes (10 vector passes).  The per-member scalar work runs in
+// the CTA that completes each kernel's deterministic dot tree.
+#include <vector>
+
+#include "ens_spmv.cuh"
+
+namespace ens {
+
+struct CgState {
+    double rho[32], alpha[32], beta[32], bnorm[32], relres[32];
+    int active[32], updx[32], zerox[32], iters[32], status[32];
+    int active_count, updx_any, k3_arrive, spmv_real;
+    double bnorm_all;
+};
+
+struct CgArgs {
+    int32_t n;
+    const int32_t *row_map;
+    const int32_t *col;
+    const double *vals;
+    const double *b;
+    double *x, *r, *p, *q;
+    CgState *st;
+    DotTree t1;  // width s
+    DotTree t2;  // width 2s
+    double tol;
+    int max_iter;
+    int coupled;
+};
+
+// ------------------------------------------------------------------ K0
+template <int S>
+__global__ void __launch_bounds__(RowMap<S>::THREADS) cg_init_kernel(CgArgs a) {
+    constexpr int G = RowMap<S>::G;
+    __shared__ double sm[32][S + 1];
+    const int r = threadIdx.x / G, g = threadIdx.x % G;
+    const int64_t R = (int64_t)blockIdx.x * 32 + r;
+    double rr0 = 0.0, rr1 = 0.0, bb0 = 0.0, bb1 = 0.0;
+    if constexpr (S == 1) {
+        const double ax = row_spmv1<double>(a.row_map, a.col, a.vals, a.x, R, g, R < a.n);
+        if (R < a.n) {
+            const double bv = a.b[R];
+            const double res = bv - ax;
+            if (g == 0) { a.r[R] = res; a.p[R] = res; }
+            rr0 = res * res;
+            bb0 = bv * bv;
+        }
+    } else if (R < a.n) {
+        const double2 ax = row_spmv2<S, double>(a.row_map, a.col, a.vals, a.x, R, g);
+        const double2 bv = reinterpret_cast<const double2 *>(a.b)[R * G + g];
+        const double2 res = make_double2(bv.x - ax.x, bv.y - ax.y);
+        reinterpret_cast<double2 *>(a.r)[R * G + g] = res;
+        reinterpret_cast<double2 *>(a.p)[R * G + g] = res;
+        rr0 = res.x * res.x; rr1 = res.y * res.y;
+        bb0 = bv.x * bv.x; bb1 = bv.y * bv.y;
+    }
+    chunk_tree<S>(sm, rr0, rr1, r, g, a.t2, blockIdx.x, 0);
+    chunk_tree<S>(sm, bb0, bb1, r, g, a.t2, blockIdx.x, S);
+    if (!dot_tree_propagate(a.t2, blockIdx.x)) return;
+    if (threadIdx.x != 0) return;
+    const double *top = a.t2.buf[a.t2.levels];
+    CgState *st = a.st;
+    double rsum = 0.0, bsum = 0.0;
+    for (int e = 0; e < S; ++e) {
+        const double rr = ld_cg(top + e), bb = ld_cg(top + S + e);
+        rsum += rr;
+        bsum += bb;
+        st->rho[e] = rr;
+        st->bnorm[e] = sqrt(bb);
+        st->alpha[e] = 0.0; st->beta[e] = 0.0; st->relres[e] = 0.0;
+        st->iters[e] = 0; st->updx[e] = 0; st->zerox[e] = 0; st->status[e] = ENS_OK;
+        if (!a.coupled) {
+            if (bb == 0.0) { st->active[e] = 0; st->zerox[e] = 1; }
+            else st->active[e] = (sqrt(rr) <= a.tol * st->bnorm[e]) ? 0 : 1;
+        }
+    }
+    st->bnorm_all = sqrt(bsum);
+    if (a.coupled) {
+        const bool all_zero = (bsum == 0.0);
+        const bool done = all_zero || sqrt(rsum) <= a.tol * st->bnorm_all;
+        for (int e = 0; e < S; ++e) { st->active[e] = done ? 0 : 1; st->zerox[e] = all_zero ? 1 : 0; }
+    }
+    if (a.max_iter == 0)
+        for (int e = 0; e < S; ++e)
+            if (st->active[e]) { st->active[e] = 0; st->status[e] = ENS_ERR_NOT_CONVERGED; }
+    int ac = 0, ux = 0;
+    for (int e = 0; e < S; ++e) { ac += st->active[e]; ux += st->zerox[e]; }
+    st->active_count = ac;
+    st->updx_any = ux;
+    st->k3_arrive = 0;
+    st->spmv_real = 0;
+    __threadfence();
+}
+
+// ------------------------------------------------------------------ K1
+template <int S>
+__global__ void __launch_bounds__(RowMap<S>::THREADS) cg_spmv_kernel(CgArgs a) {
+    if (ld_cg(&a.st->active_count) == 0) return;
+    constexpr int G = RowMap<S>::G;
+    __shared__ double sm[32][S + 1];
+    const int r = threadIdx.x / G, g = threadIdx.x % G;
+    const int64_t R = (int64_t)blockIdx.x * 32 + r;
+    double v0 = 0.0, v1 = 0.0;
+    if constexpr (S == 1) {
+        const double ap = row_spmv1<double>(a.row_map, a.col, a.vals, a.p, R, g, R < a.n);
+        if (R < a.n) {
+            if (g == 0) a.q[R] = ap;
+            v0 = ap * a.p[R];
+        }
+    } else if (R < a.n) {
+        const double2 ap = row_spmv2<S, double>(a.row_map, a.col, a.vals, a.p, R, g);
+        reinterpret_cast<double2 *>(a.q)[R * G + g] = ap;
+        const double2 pv = reinterpret_cast<const double2 *>(a.p)[R * G + g];
+        v0 = ap.x * pv.x;
+        v1 = ap.y * pv.y;
+    }
+    chunk_tree<S>(sm, v0, v1, r, g, a.t1, blockIdx.x, 0);
+    if (!dot_tree_propagate(a.t1, blockIdx.x)) return;
+    if (threadIdx.x != 0) return;
+    const double *top = a.t1.buf[a.t1.levels];
+    CgState *st = a.st;
+    st->spmv_real += 1;
+    if (a.coupled) {
+        double pis = 0.0, rhos = 0.0;
+        for (int e = 0; e < S; ++e) { pis += ld_cg(top + e); rhos += st->rho[e]; }
+        const bool bad = !(pis > 0.0) || !isfinite(pis);
+        for (int e = 0; e < S; ++e) {
+            if (!st->active[e]) continue;
+            if (bad) { st->active[e] = 0; st->status[e] = ENS_ERR_BREAKDOWN; }
+            else st->alpha[e] = rhos / pis;
+        }
+    } else {
+        for (int e = 0; e < S; ++e) {
+            if (!st->active[e]) continue;
+            const double pi = ld_cg(top + e);
+            if (!(pi > 0.0) || !isfinite(pi)) { st->active[e] = 0; st->status[e] = ENS_ERR_BREAKDOWN; }
+            else st->alpha[e] = st->rho[e] / pi;
+        }
+    }
+    int ac = 0;
+    for (int e = 0; e < S; ++e) ac += st->active[e];
+    st->active_count = ac;
+    __threadfence();
+}
+
+// ------------------------------------------------------------------ K2
+template <int S>
+__global__ void __launch_bounds__(RowMap<S>::THREADS) cg_resid_kernel(CgArgs a) {
+    if (ld_cg(&a.st->active_count) == 0) return;
+    constexpr int G = (S == 1) ? 4 : S / 2;
+    __shared__ double sm[32][S + 1];
+    const int r = threadIdx.x / G, g = threadIdx.x % G;
+    const int64_t R = (int64_t)blockIdx.x * 32 + r;
+    const CgState *cs = a.st;
+    double v0 = 0.0, v1 = 0.0;
+    if (R < a.n) {
+        if constexpr (S == 1) {
+            if (g == 0) {
+                double rv = a.r[R];
+                if (cs->active[0]) rv = fma(-cs->alpha[0], a.q[R], rv);
+                a.r[R] = rv;
+                v0 = rv * rv;
+            }
+        } else {
+            const int m = 2 * g;
+            double2 rv = reinterpret_cast<const double2 *>(a.r)[R * G + g];
+            const double2 qv = reinterpret_cast<const double2 *>(a.q)[R * G + g];
+            if (cs->active[m]) rv.x = fma(-cs->alpha[m], qv.x, rv.x);
+            if (cs->active[m + 1]) rv.y = fma(-cs->alpha[m + 1], qv.y, rv.y);
+            reinterpret_cast<double2 *>(a.r)[R * G + g] = rv;
+            v0 = rv.x * rv.x;
+            v1 = rv.y * rv.y;
+        }
+    }
+    chunk_tree<S>(sm, v0, v1, r, g, a.t1, blockIdx.x, 0);
+    if (!dot_tree_propagate(a.t1, blockIdx.x)) return;
+    if (threadIdx.x != 0) return;
+    const double *top = a.t1.buf[a.t1.levels];
+    CgState *st = a.st;
+    if (a.coupled) {
+        double rn = 0.0, ro = 0.0;
+        for (int e = 0; e < S; ++e) { rn += ld_cg(top + e); ro += st->rho[e]; }
+        const bool conv = sqrt(rn) <= a.tol * st->bnorm_all;
+        for (int e = 0; e < S; ++e) {
+            if (st->active[e]) {
+                st->iters[e] += 1;
+                st->updx[e] = 1;
+                if (conv) { st->active[e] = 0; st->status[e] = ENS_OK; }
+                else if (st->iters[e] >= a.max_iter) { st->active[e] = 0; st->status[e] = ENS_ERR_NOT_CONVERGED; }
+                else st->beta[e] = rn / ro;
+            }
+            st->rho[e] = ld_cg(top + e);
+        }
+    } else {
+        for (int e = 0; e < S; ++e) {
+            if (!st->active[e]) continue;
+            const double rn = ld_cg(top + e);
+            st->iters[e] += 1;
+            st->updx[e] = 1;
+            if (sqrt(rn) <= a.tol * st->bnorm[e]) { st->active[e] = 0; st->status[e] = ENS_OK; }
+            else if (st->iters[e] >= a.max_iter) { st->active[e] = 0; st->status[e] = ENS_ERR_NOT_CONVERGED; }
+            else st->beta[e] = rn / st->rho[e];
+            st->rho[e] = rn;
+        }
+    }
+    int ac = 0, ux = 0;
+    for (int e = 0; e < S; ++e) { ac += st->active[e]; ux += st->updx[e]; }
+    st->active_count = ac;
+    st->updx_any = ux;
+    __threadfence();
+}
+
+// ------------------------------------------------------------------ K3
+template <int S>
+__global__ void __launch_bounds__(RowMap<S>::THREADS) cg_update_kernel(CgArgs a) {
+    if (ld_cg(&a.st->updx_any) == 0) return;
+    constexpr int G = (S == 1) ? 4 : S / 2;
+    const int r = threadIdx.x / G, g = threadIdx.x % G;
+    const int64_t R = (int64_t)blockIdx.x * 32 + r;
+    CgState *st = a.st;
+    if (R < a.n) {
+        if constexpr (S == 1) {
+            if (g == 0) {
+                const double pv = a.p[R];
+                if (st->zerox[0]) a.x[R] = 0.0;
+                else if (st->updx[0]) a.x[R] = fma(st->alpha[0], pv, a.x[R]);
+                if (st->active[0]) a.p[R] = fma(st->beta[0], pv, a.r[R]);
+            }
+        } else {
+            const int m = 2 * g;
+            const double2 pv = reinterpret_cast<const double2 *>(a.p)[R * G + g];
+            double2 xv = reinterpret_cast<const double2 *>(a.x)[R * G + g];
+            const double2 rv = reinterpret_cast<const double2 *>(a.r)[R * G + g];
+            if (st->zerox[m]) xv.x = 0.0; else if (st->updx[m]) xv.x = fma(st->alpha[m], pv.x, xv.x);
+            if (st->zerox[m + 1]) xv.y = 0.0; else if (st->updx[m + 1]) xv.y = fma(st->alpha[m + 1], pv.y, xv.y);
+            reinterpret_cast<double2 *>(a.x)[R * G + g] = xv;
+            double2 pn = pv;
+            if (st->active[m]) pn.x = fma(st->beta[m], pv.x, rv.x);
+            if (st->active[m + 1]) pn.y = fma(st->beta[m + 1], pv.y, rv.y);
+            reinterpret_cast<double2 *>(a.p)[R * G + g] = pn;
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        const int old = atomicAdd(&st->k3_arrive, 1);
+        if (old == (int)gridDim.x - 1) {
+            for (int e = 0; e < S; ++e) { st->updx[e] = 0; st->zerox[e] = 0; }
+            st->updx_any = 0;
+            st->k3_arrive = 0;
+            __threadfence();
+        }
+    }
+}
+
+// ------------------------------------------------------------------ KF
+template <int S>
+__global__ void __launch_bounds__(RowMap<S>::THREADS) cg_final_kernel(CgArgs a) {
+    constexpr int G = RowMap<S>::G;
+    __shared__ double sm[32][S + 1];
+    const int r = threadIdx.x / G, g = threadIdx.x % G;
+    const int64_t R = (int64_t)blockIdx.x * 32 + r;
+    double v0 = 0.0, v1 = 0.0;
+    if constexpr (S == 1) {
+        const double ax = row_spmv1<double>(a.row_map, a.col, a.vals, a.x, R, g, R < a.n);
+        if (R < a.n) { const double res = a.b[R] - ax; v0 = res * res; }
+    } else if (R < a.n) {
+        const double2 ax = row_spmv2<S, double>(a.row_map, a.col, a.vals, a.x, R, g);
+        const double2 bv = reinterpret_cast<const double2 *>(a.b)[R * G + g];
+        const double rx = bv.x - ax.x, ry = bv.y - ax.y;
+        v0 = rx * rx;
+        v1 = ry * ry;
+    }
+    chunk_tree<S>(sm, v0, v1, r, g, a.t1, blockIdx.x, 0);
+    if (!dot_tree_propagate(a.t1, blockIdx.x)) return;
+    if (threadIdx.x != 0) return;
+    const double *top = a.t1.buf[a.t1.levels];
+    for (int e = 0; e < S; ++e) {
+        const double bn = a.st->bnorm[e];
+        a.st->relres[e] = (bn > 0.0) ? sqrt(ld_cg(top + e)) / bn : 0.0;
+    }
+    __threadfence();
+}
+
+// ------------------------------------------------------------ host side
+static size_t align256(size_t x) { return (x + 255) / 256 * 256; }
+
+static size_t cg_bytes(int64_t n, int s) {
+    return align256(sizeof(CgState)) + 3 * align256(sizeof(double) * (size_t)n * s) +
+           dot_tree_bytes(n, s) + dot_tree_bytes(n, 2 * s);
+}
+
+template <int S>
+struct CgKernels {
+    static void init(const CgArgs &a, unsigned grid, cudaStream_t st) {
+        cg_init_kernel<S><<<grid, RowMap<S>::THREADS, 0, st>>>(a);
+    }
+    static void spmv(const CgArgs &a, unsigned grid, cudaStream_t st) {
+        cg_spmv_kernel<S><<<grid, RowMap<S>::THREADS, 0, st>>>(a);
+    }
+    static void resid(const CgArgs &a, unsigned grid, cudaStream_t st) {
+        cg_resid_kernel<S><<<grid, RowMap<S>::THREADS, 0, st>>>(a);
+    }
+    static void update(const CgArgs &a, unsigned grid, cudaStream_t st) {
+        cg_update_kernel<S><<<grid, RowMap<S>::THREADS, 0, st>>>(a);
+    }
+    static void final_(const CgArgs &a, unsigned grid, cudaStream_t st) {
+        cg_final_kernel<S><<<grid, RowMap<S>::THREADS, 0, st>>>(a);
+    }
+};
+
+struct CgHostOut {
+    int32_t *iters;
+    double *relres;
+    int32_t *status;
+    ens_cg_stats *stats;
+};
+
+template <int S>
+static int cg_run(const ens_graph *g, const double *vals, const double *b, double *x, double tol,
+                  int max_iter, int flags, int check_every, void *work, CgHostOut out,
+                  cudaStream_t st) {
+    using K = CgKernels<S>;
+    const int64_t n = g->num_rows;
+    char *w = static_cast<char *>(work);
+    CgArgs a;
+    a.n = g->num_rows;
+    a.row_map = g->row_map;
+    a.col = g->col_entry;
+    a.vals = vals;
+    a.b = b;
+    a.x = x;
+    a.st = reinterpret_cast<CgState *>(w);
+    w += align256(sizeof(CgState));
+    a.r = reinterpret_cast<double *>(w); w += align256(sizeof(double) * (size_t)n * S);
+    a.p = reinterpret_cast<double *>(w); w += align256(sizeof(double) * (size_t)n * S);
+    a.q = reinterpret_cast<double *>(w); w += align256(sizeof(double) * (size_t)n * S);
+    dot_tree_layout(&a.t1, n, S, w);
+    w += dot_tree_bytes(n, S);
+    dot_tree_layout(&a.t2, n, 2 * S, w);
+    a.tol = tol;
+    a.max_iter = max_iter;
+    a.coupled = (flags & ENS_CG_COUPLED) ? 1 : 0;
+    const unsigned grid = (unsigned)a.t1.count[1];
+    int rc;
+    if ((rc = dot_tree_clear(a.t1, st))) return rc;
+    if ((rc = dot_tree_clear(a.t2, st))) return rc;
+    ENS_CUDA_TRY(cudaMemsetAsync(a.st, 0, sizeof(CgState), st));
+
+    const bool timing = (flags & ENS_CG_TIME_SPMV) != 0;
+    const bool use_graph = (flags & ENS_CG_GRAPH) != 0 && !timing;
+    int launches = 0, polls = 0;
+    std::vector<cudaEvent_t> ev;
+    std::vector<float> spmv_ms;
+    if (timing) {
+        ev.resize(2 * (size_t)check_every);
+        for (auto &e : ev) ENS_CUDA_TRY(cudaEventCreate(&e));
+    }
+    auto destroy_events = [&]() { for (auto &e : ev) cudaEventDestroy(e); };
+
+    K::init(a, grid, st);
+    ++launches;
+    ENS_LAUNCH_CHECK("cg_init_kernel");
+
+    cudaGraphExec_t gexec = nullptr;
+    cudaGraph_t graph = nullptr;
+    if (use_graph) {
+        ENS_CUDA_TRY(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+        for (int i = 0; i < check_every; ++i) {
+            K::spmv(a, grid, st);
+            K::resid(a, grid, st);
+            K::update(a, grid, st);
+        }
+        cudaError_t ce = cudaStreamEndCapture(st, &graph);
+        if (ce != cudaSuccess) return cuda_fail(ce, "cudaStreamEndCapture");
+        ce = cudaGraphInstantiate(&gexec, graph, 0);
+        if (ce != cudaSuccess) { cudaGraphDestroy(graph); return cuda_fail(ce, "cudaGraphInstantiate"); }
+    }
+
+    int32_t flags_h[2];
+    int iter_blocks = 0;
+    const int max_blocks = max_iter / check_every + 3;
+    rc = ENS_OK;
+    while (iter_blocks < max_blocks) {
+        if (use_graph) {
+            cudaError_t ce = cudaGraphLaunch(gexec, st);
+            if (ce != cudaSuccess) { rc = cuda_fail(ce, "cudaGraphLaunch"); break; }
+        } else {
+            for (int i = 0; i < check_every; ++i) {
+                if (timing) cudaEventRecord(ev[2 * i], st);
+                K::spmv(a, grid, st);
+                if (timing) cudaEventRecord(ev[2 * i + 1], st);
+                K::resid(a, grid, st);
+                K::update(a, grid, st);
+            }
+        }
+        launches += 3 * check_every;
+        ++iter_blocks;
+        cudaError_t ce = cudaGetLastError();
+        if (ce != cudaSuccess) { rc = cuda_fail(ce, "cg iteration launch"); break; }
+        ce = cudaMemcpyAsync(flags_h, &a.st->active_count, 2 * sizeof(int32_t), cudaMemcpyDeviceToHost, st);
+        if (ce == cudaSuccess) ce = cudaStreamSynchronize(st);
+        if (ce != cudaSuccess) { rc = cuda_fail(ce, "cg convergence poll"); break; }
+        ++polls;
+        if (timing) {
+            for (int i = 0; i < check_every; ++i) {
+                float ms = 0.f;
+                cudaEventElapsedTime(&ms, ev[2 * i], ev[2 * i + 1]);
+                spmv_ms.push_back(ms);
+            }
+        }
+        if (flags_h[0] == 0 && flags_h[1] == 0) break;
+    }
+    if (gexec) cudaGraphExecDestroy(gexec);
+    if (graph) cudaGraphDestroy(graph);
+    if (rc != ENS_OK) { destroy_events(); return rc; }
+
+    K::final_(a, grid, st);
+    ++launches;
+    ENS_LAUNCH_CHECK("cg_final_kernel");
+    CgState hs;
+    ENS_CUDA_TRY(cudaMemcpyAsync(&hs, a.st, sizeof(CgState), cudaMemcpyDeviceToHost, st));
+    ENS_CUDA_TRY(cudaStreamSynchronize(st));
+    destroy_events();
+    int maxit = 0, first_bad = ENS_OK;
+    for (int e = 0; e < S; ++e) {
+        if (out.iters) out.iters[e] = hs.iters[e];
+        if (out.relres) out.relres[e] = hs.relres[e];
+        if (out.status) out.status[e] = hs.status[e];
+        maxit = hs.iters[e] > maxit ? hs.iters[e] : maxit;
+        if (hs.status[e] != ENS_OK && first_bad == ENS_OK) first_bad = hs.status[e];
+    }
+    if (out.stats) {
+        out.stats->iterations = maxit;
+        out.stats->kernel_launches = launches;
+        out.stats->host_checks = polls;
+        out.stats->spmv_launches = 0;
+        out.stats->spmv_ms = 0.0;
+        if (timing) {
+            const int real = hs.spmv_real < (int)spmv_ms.size() ? hs.spmv_real : (int)spmv_ms.size();
+            double tot = 0.0;
+            for (int i = 0; i < real; ++i) tot += spmv_ms[i];
+            out.stats->spmv_launches = real;
+            out.stats->spmv_ms = tot;
+        }
+    }
+    if (first_bad != ENS_OK)
+        set_error("ens_cg: member status %d (%s)", first_bad, ens_status_string(first_bad));
+    return first_bad;
+}
+
+}  // namespace ens
+
+using namespace ens;
+
+extern "C" int ens_cg_workspace_size(int32_t num_rows, int s, size_t *bytes) {
+    if (num_rows < 0) return fail(ENS_ERR_ARG, "num_rows < 0");
+    if (!supported_s(s)) return fail(ENS_ERR_UNSUPPORTED, "ensemble size s=%d not in {1,4,8,16,32}", s);
+    if (!bytes) return fail(ENS_ERR_ARG, "bytes is NULL");
+    *bytes = cg_bytes(num_rows, s);
+    return ENS_OK;
+}
+
+extern "C" int ens_cg(const ens_graph *graph, int s, const double *values, const double *b,
+                      double *x, double tol, int max_iter, int flags, int check_every, void *work,
+                      size_t work_bytes, int32_t *iters_host, double *relres_host,
+                      int32_t *status_host, ens_cg_stats *stats_host, void *stream) {
+    int rc = check_graph(graph);
+    if (rc) return rc;
+    if (!supported_s(s)) return fail(ENS_ERR_UNSUPPORTED, "ensemble size s=%d not in {1,4,8,16,32}", s);
+    if (graph->num_rows == 0) return fail(ENS_ERR_ARG, "empty graph");
+    if (!values || !b || !x || !work) return fail(ENS_ERR_ARG, "NULL values/b/x/work");
+    if (!(tol >= 0.0) || max_iter < 0 || check_every < 1)
+        return fail(ENS_ERR_ARG, "tol=%g max_iter=%d check_every=%d", tol, max_iter, check_every);
+    if (!aligned16(work) || (s > 1 && (!aligned16(values) || !aligned16(b) || !aligned16(x))))
+        return fail(ENS_ERR_ALIGN, "values/b/x/work must be 16-byte aligned");
+    const size_t need = cg_bytes(graph->num_rows, s);
+    if (work_bytes < need) return fail(ENS_ERR_WORKSPACE, "cg workspace %zu < %zu bytes", work_bytes, need);
+    CgHostOut out{iters_host, relres_host, status_host, stats_host};
+    cudaStream_t st = as_stream(stream);
+    switch (s) {
+        case 1: return cg_run<1>(graph, values, b, x, tol, max_iter, flags, check_every, work, out, st);
+        case 4: return cg_run<4>(graph, values, b, x, tol, max_iter, flags, check_every, work, out, st);
+        case 8: return cg_run<8>(graph, values, b, x, tol, max_iter, flags, check_every, work, out, st);
+        case 16: return cg_run<16>(graph, values, b, x, tol, max_iter, flags, check_every, work, out, st);
+        default: return cg_run<32>(graph, values, b, x, tol, max_iter, flags, check_every, work, out, st);
+    }
+}

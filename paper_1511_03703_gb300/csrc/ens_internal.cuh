@@ -1,0 +1,147 @@
+// ens_internal.cuh -- shared device/host helpers of the CUDA library (not the oracle).
+#pragma once
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+#include <stdio.h>
+
+#include "../../include/ens.h"
+
+namespace ens {
+
+// ------------------------------------------------------------ error state
+void set_error(const char *fmt, ...);
+int fail(int status, const char *fmt, ...);
+int cuda_fail(cudaError_t err, const char *what);
+
+#define ENS_CUDA_TRY(expr)                                        \
+    do {                                                          \
+        cudaError_t _e = (expr);                                  \
+        if (_e != cudaSuccess) return ::ens::cuda_fail(_e, #expr); \
+    } while (0)
+
+#define ENS_LAUNCH_CHECK(what)                                     \
+    do {                                                           \
+        cudaError_t _e = cudaGetLastError();                       \
+        if (_e != cudaSuccess) return ::ens::cuda_fail(_e, what);  \
+    } while (0)
+
+inline cudaStream_t as_stream(void *s) { return reinterpret_cast<cudaStream_t>(s); }
+inline bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+inline bool supported_s(int s) { return s == 1 || s == 4 || s == 8 || s == 16 || s == 32; }
+
+int check_graph(const ens_graph *g);
+
+// -------------------------------------------------------- cache-hinted loads
+// streaming loads for data read exactly once (matrix values): evict-first
+__device__ __forceinline__ double2 ld_stream(const double2 *p) {
+    double2 v;
+    asm volatile("ld.global.cs.v2.f64 {%0, %1}, [%2];" : "=d"(v.x), "=d"(v.y) : "l"(p));
+    return v;
+}
+__device__ __forceinline__ double ld_stream(const double *p) {
+    double v;
+    asm volatile("ld.global.cs.f64 %0, [%1];" : "=d"(v) : "l"(p));
+    return v;
+}
+__device__ __forceinline__ float2 ld_stream(const float2 *p) {
+    float2 v;
+    asm volatile("ld.global.cs.v2.f32 {%0, %1}, [%2];" : "=f"(v.x), "=f"(v.y) : "l"(p));
+    return v;
+}
+__device__ __forceinline__ float ld_stream(const float *p) {
+    float v;
+    asm volatile("ld.global.cs.f32 %0, [%1];" : "=f"(v) : "l"(p));
+    return v;
+}
+__device__ __forceinline__ uint32_t ld_stream_u32(const void *p) {
+    uint32_t v;
+    asm volatile("ld.global.cs.u32 %0, [%1];" : "=r"(v) : "l"(p));
+    return v;
+}
+__device__ __forceinline__ uint16_t ld_stream_u16(const void *p) {
+    uint16_t v;
+    asm volatile("ld.global.cs.u16 %0, [%1];" : "=h"(v) : "l"(p));
+    return v;
+}
+// L2-coherent load that bypasses L1 (reads data written by other CTAs of the
+// same kernel after a fence)
+__device__ __forceinline__ double ld_cg(const double *p) {
+    double v;
+    asm volatile("ld.global.cg.f64 %0, [%1];" : "=d"(v) : "l"(p));
+    return v;
+}
+__device__ __forceinline__ int ld_cg(const int *p) {
+    int v;
+    asm volatile("ld.global.cg.s32 %0, [%1];" : "=r"(v) : "l"(p));
+    return v;
+}
+
+// ------------------------------------------------ deterministic dot trees
+// Canonical per-member reduction shared by every dot product of the library
+// (ens_dot and the CG kernels).  Level 0: one product per row.  Level 1: the
+// 32 rows of a chunk [32c, 32c+32) are combined by the butterfly
+//     t_i <- t_i + t_{i^16}, then ^8, ^4, ^2, ^1
+// (rows past the end contribute 0).  Level l+1 combines 32 consecutive level-l
+// results the same way, until one value per member remains.  The order
+// depends only on the row index, never on s or on the launch shape, so a
+// member's dot is bitwise the same at every ensemble size.
+constexpr int kTreeMaxLevels = 8;
+
+struct DotTree {
+    int levels;                       // number of levels above level 0 (>= 1)
+    int width;                        // doubles per item = ndots * s
+    int64_t count[kTreeMaxLevels];    // items at level l (level 1 = chunks)
+    double *buf[kTreeMaxLevels];      // buf[l][item*width + w]
+    int *counter[kTreeMaxLevels];     // counter[l][g]: arrivals of level-l items in group g
+};
+
+__device__ __forceinline__ double warp_tree32(double v) {
+    v += __shfl_xor_sync(0xffffffffu, v, 16);
+    v += __shfl_xor_sync(0xffffffffu, v, 8);
+    v += __shfl_xor_sync(0xffffffffu, v, 4);
+    v += __shfl_xor_sync(0xffffffffu, v, 2);
+    v += __shfl_xor_sync(0xffffffffu, v, 1);
+    return v;
+}
+
+// Host: lay a DotTree out in caller scratch; returns bytes used (align 256).
+size_t dot_tree_bytes(int64_t n_rows, int width);
+void dot_tree_layout(DotTree *t, int64_t n_rows, int width, void *base);
+// zero all arrival counters of a tree (the tree's kernels self-reset them)
+int dot_tree_clear(const DotTree &t, cudaStream_t st);
+
+// Device: called by all threads of a CTA after it wrote level-1 item `item`
+// (buf[1][item*width ...]) with plain stores.  Propagates through the levels;
+// returns true in the single CTA that produced the top value (buf[levels][0..width)).
+__device__ __forceinline__ bool dot_tree_propagate(const DotTree &t, int64_t item) {
+    __shared__ int s_last;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
+    for (int l = 1; l < t.levels; ++l) {
+        const int64_t g = item >> 5;
+        const int cnt = (int)min((int64_t)32, t.count[l] - (g << 5));
+        __threadfence();
+        __syncthreads();
+        if (tid == 0) {
+            int old = atomicAdd(&t.counter[l][g], 1);
+            s_last = (old == cnt - 1);
+            if (s_last) t.counter[l][g] = 0;  // self-reset for the next launch
+        }
+        __syncthreads();
+        if (!s_last) return false;
+        __threadfence();
+        const double *src = t.buf[l];
+        double *dst = t.buf[l + 1];
+        for (int w = warp; w < t.width; w += nwarps) {
+            double v = (lane < cnt) ? ld_cg(src + ((g << 5) + lane) * t.width + w) : 0.0;
+            v = warp_tree32(v);
+            if (lane == 0) dst[g * t.width + w] = v;
+        }
+        item = g;
+    }
+    __threadfence();
+    __syncthreads();
+    return true;
+}
+
+}  // namespace ens

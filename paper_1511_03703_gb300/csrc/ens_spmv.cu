@@ -1,0 +1,147 @@
+// ens_spmv.cu -- ens_spmv (commuted-layout SpMV, Fig. 5) and ens_dot (Sect. 3.4).
+#include "ens_spmv.cuh"
+
+namespace ens {
+
+template <int S, typename V>
+__global__ void __launch_bounds__(RowMap<S>::THREADS) spmv_kernel(
+    int32_t n, const int32_t *__restrict__ row_map, const int32_t *__restrict__ col,
+    const V *__restrict__ vals, const double *__restrict__ x, double *__restrict__ y) {
+    constexpr int G = RowMap<S>::G;
+    const int r = threadIdx.x / G, g = threadIdx.x % G;
+    const int64_t R = (int64_t)blockIdx.x * 32 + r;
+    if constexpr (S == 1) {
+        const double v = row_spmv1<V>(row_map, col, vals, x, R, g, R < n);
+        if (R < n && g == 0) y[R] = v;
+    } else {
+        if (R >= n) return;
+        const double2 v = row_spmv2<S, V>(row_map, col, vals, x, R, g);
+        reinterpret_cast<double2 *>(y)[R * G + g] = v;
+    }
+}
+
+template <int S, typename V>
+static int spmv_s(const ens_graph *g, const V *vals, const double *x, double *y, cudaStream_t st) {
+    const int64_t chunks = ((int64_t)g->num_rows + 31) / 32;
+    if (chunks == 0) return ENS_OK;
+    spmv_kernel<S, V><<<(unsigned)chunks, RowMap<S>::THREADS, 0, st>>>(g->num_rows, g->row_map,
+                                                                       g->col_entry, vals, x, y);
+    ENS_LAUNCH_CHECK("spmv_kernel");
+    return ENS_OK;
+}
+
+template <typename V>
+static int spmv_dispatch(const ens_graph *g, int s, const void *vals, const double *x, double *y,
+                         cudaStream_t st) {
+    const V *v = static_cast<const V *>(vals);
+    switch (s) {
+        case 1: return spmv_s<1, V>(g, v, x, y, st);
+        case 4: return spmv_s<4, V>(g, v, x, y, st);
+        case 8: return spmv_s<8, V>(g, v, x, y, st);
+        case 16: return spmv_s<16, V>(g, v, x, y, st);
+        default: return spmv_s<32, V>(g, v, x, y, st);
+    }
+}
+
+// ------------------------------------------------------------------ dot
+// one 32-row chunk per CTA, G = max(s/2, 1) threads per row
+template <int S>
+__global__ void __launch_bounds__(32 * (S == 1 ? 1 : S / 2)) dot_kernel(
+    int64_t n, const double *__restrict__ u, const double *__restrict__ v, DotTree t,
+    double *__restrict__ out) {
+    constexpr int G = (S == 1) ? 1 : S / 2;
+    __shared__ double sm[32][S + 1];
+    const int r = threadIdx.x / G, g = threadIdx.x % G;
+    const int64_t R = (int64_t)blockIdx.x * 32 + r;
+    double p0 = 0.0, p1 = 0.0;
+    if (R < n) {
+        if constexpr (S == 1) {
+            p0 = u[R] * v[R];
+        } else {
+            const double2 a = reinterpret_cast<const double2 *>(u)[R * G + g];
+            const double2 b = reinterpret_cast<const double2 *>(v)[R * G + g];
+            p0 = a.x * b.x;
+            p1 = a.y * b.y;
+        }
+    }
+    if constexpr (S == 1) {
+        sm[r][0] = p0;
+    } else {
+        sm[r][2 * g] = p0;
+        sm[r][2 * g + 1] = p1;
+    }
+    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int e = warp; e < S; e += nw) {
+        const double w = warp_tree32(sm[lane][e]);
+        if (lane == 0) t.buf[1][blockIdx.x * (int64_t)S + e] = w;
+    }
+    if (dot_tree_propagate(t, blockIdx.x)) {
+        for (int e = threadIdx.x; e < S; e += blockDim.x) out[e] = ld_cg(t.buf[t.levels] + e);
+    }
+}
+
+template <int S>
+static int dot_s(int64_t n, const double *u, const double *v, double *out, const DotTree &t,
+                 cudaStream_t st) {
+    const int64_t chunks = t.count[1];
+    dot_kernel<S><<<(unsigned)chunks, 32 * (S == 1 ? 1 : S / 2), 0, st>>>(n, u, v, t, out);
+    ENS_LAUNCH_CHECK("dot_kernel");
+    return ENS_OK;
+}
+
+int dot_launch(int64_t n, int s, const double *u, const double *v, double *out, const DotTree &t,
+               cudaStream_t st) {
+    switch (s) {
+        case 1: return dot_s<1>(n, u, v, out, t, st);
+        case 4: return dot_s<4>(n, u, v, out, t, st);
+        case 8: return dot_s<8>(n, u, v, out, t, st);
+        case 16: return dot_s<16>(n, u, v, out, t, st);
+        default: return dot_s<32>(n, u, v, out, t, st);
+    }
+}
+
+}  // namespace ens
+
+using namespace ens;
+
+extern "C" int ens_spmv(const ens_graph *graph, int s, int dtype, const void *values,
+                        const double *x, double *y, void *stream) {
+    int rc = check_graph(graph);
+    if (rc) return rc;
+    if (!supported_s(s)) return fail(ENS_ERR_UNSUPPORTED, "ensemble size s=%d not in {1,4,8,16,32}", s);
+    if (graph->num_rows > 0 && (!values || !x || !y)) return fail(ENS_ERR_ARG, "NULL values/x/y");
+    if (s > 1 && (!aligned16(values) || !aligned16(x) || !aligned16(y)))
+        return fail(ENS_ERR_ALIGN, "values/x/y must be 16-byte aligned for s > 1");
+    cudaStream_t st = as_stream(stream);
+    switch (dtype) {
+        case ENS_F64: return spmv_dispatch<double>(graph, s, values, x, y, st);
+        case ENS_F32: return spmv_dispatch<float>(graph, s, values, x, y, st);
+        case ENS_BF16: return spmv_dispatch<__nv_bfloat16>(graph, s, values, x, y, st);
+        default: return fail(ENS_ERR_UNSUPPORTED, "dtype %d", dtype);
+    }
+}
+
+extern "C" int ens_dot_workspace_size(int64_t n, int s, size_t *bytes) {
+    if (n < 0) return fail(ENS_ERR_ARG, "n=%lld < 0", (long long)n);
+    if (!supported_s(s)) return fail(ENS_ERR_UNSUPPORTED, "ensemble size s=%d not in {1,4,8,16,32}", s);
+    if (!bytes) return fail(ENS_ERR_ARG, "bytes is NULL");
+    *bytes = dot_tree_bytes(n, s);
+    return ENS_OK;
+}
+
+extern "C" int ens_dot(int64_t n, int s, const double *u, const double *v, double *out,
+                       void *work, size_t work_bytes, void *stream) {
+    size_t need;
+    int rc = ens_dot_workspace_size(n, s, &need);
+    if (rc) return rc;
+    if (!out || (n > 0 && (!u || !v))) return fail(ENS_ERR_ARG, "NULL u/v/out");
+    if (!work || work_bytes < need) return fail(ENS_ERR_WORKSPACE, "dot workspace %zu < %zu bytes", work_bytes, need);
+    if (!aligned16(work) || (s > 1 && (!aligned16(u) || !aligned16(v))))
+        return fail(ENS_ERR_ALIGN, "u/v/work must be 16-byte aligned");
+    cudaStream_t st = as_stream(stream);
+    DotTree t;
+    dot_tree_layout(&t, n, s, work);
+    if ((rc = dot_tree_clear(t, st))) return rc;
+    return dot_launch(n, s, u, v, out, t, st);
+}

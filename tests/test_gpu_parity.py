@@ -1,0 +1,346 @@
+"""GPU parity: the CUDA library (through its C ABI) against the CPU oracle.
+
+Tolerances (north star, and the arithmetic they follow from):
+  graph, ElemGraph, boundary mask, iteration counts on small meshes: exact
+  KL eigenvalues: 1e-14 relative; coefficient at Gauss points: 1e-14
+  assembled values: |d| <= 1e-13 * A_II (row diagonal; off-diagonal entries
+      of a constant-coefficient row cancel to ~0 so a relative test is void)
+  SpMV: |d y_i| <= 1e-12 * (|A| |x|)_i componentwise
+  dot: |d| <= 1e-13 * sum |u v| against exactly rounded summation (fsum)
+  CG: ||x - x_oracle|| / ||x_oracle|| <= 1e-8; if the iteration counts differ
+      by one (stopping test decided by rounding), both are re-run for the same
+      fixed number of iterations and must agree to 1e-10.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+import paper_1511_03703_gb300 as E
+from paper_1511_03703_gb300 import inputs
+from helpers import gpu, oracle_members, spmv_bound, to_dev, to_np
+
+pytestmark = pytest.mark.gpu
+S_ALL = [1, 4, 8, 16, 32]
+
+
+@pytest.fixture(scope="module")
+def torch():
+    import torch as T
+    assert T.cuda.is_available(), "GPU tests need a CUDA device"
+    E.lib()
+    return T
+
+
+def ens_cols(flat, s):
+    return np.asarray(flat).reshape(-1, s)
+
+
+# ---------------------------------------------------------------- A1 graph
+@pytest.mark.parametrize("N", [1, 2, 3, 8, 13, 16])
+def test_graph_bit_exact(torch, N):
+    n, nnz, nc = E.mesh_sizes(N)
+    rm = torch.empty(n + 1, dtype=torch.int32, device=gpu())
+    col = torch.empty(nnz, dtype=torch.int32, device=gpu())
+    eg = torch.empty(nc * 64, dtype=torch.int32, device=gpu())
+    bm = torch.empty(n, dtype=torch.uint8, device=gpu())
+    E.graph_build(N, rm, col, eg, bm)
+    orm, ocol = O.graph(N)
+    assert np.array_equal(to_np(rm), orm)
+    assert np.array_equal(to_np(col), ocol)
+    assert np.array_equal(to_np(eg), O.elem_graph(N, orm, ocol))
+    assert np.array_equal(to_np(bm), O.bmask(N))
+
+
+# ------------------------------------------------------------------- A2 KL
+@pytest.mark.parametrize("N,M", [(8, 3), (8, 10), (5, 17), (64, 10)])
+def test_kl_setup_matches_oracle(torch, N, M):
+    tab = torch.empty(E.kl_table_size(N, M), dtype=torch.float64, device=gpu())
+    lam, pqr = E.kl_setup(N, M, 1.0, tab)
+    opqr, olam = O.kl_modes(M)
+    assert pqr == opqr.tolist()
+    assert np.max(np.abs(np.array(lam) - olam) / olam) < 1e-14
+    T = to_np(tab)[: 3 * M * 2 * N].reshape(3, M, 2 * N)
+    xi = inputs.kl_samples(5, 0, 1, M)[0]
+    a_or = O.kl_coeff_qp(N, M, xi)
+    t = np.arange(N)
+    for q in range(8):
+        tx, ty, tz = 2 * t + (q & 1), 2 * t + ((q >> 1) & 1), 2 * t + ((q >> 2) & 1)
+        kap = (T[0][:, tx][:, None, None, :] * T[1][:, ty][:, None, :, None] *
+               T[2][:, tz][:, :, None, None])          # [k, ck, cj, ci]
+        a = 1.0 + 0.1 * np.tensordot(xi, kap, axes=(0, 0)).reshape(-1)
+        assert np.max(np.abs(a - a_or[:, q])) < 1e-14
+
+
+# ------------------------------------------------------------- A3 assembly
+def diag_of(row_map, col, vals):
+    n = len(row_map) - 1
+    rows = np.repeat(np.arange(n), np.diff(row_map))
+    d = np.zeros(n)
+    sel = col == rows
+    d[rows[sel]] = vals[sel]
+    return d[rows]
+
+
+@pytest.mark.parametrize("N,M,s", [(8, 3, 4), (5, 10, 1), (5, 10, 4), (5, 10, 8), (5, 10, 16),
+                                   (5, 10, 32), (13, 10, 8)])
+def test_assembly_matches_oracle(torch, N, M, s):
+    mesh = E.Mesh(N, M)
+    xs = inputs.kl_samples(100 + N, 0, s, M)
+    values, b = mesh.assemble(s, to_dev(inputs.ensemble_layout(xs)))
+    V, B = ens_cols(to_np(values), s), ens_cols(to_np(b), s)
+    rm, col, ov, ob = oracle_members(N, M, xs)
+    for e in range(s):
+        tol = 1e-13 * np.abs(diag_of(rm, col, ov[e]))
+        assert np.all(np.abs(V[:, e] - ov[e]) <= tol), e
+        assert np.max(np.abs(B[:, e] - ob[e])) <= 1e-13 * np.max(np.abs(ob[e]))
+
+
+# ------------------------------------------------------------------ A4 SpMV
+@pytest.mark.parametrize("N", [3, 8, 13])
+@pytest.mark.parametrize("s", S_ALL)
+@pytest.mark.parametrize("dtype", ["float64", "float32", "bfloat16"])
+def test_spmv_matches_oracle(torch, N, s, dtype):
+    M = 10
+    xs = inputs.kl_samples(200 + N, 0, min(s, 4), M)
+    rm, col, ov, _ = oracle_members(N, M, xs)
+    ov = [ov[e % len(ov)] for e in range(s)]
+    n = len(rm) - 1
+    xm = [inputs.random_vector(300 + e, n) for e in range(s)]
+    vt = torch.from_numpy(O.to_ensemble(ov)).to(getattr(torch, dtype))
+    vq = [vt.reshape(-1, s)[:, e].double().numpy() for e in range(s)]   # values as stored
+    y = torch.empty(n * s, dtype=torch.float64, device=gpu())
+    graph = E.Graph(to_dev(rm), to_dev(col))
+    E.spmv(graph, s, vt.to(gpu()), to_dev(O.to_ensemble(xm)), y)
+    Y = ens_cols(to_np(y), s)
+    for e in range(s):
+        ref = O.spmv(rm, col, vq[e], xm[e])
+        assert np.all(np.abs(Y[:, e] - ref) <= spmv_bound(rm, col, vq[e], xm[e])), e
+
+
+def test_spmv_s_invariant_bitwise(torch):
+    N, M = 9, 10
+    mesh = E.Mesh(N, M)
+    xs = inputs.kl_samples(41, 0, 32, M)
+    xm = [inputs.random_vector(500 + e, mesh.n) for e in range(32)]
+    ref = None
+    for s in S_ALL:
+        vals, _ = mesh.assemble(s, to_dev(inputs.ensemble_layout(xs[:s])))
+        y = torch.empty(mesh.n * s, dtype=torch.float64, device=gpu())
+        E.spmv(mesh.graph, s, vals, to_dev(O.to_ensemble(xm[:s])), y)
+        Y = ens_cols(to_np(y), s)
+        if ref is None:
+            ref = Y[:, 0].copy()
+        assert np.array_equal(Y[:, 0], ref), s
+
+
+# ------------------------------------------------------------------- A5 dot
+@pytest.mark.parametrize("n", [1, 31, 32, 33, 1025, 40000])
+@pytest.mark.parametrize("s", S_ALL)
+def test_dot_matches_exact_sum(torch, n, s):
+    U = [inputs.random_vector(600 + e, n) for e in range(s)]
+    V = [inputs.random_vector(700 + e, n, -2.0, 3.0) for e in range(s)]
+    out = torch.empty(s, dtype=torch.float64, device=gpu())
+    work = torch.empty(E.dot_workspace_size(n, s), dtype=torch.uint8, device=gpu())
+    E.dot(n, s, to_dev(O.to_ensemble(U)), to_dev(O.to_ensemble(V)), out, work)
+    got = to_np(out)
+    for e in range(s):
+        prod = U[e] * V[e]
+        assert abs(got[e] - math.fsum(prod.tolist())) <= 1e-13 * np.sum(np.abs(prod)), e
+    # repeated call reuses the self-resetting counters
+    E.dot(n, s, to_dev(O.to_ensemble(U)), to_dev(O.to_ensemble(V)), out, work)
+    assert np.array_equal(to_np(out), got)
+
+
+def test_dot_s_invariant_bitwise(torch):
+    n = 10007
+    U = [inputs.random_vector(800 + e, n) for e in range(32)]
+    ref = None
+    for s in S_ALL:
+        out = torch.empty(s, dtype=torch.float64, device=gpu())
+        work = torch.empty(E.dot_workspace_size(n, s), dtype=torch.uint8, device=gpu())
+        u = to_dev(O.to_ensemble(U[:s]))
+        E.dot(n, s, u, u, out, work)
+        v = to_np(out)[0]
+        ref = v if ref is None else ref
+        assert v == ref, s
+
+
+# -------------------------------------------------------------------- A6 CG
+def gpu_solve(mesh, xs, tol, max_iter=10000, flags=0, x0=None, check_every=8):
+    import torch
+    s = xs.shape[0]
+    vals, b = mesh.assemble(s, to_dev(inputs.ensemble_layout(xs)))
+    x = torch.zeros(mesh.n * s, dtype=torch.float64, device=gpu()) if x0 is None else x0.clone()
+    work = torch.empty(E.cg_workspace_size(mesh.n, s), dtype=torch.uint8, device=gpu())
+    it, rr, st, stats = E.cg(mesh.graph, s, vals, b, x, tol, max_iter, work, flags=flags,
+                             check_every=check_every)
+    return ens_cols(to_np(x), s), it, rr, st, stats
+
+
+def compare_cg(mesh, xs, tol, xg, itg):
+    rm, col, ov, ob = oracle_members(mesh.N, mesh.M, xs)
+    for e in range(xs.shape[0]):
+        xo, ito, rro, sto = O.cg(rm, col, ov[e], ob[e], tol=tol)
+        assert sto == 0
+        assert abs(itg[e] - ito) <= 1, (e, itg[e], ito)
+        err = np.linalg.norm(xg[:, e] - xo) / np.linalg.norm(xo)
+        if itg[e] == ito:
+            assert err <= 1e-8, (e, err)
+        else:  # stopping decided by rounding: compare at a fixed iteration count
+            k = max(itg[e], ito)
+            xo2, _, _, _ = O.cg(rm, col, ov[e], ob[e], tol=0.0, max_iter=k)
+            xg2, it2, _, _, _ = gpu_solve(mesh, xs, 0.0, max_iter=k)
+            assert it2[e] == k
+            assert np.linalg.norm(xg2[:, e] - xo2) / np.linalg.norm(xo2) <= 1e-10
+
+
+def test_cg_small_workload_exact_iterations(torch):
+    # 8^3 cells, M = 3, s = 4, 4 samples, relative residual 1e-10
+    mesh = E.Mesh(8, 3)
+    xs = inputs.kl_samples(inputs.SEED_SMALL, 0, 4, 3)
+    xg, it, rr, st, _ = gpu_solve(mesh, xs, 1e-10)
+    assert st == [0, 0, 0, 0]
+    rm, col, ov, ob = oracle_members(8, 3, xs)
+    for e in range(4):
+        xo, ito, rro, sto = O.cg(rm, col, ov[e], ob[e], tol=1e-10)
+        assert it[e] == ito
+        assert np.linalg.norm(xg[:, e] - xo) / np.linalg.norm(xo) <= 1e-8
+        assert rr[e] <= 2e-10 and abs(rr[e] - rro) <= 1e-12
+        assert np.all(xg[to_np(mesh.bmask) == 1, e] == 0.0)
+
+
+@pytest.mark.parametrize("s", S_ALL)
+def test_cg_matches_oracle_ragged_mesh(torch, s):
+    mesh = E.Mesh(13, 10)   # 2744 rows: 85 full 32-row chunks and a ragged one
+    xs = inputs.kl_samples(900, 0, s, 10)
+    xg, it, rr, st, _ = gpu_solve(mesh, xs, 1e-8)
+    assert all(v == 0 for v in st)
+    compare_cg(mesh, xs, 1e-8, xg, it)
+
+
+def test_cg_identical_members_bitwise(torch):
+    mesh = E.Mesh(7, 10)
+    xs = np.repeat(inputs.kl_samples(77, 3, 1, 10), 8, axis=0)
+    vals, b = mesh.assemble(8, to_dev(inputs.ensemble_layout(xs)))
+    V = ens_cols(to_np(vals), 8)
+    assert all(np.array_equal(V[:, 0], V[:, e]) for e in range(8))
+    xg, it, rr, st, _ = gpu_solve(mesh, xs, 1e-10)
+    assert len(set(it)) == 1 and all(np.array_equal(xg[:, 0], xg[:, e]) for e in range(8))
+
+
+def test_cg_sample_result_independent_of_s_bitwise(torch):
+    mesh = E.Mesh(9, 10)
+    xs = inputs.kl_samples(4242, 0, 32, 10)
+    ref = None
+    for s in S_ALL:
+        xg, it, rr, st, _ = gpu_solve(mesh, xs[:s], 1e-9)
+        cur = (xg[:, 0].copy(), it[0], rr[0])
+        if ref is None:
+            ref = cur
+        assert np.array_equal(cur[0], ref[0]) and cur[1] == ref[1] and cur[2] == ref[2], s
+
+
+def test_cg_graph_replay_matches_direct_launches(torch):
+    mesh = E.Mesh(8, 3)
+    xs = inputs.kl_samples(inputs.SEED_SMALL, 0, 4, 3)
+    a = gpu_solve(mesh, xs, 1e-10)
+    b = gpu_solve(mesh, xs, 1e-10, flags=E.CG_GRAPH, check_every=5)
+    assert np.array_equal(a[0], b[0]) and a[1] == b[1]
+
+
+def test_cg_member_edge_cases(torch):
+    mesh = E.Mesh(6, 10)
+    s = 4
+    xs = inputs.kl_samples(31, 0, s, 10)
+    vals, b = mesh.assemble(s, to_dev(inputs.ensemble_layout(xs)))
+    ref = gpu_solve(mesh, xs, 1e-10)
+    # member 1: zero right-hand side -> x = 0 in 0 iterations; member 2: -A is
+    # negative definite -> breakdown at the first p'Ap; members 0 and 3 unaffected
+    b.view(-1, s)[:, 1] = 0.0
+    vals.view(-1, s)[:, 2] *= -1.0
+    x = torch.full((mesh.n * s,), 0.0, dtype=torch.float64, device=gpu())
+    x.view(-1, s)[:, 1] = 1.0
+    work = torch.empty(E.cg_workspace_size(mesh.n, s), dtype=torch.uint8, device=gpu())
+    it, rr, st, _ = E.cg(mesh.graph, s, vals, b, x, 1e-10, 1000, work)
+    X = ens_cols(to_np(x), s)
+    assert st == [0, 0, 6, 0] and it[1] == 0 and np.all(X[:, 1] == 0.0)
+    for e in (0, 3):
+        assert it[e] == ref[1][e] and np.array_equal(X[:, e], ref[0][:, e])
+    # iteration cap -> not converged, exactly max_iter iterations
+    xg, it, rr, st, _ = gpu_solve(mesh, xs, 1e-12, max_iter=3)
+    assert st == [5] * s and it == [3] * s
+    # resume from the capped iterate converges to the same solution
+    x0 = to_dev(np.ascontiguousarray(xg).reshape(-1))
+    xr, itr, rrr, str_, _ = gpu_solve(mesh, xs, 1e-10, x0=x0)
+    assert str_ == [0] * s
+    assert np.linalg.norm(xr - ref[0]) <= 1e-8 * np.linalg.norm(ref[0])
+
+
+def test_cg_coupled_ensemble(torch):
+    mesh = E.Mesh(8, 10)
+    xs = inputs.kl_samples(55, 0, 8, 10)
+    xd, itd, rrd, std, _ = gpu_solve(mesh, xs, 1e-8)
+    xc, itc, rrc, stc, _ = gpu_solve(mesh, xs, 1e-8, flags=E.CG_COUPLED)
+    assert stc == [0] * 8 and len(set(itc)) == 1
+    # coupled iterations are never fewer than the slowest decoupled member
+    assert itc[0] >= max(itd)
+    rm, col, ov, ob = oracle_members(8, 10, xs)
+    res2 = sum((rrc[e] * np.linalg.norm(ob[e])) ** 2 for e in range(8))
+    assert math.sqrt(res2) <= 1.01e-8 * math.sqrt(sum(np.linalg.norm(v) ** 2 for v in ob))
+    for e in range(8):
+        xo, _, _, _ = O.cg(rm, col, ov[e], ob[e], tol=1e-12)
+        assert np.linalg.norm(xc[:, e] - xo) <= 1e-6 * np.linalg.norm(xo)
+
+
+def test_error_statuses(torch):
+    mesh = E.Mesh(4, 3)
+    x = torch.zeros(mesh.n * 4 + 1, dtype=torch.float64, device=gpu())
+    y = torch.zeros(mesh.n * 4, dtype=torch.float64, device=gpu())
+    vals, b = mesh.assemble(4, to_dev(inputs.ensemble_layout(inputs.kl_samples(1, 0, 4, 3))))
+    with pytest.raises(E.EnsError) as ei:
+        E.spmv(mesh.graph, 3, vals, x[:-1], y)
+    assert ei.value.code == 2
+    with pytest.raises(E.EnsError) as ei:
+        E.spmv(mesh.graph, 4, vals, x[1:], y)
+    assert ei.value.code == 3
+    small = torch.empty(64, dtype=torch.uint8, device=gpu())
+    with pytest.raises(E.EnsError) as ei:
+        E.cg(mesh.graph, 4, vals, b, y, 1e-8, 10, small)
+    assert ei.value.code == 9
+
+
+# ------------------------------------------ full-size workload, sampled checks
+def test_scale_64cubed_s32_sampled(torch):
+    """64^3 cells, M = 10, s = 32, tol 1e-8: the benchmark's launch shape."""
+    N, M, s = 64, 10, 32
+    mesh = E.Mesh(N, M)
+    xs = inputs.kl_samples(inputs.SEED_SCALE, 0, s, M)
+    vals, b = mesh.assemble(s, to_dev(inputs.ensemble_layout(xs)))
+    picks = [0, 17]
+    rm, col, ov, ob = oracle_members(N, M, xs[picks])
+    V = ens_cols(to_np(vals), s)
+    for i, e in enumerate(picks):
+        assert np.all(np.abs(V[:, e] - ov[i]) <= 1e-13 * np.abs(diag_of(rm, col, ov[i])))
+    # SpMV at full size, all 32 members: oracle values of the picked samples tiled
+    xm = [inputs.random_vector(1300 + e, mesh.n) for e in range(s)]
+    vt = to_dev(O.to_ensemble([ov[e % 2] for e in range(s)]))
+    y = torch.empty(mesh.n * s, dtype=torch.float64, device=gpu())
+    E.spmv(mesh.graph, s, vt, to_dev(O.to_ensemble(xm)), y)
+    Y = ens_cols(to_np(y), s)
+    for e in range(s):
+        ref = O.spmv(rm, col, ov[e % 2], xm[e])
+        assert np.all(np.abs(Y[:, e] - ref) <= spmv_bound(rm, col, ov[e % 2], xm[e])), e
+    # CG of the whole ensemble; two members against oracle solves
+    xg, it, rr, st, _ = gpu_solve(mesh, xs, 1e-8)
+    assert st == [0] * s and max(rr) < 2e-8
+    compare_cg_picked(mesh, xs, picks, rm, col, ov, ob, xg, it)
+
+
+def compare_cg_picked(mesh, xs, picks, rm, col, ov, ob, xg, it):
+    for i, e in enumerate(picks):
+        xo, ito, rro, sto = O.cg(rm, col, ov[i], ob[i], tol=1e-8)
+        assert sto == 0 and abs(it[e] - ito) <= 1
+        err = np.linalg.norm(xg[:, e] - xo) / np.linalg.norm(xo)
+        assert err <= 1e-8 or it[e] != ito, (e, err)
