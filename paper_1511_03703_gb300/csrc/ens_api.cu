@@ -25,6 +25,7 @@ int fail(int status, const char *fmt, ...) {
 
 int cuda_fail(cudaError_t err, const char *what) {
     set_error("%s: %s (%s)", what, cudaGetErrorName(err), cudaGetErrorString(err));
+    (void)cudaGetLastError();  // a non-sticky error must not leak into the next call's launch check
     return ENS_ERR_CUDA;
 }
 

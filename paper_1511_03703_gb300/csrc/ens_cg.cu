@@ -380,14 +380,21 @@ static int cg_run(const ens_graph *g, const double *vals, const double *b, doubl
     cudaGraphExec_t gexec = nullptr;
     cudaGraph_t graph = nullptr;
     if (use_graph) {
-        ENS_CUDA_TRY(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
-        for (int i = 0; i < check_every; ++i) {
-            K::spmv(a, grid, st);
-            K::resid(a, grid, st);
-            K::update(a, grid, st);
+        // capture on a private stream (the legacy default stream cannot be
+        // captured); the graph is then launched on the caller's stream
+        cudaStream_t cap;
+        ENS_CUDA_TRY(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
+        cudaError_t ce = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+        if (ce == cudaSuccess) {
+            for (int i = 0; i < check_every; ++i) {
+                K::spmv(a, grid, cap);
+                K::resid(a, grid, cap);
+                K::update(a, grid, cap);
+            }
+            ce = cudaStreamEndCapture(cap, &graph);
         }
-        cudaError_t ce = cudaStreamEndCapture(st, &graph);
-        if (ce != cudaSuccess) return cuda_fail(ce, "cudaStreamEndCapture");
+        cudaStreamDestroy(cap);
+        if (ce != cudaSuccess) return cuda_fail(ce, "cg iteration graph capture");
         ce = cudaGraphInstantiate(&gexec, graph, 0);
         if (ce != cudaSuccess) { cudaGraphDestroy(graph); return cuda_fail(ce, "cudaGraphInstantiate"); }
     }
