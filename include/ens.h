@@ -142,6 +142,25 @@ int ens_dot_workspace_size(int64_t n, int s, size_t *bytes);
 int ens_dot(int64_t n, int s, const double *u, const double *v, double *out, void *work,
             size_t work_bytes, void *stream);
 
+/* Allocation-free ens_dot (the paper has no counterpart; this is a library
+ * convenience).  For callers that cannot allocate device memory when they
+ * need the product -- e.g. code running while an allocator is locked or owned
+ * by another runtime -- it computes the same per-member dots as ens_dot,
+ * bitwise identical, with its reduction scratch in a static device array of
+ * ENS_DOT_STATIC_MAX_BYTES bytes that every GPU loading the library keeps
+ * until the process exits.  It calls no allocator.
+ *   Limit: ens_dot_workspace_size(n, s) must be <= ENS_DOT_STATIC_MAX_BYTES
+ *   (about 2.3 MB for n = 274,625 rows at s = 32); larger sizes return
+ *   ENS_ERR_UNSUPPORTED.
+ *   Set-up: the first call with a device current looks up the array's device
+ *   address (cudaGetSymbolAddress); make that first call before any stream
+ *   capture.  The stream must belong to the current device.
+ *   Sharing: all calls share the array and it keeps the last call's contents;
+ *   the call clears the counters it needs, but calls that overlap on the GPU
+ *   race with each other.  u, v, out: device pointers as for ens_dot. */
+#define ENS_DOT_STATIC_MAX_BYTES (4u << 20)
+int ens_dot_static(int64_t n, int s, const double *u, const double *v, double *out, void *stream);
+
 /* ----------------------------------------------------------------- A6 CG */
 /* Statistics of one ens_cg call (optional). */
 typedef struct ens_cg_stats {

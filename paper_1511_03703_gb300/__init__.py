@@ -12,7 +12,7 @@ import os
 import threading
 
 __all__ = ["EnsError", "lib", "Graph", "Mesh", "mesh_sizes", "graph_build", "kl_table_size",
-           "kl_setup", "mode_matrices", "assemble", "spmv", "dot", "dot_workspace_size", "cg",
+           "kl_setup", "mode_matrices", "assemble", "spmv", "dot", "dot_workspace_size", "dot_static", "cg",
            "cg_workspace_size", "CgStats", "F64", "F32", "BF16", "CG_COUPLED", "CG_GRAPH",
            "CG_TIME_SPMV"]
 
@@ -83,6 +83,7 @@ def _declare(L):
         "ens_spmv": (I, [P(EnsGraphC), I, I, vp, vp, vp, vp]),
         "ens_dot_workspace_size": (I, [i64, I, P(sz)]),
         "ens_dot": (I, [i64, I, vp, vp, vp, vp, sz, vp]),
+        "ens_dot_static": (I, [i64, I, vp, vp, vp, vp]),
         "ens_cg_workspace_size": (I, [i32, I, P(sz)]),
         "ens_cg": (I, [P(EnsGraphC), I, vp, vp, vp, d, I, I, I, vp, sz, vp, vp, vp, P(CgStats), vp]),
     }
@@ -203,6 +204,12 @@ def dot(n, s, u, v, out, work, stream=None):
     _require_cuda(u, v, out, work)
     _check(lib().ens_dot(n, s, _ptr(u), _ptr(v), _ptr(out), _ptr(work), work.numel() * work.element_size(),
                          _stream(stream)))
+
+
+def dot_static(n, s, u, v, out, stream=None):
+    """ens_dot without a workspace: scratch comes from the library's static array."""
+    _require_cuda(u, v, out)
+    _check(lib().ens_dot_static(n, s, _ptr(u), _ptr(v), _ptr(out), _stream(stream)))
 
 
 def cg_workspace_size(n, s):
