@@ -50,7 +50,7 @@ def kernel_source_hash():
     return h.hexdigest()[:16]
 
 
-def profiled_traffic(s):
+def profiled_traffic(s, mode="f64"):
     """DRAM bytes per launch of the CG SpMV from the committed ncu summary, if
     that summary was taken on the current kernel source; else None."""
     path = os.path.join(ROOT, "profiles", "cg_spmv_64cubed.txt")
@@ -60,8 +60,41 @@ def profiled_traffic(s):
     m = re.search(r"kernel_source_sha256_16:\s*(\w+)", txt)
     if not m or m.group(1) != kernel_source_hash():
         return None
-    m = re.search(rf"traffic_bytes_per_launch_s{s}:\s*([0-9.eE+]+)", txt)
+    m = re.search(rf"traffic_bytes_per_launch_{mode}_s{s}:\s*([0-9.eE+]+)", txt)
     return float(m.group(1)) if m else None
+
+
+def fp64_alu_peak_tflops(sm_mhz=2070.0):
+    """FP64 FMA pipe: 2 DFMA per cycle per SM (ncu peak_sustained), 152 SMs."""
+    return 152 * 2 * 2 * sm_mhz * 1e6 / 1e12
+
+
+def spmv_sweep(torch, device, s_list=(1, 4, 8, 16, 32), iters=24):
+    """CG SpMV (K1) launch time per ensemble size and arithmetic form, from a
+    fixed-iteration CG (tol 0) on the 64^3 mesh with CUDA events per launch."""
+    import paper_1511_03703_gb300 as E
+    from paper_1511_03703_gb300 import inputs
+    mesh = E.Mesh(N_MESH, M_KL, device=device)
+    peak, _ = measured_peaks()
+    out = {}
+    for s in s_list:
+        xs = inputs.kl_samples(inputs.SEED_SCALE, 0, s, M_KL)
+        vals, b = mesh.assemble(s, torch.from_numpy(inputs.ensemble_layout(xs)).to(device))
+        work = torch.empty(E.cg_workspace_size(mesh.n, s), dtype=torch.uint8, device=device)
+        row = {}
+        for name, fl in (("f64", 0), ("df", E.CG_DF64)):
+            x = torch.zeros(mesh.n * s, dtype=torch.float64, device=device)
+            E.cg(mesh.graph, s, vals, b, x, 0.0, 4, work, flags=fl, check_every=4)  # warm-up
+            x.zero_()
+            _, _, _, st = E.cg(mesh.graph, s, vals, b, x, 0.0, iters, work,
+                               flags=fl | E.CG_TIME_SPMV, check_every=iters)
+            ms = st.spmv_ms / max(st.spmv_launches, 1)
+            gbs = spmv_bytes(mesh.n, mesh.nnz, s) / (ms * 1e-3) / 1e9
+            row[name] = {"ms": ms, "gbs": gbs, "hbm_frac": gbs / peak,
+                         "fp64_tflops": 2 * mesh.nnz * s / (ms * 1e-3) / 1e12}
+        out[str(s)] = row
+        del vals, b, work
+    return out
 
 
 def measured_peaks():
@@ -137,13 +170,14 @@ def make_batch(rank, s, batch):
 class Runner:
     """Holds device buffers for one batch; run_step() is one timed step."""
 
-    def __init__(self, torch, s, batch, device, time_spmv=True):
+    def __init__(self, torch, s, batch, device, time_spmv=True, df=False):
         import paper_1511_03703_gb300 as E
         from paper_1511_03703_gb300 import inputs
         self.torch, self.E, self.s, self.batch = torch, E, s, batch
         self.dev = device
         self.nens = batch // s
         self.time_spmv = time_spmv
+        self.df = df
         n, nnz, _ = E.mesh_sizes(N_MESH)
         self.n, self.nnz = n, nnz
         T = torch
@@ -182,7 +216,7 @@ class Runner:
                    self.xi[g] if xi is None else xi, SIGMA, KAPPA0, self.values, self.b)
         x = self.x[g]
         x.zero_()
-        flags = E.CG_TIME_SPMV if self.time_spmv else 0
+        flags = (E.CG_TIME_SPMV if self.time_spmv else 0) | (E.CG_DF64 if self.df else 0)
         it, rr, st, stats = E.cg(self.graph, self.s, self.values, self.b, x, TOL, 10000, self.work,
                                  flags=flags, check_every=16)
         self.launches += 2 + stats.kernel_launches
@@ -198,9 +232,9 @@ class Runner:
             self.solve_ensemble(g)
 
 
-def per_sample_baseline(torch, device, nsamp=32):
+def per_sample_baseline(torch, device, nsamp=32, df=False):
     """The s = 1 path (samples one after another), as in the paper's speed-up."""
-    r = Runner(torch, 1, nsamp, device, time_spmv=True)
+    r = Runner(torch, 1, nsamp, device, time_spmv=True, df=df)
     r.setup_mesh()
     r.solve_ensemble(0)  # warm-up
     r.reset_stats()
@@ -285,7 +319,8 @@ def main_ours(args):
     import paper_1511_03703_gb300 as E
     E.lib()
     s = args.s
-    r = Runner(torch, s, BATCH, device, time_spmv=True)
+    df = args.spmv == "df"
+    r = Runner(torch, s, BATCH, device, time_spmv=True, df=df)
     if world > 1:  # shard: this rank's own 1024 samples
         from paper_1511_03703_gb300 import inputs
         xs = inputs.kl_samples(inputs.SEED_SCALE, shard_first_sample(rank, BATCH), BATCH, M_KL)
@@ -319,32 +354,68 @@ def main_ours(args):
     avg_spmv_ms = r.spmv_ms / max(r.spmv_launches, 1)
     bytes_launch = spmv_bytes(r.n, r.nnz, s)
     achieved = bytes_launch / (avg_spmv_ms * 1e-3) / 1e9
-    traffic = profiled_traffic(s)
+    flops = 2.0 * r.nnz * s / (avg_spmv_ms * 1e-3) / 1e12
+    traffic = profiled_traffic(s, args.spmv)
     gpu_launches = r.launches
     iters = r.iters
     bad = r.status_bad
     out = None
     if rank == 0:
+        sm_mhz = clk.get("sm_mhz") or 2070.0
+        if df:
+            roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                    "frac": achieved / peak, "traffic": traffic,
+                    "peak_source": f"{peak_kind} hbm_gbs (MEASURED_PEAKS.json)"}
+        else:
+            alu = fp64_alu_peak_tflops(sm_mhz)
+            roof = {"bound": "alu", "achieved": flops, "peak": alu, "unit": "TFLOP/s",
+                    "frac": flops / alu, "traffic": traffic,
+                    "peak_source": "FP64 FMA pipe: 152 SMs x 2 DFMA/cycle x 2 flop x median SM clock "
+                                   "under load (derived; probe measured 0.596 TFMA/s at 2.07 GHz)",
+                    "hbm": {"achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                            "peak_source": f"{peak_kind} hbm_gbs"}}
+        roof.update({"kernel": f"cg_spmv_kernel<{s},{'df' if df else 'f64'}> (q = A p fused with per-member p.q)",
+                     "bytes_per_launch": bytes_launch, "avg_launch_ms": avg_spmv_ms,
+                     "launches_timed": r.spmv_launches})
         e2e = e2e_run(torch, r, max(1, min(args.steps, 2)))
-        per = per_sample_baseline(torch, device)
+        per = per_sample_baseline(torch, device, df=df)
         ens_speedup = value / world / per["value"]
+        other = None
+        if not args.quick:
+            r2 = Runner(torch, s, BATCH, device, time_spmv=True, df=not df)
+            r2.xi = r.xi
+            r2.run_step()
+            torch.cuda.synchronize()
+            r2.reset_stats()
+            t0 = time.perf_counter()
+            r2.run_step()
+            torch.cuda.synchronize()
+            dt = time.perf_counter() - t0
+            ms2 = r2.spmv_ms / max(r2.spmv_launches, 1)
+            other = {"spmv": "f64" if df else "df", "value": BATCH / dt, "unit": UNIT, "steps": 1,
+                     "spmv_gbs": bytes_launch / (ms2 * 1e-3) / 1e9,
+                     "spmv_hbm_frac": bytes_launch / (ms2 * 1e-3) / 1e9 / peak,
+                     "mean_iters": float(np.mean(r2.iters)), "failed_members": r2.status_bad}
+            del r2
+        sweep = None if args.quick else spmv_sweep(torch, device)
         out = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64 (SpMV products and sums in double-float 2xf32, all else f64)" if df else "f64",
+            "data": "synthetic",
             "config": {"workload": WORKLOAD, "ensemble_size": s, "batch_samples": BATCH,
                        "ensembles_per_step": BATCH // s, "tol": TOL, "kl_terms": M_KL,
-                       "sigma": SIGMA, "corr_length": L_CORR, "l2": "inputs larger than L2 (1.8 GB values per ensemble)",
+                       "sigma": SIGMA, "corr_length": L_CORR, "spmv": args.spmv,
+                       "l2": "inputs larger than L2 (1.8 GB values per ensemble)",
                        "parallelism": f"replica per GPU, {world} GPU(s), samples sharded by rank"},
-            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "traffic": traffic,
-                         "kernel": f"cg_spmv_kernel<{s}> (fused q = A p and per-member p.q)",
-                         "bytes_per_launch": bytes_launch, "avg_launch_ms": avg_spmv_ms,
-                         "launches_timed": r.spmv_launches, "peak_source": f"{peak_kind} hbm_gbs"},
+            "roofline": roof,
             "cpu_baseline": cpu_baseline_run() if not args.no_cpu_baseline else None,
             "e2e": e2e,
             "per_sample_gpu": per,
             "ensemble_speedup_vs_per_sample": ens_speedup,
+            "other_spmv_form": other,
+            "spmv_sweep_64cubed": sweep,
             "cg_iterations": {"mean": float(np.mean(iters)), "min": int(min(iters)),
                               "max": int(max(iters)), "failed_members": bad},
             "gpu_launches": gpu_launches,
@@ -390,7 +461,10 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--s", type=int, default=32, choices=[4, 8, 16, 32])
+    ap.add_argument("--spmv", default="f64", choices=["f64", "df"],
+                    help="CG SpMV arithmetic: native FP64 FMA or double-float on the FP32 pipe")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--quick", action="store_true", help="skip the other-form run and the s sweep")
     args = ap.parse_args()
     if args.impl == "reference":
         main_reference(args)

@@ -49,7 +49,12 @@ typedef enum ens_status {
     ENS_ERR_WORKSPACE = 9      /* workspace smaller than the *_workspace_size value */
 } ens_status;
 
-typedef enum ens_dtype { ENS_F64 = 0, ENS_F32 = 1, ENS_BF16 = 2 } ens_dtype;
+/* Value types.  ENS_F64_DF: values and x are FP64 in memory, products and sums
+ * are formed in double-float arithmetic on the FP32 pipe (each FP64 operand
+ * split into two floats; error per term <= ~6*2^-48 |a x|, so a row is within
+ * ~1.2e-13 * sum |a_j x_j|).  GB300 runs FP64 FMA at 1/64 of its FP32 rate,
+ * which bounds the native form of the ensemble SpMV below the HBM roofline. */
+typedef enum ens_dtype { ENS_F64 = 0, ENS_F32 = 1, ENS_BF16 = 2, ENS_F64_DF = 3 } ens_dtype;
 
 /* CRS graph (Fig. 2): row_map[num_rows+1], col_entry[num_entries] (device,
  * int32, columns ascending within a row).  Values live in a separate array in
@@ -123,11 +128,12 @@ int ens_assemble(const ens_graph *graph, const uint8_t *bmask, int s, int M,
 /* --------------------------------------------------------------- A4 SpMV */
 /* y = A_c x for the commuted ensemble matrix (Fig. 5 semantics):
  *   y[I*s+e] = sum_{entry in row I} values[entry*s+e] * x[col_entry[entry]*s+e].
- * dtype = ENS_F64 (values double), ENS_F32 (float) or ENS_BF16 (bfloat16);
- * x and y are double, accumulation in FP64.  The per-member sum order is
- * fixed and independent of s: entry j goes to partial j mod 4, partials are
- * combined as (p0+p1)+(p2+p3), so member e's result is bitwise the same for
- * every s. x, y, values 16-byte aligned when s > 1. */
+ * dtype = ENS_F64 (values double), ENS_F32 (float), ENS_BF16 (bfloat16) or
+ * ENS_F64_DF (double values, double-float arithmetic); x and y are double,
+ * accumulation in FP64 (double-float for ENS_F64_DF).  The per-member sum
+ * order is fixed and independent of s: entry j goes to partial j mod 2 and
+ * the row value is p0 + p1, so member e's result is bitwise the same for
+ * every s.  x, y, values 16-byte aligned when s > 1. */
 int ens_spmv(const ens_graph *graph, int s, int dtype, const void *values, const double *x,
              double *y, void *stream);
 
@@ -175,7 +181,10 @@ enum {
     ENS_CG_COUPLED = 1,      /* paper's coupled ensemble CG (Sect. 3.6): alpha, beta
                                 from member-summed dots, one convergence test */
     ENS_CG_GRAPH = 2,        /* replay the iteration through a captured CUDA graph */
-    ENS_CG_TIME_SPMV = 4     /* record CUDA events around each CG SpMV */
+    ENS_CG_TIME_SPMV = 4,    /* record CUDA events around each CG SpMV */
+    ENS_CG_DF64 = 8          /* CG SpMV in double-float arithmetic (see ENS_F64_DF);
+                                p is kept split as float pairs, all other vector
+                                arithmetic and every dot stays FP64 */
 };
 
 /* Unpreconditioned CG (Hestenes-Stiefel) on each member of the ensemble

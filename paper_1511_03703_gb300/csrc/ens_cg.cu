@@ -2,19 +2,25 @@
 //
 // Hestenes-Stiefel CG run on every member of the commuted ensemble system at
 // once.  By default each member has its own alpha, beta and stopping test
-// (dots reduced per member: the vector sum_i u_i^T v_i (x) e_i of
-// Sect. 3.4 before its members are added), so member e follows exactly the iterates of a
+// (dots reduced per member: the vector sum_i u_i^T v_i (x) e_i of Sect. 3.4
+// before its members are added), so member e follows the iterates of a
 // standalone solve of sample e; members that converge are frozen.  With
 // ENS_CG_COUPLED the member dots are summed first, which is the paper's
 // coupled ensemble solver of Sect. 3.6.
 //
-// One iteration = 3 kernels, no host synchronisation:
-//   K1  q = A p,  pi_e = p.q            (last CTA: alpha_e = rho_e / pi_e)
-//   K2  r -= alpha q,  rho'_e = r.r     (last CTA: stop test, beta_e)
+// Launch sequence, no host synchronisation inside an iteration:
+//   K0  r = b - A x0, p = r, rho_e = r.r, |b_e|^2   (last CTA: init, stop test)
+//   KZ  x_e = 0 for members with b_e = 0 (one-shot)
+//   per iteration:
+//   K1  q = A p,  pi_e = p.q     (last CTA: alpha_e = rho_e / pi_e, breakdown)
+//   K2  r -= alpha q,  r.r       (last CTA: stop test, beta_e, x-update flags)
 //   K3  x += alpha p,  p = r + beta p   (x update deferred here so K2 reads 2 vectors)
 // Vector traffic per iteration: K1 1 gather + 1 write, K2 2 reads + 1 write,
-// K3 3 reads + 2 writes (10 vector passes).  The per-member scalar work runs in
-// the CTA that completes each kernel's deterministic dot tree.
+// K3 3 reads + 2 writes (10 vector passes; +1 write of the split p in df mode).
+// The per-member scalar work runs in the CTA that completes each kernel's
+// deterministic dot tree.  K2/K3 stream tiles of 4-8 tree chunks per CTA.
+// Flag protocol: K2 sets updx_e for members active in its iteration, K3 reads
+// them, and the next K1 clears them (also when it exits early).
 #include <vector>
 
 #include "ens_spmv.cuh"
@@ -24,7 +30,8 @@ namespace ens {
 struct CgState {
     double rho[32], alpha[32], beta[32], bnorm[32], relres[32];
     int active[32], updx[32], zerox[32], iters[32], status[32];
-    int active_count, updx_any, k3_arrive, spmv_real;
+    int active_count, updx_any, zero_any, spmv_real;
+    int df_bad_any, pad0, pad1, pad2;
     double bnorm_all;
 };
 
@@ -35,43 +42,75 @@ struct CgArgs {
     const double *vals;
     const double *b;
     double *x, *r, *p, *q;
+    float2 *pdf;  // p split into float pairs (df mode)
     CgState *st;
-    DotTree t1;  // width s
-    DotTree t2;  // width 2s
+    DotTree t1;   // width s
+    DotTree t2;   // width 2s
     double tol;
     int max_iter;
     int coupled;
 };
 
-// ------------------------------------------------------------------ K0
+// mapping of the streaming vector kernels (K2, K3): a CTA owns CPC chunks
 template <int S>
-__global__ void __launch_bounds__(RowMap<S>::THREADS) cg_init_kernel(CgArgs a) {
+struct VecMap {
+    static constexpr int VG = (S == 1) ? 1 : S / 2;            // threads per row
+    static constexpr int CHUNK_T = 32 * VG;                    // threads per chunk
+    static constexpr int THREADS = (S == 32) ? 512 : 256;
+    static constexpr int CPP = THREADS / CHUNK_T;              // chunks per pass
+    static constexpr int CPC = (S >= 16) ? 4 : 8;              // chunks per CTA
+    static constexpr int PASSES = CPC / CPP;
+};
+
+__device__ __forceinline__ void store_split(float2 *pdf, int64_t i, double v0, double v1, int *bad) {
+    bool ok0, ok1;
+    const float2 a = df_split_vec(v0, ok0), b = df_split_vec(v1, ok1);
+    reinterpret_cast<float4 *>(pdf)[i >> 1] = make_float4(a.x, a.y, b.x, b.y);
+    if (!ok0 || !ok1) *bad = 1;
+}
+__device__ __forceinline__ void store_split1(float2 *pdf, int64_t i, double v, int *bad) {
+    bool ok;
+    pdf[i] = df_split_vec(v, ok);
+    if (!ok) *bad = 1;
+}
+
+// ------------------------------------------------------------------ K0
+template <int S, bool DF>
+__global__ void __launch_bounds__(RowMap<S>::THREADS, 1024 / RowMap<S>::THREADS) cg_init_kernel(CgArgs a) {
     constexpr int G = RowMap<S>::G;
     __shared__ double sm[32][S + 1];
     const int r = threadIdx.x / G, g = threadIdx.x % G;
     const int64_t R = (int64_t)blockIdx.x * 32 + r;
+    __shared__ ChunkCols cc;
+    const bool staged = stage_chunk(cc, a.row_map, a.col, blockIdx.x, a.n);
+    const double2 axv = chunk_spmv<S, double>(cc, staged, a.col, a.vals, a.x, r, g, R < a.n);
     double rr0 = 0.0, rr1 = 0.0, bb0 = 0.0, bb1 = 0.0;
     if constexpr (S == 1) {
-        const double ax = row_spmv1<double>(a.row_map, a.col, a.vals, a.x, R, g, R < a.n);
+        const double ax = axv.x;
         if (R < a.n) {
             const double bv = a.b[R];
             const double res = bv - ax;
-            if (g == 0) { a.r[R] = res; a.p[R] = res; }
+            if (g == 0) {
+                a.r[R] = res;
+                a.p[R] = res;
+                if (DF) store_split1(a.pdf, R, res, &a.st->df_bad_any);
+            }
             rr0 = res * res;
             bb0 = bv * bv;
         }
     } else if (R < a.n) {
-        const double2 ax = row_spmv2<S, double>(a.row_map, a.col, a.vals, a.x, R, g);
+        const double2 ax = axv;
         const double2 bv = reinterpret_cast<const double2 *>(a.b)[R * G + g];
         const double2 res = make_double2(bv.x - ax.x, bv.y - ax.y);
         reinterpret_cast<double2 *>(a.r)[R * G + g] = res;
         reinterpret_cast<double2 *>(a.p)[R * G + g] = res;
+        if (DF) store_split(a.pdf, R * S + 2 * g, res.x, res.y, &a.st->df_bad_any);
         rr0 = res.x * res.x; rr1 = res.y * res.y;
         bb0 = bv.x * bv.x; bb1 = bv.y * bv.y;
     }
     chunk_tree<S>(sm, rr0, rr1, r, g, a.t2, blockIdx.x, 0);
     chunk_tree<S>(sm, bb0, bb1, r, g, a.t2, blockIdx.x, S);
-    if (!dot_tree_propagate(a.t2, blockIdx.x)) return;
+    if (!dot_tree_propagate(a.t2, blockIdx.x, 1)) return;
     if (threadIdx.x != 0) return;
     const double *top = a.t2.buf[a.t2.levels];
     CgState *st = a.st;
@@ -98,43 +137,67 @@ __global__ void __launch_bounds__(RowMap<S>::THREADS) cg_init_kernel(CgArgs a) {
     if (a.max_iter == 0)
         for (int e = 0; e < S; ++e)
             if (st->active[e]) { st->active[e] = 0; st->status[e] = ENS_ERR_NOT_CONVERGED; }
-    int ac = 0, ux = 0;
-    for (int e = 0; e < S; ++e) { ac += st->active[e]; ux += st->zerox[e]; }
+    int ac = 0, zx = 0;
+    for (int e = 0; e < S; ++e) { ac += st->active[e]; zx += st->zerox[e]; }
     st->active_count = ac;
-    st->updx_any = ux;
-    st->k3_arrive = 0;
+    st->zero_any = zx;
+    st->updx_any = 0;
     st->spmv_real = 0;
     __threadfence();
 }
 
-// ------------------------------------------------------------------ K1
+// ------------------------------------------------------------------ KZ
 template <int S>
-__global__ void __launch_bounds__(RowMap<S>::THREADS) cg_spmv_kernel(CgArgs a) {
-    if (ld_cg(&a.st->active_count) == 0) return;
+__global__ void cg_zero_kernel(CgArgs a) {
+    if (ld_cg(&a.st->zero_any) == 0) return;
+    const int64_t total = (int64_t)a.n * S;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
+         i += (int64_t)gridDim.x * blockDim.x)
+        if (a.st->zerox[i % S]) a.x[i] = 0.0;
+}
+
+// ------------------------------------------------------------------ K1
+template <int S, bool DF>
+__global__ void __launch_bounds__(RowMap<S>::THREADS, 1536 / RowMap<S>::THREADS) cg_spmv_kernel(CgArgs a) {
+    CgState *st = a.st;
+    if (ld_cg(&st->active_count) == 0) {
+        if (blockIdx.x == 0 && threadIdx.x == 0 && st->updx_any) {
+            for (int e = 0; e < S; ++e) st->updx[e] = 0;
+            st->updx_any = 0;
+        }
+        return;
+    }
     constexpr int G = RowMap<S>::G;
     __shared__ double sm[32][S + 1];
     const int r = threadIdx.x / G, g = threadIdx.x % G;
     const int64_t R = (int64_t)blockIdx.x * 32 + r;
+    const bool use_df = DF && (ld_cg(&st->df_bad_any) == 0);
+    __shared__ ChunkCols cc;
+    const bool staged = stage_chunk(cc, a.row_map, a.col, blockIdx.x, a.n);
+    const double2 apv =
+        use_df ? chunk_spmv_df<S, XPre>(cc, staged, a.col, a.vals, a.pdf, r, g, R < a.n)
+               : chunk_spmv<S, double>(cc, staged, a.col, a.vals, a.p, r, g, R < a.n);
     double v0 = 0.0, v1 = 0.0;
     if constexpr (S == 1) {
-        const double ap = row_spmv1<double>(a.row_map, a.col, a.vals, a.p, R, g, R < a.n);
+        const double ap = apv.x;
         if (R < a.n) {
             if (g == 0) a.q[R] = ap;
             v0 = ap * a.p[R];
         }
     } else if (R < a.n) {
-        const double2 ap = row_spmv2<S, double>(a.row_map, a.col, a.vals, a.p, R, g);
+        const double2 ap = apv;
         reinterpret_cast<double2 *>(a.q)[R * G + g] = ap;
         const double2 pv = reinterpret_cast<const double2 *>(a.p)[R * G + g];
         v0 = ap.x * pv.x;
         v1 = ap.y * pv.y;
     }
     chunk_tree<S>(sm, v0, v1, r, g, a.t1, blockIdx.x, 0);
-    if (!dot_tree_propagate(a.t1, blockIdx.x)) return;
+    if (!dot_tree_propagate(a.t1, blockIdx.x, 1)) return;
     if (threadIdx.x != 0) return;
     const double *top = a.t1.buf[a.t1.levels];
-    CgState *st = a.st;
     st->spmv_real += 1;
+    for (int e = 0; e < S; ++e) st->updx[e] = 0;  // consumed by the previous K3
+    st->updx_any = 0;
     if (a.coupled) {
         double pis = 0.0, rhos = 0.0;
         for (int e = 0; e < S; ++e) { pis += ld_cg(top + e); rhos += st->rho[e]; }
@@ -160,35 +223,60 @@ __global__ void __launch_bounds__(RowMap<S>::THREADS) cg_spmv_kernel(CgArgs a) {
 
 // ------------------------------------------------------------------ K2
 template <int S>
-__global__ void __launch_bounds__(RowMap<S>::THREADS) cg_resid_kernel(CgArgs a) {
+__global__ void __launch_bounds__(VecMap<S>::THREADS) cg_resid_kernel(CgArgs a) {
+    using VM = VecMap<S>;
     if (ld_cg(&a.st->active_count) == 0) return;
-    constexpr int G = (S == 1) ? 4 : S / 2;
-    __shared__ double sm[32][S + 1];
-    const int r = threadIdx.x / G, g = threadIdx.x % G;
-    const int64_t R = (int64_t)blockIdx.x * 32 + r;
+    constexpr int VG = VM::VG;
+    const int cip = threadIdx.x / VM::CHUNK_T, lt = threadIdx.x % VM::CHUNK_T;
+    const int r = lt / VG, g = lt % VG;
     const CgState *cs = a.st;
-    double v0 = 0.0, v1 = 0.0;
-    if (R < a.n) {
-        if constexpr (S == 1) {
-            if (g == 0) {
+    const int m = (S == 1) ? 0 : 2 * g;
+    const bool act0 = cs->active[m];
+    const bool act1 = (S == 1) ? false : (bool)cs->active[m + 1];
+    const double al0 = cs->alpha[m];
+    const double al1 = (S == 1) ? 0.0 : cs->alpha[m + 1];
+    __shared__ double sm[VM::CPC][32][S + 1];   // per-row products of every chunk
+    const int64_t first_chunk = (int64_t)blockIdx.x * VM::CPC;
+#pragma unroll
+    for (int pass = 0; pass < VM::PASSES; ++pass) {
+        const int c = pass * VM::CPP + cip;
+        const int64_t R = (first_chunk + c) * 32 + r;
+        double v0 = 0.0, v1 = 0.0;
+        if (R < a.n) {
+            if constexpr (S == 1) {
                 double rv = a.r[R];
-                if (cs->active[0]) rv = fma(-cs->alpha[0], a.q[R], rv);
-                a.r[R] = rv;
+                if (act0) { rv = fma(-al0, a.q[R], rv); a.r[R] = rv; }
                 v0 = rv * rv;
+            } else {
+                double2 rv = reinterpret_cast<const double2 *>(a.r)[R * VG + g];
+                const double2 qv = reinterpret_cast<const double2 *>(a.q)[R * VG + g];
+                if (act0) rv.x = fma(-al0, qv.x, rv.x);
+                if (act1) rv.y = fma(-al1, qv.y, rv.y);
+                if (act0 || act1) reinterpret_cast<double2 *>(a.r)[R * VG + g] = rv;
+                v0 = rv.x * rv.x;
+                v1 = rv.y * rv.y;
             }
-        } else {
-            const int m = 2 * g;
-            double2 rv = reinterpret_cast<const double2 *>(a.r)[R * G + g];
-            const double2 qv = reinterpret_cast<const double2 *>(a.q)[R * G + g];
-            if (cs->active[m]) rv.x = fma(-cs->alpha[m], qv.x, rv.x);
-            if (cs->active[m + 1]) rv.y = fma(-cs->alpha[m + 1], qv.y, rv.y);
-            reinterpret_cast<double2 *>(a.r)[R * G + g] = rv;
-            v0 = rv.x * rv.x;
-            v1 = rv.y * rv.y;
         }
+        sm[c][r][m] = v0;
+        if constexpr (S > 1) sm[c][r][m + 1] = v1;
     }
-    chunk_tree<S>(sm, v0, v1, r, g, a.t1, blockIdx.x, 0);
-    if (!dot_tree_propagate(a.t1, blockIdx.x)) return;
+    __syncthreads();
+    // halving tree over the 32 rows of every chunk, all members packed
+#pragma unroll
+    for (int h = 16; h >= 1; h >>= 1) {
+        for (int it = threadIdx.x; it < VM::CPC * h * S; it += VM::THREADS) {
+            const int c = it / (h * S), rem = it % (h * S), i = rem / S, e = rem % S;
+            sm[c][i][e] += sm[c][i + h][e];
+        }
+        __syncthreads();
+    }
+    for (int it = threadIdx.x; it < VM::CPC * S; it += VM::THREADS) {
+        const int c = it / S, e = it % S;
+        const int64_t ch = first_chunk + c;
+        if (ch < a.t1.count[1]) a.t1.buf[1][ch * S + e] = sm[c][0][e];
+    }
+    const int nitems = (int)min((int64_t)VM::CPC, a.t1.count[1] - first_chunk);
+    if (!dot_tree_propagate(a.t1, first_chunk, nitems)) return;
     if (threadIdx.x != 0) return;
     const double *top = a.t1.buf[a.t1.levels];
     CgState *st = a.st;
@@ -226,68 +314,76 @@ __global__ void __launch_bounds__(RowMap<S>::THREADS) cg_resid_kernel(CgArgs a) 
 }
 
 // ------------------------------------------------------------------ K3
-template <int S>
-__global__ void __launch_bounds__(RowMap<S>::THREADS) cg_update_kernel(CgArgs a) {
-    if (ld_cg(&a.st->updx_any) == 0) return;
-    constexpr int G = (S == 1) ? 4 : S / 2;
-    const int r = threadIdx.x / G, g = threadIdx.x % G;
-    const int64_t R = (int64_t)blockIdx.x * 32 + r;
+template <int S, bool DF>
+__global__ void __launch_bounds__(VecMap<S>::THREADS) cg_update_kernel(CgArgs a) {
+    using VM = VecMap<S>;
     CgState *st = a.st;
-    if (R < a.n) {
+    if (ld_cg(&st->updx_any) == 0) return;
+    constexpr int VG = VM::VG;
+    const int cip = threadIdx.x / VM::CHUNK_T, lt = threadIdx.x % VM::CHUNK_T;
+    const int r = lt / VG, g = lt % VG;
+    const int m = (S == 1) ? 0 : 2 * g;
+    const bool ux0 = st->updx[m], ac0 = st->active[m];
+    const bool ux1 = (S == 1) ? false : (bool)st->updx[m + 1];
+    const bool ac1 = (S == 1) ? false : (bool)st->active[m + 1];
+    const double al0 = st->alpha[m], be0 = st->beta[m];
+    const double al1 = (S == 1) ? 0.0 : st->alpha[m + 1], be1 = (S == 1) ? 0.0 : st->beta[m + 1];
+    const int64_t first_chunk = (int64_t)blockIdx.x * VM::CPC;
+#pragma unroll 2
+    for (int pass = 0; pass < VM::PASSES; ++pass) {
+        const int64_t R = (first_chunk + pass * VM::CPP + cip) * 32 + r;
+        if (R >= a.n) continue;
         if constexpr (S == 1) {
-            if (g == 0) {
-                const double pv = a.p[R];
-                if (st->zerox[0]) a.x[R] = 0.0;
-                else if (st->updx[0]) a.x[R] = fma(st->alpha[0], pv, a.x[R]);
-                if (st->active[0]) a.p[R] = fma(st->beta[0], pv, a.r[R]);
+            const double pv = a.p[R];
+            if (ux0) a.x[R] = fma(al0, pv, a.x[R]);
+            if (ac0) {
+                const double pn = fma(be0, pv, a.r[R]);
+                a.p[R] = pn;
+                if (DF) store_split1(a.pdf, R, pn, &st->df_bad_any);
             }
         } else {
-            const int m = 2 * g;
-            const double2 pv = reinterpret_cast<const double2 *>(a.p)[R * G + g];
-            double2 xv = reinterpret_cast<const double2 *>(a.x)[R * G + g];
-            const double2 rv = reinterpret_cast<const double2 *>(a.r)[R * G + g];
-            if (st->zerox[m]) xv.x = 0.0; else if (st->updx[m]) xv.x = fma(st->alpha[m], pv.x, xv.x);
-            if (st->zerox[m + 1]) xv.y = 0.0; else if (st->updx[m + 1]) xv.y = fma(st->alpha[m + 1], pv.y, xv.y);
-            reinterpret_cast<double2 *>(a.x)[R * G + g] = xv;
-            double2 pn = pv;
-            if (st->active[m]) pn.x = fma(st->beta[m], pv.x, rv.x);
-            if (st->active[m + 1]) pn.y = fma(st->beta[m + 1], pv.y, rv.y);
-            reinterpret_cast<double2 *>(a.p)[R * G + g] = pn;
-        }
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        __threadfence();
-        const int old = atomicAdd(&st->k3_arrive, 1);
-        if (old == (int)gridDim.x - 1) {
-            for (int e = 0; e < S; ++e) { st->updx[e] = 0; st->zerox[e] = 0; }
-            st->updx_any = 0;
-            st->k3_arrive = 0;
-            __threadfence();
+            const double2 pv = reinterpret_cast<const double2 *>(a.p)[R * VG + g];
+            if (ux0 || ux1) {
+                double2 xv = reinterpret_cast<const double2 *>(a.x)[R * VG + g];
+                if (ux0) xv.x = fma(al0, pv.x, xv.x);
+                if (ux1) xv.y = fma(al1, pv.y, xv.y);
+                reinterpret_cast<double2 *>(a.x)[R * VG + g] = xv;
+            }
+            if (ac0 || ac1) {
+                const double2 rv = reinterpret_cast<const double2 *>(a.r)[R * VG + g];
+                double2 pn = pv;
+                if (ac0) pn.x = fma(be0, pv.x, rv.x);
+                if (ac1) pn.y = fma(be1, pv.y, rv.y);
+                reinterpret_cast<double2 *>(a.p)[R * VG + g] = pn;
+                if (DF) store_split(a.pdf, R * S + m, pn.x, pn.y, &st->df_bad_any);
+            }
         }
     }
 }
 
 // ------------------------------------------------------------------ KF
 template <int S>
-__global__ void __launch_bounds__(RowMap<S>::THREADS) cg_final_kernel(CgArgs a) {
+__global__ void __launch_bounds__(RowMap<S>::THREADS, 1024 / RowMap<S>::THREADS) cg_final_kernel(CgArgs a) {
     constexpr int G = RowMap<S>::G;
     __shared__ double sm[32][S + 1];
     const int r = threadIdx.x / G, g = threadIdx.x % G;
     const int64_t R = (int64_t)blockIdx.x * 32 + r;
+    __shared__ ChunkCols cc;
+    const bool staged = stage_chunk(cc, a.row_map, a.col, blockIdx.x, a.n);
+    const double2 axv = chunk_spmv<S, double>(cc, staged, a.col, a.vals, a.x, r, g, R < a.n);
     double v0 = 0.0, v1 = 0.0;
     if constexpr (S == 1) {
-        const double ax = row_spmv1<double>(a.row_map, a.col, a.vals, a.x, R, g, R < a.n);
+        const double ax = axv.x;
         if (R < a.n) { const double res = a.b[R] - ax; v0 = res * res; }
     } else if (R < a.n) {
-        const double2 ax = row_spmv2<S, double>(a.row_map, a.col, a.vals, a.x, R, g);
+        const double2 ax = axv;
         const double2 bv = reinterpret_cast<const double2 *>(a.b)[R * G + g];
         const double rx = bv.x - ax.x, ry = bv.y - ax.y;
         v0 = rx * rx;
         v1 = ry * ry;
     }
     chunk_tree<S>(sm, v0, v1, r, g, a.t1, blockIdx.x, 0);
-    if (!dot_tree_propagate(a.t1, blockIdx.x)) return;
+    if (!dot_tree_propagate(a.t1, blockIdx.x, 1)) return;
     if (threadIdx.x != 0) return;
     const double *top = a.t1.buf[a.t1.levels];
     for (int e = 0; e < S; ++e) {
@@ -301,23 +397,27 @@ __global__ void __launch_bounds__(RowMap<S>::THREADS) cg_final_kernel(CgArgs a) 
 static size_t align256(size_t x) { return (x + 255) / 256 * 256; }
 
 static size_t cg_bytes(int64_t n, int s) {
-    return align256(sizeof(CgState)) + 3 * align256(sizeof(double) * (size_t)n * s) +
+    return align256(sizeof(CgState)) + 4 * align256(sizeof(double) * (size_t)n * s) +
            dot_tree_bytes(n, s) + dot_tree_bytes(n, 2 * s);
 }
 
-template <int S>
+template <int S, bool DF>
 struct CgKernels {
+    static unsigned vec_grid(const CgArgs &a) {
+        return (unsigned)((a.t1.count[1] + VecMap<S>::CPC - 1) / VecMap<S>::CPC);
+    }
     static void init(const CgArgs &a, unsigned grid, cudaStream_t st) {
-        cg_init_kernel<S><<<grid, RowMap<S>::THREADS, 0, st>>>(a);
+        cg_init_kernel<S, DF><<<grid, RowMap<S>::THREADS, 0, st>>>(a);
+        cg_zero_kernel<S><<<152 * 2, 256, 0, st>>>(a);
     }
     static void spmv(const CgArgs &a, unsigned grid, cudaStream_t st) {
-        cg_spmv_kernel<S><<<grid, RowMap<S>::THREADS, 0, st>>>(a);
+        cg_spmv_kernel<S, DF><<<grid, RowMap<S>::THREADS, 0, st>>>(a);
     }
-    static void resid(const CgArgs &a, unsigned grid, cudaStream_t st) {
-        cg_resid_kernel<S><<<grid, RowMap<S>::THREADS, 0, st>>>(a);
+    static void resid(const CgArgs &a, unsigned, cudaStream_t st) {
+        cg_resid_kernel<S><<<vec_grid(a), VecMap<S>::THREADS, 0, st>>>(a);
     }
-    static void update(const CgArgs &a, unsigned grid, cudaStream_t st) {
-        cg_update_kernel<S><<<grid, RowMap<S>::THREADS, 0, st>>>(a);
+    static void update(const CgArgs &a, unsigned, cudaStream_t st) {
+        cg_update_kernel<S, DF><<<vec_grid(a), VecMap<S>::THREADS, 0, st>>>(a);
     }
     static void final_(const CgArgs &a, unsigned grid, cudaStream_t st) {
         cg_final_kernel<S><<<grid, RowMap<S>::THREADS, 0, st>>>(a);
@@ -331,11 +431,11 @@ struct CgHostOut {
     ens_cg_stats *stats;
 };
 
-template <int S>
+template <int S, bool DF>
 static int cg_run(const ens_graph *g, const double *vals, const double *b, double *x, double tol,
                   int max_iter, int flags, int check_every, void *work, CgHostOut out,
                   cudaStream_t st) {
-    using K = CgKernels<S>;
+    using K = CgKernels<S, DF>;
     const int64_t n = g->num_rows;
     char *w = static_cast<char *>(work);
     CgArgs a;
@@ -350,6 +450,7 @@ static int cg_run(const ens_graph *g, const double *vals, const double *b, doubl
     a.r = reinterpret_cast<double *>(w); w += align256(sizeof(double) * (size_t)n * S);
     a.p = reinterpret_cast<double *>(w); w += align256(sizeof(double) * (size_t)n * S);
     a.q = reinterpret_cast<double *>(w); w += align256(sizeof(double) * (size_t)n * S);
+    a.pdf = reinterpret_cast<float2 *>(w); w += align256(sizeof(double) * (size_t)n * S);
     dot_tree_layout(&a.t1, n, S, w);
     w += dot_tree_bytes(n, S);
     dot_tree_layout(&a.t2, n, 2 * S, w);
@@ -374,7 +475,7 @@ static int cg_run(const ens_graph *g, const double *vals, const double *b, doubl
     auto destroy_events = [&]() { for (auto &e : ev) cudaEventDestroy(e); };
 
     K::init(a, grid, st);
-    ++launches;
+    launches += 2;
     ENS_LAUNCH_CHECK("cg_init_kernel");
 
     cudaGraphExec_t gexec = nullptr;
@@ -471,6 +572,15 @@ static int cg_run(const ens_graph *g, const double *vals, const double *b, doubl
     return first_bad;
 }
 
+template <int S>
+static int cg_dispatch_df(const ens_graph *g, const double *vals, const double *b, double *x,
+                          double tol, int max_iter, int flags, int check_every, void *work,
+                          CgHostOut out, cudaStream_t st) {
+    if (flags & ENS_CG_DF64)
+        return cg_run<S, true>(g, vals, b, x, tol, max_iter, flags, check_every, work, out, st);
+    return cg_run<S, false>(g, vals, b, x, tol, max_iter, flags, check_every, work, out, st);
+}
+
 }  // namespace ens
 
 using namespace ens;
@@ -501,10 +611,10 @@ extern "C" int ens_cg(const ens_graph *graph, int s, const double *values, const
     CgHostOut out{iters_host, relres_host, status_host, stats_host};
     cudaStream_t st = as_stream(stream);
     switch (s) {
-        case 1: return cg_run<1>(graph, values, b, x, tol, max_iter, flags, check_every, work, out, st);
-        case 4: return cg_run<4>(graph, values, b, x, tol, max_iter, flags, check_every, work, out, st);
-        case 8: return cg_run<8>(graph, values, b, x, tol, max_iter, flags, check_every, work, out, st);
-        case 16: return cg_run<16>(graph, values, b, x, tol, max_iter, flags, check_every, work, out, st);
-        default: return cg_run<32>(graph, values, b, x, tol, max_iter, flags, check_every, work, out, st);
+        case 1: return cg_dispatch_df<1>(graph, values, b, x, tol, max_iter, flags, check_every, work, out, st);
+        case 4: return cg_dispatch_df<4>(graph, values, b, x, tol, max_iter, flags, check_every, work, out, st);
+        case 8: return cg_dispatch_df<8>(graph, values, b, x, tol, max_iter, flags, check_every, work, out, st);
+        case 16: return cg_dispatch_df<16>(graph, values, b, x, tol, max_iter, flags, check_every, work, out, st);
+        default: return cg_dispatch_df<32>(graph, values, b, x, tol, max_iter, flags, check_every, work, out, st);
     }
 }

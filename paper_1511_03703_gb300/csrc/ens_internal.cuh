@@ -111,25 +111,34 @@ void dot_tree_layout(DotTree *t, int64_t n_rows, int width, void *base);
 // zero all arrival counters of a tree (the tree's kernels self-reset them)
 int dot_tree_clear(const DotTree &t, cudaStream_t st);
 
-// Device: called by all threads of a CTA after it wrote level-1 item `item`
-// (buf[1][item*width ...]) with plain stores.  Propagates through the levels;
-// returns true in the single CTA that produced the top value (buf[levels][0..width)).
-__device__ __forceinline__ bool dot_tree_propagate(const DotTree &t, int64_t item) {
+// Device: called by all threads of a CTA after the CTA wrote the level-1
+// items [item0, item0 + nitems) (buf[1][item*width ...], plain stores, all
+// items inside one level-2 group, i.e. item0/32 == (item0+nitems-1)/32).
+// Propagates through the levels; returns true in the single CTA that produced
+// the top value (buf[levels][0..width)).  Release: the barrier orders the
+// CTA's stores before thread 0's gpu-scope fence and arrival atomic (fences
+// are cumulative); acquire: the last arriver fences after its atomic and the
+// barrier orders the other threads' L2 reads after it.
+__device__ __forceinline__ bool dot_tree_propagate(const DotTree &t, int64_t item0, int nitems) {
     __shared__ int s_last;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
+    int64_t item = item0;
+    int add = nitems;
+    __syncthreads();
     for (int l = 1; l < t.levels; ++l) {
         const int64_t g = item >> 5;
         const int cnt = (int)min((int64_t)32, t.count[l] - (g << 5));
-        __threadfence();
-        __syncthreads();
         if (tid == 0) {
-            int old = atomicAdd(&t.counter[l][g], 1);
-            s_last = (old == cnt - 1);
-            if (s_last) t.counter[l][g] = 0;  // self-reset for the next launch
+            __threadfence();
+            const int old = atomicAdd(&t.counter[l][g], add);
+            s_last = (old + add == cnt);
+            if (s_last) {
+                t.counter[l][g] = 0;  // self-reset for the next launch
+                __threadfence();
+            }
         }
         __syncthreads();
         if (!s_last) return false;
-        __threadfence();
         const double *src = t.buf[l];
         double *dst = t.buf[l + 1];
         for (int w = warp; w < t.width; w += nwarps) {
@@ -137,9 +146,11 @@ __device__ __forceinline__ bool dot_tree_propagate(const DotTree &t, int64_t ite
             v = warp_tree32(v);
             if (lane == 0) dst[g * t.width + w] = v;
         }
+        __syncthreads();
         item = g;
+        add = 1;
     }
-    __threadfence();
+    if (tid == 0) __threadfence();
     __syncthreads();
     return true;
 }

@@ -5,12 +5,25 @@
 // thread g owns members 2g and 2g+1, so one entry's s values are read as one
 // contiguous run of 16-byte loads (s*8 bytes) and x[col*s + 2g..] as one
 // coalesced 16-byte gather; the column index is one broadcast load per row.
-// For s = 1 each row gets 4 threads that stride over the row's entries.
+// For s = 1 each row gets 2 threads that take alternate entries.
 //
 // Summation order (identical for every s, so member e's result does not
 // depend on the ensemble it is solved in): entry j of a row goes to partial
-// j mod 4, each partial accumulates with FMA in increasing j, and the row
-// value is (p0 + p1) + (p2 + p3).
+// j mod 2, each partial accumulates in increasing j, and the row value is
+// p0 + p1.
+//
+// Two arithmetic forms of the FP64 product:
+//  - native: IEEE FP64 FMA.  GB300 issues 2 DFMA per cycle per SM (1/64 of
+//    its FP32 rate) and the ensemble SpMV needs one FMA per 8 bytes, so this
+//    form is bound by the FP64 pipe near 60-65 % of the HBM bandwidth.
+//  - double-float ("df"): each FP64 value is split into two floats (hi + lo,
+//    truncation, 47 bits), x arrives pre-split, products are formed exactly
+//    (hi*hi by FMA error recovery, cross terms in FP32) and sums carried as an
+//    unevaluated float pair by TwoSum (Knuth; Dekker's double-float
+//    arithmetic, 1971).  About 27 FP32/INT ops per term on the 128/cycle/SM
+//    pipes; error per term <= ~6*2^-48 |a x|, so a row is within
+//    ~1.2e-13 * sum |a_j x_j| of the exact value.  Values outside
+//    [2^-103, 2^128) and non-finite values take an FP64 FMA instead.
 #pragma once
 #include "ens_internal.cuh"
 
@@ -18,7 +31,7 @@ namespace ens {
 
 template <int S>
 struct RowMap {
-    static constexpr int G = (S == 1) ? 4 : S / 2;  // threads per row
+    static constexpr int G = (S == 1) ? 2 : S / 2;  // threads per row
     static constexpr int THREADS = 32 * G;          // one 32-row chunk per CTA
 };
 
@@ -60,20 +73,56 @@ __device__ __forceinline__ double2 ld_x2(const double *x, int64_t i) {
     return __ldg(reinterpret_cast<const double2 *>(x + i));
 }
 
-// y for members (2g, 2g+1) of row R, s >= 2, FP64 accumulation
-template <int S, typename V>
-__device__ __forceinline__ double2 row_spmv2(const int32_t *__restrict__ row_map,
-                                             const int32_t *__restrict__ col,
-                                             const V *__restrict__ vals,
-                                             const double *__restrict__ x, int64_t R, int g) {
-    const int rs = __ldg(row_map + R), re = __ldg(row_map + R + 1);
-    double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;  // member 2g, partials 0..3
-    double b0 = 0.0, b1 = 0.0, b2 = 0.0, b3 = 0.0;  // member 2g+1
+// ------------------------------------------------------ column staging
+// A CTA stages the row offsets and column indices of its 32-row chunk in
+// shared memory (one coalesced copy), so each x gather waits for one shared
+// load instead of a dependent global load.  Chunks with more than kColCap
+// entries (not produced by the hex mesh, whose rows hold at most 27) read
+// their columns from global memory instead.
+constexpr int kColCap = 1024;
+
+struct ChunkCols {
+    int rm[33];
+    int col[kColCap];
+};
+
+struct ColShared {
+    const int *s;
+    int base;
+    __device__ __forceinline__ int operator()(int j) const { return s[j - base]; }
+};
+struct ColGlobal {
+    const int32_t *p;
+    __device__ __forceinline__ int operator()(int j) const { return __ldg(p + j); }
+};
+
+// all threads of the CTA; returns true when the columns are staged
+__device__ __forceinline__ bool stage_chunk(ChunkCols &cc, const int32_t *__restrict__ row_map,
+                                            const int32_t *__restrict__ col, int64_t chunk,
+                                            int32_t n) {
+    const int64_t r0 = chunk * 32;
+    const int nr = (int)min((int64_t)32, (int64_t)n - r0);
+    for (int i = threadIdx.x; i <= nr; i += blockDim.x) cc.rm[i] = __ldg(row_map + r0 + i);
+    __syncthreads();
+    const int e0 = cc.rm[0], cnt = cc.rm[nr] - e0;
+    const bool staged = cnt <= kColCap;
+    if (staged)
+        for (int i = threadIdx.x; i < cnt; i += blockDim.x) cc.col[i] = __ldg(col + e0 + i);
+    __syncthreads();
+    return staged;
+}
+
+// ------------------------------------------------------------ native FP64
+// y for members (2g, 2g+1) of a row with entries [rs, re), s >= 2
+template <int S, typename V, typename CA>
+__device__ __forceinline__ double2 row_spmv2(CA colf, int rs, int re, const V *__restrict__ vals,
+                                             const double *__restrict__ x, int g) {
+    double a0 = 0.0, a1 = 0.0;  // member 2g, partials 0 / 1
+    double b0 = 0.0, b1 = 0.0;  // member 2g+1
     const int m = 2 * g;
     int j = rs;
     for (; j + 4 <= re; j += 4) {
-        const int c0 = __ldg(col + j), c1 = __ldg(col + j + 1), c2 = __ldg(col + j + 2),
-                  c3 = __ldg(col + j + 3);
+        const int c0 = colf(j), c1 = colf(j + 1), c2 = colf(j + 2), c3 = colf(j + 3);
         const double2 v0 = ValLoad<V>::two(vals, (int64_t)j * S + m);
         const double2 v1 = ValLoad<V>::two(vals, (int64_t)(j + 1) * S + m);
         const double2 v2 = ValLoad<V>::two(vals, (int64_t)(j + 2) * S + m);
@@ -84,48 +133,274 @@ __device__ __forceinline__ double2 row_spmv2(const int32_t *__restrict__ row_map
         const double2 x3 = ld_x2(x, (int64_t)c3 * S + m);
         a0 = fma(v0.x, x0.x, a0); b0 = fma(v0.y, x0.y, b0);
         a1 = fma(v1.x, x1.x, a1); b1 = fma(v1.y, x1.y, b1);
-        a2 = fma(v2.x, x2.x, a2); b2 = fma(v2.y, x2.y, b2);
-        a3 = fma(v3.x, x3.x, a3); b3 = fma(v3.y, x3.y, b3);
+        a0 = fma(v2.x, x2.x, a0); b0 = fma(v2.y, x2.y, b0);
+        a1 = fma(v3.x, x3.x, a1); b1 = fma(v3.y, x3.y, b1);
     }
-    if (j < re) {
+    for (; j < re; ++j) {
         const double2 v = ValLoad<V>::two(vals, (int64_t)j * S + m);
-        const double2 xv = ld_x2(x, (int64_t)__ldg(col + j) * S + m);
-        a0 = fma(v.x, xv.x, a0); b0 = fma(v.y, xv.y, b0);
+        const double2 xv = ld_x2(x, (int64_t)colf(j) * S + m);
+        if ((j - rs) & 1) { a1 = fma(v.x, xv.x, a1); b1 = fma(v.y, xv.y, b1); }
+        else { a0 = fma(v.x, xv.x, a0); b0 = fma(v.y, xv.y, b0); }
     }
-    if (j + 1 < re) {
-        const double2 v = ValLoad<V>::two(vals, (int64_t)(j + 1) * S + m);
-        const double2 xv = ld_x2(x, (int64_t)__ldg(col + j + 1) * S + m);
-        a1 = fma(v.x, xv.x, a1); b1 = fma(v.y, xv.y, b1);
-    }
-    if (j + 2 < re) {
-        const double2 v = ValLoad<V>::two(vals, (int64_t)(j + 2) * S + m);
-        const double2 xv = ld_x2(x, (int64_t)__ldg(col + j + 2) * S + m);
-        a2 = fma(v.x, xv.x, a2); b2 = fma(v.y, xv.y, b2);
-    }
-    return make_double2((a0 + a1) + (a2 + a3), (b0 + b1) + (b2 + b3));
+    return make_double2(a0 + a1, b0 + b1);
 }
 
-// y of row R for s = 1: 4 threads (g = 0..3, consecutive lanes) per row; the
-// result is returned on all 4 lanes.  Must be called by full warps.
-template <typename V>
-__device__ __forceinline__ double row_spmv1(const int32_t *__restrict__ row_map,
-                                            const int32_t *__restrict__ col,
-                                            const V *__restrict__ vals,
-                                            const double *__restrict__ x, int64_t R, int g,
-                                            bool valid) {
+// y of a row for s = 1: 2 threads (g = 0, 1, adjacent lanes) per row; the
+// result is returned on both lanes.  Must be called by full warps.
+template <typename V, typename CA>
+__device__ __forceinline__ double row_spmv1(CA colf, int rs, int re, const V *__restrict__ vals,
+                                            const double *__restrict__ x, int g, bool valid) {
     double a = 0.0;
-    if (valid) {
-        const int rs = __ldg(row_map + R), re = __ldg(row_map + R + 1);
-        for (int j = rs + g; j < re; j += 4) a = fma(ValLoad<V>::one(vals, j), __ldg(x + __ldg(col + j)), a);
-    }
-    a += __shfl_xor_sync(0xffffffffu, a, 1);   // p0+p1 | p2+p3
-    a += __shfl_xor_sync(0xffffffffu, a, 2);   // (p0+p1)+(p2+p3)
+    if (valid)
+        for (int j = rs + g; j < re; j += 2) a = fma(ValLoad<V>::one(vals, j), __ldg(x + colf(j)), a);
+    a += __shfl_xor_sync(0xffffffffu, a, 1);   // p0 + p1 (commutative: same on both lanes)
     return a;
 }
 
+// --------------------------------------------------------- double-float
+struct DfAcc {
+    float s, c;   // unevaluated sum s + c
+};
+
+__device__ __forceinline__ DfAcc df_zero() { return DfAcc{0.0f, 0.0f}; }
+
+// Knuth's TwoSum: s + e == a + b exactly, s = fl(a + b)
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
+    s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+// Split of a double into hi + lo floats by truncation of its fraction:
+// hi keeps the sign, the exponent and the top 23 fraction bits, lo the next 23.
+// Returns false (hi = lo = 0) when |a| is outside [2^-103, 2^128) or not
+// finite; exact zero gives hi = lo = 0 and true.
+__device__ __forceinline__ bool df_split_trunc(double a, float &hi, float &lo) {
+    const uint32_t uh = (uint32_t)__double2hiint(a), ul = (uint32_t)__double2loint(a);
+    const uint32_t e = (uh >> 20) & 0x7ffu;
+    const uint32_t sgn = uh & 0x80000000u;
+    const bool zero = (e == 0u);
+    const bool ok = (e - 920u) <= 230u;  // 2^-103 <= |a| < 2^128
+    const uint32_t frac_hi = __funnelshift_l(ul, uh, 3) & 0x7fffffu;
+    const uint32_t hb = sgn | ((e - 896u) << 23) | frac_hi;
+    const float one_f = __uint_as_float(0x3f800000u | ((ul & 0x1fffffffu) >> 6));
+    const float scale = __uint_as_float(sgn | ((e - 919u) << 23));
+    hi = ok ? __uint_as_float(hb) : 0.0f;
+    lo = ok ? __fmul_rn(__fsub_rn(one_f, 1.0f), scale) : 0.0f;
+    return ok || zero;
+}
+
+// Split of a vector element for the pre-split x: the same truncating split,
+// integer and FP32 instructions only.  ok = false when v is non-zero and
+// outside [2^-103, 2^128) (the caller then falls back to FP64 products).
+__device__ __forceinline__ float2 df_split_vec(double v, bool &ok) {
+    float hi, lo;
+    const bool in = df_split_trunc(v, hi, lo);
+    ok = in;
+    return make_float2(hi, lo);
+}
+
+// Exact float -> double by moving the bit fields (no FP64-pipe conversion);
+// zero, subnormal and non-finite inputs take the hardware conversion.
+__device__ __forceinline__ double f2d_exact(float f) {
+    const uint32_t u = __float_as_uint(f);
+    const uint32_t e = (u >> 23) & 0xffu;
+    if (e == 0u || e == 0xffu) return (double)f;
+    const uint32_t hi = (u & 0x80000000u) | ((e + 896u) << 20) | ((u & 0x7fffffu) >> 3);
+    const uint32_t lo = u << 29;
+    return __hiloint2double((int)hi, (int)lo);
+}
+
+// one term a*(xh + xl) into A; returns false when a needs the FP64 path
+// (the term then contributes nothing here and is added by df_fixup)
+__device__ __forceinline__ bool df_term(DfAcc &A, double a, float xh, float xl) {
+    float ah, al;
+    const bool ok = df_split_trunc(a, ah, al);
+    const float p = __fmul_rn(ah, xh);
+    float e = __fmaf_rn(ah, xh, -p);        // exact: ah*xh = p + e
+    e = __fmaf_rn(ah, xl, e);
+    e = __fmaf_rn(al, xh, e);
+    float s, t;
+    two_sum(A.s, p, s, t);
+    A.s = s;
+    A.c = __fadd_rn(A.c, __fadd_rn(t, e));
+    return ok;
+}
+
+// p0 + p1 with the same operation order on every lane and every s; fb (the
+// FP64 sum of out-of-range terms) is added only when non-zero
+__device__ __forceinline__ double df_finish(const DfAcc &A0, const DfAcc &A1, double fb) {
+    float s, t;
+    two_sum(A0.s, A1.s, s, t);
+    const float c = __fadd_rn(__fadd_rn(A0.c, A1.c), t);
+    const double y = f2d_exact(s) + f2d_exact(c);
+    return (fb != 0.0) ? y + fb : y;
+}
+
+// Sources of the pre-split x: XPre reads the float pairs written by the CG
+// kernels; XSplit reads FP64 x and splits it on the fly with the same
+// rounding (used by ens_spmv, where x arrives in FP64).
+struct XPre {
+    using ptr = const float2 *;
+    __device__ __forceinline__ static float4 two(ptr x, int64_t i) {
+        return __ldg(reinterpret_cast<const float4 *>(x + i));
+    }
+    __device__ __forceinline__ static float2 one(ptr x, int64_t i) { return __ldg(x + i); }
+};
+struct XSplit {
+    using ptr = const double *;
+    __device__ __forceinline__ static float4 two(ptr x, int64_t i) {
+        const double2 v = ld_x2(x, i);
+        bool ok;
+        const float2 a = df_split_vec(v.x, ok), b = df_split_vec(v.y, ok);
+        return make_float4(a.x, a.y, b.x, b.y);
+    }
+    __device__ __forceinline__ static float2 one(ptr x, int64_t i) {
+        bool ok;
+        return df_split_vec(__ldg(x + i), ok);
+    }
+};
+
+// FP64 sum, in entry order, of the terms whose value is outside the split
+// range (rare: run only by rows that met one)
+template <int S, typename XS, typename CA>
+__device__ __noinline__ double2 df_fixup2(CA colf, int rs, int re, const double *__restrict__ vals,
+                                          typename XS::ptr x, int m) {
+    double f0[2] = {0.0, 0.0}, f1[2] = {0.0, 0.0};  // entries of even / odd position
+    for (int j = rs; j < re; ++j) {
+        const double2 v = ValLoad<double>::two(vals, (int64_t)j * S + m);
+        float h, l;
+        const bool ok0 = df_split_trunc(v.x, h, l), ok1 = df_split_trunc(v.y, h, l);
+        if (ok0 && ok1) continue;
+        const float4 xv = XS::two(x, (int64_t)colf(j) * S + m);
+        const int par = (j - rs) & 1;
+        if (!ok0) f0[par] = fma(v.x, (double)xv.x + (double)xv.y, f0[par]);
+        if (!ok1) f1[par] = fma(v.y, (double)xv.z + (double)xv.w, f1[par]);
+    }
+    return make_double2(f0[0] + f0[1], f1[0] + f1[1]);
+}
+
+// df form of row_spmv2 (members 2g, 2g+1 of a row with entries [rs, re))
+template <int S, typename XS, typename CA>
+__device__ __forceinline__ double2 row_spmv2_df(CA colf, int rs, int re,
+                                                const double *__restrict__ vals,
+                                                typename XS::ptr __restrict__ x, int g) {
+    DfAcc a0 = df_zero(), a1 = df_zero(), b0 = df_zero(), b1 = df_zero();
+    bool ok = true;
+    const int m = 2 * g;
+    int j = rs;
+    for (; j + 4 <= re; j += 4) {
+        const int c0 = colf(j), c1 = colf(j + 1), c2 = colf(j + 2), c3 = colf(j + 3);
+        const double2 v0 = ValLoad<double>::two(vals, (int64_t)j * S + m);
+        const double2 v1 = ValLoad<double>::two(vals, (int64_t)(j + 1) * S + m);
+        const double2 v2 = ValLoad<double>::two(vals, (int64_t)(j + 2) * S + m);
+        const double2 v3 = ValLoad<double>::two(vals, (int64_t)(j + 3) * S + m);
+        const float4 x0 = XS::two(x, (int64_t)c0 * S + m);
+        const float4 x1 = XS::two(x, (int64_t)c1 * S + m);
+        const float4 x2 = XS::two(x, (int64_t)c2 * S + m);
+        const float4 x3 = XS::two(x, (int64_t)c3 * S + m);
+        ok &= df_term(a0, v0.x, x0.x, x0.y); ok &= df_term(b0, v0.y, x0.z, x0.w);
+        ok &= df_term(a1, v1.x, x1.x, x1.y); ok &= df_term(b1, v1.y, x1.z, x1.w);
+        ok &= df_term(a0, v2.x, x2.x, x2.y); ok &= df_term(b0, v2.y, x2.z, x2.w);
+        ok &= df_term(a1, v3.x, x3.x, x3.y); ok &= df_term(b1, v3.y, x3.z, x3.w);
+    }
+    for (; j < re; ++j) {
+        const double2 v = ValLoad<double>::two(vals, (int64_t)j * S + m);
+        const float4 xv = XS::two(x, (int64_t)colf(j) * S + m);
+        if ((j - rs) & 1) { ok &= df_term(a1, v.x, xv.x, xv.y); ok &= df_term(b1, v.y, xv.z, xv.w); }
+        else { ok &= df_term(a0, v.x, xv.x, xv.y); ok &= df_term(b0, v.y, xv.z, xv.w); }
+    }
+    double2 fb = make_double2(0.0, 0.0);
+    if (!ok) fb = df_fixup2<S, XS, CA>(colf, rs, re, vals, x, m);
+    return make_double2(df_finish(a0, a1, fb.x), df_finish(b0, b1, fb.y));
+}
+
+// df form of row_spmv1 (s = 1, 2 threads per row, result on both lanes)
+template <typename XS, typename CA>
+__device__ __forceinline__ double row_spmv1_df(CA colf, int rs, int re,
+                                               const double *__restrict__ vals,
+                                               typename XS::ptr __restrict__ x, int g, bool valid) {
+    DfAcc a = df_zero();
+    bool ok = true;
+    if (valid)
+        for (int j = rs + g; j < re; j += 2) {
+            const float2 xv = XS::one(x, colf(j));
+            ok &= df_term(a, ValLoad<double>::one(vals, j), xv.x, xv.y);
+        }
+    double fb = 0.0;
+    if (!ok)
+        for (int j = rs + g; j < re; j += 2) {
+            const double v = ValLoad<double>::one(vals, j);
+            float h, l;
+            if (df_split_trunc(v, h, l)) continue;
+            const float2 xv = XS::one(x, colf(j));
+            fb = fma(v, (double)xv.x + (double)xv.y, fb);
+        }
+    DfAcc o;
+    o.s = __shfl_xor_sync(0xffffffffu, a.s, 1);
+    o.c = __shfl_xor_sync(0xffffffffu, a.c, 1);
+    const double ofb = __shfl_xor_sync(0xffffffffu, fb, 1);
+    return (g == 0) ? df_finish(a, o, fb + ofb) : df_finish(o, a, ofb + fb);
+}
+
+// ------------------------------------------- chunk-level row evaluation
+// Value(s) of the calling thread's row r (members 2g, 2g+1; s = 1: the row,
+// in .x) inside a staged 32-row chunk.  valid = the row exists.
+template <int S, typename V>
+__device__ __forceinline__ double2 chunk_spmv(const ChunkCols &cc, bool staged,
+                                              const int32_t *__restrict__ col,
+                                              const V *__restrict__ vals,
+                                              const double *__restrict__ x, int r, int g,
+                                              bool valid) {
+    const int rs = valid ? cc.rm[r] : 0, re = valid ? cc.rm[r + 1] : 0;
+    if constexpr (S == 1) {
+        const double v = staged ? row_spmv1<V>(ColShared{cc.col, cc.rm[0]}, rs, re, vals, x, g, valid)
+                                : row_spmv1<V>(ColGlobal{col}, rs, re, vals, x, g, valid);
+        return make_double2(v, 0.0);
+    } else {
+        if (!valid) return make_double2(0.0, 0.0);
+        return staged ? row_spmv2<S, V>(ColShared{cc.col, cc.rm[0]}, rs, re, vals, x, g)
+                      : row_spmv2<S, V>(ColGlobal{col}, rs, re, vals, x, g);
+    }
+}
+
+template <int S, typename XS>
+__device__ __forceinline__ double2 chunk_spmv_df(const ChunkCols &cc, bool staged,
+                                                 const int32_t *__restrict__ col,
+                                                 const double *__restrict__ vals,
+                                                 typename XS::ptr __restrict__ x, int r, int g,
+                                                 bool valid) {
+    const int rs = valid ? cc.rm[r] : 0, re = valid ? cc.rm[r + 1] : 0;
+    if constexpr (S == 1) {
+        const double v = staged ? row_spmv1_df<XS>(ColShared{cc.col, cc.rm[0]}, rs, re, vals, x, g, valid)
+                                : row_spmv1_df<XS>(ColGlobal{col}, rs, re, vals, x, g, valid);
+        return make_double2(v, 0.0);
+    } else {
+        if (!valid) return make_double2(0.0, 0.0);
+        return staged ? row_spmv2_df<S, XS>(ColShared{cc.col, cc.rm[0]}, rs, re, vals, x, g)
+                      : row_spmv2_df<S, XS>(ColGlobal{col}, rs, re, vals, x, g);
+    }
+}
+
 // Level-1 tree step: every thread of the CTA holds the per-row products of its
-// (row r, members 2g, 2g+1) [s >= 2] or (row r) [s = 1, value on all G lanes].
+// (row r, members 2g, 2g+1) [s >= 2] or (row r) [s = 1, value on both lanes].
 // Writes the chunk's per-member partials to t.buf[1][chunk*width + off + e].
+// The 32 rows are combined by the halving tree v[i] += v[i + h], h = 16..1,
+// which is the butterfly order of warp_tree32 (lane 0's value); the adds of
+// all members are packed into full warps (31*S adds, not 5*32*S), which
+// matters on GB300's 1/64-rate FP64 pipe.
+template <int S>
+__device__ __forceinline__ void halving_tree(double (*sm)[S + 1], int nthreads) {
+#pragma unroll
+    for (int h = 16; h >= 1; h >>= 1) {
+        for (int it = threadIdx.x; it < h * S; it += nthreads) {
+            const int i = it / S, e = it % S;
+            sm[i][e] += sm[i + h][e];
+        }
+        __syncthreads();
+    }
+}
+
 template <int S>
 __device__ __forceinline__ void chunk_tree(double (*sm)[S + 1], double v0, double v1, int r,
                                            int g, const DotTree &t, int64_t chunk, int off) {
@@ -136,11 +411,8 @@ __device__ __forceinline__ void chunk_tree(double (*sm)[S + 1], double v0, doubl
         sm[r][2 * g + 1] = v1;
     }
     __syncthreads();
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    for (int e = warp; e < S; e += nw) {
-        double v = warp_tree32(sm[lane][e]);
-        if (lane == 0) t.buf[1][chunk * t.width + off + e] = v;
-    }
+    halving_tree<S>(sm, blockDim.x);
+    for (int e = threadIdx.x; e < S; e += blockDim.x) t.buf[1][chunk * t.width + off + e] = sm[0][e];
     __syncthreads();
 }
 

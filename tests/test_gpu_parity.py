@@ -100,7 +100,7 @@ def test_assembly_matches_oracle(torch, N, M, s):
 # ------------------------------------------------------------------ A4 SpMV
 @pytest.mark.parametrize("N", [3, 8, 13])
 @pytest.mark.parametrize("s", S_ALL)
-@pytest.mark.parametrize("dtype", ["float64", "float32", "bfloat16"])
+@pytest.mark.parametrize("dtype", ["float64", "float64_df", "float32", "bfloat16"])
 def test_spmv_matches_oracle(torch, N, s, dtype):
     M = 10
     xs = inputs.kl_samples(200 + N, 0, min(s, 4), M)
@@ -108,15 +108,39 @@ def test_spmv_matches_oracle(torch, N, s, dtype):
     ov = [ov[e % len(ov)] for e in range(s)]
     n = len(rm) - 1
     xm = [inputs.random_vector(300 + e, n) for e in range(s)]
-    vt = torch.from_numpy(O.to_ensemble(ov)).to(getattr(torch, dtype))
+    df = dtype == "float64_df"
+    vt = torch.from_numpy(O.to_ensemble(ov)).to(getattr(torch, "float64" if df else dtype))
     vq = [vt.reshape(-1, s)[:, e].double().numpy() for e in range(s)]   # values as stored
     y = torch.empty(n * s, dtype=torch.float64, device=gpu())
     graph = E.Graph(to_dev(rm), to_dev(col))
-    E.spmv(graph, s, vt.to(gpu()), to_dev(O.to_ensemble(xm)), y)
+    E.spmv(graph, s, vt.to(gpu()), to_dev(O.to_ensemble(xm)), y, df=df)
     Y = ens_cols(to_np(y), s)
     for e in range(s):
         ref = O.spmv(rm, col, vq[e], xm[e])
         assert np.all(np.abs(Y[:, e] - ref) <= spmv_bound(rm, col, vq[e], xm[e])), e
+
+
+@pytest.mark.parametrize("s", [1, 8, 32])
+def test_spmv_df_extreme_values_take_exact_path(torch, s):
+    """Values outside the double-float split range ([2^-103, 2^128)), exact
+    zeros and mixed magnitudes within a row stay inside the 1e-12 bound."""
+    N, M = 5, 10
+    xs = inputs.kl_samples(250, 0, 1, M)
+    rm, col, ov, _ = oracle_members(N, M, xs)
+    n = len(rm) - 1
+    scale = np.ones(len(col))
+    scale[::7] = 1e-120      # below the split range: FP64 fallback
+    scale[3::11] = 1e60      # above it
+    scale[5::13] = 0.0       # exact zeros
+    vals = [ov[0] * scale * (1.0 + 0.01 * e) for e in range(s)]
+    xm = [inputs.random_vector(330 + e, n, -1e3, 1e3) for e in range(s)]
+    y = torch.empty(n * s, dtype=torch.float64, device=gpu())
+    graph = E.Graph(to_dev(rm), to_dev(col))
+    E.spmv(graph, s, to_dev(O.to_ensemble(vals)), to_dev(O.to_ensemble(xm)), y, df=True)
+    Y = ens_cols(to_np(y), s)
+    for e in range(s):
+        ref = O.spmv(rm, col, vals[e], xm[e])
+        assert np.all(np.abs(Y[:, e] - ref) <= spmv_bound(rm, col, vals[e], xm[e])), e
 
 
 def test_spmv_s_invariant_bitwise(torch):
@@ -130,9 +154,11 @@ def test_spmv_s_invariant_bitwise(torch):
         y = torch.empty(mesh.n * s, dtype=torch.float64, device=gpu())
         E.spmv(mesh.graph, s, vals, to_dev(O.to_ensemble(xm[:s])), y)
         Y = ens_cols(to_np(y), s)
+        E.spmv(mesh.graph, s, vals, to_dev(O.to_ensemble(xm[:s])), y, df=True)
+        Ydf = ens_cols(to_np(y), s)
         if ref is None:
-            ref = Y[:, 0].copy()
-        assert np.array_equal(Y[:, 0], ref), s
+            ref = (Y[:, 0].copy(), Ydf[:, 0].copy())
+        assert np.array_equal(Y[:, 0], ref[0]) and np.array_equal(Ydf[:, 0], ref[1]), s
 
 
 # ------------------------------------------------------------------- A5 dot
@@ -179,7 +205,7 @@ def gpu_solve(mesh, xs, tol, max_iter=10000, flags=0, x0=None, check_every=8):
     return ens_cols(to_np(x), s), it, rr, st, stats
 
 
-def compare_cg(mesh, xs, tol, xg, itg):
+def compare_cg(mesh, xs, tol, xg, itg, flags=0):
     rm, col, ov, ob = oracle_members(mesh.N, mesh.M, xs)
     for e in range(xs.shape[0]):
         xo, ito, rro, sto = O.cg(rm, col, ov[e], ob[e], tol=tol)
@@ -191,7 +217,7 @@ def compare_cg(mesh, xs, tol, xg, itg):
         else:  # stopping decided by rounding: compare at a fixed iteration count
             k = max(itg[e], ito)
             xo2, _, _, _ = O.cg(rm, col, ov[e], ob[e], tol=0.0, max_iter=k)
-            xg2, it2, _, _, _ = gpu_solve(mesh, xs, 0.0, max_iter=k)
+            xg2, it2, _, _, _ = gpu_solve(mesh, xs, 0.0, max_iter=k, flags=flags)
             assert it2[e] == k
             assert np.linalg.norm(xg2[:, e] - xo2) / np.linalg.norm(xo2) <= 1e-10
 
@@ -212,12 +238,13 @@ def test_cg_small_workload_exact_iterations(torch):
 
 
 @pytest.mark.parametrize("s", S_ALL)
-def test_cg_matches_oracle_ragged_mesh(torch, s):
+@pytest.mark.parametrize("flags", [0, E.CG_DF64])
+def test_cg_matches_oracle_ragged_mesh(torch, s, flags):
     mesh = E.Mesh(13, 10)   # 2744 rows: 85 full 32-row chunks and a ragged one
     xs = inputs.kl_samples(900, 0, s, 10)
-    xg, it, rr, st, _ = gpu_solve(mesh, xs, 1e-8)
+    xg, it, rr, st, _ = gpu_solve(mesh, xs, 1e-8, flags=flags)
     assert all(v == 0 for v in st)
-    compare_cg(mesh, xs, 1e-8, xg, it)
+    compare_cg(mesh, xs, 1e-8, xg, it, flags)
 
 
 def test_cg_identical_members_bitwise(torch):
@@ -230,12 +257,13 @@ def test_cg_identical_members_bitwise(torch):
     assert len(set(it)) == 1 and all(np.array_equal(xg[:, 0], xg[:, e]) for e in range(8))
 
 
-def test_cg_sample_result_independent_of_s_bitwise(torch):
+@pytest.mark.parametrize("flags", [0, E.CG_DF64])
+def test_cg_sample_result_independent_of_s_bitwise(torch, flags):
     mesh = E.Mesh(9, 10)
     xs = inputs.kl_samples(4242, 0, 32, 10)
     ref = None
     for s in S_ALL:
-        xg, it, rr, st, _ = gpu_solve(mesh, xs[:s], 1e-9)
+        xg, it, rr, st, _ = gpu_solve(mesh, xs[:s], 1e-9, flags=flags)
         cur = (xg[:, 0].copy(), it[0], rr[0])
         if ref is None:
             ref = cur
@@ -333,9 +361,10 @@ def test_scale_64cubed_s32_sampled(torch):
         ref = O.spmv(rm, col, ov[e % 2], xm[e])
         assert np.all(np.abs(Y[:, e] - ref) <= spmv_bound(rm, col, ov[e % 2], xm[e])), e
     # CG of the whole ensemble; two members against oracle solves
-    xg, it, rr, st, _ = gpu_solve(mesh, xs, 1e-8)
-    assert st == [0] * s and max(rr) < 2e-8
-    compare_cg_picked(mesh, xs, picks, rm, col, ov, ob, xg, it)
+    for flags in (0, E.CG_DF64):
+        xg, it, rr, st, _ = gpu_solve(mesh, xs, 1e-8, flags=flags)
+        assert st == [0] * s and max(rr) < 2e-8
+        compare_cg_picked(mesh, xs, picks, rm, col, ov, ob, xg, it)
 
 
 def compare_cg_picked(mesh, xs, picks, rm, col, ov, ob, xg, it):
