@@ -54,7 +54,12 @@ typedef enum ens_status {
  * split into two floats; error per term <= ~6*2^-48 |a x|, so a row is within
  * ~1.2e-13 * sum |a_j x_j|).  GB300 runs FP64 FMA at 1/64 of its FP32 rate,
  * which bounds the native form of the ensemble SpMV below the HBM roofline. */
-typedef enum ens_dtype { ENS_F64 = 0, ENS_F32 = 1, ENS_BF16 = 2, ENS_F64_DF = 3 } ens_dtype;
+/* ENS_F64_SPLIT: FP64 values and x; entries at even positions of a row are
+ * multiplied with the FP64 FMA, entries at odd positions in double-float, so
+ * both arithmetic pipes work at once; row value = p_even + p_odd. */
+typedef enum ens_dtype {
+    ENS_F64 = 0, ENS_F32 = 1, ENS_BF16 = 2, ENS_F64_DF = 3, ENS_F64_SPLIT = 4
+} ens_dtype;
 
 /* CRS graph (Fig. 2): row_map[num_rows+1], col_entry[num_entries] (device,
  * int32, columns ascending within a row).  Values live in a separate array in
@@ -128,9 +133,9 @@ int ens_assemble(const ens_graph *graph, const uint8_t *bmask, int s, int M,
 /* --------------------------------------------------------------- A4 SpMV */
 /* y = A_c x for the commuted ensemble matrix (Fig. 5 semantics):
  *   y[I*s+e] = sum_{entry in row I} values[entry*s+e] * x[col_entry[entry]*s+e].
- * dtype = ENS_F64 (values double), ENS_F32 (float), ENS_BF16 (bfloat16) or
- * ENS_F64_DF (double values, double-float arithmetic); x and y are double,
- * accumulation in FP64 (double-float for ENS_F64_DF).  The per-member sum
+ * dtype = ENS_F64 (values double), ENS_F32 (float), ENS_BF16 (bfloat16),
+ * ENS_F64_DF (double values, double-float arithmetic) or ENS_F64_SPLIT (double
+ * values, alternate entries FP64 / double-float); x and y are double.  The per-member sum
  * order is fixed and independent of s: entry j goes to partial j mod 2 and
  * the row value is p0 + p1, so member e's result is bitwise the same for
  * every s.  x, y, values 16-byte aligned when s > 1. */
@@ -182,9 +187,11 @@ enum {
                                 from member-summed dots, one convergence test */
     ENS_CG_GRAPH = 2,        /* replay the iteration through a captured CUDA graph */
     ENS_CG_TIME_SPMV = 4,    /* record CUDA events around each CG SpMV */
-    ENS_CG_DF64 = 8          /* CG SpMV in double-float arithmetic (see ENS_F64_DF);
+    ENS_CG_DF64 = 8,         /* CG SpMV in double-float arithmetic (see ENS_F64_DF);
                                 p is kept split as float pairs, all other vector
                                 arithmetic and every dot stays FP64 */
+    ENS_CG_SPLIT64 = 16      /* CG SpMV with alternate entries FP64 FMA / double-float
+                                (see ENS_F64_SPLIT); takes precedence over ENS_CG_DF64 */
 };
 
 /* Unpreconditioned CG (Hestenes-Stiefel) on each member of the ensemble

@@ -14,10 +14,10 @@ import threading
 __all__ = ["EnsError", "lib", "Graph", "Mesh", "mesh_sizes", "graph_build", "kl_table_size",
            "kl_setup", "mode_matrices", "assemble", "spmv", "dot", "dot_workspace_size", "dot_static", "cg",
            "cg_workspace_size", "CgStats", "F64", "F32", "BF16", "CG_COUPLED", "CG_GRAPH",
-           "CG_TIME_SPMV", "CG_DF64", "F64_DF"]
+           "CG_TIME_SPMV", "CG_DF64", "CG_SPLIT64", "F64_DF", "F64_SPLIT"]
 
-F64, F32, BF16, F64_DF = 0, 1, 2, 3
-CG_COUPLED, CG_GRAPH, CG_TIME_SPMV, CG_DF64 = 1, 2, 4, 8
+F64, F32, BF16, F64_DF, F64_SPLIT = 0, 1, 2, 3, 4
+CG_COUPLED, CG_GRAPH, CG_TIME_SPMV, CG_DF64, CG_SPLIT64 = 1, 2, 4, 8, 16
 OK, ERR_NOT_CONVERGED, ERR_BREAKDOWN = 0, 5, 6
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -188,14 +188,15 @@ def assemble(graph, bmask, s, M, modes, load, xi, sigma, kappa0, values, b, stre
 _DT = {"float64": F64, "float32": F32, "bfloat16": BF16}
 
 
-def spmv(graph, s, values, x, y, stream=None, df=False):
-    """y = A_c x.  df=True (float64 values): double-float arithmetic (ENS_F64_DF)."""
+def spmv(graph, s, values, x, y, stream=None, df=False, split=False):
+    """y = A_c x.  float64 values: df=True -> double-float arithmetic (ENS_F64_DF),
+    split=True -> alternate entries FP64 / double-float (ENS_F64_SPLIT)."""
     _require_cuda(values, x, y)
     dt = _DT[str(values.dtype).replace("torch.", "")]
-    if df:
+    if df or split:
         if dt != F64:
-            raise EnsError(2, "df arithmetic needs float64 values")
-        dt = F64_DF
+            raise EnsError(2, "df / split arithmetic needs float64 values")
+        dt = F64_SPLIT if split else F64_DF
     _check(lib().ens_spmv(graph.ref(), s, dt, _ptr(values), _ptr(x), _ptr(y), _stream(stream)))
 
 

@@ -75,7 +75,7 @@ __device__ __forceinline__ void store_split1(float2 *pdf, int64_t i, double v, i
 }
 
 // ------------------------------------------------------------------ K0
-template <int S, bool DF>
+template <int S, int MODE>
 __global__ void __launch_bounds__(RowMap<S>::THREADS, 1024 / RowMap<S>::THREADS) cg_init_kernel(CgArgs a) {
     constexpr int G = RowMap<S>::G;
     __shared__ double sm[32][S + 1];
@@ -93,7 +93,7 @@ __global__ void __launch_bounds__(RowMap<S>::THREADS, 1024 / RowMap<S>::THREADS)
             if (g == 0) {
                 a.r[R] = res;
                 a.p[R] = res;
-                if (DF) store_split1(a.pdf, R, res, &a.st->df_bad_any);
+                if (MODE != 0) store_split1(a.pdf, R, res, &a.st->df_bad_any);
             }
             rr0 = res * res;
             bb0 = bv * bv;
@@ -104,45 +104,54 @@ __global__ void __launch_bounds__(RowMap<S>::THREADS, 1024 / RowMap<S>::THREADS)
         const double2 res = make_double2(bv.x - ax.x, bv.y - ax.y);
         reinterpret_cast<double2 *>(a.r)[R * G + g] = res;
         reinterpret_cast<double2 *>(a.p)[R * G + g] = res;
-        if (DF) store_split(a.pdf, R * S + 2 * g, res.x, res.y, &a.st->df_bad_any);
+        if (MODE != 0) store_split(a.pdf, R * S + 2 * g, res.x, res.y, &a.st->df_bad_any);
         rr0 = res.x * res.x; rr1 = res.y * res.y;
         bb0 = bv.x * bv.x; bb1 = bv.y * bv.y;
     }
     chunk_tree<S>(sm, rr0, rr1, r, g, a.t2, blockIdx.x, 0);
     chunk_tree<S>(sm, bb0, bb1, r, g, a.t2, blockIdx.x, S);
     if (!dot_tree_propagate(a.t2, blockIdx.x, 1)) return;
-    if (threadIdx.x != 0) return;
+    if (threadIdx.x >= 32) return;
+    // epilogue: one lane per member (s <= 32); member sums in member order
+    const unsigned FULL = 0xffffffffu;
+    const int e = threadIdx.x;
     const double *top = a.t2.buf[a.t2.levels];
     CgState *st = a.st;
+    const double rr = (e < S) ? ld_cg(top + e) : 0.0, bb = (e < S) ? ld_cg(top + S + e) : 0.0;
     double rsum = 0.0, bsum = 0.0;
-    for (int e = 0; e < S; ++e) {
-        const double rr = ld_cg(top + e), bb = ld_cg(top + S + e);
-        rsum += rr;
-        bsum += bb;
-        st->rho[e] = rr;
-        st->bnorm[e] = sqrt(bb);
-        st->alpha[e] = 0.0; st->beta[e] = 0.0; st->relres[e] = 0.0;
-        st->iters[e] = 0; st->updx[e] = 0; st->zerox[e] = 0; st->status[e] = ENS_OK;
-        if (!a.coupled) {
-            if (bb == 0.0) { st->active[e] = 0; st->zerox[e] = 1; }
-            else st->active[e] = (sqrt(rr) <= a.tol * st->bnorm[e]) ? 0 : 1;
-        }
+    for (int k = 0; k < S; ++k) {
+        rsum += __shfl_sync(FULL, rr, k);
+        bsum += __shfl_sync(FULL, bb, k);
     }
-    st->bnorm_all = sqrt(bsum);
-    if (a.coupled) {
+    const double bn = sqrt(bb);
+    int act = 0, zx = 0;
+    if (!a.coupled) {
+        if (bb == 0.0) zx = 1;
+        else act = (sqrt(rr) <= a.tol * bn) ? 0 : 1;
+    } else {
         const bool all_zero = (bsum == 0.0);
-        const bool done = all_zero || sqrt(rsum) <= a.tol * st->bnorm_all;
-        for (int e = 0; e < S; ++e) { st->active[e] = done ? 0 : 1; st->zerox[e] = all_zero ? 1 : 0; }
+        act = (all_zero || sqrt(rsum) <= a.tol * sqrt(bsum)) ? 0 : 1;
+        zx = all_zero ? 1 : 0;
     }
-    if (a.max_iter == 0)
-        for (int e = 0; e < S; ++e)
-            if (st->active[e]) { st->active[e] = 0; st->status[e] = ENS_ERR_NOT_CONVERGED; }
-    int ac = 0, zx = 0;
-    for (int e = 0; e < S; ++e) { ac += st->active[e]; zx += st->zerox[e]; }
-    st->active_count = ac;
-    st->zero_any = zx;
-    st->updx_any = 0;
-    st->spmv_real = 0;
+    int status = ENS_OK;
+    if (a.max_iter == 0 && act) { act = 0; status = ENS_ERR_NOT_CONVERGED; }
+    if (e < S) {
+        st->rho[e] = rr;
+        st->bnorm[e] = bn;
+        st->alpha[e] = 0.0; st->beta[e] = 0.0; st->relres[e] = 0.0;
+        st->iters[e] = 0; st->updx[e] = 0; st->zerox[e] = zx; st->status[e] = status;
+        st->active[e] = act;
+    } else {
+        act = 0; zx = 0;
+    }
+    const int ac = __popc(__ballot_sync(FULL, act)), zany = __popc(__ballot_sync(FULL, zx));
+    if (e == 0) {
+        st->bnorm_all = sqrt(bsum);
+        st->active_count = ac;
+        st->zero_any = zany;
+        st->updx_any = 0;
+        st->spmv_real = 0;
+    }
     __threadfence();
 }
 
@@ -157,7 +166,7 @@ __global__ void cg_zero_kernel(CgArgs a) {
 }
 
 // ------------------------------------------------------------------ K1
-template <int S, bool DF>
+template <int S, int MODE>
 __global__ void __launch_bounds__(RowMap<S>::THREADS, 1536 / RowMap<S>::THREADS) cg_spmv_kernel(CgArgs a) {
     CgState *st = a.st;
     if (ld_cg(&st->active_count) == 0) {
@@ -171,12 +180,17 @@ __global__ void __launch_bounds__(RowMap<S>::THREADS, 1536 / RowMap<S>::THREADS)
     __shared__ double sm[32][S + 1];
     const int r = threadIdx.x / G, g = threadIdx.x % G;
     const int64_t R = (int64_t)blockIdx.x * 32 + r;
-    const bool use_df = DF && (ld_cg(&st->df_bad_any) == 0);
+    // the split form is used unless a vector element fell outside its range
+    const int mode = (MODE != 0 && ld_cg(&st->df_bad_any) != 0) ? 0 : MODE;
     __shared__ ChunkCols cc;
     const bool staged = stage_chunk(cc, a.row_map, a.col, blockIdx.x, a.n);
-    const double2 apv =
-        use_df ? chunk_spmv_df<S, XPre>(cc, staged, a.col, a.vals, a.pdf, r, g, R < a.n)
-               : chunk_spmv<S, double>(cc, staged, a.col, a.vals, a.p, r, g, R < a.n);
+    double2 apv;
+    if (MODE == 1 && mode == 1)
+        apv = chunk_spmv_df<S, XPre>(cc, staged, a.col, a.vals, a.pdf, r, g, R < a.n);
+    else if (MODE == 2 && mode == 2)
+        apv = chunk_spmv_split<S, XPre>(cc, staged, a.col, a.vals, a.p, a.pdf, r, g, R < a.n);
+    else
+        apv = chunk_spmv<S, double>(cc, staged, a.col, a.vals, a.p, r, g, R < a.n);
     double v0 = 0.0, v1 = 0.0;
     if constexpr (S == 1) {
         const double ap = apv.x;
@@ -193,31 +207,39 @@ __global__ void __launch_bounds__(RowMap<S>::THREADS, 1536 / RowMap<S>::THREADS)
     }
     chunk_tree<S>(sm, v0, v1, r, g, a.t1, blockIdx.x, 0);
     if (!dot_tree_propagate(a.t1, blockIdx.x, 1)) return;
-    if (threadIdx.x != 0) return;
+    if (threadIdx.x >= 32) return;
+    // epilogue: one lane per member
+    const unsigned FULL = 0xffffffffu;
+    const int e = threadIdx.x;
     const double *top = a.t1.buf[a.t1.levels];
-    st->spmv_real += 1;
-    for (int e = 0; e < S; ++e) st->updx[e] = 0;  // consumed by the previous K3
-    st->updx_any = 0;
+    const double pi = (e < S) ? ld_cg(top + e) : 0.0;
+    const double rho = (e < S) ? st->rho[e] : 0.0;
+    int act = (e < S) ? st->active[e] : 0;
     if (a.coupled) {
         double pis = 0.0, rhos = 0.0;
-        for (int e = 0; e < S; ++e) { pis += ld_cg(top + e); rhos += st->rho[e]; }
+        for (int k = 0; k < S; ++k) {
+            pis += __shfl_sync(FULL, pi, k);
+            rhos += __shfl_sync(FULL, rho, k);
+        }
         const bool bad = !(pis > 0.0) || !isfinite(pis);
-        for (int e = 0; e < S; ++e) {
-            if (!st->active[e]) continue;
-            if (bad) { st->active[e] = 0; st->status[e] = ENS_ERR_BREAKDOWN; }
+        if (act) {
+            if (bad) { act = 0; st->status[e] = ENS_ERR_BREAKDOWN; }
             else st->alpha[e] = rhos / pis;
         }
-    } else {
-        for (int e = 0; e < S; ++e) {
-            if (!st->active[e]) continue;
-            const double pi = ld_cg(top + e);
-            if (!(pi > 0.0) || !isfinite(pi)) { st->active[e] = 0; st->status[e] = ENS_ERR_BREAKDOWN; }
-            else st->alpha[e] = st->rho[e] / pi;
-        }
+    } else if (act) {
+        if (!(pi > 0.0) || !isfinite(pi)) { act = 0; st->status[e] = ENS_ERR_BREAKDOWN; }
+        else st->alpha[e] = rho / pi;
     }
-    int ac = 0;
-    for (int e = 0; e < S; ++e) ac += st->active[e];
-    st->active_count = ac;
+    if (e < S) {
+        st->active[e] = act;
+        st->updx[e] = 0;  // consumed by the previous K3
+    }
+    const int ac = __popc(__ballot_sync(FULL, act));
+    if (e == 0) {
+        st->spmv_real += 1;
+        st->updx_any = 0;
+        st->active_count = ac;
+    }
     __threadfence();
 }
 
@@ -277,44 +299,49 @@ __global__ void __launch_bounds__(VecMap<S>::THREADS) cg_resid_kernel(CgArgs a) 
     }
     const int nitems = (int)min((int64_t)VM::CPC, a.t1.count[1] - first_chunk);
     if (!dot_tree_propagate(a.t1, first_chunk, nitems)) return;
-    if (threadIdx.x != 0) return;
+    if (threadIdx.x >= 32) return;
+    // epilogue: one lane per member
+    const unsigned FULL = 0xffffffffu;
+    const int e = threadIdx.x;
     const double *top = a.t1.buf[a.t1.levels];
     CgState *st = a.st;
+    const double rn = (e < S) ? ld_cg(top + e) : 0.0;
+    const double rho = (e < S) ? st->rho[e] : 0.0;
+    int act = (e < S) ? st->active[e] : 0, ux = 0;
+    int it = (e < S) ? st->iters[e] : 0;
+    bool conv_all = false;
+    double rns = 0.0, ros = 0.0;
     if (a.coupled) {
-        double rn = 0.0, ro = 0.0;
-        for (int e = 0; e < S; ++e) { rn += ld_cg(top + e); ro += st->rho[e]; }
-        const bool conv = sqrt(rn) <= a.tol * st->bnorm_all;
-        for (int e = 0; e < S; ++e) {
-            if (st->active[e]) {
-                st->iters[e] += 1;
-                st->updx[e] = 1;
-                if (conv) { st->active[e] = 0; st->status[e] = ENS_OK; }
-                else if (st->iters[e] >= a.max_iter) { st->active[e] = 0; st->status[e] = ENS_ERR_NOT_CONVERGED; }
-                else st->beta[e] = rn / ro;
-            }
-            st->rho[e] = ld_cg(top + e);
+        for (int k = 0; k < S; ++k) {
+            rns += __shfl_sync(FULL, rn, k);
+            ros += __shfl_sync(FULL, rho, k);
         }
-    } else {
-        for (int e = 0; e < S; ++e) {
-            if (!st->active[e]) continue;
-            const double rn = ld_cg(top + e);
-            st->iters[e] += 1;
-            st->updx[e] = 1;
-            if (sqrt(rn) <= a.tol * st->bnorm[e]) { st->active[e] = 0; st->status[e] = ENS_OK; }
-            else if (st->iters[e] >= a.max_iter) { st->active[e] = 0; st->status[e] = ENS_ERR_NOT_CONVERGED; }
-            else st->beta[e] = rn / st->rho[e];
-            st->rho[e] = rn;
-        }
+        conv_all = sqrt(rns) <= a.tol * st->bnorm_all;
     }
-    int ac = 0, ux = 0;
-    for (int e = 0; e < S; ++e) { ac += st->active[e]; ux += st->updx[e]; }
-    st->active_count = ac;
-    st->updx_any = ux;
+    if (act) {
+        it += 1;
+        ux = 1;
+        const bool conv = a.coupled ? conv_all : (sqrt(rn) <= a.tol * st->bnorm[e]);
+        if (conv) { act = 0; st->status[e] = ENS_OK; }
+        else if (it >= a.max_iter) { act = 0; st->status[e] = ENS_ERR_NOT_CONVERGED; }
+        else st->beta[e] = a.coupled ? rns / ros : rn / rho;
+    }
+    if (e < S) {
+        if (a.coupled || ux) st->rho[e] = rn;
+        st->iters[e] = it;
+        st->updx[e] = ux;
+        st->active[e] = act;
+    }
+    const int ac = __popc(__ballot_sync(FULL, act)), uany = __popc(__ballot_sync(FULL, ux));
+    if (e == 0) {
+        st->active_count = ac;
+        st->updx_any = uany;
+    }
     __threadfence();
 }
 
 // ------------------------------------------------------------------ K3
-template <int S, bool DF>
+template <int S, int MODE>
 __global__ void __launch_bounds__(VecMap<S>::THREADS) cg_update_kernel(CgArgs a) {
     using VM = VecMap<S>;
     CgState *st = a.st;
@@ -339,7 +366,7 @@ __global__ void __launch_bounds__(VecMap<S>::THREADS) cg_update_kernel(CgArgs a)
             if (ac0) {
                 const double pn = fma(be0, pv, a.r[R]);
                 a.p[R] = pn;
-                if (DF) store_split1(a.pdf, R, pn, &st->df_bad_any);
+                if (MODE != 0) store_split1(a.pdf, R, pn, &st->df_bad_any);
             }
         } else {
             const double2 pv = reinterpret_cast<const double2 *>(a.p)[R * VG + g];
@@ -355,7 +382,7 @@ __global__ void __launch_bounds__(VecMap<S>::THREADS) cg_update_kernel(CgArgs a)
                 if (ac0) pn.x = fma(be0, pv.x, rv.x);
                 if (ac1) pn.y = fma(be1, pv.y, rv.y);
                 reinterpret_cast<double2 *>(a.p)[R * VG + g] = pn;
-                if (DF) store_split(a.pdf, R * S + m, pn.x, pn.y, &st->df_bad_any);
+                if (MODE != 0) store_split(a.pdf, R * S + m, pn.x, pn.y, &st->df_bad_any);
             }
         }
     }
@@ -384,12 +411,11 @@ __global__ void __launch_bounds__(RowMap<S>::THREADS, 1024 / RowMap<S>::THREADS)
     }
     chunk_tree<S>(sm, v0, v1, r, g, a.t1, blockIdx.x, 0);
     if (!dot_tree_propagate(a.t1, blockIdx.x, 1)) return;
-    if (threadIdx.x != 0) return;
+    const int e = threadIdx.x;
+    if (e >= S) return;
     const double *top = a.t1.buf[a.t1.levels];
-    for (int e = 0; e < S; ++e) {
-        const double bn = a.st->bnorm[e];
-        a.st->relres[e] = (bn > 0.0) ? sqrt(ld_cg(top + e)) / bn : 0.0;
-    }
+    const double bn = a.st->bnorm[e];
+    a.st->relres[e] = (bn > 0.0) ? sqrt(ld_cg(top + e)) / bn : 0.0;
     __threadfence();
 }
 
@@ -401,23 +427,23 @@ static size_t cg_bytes(int64_t n, int s) {
            dot_tree_bytes(n, s) + dot_tree_bytes(n, 2 * s);
 }
 
-template <int S, bool DF>
+template <int S, int MODE>
 struct CgKernels {
     static unsigned vec_grid(const CgArgs &a) {
         return (unsigned)((a.t1.count[1] + VecMap<S>::CPC - 1) / VecMap<S>::CPC);
     }
     static void init(const CgArgs &a, unsigned grid, cudaStream_t st) {
-        cg_init_kernel<S, DF><<<grid, RowMap<S>::THREADS, 0, st>>>(a);
+        cg_init_kernel<S, MODE><<<grid, RowMap<S>::THREADS, 0, st>>>(a);
         cg_zero_kernel<S><<<152 * 2, 256, 0, st>>>(a);
     }
     static void spmv(const CgArgs &a, unsigned grid, cudaStream_t st) {
-        cg_spmv_kernel<S, DF><<<grid, RowMap<S>::THREADS, 0, st>>>(a);
+        cg_spmv_kernel<S, MODE><<<grid, RowMap<S>::THREADS, 0, st>>>(a);
     }
     static void resid(const CgArgs &a, unsigned, cudaStream_t st) {
         cg_resid_kernel<S><<<vec_grid(a), VecMap<S>::THREADS, 0, st>>>(a);
     }
     static void update(const CgArgs &a, unsigned, cudaStream_t st) {
-        cg_update_kernel<S, DF><<<vec_grid(a), VecMap<S>::THREADS, 0, st>>>(a);
+        cg_update_kernel<S, MODE><<<vec_grid(a), VecMap<S>::THREADS, 0, st>>>(a);
     }
     static void final_(const CgArgs &a, unsigned grid, cudaStream_t st) {
         cg_final_kernel<S><<<grid, RowMap<S>::THREADS, 0, st>>>(a);
@@ -431,11 +457,11 @@ struct CgHostOut {
     ens_cg_stats *stats;
 };
 
-template <int S, bool DF>
+template <int S, int MODE>
 static int cg_run(const ens_graph *g, const double *vals, const double *b, double *x, double tol,
                   int max_iter, int flags, int check_every, void *work, CgHostOut out,
                   cudaStream_t st) {
-    using K = CgKernels<S, DF>;
+    using K = CgKernels<S, MODE>;
     const int64_t n = g->num_rows;
     char *w = static_cast<char *>(work);
     CgArgs a;
@@ -576,9 +602,11 @@ template <int S>
 static int cg_dispatch_df(const ens_graph *g, const double *vals, const double *b, double *x,
                           double tol, int max_iter, int flags, int check_every, void *work,
                           CgHostOut out, cudaStream_t st) {
+    if (flags & ENS_CG_SPLIT64)
+        return cg_run<S, 2>(g, vals, b, x, tol, max_iter, flags, check_every, work, out, st);
     if (flags & ENS_CG_DF64)
-        return cg_run<S, true>(g, vals, b, x, tol, max_iter, flags, check_every, work, out, st);
-    return cg_run<S, false>(g, vals, b, x, tol, max_iter, flags, check_every, work, out, st);
+        return cg_run<S, 1>(g, vals, b, x, tol, max_iter, flags, check_every, work, out, st);
+    return cg_run<S, 0>(g, vals, b, x, tol, max_iter, flags, check_every, work, out, st);
 }
 
 }  // namespace ens

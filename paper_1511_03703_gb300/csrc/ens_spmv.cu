@@ -40,6 +40,48 @@ __global__ void __launch_bounds__(RowMap<S>::THREADS, 512 / RowMap<S>::THREADS) 
     }
 }
 
+// split FP64 / double-float arithmetic (x split on the fly for odd positions)
+template <int S>
+__global__ void __launch_bounds__(RowMap<S>::THREADS, 1024 / RowMap<S>::THREADS) spmv_split_kernel(
+    int32_t n, const int32_t *__restrict__ row_map, const int32_t *__restrict__ col,
+    const double *__restrict__ vals, const double *__restrict__ x, double *__restrict__ y) {
+    constexpr int G = RowMap<S>::G;
+    __shared__ ChunkCols cc;
+    const int r = threadIdx.x / G, g = threadIdx.x % G;
+    const int64_t R = (int64_t)blockIdx.x * 32 + r;
+    const bool staged = stage_chunk(cc, row_map, col, blockIdx.x, n);
+    const double2 v = chunk_spmv_split<S, XSplit>(cc, staged, col, vals, x, x, r, g, R < n);
+    if (R >= n) return;
+    if constexpr (S == 1) {
+        if (g == 0) y[R] = v.x;
+    } else {
+        reinterpret_cast<double2 *>(y)[R * G + g] = v;
+    }
+}
+
+template <int S>
+static int spmv_split_s(const ens_graph *g, const double *vals, const double *x, double *y,
+                        cudaStream_t st) {
+    const int64_t chunks = ((int64_t)g->num_rows + 31) / 32;
+    if (chunks == 0) return ENS_OK;
+    spmv_split_kernel<S><<<(unsigned)chunks, RowMap<S>::THREADS, 0, st>>>(g->num_rows, g->row_map,
+                                                                         g->col_entry, vals, x, y);
+    ENS_LAUNCH_CHECK("spmv_split_kernel");
+    return ENS_OK;
+}
+
+static int spmv_split_dispatch(const ens_graph *g, int s, const void *vals, const double *x,
+                               double *y, cudaStream_t st) {
+    const double *v = static_cast<const double *>(vals);
+    switch (s) {
+        case 1: return spmv_split_s<1>(g, v, x, y, st);
+        case 4: return spmv_split_s<4>(g, v, x, y, st);
+        case 8: return spmv_split_s<8>(g, v, x, y, st);
+        case 16: return spmv_split_s<16>(g, v, x, y, st);
+        default: return spmv_split_s<32>(g, v, x, y, st);
+    }
+}
+
 template <int S>
 static int spmv_df_s(const ens_graph *g, const double *vals, const double *x, double *y,
                      cudaStream_t st) {
@@ -162,6 +204,7 @@ extern "C" int ens_spmv(const ens_graph *graph, int s, int dtype, const void *va
         case ENS_F32: return spmv_dispatch<float>(graph, s, values, x, y, st);
         case ENS_BF16: return spmv_dispatch<__nv_bfloat16>(graph, s, values, x, y, st);
         case ENS_F64_DF: return spmv_df_dispatch(graph, s, values, x, y, st);
+        case ENS_F64_SPLIT: return spmv_split_dispatch(graph, s, values, x, y, st);
         default: return fail(ENS_ERR_UNSUPPORTED, "dtype %d", dtype);
     }
 }

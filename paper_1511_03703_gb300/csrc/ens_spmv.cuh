@@ -343,6 +343,98 @@ __device__ __forceinline__ double row_spmv1_df(CA colf, int rs, int re,
     return (g == 0) ? df_finish(a, o, fb + ofb) : df_finish(o, a, ofb + fb);
 }
 
+// ------------------------------------------------- split FP64 / double-float
+// Both pipes at once: entries at even positions of a row (partial 0) use the
+// FP64 FMA with x in FP64, entries at odd positions (partial 1) use the
+// double-float product with x pre-split; row value = p0 + double(p1).
+// GB300 retires 2 DFMA and ~3 double-float terms per cycle per SM, so half of
+// the terms on each pipe keeps the SpMV under the HBM time.
+template <int S, typename XS, typename CA>
+__device__ __forceinline__ double2 row_spmv2_split(CA colf, int rs, int re,
+                                                   const double *__restrict__ vals,
+                                                   const double *__restrict__ x,
+                                                   typename XS::ptr __restrict__ xdf, int g) {
+    double a0 = 0.0, b0 = 0.0;          // FP64 partial, members m, m+1
+    DfAcc a1 = df_zero(), b1 = df_zero();  // double-float partial
+    bool ok = true;
+    const int m = 2 * g;
+    int j = rs;
+    for (; j + 4 <= re; j += 4) {
+        const int c0 = colf(j), c1 = colf(j + 1), c2 = colf(j + 2), c3 = colf(j + 3);
+        const double2 v0 = ValLoad<double>::two(vals, (int64_t)j * S + m);
+        const double2 v1 = ValLoad<double>::two(vals, (int64_t)(j + 1) * S + m);
+        const double2 v2 = ValLoad<double>::two(vals, (int64_t)(j + 2) * S + m);
+        const double2 v3 = ValLoad<double>::two(vals, (int64_t)(j + 3) * S + m);
+        const double2 x0 = ld_x2(x, (int64_t)c0 * S + m);
+        const float4 d1 = XS::two(xdf, (int64_t)c1 * S + m);
+        const double2 x2 = ld_x2(x, (int64_t)c2 * S + m);
+        const float4 d3 = XS::two(xdf, (int64_t)c3 * S + m);
+        a0 = fma(v0.x, x0.x, a0); b0 = fma(v0.y, x0.y, b0);
+        ok &= df_term(a1, v1.x, d1.x, d1.y); ok &= df_term(b1, v1.y, d1.z, d1.w);
+        a0 = fma(v2.x, x2.x, a0); b0 = fma(v2.y, x2.y, b0);
+        ok &= df_term(a1, v3.x, d3.x, d3.y); ok &= df_term(b1, v3.y, d3.z, d3.w);
+    }
+    for (; j < re; ++j) {
+        const double2 v = ValLoad<double>::two(vals, (int64_t)j * S + m);
+        const int c = colf(j);
+        if ((j - rs) & 1) {
+            const float4 d = XS::two(xdf, (int64_t)c * S + m);
+            ok &= df_term(a1, v.x, d.x, d.y); ok &= df_term(b1, v.y, d.z, d.w);
+        } else {
+            const double2 xv = ld_x2(x, (int64_t)c * S + m);
+            a0 = fma(v.x, xv.x, a0); b0 = fma(v.y, xv.y, b0);
+        }
+    }
+    double f0 = 0.0, f1 = 0.0;  // odd-position terms outside the split range, FP64, in order
+    if (!ok)
+        for (int jj = rs + 1; jj < re; jj += 2) {
+            const double2 v = ValLoad<double>::two(vals, (int64_t)jj * S + m);
+            float h, l;
+            const bool ok0 = df_split_trunc(v.x, h, l), ok1 = df_split_trunc(v.y, h, l);
+            if (ok0 && ok1) continue;
+            const double2 xv = ld_x2(x, (int64_t)colf(jj) * S + m);
+            if (!ok0) f0 = fma(v.x, xv.x, f0);
+            if (!ok1) f1 = fma(v.y, xv.y, f1);
+        }
+    const double p1a = f2d_exact(a1.s) + f2d_exact(a1.c), p1b = f2d_exact(b1.s) + f2d_exact(b1.c);
+    return make_double2(a0 + ((f0 != 0.0) ? p1a + f0 : p1a), b0 + ((f1 != 0.0) ? p1b + f1 : p1b));
+}
+
+// s = 1: lane g = 0 sums the even positions in FP64, lane 1 the odd ones in
+// double-float; the row value is returned on both lanes
+template <typename XS, typename CA>
+__device__ __forceinline__ double row_spmv1_split(CA colf, int rs, int re,
+                                                  const double *__restrict__ vals,
+                                                  const double *__restrict__ x,
+                                                  typename XS::ptr __restrict__ xdf, int g,
+                                                  bool valid) {
+    double p = 0.0;
+    if (valid) {
+        if (g == 0) {
+            for (int j = rs; j < re; j += 2) p = fma(ValLoad<double>::one(vals, j), __ldg(x + colf(j)), p);
+        } else {
+            DfAcc a = df_zero();
+            bool ok = true;
+            for (int j = rs + 1; j < re; j += 2) {
+                const float2 d = XS::one(xdf, colf(j));
+                ok &= df_term(a, ValLoad<double>::one(vals, j), d.x, d.y);
+            }
+            double f = 0.0;
+            if (!ok)
+                for (int j = rs + 1; j < re; j += 2) {
+                    const double v = ValLoad<double>::one(vals, j);
+                    float h, l;
+                    if (df_split_trunc(v, h, l)) continue;
+                    f = fma(v, __ldg(x + colf(j)), f);
+                }
+            const double p1 = f2d_exact(a.s) + f2d_exact(a.c);
+            p = (f != 0.0) ? p1 + f : p1;
+        }
+    }
+    const double o = __shfl_xor_sync(0xffffffffu, p, 1);
+    return (g == 0) ? p + o : o + p;
+}
+
 // ------------------------------------------- chunk-level row evaluation
 // Value(s) of the calling thread's row r (members 2g, 2g+1; s = 1: the row,
 // in .x) inside a staged 32-row chunk.  valid = the row exists.
@@ -379,6 +471,25 @@ __device__ __forceinline__ double2 chunk_spmv_df(const ChunkCols &cc, bool stage
         if (!valid) return make_double2(0.0, 0.0);
         return staged ? row_spmv2_df<S, XS>(ColShared{cc.col, cc.rm[0]}, rs, re, vals, x, g)
                       : row_spmv2_df<S, XS>(ColGlobal{col}, rs, re, vals, x, g);
+    }
+}
+
+template <int S, typename XS>
+__device__ __forceinline__ double2 chunk_spmv_split(const ChunkCols &cc, bool staged,
+                                                    const int32_t *__restrict__ col,
+                                                    const double *__restrict__ vals,
+                                                    const double *__restrict__ x,
+                                                    typename XS::ptr __restrict__ xdf, int r,
+                                                    int g, bool valid) {
+    const int rs = valid ? cc.rm[r] : 0, re = valid ? cc.rm[r + 1] : 0;
+    if constexpr (S == 1) {
+        const double v = staged ? row_spmv1_split<XS>(ColShared{cc.col, cc.rm[0]}, rs, re, vals, x, xdf, g, valid)
+                                : row_spmv1_split<XS>(ColGlobal{col}, rs, re, vals, x, xdf, g, valid);
+        return make_double2(v, 0.0);
+    } else {
+        if (!valid) return make_double2(0.0, 0.0);
+        return staged ? row_spmv2_split<S, XS>(ColShared{cc.col, cc.rm[0]}, rs, re, vals, x, xdf, g)
+                      : row_spmv2_split<S, XS>(ColGlobal{col}, rs, re, vals, x, xdf, g);
     }
 }
 

@@ -100,7 +100,7 @@ def test_assembly_matches_oracle(torch, N, M, s):
 # ------------------------------------------------------------------ A4 SpMV
 @pytest.mark.parametrize("N", [3, 8, 13])
 @pytest.mark.parametrize("s", S_ALL)
-@pytest.mark.parametrize("dtype", ["float64", "float64_df", "float32", "bfloat16"])
+@pytest.mark.parametrize("dtype", ["float64", "float64_df", "float64_split", "float32", "bfloat16"])
 def test_spmv_matches_oracle(torch, N, s, dtype):
     M = 10
     xs = inputs.kl_samples(200 + N, 0, min(s, 4), M)
@@ -108,12 +108,12 @@ def test_spmv_matches_oracle(torch, N, s, dtype):
     ov = [ov[e % len(ov)] for e in range(s)]
     n = len(rm) - 1
     xm = [inputs.random_vector(300 + e, n) for e in range(s)]
-    df = dtype == "float64_df"
-    vt = torch.from_numpy(O.to_ensemble(ov)).to(getattr(torch, "float64" if df else dtype))
+    df, split = dtype == "float64_df", dtype == "float64_split"
+    vt = torch.from_numpy(O.to_ensemble(ov)).to(getattr(torch, "float64" if df or split else dtype))
     vq = [vt.reshape(-1, s)[:, e].double().numpy() for e in range(s)]   # values as stored
     y = torch.empty(n * s, dtype=torch.float64, device=gpu())
     graph = E.Graph(to_dev(rm), to_dev(col))
-    E.spmv(graph, s, vt.to(gpu()), to_dev(O.to_ensemble(xm)), y, df=df)
+    E.spmv(graph, s, vt.to(gpu()), to_dev(O.to_ensemble(xm)), y, df=df, split=split)
     Y = ens_cols(to_np(y), s)
     for e in range(s):
         ref = O.spmv(rm, col, vq[e], xm[e])
@@ -121,7 +121,8 @@ def test_spmv_matches_oracle(torch, N, s, dtype):
 
 
 @pytest.mark.parametrize("s", [1, 8, 32])
-def test_spmv_df_extreme_values_take_exact_path(torch, s):
+@pytest.mark.parametrize("form", ["df", "split"])
+def test_spmv_df_extreme_values_take_exact_path(torch, s, form):
     """Values outside the double-float split range ([2^-103, 2^128)), exact
     zeros and mixed magnitudes within a row stay inside the 1e-12 bound."""
     N, M = 5, 10
@@ -136,7 +137,8 @@ def test_spmv_df_extreme_values_take_exact_path(torch, s):
     xm = [inputs.random_vector(330 + e, n, -1e3, 1e3) for e in range(s)]
     y = torch.empty(n * s, dtype=torch.float64, device=gpu())
     graph = E.Graph(to_dev(rm), to_dev(col))
-    E.spmv(graph, s, to_dev(O.to_ensemble(vals)), to_dev(O.to_ensemble(xm)), y, df=True)
+    E.spmv(graph, s, to_dev(O.to_ensemble(vals)), to_dev(O.to_ensemble(xm)), y,
+           df=form == "df", split=form == "split")
     Y = ens_cols(to_np(y), s)
     for e in range(s):
         ref = O.spmv(rm, col, vals[e], xm[e])
@@ -156,9 +158,12 @@ def test_spmv_s_invariant_bitwise(torch):
         Y = ens_cols(to_np(y), s)
         E.spmv(mesh.graph, s, vals, to_dev(O.to_ensemble(xm[:s])), y, df=True)
         Ydf = ens_cols(to_np(y), s)
+        E.spmv(mesh.graph, s, vals, to_dev(O.to_ensemble(xm[:s])), y, split=True)
+        Ysp = ens_cols(to_np(y), s)
         if ref is None:
-            ref = (Y[:, 0].copy(), Ydf[:, 0].copy())
+            ref = (Y[:, 0].copy(), Ydf[:, 0].copy(), Ysp[:, 0].copy())
         assert np.array_equal(Y[:, 0], ref[0]) and np.array_equal(Ydf[:, 0], ref[1]), s
+        assert np.array_equal(Ysp[:, 0], ref[2]), s
 
 
 # ------------------------------------------------------------------- A5 dot
@@ -238,7 +243,7 @@ def test_cg_small_workload_exact_iterations(torch):
 
 
 @pytest.mark.parametrize("s", S_ALL)
-@pytest.mark.parametrize("flags", [0, E.CG_DF64])
+@pytest.mark.parametrize("flags", [0, E.CG_DF64, E.CG_SPLIT64])
 def test_cg_matches_oracle_ragged_mesh(torch, s, flags):
     mesh = E.Mesh(13, 10)   # 2744 rows: 85 full 32-row chunks and a ragged one
     xs = inputs.kl_samples(900, 0, s, 10)
@@ -257,7 +262,7 @@ def test_cg_identical_members_bitwise(torch):
     assert len(set(it)) == 1 and all(np.array_equal(xg[:, 0], xg[:, e]) for e in range(8))
 
 
-@pytest.mark.parametrize("flags", [0, E.CG_DF64])
+@pytest.mark.parametrize("flags", [0, E.CG_DF64, E.CG_SPLIT64])
 def test_cg_sample_result_independent_of_s_bitwise(torch, flags):
     mesh = E.Mesh(9, 10)
     xs = inputs.kl_samples(4242, 0, 32, 10)
@@ -361,7 +366,7 @@ def test_scale_64cubed_s32_sampled(torch):
         ref = O.spmv(rm, col, ov[e % 2], xm[e])
         assert np.all(np.abs(Y[:, e] - ref) <= spmv_bound(rm, col, ov[e % 2], xm[e])), e
     # CG of the whole ensemble; two members against oracle solves
-    for flags in (0, E.CG_DF64):
+    for flags in (0, E.CG_DF64, E.CG_SPLIT64):
         xg, it, rr, st, _ = gpu_solve(mesh, xs, 1e-8, flags=flags)
         assert st == [0] * s and max(rr) < 2e-8
         compare_cg_picked(mesh, xs, picks, rm, col, ov, ob, xg, it)
