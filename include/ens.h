@@ -211,6 +211,39 @@ int ens_cg(const ens_graph *graph, int s, const double *values, const double *b,
            int32_t *iters_host, double *relres_host, int32_t *status_host,
            ens_cg_stats *stats_host, void *stream);
 
+/* ------------------------------------------------- A7 mixed precision */
+/* Low-precision copy of ensemble values for the inner solver of ens_cg_mixed.
+ *   dtype = ENS_F32 or ENS_BF16; values_lo: float[nnz*s] or bfloat16[nnz*s]
+ *   (commuted layout), each value rounded to nearest (BF16 via FP32).
+ *   diag_lo (float[num_rows*s], may be NULL): when given, the diagonal entry of
+ *   values_lo is stored as 0 and diag_lo[I*s+e] is set so that every row of
+ *   the low-precision matrix sums to the FP64 row sum:
+ *       diag_lo = fl32( sum_j values[j] - sum_{j != diag} values_lo[j] ).
+ *   This keeps the zero row sums of the diffusion stencil, which BF16 rounding
+ *   would otherwise break at the size of the smallest eigenvalue. */
+int ens_convert_values(const ens_graph *graph, int s, const double *values, int dtype,
+                       void *values_lo, float *diag_lo, void *stream);
+
+/* Mixed-precision ensemble CG (iterative refinement; not in the paper, see
+ * the A7 row of the design notes): per member,
+ *     r = b - A x (FP64 values and arithmetic; the true residual),
+ *     stop when ||r|| <= tol*||b|| (status ENS_OK) or after max_outer steps,
+ *     solve A_lo d = r/||r|| by FP32 CG (FP32 vectors and accumulation, values
+ *     values_lo of dtype_lo with optional diag_lo) to ||r_in|| <= inner_tol
+ *     or max_inner iterations,
+ *     x += ||r|| d (FP64).
+ * Members with b = 0 return x = 0.  outer_iters_host[s] = refinement steps,
+ * inner_iters_host[s] = total inner iterations, relres_host[s] = the final
+ * true ||b - A x||/||b||.  work: ens_cg_mixed_workspace_size bytes.
+ * Synchronises `stream`.  Returns ENS_OK when every member converged. */
+int ens_cg_mixed_workspace_size(int32_t num_rows, int s, size_t *bytes);
+int ens_cg_mixed(const ens_graph *graph, int s, const double *values, const void *values_lo,
+                 int dtype_lo, const float *diag_lo, const double *b, double *x, double tol,
+                 int max_outer, double inner_tol, int max_inner, int check_every, void *work,
+                 size_t work_bytes, int32_t *outer_iters_host, int32_t *inner_iters_host,
+                 double *relres_host, int32_t *status_host, ens_cg_stats *stats_host,
+                 void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -13,7 +13,7 @@ import threading
 
 __all__ = ["EnsError", "lib", "Graph", "Mesh", "mesh_sizes", "graph_build", "kl_table_size",
            "kl_setup", "mode_matrices", "assemble", "spmv", "dot", "dot_workspace_size", "dot_static", "cg",
-           "cg_workspace_size", "CgStats", "F64", "F32", "BF16", "CG_COUPLED", "CG_GRAPH",
+           "cg_workspace_size", "CgStats", "convert_values", "cg_mixed", "cg_mixed_workspace_size", "F64", "F32", "BF16", "CG_COUPLED", "CG_GRAPH",
            "CG_TIME_SPMV", "CG_DF64", "CG_SPLIT64", "F64_DF", "F64_SPLIT"]
 
 F64, F32, BF16, F64_DF, F64_SPLIT = 0, 1, 2, 3, 4
@@ -86,6 +86,10 @@ def _declare(L):
         "ens_dot_static": (I, [i64, I, vp, vp, vp, vp]),
         "ens_cg_workspace_size": (I, [i32, I, P(sz)]),
         "ens_cg": (I, [P(EnsGraphC), I, vp, vp, vp, d, I, I, I, vp, sz, vp, vp, vp, P(CgStats), vp]),
+        "ens_convert_values": (I, [P(EnsGraphC), I, vp, I, vp, vp, vp]),
+        "ens_cg_mixed_workspace_size": (I, [i32, I, P(sz)]),
+        "ens_cg_mixed": (I, [P(EnsGraphC), I, vp, vp, I, vp, vp, vp, d, I, d, I, I, vp, sz, vp, vp,
+                             vp, vp, P(CgStats), vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -238,6 +242,42 @@ def cg(graph, s, values, b, x, tol, max_iter, work, flags=0, check_every=8, stre
     if rc not in (0, ERR_NOT_CONVERGED, ERR_BREAKDOWN) or (rc and raise_on_failure):
         _check(rc)
     return list(it), list(rr), list(stt), stats
+
+
+# --------------------------------------------------------- mixed precision
+def convert_values(graph, s, values, values_lo, diag_lo=None, stream=None):
+    """FP64 values -> values_lo (float32 or bfloat16 tensor); diag_lo (float32) optional."""
+    _require_cuda(values, values_lo, diag_lo)
+    dt = _DT[str(values_lo.dtype).replace("torch.", "")]
+    _check(lib().ens_convert_values(graph.ref(), s, _ptr(values), dt, _ptr(values_lo), _ptr(diag_lo),
+                                    _stream(stream)))
+
+
+def cg_mixed_workspace_size(n, s):
+    v = ctypes.c_size_t()
+    _check(lib().ens_cg_mixed_workspace_size(n, s, ctypes.byref(v)))
+    return v.value
+
+
+def cg_mixed(graph, s, values, values_lo, b, x, tol, work, diag_lo=None, max_outer=20,
+             inner_tol=1e-4, max_inner=2000, check_every=8, stream=None):
+    """FP64 iterative refinement around an FP32 inner CG; synchronises.
+
+    Returns (outer_iters[s], inner_iters[s], relres[s], status[s], CgStats)."""
+    _require_cuda(values, values_lo, b, x, work, diag_lo)
+    dt = _DT[str(values_lo.dtype).replace("torch.", "")]
+    oi = (ctypes.c_int32 * s)()
+    ii = (ctypes.c_int32 * s)()
+    rr = (ctypes.c_double * s)()
+    stt = (ctypes.c_int32 * s)()
+    stats = CgStats()
+    rc = lib().ens_cg_mixed(graph.ref(), s, _ptr(values), _ptr(values_lo), dt, _ptr(diag_lo), _ptr(b),
+                            _ptr(x), tol, max_outer, inner_tol, max_inner, check_every, _ptr(work),
+                            work.numel() * work.element_size(), oi, ii, rr, stt, ctypes.byref(stats),
+                            _stream(stream))
+    if rc not in (0, ERR_NOT_CONVERGED, ERR_BREAKDOWN):
+        _check(rc)
+    return list(oi), list(ii), list(rr), list(stt), stats
 
 
 # ------------------------------------------------------------ convenience

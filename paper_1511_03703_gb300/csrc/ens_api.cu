@@ -57,36 +57,35 @@ static int tree_levels(int64_t n_rows, int64_t *count) {
     return L;
 }
 
-size_t dot_tree_bytes(int64_t n_rows, int width) {
+size_t dot_tree_bytes(int64_t n_rows, int width, size_t elem) {
     int64_t count[kTreeMaxLevels + 2] = {0};
     int L = tree_levels(n_rows, count);
     size_t bytes = 0;
-    for (int l = 1; l <= L; ++l) bytes += round_up(sizeof(double) * (size_t)count[l] * width, 256);
+    for (int l = 1; l <= L; ++l) bytes += round_up(elem * (size_t)count[l] * width, 256);
     for (int l = 1; l < L; ++l) bytes += round_up(sizeof(int) * (size_t)count[l + 1], 256);
     return bytes;
 }
 
-void dot_tree_layout(DotTree *t, int64_t n_rows, int width, void *base) {
-    memset(t, 0, sizeof(*t));
+void dot_tree_layout_raw(int *levels, int64_t *count_out, void **buf, int **counter, int64_t n_rows,
+                         int width, size_t elem, void *base) {
     int64_t count[kTreeMaxLevels + 2] = {0};
     int L = tree_levels(n_rows, count);
-    t->levels = L;
-    t->width = width;
+    *levels = L;
     char *p = static_cast<char *>(base);
     for (int l = 1; l <= L; ++l) {
-        t->count[l] = count[l];
-        t->buf[l] = reinterpret_cast<double *>(p);
-        p += round_up(sizeof(double) * (size_t)count[l] * width, 256);
+        count_out[l] = count[l];
+        buf[l] = p;
+        p += round_up(elem * (size_t)count[l] * width, 256);
     }
     for (int l = 1; l < L; ++l) {
-        t->counter[l] = reinterpret_cast<int *>(p);
+        counter[l] = reinterpret_cast<int *>(p);
         p += round_up(sizeof(int) * (size_t)count[l + 1], 256);
     }
 }
 
-int dot_tree_clear(const DotTree &t, cudaStream_t st) {
-    for (int l = 1; l < t.levels; ++l)
-        ENS_CUDA_TRY(cudaMemsetAsync(t.counter[l], 0, sizeof(int) * (size_t)t.count[l + 1], st));
+int dot_tree_clear_raw(int levels, const int64_t *count, int *const *counter, cudaStream_t st) {
+    for (int l = 1; l < levels; ++l)
+        ENS_CUDA_TRY(cudaMemsetAsync(counter[l], 0, sizeof(int) * (size_t)count[l + 1], st));
     return ENS_OK;
 }
 

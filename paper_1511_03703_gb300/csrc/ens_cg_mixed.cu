@@ -1,0 +1,677 @@
+// ens_cg_mixed.cu -- mixed-precision ensemble CG: FP64 iterative refinement
+// around an FP32 inner CG on FP32 or BF16 matrix values.
+//
+// Refinement (per member e, member-wise masks as in ens_cg):
+//   r = b - A x            FP64 values, FP64 arithmetic (the true residual)
+//   stop when |r| <= tol |b|
+//   solve A_lo d = r/|r|   FP32 CG on the low-precision copy of A (FP32 vectors,
+//                          FP32 accumulation) to |r_in| <= inner_tol
+//   x += |r| d             FP64 update
+// The low-precision copy is made by ens_convert_values.  BF16 keeps 8
+// significand bits, which perturbs the zero row sums of the diffusion stencil
+// by about as much as its smallest eigenvalue; the converter can therefore
+// keep the diagonal in FP32, chosen so that every row of A_lo sums to the FP64
+// row sum (the smooth modes that carry the small eigenvalues are preserved).
+#include <vector>
+
+#include "ens_spmv.cuh"
+
+namespace ens {
+
+// ------------------------------------------------------------ conversion
+template <typename V>
+__device__ __forceinline__ V to_lo(double v);
+template <>
+__device__ __forceinline__ float to_lo<float>(double v) { return __double2float_rn(v); }
+template <>
+__device__ __forceinline__ __nv_bfloat16 to_lo<__nv_bfloat16>(double v) {
+    return __float2bfloat16_rn(__double2float_rn(v));
+}
+template <typename V>
+__device__ __forceinline__ double lo_to_double(V v);
+template <>
+__device__ __forceinline__ double lo_to_double<float>(float v) { return (double)v; }
+template <>
+__device__ __forceinline__ double lo_to_double<__nv_bfloat16>(__nv_bfloat16 v) {
+    return (double)__bfloat162float(v);
+}
+
+// thread per (row, member)
+template <typename V>
+__global__ void convert_values_kernel(int32_t n, int s, const int32_t *__restrict__ row_map,
+                                      const int32_t *__restrict__ col,
+                                      const double *__restrict__ v64, V *__restrict__ vlo,
+                                      float *__restrict__ diag) {
+    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t I = t / s;
+    const int e = (int)(t % s);
+    if (I >= n) return;
+    const int rs = row_map[I], re = row_map[I + 1];
+    double rowsum = 0.0, offsum = 0.0;
+    for (int j = rs; j < re; ++j) {
+        const double a = v64[(int64_t)j * s + e];
+        V lo = to_lo<V>(a);
+        if (diag) {
+            rowsum += a;
+            if (col[j] == I) lo = to_lo<V>(0.0);
+            else offsum += lo_to_double<V>(lo);
+        }
+        vlo[(int64_t)j * s + e] = lo;
+    }
+    if (diag) diag[I * s + e] = __double2float_rn(rowsum - offsum);
+}
+
+// --------------------------------------------------- FP32 SpMV row evaluation
+template <typename V>
+struct ValLoad32;
+template <>
+struct ValLoad32<float> {
+    __device__ __forceinline__ static float2 two(const float *v, int64_t i) {
+        return ld_stream(reinterpret_cast<const float2 *>(v + i));
+    }
+    __device__ __forceinline__ static float one(const float *v, int64_t i) { return ld_stream(v + i); }
+};
+template <>
+struct ValLoad32<__nv_bfloat16> {
+    __device__ __forceinline__ static float2 two(const __nv_bfloat16 *v, int64_t i) {
+        const uint32_t u = ld_stream_u32(v + i);
+        return make_float2(__uint_as_float(u << 16), __uint_as_float(u & 0xffff0000u));
+    }
+    __device__ __forceinline__ static float one(const __nv_bfloat16 *v, int64_t i) {
+        return __uint_as_float(((uint32_t)ld_stream_u16(v + i)) << 16);
+    }
+};
+
+// members (2g, 2g+1); same 2-partial order as the FP64 SpMV; + diag * x_row
+template <int S, typename V, typename CA>
+__device__ __forceinline__ float2 row_spmv2_f32(CA colf, int rs, int re, const V *__restrict__ vals,
+                                                const float *__restrict__ x, int g) {
+    float a0 = 0.f, a1 = 0.f, b0 = 0.f, b1 = 0.f;
+    const int m = 2 * g;
+    int j = rs;
+    for (; j + 4 <= re; j += 4) {
+        const int c0 = colf(j), c1 = colf(j + 1), c2 = colf(j + 2), c3 = colf(j + 3);
+        const float2 v0 = ValLoad32<V>::two(vals, (int64_t)j * S + m);
+        const float2 v1 = ValLoad32<V>::two(vals, (int64_t)(j + 1) * S + m);
+        const float2 v2 = ValLoad32<V>::two(vals, (int64_t)(j + 2) * S + m);
+        const float2 v3 = ValLoad32<V>::two(vals, (int64_t)(j + 3) * S + m);
+        const float2 x0 = __ldg(reinterpret_cast<const float2 *>(x + (int64_t)c0 * S + m));
+        const float2 x1 = __ldg(reinterpret_cast<const float2 *>(x + (int64_t)c1 * S + m));
+        const float2 x2 = __ldg(reinterpret_cast<const float2 *>(x + (int64_t)c2 * S + m));
+        const float2 x3 = __ldg(reinterpret_cast<const float2 *>(x + (int64_t)c3 * S + m));
+        a0 = __fmaf_rn(v0.x, x0.x, a0); b0 = __fmaf_rn(v0.y, x0.y, b0);
+        a1 = __fmaf_rn(v1.x, x1.x, a1); b1 = __fmaf_rn(v1.y, x1.y, b1);
+        a0 = __fmaf_rn(v2.x, x2.x, a0); b0 = __fmaf_rn(v2.y, x2.y, b0);
+        a1 = __fmaf_rn(v3.x, x3.x, a1); b1 = __fmaf_rn(v3.y, x3.y, b1);
+    }
+    for (; j < re; ++j) {
+        const float2 v = ValLoad32<V>::two(vals, (int64_t)j * S + m);
+        const float2 xv = __ldg(reinterpret_cast<const float2 *>(x + (int64_t)colf(j) * S + m));
+        if ((j - rs) & 1) { a1 = __fmaf_rn(v.x, xv.x, a1); b1 = __fmaf_rn(v.y, xv.y, b1); }
+        else { a0 = __fmaf_rn(v.x, xv.x, a0); b0 = __fmaf_rn(v.y, xv.y, b0); }
+    }
+    return make_float2(__fadd_rn(a0, a1), __fadd_rn(b0, b1));
+}
+
+template <typename V, typename CA>
+__device__ __forceinline__ float row_spmv1_f32(CA colf, int rs, int re, const V *__restrict__ vals,
+                                               const float *__restrict__ x, int g, bool valid) {
+    float a = 0.f;
+    if (valid)
+        for (int j = rs + g; j < re; j += 2) a = __fmaf_rn(ValLoad32<V>::one(vals, j), __ldg(x + colf(j)), a);
+    const float o = __shfl_xor_sync(0xffffffffu, a, 1);
+    return (g == 0) ? __fadd_rn(a, o) : __fadd_rn(o, a);
+}
+
+template <int S, typename V>
+__device__ __forceinline__ float2 chunk_spmv_f32(const ChunkCols &cc, bool staged,
+                                                 const int32_t *__restrict__ col,
+                                                 const V *__restrict__ vals,
+                                                 const float *__restrict__ diag,
+                                                 const float *__restrict__ x, int r, int g,
+                                                 int64_t R, bool valid) {
+    const int rs = valid ? cc.rm[r] : 0, re = valid ? cc.rm[r + 1] : 0;
+    float2 y;
+    if constexpr (S == 1) {
+        const float v = staged ? row_spmv1_f32<V>(ColShared{cc.col, cc.rm[0]}, rs, re, vals, x, g, valid)
+                               : row_spmv1_f32<V>(ColGlobal{col}, rs, re, vals, x, g, valid);
+        y = make_float2(v, 0.f);
+        if (diag && valid) y.x = __fmaf_rn(diag[R], x[R], y.x);
+    } else {
+        if (!valid) return make_float2(0.f, 0.f);
+        y = staged ? row_spmv2_f32<S, V>(ColShared{cc.col, cc.rm[0]}, rs, re, vals, x, g)
+                   : row_spmv2_f32<S, V>(ColGlobal{col}, rs, re, vals, x, g);
+        if (diag) {
+            const float2 d = reinterpret_cast<const float2 *>(diag)[R * (S / 2) + g];
+            const float2 xr = reinterpret_cast<const float2 *>(x)[R * (S / 2) + g];
+            y.x = __fmaf_rn(d.x, xr.x, y.x);
+            y.y = __fmaf_rn(d.y, xr.y, y.y);
+        }
+    }
+    return y;
+}
+
+// float chunk tree: 32-row halving tree, members packed (same pairing as warp_tree32)
+template <int S>
+__device__ __forceinline__ void chunk_tree_f(float (*sm)[S + 1], float v0, float v1, int r, int g,
+                                             const DotTreeT<float> &t, int64_t chunk) {
+    if constexpr (S == 1) {
+        if (g == 0) sm[r][0] = v0;
+    } else {
+        sm[r][2 * g] = v0;
+        sm[r][2 * g + 1] = v1;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int h = 16; h >= 1; h >>= 1) {
+        for (int it = threadIdx.x; it < h * S; it += blockDim.x) {
+            const int i = it / S, e = it % S;
+            sm[i][e] = __fadd_rn(sm[i][e], sm[i + h][e]);
+        }
+        __syncthreads();
+    }
+    for (int e = threadIdx.x; e < S; e += blockDim.x) t.buf[1][chunk * t.width + e] = sm[0][e];
+    __syncthreads();
+}
+
+// ------------------------------------------------------------ state
+struct MxState {
+    double rn[32], bnorm[32];
+    float rho0[32], rho[32], alpha[32], beta[32];
+    int active_out[32], active_in[32], updd[32], outer_it[32], inner_it[32], inner_total[32];
+    int status[32], inner_break[32], zerox[32];
+    int active_out_count, active_in_count, updd_any, zero_any;
+};
+
+struct MxArgs {
+    int32_t n;
+    const int32_t *row_map, *col;
+    const double *v64;
+    const void *vlo;
+    const float *diag;
+    const double *b;
+    double *x;
+    float *r32, *rf, *pf, *qf, *d;
+    MxState *st;
+    DotTreeT<double> t64;  // width 2s: r.r and b.b
+    DotTreeT<float> t32;   // width s
+    double tol;
+    float inner_tol;
+    int max_outer, max_inner;
+};
+
+// ------------------------------------------------------------------ MR
+// r = b - A x in FP64 (split SpMV, x split on the fly); r32 = float(r); norms
+template <int S>
+__global__ void __launch_bounds__(RowMap<S>::THREADS, 1024 / RowMap<S>::THREADS) mx_resid_kernel(MxArgs a, int first) {
+    constexpr int G = RowMap<S>::G;
+    __shared__ ChunkCols cc;
+    __shared__ double sm[32][S + 1];
+    const int r = threadIdx.x / G, g = threadIdx.x % G;
+    const int64_t R = (int64_t)blockIdx.x * 32 + r;
+    const bool staged = stage_chunk(cc, a.row_map, a.col, blockIdx.x, a.n);
+    const double2 ax = chunk_spmv_split<S, XSplit>(cc, staged, a.col, a.v64, a.x, a.x, r, g, R < a.n);
+    double rr0 = 0.0, rr1 = 0.0, bb0 = 0.0, bb1 = 0.0;
+    if (R < a.n) {
+        if constexpr (S == 1) {
+            const double bv = a.b[R], res = bv - ax.x;
+            if (g == 0) a.r32[R] = __double2float_rn(res);
+            rr0 = res * res;
+            bb0 = bv * bv;
+        } else {
+            const double2 bv = reinterpret_cast<const double2 *>(a.b)[R * G + g];
+            const double rx = bv.x - ax.x, ry = bv.y - ax.y;
+            reinterpret_cast<float2 *>(a.r32)[R * G + g] = make_float2(__double2float_rn(rx), __double2float_rn(ry));
+            rr0 = rx * rx; rr1 = ry * ry;
+            bb0 = bv.x * bv.x; bb1 = bv.y * bv.y;
+        }
+    }
+    chunk_tree<S>(sm, rr0, rr1, r, g, a.t64, blockIdx.x, 0);
+    chunk_tree<S>(sm, bb0, bb1, r, g, a.t64, blockIdx.x, S);
+    if (!dot_tree_propagate(a.t64, blockIdx.x, 1)) return;
+    if (threadIdx.x >= 32) return;
+    const unsigned FULL = 0xffffffffu;
+    const int e = threadIdx.x;
+    MxState *st = a.st;
+    const double *top = a.t64.buf[a.t64.levels];
+    int act = 0;
+    if (e < S) {
+        const double rn = sqrt(ld_cg(top + e));
+        const double bn = first ? sqrt(ld_cg(top + S + e)) : st->bnorm[e];
+        st->rn[e] = rn;
+        if (first) {
+            st->bnorm[e] = bn;
+            st->outer_it[e] = 0;
+            st->inner_total[e] = 0;
+            st->inner_break[e] = 0;
+            st->status[e] = ENS_OK;
+            act = 1;
+        } else {
+            act = st->active_out[e];
+        }
+        int zx = 0;
+        if (act) {
+            if (bn == 0.0) { act = 0; zx = first; st->status[e] = ENS_OK; st->rn[e] = 0.0; }  // b = 0: x = 0
+            else if (rn <= a.tol * bn) { act = 0; st->status[e] = ENS_OK; }
+            else if (st->outer_it[e] >= a.max_outer) { act = 0; st->status[e] = ENS_ERR_NOT_CONVERGED; }
+        }
+        st->active_out[e] = act;
+        if (first) st->zerox[e] = zx;
+    }
+    const int ac = __popc(__ballot_sync(FULL, act));
+    const int zany = __popc(__ballot_sync(FULL, (e < S && first) ? st->zerox[e] : 0));
+    if (e == 0) {
+        st->active_out_count = ac;
+        if (first) st->zero_any = zany;
+    }
+    __threadfence();
+}
+
+// ------------------------------------------------------------------ MI0
+template <int S>
+__global__ void __launch_bounds__(RowMap<S>::THREADS) mx_inner_init_kernel(MxArgs a) {
+    if (ld_cg(&a.st->active_out_count) == 0) return;
+    constexpr int G = RowMap<S>::G;
+    __shared__ float sm[32][S + 1];
+    const int r = threadIdx.x / G, g = threadIdx.x % G;
+    const int64_t R = (int64_t)blockIdx.x * 32 + r;
+    const MxState *cs = a.st;
+    float v0 = 0.f, v1 = 0.f;
+    if (R < a.n) {
+        if constexpr (S == 1) {
+            if (g == 0) {
+                const float inv = cs->rn[0] > 0.0 ? (float)(1.0 / cs->rn[0]) : 0.f;
+                const float rv = a.r32[R] * inv;
+                a.rf[R] = rv; a.pf[R] = rv; a.d[R] = 0.f;
+                v0 = rv * rv;
+            }
+        } else {
+            const int m = 2 * g;
+            const float i0 = cs->rn[m] > 0.0 ? (float)(1.0 / cs->rn[m]) : 0.f;
+            const float i1 = cs->rn[m + 1] > 0.0 ? (float)(1.0 / cs->rn[m + 1]) : 0.f;
+            const float2 rv0 = reinterpret_cast<const float2 *>(a.r32)[R * G + g];
+            const float2 rv = make_float2(rv0.x * i0, rv0.y * i1);
+            reinterpret_cast<float2 *>(a.rf)[R * G + g] = rv;
+            reinterpret_cast<float2 *>(a.pf)[R * G + g] = rv;
+            reinterpret_cast<float2 *>(a.d)[R * G + g] = make_float2(0.f, 0.f);
+            v0 = rv.x * rv.x;
+            v1 = rv.y * rv.y;
+        }
+    }
+    chunk_tree_f<S>(sm, v0, v1, r, g, a.t32, blockIdx.x);
+    if (!dot_tree_propagate(a.t32, blockIdx.x, 1)) return;
+    if (threadIdx.x >= 32) return;
+    const unsigned FULL = 0xffffffffu;
+    const int e = threadIdx.x;
+    MxState *st = a.st;
+    int act = 0;
+    if (e < S) {
+        const float rho = ld_cg(a.t32.buf[a.t32.levels] + e);
+        st->rho0[e] = rho;
+        st->rho[e] = rho;
+        st->inner_it[e] = 0;
+        st->updd[e] = 0;
+        act = st->active_out[e] && rho > 0.f;
+        st->active_in[e] = act;
+    }
+    const int ac = __popc(__ballot_sync(FULL, act));
+    if (e == 0) { st->active_in_count = ac; st->updd_any = 0; }
+    __threadfence();
+}
+
+// ------------------------------------------------------------------ MI1
+template <int S, typename V>
+__global__ void __launch_bounds__(RowMap<S>::THREADS, 1536 / RowMap<S>::THREADS) mx_inner_spmv_kernel(MxArgs a) {
+    MxState *st = a.st;
+    if (ld_cg(&st->active_in_count) == 0) {
+        if (blockIdx.x == 0 && threadIdx.x == 0 && st->updd_any) {
+            for (int e = 0; e < S; ++e) st->updd[e] = 0;
+            st->updd_any = 0;
+        }
+        return;
+    }
+    constexpr int G = RowMap<S>::G;
+    __shared__ ChunkCols cc;
+    __shared__ float sm[32][S + 1];
+    const int r = threadIdx.x / G, g = threadIdx.x % G;
+    const int64_t R = (int64_t)blockIdx.x * 32 + r;
+    const bool staged = stage_chunk(cc, a.row_map, a.col, blockIdx.x, a.n);
+    const float2 ap = chunk_spmv_f32<S, V>(cc, staged, a.col, static_cast<const V *>(a.vlo), a.diag,
+                                           a.pf, r, g, R, R < a.n);
+    float v0 = 0.f, v1 = 0.f;
+    if (R < a.n) {
+        if constexpr (S == 1) {
+            if (g == 0) a.qf[R] = ap.x;
+            v0 = ap.x * a.pf[R];
+        } else {
+            reinterpret_cast<float2 *>(a.qf)[R * G + g] = ap;
+            const float2 pv = reinterpret_cast<const float2 *>(a.pf)[R * G + g];
+            v0 = ap.x * pv.x;
+            v1 = ap.y * pv.y;
+        }
+    }
+    chunk_tree_f<S>(sm, v0, v1, r, g, a.t32, blockIdx.x);
+    if (!dot_tree_propagate(a.t32, blockIdx.x, 1)) return;
+    if (threadIdx.x >= 32) return;
+    const unsigned FULL = 0xffffffffu;
+    const int e = threadIdx.x;
+    int act = 0;
+    if (e < S) {
+        act = st->active_in[e];
+        const float pi = ld_cg(a.t32.buf[a.t32.levels] + e);
+        if (act) {
+            if (!(pi > 0.f) || !isfinite(pi)) { act = 0; st->inner_break[e] += 1; }
+            else st->alpha[e] = st->rho[e] / pi;
+        }
+        st->active_in[e] = act;
+        st->updd[e] = 0;
+    }
+    const int ac = __popc(__ballot_sync(FULL, act));
+    if (e == 0) { st->active_in_count = ac; st->updd_any = 0; }
+    __threadfence();
+}
+
+// ------------------------------------------------------------------ MI2
+template <int S>
+__global__ void __launch_bounds__(RowMap<S>::THREADS) mx_inner_resid_kernel(MxArgs a) {
+    if (ld_cg(&a.st->active_in_count) == 0) return;
+    constexpr int G = RowMap<S>::G;
+    __shared__ float sm[32][S + 1];
+    const int r = threadIdx.x / G, g = threadIdx.x % G;
+    const int64_t R = (int64_t)blockIdx.x * 32 + r;
+    const MxState *cs = a.st;
+    float v0 = 0.f, v1 = 0.f;
+    if (R < a.n) {
+        if constexpr (S == 1) {
+            if (g == 0) {
+                float rv = a.rf[R];
+                if (cs->active_in[0]) { rv = __fmaf_rn(-cs->alpha[0], a.qf[R], rv); a.rf[R] = rv; }
+                v0 = rv * rv;
+            }
+        } else {
+            const int m = 2 * g;
+            float2 rv = reinterpret_cast<const float2 *>(a.rf)[R * G + g];
+            const float2 qv = reinterpret_cast<const float2 *>(a.qf)[R * G + g];
+            const bool a0 = cs->active_in[m], a1 = cs->active_in[m + 1];
+            if (a0) rv.x = __fmaf_rn(-cs->alpha[m], qv.x, rv.x);
+            if (a1) rv.y = __fmaf_rn(-cs->alpha[m + 1], qv.y, rv.y);
+            if (a0 || a1) reinterpret_cast<float2 *>(a.rf)[R * G + g] = rv;
+            v0 = rv.x * rv.x;
+            v1 = rv.y * rv.y;
+        }
+    }
+    chunk_tree_f<S>(sm, v0, v1, r, g, a.t32, blockIdx.x);
+    if (!dot_tree_propagate(a.t32, blockIdx.x, 1)) return;
+    if (threadIdx.x >= 32) return;
+    const unsigned FULL = 0xffffffffu;
+    const int e = threadIdx.x;
+    MxState *st = a.st;
+    int act = 0, ux = 0;
+    if (e < S) {
+        act = st->active_in[e];
+        const float rn = ld_cg(a.t32.buf[a.t32.levels] + e);
+        if (act) {
+            ux = 1;
+            const int it = st->inner_it[e] + 1;
+            st->inner_it[e] = it;
+            st->inner_total[e] += 1;
+            if (sqrtf(rn) <= a.inner_tol * sqrtf(st->rho0[e]) || it >= a.max_inner) act = 0;
+            else st->beta[e] = rn / st->rho[e];
+            st->rho[e] = rn;
+        }
+        st->active_in[e] = act;
+        st->updd[e] = ux;
+    }
+    const int ac = __popc(__ballot_sync(FULL, act)), uany = __popc(__ballot_sync(FULL, ux));
+    if (e == 0) { st->active_in_count = ac; st->updd_any = uany; }
+    __threadfence();
+}
+
+// ------------------------------------------------------------------ MI3
+template <int S>
+__global__ void __launch_bounds__(RowMap<S>::THREADS) mx_inner_update_kernel(MxArgs a) {
+    const MxState *st = a.st;
+    if (ld_cg(&st->updd_any) == 0) return;
+    constexpr int G = RowMap<S>::G;
+    const int r = threadIdx.x / G, g = threadIdx.x % G;
+    const int64_t R = (int64_t)blockIdx.x * 32 + r;
+    if (R >= a.n) return;
+    if constexpr (S == 1) {
+        if (g != 0) return;
+        const float pv = a.pf[R];
+        if (st->updd[0]) a.d[R] = __fmaf_rn(st->alpha[0], pv, a.d[R]);
+        if (st->active_in[0]) a.pf[R] = __fmaf_rn(st->beta[0], pv, a.rf[R]);
+    } else {
+        const int m = 2 * g;
+        const float2 pv = reinterpret_cast<const float2 *>(a.pf)[R * G + g];
+        const bool u0 = st->updd[m], u1 = st->updd[m + 1];
+        const bool c0 = st->active_in[m], c1 = st->active_in[m + 1];
+        if (u0 || u1) {
+            float2 dv = reinterpret_cast<const float2 *>(a.d)[R * G + g];
+            if (u0) dv.x = __fmaf_rn(st->alpha[m], pv.x, dv.x);
+            if (u1) dv.y = __fmaf_rn(st->alpha[m + 1], pv.y, dv.y);
+            reinterpret_cast<float2 *>(a.d)[R * G + g] = dv;
+        }
+        if (c0 || c1) {
+            const float2 rv = reinterpret_cast<const float2 *>(a.rf)[R * G + g];
+            float2 pn = pv;
+            if (c0) pn.x = __fmaf_rn(st->beta[m], pv.x, rv.x);
+            if (c1) pn.y = __fmaf_rn(st->beta[m + 1], pv.y, rv.y);
+            reinterpret_cast<float2 *>(a.pf)[R * G + g] = pn;
+        }
+    }
+}
+
+// x = 0 for members with b = 0 (one-shot, after the first residual)
+template <int S>
+__global__ void mx_zero_kernel(MxArgs a) {
+    if (ld_cg(&a.st->zero_any) == 0) return;
+    const int64_t total = (int64_t)a.n * S;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
+         i += (int64_t)gridDim.x * blockDim.x)
+        if (a.st->zerox[i % S]) a.x[i] = 0.0;
+}
+
+// ------------------------------------------------------------------ MU
+// x += |r| d (FP64) for members still refining; counts the refinement step
+template <int S>
+__global__ void mx_update_x_kernel(MxArgs a) {
+    const MxState *st = a.st;
+    if (ld_cg(&st->active_out_count) == 0) return;
+    const int64_t total = (int64_t)a.n * S;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int e = (int)(i % S);
+        if (st->active_out[e]) a.x[i] = fma(st->rn[e], (double)a.d[i], a.x[i]);
+    }
+    if (blockIdx.x == 0 && threadIdx.x < S && st->active_out[threadIdx.x])
+        a.st->outer_it[threadIdx.x] += 1;
+}
+
+// ------------------------------------------------------------ host side
+static size_t al256(size_t x) { return (x + 255) / 256 * 256; }
+
+static size_t mx_bytes(int64_t n, int s) {
+    return al256(sizeof(MxState)) + 5 * al256(sizeof(float) * (size_t)n * s) +
+           dot_tree_bytes(n, 2 * s, sizeof(double)) + dot_tree_bytes(n, s, sizeof(float));
+}
+
+struct MxOut {
+    int32_t *outer, *inner;
+    double *relres;
+    int32_t *status;
+    ens_cg_stats *stats;
+};
+
+template <int S, typename V>
+static int mx_run(const ens_graph *g, const double *v64, const void *vlo, const float *diag,
+                  const double *b, double *x, double tol, int max_outer, double inner_tol,
+                  int max_inner, int check_every, void *work, MxOut out, cudaStream_t st) {
+    const int64_t n = g->num_rows;
+    char *w = static_cast<char *>(work);
+    MxArgs a;
+    a.n = g->num_rows;
+    a.row_map = g->row_map;
+    a.col = g->col_entry;
+    a.v64 = v64;
+    a.vlo = vlo;
+    a.diag = diag;
+    a.b = b;
+    a.x = x;
+    a.st = reinterpret_cast<MxState *>(w);
+    w += al256(sizeof(MxState));
+    float **vecs[5] = {&a.r32, &a.rf, &a.pf, &a.qf, &a.d};
+    for (auto v : vecs) { *v = reinterpret_cast<float *>(w); w += al256(sizeof(float) * (size_t)n * S); }
+    dot_tree_layout(&a.t64, n, 2 * S, w);
+    w += dot_tree_bytes(n, 2 * S, sizeof(double));
+    dot_tree_layout(&a.t32, n, S, w);
+    a.tol = tol;
+    a.inner_tol = (float)inner_tol;
+    a.max_outer = max_outer;
+    a.max_inner = max_inner;
+    const unsigned grid = (unsigned)a.t32.count[1];
+    int rc;
+    if ((rc = dot_tree_clear(a.t64, st))) return rc;
+    if ((rc = dot_tree_clear(a.t32, st))) return rc;
+    ENS_CUDA_TRY(cudaMemsetAsync(a.st, 0, sizeof(MxState), st));
+    int launches = 0, polls = 0;
+    int32_t hflag[2];
+    auto poll = [&](const int *dev, int cnt) -> int {
+        ENS_CUDA_TRY(cudaMemcpyAsync(hflag, dev, cnt * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+        ENS_CUDA_TRY(cudaStreamSynchronize(st));
+        ++polls;
+        return ENS_OK;
+    };
+    mx_resid_kernel<S><<<grid, RowMap<S>::THREADS, 0, st>>>(a, 1);
+    mx_zero_kernel<S><<<152 * 2, 256, 0, st>>>(a);
+    launches += 2;
+    ENS_LAUNCH_CHECK("mx_resid_kernel");
+    if ((rc = poll(&a.st->active_out_count, 1))) return rc;
+    for (int outer = 0; outer < max_outer + 1 && hflag[0] > 0; ++outer) {
+        mx_inner_init_kernel<S><<<grid, RowMap<S>::THREADS, 0, st>>>(a);
+        ++launches;
+        const int max_blocks = max_inner / check_every + 2;
+        for (int blk = 0; blk < max_blocks; ++blk) {
+            for (int i = 0; i < check_every; ++i) {
+                mx_inner_spmv_kernel<S, V><<<grid, RowMap<S>::THREADS, 0, st>>>(a);
+                mx_inner_resid_kernel<S><<<grid, RowMap<S>::THREADS, 0, st>>>(a);
+                mx_inner_update_kernel<S><<<grid, RowMap<S>::THREADS, 0, st>>>(a);
+            }
+            launches += 3 * check_every;
+            ENS_LAUNCH_CHECK("mixed inner CG launch");
+            if ((rc = poll(&a.st->active_in_count, 2))) return rc;
+            if (hflag[0] == 0 && hflag[1] == 0) break;
+        }
+        mx_update_x_kernel<S><<<152 * 4, 256, 0, st>>>(a);
+        mx_resid_kernel<S><<<grid, RowMap<S>::THREADS, 0, st>>>(a, 0);
+        launches += 2;
+        ENS_LAUNCH_CHECK("mixed refinement launch");
+        if ((rc = poll(&a.st->active_out_count, 1))) return rc;
+    }
+    MxState hs;
+    ENS_CUDA_TRY(cudaMemcpyAsync(&hs, a.st, sizeof(MxState), cudaMemcpyDeviceToHost, st));
+    ENS_CUDA_TRY(cudaStreamSynchronize(st));
+    int first_bad = ENS_OK, maxit = 0;
+    for (int e = 0; e < S; ++e) {
+        if (out.outer) out.outer[e] = hs.outer_it[e];
+        if (out.inner) out.inner[e] = hs.inner_total[e];
+        if (out.relres) out.relres[e] = hs.bnorm[e] > 0.0 ? hs.rn[e] / hs.bnorm[e] : 0.0;
+        int stt = hs.status[e];
+        if (hs.active_out[e]) stt = ENS_ERR_NOT_CONVERGED;
+        if (out.status) out.status[e] = stt;
+        if (stt != ENS_OK && first_bad == ENS_OK) first_bad = stt;
+        maxit = hs.inner_total[e] > maxit ? hs.inner_total[e] : maxit;
+    }
+    if (out.stats) {
+        out.stats->spmv_ms = 0.0;
+        out.stats->spmv_launches = 0;
+        out.stats->kernel_launches = launches;
+        out.stats->iterations = maxit;
+        out.stats->host_checks = polls;
+    }
+    if (first_bad != ENS_OK)
+        set_error("ens_cg_mixed: member status %d (%s)", first_bad, ens_status_string(first_bad));
+    return first_bad;
+}
+
+template <typename V>
+static int mx_dispatch(int s, const ens_graph *g, const double *v64, const void *vlo,
+                       const float *diag, const double *b, double *x, double tol, int max_outer,
+                       double inner_tol, int max_inner, int check_every, void *work, MxOut out,
+                       cudaStream_t st) {
+    switch (s) {
+        case 1: return mx_run<1, V>(g, v64, vlo, diag, b, x, tol, max_outer, inner_tol, max_inner, check_every, work, out, st);
+        case 4: return mx_run<4, V>(g, v64, vlo, diag, b, x, tol, max_outer, inner_tol, max_inner, check_every, work, out, st);
+        case 8: return mx_run<8, V>(g, v64, vlo, diag, b, x, tol, max_outer, inner_tol, max_inner, check_every, work, out, st);
+        case 16: return mx_run<16, V>(g, v64, vlo, diag, b, x, tol, max_outer, inner_tol, max_inner, check_every, work, out, st);
+        default: return mx_run<32, V>(g, v64, vlo, diag, b, x, tol, max_outer, inner_tol, max_inner, check_every, work, out, st);
+    }
+}
+
+}  // namespace ens
+
+using namespace ens;
+
+extern "C" int ens_convert_values(const ens_graph *graph, int s, const double *values,
+                                  int dtype, void *values_lo, float *diag_lo, void *stream) {
+    int rc = check_graph(graph);
+    if (rc) return rc;
+    if (!supported_s(s)) return fail(ENS_ERR_UNSUPPORTED, "ensemble size s=%d not in {1,4,8,16,32}", s);
+    if (!values || !values_lo) return fail(ENS_ERR_ARG, "NULL values / values_lo");
+    if (s > 1 && (!aligned16(values_lo) || (diag_lo && !aligned16(diag_lo))))
+        return fail(ENS_ERR_ALIGN, "values_lo / diag_lo must be 16-byte aligned");
+    const int64_t nt = (int64_t)graph->num_rows * s;
+    if (nt == 0) return ENS_OK;
+    cudaStream_t st = as_stream(stream);
+    const unsigned grid = (unsigned)((nt + 255) / 256);
+    if (dtype == ENS_F32)
+        convert_values_kernel<float><<<grid, 256, 0, st>>>(graph->num_rows, s, graph->row_map, graph->col_entry,
+                                                           values, static_cast<float *>(values_lo), diag_lo);
+    else if (dtype == ENS_BF16)
+        convert_values_kernel<__nv_bfloat16><<<grid, 256, 0, st>>>(graph->num_rows, s, graph->row_map,
+                                                                   graph->col_entry, values,
+                                                                   static_cast<__nv_bfloat16 *>(values_lo), diag_lo);
+    else
+        return fail(ENS_ERR_UNSUPPORTED, "convert to dtype %d (ENS_F32 or ENS_BF16 only)", dtype);
+    ENS_LAUNCH_CHECK("convert_values_kernel");
+    return ENS_OK;
+}
+
+extern "C" int ens_cg_mixed_workspace_size(int32_t num_rows, int s, size_t *bytes) {
+    if (num_rows < 0) return fail(ENS_ERR_ARG, "num_rows < 0");
+    if (!supported_s(s)) return fail(ENS_ERR_UNSUPPORTED, "ensemble size s=%d not in {1,4,8,16,32}", s);
+    if (!bytes) return fail(ENS_ERR_ARG, "bytes is NULL");
+    *bytes = mx_bytes(num_rows, s);
+    return ENS_OK;
+}
+
+extern "C" int ens_cg_mixed(const ens_graph *graph, int s, const double *values,
+                            const void *values_lo, int dtype_lo, const float *diag_lo,
+                            const double *b, double *x, double tol, int max_outer,
+                            double inner_tol, int max_inner, int check_every, void *work,
+                            size_t work_bytes, int32_t *outer_iters_host,
+                            int32_t *inner_iters_host, double *relres_host,
+                            int32_t *status_host, ens_cg_stats *stats_host, void *stream) {
+    int rc = check_graph(graph);
+    if (rc) return rc;
+    if (!supported_s(s)) return fail(ENS_ERR_UNSUPPORTED, "ensemble size s=%d not in {1,4,8,16,32}", s);
+    if (graph->num_rows == 0) return fail(ENS_ERR_ARG, "empty graph");
+    if (!values || !values_lo || !b || !x || !work) return fail(ENS_ERR_ARG, "NULL pointer argument");
+    if (dtype_lo != ENS_F32 && dtype_lo != ENS_BF16)
+        return fail(ENS_ERR_UNSUPPORTED, "inner dtype %d (ENS_F32 or ENS_BF16 only)", dtype_lo);
+    if (!(tol >= 0.0) || !(inner_tol > 0.0) || max_outer < 0 || max_inner < 1 || check_every < 1)
+        return fail(ENS_ERR_ARG, "tol=%g inner_tol=%g max_outer=%d max_inner=%d check_every=%d",
+                    tol, inner_tol, max_outer, max_inner, check_every);
+    if (!aligned16(work) || (s > 1 && (!aligned16(values) || !aligned16(values_lo) || !aligned16(b) ||
+                                       !aligned16(x) || (diag_lo && !aligned16(diag_lo)))))
+        return fail(ENS_ERR_ALIGN, "arrays must be 16-byte aligned");
+    const size_t need = mx_bytes(graph->num_rows, s);
+    if (work_bytes < need) return fail(ENS_ERR_WORKSPACE, "mixed workspace %zu < %zu bytes", work_bytes, need);
+    MxOut out{outer_iters_host, inner_iters_host, relres_host, status_host, stats_host};
+    cudaStream_t st = as_stream(stream);
+    if (dtype_lo == ENS_F32)
+        return mx_dispatch<float>(s, graph, values, values_lo, diag_lo, b, x, tol, max_outer, inner_tol,
+                                  max_inner, check_every, work, out, st);
+    return mx_dispatch<__nv_bfloat16>(s, graph, values, values_lo, diag_lo, b, x, tol, max_outer,
+                                      inner_tol, max_inner, check_every, work, out, st);
+}

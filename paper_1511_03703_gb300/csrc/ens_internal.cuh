@@ -88,15 +88,18 @@ __device__ __forceinline__ int ld_cg(const int *p) {
 // member's dot is bitwise the same at every ensemble size.
 constexpr int kTreeMaxLevels = 8;
 
-struct DotTree {
+template <typename T>
+struct DotTreeT {
     int levels;                       // number of levels above level 0 (>= 1)
-    int width;                        // doubles per item = ndots * s
+    int width;                        // values per item = ndots * s
     int64_t count[kTreeMaxLevels];    // items at level l (level 1 = chunks)
-    double *buf[kTreeMaxLevels];      // buf[l][item*width + w]
+    T *buf[kTreeMaxLevels];           // buf[l][item*width + w]
     int *counter[kTreeMaxLevels];     // counter[l][g]: arrivals of level-l items in group g
 };
+using DotTree = DotTreeT<double>;
 
-__device__ __forceinline__ double warp_tree32(double v) {
+template <typename T>
+__device__ __forceinline__ T warp_tree32(T v) {
     v += __shfl_xor_sync(0xffffffffu, v, 16);
     v += __shfl_xor_sync(0xffffffffu, v, 8);
     v += __shfl_xor_sync(0xffffffffu, v, 4);
@@ -105,11 +108,30 @@ __device__ __forceinline__ double warp_tree32(double v) {
     return v;
 }
 
-// Host: lay a DotTree out in caller scratch; returns bytes used (align 256).
-size_t dot_tree_bytes(int64_t n_rows, int width);
-void dot_tree_layout(DotTree *t, int64_t n_rows, int width, void *base);
+__device__ __forceinline__ float ld_cg(const float *p) {
+    float v;
+    asm volatile("ld.global.cg.f32 %0, [%1];" : "=f"(v) : "l"(p));
+    return v;
+}
+
+// Host: lay a tree out in caller scratch; returns bytes used (align 256).
+size_t dot_tree_bytes(int64_t n_rows, int width, size_t elem = sizeof(double));
+void dot_tree_layout_raw(int *levels, int64_t *count, void **buf, int **counter, int64_t n_rows,
+                         int width, size_t elem, void *base);
+template <typename T>
+inline void dot_tree_layout(DotTreeT<T> *t, int64_t n_rows, int width, void *base) {
+    void *bufs[kTreeMaxLevels] = {nullptr};
+    t->width = width;
+    for (int l = 0; l < kTreeMaxLevels; ++l) { t->count[l] = 0; t->buf[l] = nullptr; t->counter[l] = nullptr; }
+    dot_tree_layout_raw(&t->levels, t->count, bufs, t->counter, n_rows, width, sizeof(T), base);
+    for (int l = 0; l < kTreeMaxLevels; ++l) t->buf[l] = static_cast<T *>(bufs[l]);
+}
 // zero all arrival counters of a tree (the tree's kernels self-reset them)
-int dot_tree_clear(const DotTree &t, cudaStream_t st);
+int dot_tree_clear_raw(int levels, const int64_t *count, int *const *counter, cudaStream_t st);
+template <typename T>
+inline int dot_tree_clear(const DotTreeT<T> &t, cudaStream_t st) {
+    return dot_tree_clear_raw(t.levels, t.count, t.counter, st);
+}
 
 // Device: called by all threads of a CTA after the CTA wrote the level-1
 // items [item0, item0 + nitems) (buf[1][item*width ...], plain stores, all
@@ -119,7 +141,8 @@ int dot_tree_clear(const DotTree &t, cudaStream_t st);
 // CTA's stores before thread 0's gpu-scope fence and arrival atomic (fences
 // are cumulative); acquire: the last arriver fences after its atomic and the
 // barrier orders the other threads' L2 reads after it.
-__device__ __forceinline__ bool dot_tree_propagate(const DotTree &t, int64_t item0, int nitems) {
+template <typename T>
+__device__ __forceinline__ bool dot_tree_propagate(const DotTreeT<T> &t, int64_t item0, int nitems) {
     __shared__ int s_last;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
     int64_t item = item0;
@@ -139,11 +162,11 @@ __device__ __forceinline__ bool dot_tree_propagate(const DotTree &t, int64_t ite
         }
         __syncthreads();
         if (!s_last) return false;
-        const double *src = t.buf[l];
-        double *dst = t.buf[l + 1];
+        const T *src = t.buf[l];
+        T *dst = t.buf[l + 1];
         for (int w = warp; w < t.width; w += nwarps) {
-            double v = (lane < cnt) ? ld_cg(src + ((g << 5) + lane) * t.width + w) : 0.0;
-            v = warp_tree32(v);
+            T v = (lane < cnt) ? ld_cg(src + ((g << 5) + lane) * t.width + w) : T(0);
+            v = warp_tree32<T>(v);
             if (lane == 0) dst[g * t.width + w] = v;
         }
         __syncthreads();
