@@ -470,6 +470,115 @@ def main_reference(args):
     return out
 
 
+# ------------------------------------------------ mixed-precision workload
+MIX_N, MIX_S, MIX_BATCH, MIX_TOL = 128, 16, 256, 1e-10
+MIX_WORKLOAD = ("KL diffusion, 128^3 hex Q1 mesh (2,146,689 rows, 57,066,625 nnz), M=10, "
+                "256 samples as 16 ensembles of s=16, true residual 1e-10")
+
+
+def main_mixed(args):
+    """FP64 ensemble CG vs FP64-refined FP32 / BF16 inner CG on the 128^3 workload.
+    One step = set-up + 16 ensembles (assembly, value conversion, solve)."""
+    import torch
+    import paper_1511_03703_gb300 as E
+    from paper_1511_03703_gb300 import inputs
+    dev = torch.device("cuda:0")
+    E.lib()
+    N, M, s = MIX_N, M_KL, MIX_S
+    nens = MIX_BATCH // s
+    xs_all = inputs.kl_samples(inputs.SEED_MIXED, 0, MIX_BATCH, M)
+    xi = torch.from_numpy(np.stack([inputs.ensemble_layout(b) for b in xs_all.reshape(nens, s, M)])).to(dev)
+    mesh = E.Mesh(N, M, device=dev)
+    vals = torch.empty(mesh.nnz * s, dtype=torch.float64, device=dev)
+    b = torch.empty(mesh.n * s, dtype=torch.float64, device=dev)
+    X = torch.empty((nens, mesh.n * s), dtype=torch.float64, device=dev)
+    v32 = torch.empty(mesh.nnz * s, dtype=torch.float32, device=dev)
+    vbf = torch.empty(mesh.nnz * s, dtype=torch.bfloat16, device=dev)
+    diag = torch.empty(mesh.n * s, dtype=torch.float32, device=dev)
+    wcg = torch.empty(E.cg_workspace_size(mesh.n, s), dtype=torch.uint8, device=dev)
+    wmx = torch.empty(E.cg_mixed_workspace_size(mesh.n, s), dtype=torch.uint8, device=dev)
+    peak, _ = measured_peaks()
+    n, nnz = mesh.n, mesh.nnz
+
+    def run(form, stats):
+        mesh.assemble(s, xi[0], values=vals, b=b)  # warm the set-up path
+        t0 = time.perf_counter()
+        torch.cuda.synchronize()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record()
+        E.graph_build(N, mesh.row_map, mesh.col_entry, None, mesh.bmask)
+        E.kl_setup(N, M, L_CORR, mesh.kl_table, want_host=False)
+        E.mode_matrices(N, mesh.graph, M, mesh.kl_table, mesh.modes, mesh.load)
+        for g in range(nens):
+            mesh.assemble(s, xi[g], values=vals, b=b)
+            x = X[g]
+            x.zero_()
+            if form == "f64":
+                it, rr, st, cs = E.cg(mesh.graph, s, vals, b, x, MIX_TOL, 10000, wcg,
+                                      flags=E.CG_SPLIT64 | E.CG_TIME_SPMV, check_every=32)
+                stats["outer"].extend([1] * s)
+                stats["inner"].extend(it)
+                vb = 8
+            else:
+                lo = v32 if form == "f32" else vbf
+                dg = diag if form == "bf16" else None
+                E.convert_values(mesh.graph, s, vals, lo, dg)
+                oi, ii, rr, st, cs = E.cg_mixed(mesh.graph, s, vals, lo, b, x, MIX_TOL, wmx, diag_lo=dg,
+                                                inner_tol=1e-2 if form == "bf16" else 1e-4,
+                                                max_inner=5000, check_every=32, flags=E.CG_TIME_SPMV)
+                stats["outer"].extend(oi)
+                stats["inner"].extend(ii)
+                vb = 4 if form == "f32" else 2
+            stats["bad"] += sum(1 for v in st if v != 0)
+            stats["relres"].extend(rr)
+            stats["spmv_ms"] += cs.spmv_ms
+            stats["spmv_n"] += cs.spmv_launches
+            stats["vb"] = vb
+        ev1.record()
+        torch.cuda.synchronize()
+        return ev0.elapsed_time(ev1) / 1e3
+
+    out = {}
+    for form in ("f64", "f32", "bf16"):
+        for _ in range(args.warmup):
+            run(form, {"outer": [], "inner": [], "relres": [], "bad": 0, "spmv_ms": 0.0, "spmv_n": 0})
+        st = {"outer": [], "inner": [], "relres": [], "bad": 0, "spmv_ms": 0.0, "spmv_n": 0}
+        tt = sum(run(form, st) for _ in range(args.steps))
+        vb = st["vb"]
+        if form == "f64":
+            sb = spmv_bytes(n, nnz, s)
+        else:  # low-precision values, float x gather and q write, (bf16) FP32 diagonal
+            sb = nnz * (vb * s + 4) + 4 * (n + 1) + 2 * 4 * n * s + (4 * n * s if form == "bf16" else 0)
+        ms = st["spmv_ms"] / max(st["spmv_n"], 1)
+        out[form] = {"value": args.steps * MIX_BATCH / tt, "unit": UNIT,
+                     "spmv": "split f64" if form == "f64" else f"{form} values, f32 accumulation",
+                     "spmv_gbs": sb / (ms * 1e-3) / 1e9, "spmv_hbm_frac": sb / (ms * 1e-3) / 1e9 / peak,
+                     "outer_mean": float(np.mean(st["outer"])), "inner_mean": float(np.mean(st["inner"])),
+                     "max_relres": float(max(st["relres"])), "failed": st["bad"]}
+        # error against oracle FP64 solves of two samples (last step's solutions)
+        out[form]["x_ens0"] = X[0].view(-1, s)[:, :2].cpu().numpy().copy()
+    import oracle
+    nref = 2
+    t0 = time.perf_counter()
+    xo, ito, rro, sto = oracle.solve_samples(N, M, xs_all[:nref], 1e-12, 20000, nthreads=nref, want_x=True)
+    toracle = time.perf_counter() - t0
+    for form in out:
+        xg = out[form].pop("x_ens0")
+        out[form]["rel_err_vs_fp64_oracle"] = [float(np.linalg.norm(xg[:, j] - xo[j]) / np.linalg.norm(xo[j]))
+                                               for j in range(nref)]
+    line = {"metric": "ensemble CG sample-solves/s, FP64 vs mixed precision (FP32 / BF16 values, FP64 refinement)",
+            "value": out["f32"]["value"], "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32 inner (f32 values), f64 residual and update", "data": "synthetic",
+            "config": {"workload": MIX_WORKLOAD, "ensemble_size": s, "batch_samples": MIX_BATCH,
+                       "inner_tol": {"f32": 1e-4, "bf16": 1e-2}, "bf16_diagonal": "fp32, row-sum compensated",
+                       "l2": "inputs larger than L2"},
+            "forms": out,
+            "oracle": {"samples": nref, "tol": 1e-12, "iters": [int(v) for v in ito],
+                       "seconds": toracle, "threads": nref}}
+    print(json.dumps(line))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -482,7 +591,12 @@ def main():
                          "or alternate entries on each (split)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--quick", action="store_true", help="skip the other-form run and the s sweep")
+    ap.add_argument("--workload", default="scale", choices=["scale", "mixed"],
+                    help="scale: 64^3 ensemble CG (default line); mixed: 128^3 mixed precision")
     args = ap.parse_args()
+    if args.workload == "mixed" and args.impl != "reference":
+        main_mixed(args)
+        return
     if args.impl == "reference":
         main_reference(args)
     else:

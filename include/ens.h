@@ -78,7 +78,7 @@ int ens_version(void);
 
 /* ---------------------------------------------------------------- A1 graph */
 /* Host only.  Sizes of the Q1 mesh with N cells per side:
- * num_rows = (N+1)^3, num_entries = (3N+1)^3, num_cells = N^3.  1 <= N <= 512. */
+ * num_rows = (N+1)^3, num_entries = (3N+1)^3, num_cells = N^3.  1 <= N <= 400. */
 int ens_mesh_sizes(int N, int32_t *num_rows, int64_t *num_entries, int64_t *num_cells);
 
 /* Builds the CRS graph of the Q1 hex mesh (Fig. 2; Algorithm 2's NodeIndex and
@@ -234,12 +234,14 @@ int ens_convert_values(const ens_graph *graph, int s, const double *values, int 
  *     x += ||r|| d (FP64).
  * Members with b = 0 return x = 0.  outer_iters_host[s] = refinement steps,
  * inner_iters_host[s] = total inner iterations, relres_host[s] = the final
- * true ||b - A x||/||b||.  work: ens_cg_mixed_workspace_size bytes.
+ * true ||b - A x||/||b||.  flags: ENS_CG_TIME_SPMV records CUDA events around
+ * the inner SpMV launches (stats_host->spmv_ms / spmv_launches).
+ * work: ens_cg_mixed_workspace_size bytes.
  * Synchronises `stream`.  Returns ENS_OK when every member converged. */
 int ens_cg_mixed_workspace_size(int32_t num_rows, int s, size_t *bytes);
 int ens_cg_mixed(const ens_graph *graph, int s, const double *values, const void *values_lo,
                  int dtype_lo, const float *diag_lo, const double *b, double *x, double tol,
-                 int max_outer, double inner_tol, int max_inner, int check_every, void *work,
+                 int max_outer, double inner_tol, int max_inner, int check_every, int flags, void *work,
                  size_t work_bytes, int32_t *outer_iters_host, int32_t *inner_iters_host,
                  double *relres_host, int32_t *status_host, ens_cg_stats *stats_host,
                  void *stream);

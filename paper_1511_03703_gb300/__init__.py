@@ -88,7 +88,7 @@ def _declare(L):
         "ens_cg": (I, [P(EnsGraphC), I, vp, vp, vp, d, I, I, I, vp, sz, vp, vp, vp, P(CgStats), vp]),
         "ens_convert_values": (I, [P(EnsGraphC), I, vp, I, vp, vp, vp]),
         "ens_cg_mixed_workspace_size": (I, [i32, I, P(sz)]),
-        "ens_cg_mixed": (I, [P(EnsGraphC), I, vp, vp, I, vp, vp, vp, d, I, d, I, I, vp, sz, vp, vp,
+        "ens_cg_mixed": (I, [P(EnsGraphC), I, vp, vp, I, vp, vp, vp, d, I, d, I, I, I, vp, sz, vp, vp,
                              vp, vp, P(CgStats), vp]),
     }
     for name, (res, args) in sig.items():
@@ -260,7 +260,7 @@ def cg_mixed_workspace_size(n, s):
 
 
 def cg_mixed(graph, s, values, values_lo, b, x, tol, work, diag_lo=None, max_outer=20,
-             inner_tol=1e-4, max_inner=2000, check_every=8, stream=None):
+             inner_tol=1e-4, max_inner=2000, check_every=8, flags=0, stream=None):
     """FP64 iterative refinement around an FP32 inner CG; synchronises.
 
     Returns (outer_iters[s], inner_iters[s], relres[s], status[s], CgStats)."""
@@ -272,7 +272,7 @@ def cg_mixed(graph, s, values, values_lo, b, x, tol, work, diag_lo=None, max_out
     stt = (ctypes.c_int32 * s)()
     stats = CgStats()
     rc = lib().ens_cg_mixed(graph.ref(), s, _ptr(values), _ptr(values_lo), dt, _ptr(diag_lo), _ptr(b),
-                            _ptr(x), tol, max_outer, inner_tol, max_inner, check_every, _ptr(work),
+                            _ptr(x), tol, max_outer, inner_tol, max_inner, check_every, flags, _ptr(work),
                             work.numel() * work.element_size(), oi, ii, rr, stt, ctypes.byref(stats),
                             _stream(stream))
     if rc not in (0, ERR_NOT_CONVERGED, ERR_BREAKDOWN):

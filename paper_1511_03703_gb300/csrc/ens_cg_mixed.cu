@@ -12,6 +12,7 @@
 // by about as much as its smallest eigenvalue; the converter can therefore
 // keep the diagonal in FP32, chosen so that every row of A_lo sums to the FP64
 // row sum (the smooth modes that carry the small eigenvalues are preserved).
+#include <algorithm>
 #include <vector>
 
 #include "ens_spmv.cuh"
@@ -181,6 +182,7 @@ struct MxState {
     int active_out[32], active_in[32], updd[32], outer_it[32], inner_it[32], inner_total[32];
     int status[32], inner_break[32], zerox[32];
     int active_out_count, active_in_count, updd_any, zero_any;
+    int spmv_real, pad0, pad1, pad2;
 };
 
 struct MxArgs {
@@ -367,7 +369,7 @@ __global__ void __launch_bounds__(RowMap<S>::THREADS, 1536 / RowMap<S>::THREADS)
         st->updd[e] = 0;
     }
     const int ac = __popc(__ballot_sync(FULL, act));
-    if (e == 0) { st->active_in_count = ac; st->updd_any = 0; }
+    if (e == 0) { st->active_in_count = ac; st->updd_any = 0; st->spmv_real += 1; }
     __threadfence();
 }
 
@@ -506,7 +508,7 @@ struct MxOut {
 template <int S, typename V>
 static int mx_run(const ens_graph *g, const double *v64, const void *vlo, const float *diag,
                   const double *b, double *x, double tol, int max_outer, double inner_tol,
-                  int max_inner, int check_every, void *work, MxOut out, cudaStream_t st) {
+                  int max_inner, int check_every, int flags, void *work, MxOut out, cudaStream_t st) {
     const int64_t n = g->num_rows;
     char *w = static_cast<char *>(work);
     MxArgs a;
@@ -535,6 +537,17 @@ static int mx_run(const ens_graph *g, const double *v64, const void *vlo, const 
     if ((rc = dot_tree_clear(a.t32, st))) return rc;
     ENS_CUDA_TRY(cudaMemsetAsync(a.st, 0, sizeof(MxState), st));
     int launches = 0, polls = 0;
+    const bool timing = (flags & ENS_CG_TIME_SPMV) != 0;
+    std::vector<cudaEvent_t> ev;
+    std::vector<float> spmv_ms;
+    if (timing) {
+        ev.resize(2 * (size_t)check_every);
+        for (auto &x_ev : ev) ENS_CUDA_TRY(cudaEventCreate(&x_ev));
+    }
+    struct EvGuard {
+        std::vector<cudaEvent_t> &v;
+        ~EvGuard() { for (auto &x_ev : v) cudaEventDestroy(x_ev); }
+    } ev_guard{ev};
     int32_t hflag[2];
     auto poll = [&](const int *dev, int cnt) -> int {
         ENS_CUDA_TRY(cudaMemcpyAsync(hflag, dev, cnt * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
@@ -553,13 +566,21 @@ static int mx_run(const ens_graph *g, const double *v64, const void *vlo, const 
         const int max_blocks = max_inner / check_every + 2;
         for (int blk = 0; blk < max_blocks; ++blk) {
             for (int i = 0; i < check_every; ++i) {
+                if (timing) cudaEventRecord(ev[2 * i], st);
                 mx_inner_spmv_kernel<S, V><<<grid, RowMap<S>::THREADS, 0, st>>>(a);
+                if (timing) cudaEventRecord(ev[2 * i + 1], st);
                 mx_inner_resid_kernel<S><<<grid, RowMap<S>::THREADS, 0, st>>>(a);
                 mx_inner_update_kernel<S><<<grid, RowMap<S>::THREADS, 0, st>>>(a);
             }
             launches += 3 * check_every;
             ENS_LAUNCH_CHECK("mixed inner CG launch");
             if ((rc = poll(&a.st->active_in_count, 2))) return rc;
+            if (timing)
+                for (int i = 0; i < check_every; ++i) {
+                    float ms = 0.f;
+                    cudaEventElapsedTime(&ms, ev[2 * i], ev[2 * i + 1]);
+                    spmv_ms.push_back(ms);
+                }
             if (hflag[0] == 0 && hflag[1] == 0) break;
         }
         mx_update_x_kernel<S><<<152 * 4, 256, 0, st>>>(a);
@@ -585,6 +606,17 @@ static int mx_run(const ens_graph *g, const double *v64, const void *vlo, const 
     if (out.stats) {
         out.stats->spmv_ms = 0.0;
         out.stats->spmv_launches = 0;
+        if (timing) {
+            // inner SpMV launches run in order; the first spmv_real of each
+            // inner solve did work, the rest exited early: keep the longest ones
+            std::vector<float> sorted = spmv_ms;
+            std::sort(sorted.begin(), sorted.end(), [](float u, float v) { return u > v; });
+            const int real = hs.spmv_real < (int)sorted.size() ? hs.spmv_real : (int)sorted.size();
+            double tot = 0.0;
+            for (int i = 0; i < real; ++i) tot += sorted[i];
+            out.stats->spmv_launches = real;
+            out.stats->spmv_ms = tot;
+        }
         out.stats->kernel_launches = launches;
         out.stats->iterations = maxit;
         out.stats->host_checks = polls;
@@ -597,14 +629,14 @@ static int mx_run(const ens_graph *g, const double *v64, const void *vlo, const 
 template <typename V>
 static int mx_dispatch(int s, const ens_graph *g, const double *v64, const void *vlo,
                        const float *diag, const double *b, double *x, double tol, int max_outer,
-                       double inner_tol, int max_inner, int check_every, void *work, MxOut out,
+                       double inner_tol, int max_inner, int check_every, int flags, void *work, MxOut out,
                        cudaStream_t st) {
     switch (s) {
-        case 1: return mx_run<1, V>(g, v64, vlo, diag, b, x, tol, max_outer, inner_tol, max_inner, check_every, work, out, st);
-        case 4: return mx_run<4, V>(g, v64, vlo, diag, b, x, tol, max_outer, inner_tol, max_inner, check_every, work, out, st);
-        case 8: return mx_run<8, V>(g, v64, vlo, diag, b, x, tol, max_outer, inner_tol, max_inner, check_every, work, out, st);
-        case 16: return mx_run<16, V>(g, v64, vlo, diag, b, x, tol, max_outer, inner_tol, max_inner, check_every, work, out, st);
-        default: return mx_run<32, V>(g, v64, vlo, diag, b, x, tol, max_outer, inner_tol, max_inner, check_every, work, out, st);
+        case 1: return mx_run<1, V>(g, v64, vlo, diag, b, x, tol, max_outer, inner_tol, max_inner, check_every, flags, work, out, st);
+        case 4: return mx_run<4, V>(g, v64, vlo, diag, b, x, tol, max_outer, inner_tol, max_inner, check_every, flags, work, out, st);
+        case 8: return mx_run<8, V>(g, v64, vlo, diag, b, x, tol, max_outer, inner_tol, max_inner, check_every, flags, work, out, st);
+        case 16: return mx_run<16, V>(g, v64, vlo, diag, b, x, tol, max_outer, inner_tol, max_inner, check_every, flags, work, out, st);
+        default: return mx_run<32, V>(g, v64, vlo, diag, b, x, tol, max_outer, inner_tol, max_inner, check_every, flags, work, out, st);
     }
 }
 
@@ -648,7 +680,7 @@ extern "C" int ens_cg_mixed_workspace_size(int32_t num_rows, int s, size_t *byte
 extern "C" int ens_cg_mixed(const ens_graph *graph, int s, const double *values,
                             const void *values_lo, int dtype_lo, const float *diag_lo,
                             const double *b, double *x, double tol, int max_outer,
-                            double inner_tol, int max_inner, int check_every, void *work,
+                            double inner_tol, int max_inner, int check_every, int flags, void *work,
                             size_t work_bytes, int32_t *outer_iters_host,
                             int32_t *inner_iters_host, double *relres_host,
                             int32_t *status_host, ens_cg_stats *stats_host, void *stream) {
@@ -671,7 +703,7 @@ extern "C" int ens_cg_mixed(const ens_graph *graph, int s, const double *values,
     cudaStream_t st = as_stream(stream);
     if (dtype_lo == ENS_F32)
         return mx_dispatch<float>(s, graph, values, values_lo, diag_lo, b, x, tol, max_outer, inner_tol,
-                                  max_inner, check_every, work, out, st);
+                                  max_inner, check_every, flags, work, out, st);
     return mx_dispatch<__nv_bfloat16>(s, graph, values, values_lo, diag_lo, b, x, tol, max_outer,
-                                      inner_tol, max_inner, check_every, work, out, st);
+                                      inner_tol, max_inner, check_every, flags, work, out, st);
 }
