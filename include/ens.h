@@ -211,6 +211,34 @@ int ens_cg(const ens_graph *graph, int s, const double *values, const double *b,
            int32_t *iters_host, double *relres_host, int32_t *status_host,
            ens_cg_stats *stats_host, void *stream);
 
+/* ---------------------------------------------------- A8 batched CG */
+/* One ensemble of a batch: its graph (by value), size s, values, rhs, x (in:
+ * x0, out: solution) and optional host outputs iters/relres/status [s]. */
+typedef struct ens_batch_item {
+    ens_graph graph;
+    int32_t s;
+    int32_t reserved;
+    const double *values;
+    const double *b;
+    double *x;
+    int32_t *iters_host;
+    double *relres_host;
+    int32_t *status_host;
+} ens_batch_item;
+
+/* Solves a batch of ensembles -- any mix of meshes and ensemble sizes -- with
+ * one launch per CG phase for the whole batch (a per-CTA work list maps CTAs
+ * to (ensemble, row tiles)); each ensemble follows exactly the arithmetic of
+ * ens_cg (same flags: ENS_CG_COUPLED, ENS_CG_DF64, ENS_CG_SPLIT64,
+ * ENS_CG_GRAPH replays check_every iterations of the batch as one CUDA
+ * graph, ENS_CG_TIME_SPMV).  Not in the paper (Sect. 5 leaves the grouping of
+ * samples to future work); it amortises launch latency over small meshes.
+ * work: ens_cg_batched_workspace_size bytes.  Synchronises `stream`. */
+int ens_cg_batched_workspace_size(int n_items, const ens_batch_item *items, size_t *bytes);
+int ens_cg_batched(int n_items, const ens_batch_item *items, double tol, int max_iter, int flags,
+                   int check_every, void *work, size_t work_bytes, ens_cg_stats *stats_host,
+                   void *stream);
+
 /* ------------------------------------------------- A7 mixed precision */
 /* Low-precision copy of ensemble values for the inner solver of ens_cg_mixed.
  *   dtype = ENS_F32 or ENS_BF16; values_lo: float[nnz*s] or bfloat16[nnz*s]

@@ -13,7 +13,7 @@ import threading
 
 __all__ = ["EnsError", "lib", "Graph", "Mesh", "mesh_sizes", "graph_build", "kl_table_size",
            "kl_setup", "mode_matrices", "assemble", "spmv", "dot", "dot_workspace_size", "dot_static", "cg",
-           "cg_workspace_size", "CgStats", "convert_values", "cg_mixed", "cg_mixed_workspace_size", "F64", "F32", "BF16", "CG_COUPLED", "CG_GRAPH",
+           "cg_workspace_size", "CgStats", "Batch", "convert_values", "cg_mixed", "cg_mixed_workspace_size", "F64", "F32", "BF16", "CG_COUPLED", "CG_GRAPH",
            "CG_TIME_SPMV", "CG_DF64", "CG_SPLIT64", "F64_DF", "F64_SPLIT"]
 
 F64, F32, BF16, F64_DF, F64_SPLIT = 0, 1, 2, 3, 4
@@ -35,6 +35,13 @@ class EnsGraphC(ctypes.Structure):
     _fields_ = [("num_rows", ctypes.c_int32), ("reserved", ctypes.c_int32),
                 ("num_entries", ctypes.c_int64), ("row_map", ctypes.c_void_p),
                 ("col_entry", ctypes.c_void_p)]
+
+
+class BatchItemC(ctypes.Structure):
+    _fields_ = [("graph", EnsGraphC), ("s", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("values", ctypes.c_void_p), ("b", ctypes.c_void_p), ("x", ctypes.c_void_p),
+                ("iters_host", ctypes.c_void_p), ("relres_host", ctypes.c_void_p),
+                ("status_host", ctypes.c_void_p)]
 
 
 class CgStats(ctypes.Structure):
@@ -87,6 +94,8 @@ def _declare(L):
         "ens_cg_workspace_size": (I, [i32, I, P(sz)]),
         "ens_cg": (I, [P(EnsGraphC), I, vp, vp, vp, d, I, I, I, vp, sz, vp, vp, vp, P(CgStats), vp]),
         "ens_convert_values": (I, [P(EnsGraphC), I, vp, I, vp, vp, vp]),
+        "ens_cg_batched_workspace_size": (I, [I, P(BatchItemC), P(sz)]),
+        "ens_cg_batched": (I, [I, P(BatchItemC), d, I, I, I, vp, sz, P(CgStats), vp]),
         "ens_cg_mixed_workspace_size": (I, [i32, I, P(sz)]),
         "ens_cg_mixed": (I, [P(EnsGraphC), I, vp, vp, I, vp, vp, vp, d, I, d, I, I, I, vp, sz, vp, vp,
                              vp, vp, P(CgStats), vp]),
@@ -242,6 +251,45 @@ def cg(graph, s, values, b, x, tol, max_iter, work, flags=0, check_every=8, stre
     if rc not in (0, ERR_NOT_CONVERGED, ERR_BREAKDOWN) or (rc and raise_on_failure):
         _check(rc)
     return list(it), list(rr), list(stt), stats
+
+
+# ------------------------------------------------------------- batched CG
+class Batch:
+    """A batch of ensembles (graph, s, values, b, x) solved by ens_cg_batched."""
+
+    def __init__(self, items):
+        """items: list of (graph, s, values, b, x) with device tensors."""
+        self.items = list(items)
+        n = len(self.items)
+        self.c = (BatchItemC * n)()
+        self.iters = [(ctypes.c_int32 * it[1])() for it in self.items]
+        self.relres = [(ctypes.c_double * it[1])() for it in self.items]
+        self.status = [(ctypes.c_int32 * it[1])() for it in self.items]
+        for i, (graph, s, values, b, x) in enumerate(self.items):
+            _require_cuda(values, b, x)
+            self.c[i].graph = graph.c
+            self.c[i].s = s
+            self.c[i].values, self.c[i].b, self.c[i].x = values.data_ptr(), b.data_ptr(), x.data_ptr()
+            self.c[i].iters_host = ctypes.cast(self.iters[i], ctypes.c_void_p)
+            self.c[i].relres_host = ctypes.cast(self.relres[i], ctypes.c_void_p)
+            self.c[i].status_host = ctypes.cast(self.status[i], ctypes.c_void_p)
+
+    def workspace_size(self):
+        v = ctypes.c_size_t()
+        _check(lib().ens_cg_batched_workspace_size(len(self.items), self.c, ctypes.byref(v)))
+        return v.value
+
+    def solve(self, tol, max_iter, work, flags=0, check_every=8, stream=None):
+        """Returns (iters, relres, status) lists per item, and CgStats."""
+        _require_cuda(work)
+        stats = CgStats()
+        rc = lib().ens_cg_batched(len(self.items), self.c, tol, max_iter, flags, check_every,
+                                  _ptr(work), work.numel() * work.element_size(), ctypes.byref(stats),
+                                  _stream(stream))
+        if rc not in (0, ERR_NOT_CONVERGED, ERR_BREAKDOWN):
+            _check(rc)
+        return ([list(a) for a in self.iters], [list(a) for a in self.relres],
+                [list(a) for a in self.status], stats)
 
 
 # --------------------------------------------------------- mixed precision

@@ -51,14 +51,16 @@ struct CgArgs {
     int coupled;
 };
 
-// mapping of the streaming vector kernels (K2, K3): a CTA owns CPC chunks
-template <int S>
+// mapping of the streaming vector kernels (K2, K3): a CTA of TH threads owns
+// CPC chunks, CPP of them at a time
+template <int S, int TH = (S == 32) ? 512 : 256>
 struct VecMap {
     static constexpr int VG = (S == 1) ? 1 : S / 2;            // threads per row
     static constexpr int CHUNK_T = 32 * VG;                    // threads per chunk
-    static constexpr int THREADS = (S == 32) ? 512 : 256;
+    static constexpr int THREADS = TH;
     static constexpr int CPP = THREADS / CHUNK_T;              // chunks per pass
-    static constexpr int CPC = (S >= 16) ? 4 : 8;              // chunks per CTA
+    static constexpr int CPC0 = (S >= 16) ? 4 : 8;
+    static constexpr int CPC = (CPC0 > CPP) ? CPC0 : CPP;      // chunks per CTA
     static constexpr int PASSES = CPC / CPP;
 };
 
@@ -166,6 +168,98 @@ __global__ void cg_zero_kernel(CgArgs a) {
 }
 
 // ------------------------------------------------------------------ K1
+// Body of the batched kernel: NSUB chunks of one ensemble per CTA, each on
+// its own thread group.  Its arithmetic is that of cg_spmv_kernel below (kept
+// as a separate copy because the shared form needs more registers there).
+template <int S, int NSUB>
+struct K1Smem {
+    double sm[NSUB][32][S + 1];
+    ChunkCols cc[NSUB];
+};
+
+template <int S, int MODE, int NSUB>
+__device__ __forceinline__ void k1_body(const CgArgs &a, const int cta, K1Smem<S, NSUB> &sh) {
+    CgState *st = a.st;
+    if (ld_cg(&st->active_count) == 0) {
+        if (cta == 0 && threadIdx.x == 0 && st->updx_any) {
+            for (int e = 0; e < S; ++e) st->updx[e] = 0;
+            st->updx_any = 0;
+        }
+        return;
+    }
+    constexpr int G = RowMap<S>::G, T = RowMap<S>::THREADS;
+    const int sub = (NSUB == 1) ? 0 : (int)threadIdx.x / T;
+    const int ltid = (NSUB == 1) ? (int)threadIdx.x : (int)threadIdx.x % T;
+    const int r = ltid / G, g = ltid % G;
+#define K1_CHUNK ((int64_t)cta * NSUB + sub)
+    const int64_t chunk = K1_CHUNK;
+    const bool valid = chunk * 32 + r < a.n;
+    // the split / double-float forms are used unless a vector element fell outside their range
+    const int mode = (MODE != 0 && ld_cg(&st->df_bad_any) != 0) ? 0 : MODE;
+    const bool staged = (NSUB == 1) ? stage_chunk(sh.cc[0], a.row_map, a.col, chunk, a.n)
+                                    : stage_chunk_sub(sh.cc[sub], a.row_map, a.col, chunk, a.n, ltid, T);
+    double2 apv;
+    if (MODE == 1 && mode == 1)
+        apv = chunk_spmv_df<S, XPre>(sh.cc[sub], staged, a.col, a.vals, a.pdf, r, g, valid);
+    else if (MODE == 2 && mode == 2)
+        apv = chunk_spmv_split<S, XPre>(sh.cc[sub], staged, a.col, a.vals, a.p, a.pdf, r, g, valid);
+    else
+        apv = chunk_spmv<S, double>(sh.cc[sub], staged, a.col, a.vals, a.p, r, g, valid);
+    double v0 = 0.0, v1 = 0.0;
+    const int64_t R = K1_CHUNK * 32 + r;
+    if constexpr (S == 1) {
+        if (valid) {
+            if (g == 0) a.q[R] = apv.x;
+            v0 = apv.x * a.p[R];
+        }
+    } else if (valid) {
+        reinterpret_cast<double2 *>(a.q)[R * G + g] = apv;
+        const double2 pv = reinterpret_cast<const double2 *>(a.p)[R * G + g];
+        v0 = apv.x * pv.x;
+        v1 = apv.y * pv.y;
+    }
+    if constexpr (NSUB == 1) chunk_tree<S>(sh.sm[0], v0, v1, r, g, a.t1, K1_CHUNK, 0);
+    else chunk_tree_sub<S>(sh.sm[sub], v0, v1, r, g, a.t1, K1_CHUNK, 0, ltid, T);
+    const int nitems = (NSUB == 1) ? 1 : (int)min((int64_t)NSUB, a.t1.count[1] - (int64_t)cta * NSUB);
+    if (!dot_tree_propagate(a.t1, (int64_t)cta * NSUB, nitems)) return;
+#undef K1_CHUNK
+    if (threadIdx.x >= 32) return;
+    // epilogue: one lane per member
+    const unsigned FULL = 0xffffffffu;
+    const int e = threadIdx.x;
+    const double *top = a.t1.buf[a.t1.levels];
+    const double pi = (e < S) ? ld_cg(top + e) : 0.0;
+    const double rho = (e < S) ? st->rho[e] : 0.0;
+    int act = (e < S) ? st->active[e] : 0;
+    if (a.coupled) {
+        double pis = 0.0, rhos = 0.0;
+        for (int k = 0; k < S; ++k) {
+            pis += __shfl_sync(FULL, pi, k);
+            rhos += __shfl_sync(FULL, rho, k);
+        }
+        const bool bad = !(pis > 0.0) || !isfinite(pis);
+        if (act) {
+            if (bad) { act = 0; st->status[e] = ENS_ERR_BREAKDOWN; }
+            else st->alpha[e] = rhos / pis;
+        }
+    } else if (act) {
+        if (!(pi > 0.0) || !isfinite(pi)) { act = 0; st->status[e] = ENS_ERR_BREAKDOWN; }
+        else st->alpha[e] = rho / pi;
+    }
+    if (e < S) {
+        st->active[e] = act;
+        st->updx[e] = 0;  // consumed by the previous K3
+    }
+    const int ac = __popc(__ballot_sync(FULL, act));
+    if (e == 0) {
+        st->spmv_real += 1;
+        st->updx_any = 0;
+        st->active_count = ac;
+    }
+    __threadfence();
+}
+
+// single-ensemble K1 (one chunk per CTA); same arithmetic as k1_body
 template <int S, int MODE>
 __global__ void __launch_bounds__(RowMap<S>::THREADS, 1536 / RowMap<S>::THREADS) cg_spmv_kernel(CgArgs a) {
     CgState *st = a.st;
@@ -243,10 +337,12 @@ __global__ void __launch_bounds__(RowMap<S>::THREADS, 1536 / RowMap<S>::THREADS)
     __threadfence();
 }
 
+
 // ------------------------------------------------------------------ K2
-template <int S>
-__global__ void __launch_bounds__(VecMap<S>::THREADS) cg_resid_kernel(CgArgs a) {
-    using VM = VecMap<S>;
+template <int S, int TH>
+__device__ __forceinline__ void k2_body(const CgArgs &a, int cta,
+                                        double (*sm)[32][S + 1] /* [CPC][32][S+1] */) {
+    using VM = VecMap<S, TH>;
     if (ld_cg(&a.st->active_count) == 0) return;
     constexpr int VG = VM::VG;
     const int cip = threadIdx.x / VM::CHUNK_T, lt = threadIdx.x % VM::CHUNK_T;
@@ -257,8 +353,7 @@ __global__ void __launch_bounds__(VecMap<S>::THREADS) cg_resid_kernel(CgArgs a) 
     const bool act1 = (S == 1) ? false : (bool)cs->active[m + 1];
     const double al0 = cs->alpha[m];
     const double al1 = (S == 1) ? 0.0 : cs->alpha[m + 1];
-    __shared__ double sm[VM::CPC][32][S + 1];   // per-row products of every chunk
-    const int64_t first_chunk = (int64_t)blockIdx.x * VM::CPC;
+    const int64_t first_chunk = (int64_t)cta * VM::CPC;
 #pragma unroll
     for (int pass = 0; pass < VM::PASSES; ++pass) {
         const int c = pass * VM::CPP + cip;
@@ -341,9 +436,9 @@ __global__ void __launch_bounds__(VecMap<S>::THREADS) cg_resid_kernel(CgArgs a) 
 }
 
 // ------------------------------------------------------------------ K3
-template <int S, int MODE>
-__global__ void __launch_bounds__(VecMap<S>::THREADS) cg_update_kernel(CgArgs a) {
-    using VM = VecMap<S>;
+template <int S, int MODE, int TH>
+__device__ __forceinline__ void k3_body(const CgArgs &a, int cta) {
+    using VM = VecMap<S, TH>;
     CgState *st = a.st;
     if (ld_cg(&st->updx_any) == 0) return;
     constexpr int VG = VM::VG;
@@ -355,7 +450,7 @@ __global__ void __launch_bounds__(VecMap<S>::THREADS) cg_update_kernel(CgArgs a)
     const bool ac1 = (S == 1) ? false : (bool)st->active[m + 1];
     const double al0 = st->alpha[m], be0 = st->beta[m];
     const double al1 = (S == 1) ? 0.0 : st->alpha[m + 1], be1 = (S == 1) ? 0.0 : st->beta[m + 1];
-    const int64_t first_chunk = (int64_t)blockIdx.x * VM::CPC;
+    const int64_t first_chunk = (int64_t)cta * VM::CPC;
 #pragma unroll 2
     for (int pass = 0; pass < VM::PASSES; ++pass) {
         const int64_t R = (first_chunk + pass * VM::CPP + cip) * 32 + r;
@@ -386,6 +481,17 @@ __global__ void __launch_bounds__(VecMap<S>::THREADS) cg_update_kernel(CgArgs a)
             }
         }
     }
+}
+
+template <int S>
+__global__ void __launch_bounds__(VecMap<S>::THREADS) cg_resid_kernel(CgArgs a) {
+    __shared__ double sm[VecMap<S>::CPC][32][S + 1];   // per-row products of every chunk
+    k2_body<S, VecMap<S>::THREADS>(a, blockIdx.x, sm);
+}
+
+template <int S, int MODE>
+__global__ void __launch_bounds__(VecMap<S>::THREADS) cg_update_kernel(CgArgs a) {
+    k3_body<S, MODE, VecMap<S>::THREADS>(a, blockIdx.x);
 }
 
 // ------------------------------------------------------------------ KF
@@ -609,6 +715,318 @@ static int cg_dispatch_df(const ens_graph *g, const double *vals, const double *
     return cg_run<S, 0>(g, vals, b, x, tol, max_iter, flags, check_every, work, out, st);
 }
 
+// ------------------------------------------------------------ batched
+// One launch per CG phase for a whole batch of ensembles (different meshes
+// and ensemble sizes): every CTA looks up its ensemble in a per-CTA table and
+// runs the same bodies as the single-ensemble kernels, with 512-thread CTAs
+// holding 512 / RowMap<s>::THREADS chunks (K1) or VecMap<s, 512>::CPC chunks
+// (K2, K3) of that ensemble.  Arithmetic is identical to ens_cg.
+constexpr int kBatchThreads = 512;
+
+template <int S>
+struct BatchK1 {
+    static constexpr int NSUB = kBatchThreads / RowMap<S>::THREADS;
+    using Smem = K1Smem<S, NSUB>;
+};
+
+constexpr size_t cmax(size_t a, size_t b) { return a > b ? a : b; }
+constexpr size_t kBatchK1Smem =
+    cmax(cmax(cmax(sizeof(BatchK1<1>::Smem), sizeof(BatchK1<4>::Smem)),
+              cmax(sizeof(BatchK1<8>::Smem), sizeof(BatchK1<16>::Smem))),
+         sizeof(BatchK1<32>::Smem));
+template <int S>
+constexpr size_t batch_k2_smem() { return sizeof(double) * VecMap<S, kBatchThreads>::CPC * 32 * (S + 1); }
+constexpr size_t kBatchK2Smem = cmax(cmax(cmax(batch_k2_smem<1>(), batch_k2_smem<4>()),
+                                          cmax(batch_k2_smem<8>(), batch_k2_smem<16>())),
+                                     batch_k2_smem<32>());
+
+struct BItem {
+    CgArgs a;
+    int S;
+    int k1_cta0, v_cta0;
+};
+
+struct BatchTables {
+    const BItem *items;
+    const int *k1_map;  // CTA -> item for K1 launches
+    const int *v_map;   // CTA -> item for K2 / K3 launches
+};
+
+template <int MODE>
+__global__ void __launch_bounds__(kBatchThreads, 2) cg_spmv_batched(BatchTables bt) {
+    __shared__ __align__(16) unsigned char raw[kBatchK1Smem];
+    const BItem &it = bt.items[__ldg(bt.k1_map + blockIdx.x)];
+    const int cta = blockIdx.x - it.k1_cta0;
+    switch (it.S) {
+        case 1: k1_body<1, MODE, BatchK1<1>::NSUB>(it.a, cta, *reinterpret_cast<BatchK1<1>::Smem *>(raw)); break;
+        case 4: k1_body<4, MODE, BatchK1<4>::NSUB>(it.a, cta, *reinterpret_cast<BatchK1<4>::Smem *>(raw)); break;
+        case 8: k1_body<8, MODE, BatchK1<8>::NSUB>(it.a, cta, *reinterpret_cast<BatchK1<8>::Smem *>(raw)); break;
+        case 16: k1_body<16, MODE, BatchK1<16>::NSUB>(it.a, cta, *reinterpret_cast<BatchK1<16>::Smem *>(raw)); break;
+        default: k1_body<32, MODE, BatchK1<32>::NSUB>(it.a, cta, *reinterpret_cast<BatchK1<32>::Smem *>(raw)); break;
+    }
+}
+
+template <int S>
+__device__ __forceinline__ void k2_batched_s(const CgArgs &a, int cta, unsigned char *raw) {
+    k2_body<S, kBatchThreads>(a, cta, reinterpret_cast<double(*)[32][S + 1]>(raw));
+}
+
+__global__ void __launch_bounds__(kBatchThreads) cg_resid_batched(BatchTables bt) {
+    __shared__ __align__(16) unsigned char raw[kBatchK2Smem];
+    const BItem &it = bt.items[__ldg(bt.v_map + blockIdx.x)];
+    const int cta = blockIdx.x - it.v_cta0;
+    switch (it.S) {
+        case 1: k2_batched_s<1>(it.a, cta, raw); break;
+        case 4: k2_batched_s<4>(it.a, cta, raw); break;
+        case 8: k2_batched_s<8>(it.a, cta, raw); break;
+        case 16: k2_batched_s<16>(it.a, cta, raw); break;
+        default: k2_batched_s<32>(it.a, cta, raw); break;
+    }
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(kBatchThreads) cg_update_batched(BatchTables bt) {
+    const BItem &it = bt.items[__ldg(bt.v_map + blockIdx.x)];
+    const int cta = blockIdx.x - it.v_cta0;
+    switch (it.S) {
+        case 1: k3_body<1, MODE, kBatchThreads>(it.a, cta); break;
+        case 4: k3_body<4, MODE, kBatchThreads>(it.a, cta); break;
+        case 8: k3_body<8, MODE, kBatchThreads>(it.a, cta); break;
+        case 16: k3_body<16, MODE, kBatchThreads>(it.a, cta); break;
+        default: k3_body<32, MODE, kBatchThreads>(it.a, cta); break;
+    }
+}
+
+// sums of the convergence words of all ensembles (one thread per ensemble)
+__global__ void batch_poll_kernel(const BItem *items, int n_items, int *out) {
+    __shared__ int s_act, s_upd;
+    if (threadIdx.x == 0) { s_act = 0; s_upd = 0; }
+    __syncthreads();
+    for (int i = threadIdx.x; i < n_items; i += blockDim.x) {
+        const CgState *st = items[i].a.st;
+        atomicAdd(&s_act, ld_cg(&st->active_count));
+        atomicAdd(&s_upd, ld_cg(&st->updx_any));
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) { out[0] = s_act; out[1] = s_upd; }
+}
+
+static void cg_layout_args(CgArgs &a, const ens_graph *g, int S, const double *vals,
+                           const double *b, double *x, double tol, int max_iter, int coupled,
+                           void *work) {
+    const int64_t n = g->num_rows;
+    char *w = static_cast<char *>(work);
+    a.n = g->num_rows;
+    a.row_map = g->row_map;
+    a.col = g->col_entry;
+    a.vals = vals;
+    a.b = b;
+    a.x = x;
+    a.st = reinterpret_cast<CgState *>(w);
+    w += align256(sizeof(CgState));
+    a.r = reinterpret_cast<double *>(w); w += align256(sizeof(double) * (size_t)n * S);
+    a.p = reinterpret_cast<double *>(w); w += align256(sizeof(double) * (size_t)n * S);
+    a.q = reinterpret_cast<double *>(w); w += align256(sizeof(double) * (size_t)n * S);
+    a.pdf = reinterpret_cast<float2 *>(w); w += align256(sizeof(double) * (size_t)n * S);
+    dot_tree_layout(&a.t1, n, S, w);
+    w += dot_tree_bytes(n, S);
+    dot_tree_layout(&a.t2, n, 2 * S, w);
+    a.tol = tol;
+    a.max_iter = max_iter;
+    a.coupled = coupled;
+}
+
+template <int MODE>
+static void launch_single(int which, int S, const CgArgs &a, cudaStream_t st) {
+    const unsigned grid = (unsigned)a.t1.count[1];
+#define ENS_ONE(SS)                                                        \
+    if (which == 0) CgKernels<SS, MODE>::init(a, grid, st);                \
+    else CgKernels<SS, MODE>::final_(a, grid, st);
+    switch (S) {
+        case 1: { ENS_ONE(1) break; }
+        case 4: { ENS_ONE(4) break; }
+        case 8: { ENS_ONE(8) break; }
+        case 16: { ENS_ONE(16) break; }
+        default: { ENS_ONE(32) break; }
+    }
+#undef ENS_ONE
+}
+
+static int64_t batch_k1_ctas(int S, int64_t chunks) {
+    const int nsub = kBatchThreads / (32 * ((S == 1) ? 2 : S / 2));
+    return (chunks + nsub - 1) / nsub;
+}
+static int64_t batch_v_ctas(int S, int64_t chunks) {
+    int cpc = 0;
+    switch (S) {
+        case 1: cpc = VecMap<1, kBatchThreads>::CPC; break;
+        case 4: cpc = VecMap<4, kBatchThreads>::CPC; break;
+        case 8: cpc = VecMap<8, kBatchThreads>::CPC; break;
+        case 16: cpc = VecMap<16, kBatchThreads>::CPC; break;
+        default: cpc = VecMap<32, kBatchThreads>::CPC; break;
+    }
+    return (chunks + cpc - 1) / cpc;
+}
+
+struct BatchPlan {
+    size_t head;           // items + poll words + CTA maps
+    int64_t k1_total, v_total;
+    size_t total;
+};
+
+static BatchPlan batch_plan(int n_items, const ens_batch_item *items) {
+    BatchPlan p{};
+    for (int i = 0; i < n_items; ++i) {
+        const int64_t chunks = ((int64_t)items[i].graph.num_rows + 31) / 32;
+        p.k1_total += batch_k1_ctas(items[i].s, chunks);
+        p.v_total += batch_v_ctas(items[i].s, chunks);
+    }
+    p.head = align256(sizeof(BItem) * n_items) + 256 + align256(sizeof(int) * (size_t)p.k1_total) +
+             align256(sizeof(int) * (size_t)p.v_total);
+    p.total = p.head;
+    for (int i = 0; i < n_items; ++i) p.total += cg_bytes(items[i].graph.num_rows, items[i].s);
+    return p;
+}
+
+template <int MODE>
+static int batched_run(int n_items, const ens_batch_item *items, double tol, int max_iter,
+                       int flags, int check_every, void *work, ens_cg_stats *stats,
+                       cudaStream_t st) {
+    const BatchPlan plan = batch_plan(n_items, items);
+    char *w = static_cast<char *>(work);
+    BItem *d_items = reinterpret_cast<BItem *>(w);
+    int *d_poll = reinterpret_cast<int *>(w + align256(sizeof(BItem) * n_items));
+    int *d_k1map = reinterpret_cast<int *>(w + align256(sizeof(BItem) * n_items) + 256);
+    int *d_vmap = d_k1map + align256(sizeof(int) * (size_t)plan.k1_total) / sizeof(int);
+    char *wi = w + plan.head;
+    std::vector<BItem> h(n_items);
+    std::vector<int> k1map((size_t)plan.k1_total), vmap((size_t)plan.v_total);
+    int64_t k1c = 0, vc = 0;
+    int rc;
+    for (int i = 0; i < n_items; ++i) {
+        const ens_batch_item &it = items[i];
+        cg_layout_args(h[i].a, &it.graph, it.s, it.values, it.b, it.x, tol, max_iter,
+                       (flags & ENS_CG_COUPLED) ? 1 : 0, wi);
+        wi += cg_bytes(it.graph.num_rows, it.s);
+        h[i].S = it.s;
+        const int64_t chunks = h[i].a.t1.count[1];
+        const int64_t nk = batch_k1_ctas(it.s, chunks), nv = batch_v_ctas(it.s, chunks);
+        h[i].k1_cta0 = (int)k1c;
+        h[i].v_cta0 = (int)vc;
+        for (int64_t c = 0; c < nk; ++c) k1map[k1c++] = i;
+        for (int64_t c = 0; c < nv; ++c) vmap[vc++] = i;
+        if ((rc = dot_tree_clear(h[i].a.t1, st))) return rc;
+        if ((rc = dot_tree_clear(h[i].a.t2, st))) return rc;
+        ENS_CUDA_TRY(cudaMemsetAsync(h[i].a.st, 0, sizeof(CgState), st));
+    }
+    ENS_CUDA_TRY(cudaMemcpyAsync(d_items, h.data(), sizeof(BItem) * n_items, cudaMemcpyHostToDevice, st));
+    ENS_CUDA_TRY(cudaMemcpyAsync(d_k1map, k1map.data(), sizeof(int) * k1map.size(), cudaMemcpyHostToDevice, st));
+    ENS_CUDA_TRY(cudaMemcpyAsync(d_vmap, vmap.data(), sizeof(int) * vmap.size(), cudaMemcpyHostToDevice, st));
+    int launches = 0, polls = 0;
+    for (int i = 0; i < n_items; ++i) { launch_single<MODE>(0, h[i].S, h[i].a, st); launches += 2; }
+    ENS_LAUNCH_CHECK("batched cg init");
+    const BatchTables bt{d_items, d_k1map, d_vmap};
+    const unsigned g1 = (unsigned)plan.k1_total, gv = (unsigned)plan.v_total;
+    const bool timing = (flags & ENS_CG_TIME_SPMV) != 0;
+    const bool use_graph = (flags & ENS_CG_GRAPH) != 0 && !timing;
+    std::vector<cudaEvent_t> ev;
+    std::vector<float> spmv_ms;
+    if (timing) {
+        ev.resize(2 * (size_t)check_every);
+        for (auto &e : ev) ENS_CUDA_TRY(cudaEventCreate(&e));
+    }
+    struct EvGuard {
+        std::vector<cudaEvent_t> &v;
+        ~EvGuard() { for (auto &e : v) cudaEventDestroy(e); }
+    } guard{ev};
+    auto iteration = [&](cudaStream_t s2, int i) {
+        if (timing) cudaEventRecord(ev[2 * i], s2);
+        cg_spmv_batched<MODE><<<g1, kBatchThreads, 0, s2>>>(bt);
+        if (timing) cudaEventRecord(ev[2 * i + 1], s2);
+        cg_resid_batched<<<gv, kBatchThreads, 0, s2>>>(bt);
+        cg_update_batched<MODE><<<gv, kBatchThreads, 0, s2>>>(bt);
+    };
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t gexec = nullptr;
+    if (use_graph) {
+        cudaStream_t cap;
+        ENS_CUDA_TRY(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
+        cudaError_t ce = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+        if (ce == cudaSuccess) {
+            for (int i = 0; i < check_every; ++i) iteration(cap, i);
+            batch_poll_kernel<<<1, 64, 0, cap>>>(d_items, n_items, d_poll);
+            ce = cudaStreamEndCapture(cap, &graph);
+        }
+        cudaStreamDestroy(cap);
+        if (ce != cudaSuccess) return cuda_fail(ce, "batched cg graph capture");
+        ce = cudaGraphInstantiate(&gexec, graph, 0);
+        if (ce != cudaSuccess) { cudaGraphDestroy(graph); return cuda_fail(ce, "cudaGraphInstantiate"); }
+    }
+    int32_t hp[2];
+    const int max_blocks = max_iter / check_every + 3;
+    rc = ENS_OK;
+    for (int blk = 0; blk < max_blocks; ++blk) {
+        if (use_graph) {
+            cudaError_t ce = cudaGraphLaunch(gexec, st);
+            if (ce != cudaSuccess) { rc = cuda_fail(ce, "cudaGraphLaunch"); break; }
+        } else {
+            for (int i = 0; i < check_every; ++i) iteration(st, i);
+            batch_poll_kernel<<<1, 64, 0, st>>>(d_items, n_items, d_poll);
+        }
+        launches += 3 * check_every + 1;
+        cudaError_t ce = cudaGetLastError();
+        if (ce == cudaSuccess) ce = cudaMemcpyAsync(hp, d_poll, sizeof(hp), cudaMemcpyDeviceToHost, st);
+        if (ce == cudaSuccess) ce = cudaStreamSynchronize(st);
+        if (ce != cudaSuccess) { rc = cuda_fail(ce, "batched cg iteration"); break; }
+        ++polls;
+        if (timing)
+            for (int i = 0; i < check_every; ++i) {
+                float ms = 0.f;
+                cudaEventElapsedTime(&ms, ev[2 * i], ev[2 * i + 1]);
+                spmv_ms.push_back(ms);
+            }
+        if (hp[0] == 0 && hp[1] == 0) break;
+    }
+    if (gexec) cudaGraphExecDestroy(gexec);
+    if (graph) cudaGraphDestroy(graph);
+    if (rc != ENS_OK) return rc;
+    for (int i = 0; i < n_items; ++i) { launch_single<MODE>(1, h[i].S, h[i].a, st); ++launches; }
+    ENS_LAUNCH_CHECK("batched cg final");
+    std::vector<CgState> hs(n_items);
+    for (int i = 0; i < n_items; ++i)
+        ENS_CUDA_TRY(cudaMemcpyAsync(&hs[i], h[i].a.st, sizeof(CgState), cudaMemcpyDeviceToHost, st));
+    ENS_CUDA_TRY(cudaStreamSynchronize(st));
+    int first_bad = ENS_OK, maxit = 0, real = 0;
+    for (int i = 0; i < n_items; ++i) {
+        const ens_batch_item &it = items[i];
+        for (int e = 0; e < it.s; ++e) {
+            if (it.iters_host) it.iters_host[e] = hs[i].iters[e];
+            if (it.relres_host) it.relres_host[e] = hs[i].relres[e];
+            if (it.status_host) it.status_host[e] = hs[i].status[e];
+            if (hs[i].status[e] != ENS_OK && first_bad == ENS_OK) first_bad = hs[i].status[e];
+            maxit = hs[i].iters[e] > maxit ? hs[i].iters[e] : maxit;
+        }
+        real = hs[i].spmv_real > real ? hs[i].spmv_real : real;
+    }
+    if (stats) {
+        stats->iterations = maxit;
+        stats->kernel_launches = launches;
+        stats->host_checks = polls;
+        stats->spmv_launches = 0;
+        stats->spmv_ms = 0.0;
+        if (timing) {
+            const int nreal = real < (int)spmv_ms.size() ? real : (int)spmv_ms.size();
+            double tot = 0.0;
+            for (int i = 0; i < nreal; ++i) tot += spmv_ms[i];
+            stats->spmv_launches = nreal;
+            stats->spmv_ms = tot;
+        }
+    }
+    if (first_bad != ENS_OK)
+        set_error("ens_cg_batched: member status %d (%s)", first_bad, ens_status_string(first_bad));
+    return first_bad;
+}
+
 }  // namespace ens
 
 using namespace ens;
@@ -645,4 +1063,45 @@ extern "C" int ens_cg(const ens_graph *graph, int s, const double *values, const
         case 16: return cg_dispatch_df<16>(graph, values, b, x, tol, max_iter, flags, check_every, work, out, st);
         default: return cg_dispatch_df<32>(graph, values, b, x, tol, max_iter, flags, check_every, work, out, st);
     }
+}
+
+static int check_batch(int n_items, const ens_batch_item *items) {
+    if (n_items < 1 || n_items > 4096) return fail(ENS_ERR_ARG, "n_items=%d outside [1, 4096]", n_items);
+    if (!items) return fail(ENS_ERR_ARG, "items is NULL");
+    for (int i = 0; i < n_items; ++i) {
+        int rc = check_graph(&items[i].graph);
+        if (rc) return rc;
+        if (!supported_s(items[i].s))
+            return fail(ENS_ERR_UNSUPPORTED, "item %d: ensemble size s=%d not in {1,4,8,16,32}", i, items[i].s);
+        if (items[i].graph.num_rows == 0) return fail(ENS_ERR_ARG, "item %d: empty graph", i);
+        if (!items[i].values || !items[i].b || !items[i].x)
+            return fail(ENS_ERR_ARG, "item %d: NULL values/b/x", i);
+        if (items[i].s > 1 && (!aligned16(items[i].values) || !aligned16(items[i].b) || !aligned16(items[i].x)))
+            return fail(ENS_ERR_ALIGN, "item %d: values/b/x must be 16-byte aligned", i);
+    }
+    return ENS_OK;
+}
+
+extern "C" int ens_cg_batched_workspace_size(int n_items, const ens_batch_item *items, size_t *bytes) {
+    int rc = check_batch(n_items, items);
+    if (rc) return rc;
+    if (!bytes) return fail(ENS_ERR_ARG, "bytes is NULL");
+    *bytes = batch_plan(n_items, items).total;
+    return ENS_OK;
+}
+
+extern "C" int ens_cg_batched(int n_items, const ens_batch_item *items, double tol, int max_iter,
+                              int flags, int check_every, void *work, size_t work_bytes,
+                              ens_cg_stats *stats_host, void *stream) {
+    int rc = check_batch(n_items, items);
+    if (rc) return rc;
+    if (!(tol >= 0.0) || max_iter < 0 || check_every < 1)
+        return fail(ENS_ERR_ARG, "tol=%g max_iter=%d check_every=%d", tol, max_iter, check_every);
+    if (!work || !aligned16(work)) return fail(ENS_ERR_ALIGN, "work must be a 16-byte aligned device pointer");
+    const size_t need = batch_plan(n_items, items).total;
+    if (work_bytes < need) return fail(ENS_ERR_WORKSPACE, "batched workspace %zu < %zu bytes", work_bytes, need);
+    cudaStream_t st = as_stream(stream);
+    if (flags & ENS_CG_SPLIT64) return batched_run<2>(n_items, items, tol, max_iter, flags, check_every, work, stats_host, st);
+    if (flags & ENS_CG_DF64) return batched_run<1>(n_items, items, tol, max_iter, flags, check_every, work, stats_host, st);
+    return batched_run<0>(n_items, items, tol, max_iter, flags, check_every, work, stats_host, st);
 }

@@ -112,6 +112,27 @@ __device__ __forceinline__ bool stage_chunk(ChunkCols &cc, const int32_t *__rest
     return staged;
 }
 
+// Subset form used when one CTA works on NSUB chunks at once (nthr threads
+// per chunk, ltid the thread's index inside its chunk): the same copy, with
+// chunks past the end of the matrix left empty.  All threads of the CTA call it.
+__device__ __forceinline__ bool stage_chunk_sub(ChunkCols &cc, const int32_t *__restrict__ row_map,
+                                                const int32_t *__restrict__ col, int64_t chunk,
+                                                int32_t n, int ltid, int nthr) {
+    const int64_t r0 = chunk * 32;
+    const int nr = (int)max((int64_t)0, min((int64_t)32, (int64_t)n - r0));
+    if (nr > 0)
+        for (int i = ltid; i <= nr; i += nthr) cc.rm[i] = __ldg(row_map + r0 + i);
+    else if (ltid == 0)
+        cc.rm[0] = 0;
+    __syncthreads();
+    const int e0 = cc.rm[0], cnt = (nr > 0) ? cc.rm[nr] - e0 : 0;
+    const bool staged = cnt <= kColCap;
+    if (staged)
+        for (int i = ltid; i < cnt; i += nthr) cc.col[i] = __ldg(col + e0 + i);
+    __syncthreads();
+    return staged;
+}
+
 // ------------------------------------------------------------ native FP64
 // y for members (2g, 2g+1) of a row with entries [rs, re), s >= 2
 template <int S, typename V, typename CA>
@@ -524,6 +545,33 @@ __device__ __forceinline__ void chunk_tree(double (*sm)[S + 1], double v0, doubl
     __syncthreads();
     halving_tree<S>(sm, blockDim.x);
     for (int e = threadIdx.x; e < S; e += blockDim.x) t.buf[1][chunk * t.width + off + e] = sm[0][e];
+    __syncthreads();
+}
+
+// Subset form of chunk_tree: the chunk's threads are [ltid = 0, nthr); all
+// threads of the CTA call it (its barriers are CTA-wide); writes only when
+// the chunk exists.
+template <int S>
+__device__ __forceinline__ void chunk_tree_sub(double (*sm)[S + 1], double v0, double v1, int r,
+                                               int g, const DotTree &t, int64_t chunk, int off,
+                                               int ltid, int nthr) {
+    if constexpr (S == 1) {
+        if (g == 0) sm[r][0] = v0;
+    } else {
+        sm[r][2 * g] = v0;
+        sm[r][2 * g + 1] = v1;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int h = 16; h >= 1; h >>= 1) {
+        for (int it = ltid; it < h * S; it += nthr) {
+            const int i = it / S, e = it % S;
+            sm[i][e] += sm[i + h][e];
+        }
+        __syncthreads();
+    }
+    if (chunk < t.count[1])
+        for (int e = ltid; e < S; e += nthr) t.buf[1][chunk * t.width + off + e] = sm[0][e];
     __syncthreads();
 }
 

@@ -1,0 +1,82 @@
+"""Batched CG (one launch per CG phase for a mix of meshes and ensemble sizes)
+against separate ens_cg solves of the same ensembles, and against the oracle.
+
+The batched kernels run the same per-chunk arithmetic as the single-ensemble
+kernels, so every member must come out bitwise identical."""
+import numpy as np
+import pytest
+
+import oracle as O
+import paper_1511_03703_gb300 as E
+from paper_1511_03703_gb300 import inputs
+from helpers import gpu, oracle_members, to_dev, to_np
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def torch():
+    import torch as T
+    assert T.cuda.is_available()
+    E.lib()
+    return T
+
+
+def make_items(torch, spec, seed=500):
+    items, meta = [], []
+    meshes = {}
+    for k, (N, s) in enumerate(spec):
+        mesh = meshes.setdefault(N, E.Mesh(N, 10))
+        xs = inputs.kl_samples(seed + k, 0, s, 10)
+        vals, b = mesh.assemble(s, to_dev(inputs.ensemble_layout(xs)))
+        x = torch.zeros(mesh.n * s, dtype=torch.float64, device=gpu())
+        items.append((mesh.graph, s, vals, b, x))
+        meta.append((mesh, xs))
+    return items, meta
+
+
+SPEC = [(5, 4), (9, 32), (7, 1), (12, 8), (9, 16), (5, 32), (3, 4)]
+
+
+@pytest.mark.parametrize("flags", [0, E.CG_SPLIT64, E.CG_DF64 | E.CG_GRAPH, E.CG_GRAPH])
+def test_batched_equals_separate_solves_bitwise(torch, flags):
+    items, meta = make_items(torch, SPEC)
+    batch = E.Batch(items)
+    work = torch.empty(batch.workspace_size(), dtype=torch.uint8, device=gpu())
+    it_b, rr_b, st_b, stats = batch.solve(1e-9, 2000, work, flags=flags, check_every=4)
+    assert stats.kernel_launches > 0
+    for i, (graph, s, vals, b, x) in enumerate(items):
+        assert st_b[i] == [0] * s
+        x2 = torch.zeros_like(x)
+        w2 = torch.empty(E.cg_workspace_size(graph.num_rows, s), dtype=torch.uint8, device=gpu())
+        it, rr, st, _ = E.cg(graph, s, vals, b, x2, 1e-9, 2000, w2, flags=flags & ~E.CG_GRAPH)
+        assert it == it_b[i] and rr == rr_b[i]
+        assert torch.equal(x, x2), i
+
+
+def test_batched_matches_oracle(torch):
+    items, meta = make_items(torch, [(6, 4), (10, 8)], seed=610)
+    batch = E.Batch(items)
+    work = torch.empty(batch.workspace_size(), dtype=torch.uint8, device=gpu())
+    it_b, rr_b, st_b, _ = batch.solve(1e-10, 2000, work, flags=E.CG_SPLIT64, check_every=8)
+    for i, (graph, s, vals, b, x) in enumerate(items):
+        mesh, xs = meta[i]
+        rm, col, ov, ob = oracle_members(mesh.N, 10, xs)
+        X = to_np(x).reshape(-1, s)
+        for e in range(s):
+            xo, ito, _, sto = O.cg(rm, col, ov[e], ob[e], tol=1e-12)
+            assert np.linalg.norm(X[:, e] - xo) <= 1e-8 * np.linalg.norm(xo)
+
+
+def test_batched_argument_errors(torch):
+    items, _ = make_items(torch, [(4, 4)])
+    graph, s, vals, b, x = items[0]
+    bad = E.Batch([(graph, 4, vals, b, x)])
+    small = torch.empty(16, dtype=torch.uint8, device=gpu())
+    with pytest.raises(E.EnsError) as ei:
+        bad.solve(1e-8, 10, small)
+    assert ei.value.code == 9
+    bad2 = E.Batch([(graph, 3, vals, b, x)])
+    with pytest.raises(E.EnsError) as ei:
+        bad2.workspace_size()
+    assert ei.value.code == 2
