@@ -579,6 +579,116 @@ def main_mixed(args):
     print(json.dumps(line))
 
 
+# ------------------------------------------------------- batched workload
+BAT_MESHES, BAT_WIDTHS, BAT_GROUP = (16, 32, 48, 64), (4, 8, 16, 32), 128
+BAT_WORKLOAD = ("KL diffusion, hex Q1 meshes 16^3, 32^3, 48^3, 64^3 x ensemble widths 4, 8, 16, 32, "
+                "128 samples per (mesh, width) group, 2048 samples, M=10, CG to 1e-8")
+
+
+def main_batched(args):
+    """16 groups of 128 samples solved (a) one ens_cg call per ensemble and
+    (b) one ens_cg_batched call for all 240 ensembles, with knobs from the
+    autotuner (SpMV form per (mesh, s); graph length for the batch)."""
+    import torch
+    import paper_1511_03703_gb300 as E
+    from paper_1511_03703_gb300 import autotune, inputs
+    dev = torch.device("cuda:0")
+    E.lib()
+    meshes = {N: E.Mesh(N, M_KL, device=dev) for N in BAT_MESHES}
+    items, groups = [], []
+    g = 0
+    for N in BAT_MESHES:
+        for s in BAT_WIDTHS:
+            xs = inputs.kl_samples(inputs.SEED_BATCHED, g * BAT_GROUP, BAT_GROUP, M_KL)
+            for k in range(BAT_GROUP // s):
+                xi = torch.from_numpy(inputs.ensemble_layout(xs[k * s:(k + 1) * s])).to(dev)
+                vals, b = meshes[N].assemble(s, xi)
+                x = torch.zeros(meshes[N].n * s, dtype=torch.float64, device=dev)
+                items.append({"N": N, "s": s, "xi": xi, "vals": vals, "b": b, "x": x, "group": g})
+            groups.append((N, s))
+            g += 1
+    t0 = time.perf_counter()
+    forms = {(N, s): autotune.best_form(meshes[N], s) for N in BAT_MESHES for s in BAT_WIDTHS}
+    works = {}
+    for it in items:
+        key = (it["N"], it["s"])
+        if key not in works:
+            works[key] = torch.empty(E.cg_workspace_size(meshes[it["N"]].n, it["s"]), dtype=torch.uint8, device=dev)
+    batch = E.Batch([(meshes[it["N"]].graph, it["s"], it["vals"], it["b"], it["x"]) for it in items])
+    bwork = torch.empty(batch.workspace_size(), dtype=torch.uint8, device=dev)
+    # batch-wide form: the one most groups chose, weighted by their bytes
+    votes = {}
+    for it in items:
+        f = forms[(it["N"], it["s"])]
+        votes[f] = votes.get(f, 0) + meshes[it["N"]].nnz * it["s"]
+    bform = max(votes, key=votes.get)
+    bflags = autotune.FORMS[bform]
+    ce = autotune.best_check_every(batch, bwork, bflags, tag="batched-16^3-64^3")
+    tune_s = time.perf_counter() - t0
+
+    def reassemble():
+        for N in BAT_MESHES:
+            mesh = meshes[N]
+            E.graph_build(N, mesh.row_map, mesh.col_entry, None, mesh.bmask)
+            E.kl_setup(N, M_KL, L_CORR, mesh.kl_table, want_host=False)
+            E.mode_matrices(N, mesh.graph, M_KL, mesh.kl_table, mesh.modes, mesh.load)
+        for it in items:
+            meshes[it["N"]].assemble(it["s"], it["xi"], values=it["vals"], b=it["b"])
+            it["x"].zero_()
+
+    def separate():
+        iters = []
+        for it in items:
+            mesh = meshes[it["N"]]
+            fl = autotune.FORMS[forms[(it["N"], it["s"])]]
+            i, r, st, _ = E.cg(mesh.graph, it["s"], it["vals"], it["b"], it["x"], TOL, 10000,
+                               works[(it["N"], it["s"])], flags=fl, check_every=16)
+            iters.append(i)
+        return iters
+
+    def batched():
+        i, r, st, stats = batch.solve(TOL, 10000, bwork, flags=bflags | E.CG_GRAPH, check_every=ce)
+        return i
+
+    def timed(fn):
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        reassemble()
+        res = fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / 1e3, res
+
+    total = len(items) and sum(it["s"] for it in items)
+    for _ in range(args.warmup):
+        timed(separate)
+        timed(batched)
+    ts = tb = 0.0
+    for _ in range(args.steps):
+        t, it_sep = timed(separate)
+        ts += t
+        t, it_bat = timed(batched)
+        tb += t
+    same = all(a == b for a, b in zip(it_sep, it_bat))
+    per_group = {}
+    for it, its in zip(items, it_bat):
+        per_group.setdefault(f"{it['N']}^3,s={it['s']}", []).extend(its)
+    line = {"metric": "batched ensemble CG sample-solves/s: one launch per CG phase vs separate launches",
+            "value": args.steps * total / tb, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64", "data": "synthetic",
+            "config": {"workload": BAT_WORKLOAD, "ensembles": len(items), "samples": total,
+                       "batch_spmv_form": bform, "graph_check_every": ce,
+                       "per_group_forms": {f"{N}^3,s={s}": forms[(N, s)] for (N, s) in groups},
+                       "tuning_seconds": tune_s, "step": "mesh set-up + assembly of every ensemble + solve"},
+            "separate_launches": {"value": args.steps * total / ts, "unit": UNIT},
+            "speedup_batched_vs_separate": ts / tb,
+            "iterations_identical": same,
+            "mean_iterations_per_group": {k: float(np.mean(v)) for k, v in per_group.items()}}
+    print(json.dumps(line))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -591,11 +701,15 @@ def main():
                          "or alternate entries on each (split)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--quick", action="store_true", help="skip the other-form run and the s sweep")
-    ap.add_argument("--workload", default="scale", choices=["scale", "mixed"],
-                    help="scale: 64^3 ensemble CG (default line); mixed: 128^3 mixed precision")
+    ap.add_argument("--workload", default="scale", choices=["scale", "mixed", "batched"],
+                    help="scale: 64^3 ensemble CG (default line); mixed: 128^3 mixed precision; "
+                         "batched: 16^3..64^3 x s=4..32 in one batch")
     args = ap.parse_args()
     if args.workload == "mixed" and args.impl != "reference":
         main_mixed(args)
+        return
+    if args.workload == "batched" and args.impl != "reference":
+        main_batched(args)
         return
     if args.impl == "reference":
         main_reference(args)

@@ -1,0 +1,135 @@
+"""Autotuner for the ensemble CG launch knobs.
+
+Knobs, all exposed through the C ABI:
+  - SpMV arithmetic form per (mesh, s): native FP64 FMA, double-float on the
+    FP32 pipe, or alternate entries on each (ENS_CG_DF64 / ENS_CG_SPLIT64);
+    GB300's 1/64-rate FP64 makes the best form depend on s and mesh size;
+  - graph length (check_every): iterations replayed per CUDA graph launch
+    between host polls of the convergence word;
+  - ensemble width s for a group of samples on one mesh (when the caller
+    leaves it free): the width with the most member-iterations per second.
+Each candidate is timed on the device (CUDA events around the CG SpMV
+launches, or wall time of a fixed-iteration solve), and the winners are
+cached in a JSON file keyed by GPU name and problem shape
+(ENS_AUTOTUNE_CACHE, default ~/.cache/ens_autotune.json).
+"""
+import json
+import os
+import time
+
+import paper_1511_03703_gb300 as E
+
+FORMS = {"f64": 0, "df": E.CG_DF64, "split": E.CG_SPLIT64}
+CHECK_EVERY = (4, 8, 16, 32)
+WIDTHS = (4, 8, 16, 32)
+
+
+def cache_path():
+    return os.environ.get("ENS_AUTOTUNE_CACHE",
+                          os.path.join(os.path.expanduser("~"), ".cache", "ens_autotune.json"))
+
+
+def _load():
+    try:
+        with open(cache_path()) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return {}
+
+
+def _store(db):
+    path = cache_path()
+    try:
+        os.makedirs(os.path.dirname(path), exist_ok=True)
+        tmp = path + f".tmp{os.getpid()}"
+        with open(tmp, "w") as f:
+            json.dump(db, f, indent=1, sort_keys=True)
+        os.replace(tmp, path)
+    except OSError:
+        pass  # a read-only home: tuning still works, it is just not remembered
+
+
+def _key(*parts):
+    import torch
+    return "|".join([torch.cuda.get_device_name()] + [str(p) for p in parts])
+
+
+def _ensemble(mesh, s, seed=1004):
+    import torch
+    from paper_1511_03703_gb300 import inputs
+    xs = inputs.kl_samples(seed, 0, s, mesh.M)
+    dev = mesh.row_map.device
+    vals, b = mesh.assemble(s, torch.from_numpy(inputs.ensemble_layout(xs)).to(dev))
+    return vals, b
+
+
+def time_spmv_forms(mesh, s, iters=24, vals=None, b=None):
+    """Mean CG SpMV launch time (ms) of each arithmetic form on one ensemble."""
+    import torch
+    if vals is None:
+        vals, b = _ensemble(mesh, s)
+    dev = vals.device
+    work = torch.empty(E.cg_workspace_size(mesh.n, s), dtype=torch.uint8, device=dev)
+    out = {}
+    for name, fl in FORMS.items():
+        x = torch.zeros(mesh.n * s, dtype=torch.float64, device=dev)
+        E.cg(mesh.graph, s, vals, b, x, 0.0, 4, work, flags=fl, check_every=4)
+        x.zero_()
+        _, _, _, st = E.cg(mesh.graph, s, vals, b, x, 0.0, iters, work,
+                           flags=fl | E.CG_TIME_SPMV, check_every=iters)
+        out[name] = st.spmv_ms / max(st.spmv_launches, 1)
+    return out
+
+
+def best_form(mesh, s, refresh=False):
+    """Fastest SpMV form for (mesh, s), cached."""
+    db = _load()
+    k = _key("form", mesh.N, mesh.M, s)
+    if not refresh and k in db:
+        return db[k]["form"]
+    t = time_spmv_forms(mesh, s)
+    form = min(t, key=t.get)
+    db[k] = {"form": form, "spmv_ms": t}
+    _store(db)
+    return form
+
+
+def best_check_every(batch, work, flags, iters=64, refresh=False, tag=""):
+    """Graph length with the least wall time for `iters` iterations of a batch
+    (tolerance 0: every candidate does the same work)."""
+    import torch
+    db = _load()
+    k = _key("check_every", tag, flags)
+    if not refresh and k in db:
+        return db[k]["check_every"]
+    res = {}
+    for ce in CHECK_EVERY:
+        batch.solve(0.0, ce, work, flags=flags | E.CG_GRAPH, check_every=ce)  # warm-up, capture
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        batch.solve(0.0, iters, work, flags=flags | E.CG_GRAPH, check_every=ce)
+        torch.cuda.synchronize()
+        res[ce] = time.perf_counter() - t0
+    best = min(res, key=res.get)
+    db[k] = {"check_every": best, "seconds": {str(c): v for c, v in res.items()}}
+    _store(db)
+    return best
+
+
+def best_width(mesh, refresh=False):
+    """Ensemble width with the most member-iterations per second of CG SpMV
+    (each width at its own fastest form), for groups whose width is free."""
+    db = _load()
+    k = _key("width", mesh.N, mesh.M)
+    if not refresh and k in db:
+        return db[k]["width"], db[k]["form"]
+    rates = {}
+    for s in WIDTHS:
+        t = time_spmv_forms(mesh, s)
+        f = min(t, key=t.get)
+        rates[s] = (s / t[f], f)
+    s_best = max(rates, key=lambda v: rates[v][0])
+    db[k] = {"width": s_best, "form": rates[s_best][1],
+             "member_spmv_per_ms": {str(s): r for s, (r, _) in rates.items()}}
+    _store(db)
+    return s_best, rates[s_best][1]

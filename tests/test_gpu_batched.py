@@ -80,3 +80,21 @@ def test_batched_argument_errors(torch):
     with pytest.raises(E.EnsError) as ei:
         bad2.workspace_size()
     assert ei.value.code == 2
+
+
+def test_autotuner_picks_and_caches(torch, tmp_path, monkeypatch):
+    from paper_1511_03703_gb300 import autotune
+    monkeypatch.setenv("ENS_AUTOTUNE_CACHE", str(tmp_path / "tune.json"))
+    mesh = E.Mesh(12, 10)
+    form = autotune.best_form(mesh, 8)
+    assert form in autotune.FORMS
+    assert autotune.best_form(mesh, 8) == form          # served from the cache
+    import json
+    db = json.loads((tmp_path / "tune.json").read_text())
+    assert any(k.endswith("|form|12|10|8") for k in db)
+    s, f = autotune.best_width(mesh)
+    assert s in autotune.WIDTHS and f in autotune.FORMS
+    items, _ = make_items(torch, [(6, 4), (8, 8)])
+    batch = E.Batch(items)
+    work = torch.empty(batch.workspace_size(), dtype=torch.uint8, device=gpu())
+    assert autotune.best_check_every(batch, work, 0, iters=16, tag="t") in autotune.CHECK_EVERY
