@@ -70,3 +70,20 @@ SEED_MIXED = 1003        # 128^3 mesh, M = 10, 256 samples
 SEED_BATCHED = 1004      # 16^3 .. 64^3 meshes, 2048 samples
 SEED_GUESS_TRAIN = 2005  # learned initial guess: training samples
 SEED_GUESS_TEST = 3005   # learned initial guess: fresh test samples
+
+# stream offsets of the learned-guess draws: far beyond every KL element
+# 64*j + k + 1 used by any workload, so the streams never overlap
+MLP_INIT_OFFSET = 1 << 40
+POD_TEST_OFFSET = 1 << 41
+
+
+def mlp_init_draws(seed, count):
+    """count uniform draws in [-1, 1) for the MLP's initial parameters,
+    rounded to float32 (the network's precision); both the CUDA path and the
+    oracle scale the same draws."""
+    return random_vector(seed, count, -1.0, 1.0, MLP_INIT_OFFSET).astype(np.float32)
+
+
+def pod_test_matrix(seed, m, l):
+    """m x l uniform draws in [-1, 1): the random test matrix of the POD range finder."""
+    return random_vector(seed, m * l, -1.0, 1.0, POD_TEST_OFFSET).reshape(m, l)
