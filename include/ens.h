@@ -180,6 +180,8 @@ typedef struct ens_cg_stats {
     int32_t kernel_launches; /* all kernels launched by the call */
     int32_t iterations;      /* iterations run (max over members) */
     int32_t host_checks;     /* device->host convergence polls */
+    int32_t guess_fallbacks; /* members restarted from x = 0 (ENS_CG_GUESS_FALLBACK) */
+    int32_t reserved;        /* zero */
 } ens_cg_stats;
 
 enum {
@@ -190,8 +192,13 @@ enum {
     ENS_CG_DF64 = 8,         /* CG SpMV in double-float arithmetic (see ENS_F64_DF);
                                 p is kept split as float pairs, all other vector
                                 arithmetic and every dot stays FP64 */
-    ENS_CG_SPLIT64 = 16      /* CG SpMV with alternate entries FP64 FMA / double-float
+    ENS_CG_SPLIT64 = 16,     /* CG SpMV with alternate entries FP64 FMA / double-float
                                 (see ENS_F64_SPLIT); takes precedence over ENS_CG_DF64 */
+    ENS_CG_GUESS_FALLBACK = 32 /* zero-guess fallback for a supplied start x0 (a learned
+                                guess, not in the paper): a member whose ||b - A x0||
+                                is not below ||b|| (or is not finite) restarts from
+                                x = 0, so its iterates are exactly those of a zero-guess
+                                solve; counted in ens_cg_stats.guess_fallbacks */
 };
 
 /* Unpreconditioned CG (Hestenes-Stiefel) on each member of the ensemble
@@ -273,6 +280,99 @@ int ens_cg_mixed(const ens_graph *graph, int s, const double *values, const void
                  size_t work_bytes, int32_t *outer_iters_host, int32_t *inner_iters_host,
                  double *relres_host, int32_t *status_host, ens_cg_stats *stats_host,
                  void *stream);
+
+/* ----------------------------------------- A9 learned initial guess */
+/* Not in the paper (its CG starts from x = 0, Sect. 4).  A reduced basis of
+ * solutions (POD) and a small MLP map the KL variables xi of a sample to a
+ * start x0 for ens_cg (with ENS_CG_GUESS_FALLBACK the zero guess stays the
+ * fallback, and CG always runs to the same ||r|| <= tol ||b||).
+ *
+ * Snapshots: X is row-major n x m with leading dimension ldx >= m (column j =
+ * solution of sample j).  ens_snapshots_put copies an ensemble solution x
+ * (n x s, commuted layout, Eq. 3) into columns col0 .. col0+s-1 of X
+ * (device pointers; ENS_ERR_ARG if ldx < col0 + s). */
+int ens_snapshots_put(int64_t n, int32_t s, const double *x, double *X, int64_t ldx, int64_t col0,
+                      void *stream);
+
+/* POD basis: centres X in place (mean[n] = row means, X -= mean), then the
+ * k leading left singular vectors of the centred X by a randomized range
+ * finder with power_iters stabilised power iterations (Halko, Martinsson and
+ * Tropp, SIAM Review 53 (2011), Algorithms 4.1 and 4.4) and a Rayleigh-Ritz
+ * step: Y = X Omega, Q = orth(Y); q times {Z = orth(X^T Q), Q = orth(X Z)};
+ * eigen-decomposition of (X^T Q)^T (X^T Q) by cyclic Jacobi; Phi = Q W_k.
+ * orth is shifted CholeskyQR3 (Fukaya et al., SIAM J. Sci. Comput. 42 (2020)).
+ *   Omega: m x l row-major test matrix (device; drawn by the caller),
+ *          1 <= k <= l <= min(80, m - 1), l <= n, 0 <= power_iters <= 8;
+ *   Phi: n x k row-major (device), column i scaled to unit 2-norm and signed
+ *        so that its largest-magnitude entry (first on ties) is positive;
+ *   sigma: k singular-value estimates (device), descending.
+ * All arithmetic FP64.  Returns ENS_ERR_BREAKDOWN if a Gram matrix is not
+ * positive definite (centred snapshots of numerical rank below l).
+ * Synchronises `stream`. */
+int ens_pod_workspace_size(int64_t n, int32_t m, int32_t l, size_t *bytes);
+int ens_pod(int64_t n, int32_t m, double *X, int64_t ldx, int32_t k, int32_t l, const double *Omega,
+            int32_t power_iters, double *mean, double *Phi, double *sigma, void *work, size_t work_bytes,
+            void *stream);
+
+/* Training targets: coefficients C = X^T Phi (m x k) of the centred
+ * snapshots, coef_mean[k] and coef_scale[k] = per-column mean and population
+ * standard deviation (1 where it is 0), T = (C - coef_mean) / coef_scale as
+ * float[m x k] row-major.  FP64 except the final rounding of T. */
+int ens_pod_targets_workspace_size(int64_t n, int32_t m, int32_t k, size_t *bytes);
+int ens_pod_targets(int64_t n, int32_t m, const double *X, int64_t ldx, int32_t k, const double *Phi,
+                    double *coef_mean, double *coef_scale, float *T, void *work, size_t work_bytes,
+                    void *stream);
+
+/* dst[i] = (float)src[i] (round to nearest), e.g. the FP32 copy of Phi. */
+int ens_to_f32(int64_t count, const double *src, float *dst, void *stream);
+
+/* MLP d0 -> d1 -> d2 -> d3 (dims[4], host array, each 1..4096): three affine
+ * layers, the exact GELU g(z) = z (1 + erf(z / sqrt 2)) / 2 after the first
+ * two, FP32.  Parameters: one float vector in the order W1 [d1 x d0], b1
+ * [d1], W2 [d2 x d1], b2 [d2], W3 [d3 x d2], b3 [d3] (row-major, W_l maps
+ * layer l-1 to layer l: z = W a + b).  Inputs xin [batch x d0], outputs and
+ * targets [batch x d3], row-major float (device).
+ * ens_mlp_init: He-uniform start from uniform draws u[count] in [-1, 1]:
+ * W_l = u sqrt(6 / fan_in), b_l = 0. */
+int ens_mlp_param_count(const int32_t *dims, int64_t *count);
+int ens_mlp_init(const int32_t *dims, const float *u, float *params, void *stream);
+int ens_mlp_workspace_size(const int32_t *dims, int32_t batch, size_t *bytes);
+int ens_mlp_forward(const int32_t *dims, const float *params, int32_t batch, const float *xin, float *y,
+                    void *work, size_t work_bytes, void *stream);
+/* Gradient of the mean squared error L = sum (y - target)^2 / (batch d3)
+ * with respect to the parameters (grad: float[count], device; loss: device
+ * float or NULL).  FP32 with sums in a fixed order (deterministic). */
+int ens_mlp_grad(const int32_t *dims, const float *params, int32_t batch, const float *xin, const float *target,
+                 float *grad, float *loss, void *work, size_t work_bytes, void *stream);
+/* One Adam step (Kingma and Ba, ICLR 2015) on P parameters: with t = step[0],
+ * m = b1 m + (1 - b1) g, v = b2 v + (1 - b2) g^2,
+ * w -= lr_t (m / (1 - b1^(t+1))) / (sqrt(v / (1 - b2^(t+1))) + eps),
+ * lr_t = lr0 (1 + cos(pi t / total_steps)) / 2; then step[0] = t + 1.
+ * step: device int64[2]; step[1] is scratch that must be 0 before the first
+ * call (every call leaves it 0). */
+int ens_mlp_adam(int64_t P, float *params, const float *grad, float *m, float *v, int64_t *step,
+                 int64_t total_steps, float lr0, float beta1, float beta2, float eps, void *stream);
+/* `epochs` passes over n_samples (a positive multiple of batch) in fixed
+ * consecutive mini-batches, each an ens_mlp_grad + ens_mlp_adam step on
+ * params, m, v, step (as above; step[0] must be a multiple of
+ * n_samples / batch).  epoch_loss (device float[epochs] or NULL) receives
+ * each epoch's mean batch loss.  use_graph != 0 captures one epoch as a CUDA
+ * graph and replays it.  work: ens_mlp_workspace_size(dims, batch). */
+int ens_mlp_train(const int32_t *dims, float *params, float *m, float *v, int64_t *step, int64_t n_samples,
+                  const float *xin, const float *target, int32_t batch, int32_t epochs, int64_t total_steps,
+                  float lr0, float beta1, float beta2, float eps, float *epoch_loss, int32_t use_graph,
+                  void *work, size_t work_bytes, void *stream);
+
+/* Learned start of one ensemble: for each member e (s <= 32),
+ *   chat_e = MLP(xi_e) with xi_e[k] = xi[k*s + e] (the ens_assemble input,
+ *            k < dims[0], rounded to float),
+ *   x0[i*s + e] = mean[i] + sum_k Phi32[i][k] (coef_mean[k] + coef_scale[k] chat_e[k]),
+ * the sum over k = dims[3] <= 256 in FP32, mean added in FP64.  Phi32: float
+ * n x dims[3] row-major.  Synchronises nothing. */
+int ens_guess_workspace_size(const int32_t *dims, int32_t s, size_t *bytes);
+int ens_guess(const int32_t *dims, const float *params, int64_t n, int32_t s, const double *xi,
+              const double *mean, const float *Phi32, const double *coef_mean, const double *coef_scale,
+              double *x0, void *work, size_t work_bytes, void *stream);
 
 #ifdef __cplusplus
 }

@@ -14,10 +14,14 @@ import threading
 __all__ = ["EnsError", "lib", "Graph", "Mesh", "mesh_sizes", "graph_build", "kl_table_size",
            "kl_setup", "mode_matrices", "assemble", "spmv", "dot", "dot_workspace_size", "dot_static", "cg",
            "cg_workspace_size", "CgStats", "Batch", "convert_values", "cg_mixed", "cg_mixed_workspace_size", "F64", "F32", "BF16", "CG_COUPLED", "CG_GRAPH",
-           "CG_TIME_SPMV", "CG_DF64", "CG_SPLIT64", "F64_DF", "F64_SPLIT"]
+           "CG_TIME_SPMV", "CG_DF64", "CG_SPLIT64", "CG_GUESS_FALLBACK", "F64_DF", "F64_SPLIT",
+           "snapshots_put", "pod", "pod_workspace_size", "pod_targets", "to_f32", "mlp_param_count",
+           "mlp_init", "mlp_workspace_size", "mlp_forward", "mlp_grad", "mlp_adam", "mlp_train",
+           "guess", "guess_workspace_size", "MLP_DIMS"]
 
 F64, F32, BF16, F64_DF, F64_SPLIT = 0, 1, 2, 3, 4
-CG_COUPLED, CG_GRAPH, CG_TIME_SPMV, CG_DF64, CG_SPLIT64 = 1, 2, 4, 8, 16
+CG_COUPLED, CG_GRAPH, CG_TIME_SPMV, CG_DF64, CG_SPLIT64, CG_GUESS_FALLBACK = 1, 2, 4, 8, 16, 32
+MLP_DIMS = (10, 256, 256, 64)
 OK, ERR_NOT_CONVERGED, ERR_BREAKDOWN = 0, 5, 6
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -47,7 +51,8 @@ class BatchItemC(ctypes.Structure):
 class CgStats(ctypes.Structure):
     _fields_ = [("spmv_ms", ctypes.c_double), ("spmv_launches", ctypes.c_int32),
                 ("kernel_launches", ctypes.c_int32), ("iterations", ctypes.c_int32),
-                ("host_checks", ctypes.c_int32)]
+                ("host_checks", ctypes.c_int32), ("guess_fallbacks", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -99,6 +104,23 @@ def _declare(L):
         "ens_cg_mixed_workspace_size": (I, [i32, I, P(sz)]),
         "ens_cg_mixed": (I, [P(EnsGraphC), I, vp, vp, I, vp, vp, vp, d, I, d, I, I, I, vp, sz, vp, vp,
                              vp, vp, P(CgStats), vp]),
+        "ens_snapshots_put": (I, [i64, i32, vp, vp, i64, i64, vp]),
+        "ens_pod_workspace_size": (I, [i64, i32, i32, P(sz)]),
+        "ens_pod": (I, [i64, i32, vp, i64, i32, i32, vp, i32, vp, vp, vp, vp, sz, vp]),
+        "ens_pod_targets_workspace_size": (I, [i64, i32, i32, P(sz)]),
+        "ens_pod_targets": (I, [i64, i32, vp, i64, i32, vp, vp, vp, vp, vp, sz, vp]),
+        "ens_to_f32": (I, [i64, vp, vp, vp]),
+        "ens_mlp_param_count": (I, [P(i32), P(i64)]),
+        "ens_mlp_init": (I, [P(i32), vp, vp, vp]),
+        "ens_mlp_workspace_size": (I, [P(i32), i32, P(sz)]),
+        "ens_mlp_forward": (I, [P(i32), vp, i32, vp, vp, vp, sz, vp]),
+        "ens_mlp_grad": (I, [P(i32), vp, i32, vp, vp, vp, vp, vp, sz, vp]),
+        "ens_mlp_adam": (I, [i64, vp, vp, vp, vp, vp, i64, ctypes.c_float, ctypes.c_float, ctypes.c_float,
+                             ctypes.c_float, vp]),
+        "ens_mlp_train": (I, [P(i32), vp, vp, vp, vp, i64, vp, vp, i32, i32, i64, ctypes.c_float,
+                              ctypes.c_float, ctypes.c_float, ctypes.c_float, vp, i32, vp, sz, vp]),
+        "ens_guess_workspace_size": (I, [P(i32), i32, P(sz)]),
+        "ens_guess": (I, [P(i32), vp, i64, i32, vp, vp, vp, vp, vp, vp, vp, sz, vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -326,6 +348,117 @@ def cg_mixed(graph, s, values, values_lo, b, x, tol, work, diag_lo=None, max_out
     if rc not in (0, ERR_NOT_CONVERGED, ERR_BREAKDOWN):
         _check(rc)
     return list(oi), list(ii), list(rr), list(stt), stats
+
+
+# ------------------------------------------------- learned initial guess
+def _nbytes(t):
+    return t.numel() * t.element_size()
+
+
+def _dims(dims):
+    return (ctypes.c_int32 * 4)(*dims)
+
+
+def snapshots_put(x, X, col0, s, stream=None):
+    """Copy ensemble solution x (n*s, commuted layout) into columns col0.. of X (n x m)."""
+    _require_cuda(x, X)
+    n, ldx = X.shape
+    _check(lib().ens_snapshots_put(n, s, _ptr(x), _ptr(X), ldx, col0, _stream(stream)))
+
+
+def pod_workspace_size(n, m, l):
+    v = ctypes.c_size_t()
+    _check(lib().ens_pod_workspace_size(n, m, l, ctypes.byref(v)))
+    return v.value
+
+
+def pod(X, k, l, Omega, mean, Phi, sigma, work, power_iters=1, m=None, stream=None):
+    """POD basis of the snapshot columns of X (centred in place); synchronises."""
+    _require_cuda(X, Omega, mean, Phi, sigma, work)
+    n, ldx = X.shape
+    m = ldx if m is None else m
+    _check(lib().ens_pod(n, m, _ptr(X), ldx, k, l, _ptr(Omega), power_iters, _ptr(mean), _ptr(Phi),
+                         _ptr(sigma), _ptr(work), _nbytes(work), _stream(stream)))
+
+
+def pod_targets(X, Phi, coef_mean, coef_scale, T, work=None, m=None, stream=None):
+    """Standardised coefficients T (float32 m x k) of the centred snapshots X."""
+    import torch
+    _require_cuda(X, Phi, coef_mean, coef_scale, T)
+    n, ldx = X.shape
+    m = ldx if m is None else m
+    k = Phi.shape[1]
+    if work is None:
+        v = ctypes.c_size_t()
+        _check(lib().ens_pod_targets_workspace_size(n, m, k, ctypes.byref(v)))
+        work = torch.empty(v.value, dtype=torch.uint8, device=X.device)
+    _check(lib().ens_pod_targets(n, m, _ptr(X), ldx, k, _ptr(Phi), _ptr(coef_mean), _ptr(coef_scale),
+                                 _ptr(T), _ptr(work), _nbytes(work), _stream(stream)))
+
+
+def to_f32(src, dst, stream=None):
+    _require_cuda(src, dst)
+    _check(lib().ens_to_f32(src.numel(), _ptr(src), _ptr(dst), _stream(stream)))
+
+
+def mlp_param_count(dims=MLP_DIMS):
+    v = ctypes.c_int64()
+    _check(lib().ens_mlp_param_count(_dims(dims), ctypes.byref(v)))
+    return v.value
+
+
+def mlp_init(u, params, dims=MLP_DIMS, stream=None):
+    _require_cuda(u, params)
+    _check(lib().ens_mlp_init(_dims(dims), _ptr(u), _ptr(params), _stream(stream)))
+
+
+def mlp_workspace_size(batch, dims=MLP_DIMS):
+    v = ctypes.c_size_t()
+    _check(lib().ens_mlp_workspace_size(_dims(dims), batch, ctypes.byref(v)))
+    return v.value
+
+
+def mlp_forward(params, xin, y, work, dims=MLP_DIMS, stream=None):
+    _require_cuda(params, xin, y, work)
+    _check(lib().ens_mlp_forward(_dims(dims), _ptr(params), xin.shape[0], _ptr(xin), _ptr(y), _ptr(work),
+                                 _nbytes(work), _stream(stream)))
+
+
+def mlp_grad(params, xin, target, grad, work, loss=None, dims=MLP_DIMS, stream=None):
+    _require_cuda(params, xin, target, grad, work, loss)
+    _check(lib().ens_mlp_grad(_dims(dims), _ptr(params), xin.shape[0], _ptr(xin), _ptr(target), _ptr(grad),
+                              _ptr(loss), _ptr(work), _nbytes(work), _stream(stream)))
+
+
+def mlp_adam(params, grad, m, v, step, total_steps, lr0=1e-3, beta1=0.9, beta2=0.999, eps=1e-8,
+             stream=None):
+    """step: int64 device tensor of 2 (step count, scratch 0)."""
+    _require_cuda(params, grad, m, v, step)
+    _check(lib().ens_mlp_adam(params.numel(), _ptr(params), _ptr(grad), _ptr(m), _ptr(v), _ptr(step),
+                              total_steps, lr0, beta1, beta2, eps, _stream(stream)))
+
+
+def mlp_train(params, m, v, step, xin, target, batch, epochs, total_steps, work, lr0=1e-3, beta1=0.9,
+              beta2=0.999, eps=1e-8, epoch_loss=None, use_graph=True, dims=MLP_DIMS, stream=None):
+    _require_cuda(params, m, v, step, xin, target, work, epoch_loss)
+    _check(lib().ens_mlp_train(_dims(dims), _ptr(params), _ptr(m), _ptr(v), _ptr(step), xin.shape[0],
+                               _ptr(xin), _ptr(target), batch, epochs, total_steps, lr0, beta1, beta2, eps,
+                               _ptr(epoch_loss), 1 if use_graph else 0, _ptr(work), _nbytes(work),
+                               _stream(stream)))
+
+
+def guess_workspace_size(s, dims=MLP_DIMS):
+    v = ctypes.c_size_t()
+    _check(lib().ens_guess_workspace_size(_dims(dims), s, ctypes.byref(v)))
+    return v.value
+
+
+def guess(params, s, xi, mean, Phi32, coef_mean, coef_scale, x0, work, dims=MLP_DIMS, stream=None):
+    """x0 (n*s, commuted layout) = mean + Phi (coef_mean + coef_scale * MLP(xi))."""
+    _require_cuda(params, xi, mean, Phi32, coef_mean, coef_scale, x0, work)
+    _check(lib().ens_guess(_dims(dims), _ptr(params), mean.numel(), s, _ptr(xi), _ptr(mean), _ptr(Phi32),
+                           _ptr(coef_mean), _ptr(coef_scale), _ptr(x0), _ptr(work), _nbytes(work),
+                           _stream(stream)))
 
 
 # ------------------------------------------------------------ convenience

@@ -29,9 +29,9 @@ namespace ens {
 
 struct CgState {
     double rho[32], alpha[32], beta[32], bnorm[32], relres[32];
-    int active[32], updx[32], zerox[32], iters[32], status[32];
+    int active[32], updx[32], zerox[32], iters[32], status[32], fb[32];
     int active_count, updx_any, zero_any, spmv_real;
-    int df_bad_any, pad0, pad1, pad2;
+    int df_bad_any, fb_count, pad1, pad2;
     double bnorm_all;
 };
 
@@ -49,6 +49,7 @@ struct CgArgs {
     double tol;
     int max_iter;
     int coupled;
+    int fallback;  // restart from x = 0 members whose ||b - A x0|| >= ||b||
 };
 
 // mapping of the streaming vector kernels (K2, K3): a CTA of TH threads owns
@@ -119,21 +120,25 @@ __global__ void __launch_bounds__(RowMap<S>::THREADS, 1024 / RowMap<S>::THREADS)
     const int e = threadIdx.x;
     const double *top = a.t2.buf[a.t2.levels];
     CgState *st = a.st;
-    const double rr = (e < S) ? ld_cg(top + e) : 0.0, bb = (e < S) ? ld_cg(top + S + e) : 0.0;
+    const double rrx = (e < S) ? ld_cg(top + e) : 0.0, bb = (e < S) ? ld_cg(top + S + e) : 0.0;
+    // zero-guess fallback: a start no better than x = 0 (or not finite) is
+    // replaced by x = 0, r = p = b, whose r.r is b.b in the same tree order
+    const bool fbk = a.fallback && e < S && bb != 0.0 && !(rrx < bb);
+    const double rr = fbk ? bb : rrx;
     double rsum = 0.0, bsum = 0.0;
     for (int k = 0; k < S; ++k) {
         rsum += __shfl_sync(FULL, rr, k);
         bsum += __shfl_sync(FULL, bb, k);
     }
     const double bn = sqrt(bb);
-    int act = 0, zx = 0;
+    int act = 0, zx = fbk ? 1 : 0;
     if (!a.coupled) {
         if (bb == 0.0) zx = 1;
         else act = (sqrt(rr) <= a.tol * bn) ? 0 : 1;
     } else {
         const bool all_zero = (bsum == 0.0);
         act = (all_zero || sqrt(rsum) <= a.tol * sqrt(bsum)) ? 0 : 1;
-        zx = all_zero ? 1 : 0;
+        zx = (all_zero || fbk) ? 1 : 0;
     }
     int status = ENS_OK;
     if (a.max_iter == 0 && act) { act = 0; status = ENS_ERR_NOT_CONVERGED; }
@@ -143,14 +148,17 @@ __global__ void __launch_bounds__(RowMap<S>::THREADS, 1024 / RowMap<S>::THREADS)
         st->alpha[e] = 0.0; st->beta[e] = 0.0; st->relres[e] = 0.0;
         st->iters[e] = 0; st->updx[e] = 0; st->zerox[e] = zx; st->status[e] = status;
         st->active[e] = act;
+        st->fb[e] = fbk ? 1 : 0;
     } else {
         act = 0; zx = 0;
     }
     const int ac = __popc(__ballot_sync(FULL, act)), zany = __popc(__ballot_sync(FULL, zx));
+    const int nfb = __popc(__ballot_sync(FULL, fbk));
     if (e == 0) {
         st->bnorm_all = sqrt(bsum);
         st->active_count = ac;
         st->zero_any = zany;
+        st->fb_count = nfb;
         st->updx_any = 0;
         st->spmv_real = 0;
     }
@@ -158,13 +166,24 @@ __global__ void __launch_bounds__(RowMap<S>::THREADS, 1024 / RowMap<S>::THREADS)
 }
 
 // ------------------------------------------------------------------ KZ
-template <int S>
+// x = 0 for members with b = 0 or a rejected start; for the latter also
+// r = p = b (and the split copy of p)
+template <int S, int MODE>
 __global__ void cg_zero_kernel(CgArgs a) {
     if (ld_cg(&a.st->zero_any) == 0) return;
     const int64_t total = (int64_t)a.n * S;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
-         i += (int64_t)gridDim.x * blockDim.x)
-        if (a.st->zerox[i % S]) a.x[i] = 0.0;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int e = (int)(i % S);
+        if (!a.st->zerox[e]) continue;
+        a.x[i] = 0.0;
+        if (a.st->fb[e]) {
+            const double bv = a.b[i];
+            a.r[i] = bv;
+            a.p[i] = bv;
+            if (MODE != 0) store_split1(a.pdf, i, bv, &a.st->df_bad_any);
+        }
+    }
 }
 
 // ------------------------------------------------------------------ K1
@@ -540,7 +559,7 @@ struct CgKernels {
     }
     static void init(const CgArgs &a, unsigned grid, cudaStream_t st) {
         cg_init_kernel<S, MODE><<<grid, RowMap<S>::THREADS, 0, st>>>(a);
-        cg_zero_kernel<S><<<152 * 2, 256, 0, st>>>(a);
+        cg_zero_kernel<S, MODE><<<152 * 2, 256, 0, st>>>(a);
     }
     static void spmv(const CgArgs &a, unsigned grid, cudaStream_t st) {
         cg_spmv_kernel<S, MODE><<<grid, RowMap<S>::THREADS, 0, st>>>(a);
@@ -589,6 +608,7 @@ static int cg_run(const ens_graph *g, const double *vals, const double *b, doubl
     a.tol = tol;
     a.max_iter = max_iter;
     a.coupled = (flags & ENS_CG_COUPLED) ? 1 : 0;
+    a.fallback = (flags & ENS_CG_GUESS_FALLBACK) ? 1 : 0;
     const unsigned grid = (unsigned)a.t1.count[1];
     int rc;
     if ((rc = dot_tree_clear(a.t1, st))) return rc;
@@ -689,6 +709,8 @@ static int cg_run(const ens_graph *g, const double *vals, const double *b, doubl
         out.stats->iterations = maxit;
         out.stats->kernel_launches = launches;
         out.stats->host_checks = polls;
+        out.stats->guess_fallbacks = hs.fb_count;
+        out.stats->reserved = 0;
         out.stats->spmv_launches = 0;
         out.stats->spmv_ms = 0.0;
         if (timing) {
@@ -812,7 +834,7 @@ __global__ void batch_poll_kernel(const BItem *items, int n_items, int *out) {
 }
 
 static void cg_layout_args(CgArgs &a, const ens_graph *g, int S, const double *vals,
-                           const double *b, double *x, double tol, int max_iter, int coupled,
+                           const double *b, double *x, double tol, int max_iter, int flags,
                            void *work) {
     const int64_t n = g->num_rows;
     char *w = static_cast<char *>(work);
@@ -833,7 +855,8 @@ static void cg_layout_args(CgArgs &a, const ens_graph *g, int S, const double *v
     dot_tree_layout(&a.t2, n, 2 * S, w);
     a.tol = tol;
     a.max_iter = max_iter;
-    a.coupled = coupled;
+    a.coupled = (flags & ENS_CG_COUPLED) ? 1 : 0;
+    a.fallback = (flags & ENS_CG_GUESS_FALLBACK) ? 1 : 0;
 }
 
 template <int MODE>
@@ -906,7 +929,7 @@ static int batched_run(int n_items, const ens_batch_item *items, double tol, int
     for (int i = 0; i < n_items; ++i) {
         const ens_batch_item &it = items[i];
         cg_layout_args(h[i].a, &it.graph, it.s, it.values, it.b, it.x, tol, max_iter,
-                       (flags & ENS_CG_COUPLED) ? 1 : 0, wi);
+                       flags, wi);
         wi += cg_bytes(it.graph.num_rows, it.s);
         h[i].S = it.s;
         const int64_t chunks = h[i].a.t1.count[1];
@@ -996,8 +1019,9 @@ static int batched_run(int n_items, const ens_batch_item *items, double tol, int
     for (int i = 0; i < n_items; ++i)
         ENS_CUDA_TRY(cudaMemcpyAsync(&hs[i], h[i].a.st, sizeof(CgState), cudaMemcpyDeviceToHost, st));
     ENS_CUDA_TRY(cudaStreamSynchronize(st));
-    int first_bad = ENS_OK, maxit = 0, real = 0;
+    int first_bad = ENS_OK, maxit = 0, real = 0, nfb = 0;
     for (int i = 0; i < n_items; ++i) {
+        nfb += hs[i].fb_count;
         const ens_batch_item &it = items[i];
         for (int e = 0; e < it.s; ++e) {
             if (it.iters_host) it.iters_host[e] = hs[i].iters[e];
@@ -1012,6 +1036,8 @@ static int batched_run(int n_items, const ens_batch_item *items, double tol, int
         stats->iterations = maxit;
         stats->kernel_launches = launches;
         stats->host_checks = polls;
+        stats->guess_fallbacks = nfb;
+        stats->reserved = 0;
         stats->spmv_launches = 0;
         stats->spmv_ms = 0.0;
         if (timing) {

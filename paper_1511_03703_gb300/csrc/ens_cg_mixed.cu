@@ -620,6 +620,8 @@ static int mx_run(const ens_graph *g, const double *v64, const void *vlo, const 
         out.stats->kernel_launches = launches;
         out.stats->iterations = maxit;
         out.stats->host_checks = polls;
+        out.stats->guess_fallbacks = 0;
+        out.stats->reserved = 0;
     }
     if (first_bad != ENS_OK)
         set_error("ens_cg_mixed: member status %d (%s)", first_bad, ens_status_string(first_bad));
