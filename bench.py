@@ -689,6 +689,109 @@ def main_batched(args):
     print(json.dumps(line))
 
 
+# ------------------------------------------------- learned-guess workload
+GUESS_TRAIN, GUESS_TEST, GUESS_EPOCHS, GUESS_K, GUESS_L = 4096, 1024, 2000, 64, 80
+GUESS_WORKLOAD = ("KL diffusion, 64^3 hex Q1 mesh, M=10: MLP 10-256-256-64 (GELU, FP32) -> 64 POD "
+                  "coefficients, trained on 4096 solved samples, tested on 1024 fresh samples, CG to 1e-8")
+
+
+def main_guess(args):
+    """Zero-guess ensemble CG vs CG from the learned guess on 1024 fresh
+    samples (s = 32), both to ||r|| <= 1e-8 ||b||; training (solves, POD,
+    MLP epochs) timed separately."""
+    import torch
+    import paper_1511_03703_gb300 as E
+    from paper_1511_03703_gb300 import inputs
+    from paper_1511_03703_gb300.learned import LearnedGuess, collect
+    dev = torch.device("cuda:0")
+    E.lib()
+    s = 32
+    flags = E.CG_SPLIT64 | E.CG_GRAPH
+    mesh = E.Mesh(N_MESH, M_KL, device=dev)
+
+    def wall(fn):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        out = fn()
+        torch.cuda.synchronize()
+        return time.perf_counter() - t0, out
+
+    xtr = inputs.kl_samples(inputs.SEED_GUESS_TRAIN, 0, GUESS_TRAIN, M_KL)
+    t_solve, (X, it_train) = wall(lambda: collect(mesh, xtr, s=s, tol=TOL, flags=E.CG_SPLIT64))
+    g = LearnedGuess(mesh.n, GUESS_K)
+    t_pod, T = wall(lambda: g.fit_basis(X, l=GUESS_L, power_iters=1))
+    del X
+    torch.cuda.empty_cache()
+    g.init_params()
+    t_train, losses = wall(lambda: g.train(xtr, T, epochs=GUESS_EPOCHS))
+    sig = g.sigma.cpu().numpy()
+
+    xte = inputs.kl_samples(inputs.SEED_GUESS_TEST, 0, GUESS_TEST, M_KL)
+    xis = [torch.from_numpy(inputs.ensemble_layout(xte[j:j + s])).to(dev) for j in range(0, GUESS_TEST, s)]
+    vals = torch.empty(mesh.nnz * s, dtype=torch.float64, device=dev)
+    b = torch.empty(mesh.n * s, dtype=torch.float64, device=dev)
+    x = torch.empty(mesh.n * s, dtype=torch.float64, device=dev)
+    work = torch.empty(E.cg_workspace_size(mesh.n, s), dtype=torch.uint8, device=dev)
+
+    def run(learned):
+        iters, fb, launches = [], 0, 0
+        for xi in xis:
+            mesh.assemble(s, xi, values=vals, b=b)
+            launches += 2
+            if learned:
+                g.predict(xi, s, x)
+                launches += 5
+            else:
+                x.zero_()
+            it, rr, st, stats = E.cg(mesh.graph, s, vals, b, x, TOL, 10000, work,
+                                     flags=flags | (E.CG_GUESS_FALLBACK if learned else 0), check_every=8)
+            if any(st):
+                raise RuntimeError(f"CG status {st}")
+            iters += it
+            fb += stats.guess_fallbacks
+            launches += stats.kernel_launches
+        return iters, fb, launches
+
+    def timed(learned):
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        res = run(learned)
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / 1e3, res
+
+    for _ in range(args.warmup):
+        timed(False)
+        timed(True)
+    tz = tl = 0.0
+    for _ in range(args.steps):
+        t, (iz, _, lz) = timed(False)
+        tz += t
+        t, (il, fb, ll) = timed(True)
+        tl += t
+    line = {"metric": "ensemble CG sample-solves/s from the learned initial guess vs from zero, 1 GB300",
+            "value": args.steps * GUESS_TEST / tl, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * tl / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64 CG, f32 network", "data": "synthetic",
+            "config": {"workload": GUESS_WORKLOAD, "ensemble_size": s, "spmv": "split",
+                       "step": "assembly + guess + CG of all 1024 test samples",
+                       "pod_modes": GUESS_K, "pod_oversampled": GUESS_L, "epochs": GUESS_EPOCHS,
+                       "batch": 256},
+            "zero_guess": {"value": args.steps * GUESS_TEST / tz, "unit": UNIT,
+                           "mean_iterations": float(np.mean(iz)), "max_iterations": int(np.max(iz))},
+            "learned_guess": {"mean_iterations": float(np.mean(il)), "max_iterations": int(np.max(il)),
+                              "min_iterations": int(np.min(il)), "fallback_rate": fb / GUESS_TEST},
+            "speedup_vs_zero_guess": tz / tl,
+            "training": {"solve_seconds": t_solve, "train_mean_iterations": float(np.mean(it_train)),
+                         "pod_seconds": t_pod, "mlp_seconds": t_train,
+                         "mlp_steps": GUESS_EPOCHS * GUESS_TRAIN // 256,
+                         "loss_first_epoch": float(losses[0]), "loss_last_epoch": float(losses[-1]),
+                         "sigma_1": float(sig[0]), "sigma_64_over_sigma_1": float(sig[-1] / sig[0])},
+            "gpu_launches": ll}
+    print(json.dumps(line))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -701,15 +804,18 @@ def main():
                          "or alternate entries on each (split)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--quick", action="store_true", help="skip the other-form run and the s sweep")
-    ap.add_argument("--workload", default="scale", choices=["scale", "mixed", "batched"],
+    ap.add_argument("--workload", default="scale", choices=["scale", "mixed", "batched", "guess"],
                     help="scale: 64^3 ensemble CG (default line); mixed: 128^3 mixed precision; "
-                         "batched: 16^3..64^3 x s=4..32 in one batch")
+                         "batched: 16^3..64^3 x s=4..32 in one batch; guess: learned initial guess")
     args = ap.parse_args()
     if args.workload == "mixed" and args.impl != "reference":
         main_mixed(args)
         return
     if args.workload == "batched" and args.impl != "reference":
         main_batched(args)
+        return
+    if args.workload == "guess" and args.impl != "reference":
+        main_guess(args)
         return
     if args.impl == "reference":
         main_reference(args)
