@@ -82,18 +82,22 @@ def spmv_sweep(torch, device, s_list=(1, 4, 8, 16, 32), iters=24):
         vals, b = mesh.assemble(s, torch.from_numpy(inputs.ensemble_layout(xs)).to(device))
         work = torch.empty(E.cg_workspace_size(mesh.n, s), dtype=torch.uint8, device=device)
         row = {}
-        for name, fl in (("f64", 0), ("df", E.CG_DF64), ("split", E.CG_SPLIT64)):
+        vdf = torch.empty(2 * mesh.nnz * s, dtype=torch.float32, device=device)
+        E.convert_values(mesh.graph, s, vals, vdf, dtype=E.F64_DF)
+        for name in FORMS:
+            fl = form_flag(name)
+            vd = vdf if name == "dfv" else None
             x = torch.zeros(mesh.n * s, dtype=torch.float64, device=device)
-            E.cg(mesh.graph, s, vals, b, x, 0.0, 4, work, flags=fl, check_every=4)  # warm-up
+            E.cg(mesh.graph, s, vals, b, x, 0.0, 4, work, flags=fl, check_every=4, values_df=vd)  # warm-up
             x.zero_()
             _, _, _, st = E.cg(mesh.graph, s, vals, b, x, 0.0, iters, work,
-                               flags=fl | E.CG_TIME_SPMV, check_every=iters)
+                               flags=fl | E.CG_TIME_SPMV, check_every=iters, values_df=vd)
             ms = st.spmv_ms / max(st.spmv_launches, 1)
             gbs = spmv_bytes(mesh.n, mesh.nnz, s) / (ms * 1e-3) / 1e9
             row[name] = {"ms": ms, "gbs": gbs, "hbm_frac": gbs / peak,
                          "fp64_tflops": 2 * mesh.nnz * s / (ms * 1e-3) / 1e12}
         out[str(s)] = row
-        del vals, b, work
+        del vals, b, work, vdf
     return out
 
 
@@ -161,6 +165,15 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------- the solver
+FORMS = ("f64", "df", "split", "dfv")
+
+
+def form_flag(form):
+    """ens_cg flags of an SpMV form (dfv: ens_cg_df with the pre-split copy)."""
+    import paper_1511_03703_gb300 as E
+    return {"f64": 0, "df": E.CG_DF64, "split": E.CG_SPLIT64, "dfv": 0}[form]
+
+
 def make_batch(rank, s, batch):
     from paper_1511_03703_gb300 import inputs
     first = rank * batch
@@ -188,6 +201,8 @@ class Runner:
         self.modes = T.empty((M_KL + 1) * nnz, dtype=T.float64, device=device)
         self.load = T.empty(n, dtype=T.float64, device=device)
         self.values = T.empty(nnz * s, dtype=T.float64, device=device)
+        # pre-split double-float copy of the values (dfv form only)
+        self.vdf = T.empty(2 * nnz * s, dtype=T.float32, device=device) if df == "dfv" else None
         self.b = T.empty(n * s, dtype=T.float64, device=device)
         self.x = T.empty((self.nens, n * s), dtype=T.float64, device=device)
         self.work = T.empty(E.cg_workspace_size(n, s), dtype=T.uint8, device=device)
@@ -214,12 +229,14 @@ class Runner:
         E = self.E
         E.assemble(self.graph, self.bmask, self.s, M_KL, self.modes, self.load,
                    self.xi[g] if xi is None else xi, SIGMA, KAPPA0, self.values, self.b)
+        if self.vdf is not None:
+            E.convert_values(self.graph, self.s, self.values, self.vdf, dtype=E.F64_DF)
+            self.launches += 1
         x = self.x[g]
         x.zero_()
-        flags = (E.CG_TIME_SPMV if self.time_spmv else 0) | {"f64": 0, "df": E.CG_DF64,
-                                                             "split": E.CG_SPLIT64}[self.df]
+        flags = (E.CG_TIME_SPMV if self.time_spmv else 0) | form_flag(self.df)
         it, rr, st, stats = E.cg(self.graph, self.s, self.values, self.b, x, TOL, 10000, self.work,
-                                 flags=flags, check_every=16)
+                                 flags=flags, check_every=16, values_df=self.vdf)
         self.launches += 2 + stats.kernel_launches
         self.iters.extend(it)
         self.status_bad += sum(1 for v in st if v != 0)
@@ -237,7 +254,7 @@ def per_sample_baseline(torch, device, nsamp=32, df="f64"):
     """The s = 1 path (samples one after another), as in the paper's speed-up
     (s * T1 / Ts, Sect. 4); every SpMV form is timed and the fastest reported."""
     best = None
-    for form in ("f64", "df", "split"):
+    for form in FORMS:
         res = _per_sample_form(torch, device, nsamp, form)
         if best is None or res["value"] > best["value"]:
             best = res
@@ -393,7 +410,7 @@ def main_ours(args):
         ens_speedup = value / world / per["value"]
         others = {}
         if not args.quick:
-            for form in ("f64", "df", "split"):
+            for form in FORMS:
                 if form == df:
                     continue
                 r2 = Runner(torch, s, BATCH, device, time_spmv=True, df=form)
@@ -418,7 +435,9 @@ def main_ours(args):
             "scaling": "weak", "vs_baseline": None,
             "dtype": {"f64": "f64",
                       "df": "f64 (SpMV products and sums in double-float 2xf32, all else f64)",
-                      "split": "f64 (SpMV: even entries FP64 FMA, odd entries double-float 2xf32; all else f64)"}[df],
+                      "split": "f64 (SpMV: even entries FP64 FMA, odd entries double-float 2xf32; all else f64)",
+                      "dfv": "f64 (SpMV in double-float 2xf32 from values pre-split once per ensemble, "
+                             "bitwise the df form; all else f64)"}[df],
             "data": "synthetic",
             "config": {"workload": WORKLOAD, "ensemble_size": s, "batch_samples": BATCH,
                        "ensembles_per_step": BATCH // s, "tol": TOL, "kl_terms": M_KL,
@@ -608,7 +627,9 @@ def main_batched(args):
             groups.append((N, s))
             g += 1
     t0 = time.perf_counter()
-    forms = {(N, s): autotune.best_form(meshes[N], s) for N in BAT_MESHES for s in BAT_WIDTHS}
+    # the batched launch reads FP64 values: forms without a pre-split copy
+    cand = ("f64", "df", "split")
+    forms = {(N, s): autotune.best_form(meshes[N], s, candidates=cand) for N in BAT_MESHES for s in BAT_WIDTHS}
     works = {}
     for it in items:
         key = (it["N"], it["s"])
@@ -706,7 +727,7 @@ def main_guess(args):
     dev = torch.device("cuda:0")
     E.lib()
     s = 32
-    flags = E.CG_SPLIT64 | E.CG_GRAPH
+    flags = E.CG_GRAPH
     mesh = E.Mesh(N_MESH, M_KL, device=dev)
 
     def wall(fn):
@@ -717,7 +738,7 @@ def main_guess(args):
         return time.perf_counter() - t0, out
 
     xtr = inputs.kl_samples(inputs.SEED_GUESS_TRAIN, 0, GUESS_TRAIN, M_KL)
-    t_solve, (X, it_train) = wall(lambda: collect(mesh, xtr, s=s, tol=TOL, flags=E.CG_SPLIT64))
+    t_solve, (X, it_train) = wall(lambda: collect(mesh, xtr, s=s, tol=TOL))
     g = LearnedGuess(mesh.n, GUESS_K)
     t_pod, T = wall(lambda: g.fit_basis(X, l=GUESS_L, power_iters=1))
     del X
@@ -731,20 +752,23 @@ def main_guess(args):
     vals = torch.empty(mesh.nnz * s, dtype=torch.float64, device=dev)
     b = torch.empty(mesh.n * s, dtype=torch.float64, device=dev)
     x = torch.empty(mesh.n * s, dtype=torch.float64, device=dev)
+    vdf = torch.empty(2 * mesh.nnz * s, dtype=torch.float32, device=dev)
     work = torch.empty(E.cg_workspace_size(mesh.n, s), dtype=torch.uint8, device=dev)
 
     def run(learned):
         iters, fb, launches = [], 0, 0
         for xi in xis:
             mesh.assemble(s, xi, values=vals, b=b)
-            launches += 2
+            E.convert_values(mesh.graph, s, vals, vdf, dtype=E.F64_DF)
+            launches += 3
             if learned:
                 g.predict(xi, s, x)
                 launches += 5
             else:
                 x.zero_()
             it, rr, st, stats = E.cg(mesh.graph, s, vals, b, x, TOL, 10000, work,
-                                     flags=flags | (E.CG_GUESS_FALLBACK if learned else 0), check_every=8)
+                                     flags=flags | (E.CG_GUESS_FALLBACK if learned else 0), check_every=8,
+                                     values_df=vdf)
             if any(st):
                 raise RuntimeError(f"CG status {st}")
             iters += it
@@ -774,7 +798,7 @@ def main_guess(args):
             "value": args.steps * GUESS_TEST / tl, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * tl / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64 CG, f32 network", "data": "synthetic",
-            "config": {"workload": GUESS_WORKLOAD, "ensemble_size": s, "spmv": "split",
+            "config": {"workload": GUESS_WORKLOAD, "ensemble_size": s, "spmv": "dfv",
                        "step": "assembly + guess + CG of all 1024 test samples",
                        "pod_modes": GUESS_K, "pod_oversampled": GUESS_L, "epochs": GUESS_EPOCHS,
                        "batch": 256},
@@ -799,9 +823,10 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--s", type=int, default=32, choices=[4, 8, 16, 32])
-    ap.add_argument("--spmv", default="split", choices=["f64", "df", "split"],
+    ap.add_argument("--spmv", default="dfv", choices=list(FORMS),
                     help="CG SpMV arithmetic: native FP64 FMA, double-float on the FP32 pipe, "
-                         "or alternate entries on each (split)")
+                         "alternate entries on each (split), or double-float reading values "
+                         "pre-split once per ensemble (dfv)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--quick", action="store_true", help="skip the other-form run and the s sweep")
     ap.add_argument("--workload", default="scale", choices=["scale", "mixed", "batched", "guess"],

@@ -218,6 +218,19 @@ int ens_cg(const ens_graph *graph, int s, const double *values, const double *b,
            int32_t *iters_host, double *relres_host, int32_t *status_host,
            ens_cg_stats *stats_host, void *stream);
 
+/* ens_cg with the double-float CG SpMV reading pre-split values: values_df is
+ * the ens_convert_values(..., ENS_F64_DF, ...) copy of `values` (float2[nnz*s]),
+ * read by every iteration's SpMV instead of splitting each FP64 value again;
+ * `values` (FP64) is still read by the initial and final residuals and by
+ * rows whose double-float sum is not finite.  Every result is bitwise that of
+ * ens_cg with ENS_CG_DF64 (the same operations in the same order).  flags:
+ * ENS_CG_COUPLED, ENS_CG_GRAPH, ENS_CG_TIME_SPMV, ENS_CG_GUESS_FALLBACK
+ * (ENS_CG_DF64 / ENS_CG_SPLIT64 are implied / ignored).  Same workspace. */
+int ens_cg_df(const ens_graph *graph, int s, const double *values, const void *values_df, const double *b,
+              double *x, double tol, int max_iter, int flags, int check_every, void *work, size_t work_bytes,
+              int32_t *iters_host, double *relres_host, int32_t *status_host, ens_cg_stats *stats_host,
+              void *stream);
+
 /* ---------------------------------------------------- A8 batched CG */
 /* One ensemble of a batch: its graph (by value), size s, values, rhs, x (in:
  * x0, out: solution) and optional host outputs iters/relres/status [s]. */
@@ -258,6 +271,11 @@ int ens_cg_batched(int n_items, const ens_batch_item *items, double tol, int max
  *   would otherwise break at the size of the smallest eigenvalue. */
 int ens_convert_values(const ens_graph *graph, int s, const double *values, int dtype,
                        void *values_lo, float *diag_lo, void *stream);
+/* dtype = ENS_F64_DF (for ens_cg_df): values_lo is float2[nnz*s] (commuted
+ * layout), each value split by truncation into hi + lo floats (the split of
+ * the ENS_F64_DF SpMV, 47 significant bits); a value whose magnitude is
+ * outside [2^-103, 2^128) or that is not finite is stored as (NaN, 0).
+ * diag_lo must be NULL. */
 
 /* Mixed-precision ensemble CG (iterative refinement; not in the paper, see
  * the A7 row of the design notes): per member,

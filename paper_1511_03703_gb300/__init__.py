@@ -98,6 +98,7 @@ def _declare(L):
         "ens_dot_static": (I, [i64, I, vp, vp, vp, vp]),
         "ens_cg_workspace_size": (I, [i32, I, P(sz)]),
         "ens_cg": (I, [P(EnsGraphC), I, vp, vp, vp, d, I, I, I, vp, sz, vp, vp, vp, P(CgStats), vp]),
+        "ens_cg_df": (I, [P(EnsGraphC), I, vp, vp, vp, vp, d, I, I, I, vp, sz, vp, vp, vp, P(CgStats), vp]),
         "ens_convert_values": (I, [P(EnsGraphC), I, vp, I, vp, vp, vp]),
         "ens_cg_batched_workspace_size": (I, [I, P(BatchItemC), P(sz)]),
         "ens_cg_batched": (I, [I, P(BatchItemC), d, I, I, I, vp, sz, P(CgStats), vp]),
@@ -260,16 +261,23 @@ def cg_workspace_size(n, s):
 
 
 def cg(graph, s, values, b, x, tol, max_iter, work, flags=0, check_every=8, stream=None,
-       raise_on_failure=False):
-    """Runs ens_cg; returns (iters[s], relres[s], status[s], CgStats).  Synchronises."""
-    _require_cuda(values, b, x, work)
+       raise_on_failure=False, values_df=None):
+    """Runs ens_cg (or ens_cg_df when values_df, the ENS_F64_DF split copy of
+    values, is given); returns (iters[s], relres[s], status[s], CgStats).
+    Synchronises."""
+    _require_cuda(values, b, x, work, values_df)
     it = (ctypes.c_int32 * s)()
     rr = (ctypes.c_double * s)()
     stt = (ctypes.c_int32 * s)()
     stats = CgStats()
-    rc = lib().ens_cg(graph.ref(), s, _ptr(values), _ptr(b), _ptr(x), tol, max_iter, flags,
-                      check_every, _ptr(work), work.numel() * work.element_size(), it, rr, stt,
-                      ctypes.byref(stats), _stream(stream))
+    if values_df is None:
+        rc = lib().ens_cg(graph.ref(), s, _ptr(values), _ptr(b), _ptr(x), tol, max_iter, flags,
+                          check_every, _ptr(work), work.numel() * work.element_size(), it, rr, stt,
+                          ctypes.byref(stats), _stream(stream))
+    else:
+        rc = lib().ens_cg_df(graph.ref(), s, _ptr(values), _ptr(values_df), _ptr(b), _ptr(x), tol, max_iter,
+                             flags, check_every, _ptr(work), work.numel() * work.element_size(), it, rr, stt,
+                             ctypes.byref(stats), _stream(stream))
     if rc not in (0, ERR_NOT_CONVERGED, ERR_BREAKDOWN) or (rc and raise_on_failure):
         _check(rc)
     return list(it), list(rr), list(stt), stats
@@ -315,10 +323,11 @@ class Batch:
 
 
 # --------------------------------------------------------- mixed precision
-def convert_values(graph, s, values, values_lo, diag_lo=None, stream=None):
-    """FP64 values -> values_lo (float32 or bfloat16 tensor); diag_lo (float32) optional."""
+def convert_values(graph, s, values, values_lo, diag_lo=None, stream=None, dtype=None):
+    """FP64 values -> values_lo (float32 or bfloat16 tensor); diag_lo (float32)
+    optional.  dtype=F64_DF: values_lo holds 2*nnz*s float32 (the split pairs)."""
     _require_cuda(values, values_lo, diag_lo)
-    dt = _DT[str(values_lo.dtype).replace("torch.", "")]
+    dt = _DT[str(values_lo.dtype).replace("torch.", "")] if dtype is None else dtype
     _check(lib().ens_convert_values(graph.ref(), s, _ptr(values), dt, _ptr(values_lo), _ptr(diag_lo),
                                     _stream(stream)))
 

@@ -2,7 +2,8 @@
 
 Knobs, all exposed through the C ABI:
   - SpMV arithmetic form per (mesh, s): native FP64 FMA, double-float on the
-    FP32 pipe, or alternate entries on each (ENS_CG_DF64 / ENS_CG_SPLIT64);
+    FP32 pipe, alternate entries on each (ENS_CG_DF64 / ENS_CG_SPLIT64), or
+    double-float on values pre-split once per ensemble (ens_cg_df);
     GB300's 1/64-rate FP64 makes the best form depend on s and mesh size;
   - graph length (check_every): iterations replayed per CUDA graph launch
     between host polls of the convergence word;
@@ -19,7 +20,7 @@ import time
 
 import paper_1511_03703_gb300 as E
 
-FORMS = {"f64": 0, "df": E.CG_DF64, "split": E.CG_SPLIT64}
+FORMS = {"f64": 0, "df": E.CG_DF64, "split": E.CG_SPLIT64, "dfv": 0}  # dfv: ens_cg_df, pre-split values
 CHECK_EVERY = (4, 8, 16, 32)
 WIDTHS = (4, 8, 16, 32)
 
@@ -63,31 +64,35 @@ def _ensemble(mesh, s, seed=1004):
     return vals, b
 
 
-def time_spmv_forms(mesh, s, iters=24, vals=None, b=None):
+def time_spmv_forms(mesh, s, iters=24, vals=None, b=None, candidates=tuple(FORMS)):
     """Mean CG SpMV launch time (ms) of each arithmetic form on one ensemble."""
     import torch
     if vals is None:
         vals, b = _ensemble(mesh, s)
     dev = vals.device
     work = torch.empty(E.cg_workspace_size(mesh.n, s), dtype=torch.uint8, device=dev)
+    vdf = torch.empty(2 * vals.numel(), dtype=torch.float32, device=dev)
+    E.convert_values(mesh.graph, s, vals, vdf, dtype=E.F64_DF)
     out = {}
-    for name, fl in FORMS.items():
+    for name in candidates:
+        fl = FORMS[name]
+        vd = vdf if name == "dfv" else None
         x = torch.zeros(mesh.n * s, dtype=torch.float64, device=dev)
-        E.cg(mesh.graph, s, vals, b, x, 0.0, 4, work, flags=fl, check_every=4)
+        E.cg(mesh.graph, s, vals, b, x, 0.0, 4, work, flags=fl, check_every=4, values_df=vd)
         x.zero_()
         _, _, _, st = E.cg(mesh.graph, s, vals, b, x, 0.0, iters, work,
-                           flags=fl | E.CG_TIME_SPMV, check_every=iters)
+                           flags=fl | E.CG_TIME_SPMV, check_every=iters, values_df=vd)
         out[name] = st.spmv_ms / max(st.spmv_launches, 1)
     return out
 
 
-def best_form(mesh, s, refresh=False):
-    """Fastest SpMV form for (mesh, s), cached."""
+def best_form(mesh, s, refresh=False, candidates=tuple(FORMS)):
+    """Fastest SpMV form for (mesh, s) among `candidates`, cached."""
     db = _load()
-    k = _key("form", mesh.N, mesh.M, s)
+    k = _key("form", mesh.N, mesh.M, s, ",".join(candidates))
     if not refresh and k in db:
         return db[k]["form"]
-    t = time_spmv_forms(mesh, s)
+    t = time_spmv_forms(mesh, s, candidates=candidates)
     form = min(t, key=t.get)
     db[k] = {"form": form, "spmv_ms": t}
     _store(db)

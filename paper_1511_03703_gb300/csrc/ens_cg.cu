@@ -21,6 +21,8 @@
 // deterministic dot tree.  K2/K3 stream tiles of 4-8 tree chunks per CTA.
 // Flag protocol: K2 sets updx_e for members active in its iteration, K3 reads
 // them, and the next K1 clears them (also when it exits early).
+#include <stdlib.h>
+
 #include <vector>
 
 #include "ens_spmv.cuh"
@@ -40,9 +42,10 @@ struct CgArgs {
     const int32_t *row_map;
     const int32_t *col;
     const double *vals;
+    const float2 *vdf;  // values pre-split into float pairs (MODE 3), else NULL
     const double *b;
     double *x, *r, *p, *q;
-    float2 *pdf;  // p split into float pairs (df mode)
+    float2 *pdf;  // p split into float pairs (df modes)
     CgState *st;
     DotTree t1;   // width s
     DotTree t2;   // width 2s
@@ -50,6 +53,8 @@ struct CgArgs {
     int max_iter;
     int coupled;
     int fallback;  // restart from x = 0 members whose ||b - A x0|| >= ||b||
+    uint32_t pf_cap;       // bytes of each chunk's value block prefetched into L2 by K1
+    uint64_t val_bytes;    // size of the value array read by K1 (8 bytes per value in every form)
 };
 
 // mapping of the streaming vector kernels (K2, K3): a CTA of TH threads owns
@@ -279,8 +284,17 @@ __device__ __forceinline__ void k1_body(const CgArgs &a, const int cta, K1Smem<S
 }
 
 // single-ensemble K1 (one chunk per CTA); same arithmetic as k1_body
+#ifndef ENS_K1_DFV_THREADS_PER_SM
+#define ENS_K1_DFV_THREADS_PER_SM 1536
+#endif
 template <int S, int MODE>
-__global__ void __launch_bounds__(RowMap<S>::THREADS, 1536 / RowMap<S>::THREADS) cg_spmv_kernel(CgArgs a) {
+struct K1Occ {
+    static constexpr int THREADS_PER_SM = (MODE == 3) ? ENS_K1_DFV_THREADS_PER_SM : 1536;
+};
+
+template <int S, int MODE>
+__global__ void __launch_bounds__(RowMap<S>::THREADS, K1Occ<S, MODE>::THREADS_PER_SM / RowMap<S>::THREADS)
+    cg_spmv_kernel(CgArgs a) {
     CgState *st = a.st;
     if (ld_cg(&st->active_count) == 0) {
         if (blockIdx.x == 0 && threadIdx.x == 0 && st->updx_any) {
@@ -296,10 +310,14 @@ __global__ void __launch_bounds__(RowMap<S>::THREADS, 1536 / RowMap<S>::THREADS)
     // the split form is used unless a vector element fell outside its range
     const int mode = (MODE != 0 && ld_cg(&st->df_bad_any) != 0) ? 0 : MODE;
     __shared__ ChunkCols cc;
-    const bool staged = stage_chunk(cc, a.row_map, a.col, blockIdx.x, a.n);
+    const void *vblock = (MODE == 3) ? static_cast<const void *>(a.vdf) : static_cast<const void *>(a.vals);
+    const bool staged = stage_chunk_pf(cc, a.row_map, a.col, blockIdx.x, a.n, vblock, S * 8u, a.val_bytes,
+                                       a.pf_cap);
     double2 apv;
     if (MODE == 1 && mode == 1)
         apv = chunk_spmv_df<S, XPre>(cc, staged, a.col, a.vals, a.pdf, r, g, R < a.n);
+    else if (MODE == 3 && mode == 3)
+        apv = chunk_spmv_dfv<S>(cc, staged, a.col, a.vdf, a.vals, a.pdf, r, g, R < a.n);
     else if (MODE == 2 && mode == 2)
         apv = chunk_spmv_split<S, XPre>(cc, staged, a.col, a.vals, a.p, a.pdf, r, g, R < a.n);
     else
@@ -547,6 +565,20 @@ __global__ void __launch_bounds__(RowMap<S>::THREADS, 1024 / RowMap<S>::THREADS)
 // ------------------------------------------------------------ host side
 static size_t align256(size_t x) { return (x + 255) / 256 * 256; }
 
+// Bytes of each chunk's value block that K1 prefetches into L2 at its start:
+// the whole block for the pre-split double-float form, whose SpMV is bound by
+// memory latency without it (measured on the 64^3 mesh: 0.425 -> 0.372 ms at
+// s = 32); none for the FP64-pipe-bound forms.  ENS_L2_PREFETCH (bytes)
+// overrides both.
+static uint32_t l2_prefetch_cap(int mode) {
+    static const long long env = [] {
+        const char *e = getenv("ENS_L2_PREFETCH");
+        return e ? (long long)strtoull(e, nullptr, 10) : -1LL;
+    }();
+    if (env >= 0) return (uint32_t)(env > 0xffffffffLL ? 0xffffffffLL : env);
+    return mode == 3 ? 0xffffffffu : 0u;
+}
+
 static size_t cg_bytes(int64_t n, int s) {
     return align256(sizeof(CgState)) + 4 * align256(sizeof(double) * (size_t)n * s) +
            dot_tree_bytes(n, s) + dot_tree_bytes(n, 2 * s);
@@ -583,8 +615,8 @@ struct CgHostOut {
 };
 
 template <int S, int MODE>
-static int cg_run(const ens_graph *g, const double *vals, const double *b, double *x, double tol,
-                  int max_iter, int flags, int check_every, void *work, CgHostOut out,
+static int cg_run(const ens_graph *g, const double *vals, const float2 *vdf, const double *b, double *x,
+                  double tol, int max_iter, int flags, int check_every, void *work, CgHostOut out,
                   cudaStream_t st) {
     using K = CgKernels<S, MODE>;
     const int64_t n = g->num_rows;
@@ -594,6 +626,7 @@ static int cg_run(const ens_graph *g, const double *vals, const double *b, doubl
     a.row_map = g->row_map;
     a.col = g->col_entry;
     a.vals = vals;
+    a.vdf = vdf;
     a.b = b;
     a.x = x;
     a.st = reinterpret_cast<CgState *>(w);
@@ -609,6 +642,8 @@ static int cg_run(const ens_graph *g, const double *vals, const double *b, doubl
     a.max_iter = max_iter;
     a.coupled = (flags & ENS_CG_COUPLED) ? 1 : 0;
     a.fallback = (flags & ENS_CG_GUESS_FALLBACK) ? 1 : 0;
+    a.pf_cap = l2_prefetch_cap(MODE);
+    a.val_bytes = (uint64_t)g->num_entries * S * 8u;
     const unsigned grid = (unsigned)a.t1.count[1];
     int rc;
     if ((rc = dot_tree_clear(a.t1, st))) return rc;
@@ -727,14 +762,15 @@ static int cg_run(const ens_graph *g, const double *vals, const double *b, doubl
 }
 
 template <int S>
-static int cg_dispatch_df(const ens_graph *g, const double *vals, const double *b, double *x,
-                          double tol, int max_iter, int flags, int check_every, void *work,
+static int cg_dispatch_df(const ens_graph *g, const double *vals, const float2 *vdf, const double *b,
+                          double *x, double tol, int max_iter, int flags, int check_every, void *work,
                           CgHostOut out, cudaStream_t st) {
+    if (vdf) return cg_run<S, 3>(g, vals, vdf, b, x, tol, max_iter, flags, check_every, work, out, st);
     if (flags & ENS_CG_SPLIT64)
-        return cg_run<S, 2>(g, vals, b, x, tol, max_iter, flags, check_every, work, out, st);
+        return cg_run<S, 2>(g, vals, nullptr, b, x, tol, max_iter, flags, check_every, work, out, st);
     if (flags & ENS_CG_DF64)
-        return cg_run<S, 1>(g, vals, b, x, tol, max_iter, flags, check_every, work, out, st);
-    return cg_run<S, 0>(g, vals, b, x, tol, max_iter, flags, check_every, work, out, st);
+        return cg_run<S, 1>(g, vals, nullptr, b, x, tol, max_iter, flags, check_every, work, out, st);
+    return cg_run<S, 0>(g, vals, nullptr, b, x, tol, max_iter, flags, check_every, work, out, st);
 }
 
 // ------------------------------------------------------------ batched
@@ -842,6 +878,7 @@ static void cg_layout_args(CgArgs &a, const ens_graph *g, int S, const double *v
     a.row_map = g->row_map;
     a.col = g->col_entry;
     a.vals = vals;
+    a.vdf = nullptr;
     a.b = b;
     a.x = x;
     a.st = reinterpret_cast<CgState *>(w);
@@ -857,6 +894,8 @@ static void cg_layout_args(CgArgs &a, const ens_graph *g, int S, const double *v
     a.max_iter = max_iter;
     a.coupled = (flags & ENS_CG_COUPLED) ? 1 : 0;
     a.fallback = (flags & ENS_CG_GUESS_FALLBACK) ? 1 : 0;
+    a.pf_cap = 0;
+    a.val_bytes = 0;
 }
 
 template <int MODE>
@@ -1065,10 +1104,10 @@ extern "C" int ens_cg_workspace_size(int32_t num_rows, int s, size_t *bytes) {
     return ENS_OK;
 }
 
-extern "C" int ens_cg(const ens_graph *graph, int s, const double *values, const double *b,
-                      double *x, double tol, int max_iter, int flags, int check_every, void *work,
-                      size_t work_bytes, int32_t *iters_host, double *relres_host,
-                      int32_t *status_host, ens_cg_stats *stats_host, void *stream) {
+static int cg_entry(const ens_graph *graph, int s, const double *values, const float2 *vdf, const double *b,
+                    double *x, double tol, int max_iter, int flags, int check_every, void *work,
+                    size_t work_bytes, int32_t *iters_host, double *relres_host, int32_t *status_host,
+                    ens_cg_stats *stats_host, void *stream) {
     int rc = check_graph(graph);
     if (rc) return rc;
     if (!supported_s(s)) return fail(ENS_ERR_UNSUPPORTED, "ensemble size s=%d not in {1,4,8,16,32}", s);
@@ -1083,12 +1122,31 @@ extern "C" int ens_cg(const ens_graph *graph, int s, const double *values, const
     CgHostOut out{iters_host, relres_host, status_host, stats_host};
     cudaStream_t st = as_stream(stream);
     switch (s) {
-        case 1: return cg_dispatch_df<1>(graph, values, b, x, tol, max_iter, flags, check_every, work, out, st);
-        case 4: return cg_dispatch_df<4>(graph, values, b, x, tol, max_iter, flags, check_every, work, out, st);
-        case 8: return cg_dispatch_df<8>(graph, values, b, x, tol, max_iter, flags, check_every, work, out, st);
-        case 16: return cg_dispatch_df<16>(graph, values, b, x, tol, max_iter, flags, check_every, work, out, st);
-        default: return cg_dispatch_df<32>(graph, values, b, x, tol, max_iter, flags, check_every, work, out, st);
+        case 1: return cg_dispatch_df<1>(graph, values, vdf, b, x, tol, max_iter, flags, check_every, work, out, st);
+        case 4: return cg_dispatch_df<4>(graph, values, vdf, b, x, tol, max_iter, flags, check_every, work, out, st);
+        case 8: return cg_dispatch_df<8>(graph, values, vdf, b, x, tol, max_iter, flags, check_every, work, out, st);
+        case 16: return cg_dispatch_df<16>(graph, values, vdf, b, x, tol, max_iter, flags, check_every, work, out, st);
+        default: return cg_dispatch_df<32>(graph, values, vdf, b, x, tol, max_iter, flags, check_every, work, out, st);
     }
+}
+
+extern "C" int ens_cg(const ens_graph *graph, int s, const double *values, const double *b,
+                      double *x, double tol, int max_iter, int flags, int check_every, void *work,
+                      size_t work_bytes, int32_t *iters_host, double *relres_host,
+                      int32_t *status_host, ens_cg_stats *stats_host, void *stream) {
+    return cg_entry(graph, s, values, nullptr, b, x, tol, max_iter, flags, check_every, work, work_bytes,
+                    iters_host, relres_host, status_host, stats_host, stream);
+}
+
+extern "C" int ens_cg_df(const ens_graph *graph, int s, const double *values, const void *values_df,
+                         const double *b, double *x, double tol, int max_iter, int flags, int check_every,
+                         void *work, size_t work_bytes, int32_t *iters_host, double *relres_host,
+                         int32_t *status_host, ens_cg_stats *stats_host, void *stream) {
+    if (!values_df) return fail(ENS_ERR_ARG, "ens_cg_df: values_df is NULL");
+    if (s > 1 && !aligned16(values_df)) return fail(ENS_ERR_ALIGN, "ens_cg_df: values_df must be 16-byte aligned");
+    return cg_entry(graph, s, values, static_cast<const float2 *>(values_df), b, x, tol, max_iter,
+                    flags & ~(ENS_CG_DF64 | ENS_CG_SPLIT64), check_every, work, work_bytes, iters_host,
+                    relres_host, status_host, stats_host, stream);
 }
 
 static int check_batch(int n_items, const ens_batch_item *items) {

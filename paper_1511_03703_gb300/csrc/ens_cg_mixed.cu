@@ -646,6 +646,18 @@ static int mx_dispatch(int s, const ens_graph *g, const double *v64, const void 
 
 using namespace ens;
 
+// values -> float pairs (hi, lo) by the truncating split of the double-float
+// SpMV; values outside the split range (or not finite) become (NaN, 0)
+__global__ void split_values_kernel(int64_t count, const double *__restrict__ values,
+                                    float2 *__restrict__ out) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < count;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        float hi, lo;
+        const bool ok = df_split_trunc(ld_stream(values + i), hi, lo);
+        out[i] = ok ? make_float2(hi, lo) : make_float2(__int_as_float(0x7fc00000), 0.0f);
+    }
+}
+
 extern "C" int ens_convert_values(const ens_graph *graph, int s, const double *values,
                                   int dtype, void *values_lo, float *diag_lo, void *stream) {
     int rc = check_graph(graph);
@@ -658,6 +670,14 @@ extern "C" int ens_convert_values(const ens_graph *graph, int s, const double *v
     if (nt == 0) return ENS_OK;
     cudaStream_t st = as_stream(stream);
     const unsigned grid = (unsigned)((nt + 255) / 256);
+    if (dtype == ENS_F64_DF) {
+        if (diag_lo) return fail(ENS_ERR_ARG, "convert to ENS_F64_DF takes no diag_lo");
+        const int64_t count = graph->num_entries * s;
+        const int64_t blocks = std::min<int64_t>((count + 255) / 256, 152 * 16);
+        split_values_kernel<<<(unsigned)blocks, 256, 0, st>>>(count, values, static_cast<float2 *>(values_lo));
+        ENS_LAUNCH_CHECK("split_values_kernel");
+        return ENS_OK;
+    }
     if (dtype == ENS_F32)
         convert_values_kernel<float><<<grid, 256, 0, st>>>(graph->num_rows, s, graph->row_map, graph->col_entry,
                                                            values, static_cast<float *>(values_lo), diag_lo);
@@ -666,7 +686,7 @@ extern "C" int ens_convert_values(const ens_graph *graph, int s, const double *v
                                                                    graph->col_entry, values,
                                                                    static_cast<__nv_bfloat16 *>(values_lo), diag_lo);
     else
-        return fail(ENS_ERR_UNSUPPORTED, "convert to dtype %d (ENS_F32 or ENS_BF16 only)", dtype);
+        return fail(ENS_ERR_UNSUPPORTED, "convert to dtype %d (ENS_F32, ENS_BF16 or ENS_F64_DF only)", dtype);
     ENS_LAUNCH_CHECK("convert_values_kernel");
     return ENS_OK;
 }

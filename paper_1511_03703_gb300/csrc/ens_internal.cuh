@@ -49,6 +49,12 @@ __device__ __forceinline__ float2 ld_stream(const float2 *p) {
     asm volatile("ld.global.cs.v2.f32 {%0, %1}, [%2];" : "=f"(v.x), "=f"(v.y) : "l"(p));
     return v;
 }
+__device__ __forceinline__ float4 ld_stream(const float4 *p) {
+    float4 v;
+    asm volatile("ld.global.cs.v4.f32 {%0, %1, %2, %3}, [%4];"
+                 : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w) : "l"(p));
+    return v;
+}
 __device__ __forceinline__ float ld_stream(const float *p) {
     float v;
     asm volatile("ld.global.cs.f32 %0, [%1];" : "=f"(v) : "l"(p));

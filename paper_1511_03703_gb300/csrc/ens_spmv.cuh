@@ -112,6 +112,43 @@ __device__ __forceinline__ bool stage_chunk(ChunkCols &cc, const int32_t *__rest
     return staged;
 }
 
+// Staging with an L2 prefetch of the chunk's value block: once the row
+// offsets are known, thread 0 asks the copy engine to bring up to cap bytes
+// of the block [e0*bpe, e1*bpe) (16-byte aligned, clamped to the array of
+// total_bytes) into L2 with evict-first priority, so the row loops' value
+// loads hit L2 while the column indices are still being staged.
+__device__ __forceinline__ void l2_prefetch_bulk(const void *base, uint64_t begin, uint64_t end,
+                                                 uint64_t total_bytes, uint32_t cap) {
+    begin &= ~(uint64_t)15;
+    end = min((end + 15) & ~(uint64_t)15, total_bytes & ~(uint64_t)15);
+    if (end > begin + cap) end = begin + cap;
+    if (end <= begin) return;
+    const char *p = static_cast<const char *>(base) + begin;
+    uint64_t policy;
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(policy));
+    asm volatile("cp.async.bulk.prefetch.L2.global.L2::cache_hint [%0], %1, %2;"
+                 :: "l"(p), "r"((uint32_t)(end - begin)), "l"(policy) : "memory");
+}
+
+__device__ __forceinline__ bool stage_chunk_pf(ChunkCols &cc, const int32_t *__restrict__ row_map,
+                                               const int32_t *__restrict__ col, int64_t chunk, int32_t n,
+                                               const void *vbase, uint32_t bytes_per_entry,
+                                               uint64_t total_bytes, uint32_t cap) {
+    const int64_t r0 = chunk * 32;
+    const int nr = (int)min((int64_t)32, (int64_t)n - r0);
+    for (int i = threadIdx.x; i <= nr; i += blockDim.x) cc.rm[i] = __ldg(row_map + r0 + i);
+    __syncthreads();
+    const int e0 = cc.rm[0], cnt = cc.rm[nr] - e0;
+    if (threadIdx.x == 0 && cap > 0)
+        l2_prefetch_bulk(vbase, (uint64_t)e0 * bytes_per_entry, (uint64_t)cc.rm[nr] * bytes_per_entry,
+                         total_bytes, cap);
+    const bool staged = cnt <= kColCap;
+    if (staged)
+        for (int i = threadIdx.x; i < cnt; i += blockDim.x) cc.col[i] = __ldg(col + e0 + i);
+    __syncthreads();
+    return staged;
+}
+
 // Subset form used when one CTA works on NSUB chunks at once (nthr threads
 // per chunk, ltid the thread's index inside its chunk): the same copy, with
 // chunks past the end of the matrix left empty.  All threads of the CTA call it.
@@ -232,11 +269,8 @@ __device__ __forceinline__ double f2d_exact(float f) {
     return __hiloint2double((int)hi, (int)lo);
 }
 
-// one term a*(xh + xl) into A; returns false when a needs the FP64 path
-// (the term then contributes nothing here and is added by df_fixup)
-__device__ __forceinline__ bool df_term(DfAcc &A, double a, float xh, float xl) {
-    float ah, al;
-    const bool ok = df_split_trunc(a, ah, al);
+// one term (ah + al)*(xh + xl) of already split operands into A
+__device__ __forceinline__ void df_term_pre(DfAcc &A, float ah, float al, float xh, float xl) {
     const float p = __fmul_rn(ah, xh);
     float e = __fmaf_rn(ah, xh, -p);        // exact: ah*xh = p + e
     e = __fmaf_rn(ah, xl, e);
@@ -245,7 +279,21 @@ __device__ __forceinline__ bool df_term(DfAcc &A, double a, float xh, float xl) 
     two_sum(A.s, p, s, t);
     A.s = s;
     A.c = __fadd_rn(A.c, __fadd_rn(t, e));
+}
+
+// one term a*(xh + xl) into A; returns false when a needs the FP64 path
+// (the term then contributes nothing here and is added by df_fixup)
+__device__ __forceinline__ bool df_term(DfAcc &A, double a, float xh, float xl) {
+    float ah, al;
+    const bool ok = df_split_trunc(a, ah, al);
+    df_term_pre(A, ah, al, xh, xl);
     return ok;
+}
+
+// true when the double is neither infinite nor NaN (exponent field test on
+// the integer pipe)
+__device__ __forceinline__ bool finite_bits(double v) {
+    return ((uint32_t)__double2hiint(v) & 0x7ff00000u) != 0x7ff00000u;
 }
 
 // p0 + p1 with the same operation order on every lane and every s; fb (the
@@ -362,6 +410,74 @@ __device__ __forceinline__ double row_spmv1_df(CA colf, int rs, int re,
     o.c = __shfl_xor_sync(0xffffffffu, a.c, 1);
     const double ofb = __shfl_xor_sync(0xffffffffu, fb, 1);
     return (g == 0) ? df_finish(a, o, fb + ofb) : df_finish(o, a, ofb + fb);
+}
+
+// --------------------------------------------- double-float, pre-split values
+// The df form with the values split once per ensemble (ens_convert_values,
+// ENS_F64_DF: float pairs (hi, lo) by the same truncating split; a value
+// outside the split range is stored as (NaN, 0)).  The terms are the same
+// operations as row_spmv2_df without the per-term split, so every row whose
+// result is finite equals row_spmv2_df bitwise; a non-finite result (a marked
+// value, or a non-finite x or sum) is recomputed by row_spmv2_df from the
+// FP64 values, which keeps the equality in every case.
+template <int S, typename CA>
+__device__ __noinline__ double2 row_spmv2_df_redo(CA colf, int rs, int re, const double *__restrict__ vals,
+                                                  const float2 *__restrict__ x, int g) {
+    return row_spmv2_df<S, XPre, CA>(colf, rs, re, vals, x, g);
+}
+
+template <int S, typename CA>
+__device__ __forceinline__ double2 row_spmv2_dfv(CA colf, int rs, int re, const float2 *__restrict__ vdf,
+                                                 const double *__restrict__ vals,
+                                                 const float2 *__restrict__ x, int g) {
+    DfAcc a0 = df_zero(), a1 = df_zero(), b0 = df_zero(), b1 = df_zero();
+    const int m = 2 * g;
+    int j = rs;
+    for (; j + 4 <= re; j += 4) {
+        const int c0 = colf(j), c1 = colf(j + 1), c2 = colf(j + 2), c3 = colf(j + 3);
+        const float4 v0 = ld_stream(reinterpret_cast<const float4 *>(vdf + (int64_t)j * S + m));
+        const float4 v1 = ld_stream(reinterpret_cast<const float4 *>(vdf + (int64_t)(j + 1) * S + m));
+        const float4 v2 = ld_stream(reinterpret_cast<const float4 *>(vdf + (int64_t)(j + 2) * S + m));
+        const float4 v3 = ld_stream(reinterpret_cast<const float4 *>(vdf + (int64_t)(j + 3) * S + m));
+        const float4 x0 = XPre::two(x, (int64_t)c0 * S + m);
+        const float4 x1 = XPre::two(x, (int64_t)c1 * S + m);
+        const float4 x2 = XPre::two(x, (int64_t)c2 * S + m);
+        const float4 x3 = XPre::two(x, (int64_t)c3 * S + m);
+        df_term_pre(a0, v0.x, v0.y, x0.x, x0.y); df_term_pre(b0, v0.z, v0.w, x0.z, x0.w);
+        df_term_pre(a1, v1.x, v1.y, x1.x, x1.y); df_term_pre(b1, v1.z, v1.w, x1.z, x1.w);
+        df_term_pre(a0, v2.x, v2.y, x2.x, x2.y); df_term_pre(b0, v2.z, v2.w, x2.z, x2.w);
+        df_term_pre(a1, v3.x, v3.y, x3.x, x3.y); df_term_pre(b1, v3.z, v3.w, x3.z, x3.w);
+    }
+    for (; j < re; ++j) {
+        const float4 v = ld_stream(reinterpret_cast<const float4 *>(vdf + (int64_t)j * S + m));
+        const float4 xv = XPre::two(x, (int64_t)colf(j) * S + m);
+        if ((j - rs) & 1) { df_term_pre(a1, v.x, v.y, xv.x, xv.y); df_term_pre(b1, v.z, v.w, xv.z, xv.w); }
+        else { df_term_pre(a0, v.x, v.y, xv.x, xv.y); df_term_pre(b0, v.z, v.w, xv.z, xv.w); }
+    }
+    const double2 y = make_double2(df_finish(a0, a1, 0.0), df_finish(b0, b1, 0.0));
+    if (finite_bits(y.x) && finite_bits(y.y)) return y;
+    return row_spmv2_df_redo<S, CA>(colf, rs, re, vals, x, g);
+}
+
+// s = 1 (2 threads per row, full warps): the recomputation is taken by the
+// whole warp when any of its rows needs it (row_spmv1_df shuffles)
+template <typename CA>
+__device__ __forceinline__ double row_spmv1_dfv(CA colf, int rs, int re, const float2 *__restrict__ vdf,
+                                                const double *__restrict__ vals,
+                                                const float2 *__restrict__ x, int g, bool valid) {
+    DfAcc a = df_zero();
+    if (valid)
+        for (int j = rs + g; j < re; j += 2) {
+            const float2 xv = XPre::one(x, colf(j));
+            const float2 v = ld_stream(vdf + j);
+            df_term_pre(a, v.x, v.y, xv.x, xv.y);
+        }
+    DfAcc o;
+    o.s = __shfl_xor_sync(0xffffffffu, a.s, 1);
+    o.c = __shfl_xor_sync(0xffffffffu, a.c, 1);
+    const double y = (g == 0) ? df_finish(a, o, 0.0) : df_finish(o, a, 0.0);
+    if (!__any_sync(0xffffffffu, !finite_bits(y))) return y;
+    return row_spmv1_df<XPre, CA>(colf, rs, re, vals, x, g, valid);
 }
 
 // ------------------------------------------------- split FP64 / double-float
@@ -492,6 +608,24 @@ __device__ __forceinline__ double2 chunk_spmv_df(const ChunkCols &cc, bool stage
         if (!valid) return make_double2(0.0, 0.0);
         return staged ? row_spmv2_df<S, XS>(ColShared{cc.col, cc.rm[0]}, rs, re, vals, x, g)
                       : row_spmv2_df<S, XS>(ColGlobal{col}, rs, re, vals, x, g);
+    }
+}
+
+template <int S>
+__device__ __forceinline__ double2 chunk_spmv_dfv(const ChunkCols &cc, bool staged,
+                                                  const int32_t *__restrict__ col,
+                                                  const float2 *__restrict__ vdf,
+                                                  const double *__restrict__ vals,
+                                                  const float2 *__restrict__ x, int r, int g, bool valid) {
+    const int rs = valid ? cc.rm[r] : 0, re = valid ? cc.rm[r + 1] : 0;
+    if constexpr (S == 1) {
+        const double v = staged ? row_spmv1_dfv(ColShared{cc.col, cc.rm[0]}, rs, re, vdf, vals, x, g, valid)
+                                : row_spmv1_dfv(ColGlobal{col}, rs, re, vdf, vals, x, g, valid);
+        return make_double2(v, 0.0);
+    } else {
+        if (!valid) return make_double2(0.0, 0.0);
+        return staged ? row_spmv2_dfv<S>(ColShared{cc.col, cc.rm[0]}, rs, re, vdf, vals, x, g)
+                      : row_spmv2_dfv<S>(ColGlobal{col}, rs, re, vdf, vals, x, g);
     }
 }
 

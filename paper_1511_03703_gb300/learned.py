@@ -30,9 +30,11 @@ from paper_1511_03703_gb300 import inputs
 LR0, BETA1, BETA2, EPS, BATCH = 1e-3, 0.9, 0.999, 1e-8, 256
 
 
-def collect(mesh, xi_rows, s=32, tol=1e-8, max_iter=10000, flags=E.CG_SPLIT64, X=None, col0=0):
+def collect(mesh, xi_rows, s=32, tol=1e-8, max_iter=10000, flags=0, presplit=True, X=None, col0=0):
     """Solve the samples xi_rows[m, M] in ensembles of s and return the
-    snapshot matrix X (n x m, FP64, device) and the iteration counts."""
+    snapshot matrix X (n x m, FP64, device) and the iteration counts.
+    presplit: ens_cg_df on a pre-split copy of the values (else ens_cg with
+    `flags`)."""
     import torch
     m = xi_rows.shape[0]
     assert m % s == 0, "number of samples must be a multiple of s"
@@ -41,14 +43,17 @@ def collect(mesh, xi_rows, s=32, tol=1e-8, max_iter=10000, flags=E.CG_SPLIT64, X
         X = torch.empty((mesh.n, m), dtype=torch.float64, device=dev)
     work = torch.empty(E.cg_workspace_size(mesh.n, s), dtype=torch.uint8, device=dev)
     x = torch.empty(mesh.n * s, dtype=torch.float64, device=dev)
+    vdf = torch.empty(2 * mesh.nnz * s, dtype=torch.float32, device=dev) if presplit else None
     vals = b = None
     iters = []
     for j in range(0, m, s):
         xi = torch.from_numpy(inputs.ensemble_layout(xi_rows[j:j + s])).to(dev)
         vals, b = mesh.assemble(s, xi, values=vals, b=b)
+        if presplit:
+            E.convert_values(mesh.graph, s, vals, vdf, dtype=E.F64_DF)
         x.zero_()
         it, rr, st, _ = E.cg(mesh.graph, s, vals, b, x, tol, max_iter, work, flags=flags | E.CG_GRAPH,
-                             check_every=8)
+                             check_every=8, values_df=vdf)
         if any(st):
             raise E.EnsError(max(st), f"training solve {j // s}: member statuses {st}")
         E.snapshots_put(x, X, col0 + j, s)

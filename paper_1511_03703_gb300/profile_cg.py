@@ -1,6 +1,8 @@
 """Profiling driver: one ensemble CG with a fixed iteration count on an N^3 mesh.
 
-    python -m paper_1511_03703_gb300.profile_cg N s iters [dtype]
+    python -m paper_1511_03703_gb300.profile_cg N s iters [form]
+
+form: f64 (default), df, split, or dfv (ens_cg_df on the pre-split values).
 
 Builds the mesh set-up, assembles one ensemble of s samples (M = 10, seed of
 the 64^3 workload) and runs `iters` CG iterations (tolerance 0, so exactly
@@ -17,14 +19,19 @@ from paper_1511_03703_gb300 import inputs
 
 def main(argv):
     N, s, iters = int(argv[1]), int(argv[2]), int(argv[3])
-    flags = int(argv[4]) if len(argv) > 4 else 0
+    form = argv[4] if len(argv) > 4 else "f64"
+    flags = {"f64": 0, "df": E.CG_DF64, "split": E.CG_SPLIT64, "dfv": 0}[form]
     mesh = E.Mesh(N, 10)
     xs = inputs.kl_samples(inputs.SEED_SCALE, 0, s, 10)
     vals, b = mesh.assemble(s, torch.from_numpy(inputs.ensemble_layout(xs)).cuda())
+    vdf = None
+    if form == "dfv":
+        vdf = torch.empty(2 * mesh.nnz * s, dtype=torch.float32, device="cuda")
+        E.convert_values(mesh.graph, s, vals, vdf, dtype=E.F64_DF)
     x = torch.zeros(mesh.n * s, dtype=torch.float64, device="cuda")
     work = torch.empty(E.cg_workspace_size(mesh.n, s), dtype=torch.uint8, device="cuda")
     it, rr, st, stats = E.cg(mesh.graph, s, vals, b, x, 0.0, iters, work, flags=flags,
-                             check_every=iters)
+                             check_every=iters, values_df=vdf)
     torch.cuda.synchronize()
     print("N", N, "s", s, "iters", it[:2], "status", st[:2], "nnz", mesh.nnz, "rows", mesh.n)
 

@@ -91,7 +91,7 @@ def test_autotuner_picks_and_caches(torch, tmp_path, monkeypatch):
     assert autotune.best_form(mesh, 8) == form          # served from the cache
     import json
     db = json.loads((tmp_path / "tune.json").read_text())
-    assert any(k.endswith("|form|12|10|8") for k in db)
+    assert any("|form|12|10|8|" in k for k in db)
     s, f = autotune.best_width(mesh)
     assert s in autotune.WIDTHS and f in autotune.FORMS
     items, _ = make_items(torch, [(6, 4), (8, 8)])
