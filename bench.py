@@ -335,6 +335,31 @@ def shard_first_sample(rank, per_rank):
     return rank * per_rank
 
 
+def rank_xi(rank, per_rank, s):
+    """The KL variables of rank r's shard, one row per ensemble in the
+    commuted layout (per_rank / s ensembles of s members)."""
+    from paper_1511_03703_gb300 import inputs
+    xs = inputs.kl_samples(inputs.SEED_SCALE, shard_first_sample(rank, per_rank), per_rank, M_KL)
+    return np.stack([inputs.ensemble_layout(b) for b in xs.reshape(per_rank // s, s, M_KL)])
+
+
+def max_over_ranks(ms, world, device="cpu"):
+    """Timed-region length of the slowest rank (all-reduce MAX; barrier after)."""
+    if world <= 1:
+        return ms
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.barrier()
+    return float(t.item())
+
+
+def job_throughput(world, steps, per_rank, ms):
+    """Whole-job samples per second: every rank's samples over the slowest rank's time."""
+    return world * steps * per_rank / (ms * 1e-3)
+
+
 def main_ours(args):
     import torch
     world, rank, local = dist_setup()
@@ -350,9 +375,7 @@ def main_ours(args):
     df = args.spmv
     r = Runner(torch, s, BATCH, device, time_spmv=True, df=df)
     if world > 1:  # shard: this rank's own 1024 samples
-        from paper_1511_03703_gb300 import inputs
-        xs = inputs.kl_samples(inputs.SEED_SCALE, shard_first_sample(rank, BATCH), BATCH, M_KL)
-        r.xi_host = np.stack([inputs.ensemble_layout(b) for b in xs.reshape(r.nens, s, M_KL)])
+        r.xi_host = rank_xi(rank, BATCH, s)
         r.xi = torch.from_numpy(r.xi_host).to(device)
     for _ in range(args.warmup):
         r.run_step()
@@ -371,13 +394,8 @@ def main_ours(args):
     ev1.record(stream)
     torch.cuda.synchronize()
     clk = clocks.stop()
-    ms = ev0.elapsed_time(ev1)
-    if world > 1:
-        t = torch.tensor([ms], device=device)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        torch.distributed.barrier()
-        ms = float(t.item())
-    value = world * args.steps * BATCH / (ms * 1e-3)
+    ms = max_over_ranks(ev0.elapsed_time(ev1), world, device)
+    value = job_throughput(world, args.steps, BATCH, ms)
     peak, peak_kind = measured_peaks()
     avg_spmv_ms = r.spmv_ms / max(r.spmv_launches, 1)
     bytes_launch = spmv_bytes(r.n, r.nnz, s)
