@@ -532,6 +532,7 @@ def main_mixed(args):
     v32 = torch.empty(mesh.nnz * s, dtype=torch.float32, device=dev)
     vbf = torch.empty(mesh.nnz * s, dtype=torch.bfloat16, device=dev)
     diag = torch.empty(mesh.n * s, dtype=torch.float32, device=dev)
+    vdf = torch.empty(2 * mesh.nnz * s, dtype=torch.float32, device=dev)  # FP64 comparator: dfv form
     wcg = torch.empty(E.cg_workspace_size(mesh.n, s), dtype=torch.uint8, device=dev)
     wmx = torch.empty(E.cg_mixed_workspace_size(mesh.n, s), dtype=torch.uint8, device=dev)
     peak, _ = measured_peaks()
@@ -551,8 +552,9 @@ def main_mixed(args):
             x = X[g]
             x.zero_()
             if form == "f64":
+                E.convert_values(mesh.graph, s, vals, vdf, dtype=E.F64_DF)
                 it, rr, st, cs = E.cg(mesh.graph, s, vals, b, x, MIX_TOL, 10000, wcg,
-                                      flags=E.CG_SPLIT64 | E.CG_TIME_SPMV, check_every=32)
+                                      flags=E.CG_TIME_SPMV, check_every=32, values_df=vdf)
                 stats["outer"].extend([1] * s)
                 stats["inner"].extend(it)
                 vb = 8
@@ -588,7 +590,8 @@ def main_mixed(args):
             sb = nnz * (vb * s + 4) + 4 * (n + 1) + 2 * 4 * n * s + (4 * n * s if form == "bf16" else 0)
         ms = st["spmv_ms"] / max(st["spmv_n"], 1)
         out[form] = {"value": args.steps * MIX_BATCH / tt, "unit": UNIT,
-                     "spmv": "split f64" if form == "f64" else f"{form} values, f32 accumulation",
+                     "spmv": "f64 (dfv: pre-split double-float)" if form == "f64"
+                     else f"{form} values, f32 accumulation",
                      "spmv_gbs": sb / (ms * 1e-3) / 1e9, "spmv_hbm_frac": sb / (ms * 1e-3) / 1e9 / peak,
                      "outer_mean": float(np.mean(st["outer"])), "inner_mean": float(np.mean(st["inner"])),
                      "max_relres": float(max(st["relres"])), "failed": st["bad"]}
@@ -834,6 +837,81 @@ def main_guess(args):
     print(json.dumps(line))
 
 
+# ------------------------------------------------ coupled CG (Sect. 3.6)
+CPL_SAMPLES = 256
+CPL_WORKLOAD = ("KL diffusion, 64^3 hex Q1 mesh, M=10, 256 samples as ensembles of s = 4, 8, 16, 32, "
+                "CG to 1e-8: coupled (member-summed dots) vs per-member")
+
+
+def main_coupled(args):
+    """Iteration growth of the paper's coupled ensemble CG with s, and what
+    grouping similar samples recovers, against the per-member CG."""
+    import torch
+    import paper_1511_03703_gb300 as E
+    from paper_1511_03703_gb300 import inputs
+    dev = torch.device("cuda:0")
+    E.lib()
+    mesh = E.Mesh(N_MESH, M_KL, device=dev)
+    xs = inputs.kl_samples(inputs.SEED_SCALE, 0, CPL_SAMPLES, M_KL)
+    smax = 32
+    vals = torch.empty(mesh.nnz * smax, dtype=torch.float64, device=dev)
+    vdf = torch.empty(2 * mesh.nnz * smax, dtype=torch.float32, device=dev)
+    b = torch.empty(mesh.n * smax, dtype=torch.float64, device=dev)
+    x = torch.empty(mesh.n * smax, dtype=torch.float64, device=dev)
+    work = torch.empty(E.cg_workspace_size(mesh.n, smax), dtype=torch.uint8, device=dev)
+
+    def solve_all(order, s, coupled):
+        """Iterations per sample (in sample order) and seconds for all samples."""
+        its = np.zeros(CPL_SAMPLES, dtype=np.int64)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for g in range(CPL_SAMPLES // s):
+            idx = order[g * s:(g + 1) * s]
+            xi = torch.from_numpy(inputs.ensemble_layout(xs[idx])).to(dev)
+            v, bb = vals[:mesh.nnz * s], b[:mesh.n * s]
+            mesh.assemble(s, xi, values=v, b=bb)
+            vd = vdf[:2 * mesh.nnz * s]
+            E.convert_values(mesh.graph, s, v, vd, dtype=E.F64_DF)
+            xx = x[:mesh.n * s]
+            xx.zero_()
+            it, rr, st, _ = E.cg(mesh.graph, s, v, bb, xx, TOL, 10000, work,
+                                 flags=E.CG_GRAPH | (E.CG_COUPLED if coupled else 0), check_every=8,
+                                 values_df=vd)
+            if any(st):
+                raise RuntimeError(f"CG status {st}")
+            its[idx] = it
+        torch.cuda.synchronize()
+        return its, time.perf_counter() - t0
+
+    natural = np.arange(CPL_SAMPLES)
+    for _ in range(max(1, args.warmup)):
+        solve_all(natural, 32, True)
+    member_its, _ = solve_all(natural, 32, False)      # per-member counts do not depend on s
+    by_iters = np.argsort(member_its, kind="stable")
+    by_xi1 = np.argsort(xs[:, 0], kind="stable")
+    rows = {}
+    for s in (4, 8, 16, 32):
+        r = {}
+        for name, order, coupled in (("per_member", natural, False), ("coupled", natural, True),
+                                     ("coupled_grouped_by_xi1", by_xi1, True),
+                                     ("coupled_grouped_by_iterations", by_iters, True)):
+            its, sec = solve_all(order, s, coupled)
+            r[name] = {"mean_iterations": float(its.mean()), "max_iterations": int(its.max()),
+                       "sample_solves_per_s": CPL_SAMPLES / sec}
+        r["coupled_iteration_growth"] = r["coupled"]["mean_iterations"] / r["per_member"]["mean_iterations"]
+        rows[str(s)] = r
+    line = {"metric": "coupled ensemble CG (Sect. 3.6) iterations and sample-solves/s vs per-member CG, 1 GB300",
+            "value": rows["32"]["coupled"]["sample_solves_per_s"], "unit": UNIT, "n_gpus": 1, "steps": 1,
+            "warmup": args.warmup, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64 (dfv SpMV)", "data": "synthetic",
+            "config": {"workload": CPL_WORKLOAD, "grouping": "natural order; sorted by xi_1; sorted by the "
+                       "per-member iteration count (best case)"},
+            "per_member_iterations": {"mean": float(member_its.mean()), "min": int(member_its.min()),
+                                      "max": int(member_its.max())},
+            "by_ensemble_size": rows}
+    print(json.dumps(line))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -847,9 +925,10 @@ def main():
                          "pre-split once per ensemble (dfv)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--quick", action="store_true", help="skip the other-form run and the s sweep")
-    ap.add_argument("--workload", default="scale", choices=["scale", "mixed", "batched", "guess"],
+    ap.add_argument("--workload", default="scale", choices=["scale", "mixed", "batched", "guess", "coupled"],
                     help="scale: 64^3 ensemble CG (default line); mixed: 128^3 mixed precision; "
-                         "batched: 16^3..64^3 x s=4..32 in one batch; guess: learned initial guess")
+                         "batched: 16^3..64^3 x s=4..32 in one batch; guess: learned initial guess; "
+                         "coupled: the paper's coupled CG vs per-member CG")
     args = ap.parse_args()
     if args.workload == "mixed" and args.impl != "reference":
         main_mixed(args)
@@ -859,6 +938,9 @@ def main():
         return
     if args.workload == "guess" and args.impl != "reference":
         main_guess(args)
+        return
+    if args.workload == "coupled" and args.impl != "reference":
+        main_coupled(args)
         return
     if args.impl == "reference":
         main_reference(args)

@@ -146,7 +146,8 @@ int ens_spmv(const ens_graph *graph, int s, int dtype, const void *values, const
 /* Per-member inner products (Sect. 3.4: the ensemble inner product computed
  * first as sum_i u_i^T v_i (x) e_i):  out[e] = sum_I u[I*s+e] * v[I*s+e].
  * Deterministic, s-independent order: products are summed in a fixed tree
- * (32-row chunks by butterfly, then groups of 32 chunks, ...).
+ * (the 32 rows of a chunk pairwise, v[i] += v[i + h] for h = 16, 8, 4, 2, 1;
+ * then groups of 32 chunk sums the same way, and so on).
  * work: device scratch of ens_dot_workspace_size bytes (16-byte aligned);
  * its counters are cleared by the call.  out: device double[s]. */
 int ens_dot_workspace_size(int64_t n, int s, size_t *bytes);

@@ -199,14 +199,19 @@ def test_dot_s_invariant_bitwise(torch):
 
 
 # -------------------------------------------------------------------- A6 CG
-def gpu_solve(mesh, xs, tol, max_iter=10000, flags=0, x0=None, check_every=8):
+def gpu_solve(mesh, xs, tol, max_iter=10000, flags=0, x0=None, check_every=8, presplit=False):
+    """presplit: ens_cg_df on the ENS_F64_DF copy of the values."""
     import torch
     s = xs.shape[0]
     vals, b = mesh.assemble(s, to_dev(inputs.ensemble_layout(xs)))
+    vdf = None
+    if presplit:
+        vdf = torch.empty(2 * vals.numel(), dtype=torch.float32, device=gpu())
+        E.convert_values(mesh.graph, s, vals, vdf, dtype=E.F64_DF)
     x = torch.zeros(mesh.n * s, dtype=torch.float64, device=gpu()) if x0 is None else x0.clone()
     work = torch.empty(E.cg_workspace_size(mesh.n, s), dtype=torch.uint8, device=gpu())
     it, rr, st, stats = E.cg(mesh.graph, s, vals, b, x, tol, max_iter, work, flags=flags,
-                             check_every=check_every)
+                             check_every=check_every, values_df=vdf)
     return ens_cols(to_np(x), s), it, rr, st, stats
 
 
@@ -327,6 +332,36 @@ def test_cg_coupled_ensemble(torch):
         assert np.linalg.norm(xc[:, e] - xo) <= 1e-6 * np.linalg.norm(xo)
 
 
+def block_system(rm, col, vals, bs):
+    """The s member systems as one block-diagonal CSR system (members in order)."""
+    n = len(rm) - 1
+    rmb = np.concatenate([np.asarray(rm[:-1]) + e * len(col) for e in range(len(vals))] +
+                         [[len(col) * len(vals)]]).astype(np.int32)
+    colb = np.concatenate([np.asarray(col) + e * n for e in range(len(vals))]).astype(np.int32)
+    return rmb, colb, np.concatenate(vals), np.concatenate(bs)
+
+
+@pytest.mark.parametrize("s", [4, 8])
+def test_cg_coupled_is_cg_on_the_block_system(torch, s):
+    """The coupled ensemble CG of Sect. 3.6 (alpha, beta and the stopping test
+    from member-summed dots) is plain CG on the block-diagonal system of all
+    members: the oracle's CG on that system gives the same iterates."""
+    N, M = 9, 10
+    mesh = E.Mesh(N, M)
+    xs = inputs.kl_samples(57, 0, s, M)
+    xc, itc, rrc, stc, _ = gpu_solve(mesh, xs, 1e-10, flags=E.CG_COUPLED)
+    rm, col, ov, ob = oracle_members(N, M, xs)
+    xo, ito, rro, sto = O.cg(*block_system(rm, col, ov, ob), tol=1e-10)
+    assert stc == [0] * s and sto == 0 and len(set(itc)) == 1
+    if itc[0] != ito:  # rounding decided the stopping test: compare at a fixed count
+        assert abs(itc[0] - ito) == 1
+        k = max(itc[0], ito)
+        xc, itc, _, _, _ = gpu_solve(mesh, xs, 0.0, max_iter=k, flags=E.CG_COUPLED)
+        xo, ito, _, _ = O.cg(*block_system(rm, col, ov, ob), tol=0.0, max_iter=k)
+    Xo = xo.reshape(s, -1).T
+    assert np.linalg.norm(xc - Xo) <= 1e-10 * np.linalg.norm(Xo)
+
+
 def test_error_statuses(torch):
     mesh = E.Mesh(4, 3)
     x = torch.zeros(mesh.n * 4 + 1, dtype=torch.float64, device=gpu())
@@ -366,8 +401,8 @@ def test_scale_64cubed_s32_sampled(torch):
         ref = O.spmv(rm, col, ov[e % 2], xm[e])
         assert np.all(np.abs(Y[:, e] - ref) <= spmv_bound(rm, col, ov[e % 2], xm[e])), e
     # CG of the whole ensemble; two members against oracle solves
-    for flags in (0, E.CG_DF64, E.CG_SPLIT64):
-        xg, it, rr, st, _ = gpu_solve(mesh, xs, 1e-8, flags=flags)
+    for flags, presplit in ((0, False), (E.CG_DF64, False), (E.CG_SPLIT64, False), (0, True)):
+        xg, it, rr, st, _ = gpu_solve(mesh, xs, 1e-8, flags=flags, presplit=presplit)
         assert st == [0] * s and max(rr) < 2e-8
         compare_cg_picked(mesh, xs, picks, rm, col, ov, ob, xg, it)
 
