@@ -227,14 +227,13 @@ class Runner:
 
     def solve_ensemble(self, g, xi=None):
         E = self.E
+        # dfv: double-float assembly that also writes the pre-split copy
         E.assemble(self.graph, self.bmask, self.s, M_KL, self.modes, self.load,
-                   self.xi[g] if xi is None else xi, SIGMA, KAPPA0, self.values, self.b)
-        if self.vdf is not None:
-            E.convert_values(self.graph, self.s, self.values, self.vdf, dtype=E.F64_DF)
-            self.launches += 1
+                   self.xi[g] if xi is None else xi, SIGMA, KAPPA0, self.values, self.b,
+                   values_df=self.vdf)
         x = self.x[g]
         x.zero_()
-        flags = (E.CG_TIME_SPMV if self.time_spmv else 0) | form_flag(self.df)
+        flags = (E.CG_TIME_SPMV if self.time_spmv else 0) | form_flag(self.df) | E.CG_X0_ZERO
         it, rr, st, stats = E.cg(self.graph, self.s, self.values, self.b, x, TOL, 10000, self.work,
                                  flags=flags, check_every=16, values_df=self.vdf)
         self.launches += 2 + stats.kernel_launches
@@ -548,13 +547,14 @@ def main_mixed(args):
         E.kl_setup(N, M, L_CORR, mesh.kl_table, want_host=False)
         E.mode_matrices(N, mesh.graph, M, mesh.kl_table, mesh.modes, mesh.load)
         for g in range(nens):
-            mesh.assemble(s, xi[g], values=vals, b=b)
+            if form != "f64":
+                mesh.assemble(s, xi[g], values=vals, b=b)
             x = X[g]
             x.zero_()
             if form == "f64":
-                E.convert_values(mesh.graph, s, vals, vdf, dtype=E.F64_DF)
+                mesh.assemble(s, xi[g], values=vals, b=b, values_df=vdf)  # double-float assembly + split
                 it, rr, st, cs = E.cg(mesh.graph, s, vals, b, x, MIX_TOL, 10000, wcg,
-                                      flags=E.CG_TIME_SPMV, check_every=32, values_df=vdf)
+                                      flags=E.CG_TIME_SPMV | E.CG_X0_ZERO, check_every=32, values_df=vdf)
                 stats["outer"].extend([1] * s)
                 stats["inner"].extend(it)
                 vb = 8
@@ -779,17 +779,16 @@ def main_guess(args):
     def run(learned):
         iters, fb, launches = [], 0, 0
         for xi in xis:
-            mesh.assemble(s, xi, values=vals, b=b)
-            E.convert_values(mesh.graph, s, vals, vdf, dtype=E.F64_DF)
-            launches += 3
+            mesh.assemble(s, xi, values=vals, b=b, values_df=vdf)
+            launches += 2
             if learned:
                 g.predict(xi, s, x)
                 launches += 5
             else:
                 x.zero_()
             it, rr, st, stats = E.cg(mesh.graph, s, vals, b, x, TOL, 10000, work,
-                                     flags=flags | (E.CG_GUESS_FALLBACK if learned else 0), check_every=8,
-                                     values_df=vdf)
+                                     flags=flags | (E.CG_GUESS_FALLBACK if learned else E.CG_X0_ZERO),
+                                     check_every=8, values_df=vdf)
             if any(st):
                 raise RuntimeError(f"CG status {st}")
             iters += it
@@ -869,14 +868,13 @@ def main_coupled(args):
             idx = order[g * s:(g + 1) * s]
             xi = torch.from_numpy(inputs.ensemble_layout(xs[idx])).to(dev)
             v, bb = vals[:mesh.nnz * s], b[:mesh.n * s]
-            mesh.assemble(s, xi, values=v, b=bb)
             vd = vdf[:2 * mesh.nnz * s]
-            E.convert_values(mesh.graph, s, v, vd, dtype=E.F64_DF)
+            mesh.assemble(s, xi, values=v, b=bb, values_df=vd)
             xx = x[:mesh.n * s]
             xx.zero_()
             it, rr, st, _ = E.cg(mesh.graph, s, v, bb, xx, TOL, 10000, work,
-                                 flags=E.CG_GRAPH | (E.CG_COUPLED if coupled else 0), check_every=8,
-                                 values_df=vd)
+                                 flags=E.CG_GRAPH | E.CG_X0_ZERO | (E.CG_COUPLED if coupled else 0),
+                                 check_every=8, values_df=vd)
             if any(st):
                 raise RuntimeError(f"CG status {st}")
             its[idx] = it

@@ -130,6 +130,20 @@ int ens_assemble(const ens_graph *graph, const uint8_t *bmask, int s, int M,
                  const double *modes, const double *load, const double *xi, double sigma,
                  double kappa0, double *values, double *b, void *stream);
 
+/* ens_assemble with the KL terms in double-float arithmetic on the FP32
+ * pipe: sum_k (sigma*xi_k) modes_k (k >= 1) is formed from float pairs as in
+ * the ENS_F64_DF SpMV and summed as a float pair, and each value is
+ * kappa0*modes_0 + that sum by one FP64 FMA (coefficients or mode values
+ * outside [2^-103, 2^128) use the FP64 combination).  The KL terms carry a
+ * relative error of about 2^-46 each, so values agree with ens_assemble to
+ * within 1e-14 of their row's diagonal for sigma = 0.1 (measured 4e-15).
+ * values_df (float2[nnz*s], may be NULL): also writes the ENS_F64_DF split
+ * of values, bitwise what ens_convert_values(..., ENS_F64_DF, ...) would
+ * write, for ens_cg_df.  16-byte aligned for s > 1. */
+int ens_assemble_df(const ens_graph *graph, const uint8_t *bmask, int s, int M,
+                    const double *modes, const double *load, const double *xi, double sigma,
+                    double kappa0, double *values, void *values_df, double *b, void *stream);
+
 /* --------------------------------------------------------------- A4 SpMV */
 /* y = A_c x for the commuted ensemble matrix (Fig. 5 semantics):
  *   y[I*s+e] = sum_{entry in row I} values[entry*s+e] * x[col_entry[entry]*s+e].
@@ -195,11 +209,14 @@ enum {
                                 arithmetic and every dot stays FP64 */
     ENS_CG_SPLIT64 = 16,     /* CG SpMV with alternate entries FP64 FMA / double-float
                                 (see ENS_F64_SPLIT); takes precedence over ENS_CG_DF64 */
-    ENS_CG_GUESS_FALLBACK = 32 /* zero-guess fallback for a supplied start x0 (a learned
+    ENS_CG_GUESS_FALLBACK = 32, /* zero-guess fallback for a supplied start x0 (a learned
                                 guess, not in the paper): a member whose ||b - A x0||
                                 is not below ||b|| (or is not finite) restarts from
                                 x = 0, so its iterates are exactly those of a zero-guess
                                 solve; counted in ens_cg_stats.guess_fallbacks */
+    ENS_CG_X0_ZERO = 64      /* the caller states that x holds zeros on entry: r0 = b is
+                                taken without the initial SpMV (the result is the same,
+                                bitwise, as computing b - A*0) */
 };
 
 /* Unpreconditioned CG (Hestenes-Stiefel) on each member of the ensemble

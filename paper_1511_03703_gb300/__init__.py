@@ -14,13 +14,13 @@ import threading
 __all__ = ["EnsError", "lib", "Graph", "Mesh", "mesh_sizes", "graph_build", "kl_table_size",
            "kl_setup", "mode_matrices", "assemble", "spmv", "dot", "dot_workspace_size", "dot_static", "cg",
            "cg_workspace_size", "CgStats", "Batch", "convert_values", "cg_mixed", "cg_mixed_workspace_size", "F64", "F32", "BF16", "CG_COUPLED", "CG_GRAPH",
-           "CG_TIME_SPMV", "CG_DF64", "CG_SPLIT64", "CG_GUESS_FALLBACK", "F64_DF", "F64_SPLIT",
+           "CG_TIME_SPMV", "CG_DF64", "CG_SPLIT64", "CG_GUESS_FALLBACK", "CG_X0_ZERO", "F64_DF", "F64_SPLIT",
            "snapshots_put", "pod", "pod_workspace_size", "pod_targets", "to_f32", "mlp_param_count",
            "mlp_init", "mlp_workspace_size", "mlp_forward", "mlp_grad", "mlp_adam", "mlp_train",
            "guess", "guess_workspace_size", "MLP_DIMS"]
 
 F64, F32, BF16, F64_DF, F64_SPLIT = 0, 1, 2, 3, 4
-CG_COUPLED, CG_GRAPH, CG_TIME_SPMV, CG_DF64, CG_SPLIT64, CG_GUESS_FALLBACK = 1, 2, 4, 8, 16, 32
+CG_COUPLED, CG_GRAPH, CG_TIME_SPMV, CG_DF64, CG_SPLIT64, CG_GUESS_FALLBACK, CG_X0_ZERO = 1, 2, 4, 8, 16, 32, 64
 MLP_DIMS = (10, 256, 256, 64)
 OK, ERR_NOT_CONVERGED, ERR_BREAKDOWN = 0, 5, 6
 
@@ -92,6 +92,7 @@ def _declare(L):
         "ens_kl_setup": (I, [I, I, d, vp, vp, vp, vp]),
         "ens_mode_matrices": (I, [I, P(EnsGraphC), I, vp, vp, vp, vp]),
         "ens_assemble": (I, [P(EnsGraphC), vp, I, I, vp, vp, vp, d, d, vp, vp, vp]),
+        "ens_assemble_df": (I, [P(EnsGraphC), vp, I, I, vp, vp, vp, d, d, vp, vp, vp, vp]),
         "ens_spmv": (I, [P(EnsGraphC), I, I, vp, vp, vp, vp]),
         "ens_dot_workspace_size": (I, [i64, I, P(sz)]),
         "ens_dot": (I, [i64, I, vp, vp, vp, vp, sz, vp]),
@@ -214,10 +215,17 @@ def mode_matrices(N, graph, M, kl_table, modes, load, stream=None):
                                    _stream(stream)))
 
 
-def assemble(graph, bmask, s, M, modes, load, xi, sigma, kappa0, values, b, stream=None):
-    _require_cuda(bmask, modes, load, xi, values, b)
-    _check(lib().ens_assemble(graph.ref(), _ptr(bmask), s, M, _ptr(modes), _ptr(load), _ptr(xi),
-                              sigma, kappa0, _ptr(values), _ptr(b), _stream(stream)))
+def assemble(graph, bmask, s, M, modes, load, xi, sigma, kappa0, values, b, stream=None, df=False,
+             values_df=None):
+    """ens_assemble; df=True (or a values_df tensor, 2*nnz*s float32) runs
+    ens_assemble_df, which also writes the pre-split copy into values_df."""
+    _require_cuda(bmask, modes, load, xi, values, b, values_df)
+    if df or values_df is not None:
+        _check(lib().ens_assemble_df(graph.ref(), _ptr(bmask), s, M, _ptr(modes), _ptr(load), _ptr(xi),
+                                     sigma, kappa0, _ptr(values), _ptr(values_df), _ptr(b), _stream(stream)))
+    else:
+        _check(lib().ens_assemble(graph.ref(), _ptr(bmask), s, M, _ptr(modes), _ptr(load), _ptr(xi),
+                                  sigma, kappa0, _ptr(values), _ptr(b), _stream(stream)))
 
 
 # ------------------------------------------------------------ linear algebra
@@ -493,8 +501,10 @@ class Mesh:
         self.load = torch.empty(n, dtype=torch.float64, device=dev)
         mode_matrices(N, self.graph, M, self.kl_table, self.modes, self.load, stream)
 
-    def assemble(self, s, xi_ens, sigma=0.1, kappa0=1.0, values=None, b=None, stream=None):
-        """xi_ens: device float64[M*s] (commuted layout).  Returns (values, b)."""
+    def assemble(self, s, xi_ens, sigma=0.1, kappa0=1.0, values=None, b=None, stream=None, df=False,
+                 values_df=None):
+        """xi_ens: device float64[M*s] (commuted layout).  Returns (values, b).
+        df / values_df: see assemble()."""
         import torch
         dev = self.row_map.device
         if values is None:
@@ -502,5 +512,5 @@ class Mesh:
         if b is None:
             b = torch.empty(self.n * s, dtype=torch.float64, device=dev)
         assemble(self.graph, self.bmask, s, self.M, self.modes, self.load, xi_ens, sigma, kappa0,
-                 values, b, stream)
+                 values, b, stream, df=df, values_df=values_df)
         return values, b

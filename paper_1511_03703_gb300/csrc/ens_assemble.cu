@@ -9,7 +9,7 @@
 // remains per ensemble is M+1 fused multiply-adds per value, with the
 // ensemble dimension contiguous so each mode value is read once per entry and
 // used by all s members, and the output written as packed 16-byte stores.
-#include "ens_internal.cuh"
+#include "ens_spmv.cuh"
 
 namespace ens {
 
@@ -46,13 +46,93 @@ __global__ void __launch_bounds__(256) assemble_values_kernel(
     }
 }
 
+// The same combination with the KL terms in double-float arithmetic on the
+// FP32 pipe (GB300 runs FP64 FMAs at 1/64 of the FP32 rate): each
+// coefficient sigma*xi_k is split into a rounded float pair, each mode value
+// by truncation (47 bits), the terms c_k m_k (k >= 1) are formed as in the
+// double-float SpMV and summed as an unevaluated float pair, and the value is
+// kappa0 * m_0 + (that sum) by one FP64 FMA.  Two FP64 operations per value
+// instead of M + 1; the KL terms carry a relative error of about 2^-46 each.
+// A mode value or coefficient outside the split range [2^-103, 2^128) (or
+// not finite) makes the thread (the whole CTA, for a coefficient) compute
+// its values in FP64 instead.  With vdf the values' truncating split (the
+// ENS_F64_DF copy for ens_cg_df) is written as well.
+template <int S>
+__global__ void __launch_bounds__(256) assemble_values_df_kernel(
+    int64_t nnz, int M, const double *__restrict__ modes, const double *__restrict__ xi,
+    double sigma, double kappa0, double *__restrict__ values, float2 *__restrict__ vdf) {
+    __shared__ float2 coef[kAsmMaxCoef];  // rounded split of coef[k*S + e], k >= 1
+    __shared__ double coef64[kAsmMaxCoef];
+    __shared__ int coef_bad;
+    if (threadIdx.x == 0) coef_bad = 0;
+    __syncthreads();
+    for (int i = threadIdx.x; i < (M + 1) * S; i += blockDim.x) {
+        const double c = (i < S) ? kappa0 : sigma * xi[i - S];
+        const float h = (float)c;
+        const float l = (float)(c - (double)h);
+        const double a = fabs(c);
+        if (i >= S && !(c == 0.0 || (a >= 0x1p-103 && a < 0x1p+127))) coef_bad = 1;
+        coef[i] = make_float2(h, l);
+        coef64[i] = c;
+    }
+    __syncthreads();
+    constexpr int G = (S == 1) ? 1 : S / 2;
+    constexpr int W = (S == 1) ? 1 : 2;  // members per thread
+    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t e = t / G;
+    const int g = (int)(t % G);
+    if (e >= nnz) return;
+    const int m0 = (S == 1) ? 0 : 2 * g;
+    DfAcc A[W];
+    bool ok = coef_bad == 0;
+#pragma unroll
+    for (int w = 0; w < W; ++w) A[w] = df_zero();
+    for (int k = 1; k <= M; ++k) {
+        const double mk = __ldg(modes + (int64_t)k * nnz + e);
+        float mh, ml;
+        ok &= df_split_trunc(mk, mh, ml);
+#pragma unroll
+        for (int w = 0; w < W; ++w) {
+            const float2 c = coef[k * S + m0 + w];
+            df_term_pre(A[w], mh, ml, c.x, c.y);
+        }
+    }
+    const double mz = __ldg(modes + e);
+    double v[W];
+#pragma unroll
+    for (int w = 0; w < W; ++w) v[w] = fma(coef64[m0 + w], mz, f2d_exact(A[w].s) + f2d_exact(A[w].c));
+    if (!ok) {  // FP64 combination, in the order of assemble_values_kernel
+#pragma unroll
+        for (int w = 0; w < W; ++w) {
+            double x = coef64[m0 + w] * mz;
+            for (int k = 1; k <= M; ++k) x = fma(coef64[k * S + m0 + w], __ldg(modes + (int64_t)k * nnz + e), x);
+            v[w] = x;
+        }
+    }
+    if constexpr (S == 1) {
+        values[e] = v[0];
+    } else {
+        reinterpret_cast<double2 *>(values)[e * G + g] = make_double2(v[0], v[1]);
+    }
+    if (vdf) {
+        float2 p[W];
+#pragma unroll
+        for (int w = 0; w < W; ++w) {
+            float h, l;
+            p[w] = df_split_trunc(v[w], h, l) ? make_float2(h, l) : make_float2(__int_as_float(0x7fc00000), 0.0f);
+        }
+        if constexpr (S == 1) vdf[e] = p[0];
+        else reinterpret_cast<float4 *>(vdf)[e * G + g] = make_float4(p[0].x, p[0].y, p[1].x, p[1].y);
+    }
+}
+
 // thread per (row, member): right-hand side and the Dirichlet identity rows
 template <int S>
 __global__ void assemble_rows_kernel(int32_t n, const int32_t *__restrict__ row_map,
                                      const int32_t *__restrict__ col_entry,
                                      const uint8_t *__restrict__ bmask,
                                      const double *__restrict__ load, double *__restrict__ values,
-                                     double *__restrict__ b) {
+                                     double *__restrict__ b, float2 *__restrict__ vdf) {
     const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     const int64_t I = t / S;
     const int e = (int)(t % S);
@@ -60,29 +140,57 @@ __global__ void assemble_rows_kernel(int32_t n, const int32_t *__restrict__ row_
     b[t] = load[I];
     if (bmask[I]) {
         for (int32_t p = row_map[I]; p < row_map[I + 1]; ++p)
-            if (col_entry[p] == I) values[(int64_t)p * S + e] = 1.0;
+            if (col_entry[p] == I) {
+                values[(int64_t)p * S + e] = 1.0;
+                if (vdf) vdf[(int64_t)p * S + e] = make_float2(1.0f, 0.0f);
+            }
     }
 }
 
 template <int S>
 static int assemble_s(const ens_graph *g, const uint8_t *bmask, int M, const double *modes,
                       const double *load, const double *xi, double sigma, double kappa0,
-                      double *values, double *b, cudaStream_t st) {
+                      double *values, double *b, bool df, float2 *vdf, cudaStream_t st) {
     constexpr int G = (S == 1) ? 1 : S / 2;
     const int bs = 256;
     const int64_t nthr = g->num_entries * G;
     if (nthr > 0) {
-        assemble_values_kernel<S><<<(unsigned)((nthr + bs - 1) / bs), bs, 0, st>>>(
-            g->num_entries, M, modes, xi, sigma, kappa0, values);
+        if (df)
+            assemble_values_df_kernel<S><<<(unsigned)((nthr + bs - 1) / bs), bs, 0, st>>>(
+                g->num_entries, M, modes, xi, sigma, kappa0, values, vdf);
+        else
+            assemble_values_kernel<S><<<(unsigned)((nthr + bs - 1) / bs), bs, 0, st>>>(
+                g->num_entries, M, modes, xi, sigma, kappa0, values);
         ENS_LAUNCH_CHECK("assemble_values_kernel");
     }
     const int64_t nr = (int64_t)g->num_rows * S;
     if (nr > 0) {
         assemble_rows_kernel<S><<<(unsigned)((nr + bs - 1) / bs), bs, 0, st>>>(
-            g->num_rows, g->row_map, g->col_entry, bmask, load, values, b);
+            g->num_rows, g->row_map, g->col_entry, bmask, load, values, b, vdf);
         ENS_LAUNCH_CHECK("assemble_rows_kernel");
     }
     return ENS_OK;
+}
+
+static int assemble_entry(const ens_graph *graph, const uint8_t *bmask, int s, int M, const double *modes,
+                          const double *load, const double *xi, double sigma, double kappa0, double *values,
+                          double *b, bool df, float2 *vdf, void *stream) {
+    int rc = check_graph(graph);
+    if (rc) return rc;
+    if (!supported_s(s)) return fail(ENS_ERR_UNSUPPORTED, "ensemble size s=%d not in {1,4,8,16,32}", s);
+    if (M < 0 || M > 64) return fail(ENS_ERR_UNSUPPORTED, "M=%d outside [0, 64]", M);
+    if (!bmask || !modes || !load || !values || !b || (M > 0 && !xi))
+        return fail(ENS_ERR_ARG, "NULL pointer argument");
+    if (s > 1 && (!aligned16(values) || !aligned16(b) || (vdf && !aligned16(vdf))))
+        return fail(ENS_ERR_ALIGN, "values/b/values_df must be 16-byte aligned");
+    cudaStream_t st = as_stream(stream);
+    switch (s) {
+        case 1: return assemble_s<1>(graph, bmask, M, modes, load, xi, sigma, kappa0, values, b, df, vdf, st);
+        case 4: return assemble_s<4>(graph, bmask, M, modes, load, xi, sigma, kappa0, values, b, df, vdf, st);
+        case 8: return assemble_s<8>(graph, bmask, M, modes, load, xi, sigma, kappa0, values, b, df, vdf, st);
+        case 16: return assemble_s<16>(graph, bmask, M, modes, load, xi, sigma, kappa0, values, b, df, vdf, st);
+        default: return assemble_s<32>(graph, bmask, M, modes, load, xi, sigma, kappa0, values, b, df, vdf, st);
+    }
 }
 
 }  // namespace ens
@@ -93,20 +201,13 @@ extern "C" int ens_assemble(const ens_graph *graph, const uint8_t *bmask, int s,
                             const double *modes, const double *load, const double *xi,
                             double sigma, double kappa0, double *values, double *b,
                             void *stream) {
-    int rc = check_graph(graph);
-    if (rc) return rc;
-    if (!supported_s(s)) return fail(ENS_ERR_UNSUPPORTED, "ensemble size s=%d not in {1,4,8,16,32}", s);
-    if (M < 0 || M > 64) return fail(ENS_ERR_UNSUPPORTED, "M=%d outside [0, 64]", M);
-    if (!bmask || !modes || !load || !values || !b || (M > 0 && !xi))
-        return fail(ENS_ERR_ARG, "NULL pointer argument");
-    if (s > 1 && (!aligned16(values) || !aligned16(b)))
-        return fail(ENS_ERR_ALIGN, "values/b must be 16-byte aligned");
-    cudaStream_t st = as_stream(stream);
-    switch (s) {
-        case 1: return assemble_s<1>(graph, bmask, M, modes, load, xi, sigma, kappa0, values, b, st);
-        case 4: return assemble_s<4>(graph, bmask, M, modes, load, xi, sigma, kappa0, values, b, st);
-        case 8: return assemble_s<8>(graph, bmask, M, modes, load, xi, sigma, kappa0, values, b, st);
-        case 16: return assemble_s<16>(graph, bmask, M, modes, load, xi, sigma, kappa0, values, b, st);
-        default: return assemble_s<32>(graph, bmask, M, modes, load, xi, sigma, kappa0, values, b, st);
-    }
+    return assemble_entry(graph, bmask, s, M, modes, load, xi, sigma, kappa0, values, b, false, nullptr, stream);
+}
+
+extern "C" int ens_assemble_df(const ens_graph *graph, const uint8_t *bmask, int s, int M,
+                               const double *modes, const double *load, const double *xi,
+                               double sigma, double kappa0, double *values, void *values_df, double *b,
+                               void *stream) {
+    return assemble_entry(graph, bmask, s, M, modes, load, xi, sigma, kappa0, values, b, true,
+                          static_cast<float2 *>(values_df), stream);
 }

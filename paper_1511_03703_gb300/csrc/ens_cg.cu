@@ -53,6 +53,7 @@ struct CgArgs {
     int max_iter;
     int coupled;
     int fallback;  // restart from x = 0 members whose ||b - A x0|| >= ||b||
+    int x0_zero;   // the caller states x0 = 0: r0 = b without the initial SpMV
     uint32_t pf_cap;       // bytes of each chunk's value block prefetched into L2 by K1
     uint64_t val_bytes;    // size of the value array read by K1 (8 bytes per value in every form)
 };
@@ -90,8 +91,11 @@ __global__ void __launch_bounds__(RowMap<S>::THREADS, 1024 / RowMap<S>::THREADS)
     const int r = threadIdx.x / G, g = threadIdx.x % G;
     const int64_t R = (int64_t)blockIdx.x * 32 + r;
     __shared__ ChunkCols cc;
-    const bool staged = stage_chunk(cc, a.row_map, a.col, blockIdx.x, a.n);
-    const double2 axv = chunk_spmv<S, double>(cc, staged, a.col, a.vals, a.x, r, g, R < a.n);
+    double2 axv = make_double2(0.0, 0.0);  // A x0 = 0 when the caller states x0 = 0
+    if (!a.x0_zero) {
+        const bool staged = stage_chunk(cc, a.row_map, a.col, blockIdx.x, a.n);
+        axv = chunk_spmv<S, double>(cc, staged, a.col, a.vals, a.x, r, g, R < a.n);
+    }
     double rr0 = 0.0, rr1 = 0.0, bb0 = 0.0, bb1 = 0.0;
     if constexpr (S == 1) {
         const double ax = axv.x;
@@ -376,6 +380,34 @@ __global__ void __launch_bounds__(RowMap<S>::THREADS, K1Occ<S, MODE>::THREADS_PE
 
 
 // ------------------------------------------------------------------ K2
+// v*v of an FP64 value as an unevaluated float pair: v split by truncation
+// into hi + lo (47 bits), hi*hi exact by FMA error recovery, 2 hi lo added to
+// the error term (lo*lo, below 2^-46 |v*v|, is dropped); values outside the
+// split range square in FP64 and round to a pair (out of line, so that the
+// FP64 instructions stay off the common path)
+__device__ __noinline__ float2 df_square_wide(double v) {
+    const double q = v * v;
+    const float qh = (float)q;
+    return make_float2(qh, (float)(q - (double)qh));
+}
+
+__device__ __forceinline__ float2 df_square(double v) {
+    float hi, lo;
+    if (!df_split_trunc(v, hi, lo)) return df_square_wide(v);
+    const float p = __fmul_rn(hi, hi);
+    float e = __fmaf_rn(hi, hi, -p);
+    e = __fmaf_rn(2.0f * hi, lo, e);
+    return make_float2(p, e);
+}
+
+// (a.x + a.y) + (b.x + b.y) as a float pair: TwoSum of the leading parts,
+// the trailing parts and the rounding error summed
+__device__ __forceinline__ float2 df_add(float2 a, float2 b) {
+    float s, t;
+    two_sum(a.x, b.x, s, t);
+    return make_float2(s, __fadd_rn(__fadd_rn(a.y, b.y), t));
+}
+
 template <int S, int TH>
 __device__ __forceinline__ void k2_body(const CgArgs &a, int cta,
                                         double (*sm)[32][S + 1] /* [CPC][32][S+1] */) {
@@ -391,28 +423,32 @@ __device__ __forceinline__ void k2_body(const CgArgs &a, int cta,
     const double al0 = cs->alpha[m];
     const double al1 = (S == 1) ? 0.0 : cs->alpha[m + 1];
     const int64_t first_chunk = (int64_t)cta * VM::CPC;
+    // r.r: squares and the chunk's 32-row tree in double-float on the FP32
+    // pipe (the FP64 pipe keeps only the r update); the chunk sums enter the
+    // FP64 dot tree above the chunk
+    float2(*sf)[32][S + 1] = reinterpret_cast<float2(*)[32][S + 1]>(sm);
 #pragma unroll
     for (int pass = 0; pass < VM::PASSES; ++pass) {
         const int c = pass * VM::CPP + cip;
         const int64_t R = (first_chunk + c) * 32 + r;
-        double v0 = 0.0, v1 = 0.0;
+        float2 v0 = make_float2(0.f, 0.f), v1 = make_float2(0.f, 0.f);
         if (R < a.n) {
             if constexpr (S == 1) {
                 double rv = a.r[R];
                 if (act0) { rv = fma(-al0, a.q[R], rv); a.r[R] = rv; }
-                v0 = rv * rv;
+                v0 = df_square(rv);
             } else {
                 double2 rv = reinterpret_cast<const double2 *>(a.r)[R * VG + g];
                 const double2 qv = reinterpret_cast<const double2 *>(a.q)[R * VG + g];
                 if (act0) rv.x = fma(-al0, qv.x, rv.x);
                 if (act1) rv.y = fma(-al1, qv.y, rv.y);
                 if (act0 || act1) reinterpret_cast<double2 *>(a.r)[R * VG + g] = rv;
-                v0 = rv.x * rv.x;
-                v1 = rv.y * rv.y;
+                v0 = df_square(rv.x);
+                v1 = df_square(rv.y);
             }
         }
-        sm[c][r][m] = v0;
-        if constexpr (S > 1) sm[c][r][m + 1] = v1;
+        sf[c][r][m] = v0;
+        if constexpr (S > 1) sf[c][r][m + 1] = v1;
     }
     __syncthreads();
     // halving tree over the 32 rows of every chunk, all members packed
@@ -420,14 +456,14 @@ __device__ __forceinline__ void k2_body(const CgArgs &a, int cta,
     for (int h = 16; h >= 1; h >>= 1) {
         for (int it = threadIdx.x; it < VM::CPC * h * S; it += VM::THREADS) {
             const int c = it / (h * S), rem = it % (h * S), i = rem / S, e = rem % S;
-            sm[c][i][e] += sm[c][i + h][e];
+            sf[c][i][e] = df_add(sf[c][i][e], sf[c][i + h][e]);
         }
         __syncthreads();
     }
     for (int it = threadIdx.x; it < VM::CPC * S; it += VM::THREADS) {
         const int c = it / S, e = it % S;
         const int64_t ch = first_chunk + c;
-        if (ch < a.t1.count[1]) a.t1.buf[1][ch * S + e] = sm[c][0][e];
+        if (ch < a.t1.count[1]) a.t1.buf[1][ch * S + e] = f2d_exact(sf[c][0][e].x) + f2d_exact(sf[c][0][e].y);
     }
     const int nitems = (int)min((int64_t)VM::CPC, a.t1.count[1] - first_chunk);
     if (!dot_tree_propagate(a.t1, first_chunk, nitems)) return;
@@ -642,6 +678,7 @@ static int cg_run(const ens_graph *g, const double *vals, const float2 *vdf, con
     a.max_iter = max_iter;
     a.coupled = (flags & ENS_CG_COUPLED) ? 1 : 0;
     a.fallback = (flags & ENS_CG_GUESS_FALLBACK) ? 1 : 0;
+    a.x0_zero = (flags & ENS_CG_X0_ZERO) ? 1 : 0;
     a.pf_cap = l2_prefetch_cap(MODE);
     a.val_bytes = (uint64_t)g->num_entries * S * 8u;
     const unsigned grid = (unsigned)a.t1.count[1];
@@ -894,6 +931,7 @@ static void cg_layout_args(CgArgs &a, const ens_graph *g, int S, const double *v
     a.max_iter = max_iter;
     a.coupled = (flags & ENS_CG_COUPLED) ? 1 : 0;
     a.fallback = (flags & ENS_CG_GUESS_FALLBACK) ? 1 : 0;
+    a.x0_zero = (flags & ENS_CG_X0_ZERO) ? 1 : 0;
     a.pf_cap = 0;
     a.val_bytes = 0;
 }

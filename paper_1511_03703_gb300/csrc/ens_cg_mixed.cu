@@ -200,6 +200,7 @@ struct MxArgs {
     double tol;
     float inner_tol;
     int max_outer, max_inner;
+    uint64_t vlo_bytes;  // size of the low-precision value array (L2 prefetch bound)
 };
 
 // ------------------------------------------------------------------ MR
@@ -337,7 +338,9 @@ __global__ void __launch_bounds__(RowMap<S>::THREADS, 1536 / RowMap<S>::THREADS)
     __shared__ float sm[32][S + 1];
     const int r = threadIdx.x / G, g = threadIdx.x % G;
     const int64_t R = (int64_t)blockIdx.x * 32 + r;
-    const bool staged = stage_chunk(cc, a.row_map, a.col, blockIdx.x, a.n);
+    // the chunk's value block is prefetched into L2 while its columns are staged
+    const bool staged = stage_chunk_pf(cc, a.row_map, a.col, blockIdx.x, a.n, a.vlo, S * (uint32_t)sizeof(V),
+                                       a.vlo_bytes, 0xffffffffu);
     const float2 ap = chunk_spmv_f32<S, V>(cc, staged, a.col, static_cast<const V *>(a.vlo), a.diag,
                                            a.pf, r, g, R, R < a.n);
     float v0 = 0.f, v1 = 0.f;
@@ -531,6 +534,7 @@ static int mx_run(const ens_graph *g, const double *v64, const void *vlo, const 
     a.inner_tol = (float)inner_tol;
     a.max_outer = max_outer;
     a.max_inner = max_inner;
+    a.vlo_bytes = (uint64_t)g->num_entries * S * sizeof(V);
     const unsigned grid = (unsigned)a.t32.count[1];
     int rc;
     if ((rc = dot_tree_clear(a.t64, st))) return rc;

@@ -33,8 +33,8 @@ LR0, BETA1, BETA2, EPS, BATCH = 1e-3, 0.9, 0.999, 1e-8, 256
 def collect(mesh, xi_rows, s=32, tol=1e-8, max_iter=10000, flags=0, presplit=True, X=None, col0=0):
     """Solve the samples xi_rows[m, M] in ensembles of s and return the
     snapshot matrix X (n x m, FP64, device) and the iteration counts.
-    presplit: ens_cg_df on a pre-split copy of the values (else ens_cg with
-    `flags`)."""
+    presplit: double-float assembly with its pre-split copy and ens_cg_df
+    (else FP64 assembly and ens_cg with `flags`)."""
     import torch
     m = xi_rows.shape[0]
     assert m % s == 0, "number of samples must be a multiple of s"
@@ -48,12 +48,10 @@ def collect(mesh, xi_rows, s=32, tol=1e-8, max_iter=10000, flags=0, presplit=Tru
     iters = []
     for j in range(0, m, s):
         xi = torch.from_numpy(inputs.ensemble_layout(xi_rows[j:j + s])).to(dev)
-        vals, b = mesh.assemble(s, xi, values=vals, b=b)
-        if presplit:
-            E.convert_values(mesh.graph, s, vals, vdf, dtype=E.F64_DF)
+        vals, b = mesh.assemble(s, xi, values=vals, b=b, values_df=vdf)  # df assembly when presplit
         x.zero_()
-        it, rr, st, _ = E.cg(mesh.graph, s, vals, b, x, tol, max_iter, work, flags=flags | E.CG_GRAPH,
-                             check_every=8, values_df=vdf)
+        it, rr, st, _ = E.cg(mesh.graph, s, vals, b, x, tol, max_iter, work,
+                             flags=flags | E.CG_GRAPH | E.CG_X0_ZERO, check_every=8, values_df=vdf)
         if any(st):
             raise E.EnsError(max(st), f"training solve {j // s}: member statuses {st}")
         E.snapshots_put(x, X, col0 + j, s)

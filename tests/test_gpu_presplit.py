@@ -113,3 +113,85 @@ def test_cg_df_argument_errors(torch):
     with pytest.raises(E.EnsError) as ei:
         E.convert_values(mesh.graph, 4, vals, vdf, diag_lo=x.float(), dtype=E.F64_DF)
     assert ei.value.code == 1
+
+
+# ------------------------------------------------- double-float assembly
+def diag_of(row_map, col, vals):
+    n = len(row_map) - 1
+    rows = np.repeat(np.arange(n), np.diff(row_map))
+    d = np.zeros(n)
+    sel = col == rows
+    d[rows[sel]] = vals[sel]
+    return d[rows]
+
+
+@pytest.mark.parametrize("N,s", [(5, 1), (5, 4), (8, 8), (5, 32), (13, 16)])
+def test_assemble_df_matches_oracle_and_writes_the_split(torch, N, s):
+    import oracle as O
+    from helpers import oracle_members
+    M = 10
+    mesh = E.Mesh(N, M)
+    xs = inputs.kl_samples(900 + N, 0, s, M)
+    xi = to_dev(inputs.ensemble_layout(xs))
+    vdf = torch.empty(2 * mesh.nnz * s, dtype=torch.float32, device=gpu())
+    vals, b = mesh.assemble(s, xi, values_df=vdf)
+    V = to_np(vals).reshape(-1, s)
+    rm, col, ov, ob = oracle_members(N, M, xs)
+    for e in range(s):
+        assert np.all(np.abs(V[:, e] - ov[e]) <= 1e-13 * np.abs(diag_of(rm, col, ov[e]))), e
+    # the split is exactly what the conversion of these values writes
+    assert torch.equal(vdf, split_pairs(torch, mesh.graph, s, vals))
+    # FP64 assembly: the two agree to the double-float error of the KL terms
+    # (mode values truncated to 47 bits, the terms summed as float pairs; the
+    # kappa0 term is an FP64 FMA)
+    v64, b64 = mesh.assemble(s, xi)
+    assert torch.equal(b64, b)
+    d = np.abs(to_np(v64).reshape(-1, s) - V)
+    worst = max(float(np.max(d[:, e] / np.abs(diag_of(rm, col, ov[e])))) for e in range(s))
+    print(f"df assembly vs FP64: max |dA| / A_II = {worst:.2e}")
+    assert worst <= 1e-14
+
+
+def test_assemble_df_s_invariant_and_fp64_fallback(torch):
+    N, M = 6, 10
+    mesh = E.Mesh(N, M)
+    xs = inputs.kl_samples(950, 0, 32, M)
+    ref = None
+    for s in (1, 4, 8, 16, 32):
+        vals, _ = mesh.assemble(s, to_dev(inputs.ensemble_layout(xs[:s])), df=True)
+        v0 = to_np(vals).reshape(-1, s)[:, 0].copy()
+        ref = v0 if ref is None else ref
+        assert np.array_equal(v0, ref), s
+    # coefficients outside the split range: the FP64 combination, bitwise
+    xi = to_dev(inputs.ensemble_layout(xs[:4]))
+    vd, _ = mesh.assemble(4, xi, sigma=1e200, df=True)
+    v64, _ = mesh.assemble(4, xi, sigma=1e200)
+    assert torch.equal(vd, v64)
+
+
+def test_cg_df_on_df_assembly_matches_oracle(torch):
+    import oracle as O
+    from helpers import oracle_members
+    N, M, s = 10, 10, 8
+    mesh = E.Mesh(N, M)
+    xs = inputs.kl_samples(960, 0, s, M)
+    vdf = torch.empty(2 * mesh.nnz * s, dtype=torch.float32, device=gpu())
+    vals, b = mesh.assemble(s, to_dev(inputs.ensemble_layout(xs)), values_df=vdf)
+    x, it, rr, st, _ = run(torch, mesh, s, vals, b, E.CG_GRAPH, values_df=vdf, tol=1e-10)
+    assert st == [0] * s and max(rr) <= 1.01e-10
+    X = x.reshape(-1, s)
+    rm, col, ov, ob = oracle_members(N, M, xs)
+    for e in range(s):
+        xo = O.cg(rm, col, ov[e], ob[e], tol=1e-13)[0]
+        assert np.linalg.norm(X[:, e] - xo) <= 1e-8 * np.linalg.norm(xo), e
+
+
+@pytest.mark.parametrize("presplit", [False, True])
+def test_x0_zero_flag_is_bitwise_the_plain_start(torch, presplit):
+    s = 8
+    mesh, vals, b = ensemble(torch, 9, s, 970)
+    vdf = split_pairs(torch, mesh.graph, s, vals) if presplit else None
+    fl = 0 if presplit else E.CG_SPLIT64
+    x1, it1, rr1, st1, s1 = run(torch, mesh, s, vals, b, fl, values_df=vdf)
+    x2, it2, rr2, st2, s2 = run(torch, mesh, s, vals, b, fl | E.CG_X0_ZERO, values_df=vdf)
+    assert it1 == it2 and rr1 == rr2 and np.array_equal(x1, x2)
