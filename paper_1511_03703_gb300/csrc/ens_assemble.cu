@@ -9,6 +9,8 @@
 // remains per ensemble is M+1 fused multiply-adds per value, with the
 // ensemble dimension contiguous so each mode value is read once per entry and
 // used by all s members, and the output written as packed 16-byte stores.
+#include <algorithm>
+
 #include "ens_spmv.cuh"
 
 namespace ens {
@@ -57,6 +59,16 @@ __global__ void __launch_bounds__(256) assemble_values_kernel(
 // not finite) makes the thread (the whole CTA, for a coefficient) compute
 // its values in FP64 instead.  With vdf the values' truncating split (the
 // ENS_F64_DF copy for ens_cg_df) is written as well.
+// one member's value by the FP64 combination of assemble_values_kernel (out
+// of line: the rare path of the double-float kernel)
+static __device__ __noinline__ double asm_value_fp64(const double *coef, int stride, int M,
+                                                     const double *__restrict__ modes, int64_t nnz,
+                                                     int64_t e) {
+    double x = coef[0] * __ldg(modes + e);
+    for (int k = 1; k <= M; ++k) x = fma(coef[k * stride], __ldg(modes + (int64_t)k * nnz + e), x);
+    return x;
+}
+
 template <int S>
 __global__ void __launch_bounds__(256) assemble_values_df_kernel(
     int64_t nnz, int M, const double *__restrict__ modes, const double *__restrict__ xi,
@@ -76,53 +88,64 @@ __global__ void __launch_bounds__(256) assemble_values_df_kernel(
         coef64[i] = c;
     }
     __syncthreads();
-    constexpr int G = (S == 1) ? 1 : S / 2;
-    constexpr int W = (S == 1) ? 1 : 2;  // members per thread
-    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    const int64_t e = t / G;
-    const int g = (int)(t % G);
-    if (e >= nnz) return;
-    const int m0 = (S == 1) ? 0 : 2 * g;
-    DfAcc A[W];
-    bool ok = coef_bad == 0;
+    // W members per thread (up to 8): each mode value is split once for W
+    // members, so the split's integer work is spread over more terms
+    constexpr int W = (S < 8) ? S : 8;
+    constexpr int G = S / W;  // threads per entry
+    const int64_t total = nnz * G;
+    // grid-stride over (entry, member group): the coefficient split above is
+    // done once per CTA
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t e = t / G;
+        const int g = (int)(t % G);
+        const int m0 = g * W;
+        DfAcc A[W];
+        bool ok = coef_bad == 0;
 #pragma unroll
-    for (int w = 0; w < W; ++w) A[w] = df_zero();
-    for (int k = 1; k <= M; ++k) {
-        const double mk = __ldg(modes + (int64_t)k * nnz + e);
-        float mh, ml;
-        ok &= df_split_trunc(mk, mh, ml);
+        for (int w = 0; w < W; ++w) A[w] = df_zero();
+        for (int k = 1; k <= M; ++k) {
+            const double mk = __ldg(modes + (int64_t)k * nnz + e);
+            float mh, ml;
+            ok &= df_split_trunc(mk, mh, ml);
 #pragma unroll
-        for (int w = 0; w < W; ++w) {
-            const float2 c = coef[k * S + m0 + w];
-            df_term_pre(A[w], mh, ml, c.x, c.y);
+            for (int w = 0; w < W; ++w) {
+                const float2 c = coef[k * S + m0 + w];
+                df_term_pre(A[w], mh, ml, c.x, c.y);
+            }
         }
-    }
-    const double mz = __ldg(modes + e);
-    double v[W];
+        const double mz = __ldg(modes + e);
+        double v[W];
 #pragma unroll
-    for (int w = 0; w < W; ++w) v[w] = fma(coef64[m0 + w], mz, f2d_exact(A[w].s) + f2d_exact(A[w].c));
-    if (!ok) {  // FP64 combination, in the order of assemble_values_kernel
+        for (int w = 0; w < W; ++w) v[w] = fma(coef64[m0 + w], mz, f2d_exact(A[w].s) + f2d_exact(A[w].c));
+        if (!ok) {  // FP64 combination, in the order of assemble_values_kernel
 #pragma unroll
-        for (int w = 0; w < W; ++w) {
-            double x = coef64[m0 + w] * mz;
-            for (int k = 1; k <= M; ++k) x = fma(coef64[k * S + m0 + w], __ldg(modes + (int64_t)k * nnz + e), x);
-            v[w] = x;
+            for (int w = 0; w < W; ++w) v[w] = asm_value_fp64(coef64 + m0 + w, S, M, modes, nnz, e);
         }
-    }
-    if constexpr (S == 1) {
-        values[e] = v[0];
-    } else {
-        reinterpret_cast<double2 *>(values)[e * G + g] = make_double2(v[0], v[1]);
-    }
-    if (vdf) {
-        float2 p[W];
+        double *vo = values + e * S + m0;
+        if constexpr (W == 1) {
+            vo[0] = v[0];
+        } else {
 #pragma unroll
-        for (int w = 0; w < W; ++w) {
-            float h, l;
-            p[w] = df_split_trunc(v[w], h, l) ? make_float2(h, l) : make_float2(__int_as_float(0x7fc00000), 0.0f);
+            for (int w = 0; w < W; w += 2) reinterpret_cast<double2 *>(vo)[w / 2] = make_double2(v[w], v[w + 1]);
         }
-        if constexpr (S == 1) vdf[e] = p[0];
-        else reinterpret_cast<float4 *>(vdf)[e * G + g] = make_float4(p[0].x, p[0].y, p[1].x, p[1].y);
+        if (vdf) {
+            float2 p[W];
+#pragma unroll
+            for (int w = 0; w < W; ++w) {
+                float h, l;
+                p[w] = df_split_trunc(v[w], h, l) ? make_float2(h, l)
+                                                  : make_float2(__int_as_float(0x7fc00000), 0.0f);
+            }
+            float2 *po = vdf + e * S + m0;
+            if constexpr (W == 1) {
+                po[0] = p[0];
+            } else {
+#pragma unroll
+                for (int w = 0; w < W; w += 2)
+                    reinterpret_cast<float4 *>(po)[w / 2] = make_float4(p[w].x, p[w].y, p[w + 1].x, p[w + 1].y);
+            }
+        }
     }
 }
 
@@ -156,7 +179,7 @@ static int assemble_s(const ens_graph *g, const uint8_t *bmask, int M, const dou
     const int64_t nthr = g->num_entries * G;
     if (nthr > 0) {
         if (df)
-            assemble_values_df_kernel<S><<<(unsigned)((nthr + bs - 1) / bs), bs, 0, st>>>(
+            assemble_values_df_kernel<S><<<(unsigned)std::min<int64_t>((nthr + bs - 1) / bs, 152 * 6), bs, 0, st>>>(
                 g->num_entries, M, modes, xi, sigma, kappa0, values, vdf);
         else
             assemble_values_kernel<S><<<(unsigned)((nthr + bs - 1) / bs), bs, 0, st>>>(

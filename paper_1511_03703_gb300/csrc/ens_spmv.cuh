@@ -259,13 +259,17 @@ __device__ __forceinline__ float2 df_split_vec(double v, bool &ok) {
 }
 
 // Exact float -> double by moving the bit fields (no FP64-pipe conversion);
-// zero, subnormal and non-finite inputs take the hardware conversion.
+// zero, infinity and NaN by bits as well, subnormal floats (rare) out of
+// line by the hardware conversion.
+static __device__ __noinline__ double f2d_subnormal(float f) { return (double)f; }
+
 __device__ __forceinline__ double f2d_exact(float f) {
     const uint32_t u = __float_as_uint(f);
-    const uint32_t e = (u >> 23) & 0xffu;
-    if (e == 0u || e == 0xffu) return (double)f;
-    const uint32_t hi = (u & 0x80000000u) | ((e + 896u) << 20) | ((u & 0x7fffffu) >> 3);
-    const uint32_t lo = u << 29;
+    const uint32_t e = (u >> 23) & 0xffu, man = u & 0x7fffffu;
+    if (e == 0u && man != 0u) return f2d_subnormal(f);
+    const uint32_t de = (e == 0u) ? 0u : ((e == 0xffu) ? 0x7ffu : e + 896u);
+    const uint32_t hi = (u & 0x80000000u) | (de << 20) | (man >> 3);
+    const uint32_t lo = man << 29;
     return __hiloint2double((int)hi, (int)lo);
 }
 

@@ -2,7 +2,8 @@
 
     python -m paper_1511_03703_gb300.profile_cg N s iters [form]
 
-form: f64 (default), df, split, or dfv (ens_cg_df on the pre-split values).
+form: f64 (default), df, split, or dfv (double-float assembly with its
+pre-split copy, then ens_cg_df).
 
 Builds the mesh set-up, assembles one ensemble of s samples (M = 10, seed of
 the 64^3 workload) and runs `iters` CG iterations (tolerance 0, so exactly
@@ -23,11 +24,11 @@ def main(argv):
     flags = {"f64": 0, "df": E.CG_DF64, "split": E.CG_SPLIT64, "dfv": 0}[form]
     mesh = E.Mesh(N, 10)
     xs = inputs.kl_samples(inputs.SEED_SCALE, 0, s, 10)
-    vals, b = mesh.assemble(s, torch.from_numpy(inputs.ensemble_layout(xs)).cuda())
+    xi = torch.from_numpy(inputs.ensemble_layout(xs)).cuda()
     vdf = None
-    if form == "dfv":
+    if form == "dfv":  # double-float assembly writing the pre-split copy, as in the benchmark
         vdf = torch.empty(2 * mesh.nnz * s, dtype=torch.float32, device="cuda")
-        E.convert_values(mesh.graph, s, vals, vdf, dtype=E.F64_DF)
+    vals, b = mesh.assemble(s, xi, values_df=vdf)
     x = torch.zeros(mesh.n * s, dtype=torch.float64, device="cuda")
     work = torch.empty(E.cg_workspace_size(mesh.n, s), dtype=torch.uint8, device="cuda")
     it, rr, st, stats = E.cg(mesh.graph, s, vals, b, x, 0.0, iters, work, flags=flags,
