@@ -45,7 +45,7 @@ def spmv_bytes(n, nnz, s, vbytes=8):
 
 def kernel_source_hash():
     h = hashlib.sha256()
-    for f in ("ens_spmv.cuh", "ens_cg.cu", "ens_internal.cuh"):
+    for f in ("ens_spmv.cuh", "ens_cg_kernels.cuh", "ens_cg.cu", "ens_internal.cuh"):
         h.update(open(os.path.join(ROOT, "paper_1511_03703_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
 
@@ -910,6 +910,80 @@ def main_coupled(args):
     print(json.dumps(line))
 
 
+# --------------------------------------------- preconditioned CG (NEXT-2)
+PCG_SAMPLES = 256
+PCG_WORKLOAD = ("KL diffusion, 64^3 hex Q1 mesh, M=10, 256 samples as 8 ensembles of s=32, CG to 1e-8: "
+                "plain vs Jacobi- and Chebyshev-preconditioned ensemble CG (FP64 SpMV form)")
+
+
+def main_pcg(args):
+    """Iterations, SpMVs per solve and sample-solves/s of the preconditioned
+    ensemble CG against the plain one, all in the FP64 SpMV form (the
+    preconditioned solver is FP64 throughout); the pre-split plain CG is
+    reported for reference."""
+    import torch
+    import paper_1511_03703_gb300 as E
+    from paper_1511_03703_gb300 import inputs
+    dev = torch.device("cuda:0")
+    E.lib()
+    s = 32
+    mesh = E.Mesh(N_MESH, M_KL, device=dev)
+    xs = inputs.kl_samples(inputs.SEED_SCALE, 0, PCG_SAMPLES, M_KL)
+    xis = [torch.from_numpy(inputs.ensemble_layout(xs[j:j + s])).to(dev) for j in range(0, PCG_SAMPLES, s)]
+    vals = torch.empty(mesh.nnz * s, dtype=torch.float64, device=dev)
+    vdf = torch.empty(2 * mesh.nnz * s, dtype=torch.float32, device=dev)
+    b = torch.empty(mesh.n * s, dtype=torch.float64, device=dev)
+    x = torch.empty(mesh.n * s, dtype=torch.float64, device=dev)
+    wcg = torch.empty(E.cg_workspace_size(mesh.n, s), dtype=torch.uint8, device=dev)
+    wpc = torch.empty(E.pcg_workspace_size(mesh.n, s), dtype=torch.uint8, device=dev)
+    v0 = torch.from_numpy(np.stack([inputs.random_vector(500 + e, mesh.n) for e in range(s)], axis=1)
+                          .reshape(-1)).to(dev)
+    forms = [("cg_f64", None, 0), ("cg_dfv", None, 0), ("pcg_jacobi", E.PC_JACOBI, 0)] + \
+        [(f"pcg_chebyshev{d}", E.PC_CHEBYSHEV, d) for d in (2, 3, 4)]
+
+    def run(name, pc, deg):
+        its, lams = [], []
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for xi in xis:
+            mesh.assemble(s, xi, values=vals, b=b, values_df=vdf if name == "cg_dfv" else None)
+            x.zero_()
+            fl = E.CG_GRAPH | E.CG_X0_ZERO
+            if pc is None:
+                it, rr, st, _ = E.cg(mesh.graph, s, vals, b, x, TOL, 10000, wcg, flags=fl, check_every=8,
+                                     values_df=vdf if name == "cg_dfv" else None)
+            else:
+                it, rr, st, lam, _ = E.pcg(mesh.graph, s, vals, b, x, TOL, 10000, wpc, precond=pc,
+                                           degree=max(deg, 1), power_iters=10, power_start=v0, flags=fl,
+                                           check_every=8)
+                lams += lam
+            if any(st):
+                raise RuntimeError(f"{name}: status {st}")
+            its += it
+        torch.cuda.synchronize()
+        return its, time.perf_counter() - t0, lams
+
+    out = {}
+    for name, pc, deg in forms:
+        for _ in range(args.warmup):
+            run(name, pc, deg)
+        its, sec, lams = run(name, pc, deg)
+        spmv = 1 + (deg - 1 if deg >= 2 else 0)
+        out[name] = {"mean_iterations": float(np.mean(its)), "max_iterations": int(np.max(its)),
+                     "spmv_per_iteration": spmv, "mean_spmv_per_solve": float(np.mean(its)) * spmv,
+                     "sample_solves_per_s": PCG_SAMPLES / sec}
+        if lams:
+            out[name]["lambda_max_D^-1A_mean"] = float(np.mean(lams))
+    line = {"metric": "preconditioned ensemble CG sample-solves/s and iterations vs plain ensemble CG, 1 GB300",
+            "value": max(v["sample_solves_per_s"] for k, v in out.items() if k.startswith("pcg")), "unit": UNIT,
+            "n_gpus": 1, "steps": 1, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": PCG_WORKLOAD, "chebyshev": "interval [lam/30, lam], lam = 1.1 x a 10-step "
+                       "power estimate of the largest eigenvalue of D^-1 A"},
+            "forms": out}
+    print(json.dumps(line))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -923,10 +997,10 @@ def main():
                          "pre-split once per ensemble (dfv)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--quick", action="store_true", help="skip the other-form run and the s sweep")
-    ap.add_argument("--workload", default="scale", choices=["scale", "mixed", "batched", "guess", "coupled"],
+    ap.add_argument("--workload", default="scale", choices=["scale", "mixed", "batched", "guess", "coupled", "pcg"],
                     help="scale: 64^3 ensemble CG (default line); mixed: 128^3 mixed precision; "
                          "batched: 16^3..64^3 x s=4..32 in one batch; guess: learned initial guess; "
-                         "coupled: the paper's coupled CG vs per-member CG")
+                         "coupled: the paper's coupled CG vs per-member CG; pcg: preconditioned CG")
     args = ap.parse_args()
     if args.workload == "mixed" and args.impl != "reference":
         main_mixed(args)
@@ -939,6 +1013,9 @@ def main():
         return
     if args.workload == "coupled" and args.impl != "reference":
         main_coupled(args)
+        return
+    if args.workload == "pcg" and args.impl != "reference":
+        main_pcg(args)
         return
     if args.impl == "reference":
         main_reference(args)

@@ -249,6 +249,30 @@ int ens_cg_df(const ens_graph *graph, int s, const double *values, const void *v
               int32_t *iters_host, double *relres_host, int32_t *status_host, ens_cg_stats *stats_host,
               void *stream);
 
+/* ------------------------------------- preconditioned ensemble CG */
+/* Not in the paper as a standalone solver: its CG is preconditioned by
+ * multigrid whose smoothers are order-2 Chebyshev polynomials (Sect. 3.5).
+ * Per member, PCG (Hestenes-Stiefel with z = M^-1 r, rho = r.z, stop when
+ * ||r|| <= tol ||b||) with
+ *   ENS_PC_JACOBI     z = D^-1 r (D the diagonal of A);
+ *   ENS_PC_CHEBYSHEV  z = p(D^-1 A) D^-1 r: `degree` steps (1..8) of Chebyshev
+ *                     iteration for A z = r from z = 0 on [lam/ratio, lam]
+ *                     (Saad, Iterative Methods, Sect. 12.3), lam = boost x an
+ *                     estimate of the largest eigenvalue of D^-1 A: power_iters
+ *                     steps v <- D^-1 A v / ||D^-1 A v|| from power_start (device,
+ *                     commuted layout n*s) and the quotient v.Av / v.Dv.
+ * FP64 values and arithmetic (the ENS_F64 SpMV).  flags: ENS_CG_GRAPH,
+ * ENS_CG_X0_ZERO.  lam_host[s] (may be NULL) receives the estimates (0 for
+ * Jacobi).  Other arguments and outputs as ens_cg; work:
+ * ens_pcg_workspace_size bytes.  Synchronises `stream`. */
+enum { ENS_PC_JACOBI = 1, ENS_PC_CHEBYSHEV = 2 };
+int ens_pcg_workspace_size(int32_t num_rows, int s, size_t *bytes);
+int ens_pcg(const ens_graph *graph, int s, const double *values, const double *b, double *x, double tol,
+            int max_iter, int precond, int degree, double ratio, double boost, int power_iters,
+            const double *power_start, int flags, int check_every, void *work, size_t work_bytes,
+            int32_t *iters_host, double *relres_host, int32_t *status_host, double *lam_host,
+            ens_cg_stats *stats_host, void *stream);
+
 /* ---------------------------------------------------- A8 batched CG */
 /* One ensemble of a batch: its graph (by value), size s, values, rhs, x (in:
  * x0, out: solution) and optional host outputs iters/relres/status [s]. */

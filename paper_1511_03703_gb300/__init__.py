@@ -17,7 +17,8 @@ __all__ = ["EnsError", "lib", "Graph", "Mesh", "mesh_sizes", "graph_build", "kl_
            "CG_TIME_SPMV", "CG_DF64", "CG_SPLIT64", "CG_GUESS_FALLBACK", "CG_X0_ZERO", "F64_DF", "F64_SPLIT",
            "snapshots_put", "pod", "pod_workspace_size", "pod_targets", "to_f32", "mlp_param_count",
            "mlp_init", "mlp_workspace_size", "mlp_forward", "mlp_grad", "mlp_adam", "mlp_train",
-           "guess", "guess_workspace_size", "MLP_DIMS"]
+           "guess", "guess_workspace_size", "MLP_DIMS", "pcg", "pcg_workspace_size", "PC_JACOBI",
+           "PC_CHEBYSHEV"]
 
 F64, F32, BF16, F64_DF, F64_SPLIT = 0, 1, 2, 3, 4
 CG_COUPLED, CG_GRAPH, CG_TIME_SPMV, CG_DF64, CG_SPLIT64, CG_GUESS_FALLBACK, CG_X0_ZERO = 1, 2, 4, 8, 16, 32, 64
@@ -100,6 +101,9 @@ def _declare(L):
         "ens_cg_workspace_size": (I, [i32, I, P(sz)]),
         "ens_cg": (I, [P(EnsGraphC), I, vp, vp, vp, d, I, I, I, vp, sz, vp, vp, vp, P(CgStats), vp]),
         "ens_cg_df": (I, [P(EnsGraphC), I, vp, vp, vp, vp, d, I, I, I, vp, sz, vp, vp, vp, P(CgStats), vp]),
+        "ens_pcg_workspace_size": (I, [i32, I, P(sz)]),
+        "ens_pcg": (I, [P(EnsGraphC), I, vp, vp, vp, d, I, I, I, d, d, I, vp, I, I, vp, sz, vp, vp, vp, vp,
+                        P(CgStats), vp]),
         "ens_convert_values": (I, [P(EnsGraphC), I, vp, I, vp, vp, vp]),
         "ens_cg_batched_workspace_size": (I, [I, P(BatchItemC), P(sz)]),
         "ens_cg_batched": (I, [I, P(BatchItemC), d, I, I, I, vp, sz, P(CgStats), vp]),
@@ -289,6 +293,33 @@ def cg(graph, s, values, b, x, tol, max_iter, work, flags=0, check_every=8, stre
     if rc not in (0, ERR_NOT_CONVERGED, ERR_BREAKDOWN) or (rc and raise_on_failure):
         _check(rc)
     return list(it), list(rr), list(stt), stats
+
+
+# ------------------------------------------------------ preconditioned CG
+PC_JACOBI, PC_CHEBYSHEV = 1, 2
+
+
+def pcg_workspace_size(n, s):
+    v = ctypes.c_size_t()
+    _check(lib().ens_pcg_workspace_size(n, s, ctypes.byref(v)))
+    return v.value
+
+
+def pcg(graph, s, values, b, x, tol, max_iter, work, precond=PC_JACOBI, degree=2, ratio=30.0, boost=1.1,
+        power_iters=10, power_start=None, flags=0, check_every=8, stream=None):
+    """Runs ens_pcg; returns (iters[s], relres[s], status[s], lam[s], CgStats).  Synchronises."""
+    _require_cuda(values, b, x, work, power_start)
+    it = (ctypes.c_int32 * s)()
+    rr = (ctypes.c_double * s)()
+    stt = (ctypes.c_int32 * s)()
+    lam = (ctypes.c_double * s)()
+    stats = CgStats()
+    rc = lib().ens_pcg(graph.ref(), s, _ptr(values), _ptr(b), _ptr(x), tol, max_iter, precond, degree, ratio,
+                       boost, power_iters, _ptr(power_start), flags, check_every, _ptr(work),
+                       work.numel() * work.element_size(), it, rr, stt, lam, ctypes.byref(stats), _stream(stream))
+    if rc not in (0, ERR_NOT_CONVERGED, ERR_BREAKDOWN):
+        _check(rc)
+    return list(it), list(rr), list(stt), list(lam), stats
 
 
 # ------------------------------------------------------------- batched CG

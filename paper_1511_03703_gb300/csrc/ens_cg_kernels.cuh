@@ -1,0 +1,578 @@
+// ens_cg_kernels.cuh -- device side of the ensemble CG: state, arguments and
+// the K0/KZ/K1/K2/K3/KF kernels (shared by ens_cg.cu and ens_pcg.cu).
+#pragma once
+#include "ens_spmv.cuh"
+
+namespace ens {
+
+
+struct CgState {
+    double rho[32], alpha[32], beta[32], bnorm[32], relres[32];
+    int active[32], updx[32], zerox[32], iters[32], status[32], fb[32];
+    int active_count, updx_any, zero_any, spmv_real;
+    int df_bad_any, fb_count, pad1, pad2;
+    double bnorm_all;
+};
+
+struct CgArgs {
+    int32_t n;
+    const int32_t *row_map;
+    const int32_t *col;
+    const double *vals;
+    const float2 *vdf;  // values pre-split into float pairs (MODE 3), else NULL
+    const double *b;
+    double *x, *r, *p, *q;
+    float2 *pdf;  // p split into float pairs (df modes)
+    CgState *st;
+    DotTree t1;   // width s
+    DotTree t2;   // width 2s
+    double tol;
+    int max_iter;
+    int coupled;
+    int fallback;  // restart from x = 0 members whose ||b - A x0|| >= ||b||
+    int x0_zero;   // the caller states x0 = 0: r0 = b without the initial SpMV
+    uint32_t pf_cap;       // bytes of each chunk's value block prefetched into L2 by K1
+    uint64_t val_bytes;    // size of the value array read by K1 (8 bytes per value in every form)
+};
+
+// mapping of the streaming vector kernels (K2, K3): a CTA of TH threads owns
+// CPC chunks, CPP of them at a time
+template <int S, int TH = (S == 32) ? 512 : 256>
+struct VecMap {
+    static constexpr int VG = (S == 1) ? 1 : S / 2;            // threads per row
+    static constexpr int CHUNK_T = 32 * VG;                    // threads per chunk
+    static constexpr int THREADS = TH;
+    static constexpr int CPP = THREADS / CHUNK_T;              // chunks per pass
+    static constexpr int CPC0 = (S >= 16) ? 4 : 8;
+    static constexpr int CPC = (CPC0 > CPP) ? CPC0 : CPP;      // chunks per CTA
+    static constexpr int PASSES = CPC / CPP;
+};
+
+__device__ __forceinline__ void store_split(float2 *pdf, int64_t i, double v0, double v1, int *bad) {
+    bool ok0, ok1;
+    const float2 a = df_split_vec(v0, ok0), b = df_split_vec(v1, ok1);
+    reinterpret_cast<float4 *>(pdf)[i >> 1] = make_float4(a.x, a.y, b.x, b.y);
+    if (!ok0 || !ok1) *bad = 1;
+}
+__device__ __forceinline__ void store_split1(float2 *pdf, int64_t i, double v, int *bad) {
+    bool ok;
+    pdf[i] = df_split_vec(v, ok);
+    if (!ok) *bad = 1;
+}
+
+// ------------------------------------------------------------------ K0
+template <int S, int MODE>
+__global__ void __launch_bounds__(RowMap<S>::THREADS, 1024 / RowMap<S>::THREADS) cg_init_kernel(CgArgs a) {
+    constexpr int G = RowMap<S>::G;
+    __shared__ double sm[32][S + 1];
+    const int r = threadIdx.x / G, g = threadIdx.x % G;
+    const int64_t R = (int64_t)blockIdx.x * 32 + r;
+    __shared__ ChunkCols cc;
+    double2 axv = make_double2(0.0, 0.0);  // A x0 = 0 when the caller states x0 = 0
+    if (!a.x0_zero) {
+        const bool staged = stage_chunk(cc, a.row_map, a.col, blockIdx.x, a.n);
+        axv = chunk_spmv<S, double>(cc, staged, a.col, a.vals, a.x, r, g, R < a.n);
+    }
+    double rr0 = 0.0, rr1 = 0.0, bb0 = 0.0, bb1 = 0.0;
+    if constexpr (S == 1) {
+        const double ax = axv.x;
+        if (R < a.n) {
+            const double bv = a.b[R];
+            const double res = bv - ax;
+            if (g == 0) {
+                a.r[R] = res;
+                a.p[R] = res;
+                if (MODE != 0) store_split1(a.pdf, R, res, &a.st->df_bad_any);
+            }
+            rr0 = res * res;
+            bb0 = bv * bv;
+        }
+    } else if (R < a.n) {
+        const double2 ax = axv;
+        const double2 bv = reinterpret_cast<const double2 *>(a.b)[R * G + g];
+        const double2 res = make_double2(bv.x - ax.x, bv.y - ax.y);
+        reinterpret_cast<double2 *>(a.r)[R * G + g] = res;
+        reinterpret_cast<double2 *>(a.p)[R * G + g] = res;
+        if (MODE != 0) store_split(a.pdf, R * S + 2 * g, res.x, res.y, &a.st->df_bad_any);
+        rr0 = res.x * res.x; rr1 = res.y * res.y;
+        bb0 = bv.x * bv.x; bb1 = bv.y * bv.y;
+    }
+    chunk_tree<S>(sm, rr0, rr1, r, g, a.t2, blockIdx.x, 0);
+    chunk_tree<S>(sm, bb0, bb1, r, g, a.t2, blockIdx.x, S);
+    if (!dot_tree_propagate(a.t2, blockIdx.x, 1)) return;
+    if (threadIdx.x >= 32) return;
+    // epilogue: one lane per member (s <= 32); member sums in member order
+    const unsigned FULL = 0xffffffffu;
+    const int e = threadIdx.x;
+    const double *top = a.t2.buf[a.t2.levels];
+    CgState *st = a.st;
+    const double rrx = (e < S) ? ld_cg(top + e) : 0.0, bb = (e < S) ? ld_cg(top + S + e) : 0.0;
+    // zero-guess fallback: a start no better than x = 0 (or not finite) is
+    // replaced by x = 0, r = p = b, whose r.r is b.b in the same tree order
+    const bool fbk = a.fallback && e < S && bb != 0.0 && !(rrx < bb);
+    const double rr = fbk ? bb : rrx;
+    double rsum = 0.0, bsum = 0.0;
+    for (int k = 0; k < S; ++k) {
+        rsum += __shfl_sync(FULL, rr, k);
+        bsum += __shfl_sync(FULL, bb, k);
+    }
+    const double bn = sqrt(bb);
+    int act = 0, zx = fbk ? 1 : 0;
+    if (!a.coupled) {
+        if (bb == 0.0) zx = 1;
+        else act = (sqrt(rr) <= a.tol * bn) ? 0 : 1;
+    } else {
+        const bool all_zero = (bsum == 0.0);
+        act = (all_zero || sqrt(rsum) <= a.tol * sqrt(bsum)) ? 0 : 1;
+        zx = (all_zero || fbk) ? 1 : 0;
+    }
+    int status = ENS_OK;
+    if (a.max_iter == 0 && act) { act = 0; status = ENS_ERR_NOT_CONVERGED; }
+    if (e < S) {
+        st->rho[e] = rr;
+        st->bnorm[e] = bn;
+        st->alpha[e] = 0.0; st->beta[e] = 0.0; st->relres[e] = 0.0;
+        st->iters[e] = 0; st->updx[e] = 0; st->zerox[e] = zx; st->status[e] = status;
+        st->active[e] = act;
+        st->fb[e] = fbk ? 1 : 0;
+    } else {
+        act = 0; zx = 0;
+    }
+    const int ac = __popc(__ballot_sync(FULL, act)), zany = __popc(__ballot_sync(FULL, zx));
+    const int nfb = __popc(__ballot_sync(FULL, fbk));
+    if (e == 0) {
+        st->bnorm_all = sqrt(bsum);
+        st->active_count = ac;
+        st->zero_any = zany;
+        st->fb_count = nfb;
+        st->updx_any = 0;
+        st->spmv_real = 0;
+    }
+    __threadfence();
+}
+
+// ------------------------------------------------------------------ KZ
+// x = 0 for members with b = 0 or a rejected start; for the latter also
+// r = p = b (and the split copy of p)
+template <int S, int MODE>
+__global__ void cg_zero_kernel(CgArgs a) {
+    if (ld_cg(&a.st->zero_any) == 0) return;
+    const int64_t total = (int64_t)a.n * S;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int e = (int)(i % S);
+        if (!a.st->zerox[e]) continue;
+        a.x[i] = 0.0;
+        if (a.st->fb[e]) {
+            const double bv = a.b[i];
+            a.r[i] = bv;
+            a.p[i] = bv;
+            if (MODE != 0) store_split1(a.pdf, i, bv, &a.st->df_bad_any);
+        }
+    }
+}
+
+// ------------------------------------------------------------------ K1
+// Body of the batched kernel: NSUB chunks of one ensemble per CTA, each on
+// its own thread group.  Its arithmetic is that of cg_spmv_kernel below (kept
+// as a separate copy because the shared form needs more registers there).
+template <int S, int NSUB>
+struct K1Smem {
+    double sm[NSUB][32][S + 1];
+    ChunkCols cc[NSUB];
+};
+
+template <int S, int MODE, int NSUB>
+__device__ __forceinline__ void k1_body(const CgArgs &a, const int cta, K1Smem<S, NSUB> &sh) {
+    CgState *st = a.st;
+    if (ld_cg(&st->active_count) == 0) {
+        if (cta == 0 && threadIdx.x == 0 && st->updx_any) {
+            for (int e = 0; e < S; ++e) st->updx[e] = 0;
+            st->updx_any = 0;
+        }
+        return;
+    }
+    constexpr int G = RowMap<S>::G, T = RowMap<S>::THREADS;
+    const int sub = (NSUB == 1) ? 0 : (int)threadIdx.x / T;
+    const int ltid = (NSUB == 1) ? (int)threadIdx.x : (int)threadIdx.x % T;
+    const int r = ltid / G, g = ltid % G;
+#define K1_CHUNK ((int64_t)cta * NSUB + sub)
+    const int64_t chunk = K1_CHUNK;
+    const bool valid = chunk * 32 + r < a.n;
+    // the split / double-float forms are used unless a vector element fell outside their range
+    const int mode = (MODE != 0 && ld_cg(&st->df_bad_any) != 0) ? 0 : MODE;
+    const bool staged = (NSUB == 1) ? stage_chunk(sh.cc[0], a.row_map, a.col, chunk, a.n)
+                                    : stage_chunk_sub(sh.cc[sub], a.row_map, a.col, chunk, a.n, ltid, T);
+    double2 apv;
+    if (MODE == 1 && mode == 1)
+        apv = chunk_spmv_df<S, XPre>(sh.cc[sub], staged, a.col, a.vals, a.pdf, r, g, valid);
+    else if (MODE == 2 && mode == 2)
+        apv = chunk_spmv_split<S, XPre>(sh.cc[sub], staged, a.col, a.vals, a.p, a.pdf, r, g, valid);
+    else
+        apv = chunk_spmv<S, double>(sh.cc[sub], staged, a.col, a.vals, a.p, r, g, valid);
+    double v0 = 0.0, v1 = 0.0;
+    const int64_t R = K1_CHUNK * 32 + r;
+    if constexpr (S == 1) {
+        if (valid) {
+            if (g == 0) a.q[R] = apv.x;
+            v0 = apv.x * a.p[R];
+        }
+    } else if (valid) {
+        reinterpret_cast<double2 *>(a.q)[R * G + g] = apv;
+        const double2 pv = reinterpret_cast<const double2 *>(a.p)[R * G + g];
+        v0 = apv.x * pv.x;
+        v1 = apv.y * pv.y;
+    }
+    if constexpr (NSUB == 1) chunk_tree<S>(sh.sm[0], v0, v1, r, g, a.t1, K1_CHUNK, 0);
+    else chunk_tree_sub<S>(sh.sm[sub], v0, v1, r, g, a.t1, K1_CHUNK, 0, ltid, T);
+    const int nitems = (NSUB == 1) ? 1 : (int)min((int64_t)NSUB, a.t1.count[1] - (int64_t)cta * NSUB);
+    if (!dot_tree_propagate(a.t1, (int64_t)cta * NSUB, nitems)) return;
+#undef K1_CHUNK
+    if (threadIdx.x >= 32) return;
+    // epilogue: one lane per member
+    const unsigned FULL = 0xffffffffu;
+    const int e = threadIdx.x;
+    const double *top = a.t1.buf[a.t1.levels];
+    const double pi = (e < S) ? ld_cg(top + e) : 0.0;
+    const double rho = (e < S) ? st->rho[e] : 0.0;
+    int act = (e < S) ? st->active[e] : 0;
+    if (a.coupled) {
+        double pis = 0.0, rhos = 0.0;
+        for (int k = 0; k < S; ++k) {
+            pis += __shfl_sync(FULL, pi, k);
+            rhos += __shfl_sync(FULL, rho, k);
+        }
+        const bool bad = !(pis > 0.0) || !isfinite(pis);
+        if (act) {
+            if (bad) { act = 0; st->status[e] = ENS_ERR_BREAKDOWN; }
+            else st->alpha[e] = rhos / pis;
+        }
+    } else if (act) {
+        if (!(pi > 0.0) || !isfinite(pi)) { act = 0; st->status[e] = ENS_ERR_BREAKDOWN; }
+        else st->alpha[e] = rho / pi;
+    }
+    if (e < S) {
+        st->active[e] = act;
+        st->updx[e] = 0;  // consumed by the previous K3
+    }
+    const int ac = __popc(__ballot_sync(FULL, act));
+    if (e == 0) {
+        st->spmv_real += 1;
+        st->updx_any = 0;
+        st->active_count = ac;
+    }
+    __threadfence();
+}
+
+// single-ensemble K1 (one chunk per CTA); same arithmetic as k1_body
+#ifndef ENS_K1_DFV_THREADS_PER_SM
+#define ENS_K1_DFV_THREADS_PER_SM 1536
+#endif
+template <int S, int MODE>
+struct K1Occ {
+    static constexpr int THREADS_PER_SM = (MODE == 3) ? ENS_K1_DFV_THREADS_PER_SM : 1536;
+};
+
+template <int S, int MODE>
+__global__ void __launch_bounds__(RowMap<S>::THREADS, K1Occ<S, MODE>::THREADS_PER_SM / RowMap<S>::THREADS)
+    cg_spmv_kernel(CgArgs a) {
+    CgState *st = a.st;
+    if (ld_cg(&st->active_count) == 0) {
+        if (blockIdx.x == 0 && threadIdx.x == 0 && st->updx_any) {
+            for (int e = 0; e < S; ++e) st->updx[e] = 0;
+            st->updx_any = 0;
+        }
+        return;
+    }
+    constexpr int G = RowMap<S>::G;
+    __shared__ double sm[32][S + 1];
+    const int r = threadIdx.x / G, g = threadIdx.x % G;
+    const int64_t R = (int64_t)blockIdx.x * 32 + r;
+    // the split form is used unless a vector element fell outside its range
+    const int mode = (MODE != 0 && ld_cg(&st->df_bad_any) != 0) ? 0 : MODE;
+    __shared__ ChunkCols cc;
+    const void *vblock = (MODE == 3) ? static_cast<const void *>(a.vdf) : static_cast<const void *>(a.vals);
+    const bool staged = stage_chunk_pf(cc, a.row_map, a.col, blockIdx.x, a.n, vblock, S * 8u, a.val_bytes,
+                                       a.pf_cap);
+    double2 apv;
+    if (MODE == 1 && mode == 1)
+        apv = chunk_spmv_df<S, XPre>(cc, staged, a.col, a.vals, a.pdf, r, g, R < a.n);
+    else if (MODE == 3 && mode == 3)
+        apv = chunk_spmv_dfv<S>(cc, staged, a.col, a.vdf, a.vals, a.pdf, r, g, R < a.n);
+    else if (MODE == 2 && mode == 2)
+        apv = chunk_spmv_split<S, XPre>(cc, staged, a.col, a.vals, a.p, a.pdf, r, g, R < a.n);
+    else
+        apv = chunk_spmv<S, double>(cc, staged, a.col, a.vals, a.p, r, g, R < a.n);
+    double v0 = 0.0, v1 = 0.0;
+    if constexpr (S == 1) {
+        const double ap = apv.x;
+        if (R < a.n) {
+            if (g == 0) a.q[R] = ap;
+            v0 = ap * a.p[R];
+        }
+    } else if (R < a.n) {
+        const double2 ap = apv;
+        reinterpret_cast<double2 *>(a.q)[R * G + g] = ap;
+        const double2 pv = reinterpret_cast<const double2 *>(a.p)[R * G + g];
+        v0 = ap.x * pv.x;
+        v1 = ap.y * pv.y;
+    }
+    chunk_tree<S>(sm, v0, v1, r, g, a.t1, blockIdx.x, 0);
+    if (!dot_tree_propagate(a.t1, blockIdx.x, 1)) return;
+    if (threadIdx.x >= 32) return;
+    // epilogue: one lane per member
+    const unsigned FULL = 0xffffffffu;
+    const int e = threadIdx.x;
+    const double *top = a.t1.buf[a.t1.levels];
+    const double pi = (e < S) ? ld_cg(top + e) : 0.0;
+    const double rho = (e < S) ? st->rho[e] : 0.0;
+    int act = (e < S) ? st->active[e] : 0;
+    if (a.coupled) {
+        double pis = 0.0, rhos = 0.0;
+        for (int k = 0; k < S; ++k) {
+            pis += __shfl_sync(FULL, pi, k);
+            rhos += __shfl_sync(FULL, rho, k);
+        }
+        const bool bad = !(pis > 0.0) || !isfinite(pis);
+        if (act) {
+            if (bad) { act = 0; st->status[e] = ENS_ERR_BREAKDOWN; }
+            else st->alpha[e] = rhos / pis;
+        }
+    } else if (act) {
+        if (!(pi > 0.0) || !isfinite(pi)) { act = 0; st->status[e] = ENS_ERR_BREAKDOWN; }
+        else st->alpha[e] = rho / pi;
+    }
+    if (e < S) {
+        st->active[e] = act;
+        st->updx[e] = 0;  // consumed by the previous K3
+    }
+    const int ac = __popc(__ballot_sync(FULL, act));
+    if (e == 0) {
+        st->spmv_real += 1;
+        st->updx_any = 0;
+        st->active_count = ac;
+    }
+    __threadfence();
+}
+
+
+// ------------------------------------------------------------------ K2
+// v*v of an FP64 value as an unevaluated float pair: v split by truncation
+// into hi + lo (47 bits), hi*hi exact by FMA error recovery, 2 hi lo added to
+// the error term (lo*lo, below 2^-46 |v*v|, is dropped); values outside the
+// split range square in FP64 and round to a pair (out of line, so that the
+// FP64 instructions stay off the common path)
+static __device__ __noinline__ float2 df_square_wide(double v) {
+    const double q = v * v;
+    const float qh = (float)q;
+    return make_float2(qh, (float)(q - (double)qh));
+}
+
+__device__ __forceinline__ float2 df_square(double v) {
+    float hi, lo;
+    if (!df_split_trunc(v, hi, lo)) return df_square_wide(v);
+    const float p = __fmul_rn(hi, hi);
+    float e = __fmaf_rn(hi, hi, -p);
+    e = __fmaf_rn(2.0f * hi, lo, e);
+    return make_float2(p, e);
+}
+
+// (a.x + a.y) + (b.x + b.y) as a float pair: TwoSum of the leading parts,
+// the trailing parts and the rounding error summed
+__device__ __forceinline__ float2 df_add(float2 a, float2 b) {
+    float s, t;
+    two_sum(a.x, b.x, s, t);
+    return make_float2(s, __fadd_rn(__fadd_rn(a.y, b.y), t));
+}
+
+template <int S, int TH>
+__device__ __forceinline__ void k2_body(const CgArgs &a, int cta,
+                                        double (*sm)[32][S + 1] /* [CPC][32][S+1] */) {
+    using VM = VecMap<S, TH>;
+    if (ld_cg(&a.st->active_count) == 0) return;
+    constexpr int VG = VM::VG;
+    const int cip = threadIdx.x / VM::CHUNK_T, lt = threadIdx.x % VM::CHUNK_T;
+    const int r = lt / VG, g = lt % VG;
+    const CgState *cs = a.st;
+    const int m = (S == 1) ? 0 : 2 * g;
+    const bool act0 = cs->active[m];
+    const bool act1 = (S == 1) ? false : (bool)cs->active[m + 1];
+    const double al0 = cs->alpha[m];
+    const double al1 = (S == 1) ? 0.0 : cs->alpha[m + 1];
+    const int64_t first_chunk = (int64_t)cta * VM::CPC;
+    // r.r: squares and the chunk's 32-row tree in double-float on the FP32
+    // pipe (the FP64 pipe keeps only the r update); the chunk sums enter the
+    // FP64 dot tree above the chunk
+    float2(*sf)[32][S + 1] = reinterpret_cast<float2(*)[32][S + 1]>(sm);
+#pragma unroll
+    for (int pass = 0; pass < VM::PASSES; ++pass) {
+        const int c = pass * VM::CPP + cip;
+        const int64_t R = (first_chunk + c) * 32 + r;
+        float2 v0 = make_float2(0.f, 0.f), v1 = make_float2(0.f, 0.f);
+        if (R < a.n) {
+            if constexpr (S == 1) {
+                double rv = a.r[R];
+                if (act0) { rv = fma(-al0, a.q[R], rv); a.r[R] = rv; }
+                v0 = df_square(rv);
+            } else {
+                double2 rv = reinterpret_cast<const double2 *>(a.r)[R * VG + g];
+                const double2 qv = reinterpret_cast<const double2 *>(a.q)[R * VG + g];
+                if (act0) rv.x = fma(-al0, qv.x, rv.x);
+                if (act1) rv.y = fma(-al1, qv.y, rv.y);
+                if (act0 || act1) reinterpret_cast<double2 *>(a.r)[R * VG + g] = rv;
+                v0 = df_square(rv.x);
+                v1 = df_square(rv.y);
+            }
+        }
+        sf[c][r][m] = v0;
+        if constexpr (S > 1) sf[c][r][m + 1] = v1;
+    }
+    __syncthreads();
+    // halving tree over the 32 rows of every chunk, all members packed
+#pragma unroll
+    for (int h = 16; h >= 1; h >>= 1) {
+        for (int it = threadIdx.x; it < VM::CPC * h * S; it += VM::THREADS) {
+            const int c = it / (h * S), rem = it % (h * S), i = rem / S, e = rem % S;
+            sf[c][i][e] = df_add(sf[c][i][e], sf[c][i + h][e]);
+        }
+        __syncthreads();
+    }
+    for (int it = threadIdx.x; it < VM::CPC * S; it += VM::THREADS) {
+        const int c = it / S, e = it % S;
+        const int64_t ch = first_chunk + c;
+        if (ch < a.t1.count[1]) a.t1.buf[1][ch * S + e] = f2d_exact(sf[c][0][e].x) + f2d_exact(sf[c][0][e].y);
+    }
+    const int nitems = (int)min((int64_t)VM::CPC, a.t1.count[1] - first_chunk);
+    if (!dot_tree_propagate(a.t1, first_chunk, nitems)) return;
+    if (threadIdx.x >= 32) return;
+    // epilogue: one lane per member
+    const unsigned FULL = 0xffffffffu;
+    const int e = threadIdx.x;
+    const double *top = a.t1.buf[a.t1.levels];
+    CgState *st = a.st;
+    const double rn = (e < S) ? ld_cg(top + e) : 0.0;
+    const double rho = (e < S) ? st->rho[e] : 0.0;
+    int act = (e < S) ? st->active[e] : 0, ux = 0;
+    int it = (e < S) ? st->iters[e] : 0;
+    bool conv_all = false;
+    double rns = 0.0, ros = 0.0;
+    if (a.coupled) {
+        for (int k = 0; k < S; ++k) {
+            rns += __shfl_sync(FULL, rn, k);
+            ros += __shfl_sync(FULL, rho, k);
+        }
+        conv_all = sqrt(rns) <= a.tol * st->bnorm_all;
+    }
+    if (act) {
+        it += 1;
+        ux = 1;
+        const bool conv = a.coupled ? conv_all : (sqrt(rn) <= a.tol * st->bnorm[e]);
+        if (conv) { act = 0; st->status[e] = ENS_OK; }
+        else if (it >= a.max_iter) { act = 0; st->status[e] = ENS_ERR_NOT_CONVERGED; }
+        else st->beta[e] = a.coupled ? rns / ros : rn / rho;
+    }
+    if (e < S) {
+        if (a.coupled || ux) st->rho[e] = rn;
+        st->iters[e] = it;
+        st->updx[e] = ux;
+        st->active[e] = act;
+    }
+    const int ac = __popc(__ballot_sync(FULL, act)), uany = __popc(__ballot_sync(FULL, ux));
+    if (e == 0) {
+        st->active_count = ac;
+        st->updx_any = uany;
+    }
+    __threadfence();
+}
+
+// ------------------------------------------------------------------ K3
+template <int S, int MODE, int TH>
+__device__ __forceinline__ void k3_body(const CgArgs &a, int cta) {
+    using VM = VecMap<S, TH>;
+    CgState *st = a.st;
+    if (ld_cg(&st->updx_any) == 0) return;
+    constexpr int VG = VM::VG;
+    const int cip = threadIdx.x / VM::CHUNK_T, lt = threadIdx.x % VM::CHUNK_T;
+    const int r = lt / VG, g = lt % VG;
+    const int m = (S == 1) ? 0 : 2 * g;
+    const bool ux0 = st->updx[m], ac0 = st->active[m];
+    const bool ux1 = (S == 1) ? false : (bool)st->updx[m + 1];
+    const bool ac1 = (S == 1) ? false : (bool)st->active[m + 1];
+    const double al0 = st->alpha[m], be0 = st->beta[m];
+    const double al1 = (S == 1) ? 0.0 : st->alpha[m + 1], be1 = (S == 1) ? 0.0 : st->beta[m + 1];
+    const int64_t first_chunk = (int64_t)cta * VM::CPC;
+#pragma unroll 2
+    for (int pass = 0; pass < VM::PASSES; ++pass) {
+        const int64_t R = (first_chunk + pass * VM::CPP + cip) * 32 + r;
+        if (R >= a.n) continue;
+        if constexpr (S == 1) {
+            const double pv = a.p[R];
+            if (ux0) a.x[R] = fma(al0, pv, a.x[R]);
+            if (ac0) {
+                const double pn = fma(be0, pv, a.r[R]);
+                a.p[R] = pn;
+                if (MODE != 0) store_split1(a.pdf, R, pn, &st->df_bad_any);
+            }
+        } else {
+            const double2 pv = reinterpret_cast<const double2 *>(a.p)[R * VG + g];
+            if (ux0 || ux1) {
+                double2 xv = reinterpret_cast<const double2 *>(a.x)[R * VG + g];
+                if (ux0) xv.x = fma(al0, pv.x, xv.x);
+                if (ux1) xv.y = fma(al1, pv.y, xv.y);
+                reinterpret_cast<double2 *>(a.x)[R * VG + g] = xv;
+            }
+            if (ac0 || ac1) {
+                const double2 rv = reinterpret_cast<const double2 *>(a.r)[R * VG + g];
+                double2 pn = pv;
+                if (ac0) pn.x = fma(be0, pv.x, rv.x);
+                if (ac1) pn.y = fma(be1, pv.y, rv.y);
+                reinterpret_cast<double2 *>(a.p)[R * VG + g] = pn;
+                if (MODE != 0) store_split(a.pdf, R * S + m, pn.x, pn.y, &st->df_bad_any);
+            }
+        }
+    }
+}
+
+template <int S>
+__global__ void __launch_bounds__(VecMap<S>::THREADS) cg_resid_kernel(CgArgs a) {
+    __shared__ double sm[VecMap<S>::CPC][32][S + 1];   // per-row products of every chunk
+    k2_body<S, VecMap<S>::THREADS>(a, blockIdx.x, sm);
+}
+
+template <int S, int MODE>
+__global__ void __launch_bounds__(VecMap<S>::THREADS) cg_update_kernel(CgArgs a) {
+    k3_body<S, MODE, VecMap<S>::THREADS>(a, blockIdx.x);
+}
+
+// ------------------------------------------------------------------ KF
+template <int S>
+__global__ void __launch_bounds__(RowMap<S>::THREADS, 1024 / RowMap<S>::THREADS) cg_final_kernel(CgArgs a) {
+    constexpr int G = RowMap<S>::G;
+    __shared__ double sm[32][S + 1];
+    const int r = threadIdx.x / G, g = threadIdx.x % G;
+    const int64_t R = (int64_t)blockIdx.x * 32 + r;
+    __shared__ ChunkCols cc;
+    const bool staged = stage_chunk(cc, a.row_map, a.col, blockIdx.x, a.n);
+    const double2 axv = chunk_spmv<S, double>(cc, staged, a.col, a.vals, a.x, r, g, R < a.n);
+    double v0 = 0.0, v1 = 0.0;
+    if constexpr (S == 1) {
+        const double ax = axv.x;
+        if (R < a.n) { const double res = a.b[R] - ax; v0 = res * res; }
+    } else if (R < a.n) {
+        const double2 ax = axv;
+        const double2 bv = reinterpret_cast<const double2 *>(a.b)[R * G + g];
+        const double rx = bv.x - ax.x, ry = bv.y - ax.y;
+        v0 = rx * rx;
+        v1 = ry * ry;
+    }
+    chunk_tree<S>(sm, v0, v1, r, g, a.t1, blockIdx.x, 0);
+    if (!dot_tree_propagate(a.t1, blockIdx.x, 1)) return;
+    const int e = threadIdx.x;
+    if (e >= S) return;
+    const double *top = a.t1.buf[a.t1.levels];
+    const double bn = a.st->bnorm[e];
+    a.st->relres[e] = (bn > 0.0) ? sqrt(ld_cg(top + e)) / bn : 0.0;
+    __threadfence();
+}
+
+}  // namespace ens

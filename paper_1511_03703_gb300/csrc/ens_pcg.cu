@@ -1,0 +1,513 @@
+// ens_pcg.cu -- preconditioned ensemble CG with Jacobi or Chebyshev
+// preconditioning.  The paper preconditions its CG by multigrid whose
+// smoothers are order-2 Chebyshev polynomials (Sect. 3.5); here the two
+// SpMV-based preconditioners serve on their own, per member:
+//   Jacobi     z = D^-1 r
+//   Chebyshev  z = p(D^-1 A) D^-1 r, `degree` steps of Chebyshev iteration for
+//              A z = r from z = 0 on [lam/ratio, lam] (Saad, Sect. 12.3), lam =
+//              boost x a power-iteration estimate of the largest eigenvalue
+//              of D^-1 A (the generalized Rayleigh quotient v.Av / v.Dv after
+//              `power_iters` normalised steps from a given start vector).
+// The CG part reuses the kernels of ens_cg.cu with rho = r.z:
+//   K0  r = b - A x0 (as ens_cg)           KP  z = M^-1 r0, rho = r.z, beta = 0
+//   per iteration:
+//   K1  q = A p, p.q -> alpha              P2  r -= alpha q, z_1 (Jacobi: z), r.r
+//   PC  (Chebyshev, degree - 1 times) w = r - A z_k, d, z_{k+1}; the last one r.z
+//   K3  x += alpha p, p = z + beta p
+// The stop test ||r|| <= tol ||b|| and beta = (r.z)_new / (r.z)_old run in the
+// CTA that completes the last tree of the preconditioner stage.  All
+// arithmetic is FP64 (the FP64 SpMV form).
+#include <stdlib.h>
+
+#include <vector>
+
+#include "ens_cg_kernels.cuh"
+
+namespace ens {
+
+constexpr int kPcMaxDegree = 8;
+
+struct PcgState {
+    double lam[32];                    // power-iteration estimate (before the boost)
+    double theta[32], delta[32];       // Chebyshev interval centre and half width
+    double rhoc[kPcMaxDegree][32];     // rho_k of the Chebyshev recurrence
+    double rr[32];                     // r.r of the current iteration (stop test)
+    double nrm[32];                    // power iteration: ||y||
+};
+
+struct PcgArgs {
+    CgArgs c;
+    PcgState *ps;
+    const double *dg, *dinv;  // diagonal and its inverse, commuted layout
+    double *zk[2];            // Chebyshev iterates (ping-pong); zk[0] is z for Jacobi
+    double *d;                // Chebyshev direction
+    double *v, *y;            // power iteration
+    int degree;               // 0: Jacobi, >= 1: Chebyshev steps
+    double boost, ratio;
+};
+
+// ------------------------------------------------------------ set-up kernels
+// diagonal of every member and its inverse (thread per row and member)
+template <int S>
+__global__ void pc_diag_kernel(int32_t n, const int32_t *__restrict__ row_map, const int32_t *__restrict__ col,
+                               const double *__restrict__ vals, double *__restrict__ dg, double *__restrict__ dinv) {
+    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t >= (int64_t)n * S) return;
+    const int32_t I = (int32_t)(t / S);
+    const int e = (int)(t % S);
+    double dv = 0.0;
+    for (int32_t p = row_map[I]; p < row_map[I + 1]; ++p)
+        if (col[p] == I) dv = vals[(int64_t)p * S + e];
+    dg[t] = dv;
+    dinv[t] = 1.0 / dv;
+}
+
+// power step: y = D^-1 A v, ||y||_e  (chunk per CTA, tree t1)
+template <int S>
+__global__ void __launch_bounds__(RowMap<S>::THREADS, 1024 / RowMap<S>::THREADS) pc_power_kernel(PcgArgs a) {
+    constexpr int G = RowMap<S>::G;
+    __shared__ double sm[32][S + 1];
+    __shared__ ChunkCols cc;
+    const CgArgs &c = a.c;
+    const int r = threadIdx.x / G, g = threadIdx.x % G;
+    const int64_t R = (int64_t)blockIdx.x * 32 + r;
+    const bool staged = stage_chunk(cc, c.row_map, c.col, blockIdx.x, c.n);
+    const double2 av = chunk_spmv<S, double>(cc, staged, c.col, c.vals, a.v, r, g, R < c.n);
+    double v0 = 0.0, v1 = 0.0;
+    if (R < c.n) {
+        if constexpr (S == 1) {
+            const double yv = av.x * a.dinv[R];
+            if (g == 0) a.y[R] = yv;
+            v0 = yv * yv;
+        } else {
+            const double2 di = reinterpret_cast<const double2 *>(a.dinv)[R * G + g];
+            const double2 yv = make_double2(av.x * di.x, av.y * di.y);
+            reinterpret_cast<double2 *>(a.y)[R * G + g] = yv;
+            v0 = yv.x * yv.x;
+            v1 = yv.y * yv.y;
+        }
+    }
+    chunk_tree<S>(sm, v0, v1, r, g, c.t1, blockIdx.x, 0);
+    if (!dot_tree_propagate(c.t1, blockIdx.x, 1)) return;
+    const int e = threadIdx.x;
+    if (e < S) a.ps->nrm[e] = sqrt(ld_cg(c.t1.buf[c.t1.levels] + e));
+    __threadfence();
+}
+
+// v = y / ||y||_e
+template <int S>
+__global__ void pc_scale_kernel(PcgArgs a) {
+    const int64_t total = (int64_t)a.c.n * S;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
+         t += (int64_t)gridDim.x * blockDim.x)
+        a.v[t] = a.y[t] / a.ps->nrm[t % S];
+}
+
+// lam_e = (v.Av) / (v.Dv) and the Chebyshev parameters of member e
+template <int S>
+__global__ void __launch_bounds__(RowMap<S>::THREADS, 1024 / RowMap<S>::THREADS) pc_rayleigh_kernel(PcgArgs a) {
+    constexpr int G = RowMap<S>::G;
+    __shared__ double sm[32][S + 1];
+    __shared__ ChunkCols cc;
+    const CgArgs &c = a.c;
+    const int r = threadIdx.x / G, g = threadIdx.x % G;
+    const int64_t R = (int64_t)blockIdx.x * 32 + r;
+    const bool staged = stage_chunk(cc, c.row_map, c.col, blockIdx.x, c.n);
+    const double2 av = chunk_spmv<S, double>(cc, staged, c.col, c.vals, a.v, r, g, R < c.n);
+    double n0 = 0.0, n1 = 0.0, d0 = 0.0, d1 = 0.0;
+    if (R < c.n) {
+        if constexpr (S == 1) {
+            const double vv = a.v[R];
+            n0 = vv * av.x;
+            d0 = vv * (a.dg[R] * vv);
+        } else {
+            const double2 vv = reinterpret_cast<const double2 *>(a.v)[R * G + g];
+            const double2 dd = reinterpret_cast<const double2 *>(a.dg)[R * G + g];
+            n0 = vv.x * av.x; n1 = vv.y * av.y;
+            d0 = vv.x * (dd.x * vv.x); d1 = vv.y * (dd.y * vv.y);
+        }
+    }
+    chunk_tree<S>(sm, n0, n1, r, g, c.t2, blockIdx.x, 0);
+    chunk_tree<S>(sm, d0, d1, r, g, c.t2, blockIdx.x, S);
+    if (!dot_tree_propagate(c.t2, blockIdx.x, 1)) return;
+    const int e = threadIdx.x;
+    if (e < S) {
+        const double *top = c.t2.buf[c.t2.levels];
+        const double lam = ld_cg(top + e) / ld_cg(top + S + e);
+        PcgState *ps = a.ps;
+        ps->lam[e] = lam;
+        const double lmax = a.boost * lam, lmin = lmax / a.ratio;
+        const double theta = 0.5 * (lmax + lmin), delta = 0.5 * (lmax - lmin), sigma = theta / delta;
+        ps->theta[e] = theta;
+        ps->delta[e] = delta;
+        double rho = 1.0 / sigma;
+        ps->rhoc[0][e] = rho;
+        for (int k = 1; k < kPcMaxDegree; ++k) {
+            rho = 1.0 / (2.0 * sigma - rho);
+            ps->rhoc[k][e] = rho;
+        }
+    }
+    __threadfence();
+}
+
+// ------------------------------------------------------------ CG kernels
+// Last CTA of the preconditioner stage, one lane per member: the stop test
+// on r.r, beta = r.z / rho, rho = r.z (init: rho = r.z, beta = 0, no x update)
+template <int S>
+__device__ __forceinline__ void pc_epilogue(const PcgArgs &a, double rr, double rz, bool init) {
+    const unsigned FULL = 0xffffffffu;
+    const int e = threadIdx.x;
+    CgState *st = a.c.st;
+    int act = (e < S) ? st->active[e] : 0, ux = 0;
+    int it = (e < S) ? st->iters[e] : 0;
+    if (e < S) {
+        if (init) {
+            if (act && !(rz > 0.0 && isfinite(rz))) { act = 0; st->status[e] = ENS_ERR_BREAKDOWN; }
+            st->rho[e] = rz;
+            st->beta[e] = 0.0;
+        } else if (act) {
+            it += 1;
+            ux = 1;
+            if (sqrt(rr) <= a.c.tol * st->bnorm[e]) { act = 0; st->status[e] = ENS_OK; }
+            else if (it >= a.c.max_iter) { act = 0; st->status[e] = ENS_ERR_NOT_CONVERGED; }
+            else if (!(rz > 0.0 && isfinite(rz))) { act = 0; st->status[e] = ENS_ERR_BREAKDOWN; }
+            else { st->beta[e] = rz / st->rho[e]; st->rho[e] = rz; }
+        }
+        st->iters[e] = it;
+        st->updx[e] = ux;
+        st->active[e] = act;
+    }
+    const int ac = __popc(__ballot_sync(FULL, act)), uany = __popc(__ballot_sync(FULL, ux));
+    if (e == 0) {
+        st->active_count = ac;
+        // K3 runs only when some flag is set: at init it must still set p = z
+        // (no member updates x: every updx is 0); the next K1 clears the word
+        st->updx_any = init ? 1 : uany;
+    }
+    __threadfence();
+}
+
+// P2: r -= alpha q for active members (not at init); z_1 = D^-1 r (Jacobi) or
+// D^-1 r / theta (Chebyshev, also d = z_1); dots r.r and r.z_1.  Final when
+// degree <= 1.
+template <int S>
+__global__ void __launch_bounds__(RowMap<S>::THREADS, 1024 / RowMap<S>::THREADS) pc_resid_kernel(PcgArgs a,
+                                                                                                 int init) {
+    const CgArgs &c = a.c;
+    if (ld_cg(&c.st->active_count) == 0) return;
+    constexpr int G = RowMap<S>::G;
+    __shared__ double sm[32][S + 1];
+    const int r = threadIdx.x / G, g = threadIdx.x % G;
+    const int64_t R = (int64_t)blockIdx.x * 32 + r;
+    const CgState *cs = c.st;
+    double rr0 = 0.0, rr1 = 0.0, rz0 = 0.0, rz1 = 0.0;
+    if (R < c.n) {
+        const int w = (S == 1) ? 1 : 2;
+        const int64_t i0 = (S == 1) ? R : R * S + 2 * g;
+        for (int k = 0; k < w; ++k) {
+            if (S == 1 && g != 0) break;
+            const int64_t i = i0 + k;
+            const int e = (S == 1) ? 0 : 2 * g + k;
+            double rv = c.r[i];
+            if (!init && cs->active[e]) {
+                rv = fma(-cs->alpha[e], c.q[i], rv);
+                c.r[i] = rv;
+            }
+            double z = rv * a.dinv[i];
+            if (a.degree >= 1) {
+                z = z / a.ps->theta[e];
+                a.d[i] = z;
+            }
+            a.zk[0][i] = z;
+            if (k == 0) { rr0 = rv * rv; rz0 = rv * z; }
+            else { rr1 = rv * rv; rz1 = rv * z; }
+        }
+    }
+    // (s = 1: chunk_tree takes the row's value from lane g = 0)
+    chunk_tree<S>(sm, rr0, rr1, r, g, c.t2, blockIdx.x, 0);
+    chunk_tree<S>(sm, rz0, rz1, r, g, c.t2, blockIdx.x, S);
+    if (!dot_tree_propagate(c.t2, blockIdx.x, 1)) return;
+    if (threadIdx.x >= 32) return;
+    const int e = threadIdx.x;
+    const double *top = c.t2.buf[c.t2.levels];
+    const double rr = (e < S) ? ld_cg(top + e) : 0.0, rz = (e < S) ? ld_cg(top + S + e) : 0.0;
+    if (a.degree <= 1) {
+        pc_epilogue<S>(a, rr, rz, init != 0);
+    } else {
+        if (e < S) a.ps->rr[e] = rr;
+        __threadfence();
+    }
+}
+
+// PC step k (1 <= k < degree): w = r - A z_k, d = rho_k rho_{k-1} d + (2 rho_k / delta) D^-1 w,
+// z_{k+1} = z_k + d; the last step also forms r.z and runs the epilogue
+template <int S>
+__global__ void __launch_bounds__(RowMap<S>::THREADS, 1024 / RowMap<S>::THREADS) pc_cheb_kernel(PcgArgs a, int k,
+                                                                                                int init) {
+    const CgArgs &c = a.c;
+    if (ld_cg(&c.st->active_count) == 0) return;
+    constexpr int G = RowMap<S>::G;
+    __shared__ double sm[32][S + 1];
+    __shared__ ChunkCols cc;
+    const int r = threadIdx.x / G, g = threadIdx.x % G;
+    const int64_t R = (int64_t)blockIdx.x * 32 + r;
+    const double *zin = a.zk[(k - 1) & 1];
+    double *zout = a.zk[k & 1];
+    const bool last = (k == a.degree - 1);
+    const bool staged = stage_chunk(cc, c.row_map, c.col, blockIdx.x, c.n);
+    const double2 az = chunk_spmv<S, double>(cc, staged, c.col, c.vals, zin, r, g, R < c.n);
+    const PcgState *ps = a.ps;
+    double rz0 = 0.0, rz1 = 0.0;
+    if (R < c.n && (S != 1 || g == 0)) {
+        const int w = (S == 1) ? 1 : 2;
+        const int64_t i0 = (S == 1) ? R : R * S + 2 * g;
+        for (int j = 0; j < w; ++j) {
+            const int64_t i = i0 + j;
+            const int e = (S == 1) ? 0 : 2 * g + j;
+            const double axv = (j == 0) ? az.x : az.y;
+            const double rk = ps->rhoc[k][e], rk1 = ps->rhoc[k - 1][e];
+            const double rv = c.r[i];
+            const double dv = rk * rk1 * a.d[i] + (2.0 * rk / ps->delta[e]) * (a.dinv[i] * (rv - axv));
+            const double zv = zin[i] + dv;
+            a.d[i] = dv;
+            zout[i] = zv;
+            if (j == 0) rz0 = rv * zv;
+            else rz1 = rv * zv;
+        }
+    }
+    if (!last) return;
+    chunk_tree<S>(sm, rz0, rz1, r, g, c.t1, blockIdx.x, 0);
+    if (!dot_tree_propagate(c.t1, blockIdx.x, 1)) return;
+    if (threadIdx.x >= 32) return;
+    const int e = threadIdx.x;
+    const double rz = (e < S) ? ld_cg(c.t1.buf[c.t1.levels] + e) : 0.0;
+    const double rr = (e < S) ? a.ps->rr[e] : 0.0;
+    pc_epilogue<S>(a, rr, rz, init != 0);
+}
+
+
+// ------------------------------------------------------------ host side
+static size_t pc_align(size_t x) { return (x + 255) / 256 * 256; }
+
+static size_t pcg_bytes(int64_t n, int s) {
+    const size_t vec = pc_align(sizeof(double) * (size_t)n * s);
+    return pc_align(sizeof(CgState)) + pc_align(sizeof(PcgState)) + 11 * vec + dot_tree_bytes(n, s) +
+           dot_tree_bytes(n, 2 * s);
+}
+
+struct PcgOut {
+    int32_t *iters;
+    double *relres;
+    int32_t *status;
+    double *lam;
+    ens_cg_stats *stats;
+};
+
+template <int S>
+static int pcg_run(const ens_graph *g, const double *vals, const double *b, double *x, double tol, int max_iter,
+                   int degree, double ratio, double boost, int power_iters, const double *v0, int flags,
+                   int check_every, void *work, PcgOut out, cudaStream_t st) {
+    const int64_t n = g->num_rows;
+    const size_t vec = pc_align(sizeof(double) * (size_t)n * S);
+    char *w = static_cast<char *>(work);
+    PcgArgs a;
+    CgArgs &c = a.c;
+    memset(&a, 0, sizeof(a));
+    c.n = g->num_rows;
+    c.row_map = g->row_map;
+    c.col = g->col_entry;
+    c.vals = vals;
+    c.vdf = nullptr;
+    c.b = b;
+    c.x = x;
+    c.st = reinterpret_cast<CgState *>(w); w += pc_align(sizeof(CgState));
+    a.ps = reinterpret_cast<PcgState *>(w); w += pc_align(sizeof(PcgState));
+    c.r = reinterpret_cast<double *>(w); w += vec;
+    c.p = reinterpret_cast<double *>(w); w += vec;
+    c.q = reinterpret_cast<double *>(w); w += vec;
+    c.pdf = reinterpret_cast<float2 *>(w); w += vec;
+    a.zk[0] = reinterpret_cast<double *>(w); w += vec;
+    a.zk[1] = reinterpret_cast<double *>(w); w += vec;
+    a.d = reinterpret_cast<double *>(w); w += vec;
+    double *dg = reinterpret_cast<double *>(w); w += vec;
+    double *dinv = reinterpret_cast<double *>(w); w += vec;
+    a.dg = dg;
+    a.dinv = dinv;
+    a.v = reinterpret_cast<double *>(w); w += vec;
+    a.y = reinterpret_cast<double *>(w); w += vec;
+    dot_tree_layout(&c.t1, n, S, w);
+    w += dot_tree_bytes(n, S);
+    dot_tree_layout(&c.t2, n, 2 * S, w);
+    c.tol = tol;
+    c.max_iter = max_iter;
+    c.coupled = 0;
+    c.fallback = 0;
+    c.x0_zero = (flags & ENS_CG_X0_ZERO) ? 1 : 0;
+    c.pf_cap = 0;
+    c.val_bytes = 0;
+    a.degree = degree;
+    a.boost = boost;
+    a.ratio = ratio;
+    const unsigned grid = (unsigned)c.t1.count[1];
+    const unsigned vgrid = (unsigned)((c.t1.count[1] + VecMap<S>::CPC - 1) / VecMap<S>::CPC);
+    int rc;
+    if ((rc = dot_tree_clear(c.t1, st))) return rc;
+    if ((rc = dot_tree_clear(c.t2, st))) return rc;
+    ENS_CUDA_TRY(cudaMemsetAsync(c.st, 0, sizeof(CgState), st));
+    ENS_CUDA_TRY(cudaMemsetAsync(a.ps, 0, sizeof(PcgState), st));
+    int launches = 0;
+    const int64_t nt = n * S;
+    pc_diag_kernel<S><<<(unsigned)((nt + 255) / 256), 256, 0, st>>>(c.n, c.row_map, c.col, vals, dg, dinv);
+    ++launches;
+    if (degree >= 1) {  // largest eigenvalue of D^-1 A, then the Chebyshev parameters
+        ENS_CUDA_TRY(cudaMemcpyAsync(a.v, v0, sizeof(double) * (size_t)nt, cudaMemcpyDeviceToDevice, st));
+        for (int k = 0; k < power_iters; ++k) {
+            pc_power_kernel<S><<<grid, RowMap<S>::THREADS, 0, st>>>(a);
+            pc_scale_kernel<S><<<152 * 4, 256, 0, st>>>(a);
+            launches += 2;
+        }
+        pc_rayleigh_kernel<S><<<grid, RowMap<S>::THREADS, 0, st>>>(a);
+        ++launches;
+    }
+    ENS_LAUNCH_CHECK("ens_pcg set-up");
+    // final z buffer of the preconditioner stage (K3 reads it as "r")
+    CgArgs c3 = c;
+    c3.r = a.zk[(degree >= 2) ? ((degree - 1) & 1) : 0];
+    auto precond = [&](int init, cudaStream_t s_) {
+        pc_resid_kernel<S><<<grid, RowMap<S>::THREADS, 0, s_>>>(a, init);
+        for (int k = 1; k < degree; ++k) pc_cheb_kernel<S><<<grid, RowMap<S>::THREADS, 0, s_>>>(a, k, init);
+        cg_update_kernel<S, 0><<<vgrid, VecMap<S>::THREADS, 0, s_>>>(c3);
+    };
+    const int per_iter = 2 + (degree >= 2 ? degree - 1 : 0) + 1;
+    cg_init_kernel<S, 0><<<grid, RowMap<S>::THREADS, 0, st>>>(c);
+    cg_zero_kernel<S, 0><<<152 * 2, 256, 0, st>>>(c);
+    precond(1, st);
+    launches += 2 + per_iter - 1;
+    ENS_LAUNCH_CHECK("ens_pcg init");
+
+    const bool use_graph = (flags & ENS_CG_GRAPH) != 0;
+    cudaGraphExec_t gexec = nullptr;
+    cudaGraph_t graph = nullptr;
+    if (use_graph) {
+        cudaStream_t cap;
+        ENS_CUDA_TRY(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
+        cudaError_t ce = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+        if (ce == cudaSuccess) {
+            for (int i = 0; i < check_every; ++i) {
+                cg_spmv_kernel<S, 0><<<grid, RowMap<S>::THREADS, 0, cap>>>(c);
+                precond(0, cap);
+            }
+            ce = cudaStreamEndCapture(cap, &graph);
+        }
+        cudaStreamDestroy(cap);
+        if (ce != cudaSuccess) return cuda_fail(ce, "ens_pcg graph capture");
+        ce = cudaGraphInstantiate(&gexec, graph, 0);
+        if (ce != cudaSuccess) { cudaGraphDestroy(graph); return cuda_fail(ce, "cudaGraphInstantiate"); }
+    }
+    int32_t hflag[2];
+    int polls = 0;
+    const int max_blocks = max_iter / check_every + 3;
+    rc = ENS_OK;
+    for (int blk = 0; blk < max_blocks; ++blk) {
+        if (use_graph) {
+            cudaError_t ce = cudaGraphLaunch(gexec, st);
+            if (ce != cudaSuccess) { rc = cuda_fail(ce, "cudaGraphLaunch"); break; }
+        } else {
+            for (int i = 0; i < check_every; ++i) {
+                cg_spmv_kernel<S, 0><<<grid, RowMap<S>::THREADS, 0, st>>>(c);
+                precond(0, st);
+            }
+        }
+        launches += per_iter * check_every;
+        cudaError_t ce = cudaGetLastError();
+        if (ce == cudaSuccess)
+            ce = cudaMemcpyAsync(hflag, &c.st->active_count, 2 * sizeof(int32_t), cudaMemcpyDeviceToHost, st);
+        if (ce == cudaSuccess) ce = cudaStreamSynchronize(st);
+        if (ce != cudaSuccess) { rc = cuda_fail(ce, "ens_pcg iteration"); break; }
+        ++polls;
+        if (hflag[0] == 0 && hflag[1] == 0) break;
+    }
+    if (gexec) cudaGraphExecDestroy(gexec);
+    if (graph) cudaGraphDestroy(graph);
+    if (rc != ENS_OK) return rc;
+    cg_final_kernel<S><<<grid, RowMap<S>::THREADS, 0, st>>>(c);
+    ++launches;
+    ENS_LAUNCH_CHECK("ens_pcg final");
+    CgState hs;
+    PcgState hp;
+    ENS_CUDA_TRY(cudaMemcpyAsync(&hs, c.st, sizeof(CgState), cudaMemcpyDeviceToHost, st));
+    ENS_CUDA_TRY(cudaMemcpyAsync(&hp, a.ps, sizeof(PcgState), cudaMemcpyDeviceToHost, st));
+    ENS_CUDA_TRY(cudaStreamSynchronize(st));
+    int maxit = 0, first_bad = ENS_OK;
+    for (int e = 0; e < S; ++e) {
+        if (out.iters) out.iters[e] = hs.iters[e];
+        if (out.relres) out.relres[e] = hs.relres[e];
+        if (out.status) out.status[e] = hs.status[e];
+        if (out.lam) out.lam[e] = (degree >= 1) ? hp.lam[e] : 0.0;
+        maxit = hs.iters[e] > maxit ? hs.iters[e] : maxit;
+        if (hs.status[e] != ENS_OK && first_bad == ENS_OK) first_bad = hs.status[e];
+    }
+    if (out.stats) {
+        memset(out.stats, 0, sizeof(ens_cg_stats));
+        out.stats->iterations = maxit;
+        out.stats->kernel_launches = launches;
+        out.stats->host_checks = polls;
+    }
+    if (first_bad != ENS_OK)
+        set_error("ens_pcg: member status %d (%s)", first_bad, ens_status_string(first_bad));
+    return first_bad;
+}
+
+}  // namespace ens
+
+using namespace ens;
+
+extern "C" int ens_pcg_workspace_size(int32_t num_rows, int s, size_t *bytes) {
+    if (num_rows < 0) return fail(ENS_ERR_ARG, "num_rows < 0");
+    if (!supported_s(s)) return fail(ENS_ERR_UNSUPPORTED, "ensemble size s=%d not in {1,4,8,16,32}", s);
+    if (!bytes) return fail(ENS_ERR_ARG, "bytes is NULL");
+    *bytes = pcg_bytes(num_rows, s);
+    return ENS_OK;
+}
+
+extern "C" int ens_pcg(const ens_graph *graph, int s, const double *values, const double *b, double *x,
+                       double tol, int max_iter, int precond, int degree, double ratio, double boost,
+                       int power_iters, const double *power_start, int flags, int check_every, void *work,
+                       size_t work_bytes, int32_t *iters_host, double *relres_host, int32_t *status_host,
+                       double *lam_host, ens_cg_stats *stats_host, void *stream) {
+    int rc = check_graph(graph);
+    if (rc) return rc;
+    if (!supported_s(s)) return fail(ENS_ERR_UNSUPPORTED, "ensemble size s=%d not in {1,4,8,16,32}", s);
+    if (graph->num_rows == 0) return fail(ENS_ERR_ARG, "empty graph");
+    if (!values || !b || !x || !work) return fail(ENS_ERR_ARG, "NULL values/b/x/work");
+    if (!(tol >= 0.0) || max_iter < 0 || check_every < 1)
+        return fail(ENS_ERR_ARG, "tol=%g max_iter=%d check_every=%d", tol, max_iter, check_every);
+    int deg = 0;
+    if (precond == ENS_PC_CHEBYSHEV) {
+        if (degree < 1 || degree > kPcMaxDegree || !(ratio > 1.0) || !(boost >= 1.0) || power_iters < 1 ||
+            power_iters > 1000 || !power_start)
+            return fail(ENS_ERR_ARG, "chebyshev: 1 <= degree <= %d, ratio > 1, boost >= 1, 1 <= power_iters <= 1000, "
+                        "power_start given", kPcMaxDegree);
+        deg = degree;
+    } else if (precond != ENS_PC_JACOBI) {
+        return fail(ENS_ERR_UNSUPPORTED, "precond %d (ENS_PC_JACOBI or ENS_PC_CHEBYSHEV)", precond);
+    }
+    if (!aligned16(work) || (s > 1 && (!aligned16(values) || !aligned16(b) || !aligned16(x))))
+        return fail(ENS_ERR_ALIGN, "values/b/x/work must be 16-byte aligned");
+    const size_t need = pcg_bytes(graph->num_rows, s);
+    if (work_bytes < need) return fail(ENS_ERR_WORKSPACE, "pcg workspace %zu < %zu bytes", work_bytes, need);
+    PcgOut out{iters_host, relres_host, status_host, lam_host, stats_host};
+    cudaStream_t st = as_stream(stream);
+    switch (s) {
+        case 1: return pcg_run<1>(graph, values, b, x, tol, max_iter, deg, ratio, boost, power_iters, power_start,
+                                  flags, check_every, work, out, st);
+        case 4: return pcg_run<4>(graph, values, b, x, tol, max_iter, deg, ratio, boost, power_iters, power_start,
+                                  flags, check_every, work, out, st);
+        case 8: return pcg_run<8>(graph, values, b, x, tol, max_iter, deg, ratio, boost, power_iters, power_start,
+                                  flags, check_every, work, out, st);
+        case 16: return pcg_run<16>(graph, values, b, x, tol, max_iter, deg, ratio, boost, power_iters, power_start,
+                                    flags, check_every, work, out, st);
+        default: return pcg_run<32>(graph, values, b, x, tol, max_iter, deg, ratio, boost, power_iters, power_start,
+                                    flags, check_every, work, out, st);
+    }
+}
