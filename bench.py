@@ -233,9 +233,9 @@ class Runner:
                    values_df=self.vdf)
         x = self.x[g]
         x.zero_()
-        flags = (E.CG_TIME_SPMV if self.time_spmv else 0) | form_flag(self.df) | E.CG_X0_ZERO
+        flags = (E.CG_TIME_SPMV if self.time_spmv else 0) | form_flag(self.df) | E.CG_X0_ZERO | E.CG_GRAPH
         it, rr, st, stats = E.cg(self.graph, self.s, self.values, self.b, x, TOL, 10000, self.work,
-                                 flags=flags, check_every=16, values_df=self.vdf)
+                                 flags=flags, check_every=8, values_df=self.vdf)
         self.launches += 2 + stats.kernel_launches
         self.iters.extend(it)
         self.status_bad += sum(1 for v in st if v != 0)

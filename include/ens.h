@@ -203,7 +203,8 @@ enum {
     ENS_CG_COUPLED = 1,      /* paper's coupled ensemble CG (Sect. 3.6): alpha, beta
                                 from member-summed dots, one convergence test */
     ENS_CG_GRAPH = 2,        /* replay the iteration through a captured CUDA graph */
-    ENS_CG_TIME_SPMV = 4,    /* record CUDA events around each CG SpMV */
+    ENS_CG_TIME_SPMV = 4,    /* record CUDA events around each CG SpMV (with ENS_CG_GRAPH
+                                as event-record nodes of the graph; ens_cg only) */
     ENS_CG_DF64 = 8,         /* CG SpMV in double-float arithmetic (see ENS_F64_DF);
                                 p is kept split as float pairs, all other vector
                                 arithmetic and every dot stays FP64 */

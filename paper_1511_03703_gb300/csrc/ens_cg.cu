@@ -119,7 +119,7 @@ static int cg_run(const ens_graph *g, const double *vals, const float2 *vdf, con
     ENS_CUDA_TRY(cudaMemsetAsync(a.st, 0, sizeof(CgState), st));
 
     const bool timing = (flags & ENS_CG_TIME_SPMV) != 0;
-    const bool use_graph = (flags & ENS_CG_GRAPH) != 0 && !timing;
+    const bool use_graph = (flags & ENS_CG_GRAPH) != 0;
     int launches = 0, polls = 0;
     std::vector<cudaEvent_t> ev;
     std::vector<float> spmv_ms;
@@ -137,22 +137,36 @@ static int cg_run(const ens_graph *g, const double *vals, const float2 *vdf, con
     cudaGraph_t graph = nullptr;
     if (use_graph) {
         // capture on a private stream (the legacy default stream cannot be
-        // captured); the graph is then launched on the caller's stream
+        // captured); the graph is then launched on the caller's stream.  With
+        // ENS_CG_TIME_SPMV the events around each SpMV become event-record
+        // nodes of the graph and are read after every replay.
         cudaStream_t cap;
         ENS_CUDA_TRY(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
         cudaError_t ce = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
         if (ce == cudaSuccess) {
             for (int i = 0; i < check_every; ++i) {
+                if (timing && ce == cudaSuccess) ce = cudaEventRecordWithFlags(ev[2 * i], cap, cudaEventRecordExternal);
                 K::spmv(a, grid, cap);
+                if (timing && ce == cudaSuccess)
+                    ce = cudaEventRecordWithFlags(ev[2 * i + 1], cap, cudaEventRecordExternal);
                 K::resid(a, grid, cap);
                 K::update(a, grid, cap);
             }
-            ce = cudaStreamEndCapture(cap, &graph);
+            const cudaError_t ce2 = cudaStreamEndCapture(cap, &graph);
+            if (ce == cudaSuccess) ce = ce2;
         }
         cudaStreamDestroy(cap);
-        if (ce != cudaSuccess) return cuda_fail(ce, "cg iteration graph capture");
+        if (ce != cudaSuccess) {
+            if (graph) cudaGraphDestroy(graph);
+            destroy_events();
+            return cuda_fail(ce, "cg iteration graph capture");
+        }
         ce = cudaGraphInstantiate(&gexec, graph, 0);
-        if (ce != cudaSuccess) { cudaGraphDestroy(graph); return cuda_fail(ce, "cudaGraphInstantiate"); }
+        if (ce != cudaSuccess) {
+            cudaGraphDestroy(graph);
+            destroy_events();
+            return cuda_fail(ce, "cudaGraphInstantiate");
+        }
     }
 
     int32_t flags_h[2];

@@ -286,6 +286,13 @@ def test_cg_graph_replay_matches_direct_launches(torch):
     a = gpu_solve(mesh, xs, 1e-10)
     b = gpu_solve(mesh, xs, 1e-10, flags=E.CG_GRAPH, check_every=5)
     assert np.array_equal(a[0], b[0]) and a[1] == b[1]
+    # SpMV timing inside the graph: event-record nodes, same results
+    for presplit in (False, True):
+        c = gpu_solve(mesh, xs, 1e-10, flags=E.CG_GRAPH | E.CG_TIME_SPMV, check_every=5, presplit=presplit)
+        d = gpu_solve(mesh, xs, 1e-10, flags=E.CG_TIME_SPMV, check_every=5, presplit=presplit)
+        assert np.array_equal(c[0], d[0]) and c[1] == d[1]
+        assert c[4].spmv_launches == max(c[1]) and c[4].spmv_ms > 0.0
+        assert d[4].spmv_launches == max(d[1])
 
 
 def test_cg_member_edge_cases(torch):
