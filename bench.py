@@ -984,6 +984,79 @@ def main_pcg(args):
     print(json.dumps(line))
 
 
+# ----------------------------------- multigrid-preconditioned CG (NEXT-3)
+MG_SAMPLES = 256
+MG_WORKLOAD = ("KL diffusion, 64^3 hex Q1 mesh, M=10, 256 samples as 8 ensembles of s=32, CG to 1e-8: "
+               "multigrid-preconditioned ensemble CG (V-cycle over 64^3..4^3, Chebyshev-2 smoothers, "
+               "direct coarse solve) vs plain ensemble CG")
+
+
+def main_mg(args):
+    """The paper's solver form (Sect. 3.5): MG-PCG on the nested meshes
+    against the plain CG, same samples and tolerance; each step assembles
+    every level of every ensemble and solves."""
+    import torch
+    import paper_1511_03703_gb300 as E
+    from paper_1511_03703_gb300 import inputs
+    dev = torch.device("cuda:0")
+    E.lib()
+    s = 32
+    t0 = time.perf_counter()
+    mg = E.Multigrid(N_MESH, M_KL, device=dev)
+    torch.cuda.synchronize()
+    t_setup = time.perf_counter() - t0
+    xs = inputs.kl_samples(inputs.SEED_SCALE, 0, MG_SAMPLES, M_KL)
+    xis = [torch.from_numpy(inputs.ensemble_layout(xs[j:j + s])).to(dev) for j in range(0, MG_SAMPLES, s)]
+    starts = [torch.from_numpy(np.stack([inputs.random_vector(600 + 100 * l + e, m.n) for e in range(s)],
+                                        axis=1).reshape(-1)).to(dev) for l, m in enumerate(mg.meshes)]
+    mesh = mg.meshes[0]
+    vdf = torch.empty(2 * mesh.nnz * s, dtype=torch.float32, device=dev)
+    wcg = torch.empty(E.cg_workspace_size(mesh.n, s), dtype=torch.uint8, device=dev)
+    x = torch.empty(mesh.n * s, dtype=torch.float64, device=dev)
+    vals0, _ = mg.assemble(s, xis[0])
+    wmg = torch.empty(mg.workspace_size(s, vals0, starts), dtype=torch.uint8, device=dev)
+    del vals0
+
+    def run(form):
+        its = []
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        for xi in xis:
+            x.zero_()
+            if form == "mg":
+                vals, b = mg.assemble(s, xi)
+                it, rr, st, _ = mg.solve(s, vals, b, x, TOL, 500, wmg, starts, flags=E.CG_GRAPH | E.CG_X0_ZERO,
+                                         check_every=4)
+            else:
+                vals, b = mesh.assemble(s, xi, values_df=vdf if form == "cg_dfv" else None)
+                it, rr, st, _ = E.cg(mesh.graph, s, vals, b, x, TOL, 10000, wcg,
+                                     flags=E.CG_GRAPH | E.CG_X0_ZERO, check_every=8,
+                                     values_df=vdf if form == "cg_dfv" else None)
+            if any(st):
+                raise RuntimeError(f"{form}: status {st}")
+            its += it
+        torch.cuda.synchronize()
+        return its, time.perf_counter() - t
+
+    out = {}
+    for form in ("cg_f64", "cg_dfv", "mg"):
+        for _ in range(args.warmup):
+            run(form)
+        its, sec = run(form)
+        out[form] = {"mean_iterations": float(np.mean(its)), "max_iterations": int(np.max(its)),
+                     "sample_solves_per_s": MG_SAMPLES / sec}
+    line = {"metric": "multigrid-preconditioned ensemble CG sample-solves/s vs plain ensemble CG, 1 GB300",
+            "value": out["mg"]["sample_solves_per_s"], "unit": UNIT, "n_gpus": 1, "steps": 1,
+            "warmup": args.warmup, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64", "data": "synthetic",
+            "config": {"workload": MG_WORKLOAD, "levels": mg.sizes, "smoother": "Chebyshev degree 2 on "
+                       "[lam/5, 1.1 lam], 10 power steps", "mesh_setup_seconds": t_setup,
+                       "step": "assembly of every level + solve, per ensemble"},
+            "forms": out, "speedup_vs_plain_cg_dfv": out["mg"]["sample_solves_per_s"] /
+            out["cg_dfv"]["sample_solves_per_s"]}
+    print(json.dumps(line))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -997,10 +1070,11 @@ def main():
                          "pre-split once per ensemble (dfv)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--quick", action="store_true", help="skip the other-form run and the s sweep")
-    ap.add_argument("--workload", default="scale", choices=["scale", "mixed", "batched", "guess", "coupled", "pcg"],
+    ap.add_argument("--workload", default="scale", choices=["scale", "mixed", "batched", "guess", "coupled", "pcg", "mg"],
                     help="scale: 64^3 ensemble CG (default line); mixed: 128^3 mixed precision; "
                          "batched: 16^3..64^3 x s=4..32 in one batch; guess: learned initial guess; "
-                         "coupled: the paper's coupled CG vs per-member CG; pcg: preconditioned CG")
+                         "coupled: the paper's coupled CG vs per-member CG; pcg: preconditioned CG; "
+                         "mg: multigrid-preconditioned CG")
     args = ap.parse_args()
     if args.workload == "mixed" and args.impl != "reference":
         main_mixed(args)
@@ -1016,6 +1090,9 @@ def main():
         return
     if args.workload == "pcg" and args.impl != "reference":
         main_pcg(args)
+        return
+    if args.workload == "mg" and args.impl != "reference":
+        main_mg(args)
         return
     if args.impl == "reference":
         main_reference(args)

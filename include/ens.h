@@ -274,6 +274,37 @@ int ens_pcg(const ens_graph *graph, int s, const double *values, const double *b
             int32_t *iters_host, double *relres_host, int32_t *status_host, double *lam_host,
             ens_cg_stats *stats_host, void *stream);
 
+/* ------------------------------- multigrid-preconditioned ensemble CG */
+/* The paper's solver (Sect. 3.5, Algorithm 1), geometric form: CG with
+ * z = V_0(r), a V-cycle over nested meshes N, N/2, ..., N_L (N_L <= 4).
+ * Level l: the ensemble's matrix assembled by the caller on the
+ * (N/2^l)^3-cell mesh from the same KL variables (rediscretisation).
+ *   P_l  trilinear interpolation from the interior nodes of level l+1 to the
+ *        interior nodes of level l (fine 2i <- coarse i, weight 1; 2i+1 <- i,
+ *        i+1, weight 1/2 each, per axis; boundary nodes left out), R_l = P_l^T;
+ *   S_l  Chebyshev smoother x += p(D^-1 A) D^-1 (b - A x): `degree` steps on
+ *        [lam/ratio, lam], lam = boost x the power estimate of ens_pcg
+ *        (power_iters steps from the level's power_start);
+ *   V_L  x = A_L^-1 b (inverse of the coarsest matrix, Gauss-Jordan once per
+ *        call; at most 125 rows);
+ *   V_l  x = S(b, 0); r = b - A x; x += P V_{l+1}(R r); x = S(b, x).
+ * CG as ens_cg with rho = r.z; FP64 throughout.  flags: ENS_CG_GRAPH,
+ * ENS_CG_X0_ZERO.  b, x: level-0 vectors (commuted layout).  Returns
+ * ENS_ERR_BREAKDOWN if the coarsest matrix is not positive definite.
+ * Synchronises `stream`. */
+typedef struct ens_mg_level {
+    ens_graph graph;            /* the level's mesh graph (ens_graph_build of N) */
+    int32_t N;                  /* cells per side: levels[l].N = levels[0].N / 2^l */
+    int32_t reserved;
+    const double *values;       /* the ensemble's matrix on this level, commuted layout */
+    const double *power_start;  /* n*s start vector of the level's eigenvalue estimate */
+} ens_mg_level;
+int ens_mg_workspace_size(int nlevels, const ens_mg_level *levels, int s, size_t *bytes);
+int ens_mg_pcg(int nlevels, const ens_mg_level *levels, int s, const double *b, double *x, double tol,
+               int max_iter, int degree, double ratio, double boost, int power_iters, int flags,
+               int check_every, void *work, size_t work_bytes, int32_t *iters_host, double *relres_host,
+               int32_t *status_host, ens_cg_stats *stats_host, void *stream);
+
 /* ---------------------------------------------------- A8 batched CG */
 /* One ensemble of a batch: its graph (by value), size s, values, rhs, x (in:
  * x0, out: solution) and optional host outputs iters/relres/status [s]. */

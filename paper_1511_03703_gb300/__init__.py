@@ -18,7 +18,7 @@ __all__ = ["EnsError", "lib", "Graph", "Mesh", "mesh_sizes", "graph_build", "kl_
            "snapshots_put", "pod", "pod_workspace_size", "pod_targets", "to_f32", "mlp_param_count",
            "mlp_init", "mlp_workspace_size", "mlp_forward", "mlp_grad", "mlp_adam", "mlp_train",
            "guess", "guess_workspace_size", "MLP_DIMS", "pcg", "pcg_workspace_size", "PC_JACOBI",
-           "PC_CHEBYSHEV"]
+           "PC_CHEBYSHEV", "Multigrid", "mg_level_sizes"]
 
 F64, F32, BF16, F64_DF, F64_SPLIT = 0, 1, 2, 3, 4
 CG_COUPLED, CG_GRAPH, CG_TIME_SPMV, CG_DF64, CG_SPLIT64, CG_GUESS_FALLBACK, CG_X0_ZERO = 1, 2, 4, 8, 16, 32, 64
@@ -47,6 +47,11 @@ class BatchItemC(ctypes.Structure):
                 ("values", ctypes.c_void_p), ("b", ctypes.c_void_p), ("x", ctypes.c_void_p),
                 ("iters_host", ctypes.c_void_p), ("relres_host", ctypes.c_void_p),
                 ("status_host", ctypes.c_void_p)]
+
+
+class MgLevelC(ctypes.Structure):
+    _fields_ = [("graph", EnsGraphC), ("N", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("values", ctypes.c_void_p), ("power_start", ctypes.c_void_p)]
 
 
 class CgStats(ctypes.Structure):
@@ -102,6 +107,8 @@ def _declare(L):
         "ens_cg": (I, [P(EnsGraphC), I, vp, vp, vp, d, I, I, I, vp, sz, vp, vp, vp, P(CgStats), vp]),
         "ens_cg_df": (I, [P(EnsGraphC), I, vp, vp, vp, vp, d, I, I, I, vp, sz, vp, vp, vp, P(CgStats), vp]),
         "ens_pcg_workspace_size": (I, [i32, I, P(sz)]),
+        "ens_mg_workspace_size": (I, [I, P(MgLevelC), I, P(sz)]),
+        "ens_mg_pcg": (I, [I, P(MgLevelC), I, vp, vp, d, I, I, d, d, I, I, I, vp, sz, vp, vp, vp, P(CgStats), vp]),
         "ens_pcg": (I, [P(EnsGraphC), I, vp, vp, vp, d, I, I, I, d, d, I, vp, I, I, vp, sz, vp, vp, vp, vp,
                         P(CgStats), vp]),
         "ens_convert_values": (I, [P(EnsGraphC), I, vp, I, vp, vp, vp]),
@@ -320,6 +327,69 @@ def pcg(graph, s, values, b, x, tol, max_iter, work, precond=PC_JACOBI, degree=2
     if rc not in (0, ERR_NOT_CONVERGED, ERR_BREAKDOWN):
         _check(rc)
     return list(it), list(rr), list(stt), list(lam), stats
+
+
+# ------------------------------------------------ multigrid-preconditioned CG
+def mg_level_sizes(N):
+    """N, N/2, ... while the size is even and above 4 (the coarsest has <= 125 rows)."""
+    out = [N]
+    while out[-1] % 2 == 0 and out[-1] > 4:
+        out.append(out[-1] // 2)
+    return out
+
+
+class Multigrid:
+    """The nested meshes of a V-cycle (set-up per mesh, on the GPU), and the
+    per-ensemble assembly and MG-PCG solve (ens_mg_pcg)."""
+
+    def __init__(self, N, M, L=1.0, device="cuda"):
+        self.sizes = mg_level_sizes(N)
+        if len(self.sizes) < 2 or self.sizes[-1] > 4:
+            raise EnsError(1, f"N={N}: no nested hierarchy down to N <= 4 by halving")
+        self.meshes = [Mesh(n, M, L=L, device=device) for n in self.sizes]
+        self.N, self.M = N, M
+
+    def assemble(self, s, xi_ens, sigma=0.1, kappa0=1.0):
+        """Values of every level and the level-0 right-hand side."""
+        vals, b0 = [], None
+        for l, mesh in enumerate(self.meshes):
+            v, b = mesh.assemble(s, xi_ens, sigma=sigma, kappa0=kappa0)
+            vals.append(v)
+            if l == 0:
+                b0 = b
+        return vals, b0
+
+    def _levels(self, s, values, power_starts):
+        c = (MgLevelC * len(self.meshes))()
+        for l, mesh in enumerate(self.meshes):
+            _require_cuda(values[l], power_starts[l])
+            c[l].graph = mesh.graph.c
+            c[l].N = mesh.N
+            c[l].values = values[l].data_ptr()
+            c[l].power_start = power_starts[l].data_ptr()
+        return c
+
+    def workspace_size(self, s, values, power_starts):
+        v = ctypes.c_size_t()
+        c = self._levels(s, values, power_starts)
+        _check(lib().ens_mg_workspace_size(len(self.meshes), c, s, ctypes.byref(v)))
+        return v.value
+
+    def solve(self, s, values, b, x, tol, max_iter, work, power_starts, degree=2, ratio=5.0, boost=1.1,
+              power_iters=10, flags=0, check_every=8, stream=None):
+        """Returns (iters[s], relres[s], status[s], CgStats).  Synchronises."""
+        _require_cuda(b, x, work)
+        c = self._levels(s, values, power_starts)
+        it = (ctypes.c_int32 * s)()
+        rr = (ctypes.c_double * s)()
+        stt = (ctypes.c_int32 * s)()
+        stats = CgStats()
+        rc = lib().ens_mg_pcg(len(self.meshes), c, s, _ptr(b), _ptr(x), tol, max_iter, degree, ratio, boost,
+                              power_iters, flags, check_every, _ptr(work), work.numel() * work.element_size(),
+                              it, rr, stt, ctypes.byref(stats), _stream(stream))
+        if rc not in (0, ERR_NOT_CONVERGED, ERR_BREAKDOWN):
+            _check(rc)
+        return list(it), list(rr), list(stt), stats
 
 
 # ------------------------------------------------------------- batched CG

@@ -1,0 +1,172 @@
+// ens_pcg_kernels.cuh -- device pieces shared by the preconditioned CG
+// (ens_pcg.cu) and the multigrid-preconditioned CG (ens_mg.cu): per-member
+// Chebyshev parameters, the diagonal, the power-iteration eigenvalue bound and
+// the epilogue of the preconditioner stage.
+#pragma once
+#include "ens_cg_kernels.cuh"
+
+namespace ens {
+
+constexpr int kPcMaxDegree = 8;
+
+struct PcgState {
+    double lam[32];                    // power-iteration estimate (before the boost)
+    double theta[32], delta[32];       // Chebyshev interval centre and half width
+    double rhoc[kPcMaxDegree][32];     // rho_k of the Chebyshev recurrence
+    double rr[32];                     // r.r of the current iteration (stop test)
+    double nrm[32];                    // power iteration: ||y||
+};
+
+struct PcgArgs {
+    CgArgs c;
+    PcgState *ps;
+    const double *dg, *dinv;  // diagonal and its inverse, commuted layout
+    double *zk[2];            // Chebyshev iterates (ping-pong); zk[0] is z for Jacobi
+    double *d;                // Chebyshev direction
+    double *v, *y;            // power iteration
+    int degree;               // 0: Jacobi, >= 1: Chebyshev steps
+    double boost, ratio;
+};
+
+// ------------------------------------------------------------ set-up kernels
+// diagonal of every member and its inverse (thread per row and member)
+template <int S>
+__global__ void pc_diag_kernel(int32_t n, const int32_t *__restrict__ row_map, const int32_t *__restrict__ col,
+                               const double *__restrict__ vals, double *__restrict__ dg, double *__restrict__ dinv) {
+    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t >= (int64_t)n * S) return;
+    const int32_t I = (int32_t)(t / S);
+    const int e = (int)(t % S);
+    double dv = 0.0;
+    for (int32_t p = row_map[I]; p < row_map[I + 1]; ++p)
+        if (col[p] == I) dv = vals[(int64_t)p * S + e];
+    dg[t] = dv;
+    dinv[t] = 1.0 / dv;
+}
+
+// power step: y = D^-1 A v, ||y||_e  (chunk per CTA, tree t1)
+template <int S>
+__global__ void __launch_bounds__(RowMap<S>::THREADS, 1024 / RowMap<S>::THREADS) pc_power_kernel(PcgArgs a) {
+    constexpr int G = RowMap<S>::G;
+    __shared__ double sm[32][S + 1];
+    __shared__ ChunkCols cc;
+    const CgArgs &c = a.c;
+    const int r = threadIdx.x / G, g = threadIdx.x % G;
+    const int64_t R = (int64_t)blockIdx.x * 32 + r;
+    const bool staged = stage_chunk(cc, c.row_map, c.col, blockIdx.x, c.n);
+    const double2 av = chunk_spmv<S, double>(cc, staged, c.col, c.vals, a.v, r, g, R < c.n);
+    double v0 = 0.0, v1 = 0.0;
+    if (R < c.n) {
+        if constexpr (S == 1) {
+            const double yv = av.x * a.dinv[R];
+            if (g == 0) a.y[R] = yv;
+            v0 = yv * yv;
+        } else {
+            const double2 di = reinterpret_cast<const double2 *>(a.dinv)[R * G + g];
+            const double2 yv = make_double2(av.x * di.x, av.y * di.y);
+            reinterpret_cast<double2 *>(a.y)[R * G + g] = yv;
+            v0 = yv.x * yv.x;
+            v1 = yv.y * yv.y;
+        }
+    }
+    chunk_tree<S>(sm, v0, v1, r, g, c.t1, blockIdx.x, 0);
+    if (!dot_tree_propagate(c.t1, blockIdx.x, 1)) return;
+    const int e = threadIdx.x;
+    if (e < S) a.ps->nrm[e] = sqrt(ld_cg(c.t1.buf[c.t1.levels] + e));
+    __threadfence();
+}
+
+// v = y / ||y||_e
+template <int S>
+__global__ void pc_scale_kernel(PcgArgs a) {
+    const int64_t total = (int64_t)a.c.n * S;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
+         t += (int64_t)gridDim.x * blockDim.x)
+        a.v[t] = a.y[t] / a.ps->nrm[t % S];
+}
+
+// lam_e = (v.Av) / (v.Dv) and the Chebyshev parameters of member e
+template <int S>
+__global__ void __launch_bounds__(RowMap<S>::THREADS, 1024 / RowMap<S>::THREADS) pc_rayleigh_kernel(PcgArgs a) {
+    constexpr int G = RowMap<S>::G;
+    __shared__ double sm[32][S + 1];
+    __shared__ ChunkCols cc;
+    const CgArgs &c = a.c;
+    const int r = threadIdx.x / G, g = threadIdx.x % G;
+    const int64_t R = (int64_t)blockIdx.x * 32 + r;
+    const bool staged = stage_chunk(cc, c.row_map, c.col, blockIdx.x, c.n);
+    const double2 av = chunk_spmv<S, double>(cc, staged, c.col, c.vals, a.v, r, g, R < c.n);
+    double n0 = 0.0, n1 = 0.0, d0 = 0.0, d1 = 0.0;
+    if (R < c.n) {
+        if constexpr (S == 1) {
+            const double vv = a.v[R];
+            n0 = vv * av.x;
+            d0 = vv * (a.dg[R] * vv);
+        } else {
+            const double2 vv = reinterpret_cast<const double2 *>(a.v)[R * G + g];
+            const double2 dd = reinterpret_cast<const double2 *>(a.dg)[R * G + g];
+            n0 = vv.x * av.x; n1 = vv.y * av.y;
+            d0 = vv.x * (dd.x * vv.x); d1 = vv.y * (dd.y * vv.y);
+        }
+    }
+    chunk_tree<S>(sm, n0, n1, r, g, c.t2, blockIdx.x, 0);
+    chunk_tree<S>(sm, d0, d1, r, g, c.t2, blockIdx.x, S);
+    if (!dot_tree_propagate(c.t2, blockIdx.x, 1)) return;
+    const int e = threadIdx.x;
+    if (e < S) {
+        const double *top = c.t2.buf[c.t2.levels];
+        const double lam = ld_cg(top + e) / ld_cg(top + S + e);
+        PcgState *ps = a.ps;
+        ps->lam[e] = lam;
+        const double lmax = a.boost * lam, lmin = lmax / a.ratio;
+        const double theta = 0.5 * (lmax + lmin), delta = 0.5 * (lmax - lmin), sigma = theta / delta;
+        ps->theta[e] = theta;
+        ps->delta[e] = delta;
+        double rho = 1.0 / sigma;
+        ps->rhoc[0][e] = rho;
+        for (int k = 1; k < kPcMaxDegree; ++k) {
+            rho = 1.0 / (2.0 * sigma - rho);
+            ps->rhoc[k][e] = rho;
+        }
+    }
+    __threadfence();
+}
+
+// ------------------------------------------------------------ CG kernels
+// Last CTA of the preconditioner stage, one lane per member: the stop test
+// on r.r, beta = r.z / rho, rho = r.z (init: rho = r.z, beta = 0, no x update)
+template <int S>
+__device__ __forceinline__ void pc_epilogue(const PcgArgs &a, double rr, double rz, bool init) {
+    const unsigned FULL = 0xffffffffu;
+    const int e = threadIdx.x;
+    CgState *st = a.c.st;
+    int act = (e < S) ? st->active[e] : 0, ux = 0;
+    int it = (e < S) ? st->iters[e] : 0;
+    if (e < S) {
+        if (init) {
+            if (act && !(rz > 0.0 && isfinite(rz))) { act = 0; st->status[e] = ENS_ERR_BREAKDOWN; }
+            st->rho[e] = rz;
+            st->beta[e] = 0.0;
+        } else if (act) {
+            it += 1;
+            ux = 1;
+            if (sqrt(rr) <= a.c.tol * st->bnorm[e]) { act = 0; st->status[e] = ENS_OK; }
+            else if (it >= a.c.max_iter) { act = 0; st->status[e] = ENS_ERR_NOT_CONVERGED; }
+            else if (!(rz > 0.0 && isfinite(rz))) { act = 0; st->status[e] = ENS_ERR_BREAKDOWN; }
+            else { st->beta[e] = rz / st->rho[e]; st->rho[e] = rz; }
+        }
+        st->iters[e] = it;
+        st->updx[e] = ux;
+        st->active[e] = act;
+    }
+    const int ac = __popc(__ballot_sync(FULL, act)), uany = __popc(__ballot_sync(FULL, ux));
+    if (e == 0) {
+        st->active_count = ac;
+        // K3 runs only when some flag is set: at init it must still set p = z
+        // (no member updates x: every updx is 0); the next K1 clears the word
+        st->updx_any = init ? 1 : uany;
+    }
+    __threadfence();
+}
+
+}  // namespace ens

@@ -1,0 +1,95 @@
+"""Multigrid-preconditioned ensemble CG against the FP64 oracle (oracle/multigrid.py).
+
+Bars: iteration counts within one of the oracle's MG-PCG on the same
+hierarchy, solutions to 1e-8 relative; member results bitwise independent of
+s; graph replay bitwise equal to direct launches; a mesh-independent
+iteration count.
+"""
+import numpy as np
+import pytest
+
+from oracle import multigrid as G
+import paper_1511_03703_gb300 as E
+from paper_1511_03703_gb300 import inputs
+from helpers import gpu, to_dev, to_np
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def torch():
+    import torch as T
+    assert T.cuda.is_available()
+    E.lib()
+    return T
+
+
+def start(l, e, n):
+    return inputs.random_vector(600 + 100 * l + e, n)
+
+
+def gpu_mg(torch, mg, xs, tol=1e-10, flags=0, degree=2, ratio=5.0, check_every=4):
+    s = xs.shape[0]
+    vals, b = mg.assemble(s, to_dev(inputs.ensemble_layout(xs)))
+    starts = [to_dev(np.stack([start(l, e, m.n) for e in range(s)], axis=1).reshape(-1))
+              for l, m in enumerate(mg.meshes)]
+    x = torch.zeros(mg.meshes[0].n * s, dtype=torch.float64, device=gpu())
+    work = torch.empty(mg.workspace_size(s, vals, starts), dtype=torch.uint8, device=gpu())
+    it, rr, st, stats = mg.solve(s, vals, b, x, tol, 200, work, starts, degree=degree, ratio=ratio, flags=flags,
+                                 check_every=check_every)
+    return to_np(x).reshape(-1, s), it, rr, st
+
+
+@pytest.mark.parametrize("s", [1, 4, 32])
+def test_mg_pcg_matches_oracle(torch, s):
+    N, M = 16, 10
+    mg = E.Multigrid(N, M)
+    assert mg.sizes == [16, 8, 4]
+    xs = inputs.kl_samples(800 + s, 0, s, M)
+    X, it, rr, st = gpu_mg(torch, mg, xs)
+    assert st == [0] * s and max(rr) <= 1.01e-10
+    for e in ([0, s - 1] if s > 2 else range(s)):
+        starts = [start(l, e, (n + 1) ** 3) for l, n in enumerate(G.level_sizes(N))]
+        lv = G.hierarchy(N, M, xs[e], starts)
+        xo, ito, rro, sto = G.mg_pcg(lv, lv[0].load, tol=1e-10)
+        assert sto == 0 and abs(it[e] - ito) <= 1, (e, it[e], ito)
+        assert np.linalg.norm(X[:, e] - xo) <= 1e-8 * np.linalg.norm(xo), e
+
+
+def test_mg_member_independent_of_s_and_graph(torch):
+    mg = E.Multigrid(8, 10)
+    xs = inputs.kl_samples(820, 0, 32, 10)
+    ref = None
+    for s in (1, 4, 32):
+        X, it, rr, st = gpu_mg(torch, mg, xs[:s])
+        cur = (X[:, 0].copy(), it[0])
+        ref = cur if ref is None else ref
+        assert np.array_equal(cur[0], ref[0]) and cur[1] == ref[1], s
+    Xg, itg, _, _ = gpu_mg(torch, mg, xs[:8], flags=E.CG_GRAPH)
+    Xd, itd, _, _ = gpu_mg(torch, mg, xs[:8])
+    assert itg == itd and np.array_equal(Xg, Xd)
+
+
+def test_mg_iterations_do_not_grow_with_the_mesh(torch):
+    its = []
+    for N in (16, 32):
+        mg = E.Multigrid(N, 10)
+        xs = inputs.kl_samples(830, 0, 4, 10)
+        X, it, rr, st = gpu_mg(torch, mg, xs, tol=1e-8)
+        assert st == [0] * 4
+        its.append(max(it))
+    assert its[0] <= 8 and its[1] <= its[0] + 1, its
+
+
+def test_mg_argument_errors(torch):
+    with pytest.raises(E.EnsError):
+        E.Multigrid(7, 10)          # no halving down to N <= 4
+    mg = E.Multigrid(8, 10)
+    xs = inputs.kl_samples(840, 0, 4, 10)
+    vals, b = mg.assemble(4, to_dev(inputs.ensemble_layout(xs)))
+    starts = [torch.zeros(m.n * 4, dtype=torch.float64, device=gpu()) for m in mg.meshes]
+    c = mg._levels(4, vals, starts)
+    c[1].N = 3                       # not half of level 0
+    import ctypes
+    v = ctypes.c_size_t()
+    assert E.lib().ens_mg_workspace_size(2, c, 4, ctypes.byref(v)) == 1
