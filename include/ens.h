@@ -200,7 +200,7 @@ typedef struct ens_cg_stats {
 } ens_cg_stats;
 
 enum {
-    ENS_CG_COUPLED = 1,      /* paper's coupled ensemble CG (Sect. 3.6): alpha, beta
+    ENS_CG_COUPLED = 1,      /* paper's coupled ensemble CG (Sects. 3.4, 3.7): alpha, beta
                                 from member-summed dots, one convergence test */
     ENS_CG_GRAPH = 2,        /* replay the iteration through a captured CUDA graph */
     ENS_CG_TIME_SPMV = 4,    /* record CUDA events around each CG SpMV (with ENS_CG_GRAPH

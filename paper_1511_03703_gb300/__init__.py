@@ -349,11 +349,12 @@ class Multigrid:
         self.meshes = [Mesh(n, M, L=L, device=device) for n in self.sizes]
         self.N, self.M = N, M
 
-    def assemble(self, s, xi_ens, sigma=0.1, kappa0=1.0):
-        """Values of every level and the level-0 right-hand side."""
+    def assemble(self, s, xi_ens, sigma=0.1, kappa0=1.0, df=False):
+        """Values of every level and the level-0 right-hand side (df: the
+        double-float assembly, see assemble())."""
         vals, b0 = [], None
         for l, mesh in enumerate(self.meshes):
-            v, b = mesh.assemble(s, xi_ens, sigma=sigma, kappa0=kappa0)
+            v, b = mesh.assemble(s, xi_ens, sigma=sigma, kappa0=kappa0, df=df)
             vals.append(v)
             if l == 0:
                 b0 = b

@@ -36,7 +36,9 @@ __device__ __forceinline__ int64_t node_id(int i, int j, int k, int n1) {
 // b_c = R r_f on the interior coarse nodes, 0 on the coarse boundary
 // (thread per coarse node and member)
 template <int S>
-__global__ void mg_restrict_kernel(int Nc, const double *__restrict__ rf, double *__restrict__ bc) {
+__global__ void mg_restrict_kernel(const int *active, int Nc, const double *__restrict__ rf,
+                                   double *__restrict__ bc) {
+    if (ld_cg(active) == 0) return;
     const int nc1 = Nc + 1, nf1 = 2 * Nc + 1;
     const int64_t total = (int64_t)nc1 * nc1 * nc1 * S;
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
@@ -62,7 +64,9 @@ __global__ void mg_restrict_kernel(int Nc, const double *__restrict__ rf, double
 
 // x_f += P x_c on the interior fine nodes (thread per fine node and member)
 template <int S>
-__global__ void mg_prolong_kernel(int Nc, const double *__restrict__ xc, double *__restrict__ xf) {
+__global__ void mg_prolong_kernel(const int *active, int Nc, const double *__restrict__ xc,
+                                  double *__restrict__ xf) {
+    if (ld_cg(active) == 0) return;
     const int nc1 = Nc + 1, Nf = 2 * Nc, nf1 = Nf + 1;
     const int64_t total = (int64_t)nf1 * nf1 * nf1 * S;
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
@@ -90,9 +94,10 @@ __global__ void mg_prolong_kernel(int Nc, const double *__restrict__ xc, double 
 // first Chebyshev step from z = 0: z = d = D^-1 res / theta; with x (degree 1)
 // x = z (set) or x += z (add)
 template <int S>
-__global__ void mg_cheb_first_kernel(int64_t n, const double *__restrict__ res, const double *__restrict__ dinv,
-                                     const PcgState *__restrict__ ps, double *__restrict__ z, double *__restrict__ d,
-                                     double *__restrict__ x, int add) {
+__global__ void mg_cheb_first_kernel(const int *active, int64_t n, const double *__restrict__ res,
+                                     const double *__restrict__ dinv, const PcgState *__restrict__ ps,
+                                     double *__restrict__ z, double *__restrict__ d, double *__restrict__ x, int add) {
+    if (ld_cg(active) == 0) return;
     const int64_t total = n * S;
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
          t += (int64_t)gridDim.x * blockDim.x) {
@@ -108,11 +113,12 @@ __global__ void mg_cheb_first_kernel(int64_t n, const double *__restrict__ res, 
 // z_out = z_in + d; on the last step x = z_out (set) or x += z_out (add)
 template <int S>
 __global__ void __launch_bounds__(RowMap<S>::THREADS, 1024 / RowMap<S>::THREADS)
-    mg_cheb_step_kernel(int32_t n, const int32_t *__restrict__ row_map, const int32_t *__restrict__ col,
+    mg_cheb_step_kernel(const int *active, int32_t n, const int32_t *__restrict__ row_map, const int32_t *__restrict__ col,
                         const double *__restrict__ vals, const double *__restrict__ res,
                         const double *__restrict__ dinv, const PcgState *__restrict__ ps, int k,
                         const double *__restrict__ zin, double *__restrict__ zout, double *__restrict__ d,
                         double *__restrict__ x, int add) {
+    if (ld_cg(active) == 0) return;
     constexpr int G = RowMap<S>::G;
     __shared__ ChunkCols cc;
     const int r = threadIdx.x / G, g = threadIdx.x % G;
@@ -137,9 +143,10 @@ __global__ void __launch_bounds__(RowMap<S>::THREADS, 1024 / RowMap<S>::THREADS)
 // r = b - A x
 template <int S>
 __global__ void __launch_bounds__(RowMap<S>::THREADS, 1024 / RowMap<S>::THREADS)
-    mg_residual_kernel(int32_t n, const int32_t *__restrict__ row_map, const int32_t *__restrict__ col,
-                       const double *__restrict__ vals, const double *__restrict__ b, const double *__restrict__ x,
-                       double *__restrict__ r) {
+    mg_residual_kernel(const int *active, int32_t n, const int32_t *__restrict__ row_map,
+                       const int32_t *__restrict__ col, const double *__restrict__ vals,
+                       const double *__restrict__ b, const double *__restrict__ x, double *__restrict__ r) {
+    if (ld_cg(active) == 0) return;
     constexpr int G = RowMap<S>::G;
     __shared__ ChunkCols cc;
     const int rr = threadIdx.x / G, g = threadIdx.x % G;
@@ -156,56 +163,65 @@ __global__ void __launch_bounds__(RowMap<S>::THREADS, 1024 / RowMap<S>::THREADS)
 }
 
 // ------------------------------------------------------------ coarse level
-// Ainv_e = A_e^-1 by in-place Gauss-Jordan elimination (A_e SPD: no
-// pivoting); one CTA per member, the matrix in global scratch (n x n per member)
+// Ainv_e = A_e^-1 by in-place Gauss-Jordan elimination in shared memory
+// (A_e SPD: no pivoting); one CTA per member.  The inverse is stored
+// transposed (invT[j*n+i] = Ainv[i][j]) so that the solve reads it coalesced.
 template <int S>
-__global__ void mg_coarse_inverse_kernel(int32_t n, const int32_t *__restrict__ row_map,
-                                         const int32_t *__restrict__ col, const double *__restrict__ vals,
-                                         double *__restrict__ inv, int *bad) {
+__global__ void __launch_bounds__(512) mg_coarse_inverse_kernel(int32_t n, const int32_t *__restrict__ row_map,
+                                                                const int32_t *__restrict__ col,
+                                                                const double *__restrict__ vals,
+                                                                double *__restrict__ inv, int *bad) {
+    extern __shared__ double A[];  // n x n, row-major
     const int e = blockIdx.x;
-    double *A = inv + (int64_t)e * n * n;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
     for (int t = threadIdx.x; t < n * n; t += blockDim.x) A[t] = 0.0;
     __syncthreads();
     for (int I = threadIdx.x; I < n; I += blockDim.x)
-        for (int32_t p = row_map[I]; p < row_map[I + 1]; ++p) A[(int64_t)I * n + col[p]] = vals[(int64_t)p * S + e];
+        for (int32_t p = row_map[I]; p < row_map[I + 1]; ++p) A[I * n + col[p]] = vals[(int64_t)p * S + e];
     __syncthreads();
     __shared__ double piv;
     for (int k = 0; k < n; ++k) {
         if (threadIdx.x == 0) {
-            const double a = A[(int64_t)k * n + k];
+            const double a = A[k * n + k];
             if (!(a > 0.0)) *bad = 1;
             piv = 1.0 / a;
-            A[(int64_t)k * n + k] = 1.0;
+            A[k * n + k] = 1.0;
         }
         __syncthreads();
-        for (int j = threadIdx.x; j < n; j += blockDim.x) A[(int64_t)k * n + j] *= piv;
+        for (int j = threadIdx.x; j < n; j += blockDim.x) A[k * n + j] *= piv;
         __syncthreads();
-        for (int t = threadIdx.x; t < n * n; t += blockDim.x) {
-            const int i = t / n, j = t % n;
+        // rows i != k, columns j != k: A[i][j] -= A[i][k] A[k][j] (row k and column k are not written)
+        for (int i = warp; i < n; i += nwarps) {
             if (i == k) continue;
-            const double f = A[(int64_t)i * n + k];
-            if (j == k) continue;
-            A[(int64_t)i * n + j] = fma(-f, A[(int64_t)k * n + j], A[(int64_t)i * n + j]);
+            const double f = A[i * n + k];
+            for (int j = lane; j < n; j += 32)
+                if (j != k) A[i * n + j] = fma(-f, A[k * n + j], A[i * n + j]);
         }
         __syncthreads();
         for (int i = threadIdx.x; i < n; i += blockDim.x)
-            if (i != k) A[(int64_t)i * n + k] = -A[(int64_t)i * n + k] * piv;
+            if (i != k) A[i * n + k] = -A[i * n + k] * piv;
         __syncthreads();
+    }
+    double *out = inv + (int64_t)e * n * n;
+    for (int t = threadIdx.x; t < n * n; t += blockDim.x) {
+        const int i = t / n, j = t % n;
+        out[j * n + i] = A[t];
     }
 }
 
-// x = Ainv_e b_e (one CTA per member)
+// x = Ainv_e b_e (one CTA per member; thread i reads column i of invT)
 template <int S>
-__global__ void mg_coarse_solve_kernel(int32_t n, const double *__restrict__ inv, const double *__restrict__ b,
-                                       double *__restrict__ x) {
+__global__ void mg_coarse_solve_kernel(const int *active, int32_t n, const double *__restrict__ inv,
+                                       const double *__restrict__ b, double *__restrict__ x) {
+    if (ld_cg(active) == 0) return;
     const int e = blockIdx.x;
     __shared__ double bs[kMgMaxCoarse];
     for (int i = threadIdx.x; i < n; i += blockDim.x) bs[i] = b[(int64_t)i * S + e];
     __syncthreads();
-    const double *A = inv + (int64_t)e * n * n;
+    const double *invT = inv + (int64_t)e * n * n;
     for (int i = threadIdx.x; i < n; i += blockDim.x) {
         double acc = 0.0;
-        for (int j = 0; j < n; ++j) acc = fma(A[(int64_t)i * n + j], bs[j], acc);
+        for (int j = 0; j < n; ++j) acc = fma(invT[(int64_t)j * n + i], bs[j], acc);
         x[(int64_t)i * S + e] = acc;
     }
 }
@@ -360,6 +376,7 @@ template <int S>
 struct MgSolver {
     std::vector<MgLevel> lv;
     double *inv;
+    const int *active;  // CG active-member count: every V-cycle kernel exits at entry once it is 0
     int degree;
     unsigned eg;  // grid of the elementwise kernels
 
@@ -367,11 +384,11 @@ struct MgSolver {
 
     void smooth(int l, const double *res, double *x, int add, cudaStream_t st) {
         MgLevel &m = lv[l];
-        mg_cheb_first_kernel<S><<<eg, 256, 0, st>>>(m.n, res, m.pa.dinv, m.pa.ps, m.z[0], m.d,
+        mg_cheb_first_kernel<S><<<eg, 256, 0, st>>>(active, m.n, res, m.pa.dinv, m.pa.ps, m.z[0], m.d,
                                                     degree == 1 ? x : nullptr, add);
         for (int k = 1; k < degree; ++k)
             mg_cheb_step_kernel<S><<<chunks(m.n), RowMap<S>::THREADS, 0, st>>>(
-                m.n, m.row_map, m.col, m.vals, res, m.pa.dinv, m.pa.ps, k, m.z[(k - 1) & 1], m.z[k & 1], m.d,
+                active, m.n, m.row_map, m.col, m.vals, res, m.pa.dinv, m.pa.ps, k, m.z[(k - 1) & 1], m.z[k & 1], m.d,
                 k == degree - 1 ? x : nullptr, add);
     }
 
@@ -379,16 +396,16 @@ struct MgSolver {
     void vcycle(int l, const double *b, double *x, cudaStream_t st) {
         const int L = (int)lv.size() - 1;
         if (l == L) {
-            mg_coarse_solve_kernel<S><<<S, 128, 0, st>>>(lv[L].n, inv, b, x);
+            mg_coarse_solve_kernel<S><<<S, 128, 0, st>>>(active, lv[L].n, inv, b, x);
             return;
         }
         MgLevel &m = lv[l], &mc = lv[l + 1];
         smooth(l, b, x, 0, st);                                                     // x = S(b, 0)
-        mg_residual_kernel<S><<<chunks(m.n), RowMap<S>::THREADS, 0, st>>>(m.n, m.row_map, m.col, m.vals, b, x, m.r);
-        mg_restrict_kernel<S><<<eg, 256, 0, st>>>(mc.N, m.r, mc.b);
+        mg_residual_kernel<S><<<chunks(m.n), RowMap<S>::THREADS, 0, st>>>(active, m.n, m.row_map, m.col, m.vals, b, x, m.r);
+        mg_restrict_kernel<S><<<eg, 256, 0, st>>>(active, mc.N, m.r, mc.b);
         vcycle(l + 1, mc.b, mc.x, st);
-        mg_prolong_kernel<S><<<eg, 256, 0, st>>>(mc.N, mc.x, x);                     // x += P x_c
-        mg_residual_kernel<S><<<chunks(m.n), RowMap<S>::THREADS, 0, st>>>(m.n, m.row_map, m.col, m.vals, b, x, m.r);
+        mg_prolong_kernel<S><<<eg, 256, 0, st>>>(active, mc.N, mc.x, x);                     // x += P x_c
+        mg_residual_kernel<S><<<chunks(m.n), RowMap<S>::THREADS, 0, st>>>(active, m.n, m.row_map, m.col, m.vals, b, x, m.r);
         smooth(l, m.r, x, 1, st);                                                   // x = S(b, x)
     }
 
@@ -410,6 +427,7 @@ static int mg_run(int nl, const ens_mg_level *levels, const double *b, double *x
     int *bad = nullptr;
     mg_bytes(nl, levels, S, &mg.lv, static_cast<char *>(work), &c, &z, &mg.inv, &bad);
     mg.degree = degree;
+    mg.active = &c.st->active_count;
     mg.eg = 152 * 4;
     c.b = b;
     c.x = x;
@@ -446,7 +464,10 @@ static int mg_run(int nl, const ens_mg_level *levels, const double *b, double *x
     }
     {
         MgLevel &mc = mg.lv[nl - 1];
-        mg_coarse_inverse_kernel<S><<<S, 256, 0, st>>>(mc.n, mc.row_map, mc.col, mc.vals, mg.inv, bad);
+        const size_t smem = sizeof(double) * (size_t)mc.n * mc.n;
+        ENS_CUDA_TRY(cudaFuncSetAttribute(mg_coarse_inverse_kernel<S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)smem));
+        mg_coarse_inverse_kernel<S><<<S, 512, smem, st>>>(mc.n, mc.row_map, mc.col, mc.vals, mg.inv, bad);
         ++launches;
     }
     pa0.ps = mg.lv[0].pa.ps;

@@ -350,7 +350,7 @@ def block_system(rm, col, vals, bs):
 
 @pytest.mark.parametrize("s", [4, 8])
 def test_cg_coupled_is_cg_on_the_block_system(torch, s):
-    """The coupled ensemble CG of Sect. 3.6 (alpha, beta and the stopping test
+    """The coupled ensemble CG of Sects. 3.4 and 3.7 (alpha, beta and the stopping test
     from member-summed dots) is plain CG on the block-diagonal system of all
     members: the oracle's CG on that system gives the same iterates."""
     N, M = 9, 10
