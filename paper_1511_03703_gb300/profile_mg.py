@@ -1,0 +1,48 @@
+"""Profiling driver: multigrid-preconditioned ensemble CG on an N^3 mesh.
+
+    python -m paper_1511_03703_gb300.profile_mg N s reps
+
+Builds the level hierarchy (N, N/2, ... > 4), then `reps` times assembles
+every level of one ensemble of s samples (double-float assembly, M = 10, seed
+of the 64^3 workload) and solves to 1e-8 with the V-cycle preconditioner
+(graph replay of 4 iterations), printing the wall time of each part.  Used
+for the launch-list summaries under profiles/.
+"""
+import sys
+import time
+
+import numpy as np
+import torch
+
+import paper_1511_03703_gb300 as E
+from paper_1511_03703_gb300 import inputs
+
+
+def main(argv):
+    N, s, reps = int(argv[1]), int(argv[2]), int(argv[3])
+    dev = torch.device("cuda:0")
+    mg = E.Multigrid(N, 10, device=dev)
+    xs = inputs.kl_samples(inputs.SEED_SCALE, 0, s, 10)
+    xi = torch.from_numpy(inputs.ensemble_layout(xs)).to(dev)
+    starts = [torch.from_numpy(np.stack([inputs.random_vector(600 + 100 * l + e, m.n) for e in range(s)],
+                                        axis=1).reshape(-1)).to(dev) for l, m in enumerate(mg.meshes)]
+    x = torch.zeros(mg.meshes[0].n * s, dtype=torch.float64, device=dev)
+    vals, b = mg.assemble(s, xi, df=True)
+    work = torch.empty(mg.workspace_size(s, vals, starts), dtype=torch.uint8, device=dev)
+    for rep in range(reps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        x.zero_()
+        vals, b = mg.assemble(s, xi, df=True)
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        it, rr, st, stats = mg.solve(s, vals, b, x, 1e-8, 500, work, starts, flags=E.CG_GRAPH | E.CG_X0_ZERO,
+                                     check_every=4)
+        torch.cuda.synchronize()
+        t2 = time.perf_counter()
+        print(f"rep {rep}: assemble {1e3 * (t1 - t0):.2f} ms, solve {1e3 * (t2 - t1):.2f} ms, "
+              f"iterations {max(it)}, status {sorted(set(st))}")
+
+
+if __name__ == "__main__":
+    main(sys.argv)
