@@ -1057,6 +1057,73 @@ def main_mg(args):
     print(json.dumps(line))
 
 
+# ------------------------------------------ nonlinear advection-diffusion
+NL_SAMPLES = 256
+NL_ALPHA, NL_BETA, NL_V = 1.0, 10.0, (1.0, 1.0, 1.0)
+NL_TOL, NL_LIN_TOL = 1e-8, 1e-6
+NL_WORKLOAD = ("nonlinear advection-diffusion -div(kappa grad u) + alpha v.grad u + beta u^2 = 1, 64^3 hex Q1 "
+               "mesh, M=10, alpha=1, v=(1,1,1), beta=10, 256 samples as 8 ensembles of s=32: Newton to "
+               "||F|| <= 1e-8 ||F(0)||, GMRES(30) to 1e-6 ||F_k|| per step, right-preconditioned by the V-cycle "
+               "of the diffusion operator")
+
+
+def main_nonlinear(args):
+    """NEXT-4: Newton-GMRES for the nonlinear problem (Sect. 4, Eq. 7 with
+    alpha, beta != 0; Eq. 10); each step assembles every level of every
+    ensemble and solves from u = 0."""
+    import torch
+    import paper_1511_03703_gb300 as E
+    from paper_1511_03703_gb300 import inputs
+    dev = torch.device("cuda:0")
+    E.lib()
+    s = 32
+    t0 = time.perf_counter()
+    nl = E.Nonlinear(N_MESH, M_KL, v=NL_V, precond=E.NL_PRECOND_MG, device=dev)
+    torch.cuda.synchronize()
+    t_setup = time.perf_counter() - t0
+    xs = inputs.kl_samples(inputs.SEED_SCALE, 0, NL_SAMPLES, M_KL)
+    xis = [torch.from_numpy(inputs.ensemble_layout(xs[j:j + s])).to(dev) for j in range(0, NL_SAMPLES, s)]
+    starts = [torch.from_numpy(np.stack([inputs.random_vector(600 + 100 * l + e, m.n) for e in range(s)],
+                                        axis=1).reshape(-1)).to(dev) for l, m in enumerate(nl.meshes)]
+    p = nl.params(NL_ALPHA, NL_BETA, tol=NL_TOL, lin_tol=NL_LIN_TOL, restart=30, max_lin=300, max_newton=20)
+    u = torch.empty(nl.mesh.n * s, dtype=torch.float64, device=dev)
+    vals0, _ = nl.assemble(s, xis[0], df=True)
+    work = torch.empty(nl.workspace_size(s, vals0, starts, p), dtype=torch.uint8, device=dev)
+    del vals0
+
+    def run():
+        newton, lin, launches = [], [], 0
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        for xi in xis:
+            u.zero_()
+            vals, b = nl.assemble(s, xi, df=True)
+            ni, li, rr, st, stats = nl.solve(s, vals, b, u, work, starts, p)
+            if any(st):
+                raise RuntimeError(f"nonlinear: status {st}")
+            newton += ni
+            lin += li
+            launches += stats.kernel_launches
+        torch.cuda.synchronize()
+        return newton, lin, launches, time.perf_counter() - t
+
+    for _ in range(args.warmup):
+        run()
+    newton, lin, launches, sec = run()
+    line = {"metric": "nonlinear advection-diffusion Newton-GMRES sample-solves/s, 1 GB300",
+            "value": NL_SAMPLES / sec, "unit": UNIT, "n_gpus": 1, "steps": 1, "warmup": args.warmup,
+            "ms_per_step": 1e3 * sec, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64", "data": "synthetic",
+            "config": {"workload": NL_WORKLOAD, "levels": nl.mg.sizes, "smoother": "Chebyshev degree 2 on "
+                       "[lam/5, 1.1 lam], 10 power steps", "mesh_setup_seconds": t_setup,
+                       "step": "assembly of every level + Newton solve, per ensemble"},
+            "newton_steps": {"mean": float(np.mean(newton)), "max": int(np.max(newton))},
+            "gmres_steps_per_solve": {"mean": float(np.mean(lin)), "max": int(np.max(lin))},
+            "gmres_steps_per_newton_step": float(np.sum(lin)) / float(np.sum(newton)),
+            "gpu_launches": launches}
+    print(json.dumps(line))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -1070,11 +1137,13 @@ def main():
                          "pre-split once per ensemble (dfv)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--quick", action="store_true", help="skip the other-form run and the s sweep")
-    ap.add_argument("--workload", default="scale", choices=["scale", "mixed", "batched", "guess", "coupled", "pcg", "mg"],
+    ap.add_argument("--workload", default="scale", choices=["scale", "mixed", "batched", "guess", "coupled", "pcg", "mg",
+                                                             "nonlinear"],
                     help="scale: 64^3 ensemble CG (default line); mixed: 128^3 mixed precision; "
                          "batched: 16^3..64^3 x s=4..32 in one batch; guess: learned initial guess; "
                          "coupled: the paper's coupled CG vs per-member CG; pcg: preconditioned CG; "
-                         "mg: multigrid-preconditioned CG")
+                         "mg: multigrid-preconditioned CG; nonlinear: Newton-GMRES for the "
+                         "advection-diffusion problem")
     args = ap.parse_args()
     if args.workload == "mixed" and args.impl != "reference":
         main_mixed(args)
@@ -1093,6 +1162,9 @@ def main():
         return
     if args.workload == "mg" and args.impl != "reference":
         main_mg(args)
+        return
+    if args.workload == "nonlinear" and args.impl != "reference":
+        main_nonlinear(args)
         return
     if args.impl == "reference":
         main_reference(args)

@@ -466,6 +466,84 @@ int ens_guess(const int32_t *dims, const float *params, int64_t n, int32_t s, co
               const double *mean, const float *Phi32, const double *coef_mean, const double *coef_scale,
               double *x0, void *work, size_t work_bytes, void *stream);
 
+/* ---------------------------------- NEXT-4 nonlinear advection-diffusion
+ * The model problem of Sect. 4 (Eq. 7) with alpha, beta != 0, discretised on
+ * the Q1 hex mesh of the linear problem (source 1, u = 0 on the boundary):
+ *   F_i(u) = (A u)_i + alpha int phi_i v.grad(u_h) + beta int phi_i u_h^2 - b_i
+ *   J(u)   = dF/du = A + alpha C + 2 beta M(u),
+ *            C_ij = int phi_i v.grad(phi_j),  M(u)_ij = int phi_i phi_j u_h,
+ * with A, b the ensemble's diffusion matrix and load (ens_assemble); boundary
+ * rows of F and J are those of A (identity), boundary columns of J are 0.
+ * v is a constant velocity; all integrals are exact (2x2x2 Gauss would be).
+ * Newton's method (Eq. 10) solves J(u_k) du = -F(u_k), u_{k+1} = u_k + du,
+ * per member, with restarted GMRES (right-preconditioned, classical
+ * Gram-Schmidt applied twice, Givens rotations) for the non-symmetric J.
+ * The paper's experiments take alpha = beta = 0; the velocity, the source and
+ * the GMRES preconditioner (the V-cycle of the diffusion operator A, fixed for
+ * all Newton steps) are this library's readings. */
+enum {
+    ENS_NL_PRECOND_NONE = 0,  /* plain GMRES */
+    ENS_NL_PRECOND_MG = 1     /* right preconditioner: the V-cycle of ens_mg_pcg on levels[] */
+};
+
+/* C on the graph of the N^3-cell mesh for the velocity v (host double[3]):
+ * C[nnz] FP64, one matrix for every member; boundary rows and columns 0.
+ * Asynchronous. */
+int ens_nl_advection(const ens_graph *g, int32_t N, const double *v, double *C, void *stream);
+
+/* J[nnz*s] = J(u) and F[n*s] = F(u) in one pass, commuted layout.  A: the
+ * ensemble's diffusion values; C: ens_nl_advection; u must vanish on the
+ * boundary.  work: ens_nl_jacobian_workspace_size bytes of device memory.
+ * ENS_ERR_ARG if an interior row of g is not its 27-node window (sorted).
+ * Synchronises `stream`. */
+int ens_nl_jacobian_workspace_size(size_t *bytes);
+int ens_nl_jacobian(const ens_graph *g, int32_t N, int s, const double *A, const double *C, double alpha, double beta,
+                    const double *b, const double *u, double *J, double *F, void *work, void *stream);
+
+/* GMRES(restart) for values * x = b from x = 0, per member, to
+ * ||b - values x|| <= tol ||b|| (the Givens residual estimate; relres_host
+ * gets the true relative residual).  values: ensemble matrix on the graph of
+ * levels[0]; precond ENS_NL_PRECOND_MG takes the V-cycle of ens_mg_pcg with
+ * levels[] (the diffusion hierarchy), degree, ratio, boost and power_iters;
+ * ENS_NL_PRECOND_NONE needs levels[0] only (its graph and N).
+ * 1 <= restart <= 64.  The host polls every check_every steps.
+ * work: ens_gmres_workspace_size bytes.  Synchronises `stream`. */
+int ens_gmres_workspace_size(int nlevels, const ens_mg_level *levels, int s, int restart, int precond,
+                             size_t *bytes);
+int ens_gmres(int nlevels, const ens_mg_level *levels, int s, const double *values, const double *b, double *x,
+              double tol, int restart, int max_iter, int precond, int degree, double ratio, double boost,
+              int power_iters, int check_every, void *work, size_t work_bytes, int32_t *iters_host,
+              double *relres_host, int32_t *status_host, ens_cg_stats *stats_host, void *stream);
+
+typedef struct ens_newton_params {
+    double alpha, beta;     /* advection and reaction coefficients (Eq. 7) */
+    double tol;             /* Newton: stop when ||F(u)|| <= tol ||F(u_0)|| */
+    double lin_tol;         /* GMRES: ||J du + F|| <= lin_tol ||F(u_k)|| */
+    int32_t max_newton;     /* Newton steps at most */
+    int32_t restart;        /* GMRES restart length, 1..64 */
+    int32_t max_lin;        /* GMRES steps per Newton step at most */
+    int32_t precond;        /* ENS_NL_PRECOND_NONE / _MG */
+    int32_t degree;         /* V-cycle: Chebyshev smoother degree */
+    int32_t power_iters;    /* V-cycle: power steps of the eigenvalue estimate */
+    int32_t check_every;    /* GMRES steps between host polls */
+    int32_t reserved;
+    double ratio, boost;    /* V-cycle: smoother interval [lam/ratio, lam], lam = boost x estimate */
+} ens_newton_params;
+
+/* Newton's method for F(u) = 0 per member from the caller's u (in: u_0, 0 on
+ * the boundary; out: the solution).  levels[0].values = A (the diffusion
+ * values, also the finest level of the preconditioner's hierarchy); C from
+ * ens_nl_advection; b the load.  Per member: newton_iters (steps taken),
+ * lin_iters (GMRES steps summed), relres = ||F(u)|| / ||F(u_0)||, status
+ * (ENS_ERR_NOT_CONVERGED after max_newton steps).  work:
+ * ens_newton_workspace_size bytes.  Synchronises `stream`. */
+int ens_newton_workspace_size(int nlevels, const ens_mg_level *levels, int s, const ens_newton_params *p,
+                              size_t *bytes);
+int ens_newton(int nlevels, const ens_mg_level *levels, int s, const double *C, const double *b, double *u,
+               const ens_newton_params *p, void *work, size_t work_bytes, int32_t *newton_iters_host,
+               int32_t *lin_iters_host, double *relres_host, int32_t *status_host, ens_cg_stats *stats_host,
+               void *stream);
+
 #ifdef __cplusplus
 }
 #endif

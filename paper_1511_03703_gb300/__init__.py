@@ -24,6 +24,7 @@ F64, F32, BF16, F64_DF, F64_SPLIT = 0, 1, 2, 3, 4
 CG_COUPLED, CG_GRAPH, CG_TIME_SPMV, CG_DF64, CG_SPLIT64, CG_GUESS_FALLBACK, CG_X0_ZERO = 1, 2, 4, 8, 16, 32, 64
 MLP_DIMS = (10, 256, 256, 64)
 OK, ERR_NOT_CONVERGED, ERR_BREAKDOWN = 0, 5, 6
+ERR_ARG, ERR_WORKSPACE = 1, 9
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _lib = None
@@ -52,6 +53,14 @@ class BatchItemC(ctypes.Structure):
 class MgLevelC(ctypes.Structure):
     _fields_ = [("graph", EnsGraphC), ("N", ctypes.c_int32), ("reserved", ctypes.c_int32),
                 ("values", ctypes.c_void_p), ("power_start", ctypes.c_void_p)]
+
+
+class NewtonParamsC(ctypes.Structure):
+    _fields_ = [("alpha", ctypes.c_double), ("beta", ctypes.c_double), ("tol", ctypes.c_double),
+                ("lin_tol", ctypes.c_double), ("max_newton", ctypes.c_int32), ("restart", ctypes.c_int32),
+                ("max_lin", ctypes.c_int32), ("precond", ctypes.c_int32), ("degree", ctypes.c_int32),
+                ("power_iters", ctypes.c_int32), ("check_every", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("ratio", ctypes.c_double), ("boost", ctypes.c_double)]
 
 
 class CgStats(ctypes.Structure):
@@ -132,6 +141,15 @@ def _declare(L):
                              ctypes.c_float, vp]),
         "ens_mlp_train": (I, [P(i32), vp, vp, vp, vp, i64, vp, vp, i32, i32, i64, ctypes.c_float,
                               ctypes.c_float, ctypes.c_float, ctypes.c_float, vp, i32, vp, sz, vp]),
+        "ens_nl_advection": (I, [P(EnsGraphC), i32, vp, vp, vp]),
+        "ens_nl_jacobian_workspace_size": (I, [P(sz)]),
+        "ens_nl_jacobian": (I, [P(EnsGraphC), i32, I, vp, vp, d, d, vp, vp, vp, vp, vp, vp]),
+        "ens_gmres_workspace_size": (I, [I, P(MgLevelC), I, I, I, P(sz)]),
+        "ens_gmres": (I, [I, P(MgLevelC), I, vp, vp, vp, d, I, I, I, I, d, d, I, I, vp, sz, vp, vp, vp,
+                          P(CgStats), vp]),
+        "ens_newton_workspace_size": (I, [I, P(MgLevelC), I, P(NewtonParamsC), P(sz)]),
+        "ens_newton": (I, [I, P(MgLevelC), I, vp, vp, vp, P(NewtonParamsC), vp, sz, vp, vp, vp, vp, P(CgStats),
+                           vp]),
         "ens_guess_workspace_size": (I, [P(i32), i32, P(sz)]),
         "ens_guess": (I, [P(i32), vp, i64, i32, vp, vp, vp, vp, vp, vp, vp, sz, vp]),
     }
@@ -388,6 +406,125 @@ class Multigrid:
         rc = lib().ens_mg_pcg(len(self.meshes), c, s, _ptr(b), _ptr(x), tol, max_iter, degree, ratio, boost,
                               power_iters, flags, check_every, _ptr(work), work.numel() * work.element_size(),
                               it, rr, stt, ctypes.byref(stats), _stream(stream))
+        if rc not in (0, ERR_NOT_CONVERGED, ERR_BREAKDOWN):
+            _check(rc)
+        return list(it), list(rr), list(stt), stats
+
+
+# ------------------------------------------ nonlinear advection-diffusion
+NL_PRECOND_NONE, NL_PRECOND_MG = 0, 1
+
+
+def nl_advection(mesh, v=(1.0, 1.0, 1.0), out=None, stream=None):
+    """C (nnz float64) of the advection term int phi_i v.grad(phi_j), constant v."""
+    import torch
+    C = out if out is not None else torch.empty(mesh.nnz, dtype=torch.float64, device=mesh.row_map.device)
+    _require_cuda(C)
+    vh = (ctypes.c_double * 3)(*[float(t) for t in v])
+    _check(lib().ens_nl_advection(mesh.graph.ref(), mesh.N, vh, _ptr(C), _stream(stream)))
+    return C
+
+
+def nl_jacobian(mesh, s, A, C, alpha, beta, b, u, J=None, F=None, stream=None):
+    """(J, F) = (J(u), F(u)) of the nonlinear problem (ens_nl_jacobian).  Synchronises."""
+    import torch
+    _require_cuda(A, C, b, u, J, F)
+    dev = A.device
+    J = J if J is not None else torch.empty(mesh.nnz * s, dtype=torch.float64, device=dev)
+    F = F if F is not None else torch.empty(mesh.n * s, dtype=torch.float64, device=dev)
+    nb = ctypes.c_size_t()
+    _check(lib().ens_nl_jacobian_workspace_size(ctypes.byref(nb)))
+    work = torch.empty(nb.value, dtype=torch.uint8, device=dev)
+    _check(lib().ens_nl_jacobian(mesh.graph.ref(), mesh.N, s, _ptr(A), _ptr(C), alpha, beta, _ptr(b), _ptr(u),
+                                 _ptr(J), _ptr(F), _ptr(work), _stream(stream)))
+    return J, F
+
+
+class Nonlinear:
+    """Newton-GMRES for the nonlinear advection-diffusion problem on the
+    N^3 mesh (ens_newton): the advection matrix of the velocity v, and the
+    hierarchy of the multigrid preconditioner (or the single mesh)."""
+
+    def __init__(self, N, M, v=(1.0, 1.0, 1.0), precond=NL_PRECOND_MG, L=1.0, device="cuda"):
+        self.precond = precond
+        if precond == NL_PRECOND_MG:
+            self.mg = Multigrid(N, M, L=L, device=device)
+            self.meshes = self.mg.meshes
+        else:
+            self.mg = None
+            self.meshes = [Mesh(N, M, L=L, device=device)]
+        self.mesh = self.meshes[0]
+        self.N, self.M = N, M
+        self.v = tuple(float(t) for t in v)
+        self.C = nl_advection(self.mesh, self.v)
+
+    def assemble(self, s, xi_ens, sigma=0.1, kappa0=1.0, df=False):
+        """Diffusion values of every level and the load (see Multigrid.assemble)."""
+        if self.mg is not None:
+            return self.mg.assemble(s, xi_ens, sigma=sigma, kappa0=kappa0, df=df)
+        v, b = self.mesh.assemble(s, xi_ens, sigma=sigma, kappa0=kappa0, df=df)
+        return [v], b
+
+    def _levels(self, values, power_starts):
+        c = (MgLevelC * len(self.meshes))()
+        for l, mesh in enumerate(self.meshes):
+            _require_cuda(values[l])
+            c[l].graph = mesh.graph.c
+            c[l].N = mesh.N
+            c[l].values = values[l].data_ptr()
+            c[l].power_start = power_starts[l].data_ptr() if power_starts is not None else None
+        return c
+
+    def params(self, alpha, beta, tol=1e-8, lin_tol=1e-10, max_newton=20, restart=30, max_lin=500, degree=2,
+               ratio=5.0, boost=1.1, power_iters=10, check_every=4):
+        p = NewtonParamsC()
+        p.alpha, p.beta, p.tol, p.lin_tol = alpha, beta, tol, lin_tol
+        p.max_newton, p.restart, p.max_lin, p.precond = max_newton, restart, max_lin, self.precond
+        p.degree, p.power_iters, p.check_every = degree, power_iters, check_every
+        p.ratio, p.boost = ratio, boost
+        return p
+
+    def workspace_size(self, s, values, power_starts, params):
+        v = ctypes.c_size_t()
+        _check(lib().ens_newton_workspace_size(len(self.meshes), self._levels(values, power_starts), s,
+                                               ctypes.byref(params), ctypes.byref(v)))
+        return v.value
+
+    def solve(self, s, values, b, u, work, power_starts, params, stream=None):
+        """Newton from the given u.  Returns (newton_iters[s], lin_iters[s],
+        relres[s], status[s], CgStats).  Synchronises."""
+        _require_cuda(b, u, work)
+        ni = (ctypes.c_int32 * s)()
+        li = (ctypes.c_int32 * s)()
+        rr = (ctypes.c_double * s)()
+        stt = (ctypes.c_int32 * s)()
+        stats = CgStats()
+        rc = lib().ens_newton(len(self.meshes), self._levels(values, power_starts), s, _ptr(self.C), _ptr(b),
+                              _ptr(u), ctypes.byref(params), _ptr(work), work.numel() * work.element_size(), ni,
+                              li, rr, stt, ctypes.byref(stats), _stream(stream))
+        if rc not in (0, ERR_NOT_CONVERGED, ERR_BREAKDOWN):
+            _check(rc)
+        return list(ni), list(li), list(rr), list(stt), stats
+
+    def gmres_workspace_size(self, s, values, power_starts, restart):
+        v = ctypes.c_size_t()
+        _check(lib().ens_gmres_workspace_size(len(self.meshes), self._levels(values, power_starts), s, restart,
+                                              self.precond, ctypes.byref(v)))
+        return v.value
+
+    def gmres(self, s, values, J, b, x, work, power_starts, tol, restart=30, max_iter=500, degree=2, ratio=5.0,
+              boost=1.1, power_iters=10, check_every=4, stream=None):
+        """ens_gmres for J x = b (values: the preconditioner's levels).
+        Returns (iters[s], relres[s], status[s], CgStats).  Synchronises."""
+        _require_cuda(J, b, x, work)
+        it = (ctypes.c_int32 * s)()
+        rr = (ctypes.c_double * s)()
+        stt = (ctypes.c_int32 * s)()
+        stats = CgStats()
+        rc = lib().ens_gmres(len(self.meshes), self._levels(values, power_starts), s, _ptr(J), _ptr(b), _ptr(x),
+                             tol, restart, max_iter, self.precond, degree, ratio, boost, power_iters, check_every,
+                             _ptr(work), work.numel() * work.element_size(), it, rr, stt, ctypes.byref(stats),
+                             _stream(stream))
         if rc not in (0, ERR_NOT_CONVERGED, ERR_BREAKDOWN):
             _check(rc)
         return list(it), list(rr), list(stt), stats

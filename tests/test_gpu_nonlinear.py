@@ -1,0 +1,180 @@
+"""Newton-GMRES for the nonlinear advection-diffusion problem against the FP64
+oracle (oracle/nonlinear.py).
+
+Bars: the advection matrix, the Jacobian and the residual to 1e-14 of their
+scale; GMRES iteration counts within one of the oracle's (two with restarts)
+and solutions to 1e-8 relative; Newton step counts equal to the oracle's,
+GMRES steps per solve within one per Newton step, solutions to 1e-8; member
+results bitwise independent of s.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from oracle import multigrid as G
+from oracle import nonlinear as NL
+import paper_1511_03703_gb300 as E
+from paper_1511_03703_gb300 import inputs
+from helpers import gpu, to_dev, to_np
+
+pytestmark = pytest.mark.gpu
+
+V = (1.0, 1.0, 1.0)
+
+
+@pytest.fixture(scope="module")
+def torch():
+    import torch as T
+    assert T.cuda.is_available()
+    E.lib()
+    return T
+
+
+def start(l, e, n):
+    return inputs.random_vector(600 + 100 * l + e, n)
+
+
+def dev_starts(nl, s):
+    return [to_dev(np.stack([start(l, e, m.n) for e in range(s)], axis=1).reshape(-1))
+            for l, m in enumerate(nl.meshes)]
+
+
+def zero_boundary_field(seed, mesh_o, s, scale=0.3):
+    return [scale * inputs.random_vector(seed + e, mesh_o.n) * ~mesh_o.bm for e in range(s)]
+
+
+def test_advection_matches_oracle(torch):
+    N, v = 7, (0.7, -1.3, 2.1)
+    mesh = E.Mesh(N, 3)
+    C = to_np(E.nl_advection(mesh, v))
+    ref = NL.advection_values(NL.Mesh(N), v)
+    assert np.max(np.abs(C - ref)) <= 1e-15 * np.max(np.abs(ref))
+
+
+@pytest.mark.parametrize("s", [1, 4, 32])
+def test_jacobian_and_residual_match_oracle(torch, s):
+    N, M, alpha, beta = 6, 4, 5.0, 10.0
+    mesh = E.Mesh(N, M)
+    xs = inputs.kl_samples(900 + s, 0, s, M)
+    A, b = mesh.assemble(s, to_dev(inputs.ensemble_layout(xs)))
+    C = E.nl_advection(mesh, V)
+    mo = NL.Mesh(N)
+    us = zero_boundary_field(910, mo, s)
+    J, F = E.nl_jacobian(mesh, s, A, C, alpha, beta, b, to_dev(O.to_ensemble(us)))
+    J, F = to_np(J).reshape(-1, s), to_np(F).reshape(-1, s)
+    for e in ([0, s - 1] if s > 2 else range(s)):
+        prob = NL.Problem(N, M, xs[e], alpha, beta, v=V)
+        Jo, Fo = prob.jacobian(us[e]), prob.residual(us[e])
+        assert np.max(np.abs(J[:, e] - Jo)) <= 1e-14 * np.max(np.abs(Jo)), e
+        # F's scale: the terms it sums, |J| |u| + |b|
+        scale = np.max(O.spmv(mo.rm, mo.col, np.abs(Jo), np.abs(us[e])) + np.abs(prob.b))
+        assert np.max(np.abs(F[:, e] - Fo)) <= 1e-14 * scale, e
+
+
+def gmres_case(torch, s, precond, restart, N=8, seed=920):
+    M = 10
+    nl = E.Nonlinear(N, M, v=V, precond=precond)
+    xs = inputs.kl_samples(seed, 0, s, M)
+    vals, b = nl.assemble(s, to_dev(inputs.ensemble_layout(xs)))
+    mo = NL.Mesh(N)
+    us = zero_boundary_field(seed + 50, mo, s)
+    J, _ = E.nl_jacobian(nl.mesh, s, vals[0], nl.C, 5.0, 10.0, b, to_dev(O.to_ensemble(us)))
+    rhs = [inputs.random_vector(seed + 100 + e, mo.n) for e in range(s)]
+    starts = dev_starts(nl, s) if precond == E.NL_PRECOND_MG else None
+    x = torch.empty(mo.n * s, dtype=torch.float64, device=gpu())
+    work = torch.empty(nl.gmres_workspace_size(s, vals, starts, restart), dtype=torch.uint8, device=gpu())
+    it, rr, st, stats = nl.gmres(s, vals, J, to_dev(O.to_ensemble(rhs)), x, work, starts, 1e-10, restart=restart,
+                                 max_iter=400)
+    return nl, xs, us, rhs, to_np(J).reshape(-1, s), to_np(x).reshape(-1, s), it, rr, st
+
+
+@pytest.mark.parametrize("s", [1, 4, 32])
+@pytest.mark.parametrize("precond", [E.NL_PRECOND_NONE, E.NL_PRECOND_MG])
+def test_gmres_matches_oracle(torch, s, precond):
+    nl, xs, us, rhs, J, X, it, rr, st = gmres_case(torch, s, precond, 30)
+    assert st == [0] * s and max(rr) <= 1.01e-10
+    mo = NL.Mesh(8)
+    for e in ([0, s - 1] if s > 2 else range(s)):
+        pre = None
+        if precond == E.NL_PRECOND_MG:
+            lv = G.hierarchy(8, 10, xs[e], [start(l, e, (n + 1) ** 3) for l, n in enumerate(G.level_sizes(8))])
+            pre = lambda r, lv=lv: G.vcycle(lv, r)
+        xo, ito, rro, sto = NL.gmres(mo.rm, mo.col, J[:, e], rhs[e], pre, restart=30, tol=1e-10, max_iter=400)
+        assert sto == 0 and abs(it[e] - ito) <= 1, (e, it[e], ito)
+        assert np.linalg.norm(X[:, e] - xo) <= 1e-8 * np.linalg.norm(xo), e
+
+
+def test_gmres_restarts_match_oracle(torch):
+    s = 4
+    nl, xs, us, rhs, J, X, it, rr, st = gmres_case(torch, s, E.NL_PRECOND_NONE, 5, N=6, seed=940)
+    assert st == [0] * s and max(rr) <= 1.01e-10
+    mo = NL.Mesh(6)
+    for e in range(s):
+        xo, ito, rro, sto = NL.gmres(mo.rm, mo.col, J[:, e], rhs[e], None, restart=5, tol=1e-10, max_iter=400)
+        assert sto == 0 and ito > 5 and abs(it[e] - ito) <= 2, (e, it[e], ito)
+        assert np.linalg.norm(X[:, e] - xo) <= 1e-8 * np.linalg.norm(xo), e
+
+
+def newton_case(torch, s, N, alpha, beta, precond=E.NL_PRECOND_MG, seed=960, **kw):
+    M = 10
+    nl = E.Nonlinear(N, M, v=V, precond=precond)
+    xs = inputs.kl_samples(seed, 0, s, M)
+    vals, b = nl.assemble(s, to_dev(inputs.ensemble_layout(xs)))
+    starts = dev_starts(nl, s) if precond == E.NL_PRECOND_MG else None
+    p = nl.params(alpha, beta, **kw)
+    u = torch.zeros(nl.mesh.n * s, dtype=torch.float64, device=gpu())
+    work = torch.empty(nl.workspace_size(s, vals, starts, p), dtype=torch.uint8, device=gpu())
+    ni, li, rr, st, stats = nl.solve(s, vals, b, u, work, starts, p)
+    return xs, to_np(u).reshape(-1, s), ni, li, rr, st
+
+
+@pytest.mark.parametrize("s", [1, 4, 32])
+def test_newton_matches_oracle(torch, s):
+    N, alpha, beta, tol, lin_tol = 8, 1.0, 10.0, 1e-10, 1e-11
+    xs, U, ni, li, rr, st = newton_case(torch, s, N, alpha, beta, tol=tol, lin_tol=lin_tol)
+    assert st == [0] * s and max(rr) <= tol
+    for e in ([0, s - 1] if s > 2 else range(s)):
+        prob = NL.Problem(N, 10, xs[e], alpha, beta, v=V)
+        lv = G.hierarchy(N, 10, xs[e], [start(l, e, (n + 1) ** 3) for l, n in enumerate(G.level_sizes(N))])
+        uo, ko, lino, hist, sto = NL.newton(prob, tol=tol, lin_tol=lin_tol, precond=lambda r, lv=lv: G.vcycle(lv, r))
+        assert sto == 0 and ni[e] == ko, (e, ni[e], ko)
+        assert abs(li[e] - sum(lino)) <= ko, (e, li[e], lino)
+        assert np.linalg.norm(U[:, e] - uo) <= 1e-8 * np.linalg.norm(uo), e
+
+
+def test_newton_member_independent_of_s(torch):
+    ref = None
+    for s in (1, 4, 32):
+        xs, U, ni, li, rr, st = newton_case(torch, s, 8, 1.0, 10.0, seed=980, tol=1e-10, lin_tol=1e-11)
+        cur = (U[:, 0].copy(), ni[0], li[0])
+        ref = cur if ref is None else ref
+        assert np.array_equal(cur[0], ref[0]) and cur[1:] == ref[1:], s
+
+
+def test_newton_linear_case_is_one_solve(torch):
+    s, N = 4, 8
+    xs, U, ni, li, rr, st = newton_case(torch, s, N, 0.0, 0.0, precond=E.NL_PRECOND_NONE, tol=1e-10,
+                                        lin_tol=1e-12, restart=60)
+    assert st == [0] * s and ni == [1] * s
+    rm, col = O.graph(N)
+    for e in range(s):
+        v, bo = O.assemble(N, 10, xs[e], rm, col)
+        xo, _, _, _ = O.cg(rm, col, v, bo, tol=1e-12)
+        assert np.linalg.norm(U[:, e] - xo) <= 1e-9 * np.linalg.norm(xo), e
+
+
+def test_newton_argument_errors(torch):
+    nl = E.Nonlinear(8, 10, v=V, precond=E.NL_PRECOND_NONE)
+    xs = inputs.kl_samples(990, 0, 4, 10)
+    vals, b = nl.assemble(4, to_dev(inputs.ensemble_layout(xs)))
+    u = torch.zeros(nl.mesh.n * 4, dtype=torch.float64, device=gpu())
+    for kw in ({"restart": 0}, {"restart": 65}, {"check_every": 0}):
+        p = nl.params(1.0, 1.0, **kw)
+        with pytest.raises(E.EnsError):
+            nl.workspace_size(4, vals, None, p) if "restart" in kw else nl.solve(
+                4, vals, b, u, torch.empty(1 << 20, dtype=torch.uint8, device=gpu()), None, p)
+    p = nl.params(1.0, 1.0)
+    small = torch.empty(1024, dtype=torch.uint8, device=gpu())
+    with pytest.raises(E.EnsError) as ei:
+        nl.solve(4, vals, b, u, small, None, p)
+    assert ei.value.code == E.ERR_WORKSPACE
