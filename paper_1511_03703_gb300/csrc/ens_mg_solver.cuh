@@ -104,7 +104,7 @@ __global__ void mg_cheb_first_kernel(const int *active, int64_t n, const double 
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
          t += (int64_t)gridDim.x * blockDim.x) {
         const int e = (int)(t % S);
-        const double zv = res[t] * dinv[t] / ps->theta[e];
+        const double zv = res[t] * dinv[t] * ps->inv_theta[e];
         z[t] = zv;
         d[t] = zv;
         if (x) x[t] = add ? x[t] + zv : zv;
@@ -134,7 +134,7 @@ __global__ void __launch_bounds__(RowMap<S>::THREADS, 1024 / RowMap<S>::THREADS)
         const int64_t i = i0 + j;
         const int e = (S == 1) ? 0 : 2 * g + j;
         const double rk = ps->rhoc[k][e], rk1 = ps->rhoc[k - 1][e];
-        const double dv = rk * rk1 * d[i] + (2.0 * rk / ps->delta[e]) * (dinv[i] * (res[i] - (j == 0 ? az.x : az.y)));
+        const double dv = rk * rk1 * d[i] + ps->c2[k][e] * (dinv[i] * (res[i] - (j == 0 ? az.x : az.y)));
         const double zv = zin[i] + dv;
         d[i] = dv;
         zout[i] = zv;

@@ -35,6 +35,7 @@ constexpr int kGmMaxRestart = 64;
 // ------------------------------------------------------------ device state
 struct NlState {            // Newton (and the right-hand-side norm of ens_gmres)
     double f0[32], fn[32];  // ||F(u_0)||, ||F(u_k)||
+    double inv_fn[32];      // 1 / ||F(u_k)|| (0 when ||F|| = 0)
     int nact[32];           // member takes a Newton step (or a linear solve) now
     int newton_iters[32], lin_iters[32], status[32];
     int active_count;
@@ -111,13 +112,14 @@ __device__ __forceinline__ void window_pass(double (&T)[27]) {
 //   interior row: J_p = A_p + alpha C_p + 2 beta M_p, N_p = A_p + alpha C_p + beta M_p,
 //                 F_i = sum_p N_p u_col(p) - b_i  (M_p = 0 for boundary columns)
 //   boundary row: J_p = A_p, F_i = sum_p A_p u_col(p) - b_i
+// (h3 = h^3 = 1 / N^3)
 template <int S>
 __global__ void __launch_bounds__(256) nl_jacobian_kernel(int32_t n, int32_t N, const int32_t *__restrict__ row_map,
                                                           const int32_t *__restrict__ col,
                                                           const double *__restrict__ A, const double *__restrict__ C,
                                                           double alpha, double beta, const double *__restrict__ b,
                                                           const double *__restrict__ u, double *__restrict__ J,
-                                                          double *__restrict__ F, NlState *ns) {
+                                                          double *__restrict__ F, NlState *ns, double h3) {
     const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (t >= (int64_t)n * S) return;
     const int e = (int)(t % S);
@@ -149,7 +151,6 @@ __global__ void __launch_bounds__(256) nl_jacobian_kernel(int32_t n, int32_t N, 
     window_pass<1>(T);
     window_pass<3>(T);
     window_pass<9>(T);
-    const double h3 = 1.0 / ((double)N * N * N);
     int bad = 0;
 #pragma unroll
     for (int w = 0; w < 27; ++w) {
@@ -198,6 +199,7 @@ __global__ void __launch_bounds__(RowMap<S>::THREADS, 1024 / RowMap<S>::THREADS)
     if (e < S) {
         const double fn = sqrt(ld_cg(tn.buf[tn.levels] + e));
         ns->fn[e] = fn;
+        if (mode != 2) ns->inv_fn[e] = (fn > 0.0) ? 1.0 / fn : 0.0;
         if (mode == 1) {
             ns->f0[e] = fn;
             ns->status[e] = (fn == fn) ? ENS_OK : ENS_ERR_BREAKDOWN;
@@ -289,7 +291,7 @@ __global__ void gm_start_kernel(GmArgs a) {
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
          t += (int64_t)gridDim.x * blockDim.x) {
         const int e = (int)(t % S);
-        a.V[t] = ns->nact[e] ? a.sign * a.rhs[t] / ns->fn[e] : 0.0;
+        a.V[t] = ns->nact[e] ? a.sign * a.rhs[t] * ns->inv_fn[e] : 0.0;
         a.x[t] = 0.0;
     }
     if (blockIdx.x == 0 && threadIdx.x < 32) {
@@ -773,7 +775,7 @@ static int newton_run(int nlevels, const ens_mg_level *lv, const double *C, cons
     int32_t h[2];
     for (int it = 0; it <= p->max_newton; ++it) {
         nl_jacobian_kernel<S><<<jgrid, 256, 0, st>>>(n, N, a.row_map, a.col, lv[0].values, C, p->alpha, p->beta, b,
-                                                    u, bufs.J, bufs.F, bufs.ns);
+                                                    u, bufs.J, bufs.F, bufs.ns, 1.0 / ((double)N * N * N));
         nl_norm_kernel<S><<<sv.grid, RowMap<S>::THREADS, 0, st>>>(n, bufs.F, a.tn, bufs.ns, 0, it, p->tol,
                                                                  p->max_newton);
         sv.launches += 2;
@@ -854,7 +856,7 @@ extern "C" int ens_nl_jacobian(const ens_graph *gp, int32_t N, int s, const doub
     const unsigned grid = (unsigned)(((int64_t)g.num_rows * s + 255) / 256);
 #define NL_JAC(SS)                                                                                              \
     (nl_jacobian_kernel<SS><<<grid, 256, 0, st>>>(g.num_rows, N, g.row_map, g.col_entry, A, C, alpha, beta, b, u, \
-                                                  J, F, ns),                                                    \
+                                                  J, F, ns, 1.0 / ((double)N * N * N)),                         \
      ENS_OK)
     switch (s) {
         case 1: NL_JAC(1); break;

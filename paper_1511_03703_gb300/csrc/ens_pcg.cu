@@ -53,7 +53,7 @@ __global__ void __launch_bounds__(RowMap<S>::THREADS, 1024 / RowMap<S>::THREADS)
             }
             double z = rv * a.dinv[i];
             if (a.degree >= 1) {
-                z = z / a.ps->theta[e];
+                z = z * a.ps->inv_theta[e];
                 a.d[i] = z;
             }
             a.zk[0][i] = z;
@@ -105,7 +105,7 @@ __global__ void __launch_bounds__(RowMap<S>::THREADS, 1024 / RowMap<S>::THREADS)
             const double axv = (j == 0) ? az.x : az.y;
             const double rk = ps->rhoc[k][e], rk1 = ps->rhoc[k - 1][e];
             const double rv = c.r[i];
-            const double dv = rk * rk1 * a.d[i] + (2.0 * rk / ps->delta[e]) * (a.dinv[i] * (rv - axv));
+            const double dv = rk * rk1 * a.d[i] + ps->c2[k][e] * (a.dinv[i] * (rv - axv));
             const double zv = zin[i] + dv;
             a.d[i] = dv;
             zout[i] = zv;

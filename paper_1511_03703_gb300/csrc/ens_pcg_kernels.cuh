@@ -15,6 +15,11 @@ struct PcgState {
     double rhoc[kPcMaxDegree][32];     // rho_k of the Chebyshev recurrence
     double rr[32];                     // r.r of the current iteration (stop test)
     double nrm[32];                    // power iteration: ||y||
+    // per-member factors of the element-wise updates, formed once so that no
+    // kernel divides per element (an FP64 division costs many FP64-pipe slots)
+    double inv_nrm[32];                // 1 / ||y||
+    double inv_theta[32];              // 1 / theta
+    double c2[kPcMaxDegree][32];       // 2 rho_k / delta
 };
 
 struct PcgArgs {
@@ -72,17 +77,21 @@ __global__ void __launch_bounds__(RowMap<S>::THREADS, 1024 / RowMap<S>::THREADS)
     chunk_tree<S>(sm, v0, v1, r, g, c.t1, blockIdx.x, 0);
     if (!dot_tree_propagate(c.t1, blockIdx.x, 1)) return;
     const int e = threadIdx.x;
-    if (e < S) a.ps->nrm[e] = sqrt(ld_cg(c.t1.buf[c.t1.levels] + e));
+    if (e < S) {
+        const double nv = sqrt(ld_cg(c.t1.buf[c.t1.levels] + e));
+        a.ps->nrm[e] = nv;
+        a.ps->inv_nrm[e] = 1.0 / nv;
+    }
     __threadfence();
 }
 
-// v = y / ||y||_e
+// v = y / ||y||_e (as y * (1 / ||y||_e))
 template <int S>
 __global__ void pc_scale_kernel(PcgArgs a) {
     const int64_t total = (int64_t)a.c.n * S;
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
          t += (int64_t)gridDim.x * blockDim.x)
-        a.v[t] = a.y[t] / a.ps->nrm[t % S];
+        a.v[t] = a.y[t] * a.ps->inv_nrm[t % S];
 }
 
 // lam_e = (v.Av) / (v.Dv) and the Chebyshev parameters of member e
@@ -122,11 +131,14 @@ __global__ void __launch_bounds__(RowMap<S>::THREADS, 1024 / RowMap<S>::THREADS)
         const double theta = 0.5 * (lmax + lmin), delta = 0.5 * (lmax - lmin), sigma = theta / delta;
         ps->theta[e] = theta;
         ps->delta[e] = delta;
+        ps->inv_theta[e] = 1.0 / theta;
         double rho = 1.0 / sigma;
         ps->rhoc[0][e] = rho;
+        ps->c2[0][e] = 2.0 * rho / delta;
         for (int k = 1; k < kPcMaxDegree; ++k) {
             rho = 1.0 / (2.0 * sigma - rho);
             ps->rhoc[k][e] = rho;
+            ps->c2[k][e] = 2.0 * rho / delta;
         }
     }
     __threadfence();
