@@ -988,7 +988,8 @@ def main_pcg(args):
 MG_SAMPLES = 256
 MG_WORKLOAD = ("KL diffusion, 64^3 hex Q1 mesh, M=10, 256 samples as 8 ensembles of s=32, CG to 1e-8: "
                "multigrid-preconditioned ensemble CG (V-cycle over 64^3..4^3, Chebyshev-2 smoothers, "
-               "direct coarse solve) vs plain ensemble CG")
+               "direct coarse solve; mg: level-0 SpMVs in double-float from pre-split values, mg_f64: all "
+               "FP64) vs plain ensemble CG")
 
 
 def main_mg(args):
@@ -1013,8 +1014,8 @@ def main_mg(args):
     vdf = torch.empty(2 * mesh.nnz * s, dtype=torch.float32, device=dev)
     wcg = torch.empty(E.cg_workspace_size(mesh.n, s), dtype=torch.uint8, device=dev)
     x = torch.empty(mesh.n * s, dtype=torch.float64, device=dev)
-    vals0, _ = mg.assemble(s, xis[0])
-    wmg = torch.empty(mg.workspace_size(s, vals0, starts), dtype=torch.uint8, device=dev)
+    vals0, _ = mg.assemble(s, xis[0], values_df=vdf)
+    wmg = torch.empty(mg.workspace_size(s, vals0, starts, vdf), dtype=torch.uint8, device=dev)
     del vals0
 
     def run(form):
@@ -1023,10 +1024,12 @@ def main_mg(args):
         t = time.perf_counter()
         for xi in xis:
             x.zero_()
-            if form == "mg":
-                vals, b = mg.assemble(s, xi, df=True)
+            if form in ("mg", "mg_f64"):
+                # mg: level 0 (K1 and the V-cycle's finest SpMVs) from pre-split values
+                pre = vdf if form == "mg" else None
+                vals, b = mg.assemble(s, xi, df=True, values_df=pre)
                 it, rr, st, _ = mg.solve(s, vals, b, x, TOL, 500, wmg, starts, flags=E.CG_GRAPH | E.CG_X0_ZERO,
-                                         check_every=4)
+                                         check_every=4, values_df=pre)
             else:
                 vals, b = mesh.assemble(s, xi, values_df=vdf if form == "cg_dfv" else None)
                 it, rr, st, _ = E.cg(mesh.graph, s, vals, b, x, TOL, 10000, wcg,
@@ -1039,7 +1042,7 @@ def main_mg(args):
         return its, time.perf_counter() - t
 
     out = {}
-    for form in ("cg_f64", "cg_dfv", "mg"):
+    for form in ("cg_f64", "cg_dfv", "mg_f64", "mg"):
         for _ in range(args.warmup):
             run(form)
         its, sec = run(form)
@@ -1087,8 +1090,9 @@ def main_nonlinear(args):
                                         axis=1).reshape(-1)).to(dev) for l, m in enumerate(nl.meshes)]
     p = nl.params(NL_ALPHA, NL_BETA, tol=NL_TOL, lin_tol=NL_LIN_TOL, restart=30, max_lin=300, max_newton=20)
     u = torch.empty(nl.mesh.n * s, dtype=torch.float64, device=dev)
-    vals0, _ = nl.assemble(s, xis[0], df=True)
-    work = torch.empty(nl.workspace_size(s, vals0, starts, p), dtype=torch.uint8, device=dev)
+    vdf = torch.empty(2 * nl.mesh.nnz * s, dtype=torch.float32, device=dev)  # level 0 pre-split (V-cycle)
+    vals0, _ = nl.assemble(s, xis[0], values_df=vdf)
+    work = torch.empty(nl.workspace_size(s, vals0, starts, p, vdf), dtype=torch.uint8, device=dev)
     del vals0
 
     def run():
@@ -1097,8 +1101,8 @@ def main_nonlinear(args):
         t = time.perf_counter()
         for xi in xis:
             u.zero_()
-            vals, b = nl.assemble(s, xi, df=True)
-            ni, li, rr, st, stats = nl.solve(s, vals, b, u, work, starts, p)
+            vals, b = nl.assemble(s, xi, values_df=vdf)
+            ni, li, rr, st, stats = nl.solve(s, vals, b, u, work, starts, p, values_df=vdf)
             if any(st):
                 raise RuntimeError(f"nonlinear: status {st}")
             newton += ni

@@ -298,6 +298,9 @@ typedef struct ens_mg_level {
     int32_t reserved;
     const double *values;       /* the ensemble's matrix on this level, commuted layout */
     const double *power_start;  /* n*s start vector of the level's eigenvalue estimate */
+    const float *values_df;     /* optional: values pre-split into float pairs (ens_assemble_df or
+                                   ens_convert_values ENS_F64_DF); the level's SpMVs then run in
+                                   double-float (FP64-class, as ens_cg_df); NULL: FP64 SpMVs */
 } ens_mg_level;
 int ens_mg_workspace_size(int nlevels, const ens_mg_level *levels, int s, size_t *bytes);
 int ens_mg_pcg(int nlevels, const ens_mg_level *levels, int s, const double *b, double *x, double tol,

@@ -52,7 +52,7 @@ class BatchItemC(ctypes.Structure):
 
 class MgLevelC(ctypes.Structure):
     _fields_ = [("graph", EnsGraphC), ("N", ctypes.c_int32), ("reserved", ctypes.c_int32),
-                ("values", ctypes.c_void_p), ("power_start", ctypes.c_void_p)]
+                ("values", ctypes.c_void_p), ("power_start", ctypes.c_void_p), ("values_df", ctypes.c_void_p)]
 
 
 class NewtonParamsC(ctypes.Structure):
@@ -367,18 +367,20 @@ class Multigrid:
         self.meshes = [Mesh(n, M, L=L, device=device) for n in self.sizes]
         self.N, self.M = N, M
 
-    def assemble(self, s, xi_ens, sigma=0.1, kappa0=1.0, df=False):
+    def assemble(self, s, xi_ens, sigma=0.1, kappa0=1.0, df=False, values_df=None):
         """Values of every level and the level-0 right-hand side (df: the
-        double-float assembly, see assemble())."""
+        double-float assembly, see assemble(); values_df: a 2*nnz*s float32
+        tensor that receives level 0's pre-split values, for solve())."""
         vals, b0 = [], None
         for l, mesh in enumerate(self.meshes):
-            v, b = mesh.assemble(s, xi_ens, sigma=sigma, kappa0=kappa0, df=df)
+            v, b = mesh.assemble(s, xi_ens, sigma=sigma, kappa0=kappa0, df=df,
+                                 values_df=values_df if l == 0 else None)
             vals.append(v)
             if l == 0:
                 b0 = b
         return vals, b0
 
-    def _levels(self, s, values, power_starts):
+    def _levels(self, s, values, power_starts, values_df=None):
         c = (MgLevelC * len(self.meshes))()
         for l, mesh in enumerate(self.meshes):
             _require_cuda(values[l], power_starts[l])
@@ -386,19 +388,23 @@ class Multigrid:
             c[l].N = mesh.N
             c[l].values = values[l].data_ptr()
             c[l].power_start = power_starts[l].data_ptr()
+        if values_df is not None:
+            _require_cuda(values_df)
+            c[0].values_df = values_df.data_ptr()
         return c
 
-    def workspace_size(self, s, values, power_starts):
+    def workspace_size(self, s, values, power_starts, values_df=None):
         v = ctypes.c_size_t()
-        c = self._levels(s, values, power_starts)
+        c = self._levels(s, values, power_starts, values_df)
         _check(lib().ens_mg_workspace_size(len(self.meshes), c, s, ctypes.byref(v)))
         return v.value
 
     def solve(self, s, values, b, x, tol, max_iter, work, power_starts, degree=2, ratio=5.0, boost=1.1,
-              power_iters=10, flags=0, check_every=8, stream=None):
-        """Returns (iters[s], relres[s], status[s], CgStats).  Synchronises."""
+              power_iters=10, flags=0, check_every=8, stream=None, values_df=None):
+        """Returns (iters[s], relres[s], status[s], CgStats).  values_df: level
+        0's pre-split values (the level-0 SpMVs in double-float).  Synchronises."""
         _require_cuda(b, x, work)
-        c = self._levels(s, values, power_starts)
+        c = self._levels(s, values, power_starts, values_df)
         it = (ctypes.c_int32 * s)()
         rr = (ctypes.c_double * s)()
         stt = (ctypes.c_int32 * s)()
@@ -458,14 +464,14 @@ class Nonlinear:
         self.v = tuple(float(t) for t in v)
         self.C = nl_advection(self.mesh, self.v)
 
-    def assemble(self, s, xi_ens, sigma=0.1, kappa0=1.0, df=False):
+    def assemble(self, s, xi_ens, sigma=0.1, kappa0=1.0, df=False, values_df=None):
         """Diffusion values of every level and the load (see Multigrid.assemble)."""
         if self.mg is not None:
-            return self.mg.assemble(s, xi_ens, sigma=sigma, kappa0=kappa0, df=df)
-        v, b = self.mesh.assemble(s, xi_ens, sigma=sigma, kappa0=kappa0, df=df)
+            return self.mg.assemble(s, xi_ens, sigma=sigma, kappa0=kappa0, df=df, values_df=values_df)
+        v, b = self.mesh.assemble(s, xi_ens, sigma=sigma, kappa0=kappa0, df=df, values_df=values_df)
         return [v], b
 
-    def _levels(self, values, power_starts):
+    def _levels(self, values, power_starts, values_df=None):
         c = (MgLevelC * len(self.meshes))()
         for l, mesh in enumerate(self.meshes):
             _require_cuda(values[l])
@@ -473,6 +479,9 @@ class Nonlinear:
             c[l].N = mesh.N
             c[l].values = values[l].data_ptr()
             c[l].power_start = power_starts[l].data_ptr() if power_starts is not None else None
+        if values_df is not None:
+            _require_cuda(values_df)
+            c[0].values_df = values_df.data_ptr()
         return c
 
     def params(self, alpha, beta, tol=1e-8, lin_tol=1e-10, max_newton=20, restart=30, max_lin=500, degree=2,
@@ -484,14 +493,15 @@ class Nonlinear:
         p.ratio, p.boost = ratio, boost
         return p
 
-    def workspace_size(self, s, values, power_starts, params):
+    def workspace_size(self, s, values, power_starts, params, values_df=None):
         v = ctypes.c_size_t()
-        _check(lib().ens_newton_workspace_size(len(self.meshes), self._levels(values, power_starts), s,
+        _check(lib().ens_newton_workspace_size(len(self.meshes), self._levels(values, power_starts, values_df), s,
                                                ctypes.byref(params), ctypes.byref(v)))
         return v.value
 
-    def solve(self, s, values, b, u, work, power_starts, params, stream=None):
-        """Newton from the given u.  Returns (newton_iters[s], lin_iters[s],
+    def solve(self, s, values, b, u, work, power_starts, params, stream=None, values_df=None):
+        """Newton from the given u (values_df: level 0's pre-split values for
+        the preconditioner).  Returns (newton_iters[s], lin_iters[s],
         relres[s], status[s], CgStats).  Synchronises."""
         _require_cuda(b, u, work)
         ni = (ctypes.c_int32 * s)()
@@ -499,9 +509,9 @@ class Nonlinear:
         rr = (ctypes.c_double * s)()
         stt = (ctypes.c_int32 * s)()
         stats = CgStats()
-        rc = lib().ens_newton(len(self.meshes), self._levels(values, power_starts), s, _ptr(self.C), _ptr(b),
-                              _ptr(u), ctypes.byref(params), _ptr(work), work.numel() * work.element_size(), ni,
-                              li, rr, stt, ctypes.byref(stats), _stream(stream))
+        rc = lib().ens_newton(len(self.meshes), self._levels(values, power_starts, values_df), s, _ptr(self.C),
+                              _ptr(b), _ptr(u), ctypes.byref(params), _ptr(work), work.numel() * work.element_size(),
+                              ni, li, rr, stt, ctypes.byref(stats), _stream(stream))
         if rc not in (0, ERR_NOT_CONVERGED, ERR_BREAKDOWN):
             _check(rc)
         return list(ni), list(li), list(rr), list(stt), stats

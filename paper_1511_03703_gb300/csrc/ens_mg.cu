@@ -92,6 +92,7 @@ static size_t mg_pcg_layout(int nl, const ens_mg_level *lv, int s, std::vector<M
     double *pp = reinterpret_cast<double *>(take(v0));
     double *pq = reinterpret_cast<double *>(take(v0));
     double *pz = reinterpret_cast<double *>(take(v0));
+    float2 *pdf = lv[0].values_df ? reinterpret_cast<float2 *>(take(v0)) : nullptr;  // split p for K1
     off += mg_layout(nl, lv, s, out, base ? base + off : nullptr, coarse_inv, bad);
     if (base && c0) {
         *c0 = (*out)[0].pa.c;
@@ -99,13 +100,20 @@ static size_t mg_pcg_layout(int nl, const ens_mg_level *lv, int s, std::vector<M
         c0->r = pr;
         c0->p = pp;
         c0->q = pq;
-        c0->pdf = nullptr;
+        c0->pdf = pdf;
+        if (pdf) {
+            c0->vdf = reinterpret_cast<const float2 *>(lv[0].values_df);
+            c0->pf_cap = 0xffffffffu;
+            c0->val_bytes = (uint64_t)lv[0].graph.num_entries * s * 8u;
+        }
         *zpcg = pz;
     }
     return off;
 }
 
-template <int S>
+// MODE 3: level 0 has pre-split values, so K1 runs the pre-split SpMV (K3
+// writes the split copy of p) and the V-cycle's level-0 SpMVs run in MODE 3
+template <int S, int MODE>
 static int mg_run(int nl, const ens_mg_level *levels, const double *b, double *x, double tol, int max_iter,
                   int degree, double ratio, double boost, int power_iters, int flags, int check_every, void *work,
                   int32_t *iters_host, double *relres_host, int32_t *status_host, ens_cg_stats *stats,
@@ -142,11 +150,11 @@ static int mg_run(int nl, const ens_mg_level *levels, const double *b, double *x
         if (!init) mg_pcg_resid_kernel<S><<<grid, RowMap<S>::THREADS, 0, s_>>>(pa0);
         mg.vcycle(0, c.r, z, s_);
         mg_pcg_rz_kernel<S><<<grid, RowMap<S>::THREADS, 0, s_>>>(pa0, z, init);
-        cg_update_kernel<S, 0><<<vgrid, VecMap<S>::THREADS, 0, s_>>>(c3);
+        cg_update_kernel<S, MODE><<<vgrid, VecMap<S>::THREADS, 0, s_>>>(c3);
     };
     const int per_iter = 4 + mg.launches_per_vcycle();
-    cg_init_kernel<S, 0><<<grid, RowMap<S>::THREADS, 0, st>>>(c);
-    cg_zero_kernel<S, 0><<<152 * 2, 256, 0, st>>>(c);
+    cg_init_kernel<S, MODE><<<grid, RowMap<S>::THREADS, 0, st>>>(c);
+    cg_zero_kernel<S, MODE><<<152 * 2, 256, 0, st>>>(c);
     stage(1, st);
     launches += 2 + per_iter - 2;
     ENS_LAUNCH_CHECK("ens_mg_pcg init");
@@ -164,7 +172,7 @@ static int mg_run(int nl, const ens_mg_level *levels, const double *b, double *x
         cudaError_t ce = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
         if (ce == cudaSuccess) {
             for (int i = 0; i < check_every; ++i) {
-                cg_spmv_kernel<S, 0><<<grid, RowMap<S>::THREADS, 0, cap>>>(c);
+                cg_spmv_kernel<S, MODE><<<grid, RowMap<S>::THREADS, 0, cap>>>(c);
                 stage(0, cap);
             }
             ce = cudaStreamEndCapture(cap, &graph);
@@ -184,7 +192,7 @@ static int mg_run(int nl, const ens_mg_level *levels, const double *b, double *x
             if (ce != cudaSuccess) { rc = cuda_fail(ce, "cudaGraphLaunch"); break; }
         } else {
             for (int i = 0; i < check_every; ++i) {
-                cg_spmv_kernel<S, 0><<<grid, RowMap<S>::THREADS, 0, st>>>(c);
+                cg_spmv_kernel<S, MODE><<<grid, RowMap<S>::THREADS, 0, st>>>(c);
                 stage(0, st);
             }
         }
@@ -253,16 +261,16 @@ extern "C" int ens_mg_pcg(int nlevels, const ens_mg_level *levels, int s, const 
     const size_t need = mg_pcg_layout(nlevels, levels, s, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr);
     if (work_bytes < need) return fail(ENS_ERR_WORKSPACE, "mg workspace %zu < %zu bytes", work_bytes, need);
     cudaStream_t st = as_stream(stream);
+    const bool pre = levels[0].values_df != nullptr;
+#define MG_CALL(SS, MM)                                                                                        \
+    mg_run<SS, MM>(nlevels, levels, b, x, tol, max_iter, degree, ratio, boost, power_iters, flags, check_every, \
+                   work, iters_host, relres_host, status_host, stats_host, st)
     switch (s) {
-        case 1: return mg_run<1>(nlevels, levels, b, x, tol, max_iter, degree, ratio, boost, power_iters, flags,
-                                 check_every, work, iters_host, relres_host, status_host, stats_host, st);
-        case 4: return mg_run<4>(nlevels, levels, b, x, tol, max_iter, degree, ratio, boost, power_iters, flags,
-                                 check_every, work, iters_host, relres_host, status_host, stats_host, st);
-        case 8: return mg_run<8>(nlevels, levels, b, x, tol, max_iter, degree, ratio, boost, power_iters, flags,
-                                 check_every, work, iters_host, relres_host, status_host, stats_host, st);
-        case 16: return mg_run<16>(nlevels, levels, b, x, tol, max_iter, degree, ratio, boost, power_iters, flags,
-                                   check_every, work, iters_host, relres_host, status_host, stats_host, st);
-        default: return mg_run<32>(nlevels, levels, b, x, tol, max_iter, degree, ratio, boost, power_iters, flags,
-                                   check_every, work, iters_host, relres_host, status_host, stats_host, st);
+        case 1: return pre ? MG_CALL(1, 3) : MG_CALL(1, 0);
+        case 4: return pre ? MG_CALL(4, 3) : MG_CALL(4, 0);
+        case 8: return pre ? MG_CALL(8, 3) : MG_CALL(8, 0);
+        case 16: return pre ? MG_CALL(16, 3) : MG_CALL(16, 0);
+        default: return pre ? MG_CALL(32, 3) : MG_CALL(32, 0);
     }
+#undef MG_CALL
 }

@@ -64,10 +64,11 @@ __global__ void mg_restrict_kernel(const int *active, int Nc, const double *__re
     }
 }
 
-// x_f += P x_c on the interior fine nodes (thread per fine node and member)
+// x_f += P x_c on the interior fine nodes (thread per fine node and member);
+// xfs != NULL: also the double-float split of the new x_f
 template <int S>
 __global__ void mg_prolong_kernel(const int *active, int Nc, const double *__restrict__ xc,
-                                  double *__restrict__ xf) {
+                                  double *__restrict__ xf, float2 *__restrict__ xfs, int *split_bad) {
     if (ld_cg(active) == 0) return;
     const int nc1 = Nc + 1, Nf = 2 * Nc, nf1 = Nf + 1;
     const int64_t total = (int64_t)nf1 * nf1 * nf1 * S;
@@ -88,17 +89,60 @@ __global__ void mg_prolong_kernel(const int *active, int Nc, const double *__res
                     const double w = ((i & 1) ? 0.5 : 1.0) * ((j & 1) ? 0.5 : 1.0) * ((k & 1) ? 0.5 : 1.0);
                     acc = fma(w, xc[node_id(ci, cj, ck, nc1) * S + e], acc);
                 }
-        xf[t] += acc;
+        const double xn = xf[t] + acc;
+        xf[t] = xn;
+        if (xfs) store_split1(xfs, t, xn, split_bad);
     }
 }
 
 // ------------------------------------------------------------ smoother
+// Level SpMVs in two forms: MODE 0 FP64; MODE 3 double-float from the
+// level's pre-split values and the pre-split input vector (the form of the
+// pre-split CG SpMV, values prefetched into L2), falling back to FP64 once a
+// producer met a value outside the split range (*split_bad).  Producers
+// write the split copy next to every FP64 vector that an SpMV reads.
+struct MgSpmv {
+    const int32_t *row_map, *col;
+    const double *vals;
+    const float2 *vdf;   // MODE 3: pre-split values
+    uint64_t val_bytes;  // MODE 3: bytes of the pre-split values (prefetch bound)
+    int *split_bad;
+};
+
+template <int S, int MODE>
+__device__ __forceinline__ double2 mg_chunk_spmv(const MgSpmv &A, ChunkCols &cc, int32_t n, const double *x,
+                                                 const float2 *xs, int r, int g, bool valid) {
+    if constexpr (MODE == 3) {
+        const bool staged =
+            stage_chunk_pf(cc, A.row_map, A.col, blockIdx.x, n, A.vdf, S * 8u, A.val_bytes, 0xffffffffu);
+        if (ld_cg(A.split_bad) == 0) return chunk_spmv_dfv<S>(cc, staged, A.col, A.vdf, A.vals, xs, r, g, valid);
+        return chunk_spmv<S, double>(cc, staged, A.col, A.vals, x, r, g, valid);
+    } else {
+        const bool staged = stage_chunk(cc, A.row_map, A.col, blockIdx.x, n);
+        return chunk_spmv<S, double>(cc, staged, A.col, A.vals, x, r, g, valid);
+    }
+}
+
+// write a pair of members' values (and their split when vs != NULL)
+template <int S>
+__device__ __forceinline__ void mg_put2(double *v, float2 *vs, int64_t R, int g, double a0, double a1, int *bad) {
+    if constexpr (S == 1) {
+        v[R] = a0;
+        if (vs) store_split1(vs, R, a0, bad);
+    } else {
+        const int64_t i = R * S + 2 * g;
+        reinterpret_cast<double2 *>(v)[i >> 1] = make_double2(a0, a1);
+        if (vs) store_split(vs, i, a0, a1, bad);
+    }
+}
+
 // first Chebyshev step from z = 0: z = d = D^-1 res / theta; with x (degree 1)
-// x = z (set) or x += z (add)
+// x = z (set) or x += z (add); zs / xs: the split copies (NULL: none)
 template <int S>
 __global__ void mg_cheb_first_kernel(const int *active, int64_t n, const double *__restrict__ res,
                                      const double *__restrict__ dinv, const PcgState *__restrict__ ps,
-                                     double *__restrict__ z, double *__restrict__ d, double *__restrict__ x, int add) {
+                                     double *__restrict__ z, float2 *__restrict__ zs, double *__restrict__ d,
+                                     double *__restrict__ x, float2 *__restrict__ xs, int add, int *split_bad) {
     if (ld_cg(active) == 0) return;
     const int64_t total = n * S;
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
@@ -107,54 +151,58 @@ __global__ void mg_cheb_first_kernel(const int *active, int64_t n, const double 
         const double zv = res[t] * dinv[t] * ps->inv_theta[e];
         z[t] = zv;
         d[t] = zv;
-        if (x) x[t] = add ? x[t] + zv : zv;
+        if (zs) store_split1(zs, t, zv, split_bad);
+        if (x) {
+            const double xv = add ? x[t] + zv : zv;
+            x[t] = xv;
+            if (xs) store_split1(xs, t, xv, split_bad);
+        }
     }
 }
 
 // Chebyshev step k: w = res - A z_in, d = rho_k rho_{k-1} d + (2 rho_k/delta) D^-1 w,
 // z_out = z_in + d; on the last step x = z_out (set) or x += z_out (add)
-template <int S>
+template <int S, int MODE>
 __global__ void __launch_bounds__(RowMap<S>::THREADS, 1024 / RowMap<S>::THREADS)
-    mg_cheb_step_kernel(const int *active, int32_t n, const int32_t *__restrict__ row_map, const int32_t *__restrict__ col,
-                        const double *__restrict__ vals, const double *__restrict__ res,
+    mg_cheb_step_kernel(const int *active, int32_t n, MgSpmv A, const double *__restrict__ res,
                         const double *__restrict__ dinv, const PcgState *__restrict__ ps, int k,
-                        const double *__restrict__ zin, double *__restrict__ zout, double *__restrict__ d,
-                        double *__restrict__ x, int add) {
+                        const double *__restrict__ zin, const float2 *__restrict__ zins, double *__restrict__ zout,
+                        float2 *__restrict__ zouts, double *__restrict__ d, double *__restrict__ x,
+                        float2 *__restrict__ xs, int add) {
     if (ld_cg(active) == 0) return;
     constexpr int G = RowMap<S>::G;
     __shared__ ChunkCols cc;
     const int r = threadIdx.x / G, g = threadIdx.x % G;
     const int64_t R = (int64_t)blockIdx.x * 32 + r;
-    const bool staged = stage_chunk(cc, row_map, col, blockIdx.x, n);
-    const double2 az = chunk_spmv<S, double>(cc, staged, col, vals, zin, r, g, R < n);
+    const double2 az = mg_chunk_spmv<S, MODE>(A, cc, n, zin, zins, r, g, R < n);
     if (R >= n || (S == 1 && g != 0)) return;
     const int w = (S == 1) ? 1 : 2;
     const int64_t i0 = (S == 1) ? R : R * S + 2 * g;
+    double zo[2] = {0.0, 0.0}, xo[2] = {0.0, 0.0};
     for (int j = 0; j < w; ++j) {
         const int64_t i = i0 + j;
         const int e = (S == 1) ? 0 : 2 * g + j;
         const double rk = ps->rhoc[k][e], rk1 = ps->rhoc[k - 1][e];
         const double dv = rk * rk1 * d[i] + ps->c2[k][e] * (dinv[i] * (res[i] - (j == 0 ? az.x : az.y)));
-        const double zv = zin[i] + dv;
+        zo[j] = zin[i] + dv;
         d[i] = dv;
-        zout[i] = zv;
-        if (x) x[i] = add ? x[i] + zv : zv;
+        if (x) xo[j] = add ? x[i] + zo[j] : zo[j];
     }
+    mg_put2<S>(zout, zouts, R, g, zo[0], zo[1], A.split_bad);
+    if (x) mg_put2<S>(x, xs, R, g, xo[0], xo[1], A.split_bad);
 }
 
 // r = b - A x
-template <int S>
+template <int S, int MODE>
 __global__ void __launch_bounds__(RowMap<S>::THREADS, 1024 / RowMap<S>::THREADS)
-    mg_residual_kernel(const int *active, int32_t n, const int32_t *__restrict__ row_map,
-                       const int32_t *__restrict__ col, const double *__restrict__ vals,
-                       const double *__restrict__ b, const double *__restrict__ x, double *__restrict__ r) {
+    mg_residual_kernel(const int *active, int32_t n, MgSpmv A, const double *__restrict__ b,
+                       const double *__restrict__ x, const float2 *__restrict__ xs, double *__restrict__ r) {
     if (ld_cg(active) == 0) return;
     constexpr int G = RowMap<S>::G;
     __shared__ ChunkCols cc;
     const int rr = threadIdx.x / G, g = threadIdx.x % G;
     const int64_t R = (int64_t)blockIdx.x * 32 + rr;
-    const bool staged = stage_chunk(cc, row_map, col, blockIdx.x, n);
-    const double2 ax = chunk_spmv<S, double>(cc, staged, col, vals, x, rr, g, R < n);
+    const double2 ax = mg_chunk_spmv<S, MODE>(A, cc, n, x, xs, rr, g, R < n);
     if (R >= n) return;
     if constexpr (S == 1) {
         if (g == 0) r[R] = b[R] - ax.x;
@@ -235,16 +283,19 @@ struct MgLevel {
     int32_t n, N;
     const int32_t *row_map, *col;
     const double *vals;
-    PcgArgs pa;      // per-level set-up (power iteration) and Chebyshev state
+    const float2 *vdf;    // pre-split values (the level's SpMVs in MODE 3), or NULL
+    uint64_t val_bytes;   // 8 bytes per value and member
+    PcgArgs pa;           // per-level set-up (power iteration) and Chebyshev state
     double *b, *x, *r, *z[2], *d;
+    float2 *xs, *zs[2];   // split copies of x, z0, z1 (MODE 3 levels)
+    int *split_bad;       // shared by all levels
 };
-
-// workspace of the whole solve; with lv != NULL also lays the levels out
 
 // Scratch of the hierarchy from `base` (NULL: only count the bytes): per
 // level the Chebyshev state, ten vectors (D, D^-1, two power-iteration
-// vectors, b, x, r, z0, z1, d) and two dot trees; then the coarsest level's
-// inverses and a status word.  Returns the bytes (a multiple of 256).
+// vectors, b, x, r, z0, z1, d) and two dot trees, plus four split copies
+// (x, z0, z1, v) on levels with pre-split values; then the coarsest level's
+// inverses and two status words.  Returns the bytes (a multiple of 256).
 static size_t mg_layout(int nl, const ens_mg_level *lv, int s, std::vector<MgLevel> *out, char *base,
                         double **coarse_inv, int **bad) {
     size_t off = 0;
@@ -262,6 +313,9 @@ static size_t mg_layout(int nl, const ens_mg_level *lv, int s, std::vector<MgLev
         for (int i = 0; i < 10; ++i) vec[i] = reinterpret_cast<double *>(take(vb));
         char *t1 = take(dot_tree_bytes(n, s));
         char *t2 = take(dot_tree_bytes(n, 2 * s));
+        float2 *sv[4] = {nullptr, nullptr, nullptr, nullptr};
+        if (lv[l].values_df)
+            for (int i = 0; i < 4; ++i) sv[i] = reinterpret_cast<float2 *>(take(vb));
         if (out && base) {
             MgLevel &m = (*out)[l];
             m.n = (int32_t)n;
@@ -269,12 +323,20 @@ static size_t mg_layout(int nl, const ens_mg_level *lv, int s, std::vector<MgLev
             m.row_map = lv[l].graph.row_map;
             m.col = lv[l].graph.col_entry;
             m.vals = lv[l].values;
+            m.vdf = reinterpret_cast<const float2 *>(lv[l].values_df);
+            m.val_bytes = (uint64_t)lv[l].graph.num_entries * s * 8u;
             memset(&m.pa, 0, sizeof(m.pa));
             CgArgs &c = m.pa.c;
             c.n = (int32_t)n;
             c.row_map = m.row_map;
             c.col = m.col;
             c.vals = m.vals;
+            c.vdf = m.vdf;
+            c.pdf = sv[3];
+            c.val_bytes = m.val_bytes;
+            m.xs = sv[0];
+            m.zs[0] = sv[1];
+            m.zs[1] = sv[2];
             dot_tree_layout(&c.t1, n, s, t1);
             dot_tree_layout(&c.t2, n, 2 * s, t2);
             m.pa.ps = ps;
@@ -293,9 +355,15 @@ static size_t mg_layout(int nl, const ens_mg_level *lv, int s, std::vector<MgLev
     const int64_t nc = lv[nl - 1].graph.num_rows;
     double *inv = reinterpret_cast<double *>(take(sizeof(double) * (size_t)nc * nc * s));
     int *badp = reinterpret_cast<int *>(take(sizeof(int)));
+    int *split_bad = reinterpret_cast<int *>(take(sizeof(int)));
     if (base) {
         *coarse_inv = inv;
         *bad = badp;
+        if (out)
+            for (int l = 0; l < nl; ++l) {
+                (*out)[l].split_bad = split_bad;
+                (*out)[l].pa.split_bad = split_bad;
+            }
     }
     return off;
 }
@@ -310,14 +378,50 @@ struct MgSolver {
 
     static unsigned chunks(int64_t n) { return (unsigned)((n + 31) / 32); }
 
-    void smooth(int l, const double *res, double *x, int add, cudaStream_t st) {
+    static MgSpmv spmv_of(const MgLevel &m) {
+        MgSpmv A;
+        A.row_map = m.row_map;
+        A.col = m.col;
+        A.vals = m.vals;
+        A.vdf = m.vdf;
+        A.val_bytes = m.val_bytes;
+        A.split_bad = m.split_bad;
+        return A;
+    }
+
+    // x = S(res, x) (add) or S(res, 0); xs: the split copy of x to write (NULL: none)
+    void smooth(int l, const double *res, double *x, float2 *xs, int add, cudaStream_t st) {
         MgLevel &m = lv[l];
-        mg_cheb_first_kernel<S><<<eg, 256, 0, st>>>(active, m.n, res, m.pa.dinv, m.pa.ps, m.z[0], m.d,
-                                                    degree == 1 ? x : nullptr, add);
-        for (int k = 1; k < degree; ++k)
-            mg_cheb_step_kernel<S><<<chunks(m.n), RowMap<S>::THREADS, 0, st>>>(
-                active, m.n, m.row_map, m.col, m.vals, res, m.pa.dinv, m.pa.ps, k, m.z[(k - 1) & 1], m.z[k & 1], m.d,
-                k == degree - 1 ? x : nullptr, add);
+        const bool pre = m.vdf != nullptr;
+        mg_cheb_first_kernel<S><<<eg, 256, 0, st>>>(active, m.n, res, m.pa.dinv, m.pa.ps, m.z[0],
+                                                    (pre && degree > 1) ? m.zs[0] : nullptr, m.d,
+                                                    degree == 1 ? x : nullptr, degree == 1 ? xs : nullptr, add,
+                                                    m.split_bad);
+        const MgSpmv A = spmv_of(m);
+        for (int k = 1; k < degree; ++k) {
+            const bool last = (k == degree - 1);
+            const double *zin = m.z[(k - 1) & 1];
+            const float2 *zins = m.zs[(k - 1) & 1];
+            double *zout = m.z[k & 1];
+            float2 *zouts = (pre && !last) ? m.zs[k & 1] : nullptr;
+            double *xo = last ? x : nullptr;
+            float2 *xso = last ? xs : nullptr;
+            if (pre)
+                mg_cheb_step_kernel<S, 3><<<chunks(m.n), RowMap<S>::THREADS, 0, st>>>(
+                    active, m.n, A, res, m.pa.dinv, m.pa.ps, k, zin, zins, zout, zouts, m.d, xo, xso, add);
+            else
+                mg_cheb_step_kernel<S, 0><<<chunks(m.n), RowMap<S>::THREADS, 0, st>>>(
+                    active, m.n, A, res, m.pa.dinv, m.pa.ps, k, zin, nullptr, zout, nullptr, m.d, xo, nullptr, add);
+        }
+    }
+
+    void residual(int l, const double *b, const double *x, cudaStream_t st) {
+        MgLevel &m = lv[l];
+        const MgSpmv A = spmv_of(m);
+        if (m.vdf)
+            mg_residual_kernel<S, 3><<<chunks(m.n), RowMap<S>::THREADS, 0, st>>>(active, m.n, A, b, x, m.xs, m.r);
+        else
+            mg_residual_kernel<S, 0><<<chunks(m.n), RowMap<S>::THREADS, 0, st>>>(active, m.n, A, b, x, nullptr, m.r);
     }
 
     // x = V_l(b)
@@ -328,13 +432,14 @@ struct MgSolver {
             return;
         }
         MgLevel &m = lv[l], &mc = lv[l + 1];
-        smooth(l, b, x, 0, st);                                                     // x = S(b, 0)
-        mg_residual_kernel<S><<<chunks(m.n), RowMap<S>::THREADS, 0, st>>>(active, m.n, m.row_map, m.col, m.vals, b, x, m.r);
+        float2 *xs = m.vdf ? m.xs : nullptr;  // x's split copy: read by this level's residuals
+        smooth(l, b, x, xs, 0, st);                                                 // x = S(b, 0)
+        residual(l, b, x, st);
         mg_restrict_kernel<S><<<eg, 256, 0, st>>>(active, mc.N, m.r, mc.b);
         vcycle(l + 1, mc.b, mc.x, st);
-        mg_prolong_kernel<S><<<eg, 256, 0, st>>>(active, mc.N, mc.x, x);                     // x += P x_c
-        mg_residual_kernel<S><<<chunks(m.n), RowMap<S>::THREADS, 0, st>>>(active, m.n, m.row_map, m.col, m.vals, b, x, m.r);
-        smooth(l, m.r, x, 1, st);                                                   // x = S(b, x)
+        mg_prolong_kernel<S><<<eg, 256, 0, st>>>(active, mc.N, mc.x, x, xs, m.split_bad);  // x += P x_c
+        residual(l, b, x, st);
+        smooth(l, m.r, x, nullptr, 1, st);                                          // x = S(b, x)
     }
 
     // Per level: D and D^-1, the power estimate of the largest eigenvalue of
@@ -346,6 +451,7 @@ struct MgSolver {
         const int nl = (int)lv.size();
         int rc;
         ENS_CUDA_TRY(cudaMemsetAsync(bad, 0, sizeof(int), st));
+        ENS_CUDA_TRY(cudaMemsetAsync(lv[0].split_bad, 0, sizeof(int), st));
         for (int l = 0; l < nl; ++l) {
             MgLevel &m = lv[l];
             PcgArgs &a = m.pa;
@@ -361,12 +467,22 @@ struct MgSolver {
                                                                          const_cast<double *>(a.dinv));
             ENS_CUDA_TRY(cudaMemcpyAsync(a.v, levels[l].power_start, sizeof(double) * (size_t)nt,
                                          cudaMemcpyDeviceToDevice, st));
-            for (int k = 0; k < power_iters; ++k) {
-                pc_power_kernel<S><<<chunks(m.n), RowMap<S>::THREADS, 0, st>>>(a);
-                pc_scale_kernel<S><<<152 * 4, 256, 0, st>>>(a);
+            if (m.vdf) {
+                pc_split_kernel<S><<<152 * 4, 256, 0, st>>>(a);
+                for (int k = 0; k < power_iters; ++k) {
+                    pc_power_kernel<S, 3><<<chunks(m.n), RowMap<S>::THREADS, 0, st>>>(a);
+                    pc_scale_kernel<S, 3><<<152 * 4, 256, 0, st>>>(a);
+                }
+                pc_rayleigh_kernel<S, 3><<<chunks(m.n), RowMap<S>::THREADS, 0, st>>>(a);
+                *launches += 3 + 2 * power_iters;
+            } else {
+                for (int k = 0; k < power_iters; ++k) {
+                    pc_power_kernel<S><<<chunks(m.n), RowMap<S>::THREADS, 0, st>>>(a);
+                    pc_scale_kernel<S><<<152 * 4, 256, 0, st>>>(a);
+                }
+                pc_rayleigh_kernel<S><<<chunks(m.n), RowMap<S>::THREADS, 0, st>>>(a);
+                *launches += 2 + 2 * power_iters;
             }
-            pc_rayleigh_kernel<S><<<chunks(m.n), RowMap<S>::THREADS, 0, st>>>(a);
-            *launches += 2 + 2 * power_iters;
         }
         MgLevel &mc = lv[nl - 1];
         const size_t smem = sizeof(double) * (size_t)mc.n * mc.n;
@@ -397,6 +513,8 @@ static int mg_check(int nl, const ens_mg_level *lv, int s) {
             return fail(ENS_ERR_ARG, "ens_mg: level %d has N=%d, not half of %d", l, lv[l].N, lv[l - 1].N);
         if (!lv[l].values) return fail(ENS_ERR_ARG, "ens_mg: level %d: NULL values", l);
         if (s > 1 && !aligned16(lv[l].values)) return fail(ENS_ERR_ALIGN, "ens_mg: level %d values not aligned", l);
+        if (lv[l].values_df && !aligned16(lv[l].values_df))
+            return fail(ENS_ERR_ALIGN, "ens_mg: level %d values_df not aligned", l);
     }
     if (lv[nl - 1].graph.num_rows > kMgMaxCoarse)
         return fail(ENS_ERR_UNSUPPORTED, "ens_mg: coarsest level has %d rows (at most %d: N <= 4)",

@@ -31,7 +31,24 @@ struct PcgArgs {
     double *v, *y;            // power iteration
     int degree;               // 0: Jacobi, >= 1: Chebyshev steps
     double boost, ratio;
+    int *split_bad;           // MODE 3 set-up kernels: a split copy met a value out of range
 };
+
+// the set-up SpMV of v: MODE 0 FP64; MODE 3 double-float from the pre-split
+// values c.vdf and the split copy c.pdf of v (FP64 once *split_bad is set)
+template <int S, int MODE>
+__device__ __forceinline__ double2 pc_setup_spmv(const PcgArgs &a, ChunkCols &cc, int r, int g, bool valid) {
+    const CgArgs &c = a.c;
+    if constexpr (MODE == 3) {
+        const bool staged = stage_chunk_pf(cc, c.row_map, c.col, blockIdx.x, c.n, c.vdf, S * 8u, c.val_bytes,
+                                           0xffffffffu);
+        if (ld_cg(a.split_bad) == 0) return chunk_spmv_dfv<S>(cc, staged, c.col, c.vdf, c.vals, c.pdf, r, g, valid);
+        return chunk_spmv<S, double>(cc, staged, c.col, c.vals, a.v, r, g, valid);
+    } else {
+        const bool staged = stage_chunk(cc, c.row_map, c.col, blockIdx.x, c.n);
+        return chunk_spmv<S, double>(cc, staged, c.col, c.vals, a.v, r, g, valid);
+    }
+}
 
 // ------------------------------------------------------------ set-up kernels
 // diagonal of every member and its inverse (thread per row and member)
@@ -50,7 +67,7 @@ __global__ void pc_diag_kernel(int32_t n, const int32_t *__restrict__ row_map, c
 }
 
 // power step: y = D^-1 A v, ||y||_e  (chunk per CTA, tree t1)
-template <int S>
+template <int S, int MODE = 0>
 __global__ void __launch_bounds__(RowMap<S>::THREADS, 1024 / RowMap<S>::THREADS) pc_power_kernel(PcgArgs a) {
     constexpr int G = RowMap<S>::G;
     __shared__ double sm[32][S + 1];
@@ -58,8 +75,7 @@ __global__ void __launch_bounds__(RowMap<S>::THREADS, 1024 / RowMap<S>::THREADS)
     const CgArgs &c = a.c;
     const int r = threadIdx.x / G, g = threadIdx.x % G;
     const int64_t R = (int64_t)blockIdx.x * 32 + r;
-    const bool staged = stage_chunk(cc, c.row_map, c.col, blockIdx.x, c.n);
-    const double2 av = chunk_spmv<S, double>(cc, staged, c.col, c.vals, a.v, r, g, R < c.n);
+    const double2 av = pc_setup_spmv<S, MODE>(a, cc, r, g, R < c.n);
     double v0 = 0.0, v1 = 0.0;
     if (R < c.n) {
         if constexpr (S == 1) {
@@ -85,17 +101,29 @@ __global__ void __launch_bounds__(RowMap<S>::THREADS, 1024 / RowMap<S>::THREADS)
     __threadfence();
 }
 
-// v = y / ||y||_e (as y * (1 / ||y||_e))
-template <int S>
+// v = y / ||y||_e (as y * (1 / ||y||_e)); MODE 3 also its split copy
+template <int S, int MODE = 0>
 __global__ void pc_scale_kernel(PcgArgs a) {
     const int64_t total = (int64_t)a.c.n * S;
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const double vv = a.y[t] * a.ps->inv_nrm[t % S];
+        a.v[t] = vv;
+        if (MODE == 3) store_split1(a.c.pdf, t, vv, a.split_bad);
+    }
+}
+
+// the split copy of the start vector v (MODE 3 set-up)
+template <int S>
+__global__ void pc_split_kernel(PcgArgs a) {
+    const int64_t total = (int64_t)a.c.n * S;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
          t += (int64_t)gridDim.x * blockDim.x)
-        a.v[t] = a.y[t] * a.ps->inv_nrm[t % S];
+        store_split1(a.c.pdf, t, a.v[t], a.split_bad);
 }
 
 // lam_e = (v.Av) / (v.Dv) and the Chebyshev parameters of member e
-template <int S>
+template <int S, int MODE = 0>
 __global__ void __launch_bounds__(RowMap<S>::THREADS, 1024 / RowMap<S>::THREADS) pc_rayleigh_kernel(PcgArgs a) {
     constexpr int G = RowMap<S>::G;
     __shared__ double sm[32][S + 1];
@@ -103,8 +131,7 @@ __global__ void __launch_bounds__(RowMap<S>::THREADS, 1024 / RowMap<S>::THREADS)
     const CgArgs &c = a.c;
     const int r = threadIdx.x / G, g = threadIdx.x % G;
     const int64_t R = (int64_t)blockIdx.x * 32 + r;
-    const bool staged = stage_chunk(cc, c.row_map, c.col, blockIdx.x, c.n);
-    const double2 av = chunk_spmv<S, double>(cc, staged, c.col, c.vals, a.v, r, g, R < c.n);
+    const double2 av = pc_setup_spmv<S, MODE>(a, cc, r, g, R < c.n);
     double n0 = 0.0, n1 = 0.0, d0 = 0.0, d1 = 0.0;
     if (R < c.n) {
         if constexpr (S == 1) {

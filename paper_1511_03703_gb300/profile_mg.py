@@ -1,11 +1,13 @@
 """Profiling driver: multigrid-preconditioned ensemble CG on an N^3 mesh.
 
-    python -m paper_1511_03703_gb300.profile_mg N s reps
+    python -m paper_1511_03703_gb300.profile_mg N s reps [presplit]
 
 Builds the level hierarchy (N, N/2, ... > 4), then `reps` times assembles
 every level of one ensemble of s samples (double-float assembly, M = 10, seed
 of the 64^3 workload) and solves to 1e-8 with the V-cycle preconditioner
-(graph replay of 4 iterations), printing the wall time of each part.  Used
+(graph replay of 4 iterations), printing the wall time of each part.
+presplit: level 0 also writes its pre-split values, so that the level-0 SpMVs
+run in double-float (as in the benchmark).  Used
 for the launch-list summaries under profiles/.
 """
 import sys
@@ -20,6 +22,7 @@ from paper_1511_03703_gb300 import inputs
 
 def main(argv):
     N, s, reps = int(argv[1]), int(argv[2]), int(argv[3])
+    presplit = len(argv) > 4 and argv[4] == "presplit"
     dev = torch.device("cuda:0")
     mg = E.Multigrid(N, 10, device=dev)
     xs = inputs.kl_samples(inputs.SEED_SCALE, 0, s, 10)
@@ -27,17 +30,18 @@ def main(argv):
     starts = [torch.from_numpy(np.stack([inputs.random_vector(600 + 100 * l + e, m.n) for e in range(s)],
                                         axis=1).reshape(-1)).to(dev) for l, m in enumerate(mg.meshes)]
     x = torch.zeros(mg.meshes[0].n * s, dtype=torch.float64, device=dev)
-    vals, b = mg.assemble(s, xi, df=True)
-    work = torch.empty(mg.workspace_size(s, vals, starts), dtype=torch.uint8, device=dev)
+    vdf = torch.empty(2 * mg.meshes[0].nnz * s, dtype=torch.float32, device=dev) if presplit else None
+    vals, b = mg.assemble(s, xi, df=True, values_df=vdf)
+    work = torch.empty(mg.workspace_size(s, vals, starts, vdf), dtype=torch.uint8, device=dev)
     for rep in range(reps):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         x.zero_()
-        vals, b = mg.assemble(s, xi, df=True)
+        vals, b = mg.assemble(s, xi, df=True, values_df=vdf)
         torch.cuda.synchronize()
         t1 = time.perf_counter()
         it, rr, st, stats = mg.solve(s, vals, b, x, 1e-8, 500, work, starts, flags=E.CG_GRAPH | E.CG_X0_ZERO,
-                                     check_every=4)
+                                     check_every=4, values_df=vdf)
         torch.cuda.synchronize()
         t2 = time.perf_counter()
         print(f"rep {rep}: assemble {1e3 * (t1 - t0):.2f} ms, solve {1e3 * (t2 - t1):.2f} ms, "

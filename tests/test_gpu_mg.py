@@ -28,25 +28,29 @@ def start(l, e, n):
     return inputs.random_vector(600 + 100 * l + e, n)
 
 
-def gpu_mg(torch, mg, xs, tol=1e-10, flags=0, degree=2, ratio=5.0, check_every=4):
+def gpu_mg(torch, mg, xs, tol=1e-10, flags=0, degree=2, ratio=5.0, check_every=4, presplit=False):
+    """presplit: level 0 assembled in double-float with its pre-split copy, so
+    that the level-0 SpMVs (K1 and the V-cycle's) run in double-float."""
     s = xs.shape[0]
-    vals, b = mg.assemble(s, to_dev(inputs.ensemble_layout(xs)))
+    vdf = torch.empty(2 * mg.meshes[0].nnz * s, dtype=torch.float32, device=gpu()) if presplit else None
+    vals, b = mg.assemble(s, to_dev(inputs.ensemble_layout(xs)), values_df=vdf)
     starts = [to_dev(np.stack([start(l, e, m.n) for e in range(s)], axis=1).reshape(-1))
               for l, m in enumerate(mg.meshes)]
     x = torch.zeros(mg.meshes[0].n * s, dtype=torch.float64, device=gpu())
-    work = torch.empty(mg.workspace_size(s, vals, starts), dtype=torch.uint8, device=gpu())
+    work = torch.empty(mg.workspace_size(s, vals, starts, vdf), dtype=torch.uint8, device=gpu())
     it, rr, st, stats = mg.solve(s, vals, b, x, tol, 200, work, starts, degree=degree, ratio=ratio, flags=flags,
-                                 check_every=check_every)
+                                 check_every=check_every, values_df=vdf)
     return to_np(x).reshape(-1, s), it, rr, st
 
 
+@pytest.mark.parametrize("presplit", [False, True])
 @pytest.mark.parametrize("s", [1, 4, 32])
-def test_mg_pcg_matches_oracle(torch, s):
+def test_mg_pcg_matches_oracle(torch, s, presplit):
     N, M = 16, 10
     mg = E.Multigrid(N, M)
     assert mg.sizes == [16, 8, 4]
     xs = inputs.kl_samples(800 + s, 0, s, M)
-    X, it, rr, st = gpu_mg(torch, mg, xs)
+    X, it, rr, st = gpu_mg(torch, mg, xs, presplit=presplit)
     assert st == [0] * s and max(rr) <= 1.01e-10
     for e in ([0, s - 1] if s > 2 else range(s)):
         starts = [start(l, e, (n + 1) ** 3) for l, n in enumerate(G.level_sizes(N))]
@@ -56,17 +60,18 @@ def test_mg_pcg_matches_oracle(torch, s):
         assert np.linalg.norm(X[:, e] - xo) <= 1e-8 * np.linalg.norm(xo), e
 
 
-def test_mg_member_independent_of_s_and_graph(torch):
+@pytest.mark.parametrize("presplit", [False, True])
+def test_mg_member_independent_of_s_and_graph(torch, presplit):
     mg = E.Multigrid(8, 10)
     xs = inputs.kl_samples(820, 0, 32, 10)
     ref = None
     for s in (1, 4, 32):
-        X, it, rr, st = gpu_mg(torch, mg, xs[:s])
+        X, it, rr, st = gpu_mg(torch, mg, xs[:s], presplit=presplit)
         cur = (X[:, 0].copy(), it[0])
         ref = cur if ref is None else ref
         assert np.array_equal(cur[0], ref[0]) and cur[1] == ref[1], s
-    Xg, itg, _, _ = gpu_mg(torch, mg, xs[:8], flags=E.CG_GRAPH)
-    Xd, itd, _, _ = gpu_mg(torch, mg, xs[:8])
+    Xg, itg, _, _ = gpu_mg(torch, mg, xs[:8], flags=E.CG_GRAPH, presplit=presplit)
+    Xd, itd, _, _ = gpu_mg(torch, mg, xs[:8], presplit=presplit)
     assert itg == itd and np.array_equal(Xg, Xd)
 
 

@@ -115,23 +115,24 @@ def test_gmres_restarts_match_oracle(torch):
         assert np.linalg.norm(X[:, e] - xo) <= 1e-8 * np.linalg.norm(xo), e
 
 
-def newton_case(torch, s, N, alpha, beta, precond=E.NL_PRECOND_MG, seed=960, **kw):
+def newton_case(torch, s, N, alpha, beta, precond=E.NL_PRECOND_MG, seed=960, presplit=False, **kw):
     M = 10
     nl = E.Nonlinear(N, M, v=V, precond=precond)
     xs = inputs.kl_samples(seed, 0, s, M)
-    vals, b = nl.assemble(s, to_dev(inputs.ensemble_layout(xs)))
+    vdf = torch.empty(2 * nl.mesh.nnz * s, dtype=torch.float32, device=gpu()) if presplit else None
+    vals, b = nl.assemble(s, to_dev(inputs.ensemble_layout(xs)), values_df=vdf)
     starts = dev_starts(nl, s) if precond == E.NL_PRECOND_MG else None
     p = nl.params(alpha, beta, **kw)
     u = torch.zeros(nl.mesh.n * s, dtype=torch.float64, device=gpu())
-    work = torch.empty(nl.workspace_size(s, vals, starts, p), dtype=torch.uint8, device=gpu())
-    ni, li, rr, st, stats = nl.solve(s, vals, b, u, work, starts, p)
+    work = torch.empty(nl.workspace_size(s, vals, starts, p, vdf), dtype=torch.uint8, device=gpu())
+    ni, li, rr, st, stats = nl.solve(s, vals, b, u, work, starts, p, values_df=vdf)
     return xs, to_np(u).reshape(-1, s), ni, li, rr, st
 
 
-@pytest.mark.parametrize("s", [1, 4, 32])
-def test_newton_matches_oracle(torch, s):
+@pytest.mark.parametrize("s,presplit", [(1, False), (4, False), (32, False), (4, True), (32, True)])
+def test_newton_matches_oracle(torch, s, presplit):
     N, alpha, beta, tol, lin_tol = 8, 1.0, 10.0, 1e-10, 1e-11
-    xs, U, ni, li, rr, st = newton_case(torch, s, N, alpha, beta, tol=tol, lin_tol=lin_tol)
+    xs, U, ni, li, rr, st = newton_case(torch, s, N, alpha, beta, tol=tol, lin_tol=lin_tol, presplit=presplit)
     assert st == [0] * s and max(rr) <= tol
     for e in ([0, s - 1] if s > 2 else range(s)):
         prob = NL.Problem(N, 10, xs[e], alpha, beta, v=V)
