@@ -6,7 +6,7 @@
 // before its members are added), so member e follows the iterates of a
 // standalone solve of sample e; members that converge are frozen.  With
 // ENS_CG_COUPLED the member dots are summed first, which is the paper's
-// coupled ensemble solver of Sect. 3.6.
+// coupled ensemble solver of Sects. 3.4 and 3.7.
 //
 // Launch sequence, no host synchronisation inside an iteration:
 //   K0  r = b - A x0, p = r, rho_e = r.r, |b_e|^2   (last CTA: init, stop test)

@@ -212,14 +212,28 @@ __device__ __forceinline__ void k1_body(const CgArgs &a, const int cta, K1Smem<S
         apv = chunk_spmv<S, double>(sh.cc[sub], staged, a.col, a.vals, a.p, r, g, valid);
     double v0 = 0.0, v1 = 0.0;
     const int64_t R = K1_CHUNK * 32 + r;
+    const bool pre = (MODE == 1 || MODE == 3) && mode == MODE;  // p.q from the split p, as cg_spmv_kernel
     if constexpr (S == 1) {
         if (valid) {
             if (g == 0) a.q[R] = apv.x;
-            v0 = apv.x * a.p[R];
+            double pr;
+            if (pre) {
+                const float2 h = a.pdf[R];
+                pr = f2d_exact(h.x) + f2d_exact(h.y);
+            } else {
+                pr = a.p[R];
+            }
+            v0 = apv.x * pr;
         }
     } else if (valid) {
         reinterpret_cast<double2 *>(a.q)[R * G + g] = apv;
-        const double2 pv = reinterpret_cast<const double2 *>(a.p)[R * G + g];
+        double2 pv;
+        if (pre) {
+            const float4 h = reinterpret_cast<const float4 *>(a.pdf)[R * G + g];
+            pv = make_double2(f2d_exact(h.x) + f2d_exact(h.y), f2d_exact(h.z) + f2d_exact(h.w));
+        } else {
+            pv = reinterpret_cast<const double2 *>(a.p)[R * G + g];
+        }
         v0 = apv.x * pv.x;
         v1 = apv.y * pv.y;
     }
@@ -303,17 +317,34 @@ __global__ void __launch_bounds__(RowMap<S>::THREADS, K1Occ<S, MODE>::THREADS_PE
         apv = chunk_spmv_split<S, XPre>(cc, staged, a.col, a.vals, a.p, a.pdf, r, g, R < a.n);
     else
         apv = chunk_spmv<S, double>(cc, staged, a.col, a.vals, a.p, r, g, R < a.n);
+    // p.q: the double-float forms take p as the SpMV saw it, hi + lo of the
+    // split copy (exact in FP64; the SpMV's neighbours' gathers have usually
+    // brought it into L2), which saves reading the FP64 p
+    const bool pre = (MODE == 1 || MODE == 3) && mode == MODE;
     double v0 = 0.0, v1 = 0.0;
     if constexpr (S == 1) {
         const double ap = apv.x;
         if (R < a.n) {
             if (g == 0) a.q[R] = ap;
-            v0 = ap * a.p[R];
+            double pr;
+            if (pre) {
+                const float2 h = a.pdf[R];
+                pr = f2d_exact(h.x) + f2d_exact(h.y);
+            } else {
+                pr = a.p[R];
+            }
+            v0 = ap * pr;
         }
     } else if (R < a.n) {
         const double2 ap = apv;
         reinterpret_cast<double2 *>(a.q)[R * G + g] = ap;
-        const double2 pv = reinterpret_cast<const double2 *>(a.p)[R * G + g];
+        double2 pv;
+        if (pre) {
+            const float4 h = reinterpret_cast<const float4 *>(a.pdf)[R * G + g];
+            pv = make_double2(f2d_exact(h.x) + f2d_exact(h.y), f2d_exact(h.z) + f2d_exact(h.w));
+        } else {
+            pv = reinterpret_cast<const double2 *>(a.p)[R * G + g];
+        }
         v0 = ap.x * pv.x;
         v1 = ap.y * pv.y;
     }
