@@ -18,7 +18,8 @@
 // with m(0) = 2/3, m(+-1) = 1/6; g(0) = 0, g(+-1) = +-1/2; and w(a, c) the
 // integral of hat_0 hat_a hat_c over the 1-D cells holding all three nodes
 // (w(0,0) = 1/2; 1/12 for the pairs (0,+-1), (+-1,0), (+-1,+-1); 0 for (+-1,-+1)).
-// M is formed per row by sum factorisation over the 27-node window of the row.
+// M is formed per row by sum factorisation over the 27-node window of the row,
+// in float-pair (double-float) arithmetic on the FP32 pipe.
 //
 // GMRES (Saad, Sect. 6.5 and 9.3.2) per member with classical Gram-Schmidt
 // applied twice (CGS2): every step is four row-parallel kernels after the
@@ -93,18 +94,53 @@ __global__ void nl_advection_kernel(int32_t n, int32_t N, const int32_t *__restr
     }
 }
 
-// one 1-D pass of the sum factorisation over the 27-node window T[x + 3y + 9z]
-// along the axis of the given stride: T(a) <- sum_c w(a, c) T(c)
+// ---- the sum factorisation of M(u) in double-float arithmetic (float pairs
+// on the FP32 pipe: GB300 runs FP64 at 1/64 of its FP32 rate).  M is a small
+// part of J (beta h^3 u against the diffusion entries), so its 2^-44-relative
+// float-pair rounding stays far below FP64 rounding of J and F.
+struct Dfp {
+    float h, l;  // unevaluated sum h + l
+};
+__device__ __forceinline__ Dfp dfp_of(double v) {  // truncating split (|v| < 2^-103 gives 0)
+    Dfp r;
+    df_split_trunc(v, r.h, r.l);
+    return r;
+}
+__device__ __forceinline__ Dfp dfp_norm(float s, float e) {  // fast two-sum renormalisation
+    const float h = __fadd_rn(s, e);
+    return Dfp{h, __fsub_rn(e, __fsub_rn(h, s))};
+}
+__device__ __forceinline__ Dfp dfp_add(Dfp a, Dfp b) {
+    float s, e;
+    two_sum(a.h, b.h, s, e);
+    return dfp_norm(s, __fadd_rn(e, __fadd_rn(a.l, b.l)));
+}
+// a * (ch + cl)
+__device__ __forceinline__ Dfp dfp_mulc(Dfp a, float ch, float cl) {
+    const float p = __fmul_rn(a.h, ch);
+    float e = __fmaf_rn(a.h, ch, -p);
+    e = __fmaf_rn(a.h, cl, e);
+    e = __fmaf_rn(a.l, ch, e);
+    return dfp_norm(p, e);
+}
+__device__ __forceinline__ double dfp_to_double(Dfp a) { return f2d_exact(a.h) + f2d_exact(a.l); }
+
+// 1/12 as a float pair
+constexpr float kK12H = (float)(1.0 / 12.0);
+constexpr float kK12L = (float)(1.0 / 12.0 - (double)(float)(1.0 / 12.0));
+
+// one 1-D pass over the 27-node window T[x + 3y + 9z] along the axis of the
+// given stride: T(a) <- sum_c w(a, c) T(c)
 template <int STRIDE>
-__device__ __forceinline__ void window_pass(double (&T)[27]) {
-    constexpr double K12 = 1.0 / 12.0;
+__device__ __forceinline__ void window_pass(Dfp (&T)[27]) {
 #pragma unroll
     for (int b = 0; b < 27; ++b) {
         if ((b / STRIDE) % 3 != 0) continue;  // b: the window index with this axis' coordinate -1
-        const double um = T[b], u0 = T[b + STRIDE], up = T[b + 2 * STRIDE];
-        T[b] = K12 * (um + u0);
-        T[b + STRIDE] = fma(0.5, u0, K12 * (um + up));
-        T[b + 2 * STRIDE] = K12 * (u0 + up);
+        const Dfp um = T[b], u0 = T[b + STRIDE], up = T[b + 2 * STRIDE];
+        const Dfp half0{0.5f * u0.h, 0.5f * u0.l};  // exact
+        T[b] = dfp_mulc(dfp_add(um, u0), kK12H, kK12L);
+        T[b + STRIDE] = dfp_add(half0, dfp_mulc(dfp_add(um, up), kK12H, kK12L));
+        T[b + 2 * STRIDE] = dfp_mulc(dfp_add(u0, up), kK12H, kK12L);
     }
 }
 
@@ -112,14 +148,15 @@ __device__ __forceinline__ void window_pass(double (&T)[27]) {
 //   interior row: J_p = A_p + alpha C_p + 2 beta M_p, N_p = A_p + alpha C_p + beta M_p,
 //                 F_i = sum_p N_p u_col(p) - b_i  (M_p = 0 for boundary columns)
 //   boundary row: J_p = A_p, F_i = sum_p A_p u_col(p) - b_i
-// (h3 = h^3 = 1 / N^3)
+// m2h + m2l: 2 beta h^3 as a float pair (M's integrals carry the factor h^3)
 template <int S>
 __global__ void __launch_bounds__(256) nl_jacobian_kernel(int32_t n, int32_t N, const int32_t *__restrict__ row_map,
                                                           const int32_t *__restrict__ col,
                                                           const double *__restrict__ A, const double *__restrict__ C,
-                                                          double alpha, double beta, const double *__restrict__ b,
+                                                          double alpha, float m2h, float m2l,
+                                                          const double *__restrict__ b,
                                                           const double *__restrict__ u, double *__restrict__ J,
-                                                          double *__restrict__ F, NlState *ns, double h3) {
+                                                          double *__restrict__ F, NlState *ns) {
     const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (t >= (int64_t)n * S) return;
     const int e = (int)(t % S);
@@ -142,11 +179,11 @@ __global__ void __launch_bounds__(256) nl_jacobian_kernel(int32_t n, int32_t N, 
         if (e == 0) atomicExch(&ns->graph_bad, 1);
         return;
     }
-    double T[27];
+    Dfp T[27];
 #pragma unroll
     for (int w = 0; w < 27; ++w) {
         const int64_t Jn = I + (w % 3 - 1) + (int64_t)n1 * ((w / 3) % 3 - 1) + (int64_t)n1 * n1 * (w / 9 - 1);
-        T[w] = u[Jn * S + e];
+        T[w] = dfp_of(u[Jn * S + e]);
     }
     window_pass<1>(T);
     window_pass<3>(T);
@@ -158,10 +195,13 @@ __global__ void __launch_bounds__(256) nl_jacobian_kernel(int32_t n, int32_t N, 
         const int32_t cj = col[p];
         const int64_t Jn = I + (w % 3 - 1) + (int64_t)n1 * ((w / 3) % 3 - 1) + (int64_t)n1 * n1 * (w / 9 - 1);
         bad |= (cj != Jn);
-        const double m = on_boundary(i + w % 3 - 1, j + (w / 3) % 3 - 1, k + w / 9 - 1, N) ? 0.0 : h3 * T[w];
+        // 2 beta M_p (0 for a boundary column)
+        const double m2 = on_boundary(i + w % 3 - 1, j + (w / 3) % 3 - 1, k + w / 9 - 1, N)
+                              ? 0.0
+                              : dfp_to_double(dfp_mulc(T[w], m2h, m2l));
         const double ac = fma(alpha, C[p], A[(int64_t)p * S + e]);
-        J[(int64_t)p * S + e] = fma(2.0 * beta, m, ac);
-        f = fma(fma(beta, m, ac), u[(int64_t)cj * S + e], f);
+        J[(int64_t)p * S + e] = ac + m2;
+        f = fma(fma(0.5, m2, ac), u[(int64_t)cj * S + e], f);
     }
     if (bad && e == 0) atomicExch(&ns->graph_bad, 1);
     F[t] = f;
@@ -538,6 +578,13 @@ __global__ void __launch_bounds__(RowMap<S>::THREADS, 1024 / RowMap<S>::THREADS)
 }
 
 // ------------------------------------------------------------ host side
+// 2 beta h^3 (h = 1/N) as a float pair for nl_jacobian_kernel
+static void nl_m2_split(double beta, int N, float *hi, float *lo) {
+    const double c = 2.0 * beta / ((double)N * N * N);
+    *hi = (float)c;
+    *lo = (float)(c - (double)*hi);
+}
+
 struct NlBufs {
     NlState *ns;
     GmState *gs;
@@ -772,10 +819,12 @@ static int newton_run(int nlevels, const ens_mg_level *lv, const double *C, cons
     a.max_iter = p->max_lin;
     const int32_t n = a.n, N = lv[0].N;
     const unsigned jgrid = (unsigned)(((int64_t)n * S + 255) / 256);
+    float m2h, m2l;
+    nl_m2_split(p->beta, N, &m2h, &m2l);
     int32_t h[2];
     for (int it = 0; it <= p->max_newton; ++it) {
-        nl_jacobian_kernel<S><<<jgrid, 256, 0, st>>>(n, N, a.row_map, a.col, lv[0].values, C, p->alpha, p->beta, b,
-                                                    u, bufs.J, bufs.F, bufs.ns, 1.0 / ((double)N * N * N));
+        nl_jacobian_kernel<S><<<jgrid, 256, 0, st>>>(n, N, a.row_map, a.col, lv[0].values, C, p->alpha, m2h, m2l,
+                                                    b, u, bufs.J, bufs.F, bufs.ns);
         nl_norm_kernel<S><<<sv.grid, RowMap<S>::THREADS, 0, st>>>(n, bufs.F, a.tn, bufs.ns, 0, it, p->tol,
                                                                  p->max_newton);
         sv.launches += 2;
@@ -854,9 +903,11 @@ extern "C" int ens_nl_jacobian(const ens_graph *gp, int32_t N, int s, const doub
     NlState *ns = static_cast<NlState *>(work);
     ENS_CUDA_TRY(cudaMemsetAsync(&ns->graph_bad, 0, sizeof(int), st));
     const unsigned grid = (unsigned)(((int64_t)g.num_rows * s + 255) / 256);
-#define NL_JAC(SS)                                                                                              \
-    (nl_jacobian_kernel<SS><<<grid, 256, 0, st>>>(g.num_rows, N, g.row_map, g.col_entry, A, C, alpha, beta, b, u, \
-                                                  J, F, ns, 1.0 / ((double)N * N * N)),                         \
+    float m2h, m2l;
+    nl_m2_split(beta, N, &m2h, &m2l);
+#define NL_JAC(SS)                                                                                             \
+    (nl_jacobian_kernel<SS><<<grid, 256, 0, st>>>(g.num_rows, N, g.row_map, g.col_entry, A, C, alpha, m2h, m2l, \
+                                                  b, u, J, F, ns),                                             \
      ENS_OK)
     switch (s) {
         case 1: NL_JAC(1); break;
