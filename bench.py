@@ -642,22 +642,21 @@ def main_batched(args):
             xs = inputs.kl_samples(inputs.SEED_BATCHED, g * BAT_GROUP, BAT_GROUP, M_KL)
             for k in range(BAT_GROUP // s):
                 xi = torch.from_numpy(inputs.ensemble_layout(xs[k * s:(k + 1) * s])).to(dev)
-                vals, b = meshes[N].assemble(s, xi)
+                vdf = torch.empty(2 * meshes[N].nnz * s, dtype=torch.float32, device=dev)
+                vals, b = meshes[N].assemble(s, xi, values_df=vdf)
                 x = torch.zeros(meshes[N].n * s, dtype=torch.float64, device=dev)
-                items.append({"N": N, "s": s, "xi": xi, "vals": vals, "b": b, "x": x, "group": g})
+                items.append({"N": N, "s": s, "xi": xi, "vals": vals, "vdf": vdf, "b": b, "x": x, "group": g})
             groups.append((N, s))
             g += 1
     t0 = time.perf_counter()
-    # the batched launch reads FP64 values: forms without a pre-split copy
-    cand = ("f64", "df", "split")
-    forms = {(N, s): autotune.best_form(meshes[N], s, candidates=cand) for N in BAT_MESHES for s in BAT_WIDTHS}
+    # every item carries its pre-split values (written by the double-float
+    # assembly), so all four SpMV forms are candidates
+    forms = {(N, s): autotune.best_form(meshes[N], s) for N in BAT_MESHES for s in BAT_WIDTHS}
     works = {}
     for it in items:
         key = (it["N"], it["s"])
         if key not in works:
             works[key] = torch.empty(E.cg_workspace_size(meshes[it["N"]].n, it["s"]), dtype=torch.uint8, device=dev)
-    batch = E.Batch([(meshes[it["N"]].graph, it["s"], it["vals"], it["b"], it["x"]) for it in items])
-    bwork = torch.empty(batch.workspace_size(), dtype=torch.uint8, device=dev)
     # batch-wide form: the one most groups chose, weighted by their bytes
     votes = {}
     for it in items:
@@ -665,7 +664,10 @@ def main_batched(args):
         votes[f] = votes.get(f, 0) + meshes[it["N"]].nnz * it["s"]
     bform = max(votes, key=votes.get)
     bflags = autotune.FORMS[bform]
-    ce = autotune.best_check_every(batch, bwork, bflags, tag="batched-16^3-64^3")
+    batch = E.Batch([(meshes[it["N"]].graph, it["s"], it["vals"], it["b"], it["x"])
+                     + ((it["vdf"],) if bform == "dfv" else ()) for it in items])
+    bwork = torch.empty(batch.workspace_size(), dtype=torch.uint8, device=dev)
+    ce = autotune.best_check_every(batch, bwork, bflags, tag=f"batched-16^3-64^3-{bform}")
     tune_s = time.perf_counter() - t0
 
     def reassemble():
@@ -675,16 +677,17 @@ def main_batched(args):
             E.kl_setup(N, M_KL, L_CORR, mesh.kl_table, want_host=False)
             E.mode_matrices(N, mesh.graph, M_KL, mesh.kl_table, mesh.modes, mesh.load)
         for it in items:
-            meshes[it["N"]].assemble(it["s"], it["xi"], values=it["vals"], b=it["b"])
+            meshes[it["N"]].assemble(it["s"], it["xi"], values=it["vals"], b=it["b"], values_df=it["vdf"])
             it["x"].zero_()
 
     def separate():
         iters = []
         for it in items:
             mesh = meshes[it["N"]]
-            fl = autotune.FORMS[forms[(it["N"], it["s"])]]
+            f = forms[(it["N"], it["s"])]
             i, r, st, _ = E.cg(mesh.graph, it["s"], it["vals"], it["b"], it["x"], TOL, 10000,
-                               works[(it["N"], it["s"])], flags=fl, check_every=16)
+                               works[(it["N"], it["s"])], flags=autotune.FORMS[f], check_every=16,
+                               values_df=it["vdf"] if f == "dfv" else None)
             iters.append(i)
         return iters
 

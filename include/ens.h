@@ -310,7 +310,9 @@ int ens_mg_pcg(int nlevels, const ens_mg_level *levels, int s, const double *b, 
 
 /* ---------------------------------------------------- A8 batched CG */
 /* One ensemble of a batch: its graph (by value), size s, values, rhs, x (in:
- * x0, out: solution) and optional host outputs iters/relres/status [s]. */
+ * x0, out: solution), optional host outputs iters/relres/status [s], and
+ * optional pre-split values (as for ens_cg_df; either every item of a batch
+ * gives them, and the batch runs the pre-split double-float SpMV, or none). */
 typedef struct ens_batch_item {
     ens_graph graph;
     int32_t s;
@@ -321,12 +323,15 @@ typedef struct ens_batch_item {
     int32_t *iters_host;
     double *relres_host;
     int32_t *status_host;
+    const float *values_df;
 } ens_batch_item;
 
 /* Solves a batch of ensembles -- any mix of meshes and ensemble sizes -- with
  * one launch per CG phase for the whole batch (a per-CTA work list maps CTAs
  * to (ensemble, row tiles)); each ensemble follows exactly the arithmetic of
- * ens_cg (same flags: ENS_CG_COUPLED, ENS_CG_DF64, ENS_CG_SPLIT64,
+ * ens_cg, or of ens_cg_df when the items carry values_df (ENS_ERR_ARG if only
+ * some do, or together with ENS_CG_DF64 / ENS_CG_SPLIT64) (same flags:
+ * ENS_CG_COUPLED, ENS_CG_DF64, ENS_CG_SPLIT64,
  * ENS_CG_GRAPH replays check_every iterations of the batch as one CUDA
  * graph, ENS_CG_TIME_SPMV).  Not in the paper (Sect. 5 leaves the grouping of
  * samples to future work); it amortises launch latency over small meshes.

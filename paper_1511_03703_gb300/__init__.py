@@ -47,7 +47,7 @@ class BatchItemC(ctypes.Structure):
     _fields_ = [("graph", EnsGraphC), ("s", ctypes.c_int32), ("reserved", ctypes.c_int32),
                 ("values", ctypes.c_void_p), ("b", ctypes.c_void_p), ("x", ctypes.c_void_p),
                 ("iters_host", ctypes.c_void_p), ("relres_host", ctypes.c_void_p),
-                ("status_host", ctypes.c_void_p)]
+                ("status_host", ctypes.c_void_p), ("values_df", ctypes.c_void_p)]
 
 
 class MgLevelC(ctypes.Structure):
@@ -542,21 +542,27 @@ class Nonlinear:
 
 # ------------------------------------------------------------- batched CG
 class Batch:
-    """A batch of ensembles (graph, s, values, b, x) solved by ens_cg_batched."""
+    """A batch of ensembles (graph, s, values, b, x[, values_df]) solved by
+    ens_cg_batched; with values_df (pre-split values, on every item) the batch
+    runs the pre-split double-float SpMV of ens_cg_df."""
 
     def __init__(self, items):
-        """items: list of (graph, s, values, b, x) with device tensors."""
+        """items: list of (graph, s, values, b, x) or (graph, s, values, b, x,
+        values_df) with device tensors."""
         self.items = list(items)
         n = len(self.items)
         self.c = (BatchItemC * n)()
         self.iters = [(ctypes.c_int32 * it[1])() for it in self.items]
         self.relres = [(ctypes.c_double * it[1])() for it in self.items]
         self.status = [(ctypes.c_int32 * it[1])() for it in self.items]
-        for i, (graph, s, values, b, x) in enumerate(self.items):
-            _require_cuda(values, b, x)
+        for i, item in enumerate(self.items):
+            graph, s, values, b, x = item[:5]
+            vdf = item[5] if len(item) > 5 else None
+            _require_cuda(values, b, x, vdf)
             self.c[i].graph = graph.c
             self.c[i].s = s
             self.c[i].values, self.c[i].b, self.c[i].x = values.data_ptr(), b.data_ptr(), x.data_ptr()
+            self.c[i].values_df = vdf.data_ptr() if vdf is not None else None
             self.c[i].iters_host = ctypes.cast(self.iters[i], ctypes.c_void_p)
             self.c[i].relres_host = ctypes.cast(self.relres[i], ctypes.c_void_p)
             self.c[i].status_host = ctypes.cast(self.status[i], ctypes.c_void_p)

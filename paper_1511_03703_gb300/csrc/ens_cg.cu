@@ -452,6 +452,11 @@ static int batched_run(int n_items, const ens_batch_item *items, double tol, int
         const ens_batch_item &it = items[i];
         cg_layout_args(h[i].a, &it.graph, it.s, it.values, it.b, it.x, tol, max_iter,
                        flags, wi);
+        if (MODE == 3) {  // pre-split values; a whole-chunk CTA prefetches its value block into L2
+            h[i].a.vdf = reinterpret_cast<const float2 *>(it.values_df);
+            h[i].a.val_bytes = (uint64_t)it.graph.num_entries * it.s * 8u;
+            h[i].a.pf_cap = (kBatchThreads / (32 * ((it.s == 1) ? 2 : it.s / 2)) == 1) ? l2_prefetch_cap(3) : 0u;
+        }
         wi += cg_bytes(it.graph.num_rows, it.s);
         h[i].S = it.s;
         const int64_t chunks = h[i].a.t1.count[1];
@@ -645,6 +650,10 @@ static int check_batch(int n_items, const ens_batch_item *items) {
             return fail(ENS_ERR_ARG, "item %d: NULL values/b/x", i);
         if (items[i].s > 1 && (!aligned16(items[i].values) || !aligned16(items[i].b) || !aligned16(items[i].x)))
             return fail(ENS_ERR_ALIGN, "item %d: values/b/x must be 16-byte aligned", i);
+        if ((items[i].values_df != nullptr) != (items[0].values_df != nullptr))
+            return fail(ENS_ERR_ARG, "item %d: either every item gives values_df or none", i);
+        if (items[i].values_df && !aligned16(items[i].values_df))
+            return fail(ENS_ERR_ALIGN, "item %d: values_df must be 16-byte aligned", i);
     }
     return ENS_OK;
 }
@@ -668,6 +677,11 @@ extern "C" int ens_cg_batched(int n_items, const ens_batch_item *items, double t
     const size_t need = batch_plan(n_items, items).total;
     if (work_bytes < need) return fail(ENS_ERR_WORKSPACE, "batched workspace %zu < %zu bytes", work_bytes, need);
     cudaStream_t st = as_stream(stream);
+    if (items[0].values_df) {
+        if (flags & (ENS_CG_DF64 | ENS_CG_SPLIT64))
+            return fail(ENS_ERR_ARG, "ens_cg_batched: values_df excludes ENS_CG_DF64 / ENS_CG_SPLIT64");
+        return batched_run<3>(n_items, items, tol, max_iter, flags, check_every, work, stats_host, st);
+    }
     if (flags & ENS_CG_SPLIT64) return batched_run<2>(n_items, items, tol, max_iter, flags, check_every, work, stats_host, st);
     if (flags & ENS_CG_DF64) return batched_run<1>(n_items, items, tol, max_iter, flags, check_every, work, stats_host, st);
     return batched_run<0>(n_items, items, tol, max_iter, flags, check_every, work, stats_host, st);

@@ -201,11 +201,19 @@ __device__ __forceinline__ void k1_body(const CgArgs &a, const int cta, K1Smem<S
     const bool valid = chunk * 32 + r < a.n;
     // the split / double-float forms are used unless a vector element fell outside their range
     const int mode = (MODE != 0 && ld_cg(&st->df_bad_any) != 0) ? 0 : MODE;
-    const bool staged = (NSUB == 1) ? stage_chunk(sh.cc[0], a.row_map, a.col, chunk, a.n)
-                                    : stage_chunk_sub(sh.cc[sub], a.row_map, a.col, chunk, a.n, ltid, T);
+    bool staged;
+    if constexpr (NSUB == 1) {
+        if (MODE == 3) staged = stage_chunk_pf(sh.cc[0], a.row_map, a.col, chunk, a.n, a.vdf, S * 8u, a.val_bytes,
+                                               a.pf_cap);
+        else staged = stage_chunk(sh.cc[0], a.row_map, a.col, chunk, a.n);
+    } else {
+        staged = stage_chunk_sub(sh.cc[sub], a.row_map, a.col, chunk, a.n, ltid, T);
+    }
     double2 apv;
     if (MODE == 1 && mode == 1)
         apv = chunk_spmv_df<S, XPre>(sh.cc[sub], staged, a.col, a.vals, a.pdf, r, g, valid);
+    else if (MODE == 3 && mode == 3)
+        apv = chunk_spmv_dfv<S>(sh.cc[sub], staged, a.col, a.vdf, a.vals, a.pdf, r, g, valid);
     else if (MODE == 2 && mode == 2)
         apv = chunk_spmv_split<S, XPre>(sh.cc[sub], staged, a.col, a.vals, a.p, a.pdf, r, g, valid);
     else

@@ -54,6 +54,34 @@ def test_batched_equals_separate_solves_bitwise(torch, flags):
         assert torch.equal(x, x2), i
 
 
+@pytest.mark.parametrize("flags", [0, E.CG_GRAPH])
+def test_batched_presplit_equals_separate_cg_df_bitwise(torch, flags):
+    """Items with pre-split values: the batch runs the ens_cg_df arithmetic."""
+    items, meta = make_items(torch, SPEC, seed=540)
+    pitems = []
+    for graph, s, vals, b, x in items:
+        vdf = torch.empty(2 * vals.numel(), dtype=torch.float32, device=gpu())
+        E.convert_values(graph, s, vals, vdf, dtype=E.F64_DF)
+        pitems.append((graph, s, vals, b, x, vdf))
+    batch = E.Batch(pitems)
+    work = torch.empty(batch.workspace_size(), dtype=torch.uint8, device=gpu())
+    it_b, rr_b, st_b, _ = batch.solve(1e-9, 2000, work, flags=flags, check_every=4)
+    for i, (graph, s, vals, b, x, vdf) in enumerate(pitems):
+        assert st_b[i] == [0] * s
+        x2 = torch.zeros_like(x)
+        w2 = torch.empty(E.cg_workspace_size(graph.num_rows, s), dtype=torch.uint8, device=gpu())
+        it, rr, st, _ = E.cg(graph, s, vals, b, x2, 1e-9, 2000, w2, values_df=vdf)
+        assert it == it_b[i] and rr == rr_b[i]
+        assert torch.equal(x, x2), i
+    # every item or none; no second arithmetic flag
+    with pytest.raises(E.EnsError) as ei:
+        E.Batch(pitems[:2] + [items[2]]).workspace_size()
+    assert ei.value.code == 1
+    with pytest.raises(E.EnsError) as ei:
+        batch.solve(1e-9, 10, work, flags=E.CG_DF64)
+    assert ei.value.code == 1
+
+
 def test_batched_matches_oracle(torch):
     items, meta = make_items(torch, [(6, 4), (10, 8)], seed=610)
     batch = E.Batch(items)
