@@ -339,11 +339,11 @@ __global__ void gm_start_kernel(GmArgs a) {
         GmState *gs = a.gs;
         int act = 0;
         if (e < S) {
-            act = ns->nact[e];
+            act = (ns->nact[e] && a.max_iter > 0) ? 1 : 0;
             gs->beta0[e] = ns->fn[e];
             gs->g[0][e] = ns->fn[e];
             gs->active[e] = act;
-            gs->conv[e] = act ? 0 : 1;
+            gs->conv[e] = ns->nact[e] ? 0 : 1;  // a member to solve with max_iter = 0 stays unconverged
             gs->k[e] = 0;
             gs->iters[e] = 0;
             gs->scale[e] = 0.0;

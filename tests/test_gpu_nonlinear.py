@@ -88,7 +88,7 @@ def gmres_case(torch, s, precond, restart, N=8, seed=920):
     return nl, xs, us, rhs, to_np(J).reshape(-1, s), to_np(x).reshape(-1, s), it, rr, st
 
 
-@pytest.mark.parametrize("s", [1, 4, 32])
+@pytest.mark.parametrize("s", [1, 4, 8, 16, 32])
 @pytest.mark.parametrize("precond", [E.NL_PRECOND_NONE, E.NL_PRECOND_MG])
 def test_gmres_matches_oracle(torch, s, precond):
     nl, xs, us, rhs, J, X, it, rr, st = gmres_case(torch, s, precond, 30)
@@ -115,6 +115,24 @@ def test_gmres_restarts_match_oracle(torch):
         assert np.linalg.norm(X[:, e] - xo) <= 1e-8 * np.linalg.norm(xo), e
 
 
+def test_gmres_longest_restart_and_no_iterations(torch):
+    s = 4
+    nl, xs, us, rhs, J, X, it, rr, st = gmres_case(torch, s, E.NL_PRECOND_NONE, 64, N=6, seed=950)
+    assert st == [0] * s and max(rr) <= 1.01e-10
+    mo = NL.Mesh(6)
+    for e in range(s):
+        xo, ito, rro, sto = NL.gmres(mo.rm, mo.col, J[:, e], rhs[e], None, restart=400, tol=1e-10)
+        assert ito <= 64 and abs(it[e] - ito) <= 1, (e, it[e], ito)
+        assert np.linalg.norm(X[:, e] - xo) <= 1e-8 * np.linalg.norm(xo), e
+    # max_iter = 0: x stays 0 and every member with b != 0 is reported not converged
+    vals, _ = nl.assemble(s, to_dev(inputs.ensemble_layout(xs)))
+    x = torch.full((mo.n * s,), 7.0, dtype=torch.float64, device=gpu())
+    work = torch.empty(nl.gmres_workspace_size(s, vals, None, 8), dtype=torch.uint8, device=gpu())
+    it0, rr0, st0, _ = nl.gmres(s, vals, to_dev(J.reshape(-1)), to_dev(O.to_ensemble(rhs)), x, work, None,
+                                1e-10, restart=8, max_iter=0)
+    assert it0 == [0] * s and st0 == [E.ERR_NOT_CONVERGED] * s and not torch.any(x != 0)
+
+
 def newton_case(torch, s, N, alpha, beta, precond=E.NL_PRECOND_MG, seed=960, presplit=False, **kw):
     M = 10
     nl = E.Nonlinear(N, M, v=V, precond=precond)
@@ -129,7 +147,8 @@ def newton_case(torch, s, N, alpha, beta, precond=E.NL_PRECOND_MG, seed=960, pre
     return xs, to_np(u).reshape(-1, s), ni, li, rr, st
 
 
-@pytest.mark.parametrize("s,presplit", [(1, False), (4, False), (32, False), (4, True), (32, True)])
+@pytest.mark.parametrize("s,presplit", [(1, False), (4, False), (8, False), (16, True), (32, False), (4, True),
+                                        (32, True)])
 def test_newton_matches_oracle(torch, s, presplit):
     N, alpha, beta, tol, lin_tol = 8, 1.0, 10.0, 1e-10, 1e-11
     xs, U, ni, li, rr, st = newton_case(torch, s, N, alpha, beta, tol=tol, lin_tol=lin_tol, presplit=presplit)
