@@ -27,6 +27,8 @@ This oracle states the geometric version on the nested hex meshes:
 
 Pins: tests/test_oracle_multigrid.py.
 """
+import functools
+
 import numpy as np
 import scipy.sparse as sp
 
@@ -41,8 +43,11 @@ def level_sizes(N):
     return out
 
 
+@functools.lru_cache(maxsize=16)
 def prolongation(Nc):
-    """Sparse P: interior nodes of the (2 Nc)^3-cell mesh <- interior nodes of the Nc^3 mesh."""
+    """Sparse P: interior nodes of the (2 Nc)^3-cell mesh <- interior nodes of the
+    Nc^3 mesh.  A pure function of Nc, built once per size (the cache only saves
+    the Python loops; callers do not modify the matrix)."""
     Nf = 2 * Nc
     nf1, nc1 = Nf + 1, Nc + 1
     rows, cols, vals = [], [], []

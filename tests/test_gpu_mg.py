@@ -98,3 +98,20 @@ def test_mg_argument_errors(torch):
     import ctypes
     v = ctypes.c_size_t()
     assert E.lib().ens_mg_workspace_size(2, c, 4, ctypes.byref(v)) == 1
+
+
+def test_mg_64cubed_s32_sampled(torch):
+    """The benchmark's shape: 64^3 cells, M = 10, s = 32, level 0 pre-split,
+    tol 1e-8; two members against oracle MG-PCG solves."""
+    N, M, s = 64, 10, 32
+    mg = E.Multigrid(N, M)
+    xs = inputs.kl_samples(inputs.SEED_SCALE, 0, s, M)
+    X, it, rr, st = gpu_mg(torch, mg, xs, tol=1e-8, presplit=True)
+    assert st == [0] * s and max(rr) <= 1.01e-8 and max(it) <= 8
+    for e in (0, 17):
+        starts = [start(l, e, (n + 1) ** 3) for l, n in enumerate(G.level_sizes(N))]
+        lv = G.hierarchy(N, M, xs[e], starts)
+        xo, ito, rro, sto = G.mg_pcg(lv, lv[0].load, tol=1e-8)
+        assert sto == 0 and abs(it[e] - ito) <= 1, (e, it[e], ito)
+        err = np.linalg.norm(X[:, e] - xo) / np.linalg.norm(xo)
+        assert err <= 1e-8 or it[e] != ito, (e, err)

@@ -198,3 +198,24 @@ def test_newton_argument_errors(torch):
     with pytest.raises(E.EnsError) as ei:
         nl.solve(4, vals, b, u, small, None, p)
     assert ei.value.code == E.ERR_WORKSPACE
+
+
+def test_newton_64cubed_s32_sampled(torch):
+    """The benchmark's shape: 64^3 cells, s = 32, alpha = 1, beta = 10, Newton
+    to 1e-8, GMRES(30) to 1e-6 per step, V-cycle with level 0 pre-split; two
+    members against oracle Newton solves, and their residuals re-evaluated by
+    the oracle."""
+    N, s, tol, lin_tol = 64, 32, 1e-8, 1e-6
+    xs, U, ni, li, rr, st = newton_case(torch, s, N, 1.0, 10.0, seed=inputs.SEED_SCALE, presplit=True, tol=tol,
+                                        lin_tol=lin_tol, restart=30, max_lin=300)
+    assert st == [0] * s and max(rr) <= tol
+    for e in (0, 31):
+        prob = NL.Problem(N, 10, xs[e], 1.0, 10.0, v=V)
+        f0 = np.linalg.norm(prob.b)
+        assert np.linalg.norm(prob.residual(U[:, e])) <= 1.01 * tol * f0, e
+        lv = G.hierarchy(N, 10, xs[e], [start(l, e, (n + 1) ** 3) for l, n in enumerate(G.level_sizes(N))])
+        uo, ko, lino, hist, sto = NL.newton(prob, tol=tol, lin_tol=lin_tol, restart=30, max_lin=300,
+                                            precond=lambda r, lv=lv: G.vcycle(lv, r))
+        assert sto == 0 and ni[e] == ko, (e, ni[e], ko)
+        assert abs(li[e] - sum(lino)) <= ko, (e, li[e], lino)
+        assert np.linalg.norm(U[:, e] - uo) <= 1e-7 * np.linalg.norm(uo), e
