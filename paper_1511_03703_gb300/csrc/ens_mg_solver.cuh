@@ -424,8 +424,9 @@ struct MgSolver {
             mg_residual_kernel<S, 0><<<chunks(m.n), RowMap<S>::THREADS, 0, st>>>(active, m.n, A, b, x, nullptr, m.r);
     }
 
-    // x = V_l(b)
-    void vcycle(int l, const double *b, double *x, cudaStream_t st) {
+    // x = V_l(b); out_split: on a pre-split level, also leave the split copy of
+    // the result in the level's xs (for a caller's pre-split SpMV of x)
+    void vcycle(int l, const double *b, double *x, cudaStream_t st, bool out_split = false) {
         const int L = (int)lv.size() - 1;
         if (l == L) {
             mg_coarse_solve_kernel<S><<<S, 128, 0, st>>>(active, lv[L].n, inv, b, x);
@@ -439,7 +440,7 @@ struct MgSolver {
         vcycle(l + 1, mc.b, mc.x, st);
         mg_prolong_kernel<S><<<eg, 256, 0, st>>>(active, mc.N, mc.x, x, xs, m.split_bad);  // x += P x_c
         residual(l, b, x, st);
-        smooth(l, m.r, x, nullptr, 1, st);                                          // x = S(b, x)
+        smooth(l, m.r, x, out_split ? xs : nullptr, 1, st);                         // x = S(b, x)
     }
 
     // Per level: D and D^-1, the power estimate of the largest eigenvalue of

@@ -125,6 +125,13 @@ __device__ __forceinline__ Dfp dfp_mulc(Dfp a, float ch, float cl) {
 }
 __device__ __forceinline__ double dfp_to_double(Dfp a) { return f2d_exact(a.h) + f2d_exact(a.l); }
 
+// a value as the pre-split SpMV reads it: the truncating split, or (NaN, 0)
+// outside the split range (the SpMV then recomputes that row in FP64)
+__device__ __forceinline__ float2 nl_split_value(double v) {
+    float hi, lo;
+    return df_split_trunc(v, hi, lo) ? make_float2(hi, lo) : make_float2(__int_as_float(0x7fc00000), 0.0f);
+}
+
 // 1/12 as a float pair
 constexpr float kK12H = (float)(1.0 / 12.0);
 constexpr float kK12L = (float)(1.0 / 12.0 - (double)(float)(1.0 / 12.0));
@@ -156,7 +163,8 @@ __global__ void __launch_bounds__(256) nl_jacobian_kernel(int32_t n, int32_t N, 
                                                           double alpha, float m2h, float m2l,
                                                           const double *__restrict__ b,
                                                           const double *__restrict__ u, double *__restrict__ J,
-                                                          double *__restrict__ F, NlState *ns) {
+                                                          float2 *__restrict__ Js, double *__restrict__ F,
+                                                          NlState *ns) {
     const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (t >= (int64_t)n * S) return;
     const int e = (int)(t % S);
@@ -170,6 +178,7 @@ __global__ void __launch_bounds__(256) nl_jacobian_kernel(int32_t n, int32_t N, 
         for (int32_t p = p0; p < p1; ++p) {
             const double a = A[(int64_t)p * S + e];
             J[(int64_t)p * S + e] = a;
+            if (Js) Js[(int64_t)p * S + e] = nl_split_value(a);
             f = fma(a, u[(int64_t)col[p] * S + e], f);
         }
         F[t] = f;
@@ -200,7 +209,9 @@ __global__ void __launch_bounds__(256) nl_jacobian_kernel(int32_t n, int32_t N, 
                               ? 0.0
                               : dfp_to_double(dfp_mulc(T[w], m2h, m2l));
         const double ac = fma(alpha, C[p], A[(int64_t)p * S + e]);
-        J[(int64_t)p * S + e] = ac + m2;
+        const double jv = ac + m2;
+        J[(int64_t)p * S + e] = jv;
+        if (Js) Js[(int64_t)p * S + e] = nl_split_value(jv);
         f = fma(fma(0.5, m2, ac), u[(int64_t)cj * S + e], f);
     }
     if (bad && e == 0) atomicExch(&ns->graph_bad, 1);
@@ -290,6 +301,10 @@ struct GmArgs {
     int32_t n;
     const int32_t *row_map, *col;
     const double *vals;  // the operator (J)
+    const float2 *vdf;   // its pre-split copy (MODE 3 steps), or NULL
+    uint64_t val_bytes;  // bytes of vdf
+    const float2 *zs;    // MODE 3: split copy of the preconditioned vector z
+    int *split_bad;      // MODE 3: a split copy met a value out of range (FP64 then)
     double *V;           // Krylov basis: restart + 1 blocks of n*S
     int64_t vs;          // n*S
     double *z;           // preconditioned vector
@@ -359,7 +374,9 @@ __global__ void gm_start_kernel(GmArgs a) {
 
 // step j, part 1: w = J z (written to V[j+1]) and the first Gram-Schmidt
 // dots hA_i = v_i . w, i <= j (tj: the tree tm at width (j + 1) s)
-template <int S>
+// MODE 3: the SpMV in double-float from the pre-split J and z (as the CG's
+// pre-split K1), unless a split copy of z met a value out of range
+template <int S, int MODE>
 __global__ void __launch_bounds__(RowMap<S>::THREADS, 1024 / RowMap<S>::THREADS)
     gm_spmv_dots_kernel(GmArgs a, int j, const double *__restrict__ zin, DotTree tj) {
     if (ld_cg(&a.gs->active_count) == 0) return;
@@ -369,8 +386,16 @@ __global__ void __launch_bounds__(RowMap<S>::THREADS, 1024 / RowMap<S>::THREADS)
     const int r = threadIdx.x / G, g = threadIdx.x % G;
     const int64_t R = (int64_t)blockIdx.x * 32 + r;
     const bool valid = R < a.n;
-    const bool staged = stage_chunk(cc, a.row_map, a.col, blockIdx.x, a.n);
-    const double2 w = chunk_spmv<S, double>(cc, staged, a.col, a.vals, zin, r, g, valid);
+    double2 w;
+    if constexpr (MODE == 3) {
+        const bool staged =
+            stage_chunk_pf(cc, a.row_map, a.col, blockIdx.x, a.n, a.vdf, S * 8u, a.val_bytes, 0xffffffffu);
+        w = (ld_cg(a.split_bad) == 0) ? chunk_spmv_dfv<S>(cc, staged, a.col, a.vdf, a.vals, a.zs, r, g, valid)
+                                      : chunk_spmv<S, double>(cc, staged, a.col, a.vals, zin, r, g, valid);
+    } else {
+        const bool staged = stage_chunk(cc, a.row_map, a.col, blockIdx.x, a.n);
+        w = chunk_spmv<S, double>(cc, staged, a.col, a.vals, zin, r, g, valid);
+    }
     if (valid) st_row2<S>(a.V + (int64_t)(j + 1) * a.vs, R, g, w);
     for (int i = 0; i <= j; ++i) {
         double p0 = 0.0, p1 = 0.0;
@@ -589,6 +614,7 @@ struct NlBufs {
     NlState *ns;
     GmState *gs;
     double *V, *z, *t, *du, *J, *F;
+    float2 *Js;  // pre-split J (Newton with a pre-split level 0 of the preconditioner)
     char *tm, *tn;
 };
 
@@ -617,6 +643,7 @@ static size_t nl_layout(int nlevels, const ens_mg_level *lv, int s, int restart,
         o.du = reinterpret_cast<double *>(take(vb));
         o.F = reinterpret_cast<double *>(take(vb));
         o.J = reinterpret_cast<double *>(take(sizeof(double) * (size_t)nnz * s));
+        if (precond && lv[0].values_df) o.Js = reinterpret_cast<float2 *>(take(sizeof(double) * (size_t)nnz * s));
     }
     if (precond) off += mg_layout(nlevels, lv, s, mglv, base ? base + off : nullptr, inv, bad);
     if (base && b) *b = o;
@@ -628,6 +655,7 @@ struct NlSolver {
     GmArgs a;
     MgSolver<S> mg;
     bool precond = false;
+    bool pre = false;  // GMRES SpMV in the pre-split form (J and z split; needs a pre-split level 0)
     int check_every = 8;
     int launches = 0, polls = 0;
     unsigned grid = 0, eg = 152 * 4;
@@ -690,13 +718,14 @@ struct NlSolver {
                     const double *zin = a.V + (int64_t)j * a.vs;
                     if (precond) {
                         mg.active = &a.gs->active_count;
-                        mg.vcycle(0, zin, a.z, st);
+                        mg.vcycle(0, zin, a.z, st, pre);  // pre: z's split copy into level 0's xs
                         launches += mg.launches_per_vcycle();
                         zin = a.z;
                     }
                     DotTree tj = a.tm;
                     tj.width = (j + 1) * S;
-                    gm_spmv_dots_kernel<S><<<grid, T, 0, st>>>(a, j, zin, tj);
+                    if (pre) gm_spmv_dots_kernel<S, 3><<<grid, T, 0, st>>>(a, j, zin, tj);
+                    else gm_spmv_dots_kernel<S, 0><<<grid, T, 0, st>>>(a, j, zin, tj);
                     gm_orth_kernel<S><<<grid, T, 0, st>>>(a, j, 0, tj);
                     gm_orth_kernel<S><<<grid, T, 0, st>>>(a, j, 1, tj);
                     gm_scale_kernel<S><<<eg, 256, 0, st>>>(a, j + 1);
@@ -812,6 +841,13 @@ static int newton_run(int nlevels, const ens_mg_level *lv, const double *C, cons
     if (sv.precond && (rc = sv.setup_mg(lv, p->ratio, p->boost, p->power_iters, st))) return rc;
     GmArgs &a = sv.a;
     a.vals = bufs.J;
+    if (bufs.Js) {  // the GMRES SpMV reads J pre-split and z split by the V-cycle
+        sv.pre = true;
+        a.vdf = bufs.Js;
+        a.val_bytes = (uint64_t)lv[0].graph.num_entries * S * 8u;
+        a.zs = sv.mg.lv[0].xs;
+        a.split_bad = sv.mg.lv[0].split_bad;
+    }
     a.rhs = bufs.F;
     a.sign = -1.0;
     a.x = bufs.du;
@@ -824,7 +860,7 @@ static int newton_run(int nlevels, const ens_mg_level *lv, const double *C, cons
     int32_t h[2];
     for (int it = 0; it <= p->max_newton; ++it) {
         nl_jacobian_kernel<S><<<jgrid, 256, 0, st>>>(n, N, a.row_map, a.col, lv[0].values, C, p->alpha, m2h, m2l,
-                                                    b, u, bufs.J, bufs.F, bufs.ns);
+                                                    b, u, bufs.J, bufs.Js, bufs.F, bufs.ns);
         nl_norm_kernel<S><<<sv.grid, RowMap<S>::THREADS, 0, st>>>(n, bufs.F, a.tn, bufs.ns, 0, it, p->tol,
                                                                  p->max_newton);
         sv.launches += 2;
@@ -907,7 +943,7 @@ extern "C" int ens_nl_jacobian(const ens_graph *gp, int32_t N, int s, const doub
     nl_m2_split(beta, N, &m2h, &m2l);
 #define NL_JAC(SS)                                                                                             \
     (nl_jacobian_kernel<SS><<<grid, 256, 0, st>>>(g.num_rows, N, g.row_map, g.col_entry, A, C, alpha, m2h, m2l, \
-                                                  b, u, J, F, ns),                                             \
+                                                  b, u, J, nullptr, F, ns),                                    \
      ENS_OK)
     switch (s) {
         case 1: NL_JAC(1); break;
