@@ -484,8 +484,9 @@ int ens_guess(const int32_t *dims, const float *params, int64_t n, int32_t s, co
  * rows of F and J are those of A (identity), boundary columns of J are 0.
  * v is a constant velocity; all integrals are exact (2x2x2 Gauss would be).
  * Newton's method (Eq. 10) solves J(u_k) du = -F(u_k), u_{k+1} = u_k + du,
- * per member, with restarted GMRES (right-preconditioned, classical
- * Gram-Schmidt applied twice, Givens rotations) for the non-symmetric J.
+ * per member, with restarted GMRES (one of the Belos solvers of Sect. 3.4;
+ * right-preconditioned, classical Gram-Schmidt applied twice, Givens
+ * rotations) for the non-symmetric J.
  * The paper's experiments take alpha = beta = 0; the velocity, the source and
  * the GMRES preconditioner (the V-cycle of the diffusion operator A, fixed for
  * all Newton steps) are this library's readings. */
@@ -543,8 +544,11 @@ typedef struct ens_newton_params {
  * values, also the finest level of the preconditioner's hierarchy); C from
  * ens_nl_advection; b the load.  Per member: newton_iters (steps taken),
  * lin_iters (GMRES steps summed), relres = ||F(u)|| / ||F(u_0)||, status
- * (ENS_ERR_NOT_CONVERGED after max_newton steps).  work:
- * ens_newton_workspace_size bytes.  Synchronises `stream`. */
+ * (ENS_ERR_NOT_CONVERGED after max_newton steps).  With ENS_NL_PRECOND_MG
+ * and levels[0].values_df the V-cycle's finest level and the GMRES SpMV run
+ * in the pre-split double-float form (the Jacobian is then also written as
+ * float pairs).  work: ens_newton_workspace_size bytes.  Synchronises
+ * `stream`. */
 int ens_newton_workspace_size(int nlevels, const ens_mg_level *levels, int s, const ens_newton_params *p,
                               size_t *bytes);
 int ens_newton(int nlevels, const ens_mg_level *levels, int s, const double *C, const double *b, double *u,
