@@ -991,8 +991,8 @@ def main_pcg(args):
 MG_SAMPLES = 256
 MG_WORKLOAD = ("KL diffusion, 64^3 hex Q1 mesh, M=10, 256 samples as 8 ensembles of s=32, CG to 1e-8: "
                "multigrid-preconditioned ensemble CG (V-cycle over 64^3..4^3, Chebyshev-2 smoothers, "
-               "direct coarse solve; mg: level-0 SpMVs in double-float from pre-split values, mg_f64: all "
-               "FP64) vs plain ensemble CG")
+               "direct coarse solve; mg: the SpMVs in double-float from pre-split values on every level, "
+               "mg_f64: all FP64) vs plain ensemble CG")
 
 
 def main_mg(args):
@@ -1015,10 +1015,12 @@ def main_mg(args):
                                         axis=1).reshape(-1)).to(dev) for l, m in enumerate(mg.meshes)]
     mesh = mg.meshes[0]
     vdf = torch.empty(2 * mesh.nnz * s, dtype=torch.float32, device=dev)
+    # mg: every level's SpMVs from pre-split values (level 0's buffer shared with cg_dfv)
+    vdfs = [vdf] + [torch.empty(2 * m.nnz * s, dtype=torch.float32, device=dev) for m in mg.meshes[1:]]
     wcg = torch.empty(E.cg_workspace_size(mesh.n, s), dtype=torch.uint8, device=dev)
     x = torch.empty(mesh.n * s, dtype=torch.float64, device=dev)
-    vals0, _ = mg.assemble(s, xis[0], values_df=vdf)
-    wmg = torch.empty(mg.workspace_size(s, vals0, starts, vdf), dtype=torch.uint8, device=dev)
+    vals0, _ = mg.assemble(s, xis[0], values_df=vdfs)
+    wmg = torch.empty(mg.workspace_size(s, vals0, starts, vdfs), dtype=torch.uint8, device=dev)
     del vals0
 
     def run(form):
@@ -1028,8 +1030,8 @@ def main_mg(args):
         for xi in xis:
             x.zero_()
             if form in ("mg", "mg_f64"):
-                # mg: level 0 (K1 and the V-cycle's finest SpMVs) from pre-split values
-                pre = vdf if form == "mg" else None
+                # mg: K1 and every level's V-cycle SpMVs from pre-split values
+                pre = vdfs if form == "mg" else None
                 vals, b = mg.assemble(s, xi, df=True, values_df=pre)
                 it, rr, st, _ = mg.solve(s, vals, b, x, TOL, 500, wmg, starts, flags=E.CG_GRAPH | E.CG_X0_ZERO,
                                          check_every=4, values_df=pre)
@@ -1070,7 +1072,7 @@ NL_TOL, NL_LIN_TOL = 1e-8, 1e-6
 NL_WORKLOAD = ("nonlinear advection-diffusion -div(kappa grad u) + alpha v.grad u + beta u^2 = 1, 64^3 hex Q1 "
                "mesh, M=10, alpha=1, v=(1,1,1), beta=10, 256 samples as 8 ensembles of s=32: Newton to "
                "||F|| <= 1e-8 ||F(0)||, GMRES(30) to 1e-6 ||F_k|| per step, right-preconditioned by the V-cycle "
-               "of the diffusion operator")
+               "of the diffusion operator (pre-split values on every level)")
 
 
 def main_nonlinear(args):
@@ -1093,7 +1095,8 @@ def main_nonlinear(args):
                                         axis=1).reshape(-1)).to(dev) for l, m in enumerate(nl.meshes)]
     p = nl.params(NL_ALPHA, NL_BETA, tol=NL_TOL, lin_tol=NL_LIN_TOL, restart=30, max_lin=300, max_newton=20)
     u = torch.empty(nl.mesh.n * s, dtype=torch.float64, device=dev)
-    vdf = torch.empty(2 * nl.mesh.nnz * s, dtype=torch.float32, device=dev)  # level 0 pre-split (V-cycle)
+    # every level pre-split (the V-cycle's SpMVs; level 0's also makes the GMRES SpMV pre-split)
+    vdf = [torch.empty(2 * m.nnz * s, dtype=torch.float32, device=dev) for m in nl.meshes]
     vals0, _ = nl.assemble(s, xis[0], values_df=vdf)
     work = torch.empty(nl.workspace_size(s, vals0, starts, p, vdf), dtype=torch.uint8, device=dev)
     del vals0

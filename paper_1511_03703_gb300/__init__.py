@@ -348,6 +348,15 @@ def pcg(graph, s, values, b, x, tol, max_iter, work, precond=PC_JACOBI, degree=2
 
 
 # ------------------------------------------------ multigrid-preconditioned CG
+def _per_level(values_df, nlevels):
+    """values_df as a per-level list: None, one tensor (level 0) or a list."""
+    if values_df is None:
+        return [None] * nlevels
+    if isinstance(values_df, (list, tuple)):
+        return list(values_df) + [None] * (nlevels - len(values_df))
+    return [values_df] + [None] * (nlevels - 1)
+
+
 def mg_level_sizes(N):
     """N, N/2, ... while the size is even and above 4 (the coarsest has <= 125 rows)."""
     out = [N]
@@ -370,11 +379,12 @@ class Multigrid:
     def assemble(self, s, xi_ens, sigma=0.1, kappa0=1.0, df=False, values_df=None):
         """Values of every level and the level-0 right-hand side (df: the
         double-float assembly, see assemble(); values_df: a 2*nnz*s float32
-        tensor that receives level 0's pre-split values, for solve())."""
+        tensor that receives level 0's pre-split values, or a list of such
+        tensors (or None) per level, for solve())."""
+        vdfs = _per_level(values_df, len(self.meshes))
         vals, b0 = [], None
         for l, mesh in enumerate(self.meshes):
-            v, b = mesh.assemble(s, xi_ens, sigma=sigma, kappa0=kappa0, df=df,
-                                 values_df=values_df if l == 0 else None)
+            v, b = mesh.assemble(s, xi_ens, sigma=sigma, kappa0=kappa0, df=df, values_df=vdfs[l])
             vals.append(v)
             if l == 0:
                 b0 = b
@@ -388,9 +398,10 @@ class Multigrid:
             c[l].N = mesh.N
             c[l].values = values[l].data_ptr()
             c[l].power_start = power_starts[l].data_ptr()
-        if values_df is not None:
-            _require_cuda(values_df)
-            c[0].values_df = values_df.data_ptr()
+        for l, v in enumerate(_per_level(values_df, len(self.meshes))):
+            if v is not None:
+                _require_cuda(v)
+                c[l].values_df = v.data_ptr()
         return c
 
     def workspace_size(self, s, values, power_starts, values_df=None):
@@ -468,7 +479,8 @@ class Nonlinear:
         """Diffusion values of every level and the load (see Multigrid.assemble)."""
         if self.mg is not None:
             return self.mg.assemble(s, xi_ens, sigma=sigma, kappa0=kappa0, df=df, values_df=values_df)
-        v, b = self.mesh.assemble(s, xi_ens, sigma=sigma, kappa0=kappa0, df=df, values_df=values_df)
+        v, b = self.mesh.assemble(s, xi_ens, sigma=sigma, kappa0=kappa0, df=df,
+                                  values_df=_per_level(values_df, 1)[0])
         return [v], b
 
     def _levels(self, values, power_starts, values_df=None):
@@ -479,9 +491,10 @@ class Nonlinear:
             c[l].N = mesh.N
             c[l].values = values[l].data_ptr()
             c[l].power_start = power_starts[l].data_ptr() if power_starts is not None else None
-        if values_df is not None:
-            _require_cuda(values_df)
-            c[0].values_df = values_df.data_ptr()
+        for l, v in enumerate(_per_level(values_df, len(self.meshes))):
+            if v is not None:
+                _require_cuda(v)
+                c[l].values_df = v.data_ptr()
         return c
 
     def params(self, alpha, beta, tol=1e-8, lin_tol=1e-10, max_newton=20, restart=30, max_lin=500, degree=2,

@@ -6,8 +6,8 @@ Builds the level hierarchy (N, N/2, ... > 4), then `reps` times assembles
 every level of one ensemble of s samples (double-float assembly, M = 10, seed
 of the 64^3 workload) and solves to 1e-8 with the V-cycle preconditioner
 (graph replay of 4 iterations), printing the wall time of each part.
-presplit: level 0 also writes its pre-split values, so that the level-0 SpMVs
-run in double-float (as in the benchmark).  Used
+presplit: every level also writes its pre-split values, so that the V-cycle's
+SpMVs run in double-float (as in the benchmark).  Used
 for the launch-list summaries under profiles/.
 """
 import sys
@@ -30,7 +30,8 @@ def main(argv):
     starts = [torch.from_numpy(np.stack([inputs.random_vector(600 + 100 * l + e, m.n) for e in range(s)],
                                         axis=1).reshape(-1)).to(dev) for l, m in enumerate(mg.meshes)]
     x = torch.zeros(mg.meshes[0].n * s, dtype=torch.float64, device=dev)
-    vdf = torch.empty(2 * mg.meshes[0].nnz * s, dtype=torch.float32, device=dev) if presplit else None
+    vdf = ([torch.empty(2 * m.nnz * s, dtype=torch.float32, device=dev) for m in mg.meshes]
+           if presplit else None)
     vals, b = mg.assemble(s, xi, df=True, values_df=vdf)
     work = torch.empty(mg.workspace_size(s, vals, starts, vdf), dtype=torch.uint8, device=dev)
     for rep in range(reps):

@@ -5,7 +5,7 @@ problem on an N^3 mesh.
 
 Builds the level hierarchy and the advection matrix (v = (1, 1, 1)), then
 `reps` times assembles every level of one ensemble of s samples (double-float
-assembly with level 0's pre-split copy, M = 10, seed of the 64^3 workload)
+assembly with every level's pre-split copy, M = 10, seed of the 64^3 workload)
 and runs Newton from u = 0 (alpha = 1, beta = 10, tol 1e-8, GMRES(30) to
 1e-6 per step, V-cycle right preconditioner), printing the wall time of each
 part.  Used for the launch-list summaries under profiles/.
@@ -30,7 +30,7 @@ def main(argv):
                                         axis=1).reshape(-1)).to(dev) for l, m in enumerate(nl.meshes)]
     p = nl.params(1.0, 10.0, tol=1e-8, lin_tol=1e-6, restart=30, max_lin=300, max_newton=20)
     u = torch.zeros(nl.mesh.n * s, dtype=torch.float64, device=dev)
-    vdf = torch.empty(2 * nl.mesh.nnz * s, dtype=torch.float32, device=dev)
+    vdf = [torch.empty(2 * m.nnz * s, dtype=torch.float32, device=dev) for m in nl.meshes]
     vals, b = nl.assemble(s, xi, values_df=vdf)
     work = torch.empty(nl.workspace_size(s, vals, starts, p, vdf), dtype=torch.uint8, device=dev)
     for rep in range(reps):

@@ -32,7 +32,10 @@ def gpu_mg(torch, mg, xs, tol=1e-10, flags=0, degree=2, ratio=5.0, check_every=4
     """presplit: level 0 assembled in double-float with its pre-split copy, so
     that the level-0 SpMVs (K1 and the V-cycle's) run in double-float."""
     s = xs.shape[0]
-    vdf = torch.empty(2 * mg.meshes[0].nnz * s, dtype=torch.float32, device=gpu()) if presplit else None
+    if presplit == "all":   # every level pre-split
+        vdf = [torch.empty(2 * m.nnz * s, dtype=torch.float32, device=gpu()) for m in mg.meshes]
+    else:
+        vdf = torch.empty(2 * mg.meshes[0].nnz * s, dtype=torch.float32, device=gpu()) if presplit else None
     vals, b = mg.assemble(s, to_dev(inputs.ensemble_layout(xs)), values_df=vdf)
     starts = [to_dev(np.stack([start(l, e, m.n) for e in range(s)], axis=1).reshape(-1))
               for l, m in enumerate(mg.meshes)]
@@ -43,7 +46,7 @@ def gpu_mg(torch, mg, xs, tol=1e-10, flags=0, degree=2, ratio=5.0, check_every=4
     return to_np(x).reshape(-1, s), it, rr, st
 
 
-@pytest.mark.parametrize("presplit", [False, True])
+@pytest.mark.parametrize("presplit", [False, True, "all"])
 @pytest.mark.parametrize("s", [1, 4, 32])
 def test_mg_pcg_matches_oracle(torch, s, presplit):
     N, M = 16, 10
@@ -60,7 +63,7 @@ def test_mg_pcg_matches_oracle(torch, s, presplit):
         assert np.linalg.norm(X[:, e] - xo) <= 1e-8 * np.linalg.norm(xo), e
 
 
-@pytest.mark.parametrize("presplit", [False, True])
+@pytest.mark.parametrize("presplit", [False, True, "all"])
 def test_mg_member_independent_of_s_and_graph(torch, presplit):
     mg = E.Multigrid(8, 10)
     xs = inputs.kl_samples(820, 0, 32, 10)
@@ -101,12 +104,12 @@ def test_mg_argument_errors(torch):
 
 
 def test_mg_64cubed_s32_sampled(torch):
-    """The benchmark's shape: 64^3 cells, M = 10, s = 32, level 0 pre-split,
-    tol 1e-8; two members against oracle MG-PCG solves."""
+    """The benchmark's shape: 64^3 cells, M = 10, s = 32, every level
+    pre-split, tol 1e-8; two members against oracle MG-PCG solves."""
     N, M, s = 64, 10, 32
     mg = E.Multigrid(N, M)
     xs = inputs.kl_samples(inputs.SEED_SCALE, 0, s, M)
-    X, it, rr, st = gpu_mg(torch, mg, xs, tol=1e-8, presplit=True)
+    X, it, rr, st = gpu_mg(torch, mg, xs, tol=1e-8, presplit="all")
     assert st == [0] * s and max(rr) <= 1.01e-8 and max(it) <= 8
     for e in (0, 17):
         starts = [start(l, e, (n + 1) ** 3) for l, n in enumerate(G.level_sizes(N))]

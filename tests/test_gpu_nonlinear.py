@@ -137,7 +137,10 @@ def newton_case(torch, s, N, alpha, beta, precond=E.NL_PRECOND_MG, seed=960, pre
     M = 10
     nl = E.Nonlinear(N, M, v=V, precond=precond)
     xs = inputs.kl_samples(seed, 0, s, M)
-    vdf = torch.empty(2 * nl.mesh.nnz * s, dtype=torch.float32, device=gpu()) if presplit else None
+    if presplit == "all":
+        vdf = [torch.empty(2 * m.nnz * s, dtype=torch.float32, device=gpu()) for m in nl.meshes]
+    else:
+        vdf = torch.empty(2 * nl.mesh.nnz * s, dtype=torch.float32, device=gpu()) if presplit else None
     vals, b = nl.assemble(s, to_dev(inputs.ensemble_layout(xs)), values_df=vdf)
     starts = dev_starts(nl, s) if precond == E.NL_PRECOND_MG else None
     p = nl.params(alpha, beta, **kw)
@@ -148,7 +151,7 @@ def newton_case(torch, s, N, alpha, beta, precond=E.NL_PRECOND_MG, seed=960, pre
 
 
 @pytest.mark.parametrize("s,presplit", [(1, False), (4, False), (8, False), (16, True), (32, False), (4, True),
-                                        (32, True)])
+                                        (32, True), (32, "all")])
 def test_newton_matches_oracle(torch, s, presplit):
     N, alpha, beta, tol, lin_tol = 8, 1.0, 10.0, 1e-10, 1e-11
     xs, U, ni, li, rr, st = newton_case(torch, s, N, alpha, beta, tol=tol, lin_tol=lin_tol, presplit=presplit)
@@ -206,7 +209,7 @@ def test_newton_64cubed_s32_sampled(torch):
     members against oracle Newton solves, and their residuals re-evaluated by
     the oracle."""
     N, s, tol, lin_tol = 64, 32, 1e-8, 1e-6
-    xs, U, ni, li, rr, st = newton_case(torch, s, N, 1.0, 10.0, seed=inputs.SEED_SCALE, presplit=True, tol=tol,
+    xs, U, ni, li, rr, st = newton_case(torch, s, N, 1.0, 10.0, seed=inputs.SEED_SCALE, presplit="all", tol=tol,
                                         lin_tol=lin_tol, restart=30, max_lin=300)
     assert st == [0] * s and max(rr) <= tol
     for e in (0, 31):
