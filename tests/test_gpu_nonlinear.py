@@ -222,3 +222,30 @@ def test_newton_64cubed_s32_sampled(torch):
         assert sto == 0 and ni[e] == ko, (e, ni[e], ko)
         assert abs(li[e] - sum(lino)) <= ko, (e, li[e], lino)
         assert np.linalg.norm(U[:, e] - uo) <= 1e-7 * np.linalg.norm(uo), e
+
+
+def test_gmres_zero_rhs_member_and_newton_step_limit(torch):
+    """A member with b = 0 is solved by x = 0 at once while the others iterate;
+    Newton stopped by max_newton reports not converged after that many steps."""
+    s = 4
+    nl = E.Nonlinear(6, 10, v=V, precond=E.NL_PRECOND_NONE)
+    xs = inputs.kl_samples(970, 0, s, 10)
+    vals, b = nl.assemble(s, to_dev(inputs.ensemble_layout(xs)))
+    mo = NL.Mesh(6)
+    us = zero_boundary_field(975, mo, s)
+    J, _ = E.nl_jacobian(nl.mesh, s, vals[0], nl.C, 5.0, 10.0, b, to_dev(O.to_ensemble(us)))
+    rhs = [inputs.random_vector(980 + e, mo.n) for e in range(s)]
+    rhs[2] = np.zeros(mo.n)
+    x = torch.full((mo.n * s,), 3.0, dtype=torch.float64, device=gpu())
+    work = torch.empty(nl.gmres_workspace_size(s, vals, None, 10), dtype=torch.uint8, device=gpu())
+    it, rr, st, _ = nl.gmres(s, vals, J, to_dev(O.to_ensemble(rhs)), x, work, None, 1e-10, restart=10,
+                             max_iter=400)
+    X = to_np(x).reshape(-1, s)
+    Jn = to_np(J).reshape(-1, s)
+    assert st == [0] * s and it[2] == 0 and rr[2] == 0.0 and not np.any(X[:, 2])
+    for e in (0, 1, 3):
+        xo, ito, _, sto = NL.gmres(mo.rm, mo.col, Jn[:, e], rhs[e], None, restart=10, tol=1e-10, max_iter=400)
+        assert abs(it[e] - ito) <= 2 and np.linalg.norm(X[:, e] - xo) <= 1e-8 * np.linalg.norm(xo), e
+    xs2, U, ni, li, rr2, st2 = newton_case(torch, 4, 8, 1.0, 10.0, precond=E.NL_PRECOND_NONE, tol=1e-14,
+                                           lin_tol=1e-3, max_newton=1, restart=30)
+    assert ni == [1] * 4 and st2 == [E.ERR_NOT_CONVERGED] * 4 and min(rr2) > 1e-14
