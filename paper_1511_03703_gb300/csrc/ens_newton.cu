@@ -26,7 +26,9 @@
 // preconditioner (w = J z with the dots v_i.w; two orthogonalisation passes,
 // the second with ||w|| and the Givens update in its last CTA; the
 // normalisation).  All reductions use the chunk trees of the CG, so every
-// member's result is independent of the ensemble size.  All FP64.
+// member's result is independent of the ensemble size.  Vectors, dots,
+// Gram-Schmidt and Givens arithmetic are FP64; the GMRES SpMV is FP64 or, with
+// a pre-split level 0, the pre-split double-float form on a split copy of J.
 #include "ens_mg_solver.cuh"
 
 namespace ens {
@@ -618,8 +620,9 @@ struct NlBufs {
     char *tm, *tn;
 };
 
-// workspace: states, Krylov basis, z, t, trees; Newton adds du, J and F;
-// with the multigrid preconditioner the hierarchy follows (mg_layout)
+// workspace: states, Krylov basis, z, t, trees; Newton adds du, J and F (and
+// the split J when level 0 of the preconditioner is pre-split); with the
+// multigrid preconditioner the hierarchy follows (mg_layout)
 static size_t nl_layout(int nlevels, const ens_mg_level *lv, int s, int restart, bool newton, bool precond,
                         char *base, NlBufs *b, std::vector<MgLevel> *mglv, double **inv, int **bad) {
     size_t off = 0;
