@@ -3,7 +3,8 @@
 // ens_mg_solver.cuh (rho = r.z), reusing the CG kernels: per iteration
 //   K1 (q = A p, alpha), MR (r -= alpha q, r.r), the V-cycle, MZ (r.z: stop
 //   test, beta), K3 (x += alpha p, p = z + beta p).
-// All FP64.  Every launch of an iteration is asynchronous; with ENS_CG_GRAPH
+// FP64, with the SpMVs of pre-split levels (and K1 when level 0 is pre-split)
+// in double-float.  Every launch of an iteration is asynchronous; with ENS_CG_GRAPH
 // check_every iterations are replayed as one CUDA graph.
 #include "ens_mg_solver.cuh"
 

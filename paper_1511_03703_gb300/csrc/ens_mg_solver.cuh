@@ -13,7 +13,9 @@
 //   V_L   x = A_L^-1 b with the inverse of the coarsest matrix, formed once per
 //         solve by Gauss-Jordan elimination (the matrix is SPD; <= 125 rows)
 //   V_l   x = S(b, 0); r = b - A x; x += P V_{l+1}(R r); x = S(b, x)
-// All FP64.  Every V-cycle kernel exits at entry once the calling solver's
+// FP64 vectors; a level's SpMVs are FP64 or, on a level with pre-split values,
+// double-float (as the pre-split CG SpMV).  Every V-cycle kernel exits at
+// entry once the calling solver's
 // active-member count is 0, so launches queued past convergence cost nothing.
 #pragma once
 
