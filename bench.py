@@ -317,7 +317,7 @@ def e2e_run(torch, r, steps):
         copy_stream.synchronize()
     T.cuda.synchronize()
     dt = time.perf_counter() - t0
-    return {"value": steps * r.batch / dt, "unit": UNIT,
+    return {"value": steps * r.batch / dt, "unit": UNIT, "ms": 1e3 * dt, "samples": steps * r.batch,
             "h2d_bytes_per_step": int(r.xi_host.nbytes),
             "d2h_bytes_per_step": int(r.nens * r.n * r.s * 8)}
 
@@ -404,6 +404,10 @@ def main_ours(args):
     gpu_launches = r.launches
     iters = r.iters
     bad = r.status_bad
+    # end to end through the API on every rank (host buffers), slowest rank's time
+    e2e = e2e_run(torch, r, max(1, min(args.steps, 2)))
+    e2e_ms = max_over_ranks(e2e.pop("ms"), world, device)
+    e2e["value"] = world * e2e.pop("samples") / (e2e_ms * 1e-3)
     out = None
     if rank == 0:
         sm_mhz = clk.get("sm_mhz") or 2070.0
@@ -422,11 +426,13 @@ def main_ours(args):
         roof.update({"kernel": f"cg_spmv_kernel<{s},{df}> (q = A p fused with per-member p.q)",
                      "bytes_per_launch": bytes_launch, "avg_launch_ms": avg_spmv_ms,
                      "launches_timed": r.spmv_launches})
-        e2e = e2e_run(torch, r, max(1, min(args.steps, 2)))
-        per = per_sample_baseline(torch, device, df=df)
-        ens_speedup = value / world / per["value"]
+        # the single-GPU comparisons (per-sample CG, other SpMV forms, the
+        # sweep, the CPU oracle) only at N = 1
+        solo = world == 1
+        per = per_sample_baseline(torch, device, df=df) if solo else None
+        ens_speedup = value / world / per["value"] if solo else None
         others = {}
-        if not args.quick:
+        if solo and not args.quick:
             for form in FORMS:
                 if form == df:
                     continue
@@ -445,7 +451,7 @@ def main_ours(args):
                                 "spmv_hbm_frac": bytes_launch / (ms2 * 1e-3) / 1e9 / peak,
                                 "mean_iters": float(np.mean(r2.iters)), "failed_members": r2.status_bad}
                 del r2
-        sweep = None if args.quick else spmv_sweep(torch, device)
+        sweep = None if (args.quick or not solo) else spmv_sweep(torch, device)
         out = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
@@ -462,7 +468,7 @@ def main_ours(args):
                        "l2": "inputs larger than L2 (1.8 GB values per ensemble)",
                        "parallelism": f"replica per GPU, {world} GPU(s), samples sharded by rank"},
             "roofline": roof,
-            "cpu_baseline": cpu_baseline_run() if not args.no_cpu_baseline else None,
+            "cpu_baseline": cpu_baseline_run() if (solo and not args.no_cpu_baseline) else None,
             "e2e": e2e,
             "per_sample_gpu": per,
             "ensemble_speedup_vs_per_sample": ens_speedup,
