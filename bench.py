@@ -1026,7 +1026,9 @@ def main_mg(args):
     wcg = torch.empty(E.cg_workspace_size(mesh.n, s), dtype=torch.uint8, device=dev)
     x = torch.empty(mesh.n * s, dtype=torch.float64, device=dev)
     vals0, _ = mg.assemble(s, xis[0], values_df=vdfs)
-    wmg = torch.empty(mg.workspace_size(s, vals0, starts, vdfs), dtype=torch.uint8, device=dev)
+    v32s = mg.to_f32(s, vals0)
+    wmg = torch.empty(max(mg.workspace_size(s, vals0, starts, vdfs),
+                          mg.workspace_size(s, vals0, starts, [vdf], v32s)), dtype=torch.uint8, device=dev)
     del vals0
 
     def run(form):
@@ -1035,12 +1037,14 @@ def main_mg(args):
         t = time.perf_counter()
         for xi in xis:
             x.zero_()
-            if form in ("mg", "mg_f64"):
-                # mg: K1 and every level's V-cycle SpMVs from pre-split values
-                pre = vdfs if form == "mg" else None
+            if form in ("mg", "mg_f64", "mg_fp32_vcycle"):
+                # mg: K1 and every level's V-cycle SpMVs from pre-split values;
+                # mg_fp32_vcycle: K1 pre-split, the V-cycle in FP32
+                pre = vdfs if form == "mg" else ([vdf] if form == "mg_fp32_vcycle" else None)
                 vals, b = mg.assemble(s, xi, df=True, values_df=pre)
+                v32 = mg.to_f32(s, vals, out=v32s) if form == "mg_fp32_vcycle" else None
                 it, rr, st, _ = mg.solve(s, vals, b, x, TOL, 500, wmg, starts, flags=E.CG_GRAPH | E.CG_X0_ZERO,
-                                         check_every=4, values_df=pre)
+                                         check_every=4, values_df=pre, values_f32=v32)
             else:
                 vals, b = mesh.assemble(s, xi, values_df=vdf if form == "cg_dfv" else None)
                 it, rr, st, _ = E.cg(mesh.graph, s, vals, b, x, TOL, 10000, wcg,
@@ -1053,7 +1057,7 @@ def main_mg(args):
         return its, time.perf_counter() - t
 
     out = {}
-    for form in ("cg_f64", "cg_dfv", "mg_f64", "mg"):
+    for form in ("cg_f64", "cg_dfv", "mg_f64", "mg", "mg_fp32_vcycle"):
         for _ in range(args.warmup):
             run(form)
         its, sec = run(form)

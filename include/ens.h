@@ -301,6 +301,10 @@ typedef struct ens_mg_level {
     const float *values_df;     /* optional: values pre-split into float pairs (ens_assemble_df or
                                    ens_convert_values ENS_F64_DF); the level's SpMVs then run in
                                    double-float (FP64-class, as ens_cg_df); NULL: FP64 SpMVs */
+    const float *values_f32;    /* optional, on every level or none (ens_mg_pcg only): values
+                                   rounded to FP32 (ens_convert_values ENS_F32); the V-cycle then
+                                   runs in FP32 (values, vectors, arithmetic) as a mixed-precision
+                                   preconditioner of the FP64 CG; the set-up stays FP64 */
 } ens_mg_level;
 int ens_mg_workspace_size(int nlevels, const ens_mg_level *levels, int s, size_t *bytes);
 int ens_mg_pcg(int nlevels, const ens_mg_level *levels, int s, const double *b, double *x, double tol,

@@ -52,7 +52,8 @@ class BatchItemC(ctypes.Structure):
 
 class MgLevelC(ctypes.Structure):
     _fields_ = [("graph", EnsGraphC), ("N", ctypes.c_int32), ("reserved", ctypes.c_int32),
-                ("values", ctypes.c_void_p), ("power_start", ctypes.c_void_p), ("values_df", ctypes.c_void_p)]
+                ("values", ctypes.c_void_p), ("power_start", ctypes.c_void_p), ("values_df", ctypes.c_void_p),
+                ("values_f32", ctypes.c_void_p)]
 
 
 class NewtonParamsC(ctypes.Structure):
@@ -390,7 +391,7 @@ class Multigrid:
                 b0 = b
         return vals, b0
 
-    def _levels(self, s, values, power_starts, values_df=None):
+    def _levels(self, s, values, power_starts, values_df=None, values_f32=None):
         c = (MgLevelC * len(self.meshes))()
         for l, mesh in enumerate(self.meshes):
             _require_cuda(values[l], power_starts[l])
@@ -402,20 +403,34 @@ class Multigrid:
             if v is not None:
                 _require_cuda(v)
                 c[l].values_df = v.data_ptr()
+        if values_f32 is not None:
+            for l, v in enumerate(values_f32):
+                _require_cuda(v)
+                c[l].values_f32 = v.data_ptr()
         return c
 
-    def workspace_size(self, s, values, power_starts, values_df=None):
+    def to_f32(self, s, values, out=None, stream=None):
+        """FP32 copies of every level's values (for the FP32 V-cycle of solve())."""
+        import torch
+        out = out or [torch.empty(v.numel(), dtype=torch.float32, device=v.device) for v in values]
+        for l, mesh in enumerate(self.meshes):
+            convert_values(mesh.graph, s, values[l], out[l], stream=stream)
+        return out
+
+    def workspace_size(self, s, values, power_starts, values_df=None, values_f32=None):
         v = ctypes.c_size_t()
-        c = self._levels(s, values, power_starts, values_df)
+        c = self._levels(s, values, power_starts, values_df, values_f32)
         _check(lib().ens_mg_workspace_size(len(self.meshes), c, s, ctypes.byref(v)))
         return v.value
 
     def solve(self, s, values, b, x, tol, max_iter, work, power_starts, degree=2, ratio=5.0, boost=1.1,
-              power_iters=10, flags=0, check_every=8, stream=None, values_df=None):
-        """Returns (iters[s], relres[s], status[s], CgStats).  values_df: level
-        0's pre-split values (the level-0 SpMVs in double-float).  Synchronises."""
+              power_iters=10, flags=0, check_every=8, stream=None, values_df=None, values_f32=None):
+        """Returns (iters[s], relres[s], status[s], CgStats).  values_df: pre-split
+        values (level 0's, or a list per level: those SpMVs in double-float);
+        values_f32: FP32 values of every level (to_f32): the V-cycle in FP32.
+        Synchronises."""
         _require_cuda(b, x, work)
-        c = self._levels(s, values, power_starts, values_df)
+        c = self._levels(s, values, power_starts, values_df, values_f32)
         it = (ctypes.c_int32 * s)()
         rr = (ctypes.c_double * s)()
         stt = (ctypes.c_int32 * s)()

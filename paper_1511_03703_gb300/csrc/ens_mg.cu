@@ -126,6 +126,7 @@ static int mg_run(int nl, const ens_mg_level *levels, const double *b, double *x
     int *bad = nullptr;
     mg_pcg_layout(nl, levels, S, &mg.lv, static_cast<char *>(work), &c, &z, &mg.inv, &bad);
     mg.degree = degree;
+    mg.f32 = levels[0].values_f32 != nullptr;
     mg.active = &c.st->active_count;
     mg.eg = 152 * 4;
     c.b = b;
@@ -149,7 +150,8 @@ static int mg_run(int nl, const ens_mg_level *levels, const double *b, double *x
     c3.r = z;
     auto stage = [&](int init, cudaStream_t s_) {
         if (!init) mg_pcg_resid_kernel<S><<<grid, RowMap<S>::THREADS, 0, s_>>>(pa0);
-        mg.vcycle(0, c.r, z, s_);
+        if (mg.f32) mg.vcycle32(0, c.r, nullptr, mg.lv[0].x32, z, s_);
+        else mg.vcycle(0, c.r, z, s_);
         mg_pcg_rz_kernel<S><<<grid, RowMap<S>::THREADS, 0, s_>>>(pa0, z, init);
         cg_update_kernel<S, MODE><<<vgrid, VecMap<S>::THREADS, 0, s_>>>(c3);
     };

@@ -25,6 +25,7 @@
 #include <vector>
 
 #include "ens_pcg_kernels.cuh"
+#include "ens_spmv_f32.cuh"
 
 namespace ens {
 
@@ -39,9 +40,8 @@ __device__ __forceinline__ int64_t node_id(int i, int j, int k, int n1) {
 
 // b_c = R r_f on the interior coarse nodes, 0 on the coarse boundary
 // (thread per coarse node and member)
-template <int S>
-__global__ void mg_restrict_kernel(const int *active, int Nc, const double *__restrict__ rf,
-                                   double *__restrict__ bc) {
+template <int S, typename T = double>
+__global__ void mg_restrict_kernel(const int *active, int Nc, const T *__restrict__ rf, T *__restrict__ bc) {
     if (ld_cg(active) == 0) return;
     const int nc1 = Nc + 1, nf1 = 2 * Nc + 1;
     const int64_t total = (int64_t)nc1 * nc1 * nc1 * S;
@@ -50,7 +50,7 @@ __global__ void mg_restrict_kernel(const int *active, int Nc, const double *__re
         const int e = (int)(t % S);
         const int64_t I = t / S;
         const int ci = (int)(I % nc1), cj = (int)((I / nc1) % nc1), ck = (int)(I / ((int64_t)nc1 * nc1));
-        double acc = 0.0;
+        T acc = T(0);
         if (ci > 0 && ci < Nc && cj > 0 && cj < Nc && ck > 0 && ck < Nc) {
             for (int dk = -1; dk <= 1; ++dk)
                 for (int dj = -1; dj <= 1; ++dj)
@@ -58,7 +58,7 @@ __global__ void mg_restrict_kernel(const int *active, int Nc, const double *__re
                         const int fi = 2 * ci + di, fj = 2 * cj + dj, fk = 2 * ck + dk;
                         // fine boundary nodes are not in the range of P
                         if (fi <= 0 || fi >= 2 * Nc || fj <= 0 || fj >= 2 * Nc || fk <= 0 || fk >= 2 * Nc) continue;
-                        const double w = (di ? 0.5 : 1.0) * (dj ? 0.5 : 1.0) * (dk ? 0.5 : 1.0);
+                        const T w = T((di ? 0.5 : 1.0) * (dj ? 0.5 : 1.0) * (dk ? 0.5 : 1.0));
                         acc = fma(w, rf[node_id(fi, fj, fk, nf1) * S + e], acc);
                     }
         }
@@ -68,9 +68,9 @@ __global__ void mg_restrict_kernel(const int *active, int Nc, const double *__re
 
 // x_f += P x_c on the interior fine nodes (thread per fine node and member);
 // xfs != NULL: also the double-float split of the new x_f
-template <int S>
-__global__ void mg_prolong_kernel(const int *active, int Nc, const double *__restrict__ xc,
-                                  double *__restrict__ xf, float2 *__restrict__ xfs, int *split_bad) {
+template <int S, typename T = double>
+__global__ void mg_prolong_kernel(const int *active, int Nc, const T *__restrict__ xc, T *__restrict__ xf,
+                                  float2 *__restrict__ xfs, int *split_bad) {
     if (ld_cg(active) == 0) return;
     const int nc1 = Nc + 1, Nf = 2 * Nc, nf1 = Nf + 1;
     const int64_t total = (int64_t)nf1 * nf1 * nf1 * S;
@@ -80,7 +80,7 @@ __global__ void mg_prolong_kernel(const int *active, int Nc, const double *__res
         const int64_t I = t / S;
         const int i = (int)(I % nf1), j = (int)((I / nf1) % nf1), k = (int)(I / ((int64_t)nf1 * nf1));
         if (i <= 0 || i >= Nf || j <= 0 || j >= Nf || k <= 0 || k >= Nf) continue;
-        double acc = 0.0;
+        T acc = T(0);
         const int i0 = i >> 1, j0 = j >> 1, k0 = k >> 1;
         const int ni = (i & 1) ? 2 : 1, nj = (j & 1) ? 2 : 1, nk = (k & 1) ? 2 : 1;
         for (int a = 0; a < nk; ++a)
@@ -88,12 +88,12 @@ __global__ void mg_prolong_kernel(const int *active, int Nc, const double *__res
                 for (int c = 0; c < ni; ++c) {
                     const int ci = i0 + c, cj = j0 + bq, ck = k0 + a;
                     if (ci <= 0 || ci >= Nc || cj <= 0 || cj >= Nc || ck <= 0 || ck >= Nc) continue;
-                    const double w = ((i & 1) ? 0.5 : 1.0) * ((j & 1) ? 0.5 : 1.0) * ((k & 1) ? 0.5 : 1.0);
+                    const T w = T(((i & 1) ? 0.5 : 1.0) * ((j & 1) ? 0.5 : 1.0) * ((k & 1) ? 0.5 : 1.0));
                     acc = fma(w, xc[node_id(ci, cj, ck, nc1) * S + e], acc);
                 }
-        const double xn = xf[t] + acc;
+        const T xn = xf[t] + acc;
         xf[t] = xn;
-        if (xfs) store_split1(xfs, t, xn, split_bad);
+        if (xfs) store_split1(xfs, t, (double)xn, split_bad);
     }
 }
 
@@ -214,6 +214,96 @@ __global__ void __launch_bounds__(RowMap<S>::THREADS, 1024 / RowMap<S>::THREADS)
     }
 }
 
+// ------------------------------------------------------------ FP32 V-cycle
+// The same smoother and residual with FP32 values, vectors and arithmetic
+// (a mixed-precision preconditioner: the CG around it stays FP64).  TR is the
+// type of the right-hand side read (FP64 at the finest level, where it is the
+// CG residual).  x64: FP64 copy of the result (the finest level's output).
+template <int S, typename TR>
+__global__ void mg32_cheb_first_kernel(const int *active, int64_t n, const TR *__restrict__ res,
+                                       const float *__restrict__ dinv, const PcgState *__restrict__ ps,
+                                       float *__restrict__ z, float *__restrict__ d, float *__restrict__ x,
+                                       double *__restrict__ x64, int add) {
+    if (ld_cg(active) == 0) return;
+    const int64_t total = n * S;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const int e = (int)(t % S);
+        const float zv = __fmul_rn(__fmul_rn((float)res[t], dinv[t]), (float)ps->inv_theta[e]);
+        z[t] = zv;
+        d[t] = zv;
+        if (x) {
+            const float xv = add ? __fadd_rn(x[t], zv) : zv;
+            x[t] = xv;
+            if (x64) x64[t] = (double)xv;
+        }
+    }
+}
+
+template <int S, typename TR>
+__global__ void __launch_bounds__(RowMap<S>::THREADS, 1024 / RowMap<S>::THREADS)
+    mg32_cheb_step_kernel(const int *active, int32_t n, const int32_t *__restrict__ row_map,
+                          const int32_t *__restrict__ col, const float *__restrict__ vals, uint64_t val_bytes,
+                          const TR *__restrict__ res, const float *__restrict__ dinv,
+                          const PcgState *__restrict__ ps, int k, const float *__restrict__ zin,
+                          float *__restrict__ zout, float *__restrict__ d, float *__restrict__ x,
+                          double *__restrict__ x64, int add) {
+    if (ld_cg(active) == 0) return;
+    constexpr int G = RowMap<S>::G;
+    __shared__ ChunkCols cc;
+    const int r = threadIdx.x / G, g = threadIdx.x % G;
+    const int64_t R = (int64_t)blockIdx.x * 32 + r;
+    const bool staged = stage_chunk_pf(cc, row_map, col, blockIdx.x, n, vals, S * 4u, val_bytes, 0xffffffffu);
+    const float2 az = chunk_spmv_f32<S, float>(cc, staged, col, vals, nullptr, zin, r, g, R, R < n);
+    if (R >= n || (S == 1 && g != 0)) return;
+    const int w = (S == 1) ? 1 : 2;
+    const int64_t i0 = (S == 1) ? R : R * S + 2 * g;
+    for (int j = 0; j < w; ++j) {
+        const int64_t i = i0 + j;
+        const int e = (S == 1) ? 0 : 2 * g + j;
+        const float rk = (float)ps->rhoc[k][e], rk1 = (float)ps->rhoc[k - 1][e], c2 = (float)ps->c2[k][e];
+        const float wv = __fsub_rn((float)res[i], j == 0 ? az.x : az.y);
+        const float dv = __fmaf_rn(__fmul_rn(rk, rk1), d[i], __fmul_rn(c2, __fmul_rn(dinv[i], wv)));
+        const float zv = __fadd_rn(zin[i], dv);
+        d[i] = dv;
+        zout[i] = zv;
+        if (x) {
+            const float xv = add ? __fadd_rn(x[i], zv) : zv;
+            x[i] = xv;
+            if (x64) x64[i] = (double)xv;
+        }
+    }
+}
+
+template <int S, typename TR>
+__global__ void __launch_bounds__(RowMap<S>::THREADS, 1024 / RowMap<S>::THREADS)
+    mg32_residual_kernel(const int *active, int32_t n, const int32_t *__restrict__ row_map,
+                         const int32_t *__restrict__ col, const float *__restrict__ vals, uint64_t val_bytes,
+                         const TR *__restrict__ b, const float *__restrict__ x, float *__restrict__ r) {
+    if (ld_cg(active) == 0) return;
+    constexpr int G = RowMap<S>::G;
+    __shared__ ChunkCols cc;
+    const int rr = threadIdx.x / G, g = threadIdx.x % G;
+    const int64_t R = (int64_t)blockIdx.x * 32 + rr;
+    const bool staged = stage_chunk_pf(cc, row_map, col, blockIdx.x, n, vals, S * 4u, val_bytes, 0xffffffffu);
+    const float2 ax = chunk_spmv_f32<S, float>(cc, staged, col, vals, nullptr, x, rr, g, R, R < n);
+    if (R >= n) return;
+    if constexpr (S == 1) {
+        if (g == 0) r[R] = __fsub_rn((float)b[R], ax.x);
+    } else {
+        const int64_t i = R * S + 2 * g;
+        reinterpret_cast<float2 *>(r)[i >> 1] =
+            make_float2(__fsub_rn((float)b[i], ax.x), __fsub_rn((float)b[i + 1], ax.y));
+    }
+}
+
+// D^-1 in FP32 for the FP32 V-cycle
+static __global__ void mg32_to_f32_kernel(int64_t total, const double *__restrict__ v, float *__restrict__ out) {
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
+         t += (int64_t)gridDim.x * blockDim.x)
+        out[t] = __double2float_rn(v[t]);
+}
+
 // ------------------------------------------------------------ coarse level
 // Ainv_e = A_e^-1 by in-place Gauss-Jordan elimination in shared memory
 // (A_e SPD: no pivoting); one CTA per member.  The inverse is stored
@@ -262,19 +352,19 @@ __global__ void __launch_bounds__(512) mg_coarse_inverse_kernel(int32_t n, const
 }
 
 // x = Ainv_e b_e (one CTA per member; thread i reads column i of invT)
-template <int S>
+template <int S, typename T = double>
 __global__ void mg_coarse_solve_kernel(const int *active, int32_t n, const double *__restrict__ inv,
-                                       const double *__restrict__ b, double *__restrict__ x) {
+                                       const T *__restrict__ b, T *__restrict__ x) {
     if (ld_cg(active) == 0) return;
     const int e = blockIdx.x;
     __shared__ double bs[kMgMaxCoarse];
-    for (int i = threadIdx.x; i < n; i += blockDim.x) bs[i] = b[(int64_t)i * S + e];
+    for (int i = threadIdx.x; i < n; i += blockDim.x) bs[i] = (double)b[(int64_t)i * S + e];
     __syncthreads();
     const double *invT = inv + (int64_t)e * n * n;
     for (int i = threadIdx.x; i < n; i += blockDim.x) {
         double acc = 0.0;
         for (int j = 0; j < n; ++j) acc = fma(invT[(int64_t)j * n + i], bs[j], acc);
-        x[(int64_t)i * S + e] = acc;
+        x[(int64_t)i * S + e] = (T)acc;
     }
 }
 
@@ -291,6 +381,9 @@ struct MgLevel {
     double *b, *x, *r, *z[2], *d;
     float2 *xs, *zs[2];   // split copies of x, z0, z1 (MODE 3 levels)
     int *split_bad;       // shared by all levels
+    const float *v32;     // FP32 values (the FP32 V-cycle), or NULL
+    uint64_t v32_bytes;
+    float *b32, *x32, *r32, *z32[2], *d32, *dinv32;  // the FP32 V-cycle's vectors
 };
 
 // Scratch of the hierarchy from `base` (NULL: only count the bytes): per
@@ -318,6 +411,9 @@ static size_t mg_layout(int nl, const ens_mg_level *lv, int s, std::vector<MgLev
         float2 *sv[4] = {nullptr, nullptr, nullptr, nullptr};
         if (lv[l].values_df)
             for (int i = 0; i < 4; ++i) sv[i] = reinterpret_cast<float2 *>(take(vb));
+        float *fv[7] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+        if (lv[l].values_f32)
+            for (int i = 0; i < 7; ++i) fv[i] = reinterpret_cast<float *>(take(vb / 2));
         if (out && base) {
             MgLevel &m = (*out)[l];
             m.n = (int32_t)n;
@@ -339,6 +435,15 @@ static size_t mg_layout(int nl, const ens_mg_level *lv, int s, std::vector<MgLev
             m.xs = sv[0];
             m.zs[0] = sv[1];
             m.zs[1] = sv[2];
+            m.v32 = lv[l].values_f32;
+            m.v32_bytes = (uint64_t)lv[l].graph.num_entries * s * 4u;
+            m.b32 = fv[0];
+            m.x32 = fv[1];
+            m.r32 = fv[2];
+            m.z32[0] = fv[3];
+            m.z32[1] = fv[4];
+            m.d32 = fv[5];
+            m.dinv32 = fv[6];
             dot_tree_layout(&c.t1, n, s, t1);
             dot_tree_layout(&c.t2, n, 2 * s, t2);
             m.pa.ps = ps;
@@ -376,6 +481,7 @@ struct MgSolver {
     double *inv;
     const int *active;  // CG active-member count: every V-cycle kernel exits at entry once it is 0
     int degree;
+    bool f32 = false;   // the FP32 V-cycle (every level has FP32 values)
     unsigned eg;  // grid of the elementwise kernels
 
     static unsigned chunks(int64_t n) { return (unsigned)((n + 31) / 32); }
@@ -445,6 +551,63 @@ struct MgSolver {
         smooth(l, m.r, x, out_split ? xs : nullptr, 1, st);                         // x = S(b, x)
     }
 
+    // ---- the FP32 V-cycle (f32): res64 / b64 are read at the finest level
+    // (the CG residual), res32 / b32 below; x64 receives the finest level's
+    // result in FP64 (the CG's z)
+    void smooth32(int l, const double *res64, const float *res32, float *x, double *x64, int add,
+                  cudaStream_t st) {
+        MgLevel &m = lv[l];
+        const PcgState *ps = m.pa.ps;
+        if (res64)
+            mg32_cheb_first_kernel<S, double><<<eg, 256, 0, st>>>(active, m.n, res64, m.dinv32, ps, m.z32[0], m.d32,
+                                                                 degree == 1 ? x : nullptr,
+                                                                 degree == 1 ? x64 : nullptr, add);
+        else
+            mg32_cheb_first_kernel<S, float><<<eg, 256, 0, st>>>(active, m.n, res32, m.dinv32, ps, m.z32[0], m.d32,
+                                                                degree == 1 ? x : nullptr,
+                                                                degree == 1 ? x64 : nullptr, add);
+        for (int k = 1; k < degree; ++k) {
+            const bool last = (k == degree - 1);
+            float *xo = last ? x : nullptr;
+            double *x64o = last ? x64 : nullptr;
+            if (res64)
+                mg32_cheb_step_kernel<S, double><<<chunks(m.n), RowMap<S>::THREADS, 0, st>>>(
+                    active, m.n, m.row_map, m.col, m.v32, m.v32_bytes, res64, m.dinv32, ps, k, m.z32[(k - 1) & 1],
+                    m.z32[k & 1], m.d32, xo, x64o, add);
+            else
+                mg32_cheb_step_kernel<S, float><<<chunks(m.n), RowMap<S>::THREADS, 0, st>>>(
+                    active, m.n, m.row_map, m.col, m.v32, m.v32_bytes, res32, m.dinv32, ps, k, m.z32[(k - 1) & 1],
+                    m.z32[k & 1], m.d32, xo, x64o, add);
+        }
+    }
+
+    void residual32(int l, const double *b64, const float *b32, const float *x, cudaStream_t st) {
+        MgLevel &m = lv[l];
+        if (b64)
+            mg32_residual_kernel<S, double><<<chunks(m.n), RowMap<S>::THREADS, 0, st>>>(
+                active, m.n, m.row_map, m.col, m.v32, m.v32_bytes, b64, x, m.r32);
+        else
+            mg32_residual_kernel<S, float><<<chunks(m.n), RowMap<S>::THREADS, 0, st>>>(
+                active, m.n, m.row_map, m.col, m.v32, m.v32_bytes, b32, x, m.r32);
+    }
+
+    // x = V_l(b) in FP32 (b64 at l = 0, b32 below); x64: FP64 copy of the result
+    void vcycle32(int l, const double *b64, const float *b32, float *x, double *x64, cudaStream_t st) {
+        const int L = (int)lv.size() - 1;
+        if (l == L) {  // L >= 1: the coarsest level is never the finest
+            mg_coarse_solve_kernel<S, float><<<S, 128, 0, st>>>(active, lv[L].n, inv, b32, x);
+            return;
+        }
+        MgLevel &m = lv[l], &mc = lv[l + 1];
+        smooth32(l, b64, b32, x, nullptr, 0, st);                                  // x = S(b, 0)
+        residual32(l, b64, b32, x, st);
+        mg_restrict_kernel<S, float><<<eg, 256, 0, st>>>(active, mc.N, m.r32, mc.b32);
+        vcycle32(l + 1, nullptr, mc.b32, mc.x32, nullptr, st);
+        mg_prolong_kernel<S, float><<<eg, 256, 0, st>>>(active, mc.N, mc.x32, x, nullptr, m.split_bad);
+        residual32(l, b64, b32, x, st);
+        smooth32(l, nullptr, m.r32, x, x64, 1, st);                                // x = S(b, x)
+    }
+
     // Per level: D and D^-1, the power estimate of the largest eigenvalue of
     // D^-1 A from the caller's start vectors, the Chebyshev parameters; then
     // the inverse of the coarsest matrix (*bad = 1 if it is not positive
@@ -468,6 +631,7 @@ struct MgSolver {
             pc_diag_kernel<S><<<(unsigned)((nt + 255) / 256), 256, 0, st>>>(m.n, m.row_map, m.col, m.vals,
                                                                          const_cast<double *>(a.dg),
                                                                          const_cast<double *>(a.dinv));
+            if (f32) mg32_to_f32_kernel<<<152 * 4, 256, 0, st>>>(nt, a.dinv, m.dinv32);
             ENS_CUDA_TRY(cudaMemcpyAsync(a.v, levels[l].power_start, sizeof(double) * (size_t)nt,
                                          cudaMemcpyDeviceToDevice, st));
             if (m.vdf) {
@@ -518,6 +682,10 @@ static int mg_check(int nl, const ens_mg_level *lv, int s) {
         if (s > 1 && !aligned16(lv[l].values)) return fail(ENS_ERR_ALIGN, "ens_mg: level %d values not aligned", l);
         if (lv[l].values_df && !aligned16(lv[l].values_df))
             return fail(ENS_ERR_ALIGN, "ens_mg: level %d values_df not aligned", l);
+        if ((lv[l].values_f32 != nullptr) != (lv[0].values_f32 != nullptr))
+            return fail(ENS_ERR_ARG, "ens_mg: values_f32 on every level or none (level %d)", l);
+        if (lv[l].values_f32 && s > 1 && !aligned16(lv[l].values_f32))
+            return fail(ENS_ERR_ALIGN, "ens_mg: level %d values_f32 not aligned", l);
     }
     if (lv[nl - 1].graph.num_rows > kMgMaxCoarse)
         return fail(ENS_ERR_UNSUPPORTED, "ens_mg: coarsest level has %d rows (at most %d: N <= 4)",

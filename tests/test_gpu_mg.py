@@ -28,7 +28,7 @@ def start(l, e, n):
     return inputs.random_vector(600 + 100 * l + e, n)
 
 
-def gpu_mg(torch, mg, xs, tol=1e-10, flags=0, degree=2, ratio=5.0, check_every=4, presplit=False):
+def gpu_mg(torch, mg, xs, tol=1e-10, flags=0, degree=2, ratio=5.0, check_every=4, presplit=False, f32=False):
     """presplit: level 0 assembled in double-float with its pre-split copy, so
     that the level-0 SpMVs (K1 and the V-cycle's) run in double-float."""
     s = xs.shape[0]
@@ -40,9 +40,10 @@ def gpu_mg(torch, mg, xs, tol=1e-10, flags=0, degree=2, ratio=5.0, check_every=4
     starts = [to_dev(np.stack([start(l, e, m.n) for e in range(s)], axis=1).reshape(-1))
               for l, m in enumerate(mg.meshes)]
     x = torch.zeros(mg.meshes[0].n * s, dtype=torch.float64, device=gpu())
-    work = torch.empty(mg.workspace_size(s, vals, starts, vdf), dtype=torch.uint8, device=gpu())
+    v32 = mg.to_f32(s, vals) if f32 else None
+    work = torch.empty(mg.workspace_size(s, vals, starts, vdf, v32), dtype=torch.uint8, device=gpu())
     it, rr, st, stats = mg.solve(s, vals, b, x, tol, 200, work, starts, degree=degree, ratio=ratio, flags=flags,
-                                 check_every=check_every, values_df=vdf)
+                                 check_every=check_every, values_df=vdf, values_f32=v32)
     return to_np(x).reshape(-1, s), it, rr, st
 
 
@@ -118,3 +119,35 @@ def test_mg_64cubed_s32_sampled(torch):
         assert sto == 0 and abs(it[e] - ito) <= 1, (e, it[e], ito)
         err = np.linalg.norm(X[:, e] - xo) / np.linalg.norm(xo)
         assert err <= 1e-8 or it[e] != ito, (e, err)
+
+
+@pytest.mark.parametrize("s,presplit", [(1, False), (4, False), (32, False), (32, "all")])
+def test_mg_fp32_vcycle_matches_oracle(torch, s, presplit):
+    """The FP32 V-cycle (a mixed-precision preconditioner of the FP64 CG):
+    the same tolerance reached in at most one iteration more than the
+    oracle's FP64 MG-PCG, solutions to 1e-8."""
+    N, M = 16, 10
+    mg = E.Multigrid(N, M)
+    xs = inputs.kl_samples(850 + s, 0, s, M)
+    X, it, rr, st = gpu_mg(torch, mg, xs, presplit=presplit, f32=True)
+    assert st == [0] * s and max(rr) <= 1.01e-10
+    for e in ([0, s - 1] if s > 2 else range(s)):
+        starts = [start(l, e, (n + 1) ** 3) for l, n in enumerate(G.level_sizes(N))]
+        lv = G.hierarchy(N, M, xs[e], starts)
+        xo, ito, rro, sto = G.mg_pcg(lv, lv[0].load, tol=1e-10)
+        assert sto == 0 and ito - 1 <= it[e] <= ito + 1, (e, it[e], ito)
+        assert np.linalg.norm(X[:, e] - xo) <= 1e-8 * np.linalg.norm(xo), e
+
+
+def test_mg_fp32_vcycle_member_independent_of_s_and_graph(torch):
+    mg = E.Multigrid(8, 10)
+    xs = inputs.kl_samples(870, 0, 32, 10)
+    ref = None
+    for s in (1, 4, 32):
+        X, it, rr, st = gpu_mg(torch, mg, xs[:s], f32=True)
+        cur = (X[:, 0].copy(), it[0])
+        ref = cur if ref is None else ref
+        assert np.array_equal(cur[0], ref[0]) and cur[1] == ref[1], s
+    Xg, itg, _, _ = gpu_mg(torch, mg, xs[:8], flags=E.CG_GRAPH, f32=True)
+    Xd, itd, _, _ = gpu_mg(torch, mg, xs[:8], f32=True)
+    assert itg == itd and np.array_equal(Xg, Xd)
