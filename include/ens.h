@@ -301,10 +301,11 @@ typedef struct ens_mg_level {
     const float *values_df;     /* optional: values pre-split into float pairs (ens_assemble_df or
                                    ens_convert_values ENS_F64_DF); the level's SpMVs then run in
                                    double-float (FP64-class, as ens_cg_df); NULL: FP64 SpMVs */
-    const float *values_f32;    /* optional, on every level or none (ens_mg_pcg only): values
-                                   rounded to FP32 (ens_convert_values ENS_F32); the V-cycle then
-                                   runs in FP32 (values, vectors, arithmetic) as a mixed-precision
-                                   preconditioner of the FP64 CG; the set-up stays FP64 */
+    const float *values_f32;    /* optional, on every level or none: values rounded to FP32
+                                   (ens_convert_values ENS_F32); the V-cycle then runs in FP32
+                                   (values, vectors, arithmetic) as a mixed-precision
+                                   preconditioner of the FP64 CG or (flexible) GMRES; the
+                                   set-up stays FP64 */
 } ens_mg_level;
 int ens_mg_workspace_size(int nlevels, const ens_mg_level *levels, int s, size_t *bytes);
 int ens_mg_pcg(int nlevels, const ens_mg_level *levels, int s, const double *b, double *x, double tol,
@@ -489,8 +490,8 @@ int ens_guess(const int32_t *dims, const float *params, int64_t n, int32_t s, co
  * v is a constant velocity; all integrals are exact (2x2x2 Gauss would be).
  * Newton's method (Eq. 10) solves J(u_k) du = -F(u_k), u_{k+1} = u_k + du,
  * per member, with restarted GMRES (one of the Belos solvers of Sect. 3.4;
- * right-preconditioned, classical Gram-Schmidt applied twice, Givens
- * rotations) for the non-symmetric J.
+ * flexible right-preconditioned form, classical Gram-Schmidt applied twice,
+ * Givens rotations) for the non-symmetric J.
  * The paper's experiments take alpha = beta = 0; the velocity, the source and
  * the GMRES preconditioner (the V-cycle of the diffusion operator A, fixed for
  * all Newton steps) are this library's readings. */

@@ -498,7 +498,7 @@ class Nonlinear:
                                   values_df=_per_level(values_df, 1)[0])
         return [v], b
 
-    def _levels(self, values, power_starts, values_df=None):
+    def _levels(self, values, power_starts, values_df=None, values_f32=None):
         c = (MgLevelC * len(self.meshes))()
         for l, mesh in enumerate(self.meshes):
             _require_cuda(values[l])
@@ -510,6 +510,10 @@ class Nonlinear:
             if v is not None:
                 _require_cuda(v)
                 c[l].values_df = v.data_ptr()
+        if values_f32 is not None:
+            for l, v in enumerate(values_f32):
+                _require_cuda(v)
+                c[l].values_f32 = v.data_ptr()
         return c
 
     def params(self, alpha, beta, tol=1e-8, lin_tol=1e-10, max_newton=20, restart=30, max_lin=500, degree=2,
@@ -521,13 +525,14 @@ class Nonlinear:
         p.ratio, p.boost = ratio, boost
         return p
 
-    def workspace_size(self, s, values, power_starts, params, values_df=None):
+    def workspace_size(self, s, values, power_starts, params, values_df=None, values_f32=None):
         v = ctypes.c_size_t()
-        _check(lib().ens_newton_workspace_size(len(self.meshes), self._levels(values, power_starts, values_df), s,
+        _check(lib().ens_newton_workspace_size(len(self.meshes),
+                                               self._levels(values, power_starts, values_df, values_f32), s,
                                                ctypes.byref(params), ctypes.byref(v)))
         return v.value
 
-    def solve(self, s, values, b, u, work, power_starts, params, stream=None, values_df=None):
+    def solve(self, s, values, b, u, work, power_starts, params, stream=None, values_df=None, values_f32=None):
         """Newton from the given u (values_df: level 0's pre-split values for
         the preconditioner).  Returns (newton_iters[s], lin_iters[s],
         relres[s], status[s], CgStats).  Synchronises."""
@@ -537,9 +542,10 @@ class Nonlinear:
         rr = (ctypes.c_double * s)()
         stt = (ctypes.c_int32 * s)()
         stats = CgStats()
-        rc = lib().ens_newton(len(self.meshes), self._levels(values, power_starts, values_df), s, _ptr(self.C),
-                              _ptr(b), _ptr(u), ctypes.byref(params), _ptr(work), work.numel() * work.element_size(),
-                              ni, li, rr, stt, ctypes.byref(stats), _stream(stream))
+        rc = lib().ens_newton(len(self.meshes), self._levels(values, power_starts, values_df, values_f32), s,
+                              _ptr(self.C), _ptr(b), _ptr(u), ctypes.byref(params), _ptr(work),
+                              work.numel() * work.element_size(), ni, li, rr, stt, ctypes.byref(stats),
+                              _stream(stream))
         if rc not in (0, ERR_NOT_CONVERGED, ERR_BREAKDOWN):
             _check(rc)
         return list(ni), list(li), list(rr), list(stt), stats

@@ -22,10 +22,12 @@
 // in float-pair (double-float) arithmetic on the FP32 pipe.
 //
 // GMRES (Saad, Sect. 6.5 and 9.3.2) per member with classical Gram-Schmidt
-// applied twice (CGS2): every step is four row-parallel kernels after the
-// preconditioner (w = J z with the dots v_i.w; two orthogonalisation passes,
-// the second with ||w|| and the Givens update in its last CTA; the
-// normalisation).  All reductions use the chunk trees of the CG, so every
+// applied twice (CGS2), in the flexible right-preconditioned form (Saad,
+// Sect. 9.4.1: the preconditioned vectors z_j are kept, x += Z y, which equals
+// x += M^-1 V y for a fixed preconditioner and also admits the FP32 V-cycle):
+// every step is four row-parallel kernels after the preconditioner (w = J z
+// with the dots v_i.w; two orthogonalisation passes, the second with ||w||
+// and the Givens update in its last CTA; the normalisation).  All reductions use the chunk trees of the CG, so every
 // member's result is independent of the ensemble size.  Vectors, dots,
 // Gram-Schmidt and Givens arithmetic are FP64; the GMRES SpMV is FP64 or, with
 // a pre-split level 0, the pre-split double-float form on a split copy of J.
@@ -55,7 +57,6 @@ struct GmState {
     int active[32], conv[32], k[32], iters[32];
     int active_count;   // members iterating in the current cycle
     int pending_count;  // members not converged and under max_iter (need a restart)
-    int always;         // 1: the active word of V-cycles that must run after convergence
 };
 
 // ------------------------------------------------------------ mesh helpers
@@ -309,8 +310,8 @@ struct GmArgs {
     int *split_bad;      // MODE 3: a split copy met a value out of range (FP64 then)
     double *V;           // Krylov basis: restart + 1 blocks of n*S
     int64_t vs;          // n*S
-    double *z;           // preconditioned vector
-    double *t;           // sum_i y_i v_i at the end of a cycle
+    double *Z;           // flexible form: z_j = M^-1 v_j, restart blocks of n*S (with a preconditioner)
+    double *t;           // scratch n*S (the final true residual of ens_gmres)
     double *x;           // the solution
     const double *rhs;   // right-hand side = sign * rhs
     double sign;
@@ -369,7 +370,6 @@ __global__ void gm_start_kernel(GmArgs a) {
         if (e == 0) {
             gs->active_count = __popc(ball);
             gs->pending_count = gs->active_count;
-            gs->always = 1;
         }
     }
 }
@@ -525,26 +525,19 @@ __global__ void gm_solve_kernel(GmArgs a) {
     }
 }
 
-// t = sum_{i < k_e} y_i v_i; without a preconditioner x += t directly
+// x += sum_{i < k_e} y_i B_i with B the Krylov basis V (no preconditioner)
+// or the preconditioned vectors Z = M^-1 V of the flexible form
 template <int S>
-__global__ void gm_combine_kernel(GmArgs a, int add_to_x) {
+__global__ void gm_combine_kernel(GmArgs a, const double *__restrict__ B) {
     const GmState *gs = a.gs;
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < a.vs;
          t += (int64_t)gridDim.x * blockDim.x) {
         const int e = (int)(t % S);
         const int k = gs->k[e];
         double acc = 0.0;
-        for (int i = 0; i < k; ++i) acc = fma(gs->y[i][e], a.V[(int64_t)i * a.vs + t], acc);
-        if (add_to_x) a.x[t] += acc;
-        else a.t[t] = acc;
+        for (int i = 0; i < k; ++i) acc = fma(gs->y[i][e], B[(int64_t)i * a.vs + t], acc);
+        a.x[t] += acc;
     }
-}
-
-// x += z
-__global__ void gm_axpy_kernel(int64_t total, double *__restrict__ x, const double *__restrict__ z) {
-    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
-         t += (int64_t)gridDim.x * blockDim.x)
-        x[t] += z[t];
 }
 
 // out = sign * rhs - J x (row per thread pair, as the SpMV)
@@ -615,12 +608,13 @@ static void nl_m2_split(double beta, int N, float *hi, float *lo) {
 struct NlBufs {
     NlState *ns;
     GmState *gs;
-    double *V, *z, *t, *du, *J, *F;
+    double *V, *Z, *t, *du, *J, *F;
     float2 *Js;  // pre-split J (Newton with a pre-split level 0 of the preconditioner)
     char *tm, *tn;
 };
 
-// workspace: states, Krylov basis, z, t, trees; Newton adds du, J and F (and
+// workspace: states, Krylov basis V, preconditioned basis Z (with a
+// preconditioner), t, trees; Newton adds du, J and F (and
 // the split J when level 0 of the preconditioner is pre-split); with the
 // multigrid preconditioner the hierarchy follows (mg_layout)
 static size_t nl_layout(int nlevels, const ens_mg_level *lv, int s, int restart, bool newton, bool precond,
@@ -638,7 +632,7 @@ static size_t nl_layout(int nlevels, const ens_mg_level *lv, int s, int restart,
     o.ns = reinterpret_cast<NlState *>(take(sizeof(NlState)));
     o.gs = reinterpret_cast<GmState *>(take(sizeof(GmState)));
     o.V = reinterpret_cast<double *>(take(vb * (size_t)(restart + 1)));
-    o.z = reinterpret_cast<double *>(take(vb));
+    if (precond) o.Z = reinterpret_cast<double *>(take(vb * (size_t)restart));
     o.t = reinterpret_cast<double *>(take(vb));
     o.tm = take(dot_tree_bytes(n, (restart + 1) * s));
     o.tn = take(dot_tree_bytes(n, s));
@@ -646,7 +640,10 @@ static size_t nl_layout(int nlevels, const ens_mg_level *lv, int s, int restart,
         o.du = reinterpret_cast<double *>(take(vb));
         o.F = reinterpret_cast<double *>(take(vb));
         o.J = reinterpret_cast<double *>(take(sizeof(double) * (size_t)nnz * s));
-        if (precond && lv[0].values_df) o.Js = reinterpret_cast<float2 *>(take(sizeof(double) * (size_t)nnz * s));
+        // split J for the pre-split GMRES SpMV (it reads z's split copy, which
+        // the FP64-class V-cycle writes; the FP32 V-cycle does not)
+        if (precond && lv[0].values_df && !lv[0].values_f32)
+            o.Js = reinterpret_cast<float2 *>(take(sizeof(double) * (size_t)nnz * s));
     }
     if (precond) off += mg_layout(nlevels, lv, s, mglv, base ? base + off : nullptr, inv, bad);
     if (base && b) *b = o;
@@ -674,7 +671,7 @@ struct NlSolver {
         a.col = lv[0].graph.col_entry;
         a.V = bufs->V;
         a.vs = (int64_t)a.n * S;
-        a.z = bufs->z;
+        a.Z = bufs->Z;
         a.t = bufs->t;
         a.gs = bufs->gs;
         a.ns = bufs->ns;
@@ -689,6 +686,7 @@ struct NlSolver {
         if ((rc = dot_tree_clear(a.tn, st))) return rc;
         if (pc) {
             mg.degree = degree;
+            mg.f32 = lv[0].values_f32 != nullptr;  // the FP32 V-cycle (flexible GMRES admits it)
             mg.eg = 152 * 4;
             mg.active = &bufs->gs->active_count;
             mg_bad = bad;
@@ -719,11 +717,13 @@ struct NlSolver {
             while (j < a.restart) {
                 for (int q = 0; q < check_every && j < a.restart; ++q, ++j) {
                     const double *zin = a.V + (int64_t)j * a.vs;
-                    if (precond) {
+                    if (precond) {  // flexible form: z_j = M^-1 v_j kept in Z[j]
+                        double *zj = a.Z + (int64_t)j * a.vs;
                         mg.active = &a.gs->active_count;
-                        mg.vcycle(0, zin, a.z, st, pre);  // pre: z's split copy into level 0's xs
+                        if (mg.f32) mg.vcycle32(0, zin, nullptr, mg.lv[0].x32, zj, st);
+                        else mg.vcycle(0, zin, zj, st, pre);  // pre: z's split copy into level 0's xs
                         launches += mg.launches_per_vcycle();
-                        zin = a.z;
+                        zin = zj;
                     }
                     DotTree tj = a.tm;
                     tj.width = (j + 1) * S;
@@ -741,16 +741,8 @@ struct NlSolver {
                 if (h[0] == 0) break;
             }
             gm_solve_kernel<S><<<1, 32, 0, st>>>(a);
-            if (precond) {
-                gm_combine_kernel<S><<<eg, 256, 0, st>>>(a, 0);
-                mg.active = &a.gs->always;
-                mg.vcycle(0, a.t, a.z, st);
-                gm_axpy_kernel<<<eg, 256, 0, st>>>(a.vs, a.x, a.z);
-                launches += 3 + mg.launches_per_vcycle();
-            } else {
-                gm_combine_kernel<S><<<eg, 256, 0, st>>>(a, 1);
-                launches += 2;
-            }
+            gm_combine_kernel<S><<<eg, 256, 0, st>>>(a, precond ? a.Z : a.V);
+            launches += 2;
             if (h[1] == 0) break;
             gm_residual_kernel<S><<<grid, T, 0, st>>>(a, a.V);
             gm_restart_kernel<S><<<grid, T, 0, st>>>(a);

@@ -133,7 +133,7 @@ def test_gmres_longest_restart_and_no_iterations(torch):
     assert it0 == [0] * s and st0 == [E.ERR_NOT_CONVERGED] * s and not torch.any(x != 0)
 
 
-def newton_case(torch, s, N, alpha, beta, precond=E.NL_PRECOND_MG, seed=960, presplit=False, **kw):
+def newton_case(torch, s, N, alpha, beta, precond=E.NL_PRECOND_MG, seed=960, presplit=False, f32=False, **kw):
     M = 10
     nl = E.Nonlinear(N, M, v=V, precond=precond)
     xs = inputs.kl_samples(seed, 0, s, M)
@@ -145,8 +145,9 @@ def newton_case(torch, s, N, alpha, beta, precond=E.NL_PRECOND_MG, seed=960, pre
     starts = dev_starts(nl, s) if precond == E.NL_PRECOND_MG else None
     p = nl.params(alpha, beta, **kw)
     u = torch.zeros(nl.mesh.n * s, dtype=torch.float64, device=gpu())
-    work = torch.empty(nl.workspace_size(s, vals, starts, p, vdf), dtype=torch.uint8, device=gpu())
-    ni, li, rr, st, stats = nl.solve(s, vals, b, u, work, starts, p, values_df=vdf)
+    v32 = nl.mg.to_f32(s, vals) if f32 else None
+    work = torch.empty(nl.workspace_size(s, vals, starts, p, vdf, v32), dtype=torch.uint8, device=gpu())
+    ni, li, rr, st, stats = nl.solve(s, vals, b, u, work, starts, p, values_df=vdf, values_f32=v32)
     return xs, to_np(u).reshape(-1, s), ni, li, rr, st
 
 
@@ -249,3 +250,21 @@ def test_gmres_zero_rhs_member_and_newton_step_limit(torch):
     xs2, U, ni, li, rr2, st2 = newton_case(torch, 4, 8, 1.0, 10.0, precond=E.NL_PRECOND_NONE, tol=1e-14,
                                            lin_tol=1e-3, max_newton=1, restart=30)
     assert ni == [1] * 4 and st2 == [E.ERR_NOT_CONVERGED] * 4 and min(rr2) > 1e-14
+
+
+@pytest.mark.parametrize("s,presplit", [(4, False), (32, "all")])
+def test_newton_fp32_vcycle_matches_oracle(torch, s, presplit):
+    """Newton with the FP32 V-cycle inside the flexible GMRES: the same Newton
+    steps as the oracle (FP64 V-cycle), GMRES steps within one per Newton step
+    more or less, solutions to 1e-8."""
+    N, alpha, beta, tol, lin_tol = 8, 1.0, 10.0, 1e-10, 1e-11
+    xs, U, ni, li, rr, st = newton_case(torch, s, N, alpha, beta, tol=tol, lin_tol=lin_tol, presplit=presplit,
+                                        f32=True)
+    assert st == [0] * s and max(rr) <= tol
+    for e in ([0, s - 1] if s > 2 else range(s)):
+        prob = NL.Problem(N, 10, xs[e], alpha, beta, v=V)
+        lv = G.hierarchy(N, 10, xs[e], [start(l, e, (n + 1) ** 3) for l, n in enumerate(G.level_sizes(N))])
+        uo, ko, lino, hist, sto = NL.newton(prob, tol=tol, lin_tol=lin_tol, precond=lambda r, lv=lv: G.vcycle(lv, r))
+        assert sto == 0 and ni[e] == ko, (e, ni[e], ko)
+        assert abs(li[e] - sum(lino)) <= ko, (e, li[e], lino)
+        assert np.linalg.norm(U[:, e] - uo) <= 1e-8 * np.linalg.norm(uo), e
