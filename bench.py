@@ -1041,6 +1041,7 @@ def main_mg(args):
                 # mg: K1 and every level's V-cycle SpMVs from pre-split values;
                 # mg_fp32_vcycle: K1 pre-split, the V-cycle in FP32
                 pre = vdfs if form == "mg" else ([vdf] if form == "mg_fp32_vcycle" else None)
+                # (mg_fp32_vcycle: K1 pre-split; the V-cycle and its eigenvalue bound in FP32)
                 vals, b = mg.assemble(s, xi, df=True, values_df=pre)
                 v32 = mg.to_f32(s, vals, out=v32s) if form == "mg_fp32_vcycle" else None
                 it, rr, st, _ = mg.solve(s, vals, b, x, TOL, 500, wmg, starts, flags=E.CG_GRAPH | E.CG_X0_ZERO,

@@ -411,9 +411,9 @@ static size_t mg_layout(int nl, const ens_mg_level *lv, int s, std::vector<MgLev
         float2 *sv[4] = {nullptr, nullptr, nullptr, nullptr};
         if (lv[l].values_df)
             for (int i = 0; i < 4; ++i) sv[i] = reinterpret_cast<float2 *>(take(vb));
-        float *fv[7] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+        float *fv[8] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
         if (lv[l].values_f32)
-            for (int i = 0; i < 7; ++i) fv[i] = reinterpret_cast<float *>(take(vb / 2));
+            for (int i = 0; i < 8; ++i) fv[i] = reinterpret_cast<float *>(take(vb / 2));
         if (out && base) {
             MgLevel &m = (*out)[l];
             m.n = (int32_t)n;
@@ -444,6 +444,9 @@ static size_t mg_layout(int nl, const ens_mg_level *lv, int s, std::vector<MgLev
             m.z32[1] = fv[4];
             m.d32 = fv[5];
             m.dinv32 = fv[6];
+            m.pa.vals32 = m.v32;
+            m.pa.v32 = fv[7];
+            m.pa.vals32_bytes = m.v32_bytes;
             dot_tree_layout(&c.t1, n, s, t1);
             dot_tree_layout(&c.t2, n, 2 * s, t2);
             m.pa.ps = ps;
@@ -634,7 +637,15 @@ struct MgSolver {
             if (f32) mg32_to_f32_kernel<<<152 * 4, 256, 0, st>>>(nt, a.dinv, m.dinv32);
             ENS_CUDA_TRY(cudaMemcpyAsync(a.v, levels[l].power_start, sizeof(double) * (size_t)nt,
                                          cudaMemcpyDeviceToDevice, st));
-            if (m.vdf) {
+            if (f32) {  // the FP32 V-cycle's bound: power iteration on its FP32 values
+                mg32_to_f32_kernel<<<152 * 4, 256, 0, st>>>(nt, a.v, a.v32);
+                for (int k = 0; k < power_iters; ++k) {
+                    pc_power_kernel<S, 4><<<chunks(m.n), RowMap<S>::THREADS, 0, st>>>(a);
+                    pc_scale_kernel<S, 4><<<152 * 4, 256, 0, st>>>(a);
+                }
+                pc_rayleigh_kernel<S, 4><<<chunks(m.n), RowMap<S>::THREADS, 0, st>>>(a);
+                *launches += 3 + 2 * power_iters;
+            } else if (m.vdf) {
                 pc_split_kernel<S><<<152 * 4, 256, 0, st>>>(a);
                 for (int k = 0; k < power_iters; ++k) {
                     pc_power_kernel<S, 3><<<chunks(m.n), RowMap<S>::THREADS, 0, st>>>(a);

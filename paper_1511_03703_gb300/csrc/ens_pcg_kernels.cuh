@@ -4,6 +4,7 @@
 // the epilogue of the preconditioner stage.
 #pragma once
 #include "ens_cg_kernels.cuh"
+#include "ens_spmv_f32.cuh"
 
 namespace ens {
 
@@ -32,14 +33,25 @@ struct PcgArgs {
     int degree;               // 0: Jacobi, >= 1: Chebyshev steps
     double boost, ratio;
     int *split_bad;           // MODE 3 set-up kernels: a split copy met a value out of range
+    const float *vals32;      // MODE 4 set-up kernels: FP32 values (the FP32 V-cycle's)
+    float *v32;               // MODE 4: FP32 copy of v
+    uint64_t vals32_bytes;
 };
 
 // the set-up SpMV of v: MODE 0 FP64; MODE 3 double-float from the pre-split
-// values c.vdf and the split copy c.pdf of v (FP64 once *split_bad is set)
+// values c.vdf and the split copy c.pdf of v (FP64 once *split_bad is set);
+// MODE 4 FP32 from the FP32 values and the FP32 copy of v (the eigenvalue
+// bound of an FP32 V-cycle)
 template <int S, int MODE>
 __device__ __forceinline__ double2 pc_setup_spmv(const PcgArgs &a, ChunkCols &cc, int r, int g, bool valid) {
     const CgArgs &c = a.c;
-    if constexpr (MODE == 3) {
+    if constexpr (MODE == 4) {
+        const bool staged = stage_chunk_pf(cc, c.row_map, c.col, blockIdx.x, c.n, a.vals32, S * 4u, a.vals32_bytes,
+                                           0xffffffffu);
+        const int64_t R = (int64_t)blockIdx.x * 32 + r;
+        const float2 y = chunk_spmv_f32<S, float>(cc, staged, c.col, a.vals32, nullptr, a.v32, r, g, R, valid);
+        return make_double2((double)y.x, (double)y.y);
+    } else if constexpr (MODE == 3) {
         const bool staged = stage_chunk_pf(cc, c.row_map, c.col, blockIdx.x, c.n, c.vdf, S * 8u, c.val_bytes,
                                            0xffffffffu);
         if (ld_cg(a.split_bad) == 0) return chunk_spmv_dfv<S>(cc, staged, c.col, c.vdf, c.vals, c.pdf, r, g, valid);
@@ -110,6 +122,7 @@ __global__ void pc_scale_kernel(PcgArgs a) {
         const double vv = a.y[t] * a.ps->inv_nrm[t % S];
         a.v[t] = vv;
         if (MODE == 3) store_split1(a.c.pdf, t, vv, a.split_bad);
+        if (MODE == 4) a.v32[t] = __double2float_rn(vv);
     }
 }
 
