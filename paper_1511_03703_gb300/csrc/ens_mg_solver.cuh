@@ -615,59 +615,94 @@ struct MgSolver {
     // D^-1 A from the caller's start vectors, the Chebyshev parameters; then
     // the inverse of the coarsest matrix (*bad = 1 if it is not positive
     // definite; the caller reads it).  All asynchronous on st.
+    // the set-up of level l on stream st (diagonal, eigenvalue bound, Chebyshev parameters)
+    int setup_level(int l, const ens_mg_level *levels, double ratio, double boost, int power_iters,
+                    cudaStream_t st, int *launches) {
+        MgLevel &m = lv[l];
+        PcgArgs &a = m.pa;
+        int rc;
+        a.degree = degree;
+        a.boost = boost;
+        a.ratio = ratio;
+        if ((rc = dot_tree_clear(a.c.t1, st))) return rc;
+        if ((rc = dot_tree_clear(a.c.t2, st))) return rc;
+        ENS_CUDA_TRY(cudaMemsetAsync(a.ps, 0, sizeof(PcgState), st));
+        const int64_t nt = (int64_t)m.n * S;
+        pc_diag_kernel<S><<<(unsigned)((nt + 255) / 256), 256, 0, st>>>(m.n, m.row_map, m.col, m.vals,
+                                                                     const_cast<double *>(a.dg),
+                                                                     const_cast<double *>(a.dinv));
+        if (f32) mg32_to_f32_kernel<<<152 * 4, 256, 0, st>>>(nt, a.dinv, m.dinv32);
+        ENS_CUDA_TRY(cudaMemcpyAsync(a.v, levels[l].power_start, sizeof(double) * (size_t)nt,
+                                     cudaMemcpyDeviceToDevice, st));
+        if (f32) {  // the FP32 V-cycle's bound: power iteration on its FP32 values
+            mg32_to_f32_kernel<<<152 * 4, 256, 0, st>>>(nt, a.v, a.v32);
+            for (int k = 0; k < power_iters; ++k) {
+                pc_power_kernel<S, 4><<<chunks(m.n), RowMap<S>::THREADS, 0, st>>>(a);
+                pc_scale_kernel<S, 4><<<152 * 4, 256, 0, st>>>(a);
+            }
+            pc_rayleigh_kernel<S, 4><<<chunks(m.n), RowMap<S>::THREADS, 0, st>>>(a);
+            *launches += 4 + 2 * power_iters;
+        } else if (m.vdf) {
+            pc_split_kernel<S><<<152 * 4, 256, 0, st>>>(a);
+            for (int k = 0; k < power_iters; ++k) {
+                pc_power_kernel<S, 3><<<chunks(m.n), RowMap<S>::THREADS, 0, st>>>(a);
+                pc_scale_kernel<S, 3><<<152 * 4, 256, 0, st>>>(a);
+            }
+            pc_rayleigh_kernel<S, 3><<<chunks(m.n), RowMap<S>::THREADS, 0, st>>>(a);
+            *launches += 3 + 2 * power_iters;
+        } else {
+            for (int k = 0; k < power_iters; ++k) {
+                pc_power_kernel<S><<<chunks(m.n), RowMap<S>::THREADS, 0, st>>>(a);
+                pc_scale_kernel<S><<<152 * 4, 256, 0, st>>>(a);
+            }
+            pc_rayleigh_kernel<S><<<chunks(m.n), RowMap<S>::THREADS, 0, st>>>(a);
+            *launches += 2 + 2 * power_iters;
+        }
+        return ENS_OK;
+    }
+
+    // Per level: D and D^-1, the power estimate of the largest eigenvalue of
+    // D^-1 A from the caller's start vectors, the Chebyshev parameters; then
+    // the inverse of the coarsest matrix (*bad = 1 if it is not positive
+    // definite; the caller reads it).  Level 0 runs on st; the coarser levels
+    // (short, latency-bound launches) and the coarsest inverse (one CTA per
+    // member) on two forked streams that st then waits for.  Asynchronous.
     int setup(const ens_mg_level *levels, double ratio, double boost, int power_iters, int *bad,
               cudaStream_t st, int *launches) {
         const int nl = (int)lv.size();
-        int rc;
+        int rc = ENS_OK;
         ENS_CUDA_TRY(cudaMemsetAsync(bad, 0, sizeof(int), st));
         ENS_CUDA_TRY(cudaMemsetAsync(lv[0].split_bad, 0, sizeof(int), st));
-        for (int l = 0; l < nl; ++l) {
-            MgLevel &m = lv[l];
-            PcgArgs &a = m.pa;
-            a.degree = degree;
-            a.boost = boost;
-            a.ratio = ratio;
-            if ((rc = dot_tree_clear(a.c.t1, st))) return rc;
-            if ((rc = dot_tree_clear(a.c.t2, st))) return rc;
-            ENS_CUDA_TRY(cudaMemsetAsync(a.ps, 0, sizeof(PcgState), st));
-            const int64_t nt = (int64_t)m.n * S;
-            pc_diag_kernel<S><<<(unsigned)((nt + 255) / 256), 256, 0, st>>>(m.n, m.row_map, m.col, m.vals,
-                                                                         const_cast<double *>(a.dg),
-                                                                         const_cast<double *>(a.dinv));
-            if (f32) mg32_to_f32_kernel<<<152 * 4, 256, 0, st>>>(nt, a.dinv, m.dinv32);
-            ENS_CUDA_TRY(cudaMemcpyAsync(a.v, levels[l].power_start, sizeof(double) * (size_t)nt,
-                                         cudaMemcpyDeviceToDevice, st));
-            if (f32) {  // the FP32 V-cycle's bound: power iteration on its FP32 values
-                mg32_to_f32_kernel<<<152 * 4, 256, 0, st>>>(nt, a.v, a.v32);
-                for (int k = 0; k < power_iters; ++k) {
-                    pc_power_kernel<S, 4><<<chunks(m.n), RowMap<S>::THREADS, 0, st>>>(a);
-                    pc_scale_kernel<S, 4><<<152 * 4, 256, 0, st>>>(a);
-                }
-                pc_rayleigh_kernel<S, 4><<<chunks(m.n), RowMap<S>::THREADS, 0, st>>>(a);
-                *launches += 3 + 2 * power_iters;
-            } else if (m.vdf) {
-                pc_split_kernel<S><<<152 * 4, 256, 0, st>>>(a);
-                for (int k = 0; k < power_iters; ++k) {
-                    pc_power_kernel<S, 3><<<chunks(m.n), RowMap<S>::THREADS, 0, st>>>(a);
-                    pc_scale_kernel<S, 3><<<152 * 4, 256, 0, st>>>(a);
-                }
-                pc_rayleigh_kernel<S, 3><<<chunks(m.n), RowMap<S>::THREADS, 0, st>>>(a);
-                *launches += 3 + 2 * power_iters;
-            } else {
-                for (int k = 0; k < power_iters; ++k) {
-                    pc_power_kernel<S><<<chunks(m.n), RowMap<S>::THREADS, 0, st>>>(a);
-                    pc_scale_kernel<S><<<152 * 4, 256, 0, st>>>(a);
-                }
-                pc_rayleigh_kernel<S><<<chunks(m.n), RowMap<S>::THREADS, 0, st>>>(a);
-                *launches += 2 + 2 * power_iters;
-            }
-        }
         MgLevel &mc = lv[nl - 1];
         const size_t smem = sizeof(double) * (size_t)mc.n * mc.n;
         ENS_CUDA_TRY(cudaFuncSetAttribute(mg_coarse_inverse_kernel<S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                           (int)smem));
-        mg_coarse_inverse_kernel<S><<<S, 512, smem, st>>>(mc.n, mc.row_map, mc.col, mc.vals, inv, bad);
-        ++*launches;
+        cudaStream_t side[2] = {nullptr, nullptr};
+        cudaEvent_t fork = nullptr, join[2] = {nullptr, nullptr};
+        cudaError_t ce = cudaEventCreateWithFlags(&fork, cudaEventDisableTiming);
+        for (int i = 0; i < 2 && ce == cudaSuccess; ++i) {
+            ce = cudaStreamCreateWithFlags(&side[i], cudaStreamNonBlocking);
+            if (ce == cudaSuccess) ce = cudaEventCreateWithFlags(&join[i], cudaEventDisableTiming);
+        }
+        if (ce == cudaSuccess) ce = cudaEventRecord(fork, st);
+        for (int i = 0; i < 2 && ce == cudaSuccess; ++i) ce = cudaStreamWaitEvent(side[i], fork, 0);
+        if (ce == cudaSuccess) {
+            for (int l = 0; l < nl && rc == ENS_OK; ++l)
+                rc = setup_level(l, levels, ratio, boost, power_iters, l == 0 ? st : side[0], launches);
+            mg_coarse_inverse_kernel<S><<<S, 512, smem, side[1]>>>(mc.n, mc.row_map, mc.col, mc.vals, inv, bad);
+            ++*launches;
+            for (int i = 0; i < 2 && ce == cudaSuccess; ++i) {
+                ce = cudaEventRecord(join[i], side[i]);
+                if (ce == cudaSuccess) ce = cudaStreamWaitEvent(st, join[i], 0);
+            }
+        }
+        for (int i = 0; i < 2; ++i) {
+            if (side[i]) cudaStreamDestroy(side[i]);  // released once their work is done
+            if (join[i]) cudaEventDestroy(join[i]);
+        }
+        if (fork) cudaEventDestroy(fork);
+        if (ce != cudaSuccess) return cuda_fail(ce, "ens_mg set-up streams");
+        if (rc) return rc;
         ENS_LAUNCH_CHECK("ens_mg set-up");
         return ENS_OK;
     }
