@@ -62,16 +62,10 @@ __global__ void convert_values_kernel(int32_t n, int s, const int32_t *__restric
     if (diag) diag[I * s + e] = __double2float_rn(rowsum - offsum);
 }
 
-// float chunk tree: 32-row halving tree, members packed (same pairing as warp_tree32)
+// float chunk tree: 32-row halving tree, members packed (same pairing as
+// warp_tree32); sm[r][e] holds row r's value of member e on entry
 template <int S>
-__device__ __forceinline__ void chunk_tree_f(float (*sm)[S + 1], float v0, float v1, int r, int g,
-                                             const DotTreeT<float> &t, int64_t chunk) {
-    if constexpr (S == 1) {
-        if (g == 0) sm[r][0] = v0;
-    } else {
-        sm[r][2 * g] = v0;
-        sm[r][2 * g + 1] = v1;
-    }
+__device__ __forceinline__ void chunk_tree_f_sum(float (*sm)[S + 1], const DotTreeT<float> &t, int64_t chunk) {
     __syncthreads();
 #pragma unroll
     for (int h = 16; h >= 1; h >>= 1) {
@@ -83,6 +77,29 @@ __device__ __forceinline__ void chunk_tree_f(float (*sm)[S + 1], float v0, float
     }
     for (int e = threadIdx.x; e < S; e += blockDim.x) t.buf[1][chunk * t.width + e] = sm[0][e];
     __syncthreads();
+}
+
+template <int S>
+__device__ __forceinline__ void chunk_tree_f(float (*sm)[S + 1], float v0, float v1, int r, int g,
+                                             const DotTreeT<float> &t, int64_t chunk) {
+    if constexpr (S == 1) {
+        if (g == 0) sm[r][0] = v0;
+    } else {
+        sm[r][2 * g] = v0;
+        sm[r][2 * g + 1] = v1;
+    }
+    chunk_tree_f_sum<S>(sm, t, chunk);
+}
+
+// the same tree with 4 members per thread (members 4g .. 4g+3 of row r)
+template <int S>
+__device__ __forceinline__ void chunk_tree_f4(float (*sm)[S + 1], const float4 v, int r, int g,
+                                              const DotTreeT<float> &t, int64_t chunk) {
+    sm[r][4 * g] = v.x;
+    sm[r][4 * g + 1] = v.y;
+    sm[r][4 * g + 2] = v.z;
+    sm[r][4 * g + 3] = v.w;
+    chunk_tree_f_sum<S>(sm, t, chunk);
 }
 
 // ------------------------------------------------------------ state
@@ -233,16 +250,47 @@ __global__ void __launch_bounds__(RowMap<S>::THREADS) mx_inner_init_kernel(MxArg
 }
 
 // ------------------------------------------------------------------ MI1
+// alpha = rho / (p.q) per member, after the chunk trees of p.q (warp 0 of the
+// CTA that finishes the tree)
+template <int S>
+__device__ __forceinline__ void mx_inner_alpha(MxArgs &a) {
+    if (!dot_tree_propagate(a.t32, blockIdx.x, 1)) return;
+    if (threadIdx.x >= 32) return;
+    MxState *st = a.st;
+    const unsigned FULL = 0xffffffffu;
+    const int e = threadIdx.x;
+    int act = 0;
+    if (e < S) {
+        act = st->active_in[e];
+        const float pi = ld_cg(a.t32.buf[a.t32.levels] + e);
+        if (act) {
+            if (!(pi > 0.f) || !isfinite(pi)) { act = 0; st->inner_break[e] += 1; }
+            else st->alpha[e] = st->rho[e] / pi;
+        }
+        st->active_in[e] = act;
+        st->updd[e] = 0;
+    }
+    const int ac = __popc(__ballot_sync(FULL, act));
+    if (e == 0) { st->active_in_count = ac; st->updd_any = 0; st->spmv_real += 1; }
+    __threadfence();
+}
+
+// an inner solve that has finished leaves the remaining launches of its
+// block with nothing to do (clears the update flags once)
+__device__ __forceinline__ bool mx_inner_idle(MxArgs &a, int S) {
+    MxState *st = a.st;
+    if (ld_cg(&st->active_in_count) != 0) return false;
+    if (blockIdx.x == 0 && threadIdx.x == 0 && st->updd_any) {
+        for (int e = 0; e < S; ++e) st->updd[e] = 0;
+        st->updd_any = 0;
+    }
+    return true;
+}
+
+// q = A_lo p and p.q; 2 members per thread (s <= 4)
 template <int S, typename V>
 __global__ void __launch_bounds__(RowMap<S>::THREADS, 1536 / RowMap<S>::THREADS) mx_inner_spmv_kernel(MxArgs a) {
-    MxState *st = a.st;
-    if (ld_cg(&st->active_in_count) == 0) {
-        if (blockIdx.x == 0 && threadIdx.x == 0 && st->updd_any) {
-            for (int e = 0; e < S; ++e) st->updd[e] = 0;
-            st->updd_any = 0;
-        }
-        return;
-    }
+    if (mx_inner_idle(a, S)) return;
     constexpr int G = RowMap<S>::G;
     __shared__ ChunkCols cc;
     __shared__ float sm[32][S + 1];
@@ -266,24 +314,36 @@ __global__ void __launch_bounds__(RowMap<S>::THREADS, 1536 / RowMap<S>::THREADS)
         }
     }
     chunk_tree_f<S>(sm, v0, v1, r, g, a.t32, blockIdx.x);
-    if (!dot_tree_propagate(a.t32, blockIdx.x, 1)) return;
-    if (threadIdx.x >= 32) return;
-    const unsigned FULL = 0xffffffffu;
-    const int e = threadIdx.x;
-    int act = 0;
-    if (e < S) {
-        act = st->active_in[e];
-        const float pi = ld_cg(a.t32.buf[a.t32.levels] + e);
-        if (act) {
-            if (!(pi > 0.f) || !isfinite(pi)) { act = 0; st->inner_break[e] += 1; }
-            else st->alpha[e] = st->rho[e] / pi;
-        }
-        st->active_in[e] = act;
-        st->updd[e] = 0;
+    mx_inner_alpha<S>(a);
+}
+
+// the same with 4 members per thread (s >= 8): 16-byte value and p loads;
+// every member's sums are bitwise those of the 2-member form
+template <int S>
+struct RowMap4 {
+    static constexpr int G = S / 4;
+    static constexpr int THREADS = 32 * G;
+};
+template <int S, typename V>
+__global__ void __launch_bounds__(RowMap4<S>::THREADS, 1280 / RowMap4<S>::THREADS) mx_inner_spmv4_kernel(MxArgs a) {
+    if (mx_inner_idle(a, S)) return;
+    constexpr int G = RowMap4<S>::G;
+    __shared__ ChunkCols cc;
+    __shared__ float sm[32][S + 1];
+    const int r = threadIdx.x / G, g = threadIdx.x % G;
+    const int64_t R = (int64_t)blockIdx.x * 32 + r;
+    const bool staged = stage_chunk_pf(cc, a.row_map, a.col, blockIdx.x, a.n, a.vlo, S * (uint32_t)sizeof(V),
+                                       a.vlo_bytes, 0xffffffffu);
+    const float4 ap = chunk_spmv4_f32<S, V>(cc, staged, a.col, static_cast<const V *>(a.vlo), a.diag,
+                                            a.pf, r, g, R, R < a.n);
+    float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (R < a.n) {
+        reinterpret_cast<float4 *>(a.qf)[R * G + g] = ap;
+        const float4 pv = reinterpret_cast<const float4 *>(a.pf)[R * G + g];
+        v = make_float4(ap.x * pv.x, ap.y * pv.y, ap.z * pv.z, ap.w * pv.w);
     }
-    const int ac = __popc(__ballot_sync(FULL, act));
-    if (e == 0) { st->active_in_count = ac; st->updd_any = 0; st->spmv_real += 1; }
-    __threadfence();
+    chunk_tree_f4<S>(sm, v, r, g, a.t32, blockIdx.x);
+    mx_inner_alpha<S>(a);
 }
 
 // ------------------------------------------------------------------ MI2
@@ -481,7 +541,8 @@ static int mx_run(const ens_graph *g, const double *v64, const void *vlo, const 
         for (int blk = 0; blk < max_blocks; ++blk) {
             for (int i = 0; i < check_every; ++i) {
                 if (timing) cudaEventRecord(ev[2 * i], st);
-                mx_inner_spmv_kernel<S, V><<<grid, RowMap<S>::THREADS, 0, st>>>(a);
+                if constexpr (S >= 8) mx_inner_spmv4_kernel<S, V><<<grid, RowMap4<S>::THREADS, 0, st>>>(a);
+                else mx_inner_spmv_kernel<S, V><<<grid, RowMap<S>::THREADS, 0, st>>>(a);
                 if (timing) cudaEventRecord(ev[2 * i + 1], st);
                 mx_inner_resid_kernel<S><<<grid, RowMap<S>::THREADS, 0, st>>>(a);
                 mx_inner_update_kernel<S><<<grid, RowMap<S>::THREADS, 0, st>>>(a);
