@@ -240,8 +240,28 @@ __global__ void mg32_cheb_first_kernel(const int *active, int64_t n, const TR *_
     }
 }
 
+// thread map of the FP32 V-cycle kernels: W members per thread (4 from s = 8,
+// with 16-byte loads; the per-member sums are those of the 2-member SpMV)
+template <int S>
+struct Map32 {
+    static constexpr int W = (S >= 8) ? 4 : (S == 1 ? 1 : 2);
+    static constexpr int G = (S == 1) ? 2 : S / W;
+    static constexpr int THREADS = 32 * G;
+};
+template <int S, typename V>
+__device__ __forceinline__ float4 mg32_spmv(const ChunkCols &cc, bool staged, const int32_t *__restrict__ col,
+                                            const V *__restrict__ vals, const float *__restrict__ x, int r,
+                                            int g, int64_t R, bool valid) {
+    if constexpr (Map32<S>::W == 4) {
+        return chunk_spmv4_f32<S, V>(cc, staged, col, vals, nullptr, x, r, g, R, valid);
+    } else {
+        const float2 t = chunk_spmv_f32<S, V>(cc, staged, col, vals, nullptr, x, r, g, R, valid);
+        return make_float4(t.x, t.y, 0.f, 0.f);
+    }
+}
+
 template <int S, typename TR>
-__global__ void __launch_bounds__(RowMap<S>::THREADS, 1024 / RowMap<S>::THREADS)
+__global__ void __launch_bounds__(Map32<S>::THREADS, 1024 / Map32<S>::THREADS)
     mg32_cheb_step_kernel(const int *active, int32_t n, const int32_t *__restrict__ row_map,
                           const int32_t *__restrict__ col, const float *__restrict__ vals, uint64_t val_bytes,
                           const TR *__restrict__ res, const float *__restrict__ dinv,
@@ -249,20 +269,21 @@ __global__ void __launch_bounds__(RowMap<S>::THREADS, 1024 / RowMap<S>::THREADS)
                           float *__restrict__ zout, float *__restrict__ d, float *__restrict__ x,
                           double *__restrict__ x64, int add) {
     if (ld_cg(active) == 0) return;
-    constexpr int G = RowMap<S>::G;
+    constexpr int G = Map32<S>::G, W = Map32<S>::W;
     __shared__ ChunkCols cc;
     const int r = threadIdx.x / G, g = threadIdx.x % G;
     const int64_t R = (int64_t)blockIdx.x * 32 + r;
     const bool staged = stage_chunk_pf(cc, row_map, col, blockIdx.x, n, vals, S * 4u, val_bytes, 0xffffffffu);
-    const float2 az = chunk_spmv_f32<S, float>(cc, staged, col, vals, nullptr, zin, r, g, R, R < n);
+    const float4 az4 = mg32_spmv<S, float>(cc, staged, col, vals, zin, r, g, R, R < n);
     if (R >= n || (S == 1 && g != 0)) return;
-    const int w = (S == 1) ? 1 : 2;
-    const int64_t i0 = (S == 1) ? R : R * S + 2 * g;
-    for (int j = 0; j < w; ++j) {
+    const float az[4] = {az4.x, az4.y, az4.z, az4.w};
+    const int64_t i0 = (S == 1) ? R : R * S + W * g;
+#pragma unroll
+    for (int j = 0; j < W; ++j) {
         const int64_t i = i0 + j;
-        const int e = (S == 1) ? 0 : 2 * g + j;
+        const int e = (S == 1) ? 0 : W * g + j;
         const float rk = (float)ps->rhoc[k][e], rk1 = (float)ps->rhoc[k - 1][e], c2 = (float)ps->c2[k][e];
-        const float wv = __fsub_rn((float)res[i], j == 0 ? az.x : az.y);
+        const float wv = __fsub_rn((float)res[i], az[j]);
         const float dv = __fmaf_rn(__fmul_rn(rk, rk1), d[i], __fmul_rn(c2, __fmul_rn(dinv[i], wv)));
         const float zv = __fadd_rn(zin[i], dv);
         d[i] = dv;
@@ -276,24 +297,29 @@ __global__ void __launch_bounds__(RowMap<S>::THREADS, 1024 / RowMap<S>::THREADS)
 }
 
 template <int S, typename TR>
-__global__ void __launch_bounds__(RowMap<S>::THREADS, 1024 / RowMap<S>::THREADS)
+__global__ void __launch_bounds__(Map32<S>::THREADS, 1024 / Map32<S>::THREADS)
     mg32_residual_kernel(const int *active, int32_t n, const int32_t *__restrict__ row_map,
                          const int32_t *__restrict__ col, const float *__restrict__ vals, uint64_t val_bytes,
                          const TR *__restrict__ b, const float *__restrict__ x, float *__restrict__ r) {
     if (ld_cg(active) == 0) return;
-    constexpr int G = RowMap<S>::G;
+    constexpr int G = Map32<S>::G, W = Map32<S>::W;
     __shared__ ChunkCols cc;
     const int rr = threadIdx.x / G, g = threadIdx.x % G;
     const int64_t R = (int64_t)blockIdx.x * 32 + rr;
     const bool staged = stage_chunk_pf(cc, row_map, col, blockIdx.x, n, vals, S * 4u, val_bytes, 0xffffffffu);
-    const float2 ax = chunk_spmv_f32<S, float>(cc, staged, col, vals, nullptr, x, rr, g, R, R < n);
+    const float4 ax = mg32_spmv<S, float>(cc, staged, col, vals, x, rr, g, R, R < n);
     if (R >= n) return;
     if constexpr (S == 1) {
         if (g == 0) r[R] = __fsub_rn((float)b[R], ax.x);
-    } else {
+    } else if constexpr (W == 2) {
         const int64_t i = R * S + 2 * g;
         reinterpret_cast<float2 *>(r)[i >> 1] =
             make_float2(__fsub_rn((float)b[i], ax.x), __fsub_rn((float)b[i + 1], ax.y));
+    } else {
+        const int64_t i = R * S + 4 * g;
+        reinterpret_cast<float4 *>(r)[i >> 2] =
+            make_float4(__fsub_rn((float)b[i], ax.x), __fsub_rn((float)b[i + 1], ax.y),
+                        __fsub_rn((float)b[i + 2], ax.z), __fsub_rn((float)b[i + 3], ax.w));
     }
 }
 
@@ -574,11 +600,11 @@ struct MgSolver {
             float *xo = last ? x : nullptr;
             double *x64o = last ? x64 : nullptr;
             if (res64)
-                mg32_cheb_step_kernel<S, double><<<chunks(m.n), RowMap<S>::THREADS, 0, st>>>(
+                mg32_cheb_step_kernel<S, double><<<chunks(m.n), Map32<S>::THREADS, 0, st>>>(
                     active, m.n, m.row_map, m.col, m.v32, m.v32_bytes, res64, m.dinv32, ps, k, m.z32[(k - 1) & 1],
                     m.z32[k & 1], m.d32, xo, x64o, add);
             else
-                mg32_cheb_step_kernel<S, float><<<chunks(m.n), RowMap<S>::THREADS, 0, st>>>(
+                mg32_cheb_step_kernel<S, float><<<chunks(m.n), Map32<S>::THREADS, 0, st>>>(
                     active, m.n, m.row_map, m.col, m.v32, m.v32_bytes, res32, m.dinv32, ps, k, m.z32[(k - 1) & 1],
                     m.z32[k & 1], m.d32, xo, x64o, add);
         }
@@ -587,10 +613,10 @@ struct MgSolver {
     void residual32(int l, const double *b64, const float *b32, const float *x, cudaStream_t st) {
         MgLevel &m = lv[l];
         if (b64)
-            mg32_residual_kernel<S, double><<<chunks(m.n), RowMap<S>::THREADS, 0, st>>>(
+            mg32_residual_kernel<S, double><<<chunks(m.n), Map32<S>::THREADS, 0, st>>>(
                 active, m.n, m.row_map, m.col, m.v32, m.v32_bytes, b64, x, m.r32);
         else
-            mg32_residual_kernel<S, float><<<chunks(m.n), RowMap<S>::THREADS, 0, st>>>(
+            mg32_residual_kernel<S, float><<<chunks(m.n), Map32<S>::THREADS, 0, st>>>(
                 active, m.n, m.row_map, m.col, m.v32, m.v32_bytes, b32, x, m.r32);
     }
 
