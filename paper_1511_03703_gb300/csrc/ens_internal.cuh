@@ -65,11 +65,6 @@ __device__ __forceinline__ uint32_t ld_stream_u32(const void *p) {
     asm volatile("ld.global.cs.u32 %0, [%1];" : "=r"(v) : "l"(p));
     return v;
 }
-__device__ __forceinline__ uint2 ld_stream_u2(const void *p) {
-    uint2 v;
-    asm volatile("ld.global.cs.v2.u32 {%0, %1}, [%2];" : "=r"(v.x), "=r"(v.y) : "l"(p));
-    return v;
-}
 __device__ __forceinline__ uint16_t ld_stream_u16(const void *p) {
     uint16_t v;
     asm volatile("ld.global.cs.u16 %0, [%1];" : "=h"(v) : "l"(p));

@@ -6,6 +6,13 @@
 
 namespace ens {
 
+// streaming 8-byte load (4 BF16 values) for data read exactly once
+__device__ __forceinline__ uint2 ld_stream_u2(const void *p) {
+    uint2 v;
+    asm volatile("ld.global.cs.v2.u32 {%0, %1}, [%2];" : "=r"(v.x), "=r"(v.y) : "l"(p));
+    return v;
+}
+
 // --------------------------------------------------- FP32 SpMV row evaluation
 template <typename V>
 struct ValLoad32;
