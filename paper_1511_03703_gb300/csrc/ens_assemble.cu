@@ -69,11 +69,63 @@ static __device__ __noinline__ double asm_value_fp64(const double *coef, int str
     return x;
 }
 
+// Two members' double-float terms at once with the packed FP32 instructions
+// of sm_100+ (add/sub/mul/fma .rn.f32x2: per lane IEEE round-to-nearest, so
+// each lane is bitwise the scalar df_term_pre).  The product is kept negated
+// (np = -(ah*xh), exact) so that every step is an add, sub, mul or fma:
+//   e  = ah*xh - p + ah*xl + al*xh     (fma(ah, xh, np), then two fmas)
+//   s  = S + p = S - np;  bb = s - S
+//   t  = (S - (s - bb)) + (p - bb) = (S - (s - bb)) - (np + bb)
+//   S' = s,  C' = C + (t + e)
+__device__ __forceinline__ uint64_t f2_pack(float lo, float hi) {
+    uint64_t r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+    return r;
+}
+__device__ __forceinline__ void f2_unpack(uint64_t v, float &lo, float &hi) {
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+}
+__device__ __forceinline__ uint64_t f2_add(uint64_t a, uint64_t b) {
+    uint64_t r;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ uint64_t f2_sub(uint64_t a, uint64_t b) {
+    uint64_t r;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ uint64_t f2_mul(uint64_t a, uint64_t b) {
+    uint64_t r;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ uint64_t f2_fma(uint64_t a, uint64_t b, uint64_t c) {
+    uint64_t r;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
+    return r;
+}
+// (S, C) += (ah + al) * (xh + xl) for two members; nah = -ah
+__device__ __forceinline__ void df_term_pair(uint64_t &S, uint64_t &C, uint64_t ah, uint64_t nah, uint64_t al,
+                                             uint64_t xh, uint64_t xl) {
+    const uint64_t np = f2_mul(nah, xh);
+    uint64_t e = f2_fma(ah, xh, np);
+    e = f2_fma(ah, xl, e);
+    e = f2_fma(al, xh, e);
+    const uint64_t s = f2_sub(S, np);
+    const uint64_t bb = f2_sub(s, S);
+    const uint64_t t = f2_sub(f2_sub(S, f2_sub(s, bb)), f2_add(np, bb));
+    S = s;
+    C = f2_add(C, f2_add(t, e));
+}
+
 template <int S>
 __global__ void __launch_bounds__(256) assemble_values_df_kernel(
     int64_t nnz, int M, const double *__restrict__ modes, const double *__restrict__ xi,
     double sigma, double kappa0, double *__restrict__ values, float2 *__restrict__ vdf) {
-    __shared__ float2 coef[kAsmMaxCoef];  // rounded split of coef[k*S + e], k >= 1
+    // rounded split of coef[k*S + e], k >= 1: (h, l) per member, or for s >= 2
+    // per member pair (h_2j, h_2j+1, l_2j, l_2j+1) at coef4[k*S/2 + j]
+    __shared__ __align__(16) float2 coef[kAsmMaxCoef];
     __shared__ double coef64[kAsmMaxCoef];
     __shared__ int coef_bad;
     if (threadIdx.x == 0) coef_bad = 0;
@@ -84,7 +136,13 @@ __global__ void __launch_bounds__(256) assemble_values_df_kernel(
         const float l = (float)(c - (double)h);
         const double a = fabs(c);
         if (i >= S && !(c == 0.0 || (a >= 0x1p-103 && a < 0x1p+127))) coef_bad = 1;
-        coef[i] = make_float2(h, l);
+        if constexpr (S == 1) {
+            coef[i] = make_float2(h, l);
+        } else {
+            float *q = reinterpret_cast<float *>(coef) + 4 * (i >> 1) + (i & 1);
+            q[0] = h;
+            q[2] = l;
+        }
         coef64[i] = c;
     }
     __syncthreads();
@@ -102,16 +160,35 @@ __global__ void __launch_bounds__(256) assemble_values_df_kernel(
         const int m0 = g * W;
         DfAcc A[W];
         bool ok = coef_bad == 0;
+        if constexpr (W == 1) {
+            A[0] = df_zero();
+            for (int k = 1; k <= M; ++k) {
+                const double mk = __ldg(modes + (int64_t)k * nnz + e);
+                float mh, ml;
+                ok &= df_split_trunc(mk, mh, ml);
+                const float2 c = coef[k * S + m0];
+                df_term_pre(A[0], mh, ml, c.x, c.y);
+            }
+        } else {
+            uint64_t AS[W / 2], AC[W / 2];
 #pragma unroll
-        for (int w = 0; w < W; ++w) A[w] = df_zero();
-        for (int k = 1; k <= M; ++k) {
-            const double mk = __ldg(modes + (int64_t)k * nnz + e);
-            float mh, ml;
-            ok &= df_split_trunc(mk, mh, ml);
+            for (int j = 0; j < W / 2; ++j) AS[j] = AC[j] = 0ull;  // (+0, +0)
+            const float4 *c4 = reinterpret_cast<const float4 *>(coef);
+            for (int k = 1; k <= M; ++k) {
+                const double mk = __ldg(modes + (int64_t)k * nnz + e);
+                float mh, ml;
+                ok &= df_split_trunc(mk, mh, ml);
+                const uint64_t ah = f2_pack(mh, mh), nah = f2_pack(-mh, -mh), al = f2_pack(ml, ml);
 #pragma unroll
-            for (int w = 0; w < W; ++w) {
-                const float2 c = coef[k * S + m0 + w];
-                df_term_pre(A[w], mh, ml, c.x, c.y);
+                for (int j = 0; j < W / 2; ++j) {
+                    const float4 c = c4[(k * S + m0) / 2 + j];
+                    df_term_pair(AS[j], AC[j], ah, nah, al, f2_pack(c.x, c.y), f2_pack(c.z, c.w));
+                }
+            }
+#pragma unroll
+            for (int j = 0; j < W / 2; ++j) {
+                f2_unpack(AS[j], A[2 * j].s, A[2 * j + 1].s);
+                f2_unpack(AC[j], A[2 * j].c, A[2 * j + 1].c);
             }
         }
         const double mz = __ldg(modes + e);
@@ -170,6 +247,19 @@ __global__ void assemble_rows_kernel(int32_t n, const int32_t *__restrict__ row_
     }
 }
 
+// grid of the grid-stride double-float kernel: one wave of resident CTAs
+template <int S>
+static unsigned asm_df_grid() {
+    static const unsigned g = [] {
+        int occ = 0, dev = 0, sms = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, assemble_values_df_kernel<S>, 256, 0);
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        return (unsigned)((occ > 0 ? occ : 1) * (sms > 0 ? sms : 152));
+    }();
+    return g;
+}
+
 template <int S>
 static int assemble_s(const ens_graph *g, const uint8_t *bmask, int M, const double *modes,
                       const double *load, const double *xi, double sigma, double kappa0,
@@ -179,7 +269,7 @@ static int assemble_s(const ens_graph *g, const uint8_t *bmask, int M, const dou
     const int64_t nthr = g->num_entries * G;
     if (nthr > 0) {
         if (df)
-            assemble_values_df_kernel<S><<<(unsigned)std::min<int64_t>((nthr + bs - 1) / bs, 152 * 6), bs, 0, st>>>(
+            assemble_values_df_kernel<S><<<(unsigned)std::min<int64_t>((nthr + bs - 1) / bs, asm_df_grid<S>()), bs, 0, st>>>(
                 g->num_entries, M, modes, xi, sigma, kappa0, values, vdf);
         else
             assemble_values_kernel<S><<<(unsigned)((nthr + bs - 1) / bs), bs, 0, st>>>(
