@@ -44,12 +44,14 @@ template <int S, typename T = double>
 __global__ void mg_restrict_kernel(const int *active, int Nc, const T *__restrict__ rf, T *__restrict__ bc) {
     if (ld_cg(active) == 0) return;
     const int nc1 = Nc + 1, nf1 = 2 * Nc + 1;
+    const uint32_t plane = (uint32_t)nc1 * nc1;
     const int64_t total = (int64_t)nc1 * nc1 * nc1 * S;
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
          t += (int64_t)gridDim.x * blockDim.x) {
         const int e = (int)(t % S);
-        const int64_t I = t / S;
-        const int ci = (int)(I % nc1), cj = (int)((I / nc1) % nc1), ck = (int)(I / ((int64_t)nc1 * nc1));
+        // node coordinates in 32-bit arithmetic (a level has fewer than 2^32 nodes)
+        const uint32_t I = (uint32_t)(t / S), rem = I % plane;
+        const int ck = (int)(I / plane), cj = (int)(rem / nc1), ci = (int)(rem % nc1);
         T acc = T(0);
         if (ci > 0 && ci < Nc && cj > 0 && cj < Nc && ck > 0 && ck < Nc) {
             for (int dk = -1; dk <= 1; ++dk)
@@ -73,22 +75,26 @@ __global__ void mg_prolong_kernel(const int *active, int Nc, const T *__restrict
                                   float2 *__restrict__ xfs, int *split_bad) {
     if (ld_cg(active) == 0) return;
     const int nc1 = Nc + 1, Nf = 2 * Nc, nf1 = Nf + 1;
+    const uint32_t plane = (uint32_t)nf1 * nf1;
     const int64_t total = (int64_t)nf1 * nf1 * nf1 * S;
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
          t += (int64_t)gridDim.x * blockDim.x) {
         const int e = (int)(t % S);
-        const int64_t I = t / S;
-        const int i = (int)(I % nf1), j = (int)((I / nf1) % nf1), k = (int)(I / ((int64_t)nf1 * nf1));
+        // node coordinates in 32-bit arithmetic (a level has fewer than 2^32 nodes)
+        const uint32_t I = (uint32_t)(t / S), rem = I % plane;
+        const int k = (int)(I / plane), j = (int)(rem / nf1), i = (int)(rem % nf1);
         if (i <= 0 || i >= Nf || j <= 0 || j >= Nf || k <= 0 || k >= Nf) continue;
         T acc = T(0);
         const int i0 = i >> 1, j0 = j >> 1, k0 = k >> 1;
         const int ni = (i & 1) ? 2 : 1, nj = (j & 1) ? 2 : 1, nk = (k & 1) ? 2 : 1;
+        // the weight 2^-(number of odd coordinates), exact in T (no arithmetic)
+        const int odd = (i & 1) + (j & 1) + (k & 1);
+        const T w = odd == 0 ? T(1) : odd == 1 ? T(0.5) : odd == 2 ? T(0.25) : T(0.125);
         for (int a = 0; a < nk; ++a)
             for (int bq = 0; bq < nj; ++bq)
                 for (int c = 0; c < ni; ++c) {
                     const int ci = i0 + c, cj = j0 + bq, ck = k0 + a;
                     if (ci <= 0 || ci >= Nc || cj <= 0 || cj >= Nc || ck <= 0 || ck >= Nc) continue;
-                    const T w = T(((i & 1) ? 0.5 : 1.0) * ((j & 1) ? 0.5 : 1.0) * ((k & 1) ? 0.5 : 1.0));
                     acc = fma(w, xc[node_id(ci, cj, ck, nc1) * S + e], acc);
                 }
         const T xn = xf[t] + acc;
