@@ -141,7 +141,12 @@ __device__ double q1_phi(int q, int a) {
 
 __device__ __forceinline__ int axis_n(int t, int N) { return (t == 0 || t == N) ? 2 : 3; }
 
-// warp per row, lane per entry of the row (rows have at most 27 entries)
+// Thread per (row, entry position p of the row): a warp takes position p of
+// 32 consecutive rows, so the lanes of an interior warp share the same number
+// of cells with their rows and run the same FP64 loops (a warp of the 27
+// entries of one row would run the diagonal entry's 8 cells on every lane:
+// a divergent FP64 instruction still takes the FP64 pipe for the whole warp).
+// Positions p, p + gridDim.y, ... for rows longer than gridDim.y.
 __global__ void __launch_bounds__(256) mode_matrices_kernel(
     int N, int M, const int32_t *__restrict__ row_map, const int32_t *__restrict__ col_entry,
     int64_t nnz, const double *__restrict__ table, double *__restrict__ modes,
@@ -153,20 +158,18 @@ __global__ void __launch_bounds__(256) mode_matrices_kernel(
     for (int i = threadIdx.x; i < 64; i += blockDim.x) Ps[i] = q1_phi(i >> 3, i & 7) * (h * h * h * 0.125);
     __syncthreads();
     const int64_t n = (int64_t)(N + 1) * (N + 1) * (N + 1);
-    const int64_t I = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-    const int lane = threadIdx.x & 31;
+    const int64_t I = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (I >= n) return;
-    const int i = (int)(I % (N + 1)), j = (int)((I / (N + 1)) % (N + 1)),
-              k = (int)(I / ((int64_t)(N + 1) * (N + 1)));
+    const int n1 = N + 1;
+    const int i = (int)(I % n1), j = (int)((I / n1) % n1), k = (int)(I / ((int64_t)n1 * n1));
     const bool brow = (i == 0 || j == 0 || k == 0 || i == N || j == N || k == N);
     const int rs = row_map[I], len = row_map[I + 1] - rs;
     const int twoN = 2 * N;
     const double *T0 = table, *T1 = table + (int64_t)M * twoN, *T2 = table + 2LL * M * twoN;
-    if (lane < len) {
-        const int64_t e = rs + lane;
+    for (int pos = blockIdx.y; pos < len; pos += gridDim.y) {
+        const int64_t e = rs + pos;
         const int32_t J = col_entry[e];
-        const int ji = (int)(J % (N + 1)), jj = (int)((J / (N + 1)) % (N + 1)),
-                  jk = (int)(J / ((int64_t)(N + 1) * (N + 1)));
+        const int ji = (int)(J % n1), jj = (int)((J / n1) % n1), jk = (int)(J / ((int64_t)n1 * n1));
         const bool bcol = (ji == 0 || jj == 0 || jk == 0 || ji == N || jj == N || jk == N);
         // cells shared by I and J: per axis, both coordinates in {c, c+1}
         const int ci0 = max(max(i, ji) - 1, 0), ci1 = min(min(i, ji), N - 1);
@@ -199,7 +202,7 @@ __global__ void __launch_bounds__(256) mode_matrices_kernel(
             modes[(int64_t)m * nnz + e] = acc;
         }
     }
-    if (lane == 0) {
+    if (blockIdx.y == 0) {
         double f = 0.0;
         if (!brow) {
             for (int ck = max(k - 1, 0); ck <= min(k, N - 1); ++ck)
@@ -264,7 +267,8 @@ extern "C" int ens_mode_matrices(int N, const ens_graph *graph, int M, const dou
     if (!kl_table || !modes || !load) return fail(ENS_ERR_ARG, "NULL table/modes/load");
     cudaStream_t st = as_stream(stream);
     const int bs = 256;
-    mode_matrices_kernel<<<(unsigned)(((int64_t)n * 32 + bs - 1) / bs), bs, 0, st>>>(
+    // 27 = the longest row of the Q1 hex graph (the kernel strides past it)
+    mode_matrices_kernel<<<dim3((unsigned)(((int64_t)n + bs - 1) / bs), 27), bs, 0, st>>>(
         N, M, graph->row_map, graph->col_entry, nnz, kl_table, modes, load);
     ENS_LAUNCH_CHECK("mode_matrices_kernel");
     return ENS_OK;
