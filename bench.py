@@ -277,6 +277,48 @@ def _per_sample_form(torch, device, nsamp, df):
             if r.spmv_ms > 0 else None}
 
 
+def ensemble_size_sweep(torch, device, nsamp=128):
+    """Sample-solves/s (assembly + CG) at the smaller ensemble sizes on the
+    64^3 workload: nsamp samples each, in the SpMV form the s sweep finds
+    fastest at that size (the s = 32 figure is the headline's value)."""
+    out = {}
+    for s, form in ((4, "f64"), (8, "split"), (16, "dfv")):
+        r = Runner(torch, s, nsamp, device, time_spmv=False, df=form)
+        r.setup_mesh()
+        r.solve_ensemble(0)  # warm-up
+        r.reset_stats()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for g in range(r.nens):
+            r.solve_ensemble(g)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        out[str(s)] = {"value": nsamp / dt, "unit": UNIT, "samples": nsamp, "spmv": form,
+                       "mean_iters": float(np.mean(r.iters)), "failed_members": r.status_bad}
+        del r
+    return out
+
+
+def assembly_rate(torch, r, peak, reps=10):
+    """Per-ensemble assembly (values, their pre-split copy in the dfv form,
+    right-hand side) timed with CUDA events on the headline's buffers."""
+    E = r.E
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    ev0.record()
+    for _ in range(reps):
+        E.assemble(r.graph, r.bmask, r.s, M_KL, r.modes, r.load, r.xi[0], SIGMA, KAPPA0, r.values, r.b,
+                   values_df=r.vdf)
+    ev1.record()
+    torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1) / reps
+    vbytes = 16 if r.vdf is not None else 8
+    byt = 8 * (M_KL + 1) * r.nnz + vbytes * r.nnz * r.s + 8 * r.n * r.s
+    return {"ms": ms, "bytes": byt, "gbs": byt / (ms * 1e-3) / 1e9, "hbm_frac": byt / (ms * 1e-3) / 1e9 / peak,
+            "form": "double-float KL terms, values + pre-split copy" if r.vdf is not None else "FP64",
+            "bound": "instruction issue and the FP64 pipe (ncu), not HBM"}
+
+
 def cpu_baseline_run(nsamples=None, nthreads=None):
     import oracle
     cores = nthreads or oracle.max_threads()
@@ -452,6 +494,8 @@ def main_ours(args):
                                 "mean_iters": float(np.mean(r2.iters)), "failed_members": r2.status_bad}
                 del r2
         sweep = None if (args.quick or not solo) else spmv_sweep(torch, device)
+        asm = assembly_rate(torch, r, peak) if solo else None
+        ssweep = None if (args.quick or not solo) else ensemble_size_sweep(torch, device)
         out = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
@@ -474,6 +518,8 @@ def main_ours(args):
             "ensemble_speedup_vs_per_sample": ens_speedup,
             "other_spmv_forms": others,
             "spmv_sweep_64cubed": sweep,
+            "ensemble_size_sweep_64cubed": ssweep,
+            "assembly": asm,
             "cg_iterations": {"mean": float(np.mean(iters)), "min": int(min(iters)),
                               "max": int(max(iters)), "failed_members": bad},
             "gpu_launches": gpu_launches,
