@@ -444,6 +444,7 @@ def main_ours(args):
     flops = 2.0 * r.nnz * s / (avg_spmv_ms * 1e-3) / 1e12
     traffic = profiled_traffic(s, args.spmv)
     gpu_launches = r.launches
+    spmv_launches_timed = r.spmv_launches  # before e2e_run adds its own steps' launches
     iters = r.iters
     bad = r.status_bad
     # end to end through the API on every rank (host buffers), slowest rank's time
@@ -467,7 +468,7 @@ def main_ours(args):
                             "peak_source": f"{peak_kind} hbm_gbs"}}
         roof.update({"kernel": f"cg_spmv_kernel<{s},{df}> (q = A p fused with per-member p.q)",
                      "bytes_per_launch": bytes_launch, "avg_launch_ms": avg_spmv_ms,
-                     "launches_timed": r.spmv_launches})
+                     "launches_timed": spmv_launches_timed})
         # the single-GPU comparisons (per-sample CG, other SpMV forms, the
         # sweep, the CPU oracle) only at N = 1
         solo = world == 1
@@ -1202,13 +1203,122 @@ def main_nonlinear(args):
     print(json.dumps(line))
 
 
+
+def main_profile_cg(args):
+    """Profiling driver: one ensemble CG with a fixed iteration count on an
+    N^3 mesh (M = 10, seed of the 64^3 workload), so that an ncu capture
+    (`ncu --clock-control none -k regex:cg_spmv_kernel -s 1 -c 1 ...`, after
+    the same command has exited 0 without ncu) sees a steady-state launch.  The SpMV
+    form is --spmv (dfv: double-float assembly writing the pre-split copy,
+    then ens_cg_df, as in the headline).  Tolerance 0, so exactly --iters
+    iterations run."""
+    import torch
+    import paper_1511_03703_gb300 as E
+    from paper_1511_03703_gb300 import inputs
+    N, s, iters, form = args.N, args.s, args.iters, args.spmv
+    dev = torch.device("cuda:0")
+    mesh = E.Mesh(N, M_KL, device=dev)
+    xs = inputs.kl_samples(inputs.SEED_SCALE, 0, s, M_KL)
+    xi = torch.from_numpy(inputs.ensemble_layout(xs)).to(dev)
+    vdf = torch.empty(2 * mesh.nnz * s, dtype=torch.float32, device=dev) if form == "dfv" else None
+    vals, b = mesh.assemble(s, xi, values_df=vdf)
+    x = torch.zeros(mesh.n * s, dtype=torch.float64, device=dev)
+    work = torch.empty(E.cg_workspace_size(mesh.n, s), dtype=torch.uint8, device=dev)
+    it, rr, st, stats = E.cg(mesh.graph, s, vals, b, x, 0.0, iters, work, flags=form_flag(form),
+                             check_every=iters, values_df=vdf)
+    torch.cuda.synchronize()
+    print("N", N, "s", s, "iters", it[:2], "status", st[:2], "nnz", mesh.nnz, "rows", mesh.n)
+
+
+def _profile_starts(torch, meshes, s, dev):
+    from paper_1511_03703_gb300 import inputs
+    return [torch.from_numpy(np.stack([inputs.random_vector(600 + 100 * l + e, m.n) for e in range(s)],
+                                      axis=1).reshape(-1)).to(dev) for l, m in enumerate(meshes)]
+
+
+def main_profile_mg(args):
+    """Profiling driver: multigrid-preconditioned ensemble CG on an N^3 mesh.
+    --reps times: assemble every level of one ensemble of s samples
+    (double-float assembly, M = 10, seed of the 64^3 workload) and solve to
+    1e-8 (graph replay of 4 iterations), printing the wall time of each part.
+    --mode presplit: every level also writes its pre-split values (the
+    V-cycle's SpMVs in double-float, as in the benchmark); --mode f32: the
+    finest level writes its pre-split values and every level an FP32 copy for
+    the FP32 V-cycle."""
+    import torch
+    import paper_1511_03703_gb300 as E
+    from paper_1511_03703_gb300 import inputs
+    N, s, reps = args.N, args.s, args.reps
+    presplit, f32 = args.mode == "presplit", args.mode == "f32"
+    dev = torch.device("cuda:0")
+    mg = E.Multigrid(N, M_KL, device=dev)
+    xs = inputs.kl_samples(inputs.SEED_SCALE, 0, s, M_KL)
+    xi = torch.from_numpy(inputs.ensemble_layout(xs)).to(dev)
+    starts = _profile_starts(torch, mg.meshes, s, dev)
+    x = torch.zeros(mg.meshes[0].n * s, dtype=torch.float64, device=dev)
+    split_levels = mg.meshes if presplit else (mg.meshes[:1] if f32 else [])
+    pre = [torch.empty(2 * m.nnz * s, dtype=torch.float32, device=dev) for m in split_levels] or None
+    vals, b = mg.assemble(s, xi, df=True, values_df=pre)
+    v32 = mg.to_f32(s, vals) if f32 else None
+    work = torch.empty(mg.workspace_size(s, vals, starts, pre, v32), dtype=torch.uint8, device=dev)
+    for rep in range(reps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        x.zero_()
+        vals, b = mg.assemble(s, xi, df=True, values_df=pre)
+        if f32:
+            mg.to_f32(s, vals, out=v32)
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        it, rr, st, stats = mg.solve(s, vals, b, x, 1e-8, 500, work, starts, flags=E.CG_GRAPH | E.CG_X0_ZERO,
+                                     check_every=4, values_df=pre, values_f32=v32)
+        torch.cuda.synchronize()
+        t2 = time.perf_counter()
+        print(f"rep {rep}: assemble {1e3 * (t1 - t0):.2f} ms, solve {1e3 * (t2 - t1):.2f} ms, "
+              f"iterations {max(it)}, status {sorted(set(st))}")
+
+
+def main_profile_nl(args):
+    """Profiling driver: Newton-GMRES for the nonlinear advection-diffusion
+    problem on an N^3 mesh (v = (1, 1, 1), alpha = 1, beta = 10, tol 1e-8,
+    GMRES(30) to 1e-6 per step, V-cycle right preconditioner, every level
+    pre-split).  --reps times: assemble every level of one ensemble of s
+    samples and solve from u = 0, printing the wall time of each part."""
+    import torch
+    import paper_1511_03703_gb300 as E
+    from paper_1511_03703_gb300 import inputs
+    N, s, reps = args.N, args.s, args.reps
+    dev = torch.device("cuda:0")
+    nl = E.Nonlinear(N, M_KL, v=(1.0, 1.0, 1.0), precond=E.NL_PRECOND_MG, device=dev)
+    xs = inputs.kl_samples(inputs.SEED_SCALE, 0, s, M_KL)
+    xi = torch.from_numpy(inputs.ensemble_layout(xs)).to(dev)
+    starts = _profile_starts(torch, nl.meshes, s, dev)
+    p = nl.params(1.0, 10.0, tol=1e-8, lin_tol=1e-6, restart=30, max_lin=300, max_newton=20)
+    u = torch.zeros(nl.mesh.n * s, dtype=torch.float64, device=dev)
+    vdf = [torch.empty(2 * m.nnz * s, dtype=torch.float32, device=dev) for m in nl.meshes]
+    vals, b = nl.assemble(s, xi, values_df=vdf)
+    work = torch.empty(nl.workspace_size(s, vals, starts, p, vdf), dtype=torch.uint8, device=dev)
+    for rep in range(reps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        u.zero_()
+        vals, b = nl.assemble(s, xi, values_df=vdf)
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        ni, li, rr, st, stats = nl.solve(s, vals, b, u, work, starts, p, values_df=vdf)
+        torch.cuda.synchronize()
+        t2 = time.perf_counter()
+        print(f"rep {rep}: assemble {1e3 * (t1 - t0):.2f} ms, solve {1e3 * (t2 - t1):.2f} ms, "
+              f"newton {max(ni)}, gmres {max(li)}, status {sorted(set(st))}")
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--s", type=int, default=32, choices=[4, 8, 16, 32])
+    ap.add_argument("--s", type=int, default=32, choices=[1, 4, 8, 16, 32])
     ap.add_argument("--spmv", default="dfv", choices=list(FORMS),
                     help="CG SpMV arithmetic: native FP64 FMA, double-float on the FP32 pipe, "
                          "alternate entries on each (split), or double-float reading values "
@@ -1216,13 +1326,23 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--quick", action="store_true", help="skip the other-form run and the s sweep")
     ap.add_argument("--workload", default="scale", choices=["scale", "mixed", "batched", "guess", "coupled", "pcg", "mg",
-                                                             "nonlinear"],
+                                                             "nonlinear", "profile-cg", "profile-mg", "profile-nl"],
                     help="scale: 64^3 ensemble CG (default line); mixed: 128^3 mixed precision; "
                          "batched: 16^3..64^3 x s=4..32 in one batch; guess: learned initial guess; "
                          "coupled: the paper's coupled CG vs per-member CG; pcg: preconditioned CG; "
                          "mg: multigrid-preconditioned CG; nonlinear: Newton-GMRES for the "
-                         "advection-diffusion problem")
+                         "advection-diffusion problem; profile-cg / profile-mg / profile-nl: one solve on "
+                         "an --N mesh for ncu captures (no JSON line)")
+    ap.add_argument("--N", type=int, default=64, help="profile-*: cells per side")
+    ap.add_argument("--iters", type=int, default=8, help="profile-cg: fixed CG iteration count")
+    ap.add_argument("--reps", type=int, default=2, help="profile-mg / profile-nl: repetitions")
+    ap.add_argument("--mode", default="presplit", choices=["", "presplit", "f32"],
+                    help="profile-mg: which levels are pre-split / FP32")
     args = ap.parse_args()
+    profile = {"profile-cg": main_profile_cg, "profile-mg": main_profile_mg, "profile-nl": main_profile_nl}
+    if args.workload in profile:
+        profile[args.workload](args)
+        return
     if args.workload == "mixed" and args.impl != "reference":
         main_mixed(args)
         return
