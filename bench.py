@@ -110,6 +110,30 @@ def measured_peaks():
     return 6800.0, "fallback"
 
 
+class OracleJobs:
+    """Oracle solves (plain FP64 C, OpenMP over samples) on background host
+    threads, so that the CPU-side checks of the extension workloads overlap
+    their GPU work (ctypes releases the GIL during the call).  Never used
+    inside a timed region's CPU measurement."""
+
+    def __init__(self, workers=4):
+        import concurrent.futures
+        self.pool = concurrent.futures.ThreadPoolExecutor(max_workers=workers)
+
+    def solve(self, N, xs, tol, max_iter=20000):
+        """Future of (x[num_samples, n], iterations, seconds)."""
+        xs = np.array(xs, dtype=np.float64, copy=True)
+
+        def job():
+            import oracle
+            t0 = time.perf_counter()
+            x, it, rr, st = oracle.solve_samples(N, M_KL, xs, tol, max_iter, nthreads=len(xs), want_x=True)
+            if any(int(v) for v in st):
+                raise RuntimeError(f"oracle status {list(st)}")
+            return x, it, time.perf_counter() - t0
+        return self.pool.submit(job)
+
+
 class ClockSampler:
     """nvidia-smi clocks and throttle reasons sampled during the timed region."""
 
@@ -230,7 +254,7 @@ class Runner:
         # dfv: double-float assembly that also writes the pre-split copy
         E.assemble(self.graph, self.bmask, self.s, M_KL, self.modes, self.load,
                    self.xi[g] if xi is None else xi, SIGMA, KAPPA0, self.values, self.b,
-                   values_df=self.vdf)
+                   values_df=self.vdf, kl_table=self.kl)
         x = self.x[g]
         x.zero_()
         flags = (E.CG_TIME_SPMV if self.time_spmv else 0) | form_flag(self.df) | E.CG_X0_ZERO | E.CG_GRAPH
@@ -301,7 +325,9 @@ def ensemble_size_sweep(torch, device, nsamp=128):
 
 def assembly_rate(torch, r, peak, reps=10):
     """Per-ensemble assembly (values, their pre-split copy in the dfv form,
-    right-hand side) timed with CUDA events on the headline's buffers."""
+    right-hand side) timed with CUDA events on the headline's buffers: the
+    assembly kernels alone, without the coefficient check (which the timed
+    step runs once per ensemble and which synchronises)."""
     E = r.E
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
@@ -362,6 +388,31 @@ def e2e_run(torch, r, steps):
     return {"value": steps * r.batch / dt, "unit": UNIT, "ms": 1e3 * dt, "samples": steps * r.batch,
             "h2d_bytes_per_step": int(r.xi_host.nbytes),
             "d2h_bytes_per_step": int(r.nens * r.n * r.s * 8)}
+
+
+def extensions(args):
+    """The extension workloads in compact form, for the default line (after
+    the headline's timed region, N = 1 only): A7 mixed precision at 128^3
+    (2 ensembles of 16), A8 batched (all 2048 samples), A9 learned guess
+    (full training, 1024 test samples), NEXT-3 MG-PCG at 64^3 (2 ensembles).
+    Each carries its error against oracle solves of two samples, computed on
+    background host threads while the GPU runs the next workload."""
+    jobs = OracleJobs()
+    pending = {}
+    t0 = time.perf_counter()
+    for name, fn in (("mixed_128cubed", run_mixed), ("batched_16to64cubed", run_batched),
+                     ("learned_guess_64cubed", run_guess), ("mg_pcg_64cubed", run_mg)):
+        t1 = time.perf_counter()
+        res, fut, finish = fn(args, compact=True, oracle_jobs=jobs)
+        res["wall_seconds"] = time.perf_counter() - t1
+        pending[name] = (res, fut, finish)
+    t_gpu = time.perf_counter() - t0
+    out = {}
+    for name, (res, fut, finish) in pending.items():
+        finish(fut.result())
+        out[name] = res
+    out["seconds"] = {"gpu_side": t_gpu, "total_with_oracle_checks": time.perf_counter() - t0}
+    return out
 
 
 def dist_setup():
@@ -497,6 +548,8 @@ def main_ours(args):
         sweep = None if (args.quick or not solo) else spmv_sweep(torch, device)
         asm = assembly_rate(torch, r, peak) if solo else None
         ssweep = None if (args.quick or not solo) else ensemble_size_sweep(torch, device)
+        cpu = cpu_baseline_run() if (solo and not args.no_cpu_baseline) else None
+        ext = None if (args.quick or args.no_extensions or not solo) else extensions(args)
         out = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
@@ -507,13 +560,9 @@ def main_ours(args):
                       "dfv": "f64 (SpMV in double-float 2xf32 from values pre-split once per ensemble, "
                              "bitwise the df form; all else f64)"}[df],
             "data": "synthetic",
-            "config": {"workload": WORKLOAD, "ensemble_size": s, "batch_samples": BATCH,
-                       "ensembles_per_step": BATCH // s, "tol": TOL, "kl_terms": M_KL,
-                       "sigma": SIGMA, "corr_length": L_CORR, "spmv": args.spmv,
-                       "l2": "inputs larger than L2 (1.8 GB values per ensemble)",
-                       "parallelism": f"replica per GPU, {world} GPU(s), samples sharded by rank"},
+            "config": headline_config(args, world),
             "roofline": roof,
-            "cpu_baseline": cpu_baseline_run() if (solo and not args.no_cpu_baseline) else None,
+            "cpu_baseline": cpu,
             "e2e": e2e,
             "per_sample_gpu": per,
             "ensemble_speedup_vs_per_sample": ens_speedup,
@@ -521,6 +570,7 @@ def main_ours(args):
             "spmv_sweep_64cubed": sweep,
             "ensemble_size_sweep_64cubed": ssweep,
             "assembly": asm,
+            "extensions": ext,
             "cg_iterations": {"mean": float(np.mean(iters)), "min": int(min(iters)),
                               "max": int(max(iters)), "failed_members": bad},
             "gpu_launches": gpu_launches,
@@ -530,6 +580,15 @@ def main_ours(args):
     if world > 1:
         torch.distributed.destroy_process_group()
     return out
+
+
+def headline_config(args, world):
+    """The headline workload's config (both arms report the same one)."""
+    return {"workload": WORKLOAD, "ensemble_size": args.s, "batch_samples": BATCH,
+            "ensembles_per_step": BATCH // args.s, "tol": TOL, "kl_terms": M_KL,
+            "sigma": SIGMA, "corr_length": L_CORR, "spmv": args.spmv,
+            "l2": "inputs larger than L2 (1.8 GB values per ensemble)",
+            "parallelism": f"replica per GPU, {world} GPU(s), samples sharded by rank"}
 
 
 def main_reference(args):
@@ -550,10 +609,10 @@ def main_reference(args):
            "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
            "impl": "reference",
-           "config": {"workload": WORKLOAD, "ensemble_size": 1, "batch_samples": ns,
-                      "tol": TOL, "kl_terms": M_KL},
+           "config": headline_config(args, world),
            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
-                            "sample": vals[0]["sample"]},
+                            "sample": vals[0]["sample"] + f"; {ns} of the workload's samples per step "
+                                      "(a bounded sample: the oracle is per sample, no ensembles)"},
            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out))
     return out
@@ -565,17 +624,25 @@ MIX_WORKLOAD = ("KL diffusion, 128^3 hex Q1 mesh (2,146,689 rows, 57,066,625 nnz
                 "256 samples as 16 ensembles of s=16, true residual 1e-10")
 
 
-def main_mixed(args):
+def run_mixed(args, compact=False, oracle_jobs=None):
     """FP64 ensemble CG vs FP64-refined FP32 / BF16 inner CG on the 128^3 workload.
-    One step = set-up + 16 ensembles (assembly, value conversion, solve)."""
+    One step = set-up + the ensembles (assembly, value conversion, solve); the
+    full workload is 16 ensembles of s = 16, the compact one (for the default
+    bench line) 2.  Returns the result dict; the error of two samples against
+    FP64 oracle solves (tol 1e-12) is filled in when the oracle job ends."""
     import torch
     import paper_1511_03703_gb300 as E
     from paper_1511_03703_gb300 import inputs
     dev = torch.device("cuda:0")
     E.lib()
     N, M, s = MIX_N, M_KL, MIX_S
-    nens = MIX_BATCH // s
-    xs_all = inputs.kl_samples(inputs.SEED_MIXED, 0, MIX_BATCH, M)
+    batch = 2 * s if compact else MIX_BATCH
+    nens = batch // s
+    steps, warmup = (1, 1) if compact else (args.steps, args.warmup)
+    xs_all = inputs.kl_samples(inputs.SEED_MIXED, 0, batch, M)
+    nref = 2
+    jobs = oracle_jobs or OracleJobs()
+    fut = jobs.solve(N, xs_all[:nref], 1e-12)
     xi = torch.from_numpy(np.stack([inputs.ensemble_layout(b) for b in xs_all.reshape(nens, s, M)])).to(dev)
     mesh = E.Mesh(N, M, device=dev)
     vals = torch.empty(mesh.nnz * s, dtype=torch.float64, device=dev)
@@ -592,7 +659,6 @@ def main_mixed(args):
 
     def run(form, stats):
         mesh.assemble(s, xi[0], values=vals, b=b)  # warm the set-up path
-        t0 = time.perf_counter()
         torch.cuda.synchronize()
         ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         ev0.record()
@@ -630,46 +696,52 @@ def main_mixed(args):
         torch.cuda.synchronize()
         return ev0.elapsed_time(ev1) / 1e3
 
-    out = {}
+    out, xg = {}, {}
     for form in ("f64", "f32", "bf16"):
-        for _ in range(args.warmup):
+        for _ in range(warmup):
             run(form, {"outer": [], "inner": [], "relres": [], "bad": 0, "spmv_ms": 0.0, "spmv_n": 0})
         st = {"outer": [], "inner": [], "relres": [], "bad": 0, "spmv_ms": 0.0, "spmv_n": 0}
-        tt = sum(run(form, st) for _ in range(args.steps))
+        tt = sum(run(form, st) for _ in range(steps))
         vb = st["vb"]
         if form == "f64":
             sb = spmv_bytes(n, nnz, s)
         else:  # low-precision values, float x gather and q write, (bf16) FP32 diagonal
             sb = nnz * (vb * s + 4) + 4 * (n + 1) + 2 * 4 * n * s + (4 * n * s if form == "bf16" else 0)
         ms = st["spmv_ms"] / max(st["spmv_n"], 1)
-        out[form] = {"value": args.steps * MIX_BATCH / tt, "unit": UNIT,
+        out[form] = {"value": steps * batch / tt, "unit": UNIT,
                      "spmv": "f64 (dfv: pre-split double-float)" if form == "f64"
                      else f"{form} values, f32 accumulation",
                      "spmv_gbs": sb / (ms * 1e-3) / 1e9, "spmv_hbm_frac": sb / (ms * 1e-3) / 1e9 / peak,
                      "outer_mean": float(np.mean(st["outer"])), "inner_mean": float(np.mean(st["inner"])),
                      "max_relres": float(max(st["relres"])), "failed": st["bad"]}
-        # error against oracle FP64 solves of two samples (last step's solutions)
-        out[form]["x_ens0"] = X[0].view(-1, s)[:, :2].cpu().numpy().copy()
-    import oracle
-    nref = 2
-    t0 = time.perf_counter()
-    xo, ito, rro, sto = oracle.solve_samples(N, M, xs_all[:nref], 1e-12, 20000, nthreads=nref, want_x=True)
-    toracle = time.perf_counter() - t0
-    for form in out:
-        xg = out[form].pop("x_ens0")
-        out[form]["rel_err_vs_fp64_oracle"] = [float(np.linalg.norm(xg[:, j] - xo[j]) / np.linalg.norm(xo[j]))
-                                               for j in range(nref)]
-    line = {"metric": "ensemble CG sample-solves/s, FP64 vs mixed precision (FP32 / BF16 values, FP64 refinement)",
-            "value": out["f32"]["value"], "unit": UNIT, "n_gpus": 1, "steps": args.steps,
-            "warmup": args.warmup, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f32 inner (f32 values), f64 residual and update", "data": "synthetic",
-            "config": {"workload": MIX_WORKLOAD, "ensemble_size": s, "batch_samples": MIX_BATCH,
-                       "inner_tol": {"f32": 1e-4, "bf16": 1e-2}, "bf16_diagonal": "fp32, row-sum compensated",
-                       "l2": "inputs larger than L2"},
-            "forms": out,
-            "oracle": {"samples": nref, "tol": 1e-12, "iters": [int(v) for v in ito],
-                       "seconds": toracle, "threads": nref}}
-    print(json.dumps(line))
+        xg[form] = X[0].view(-1, s)[:, :nref].cpu().numpy().copy()   # last step's first two members
+    del vals, b, X, v32, vbf, diag, vdf, wcg, wmx, mesh
+    torch.cuda.empty_cache()
+    res = {"metric": "ensemble CG sample-solves/s, FP64 vs mixed precision (FP32 / BF16 values, FP64 refinement)",
+           "value": out["f32"]["value"], "unit": UNIT, "n_gpus": 1, "steps": steps,
+           "warmup": warmup, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+           "dtype": "f32 inner (f32 values), f64 residual and update", "data": "synthetic",
+           "config": {"workload": MIX_WORKLOAD if not compact else
+                      MIX_WORKLOAD.replace("256 samples as 16 ensembles", "32 samples as 2 ensembles"),
+                      "ensemble_size": s, "batch_samples": batch,
+                      "inner_tol": {"f32": 1e-4, "bf16": 1e-2}, "bf16_diagonal": "fp32, row-sum compensated",
+                      "l2": "inputs larger than L2"},
+           "forms": out}
+
+    def finish(oracle_result):
+        xo, ito, sec = oracle_result
+        for form in out:
+            out[form]["rel_err_vs_fp64_oracle"] = [
+                float(np.linalg.norm(xg[form][:, j] - xo[j]) / np.linalg.norm(xo[j])) for j in range(nref)]
+        res["oracle"] = {"samples": f"sample indices 0..{nref - 1} of the 128^3 workload", "tol": 1e-12,
+                         "iters": [int(v) for v in ito], "seconds": sec, "threads": nref}
+    return res, fut, finish
+
+
+def main_mixed(args):
+    res, fut, finish = run_mixed(args)
+    finish(fut.result())
+    print(json.dumps(res))
 
 
 # ------------------------------------------------------- batched workload
@@ -678,15 +750,23 @@ BAT_WORKLOAD = ("KL diffusion, hex Q1 meshes 16^3, 32^3, 48^3, 64^3 x ensemble w
                 "128 samples per (mesh, width) group, 2048 samples, M=10, CG to 1e-8")
 
 
-def main_batched(args):
+def run_batched(args, compact=False, oracle_jobs=None):
     """16 groups of 128 samples solved (a) one ens_cg call per ensemble and
     (b) one ens_cg_batched call for all 240 ensembles, with knobs from the
-    autotuner (SpMV form per (mesh, s); graph length for the batch)."""
+    autotuner (SpMV form per (mesh, s); graph length for the batch).  compact:
+    one warm-up and one timed step.  The first sample of the 16^3 and of the
+    32^3 group at s = 4 are checked against oracle solves (tol 1e-12)."""
     import torch
     import paper_1511_03703_gb300 as E
     from paper_1511_03703_gb300 import autotune, inputs
     dev = torch.device("cuda:0")
     E.lib()
+    steps, warmup = (1, 1) if compact else (args.steps, args.warmup)
+    jobs = oracle_jobs or OracleJobs()
+    # group g = (mesh index) * 4 + (width index); (16^3, s=4) is group 0, (32^3, s=4) group 4
+    checks = [(16, 0), (32, 4)]
+    futs = [jobs.solve(N, inputs.kl_samples(inputs.SEED_BATCHED, g * BAT_GROUP, 1, M_KL), 1e-12)
+            for N, g in checks]
     meshes = {N: E.Mesh(N, M_KL, device=dev) for N in BAT_MESHES}
     items, groups = [], []
     g = 0
@@ -759,11 +839,11 @@ def main_batched(args):
         return e0.elapsed_time(e1) / 1e3, res
 
     total = len(items) and sum(it["s"] for it in items)
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         timed(separate)
         timed(batched)
     ts = tb = 0.0
-    for _ in range(args.steps):
+    for _ in range(steps):
         t, it_sep = timed(separate)
         ts += t
         t, it_bat = timed(batched)
@@ -772,19 +852,43 @@ def main_batched(args):
     per_group = {}
     for it, its in zip(items, it_bat):
         per_group.setdefault(f"{it['N']}^3,s={it['s']}", []).extend(its)
+    # the batched solutions of the checked samples (member 0 of each group's first ensemble)
+    xg = [next(it for it in items if it["group"] == g)["x"].view(-1, 4)[:, 0].cpu().numpy().copy()
+          for _, g in checks]
     line = {"metric": "batched ensemble CG sample-solves/s: one launch per CG phase vs separate launches",
-            "value": args.steps * total / tb, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
-            "warmup": args.warmup, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "value": steps * total / tb, "unit": UNIT, "n_gpus": 1, "steps": steps,
+            "warmup": warmup, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f64", "data": "synthetic",
             "config": {"workload": BAT_WORKLOAD, "ensembles": len(items), "samples": total,
                        "batch_spmv_form": bform, "graph_check_every": ce,
                        "per_group_forms": {f"{N}^3,s={s}": forms[(N, s)] for (N, s) in groups},
                        "tuning_seconds": tune_s, "step": "mesh set-up + assembly of every ensemble + solve"},
-            "separate_launches": {"value": args.steps * total / ts, "unit": UNIT},
+            "separate_launches": {"value": steps * total / ts, "unit": UNIT},
             "speedup_batched_vs_separate": ts / tb,
             "iterations_identical": same,
             "mean_iterations_per_group": {k: float(np.mean(v)) for k, v in per_group.items()}}
-    print(json.dumps(line))
+    del items, batch, bwork, works
+    torch.cuda.empty_cache()
+
+    class _Futs:
+        def result(self):
+            return [f.result() for f in futs]
+
+    def finish(results):
+        errs, its = [], []
+        for (xo, ito, _), x in zip(results, xg):
+            errs.append(float(np.linalg.norm(x - xo[0]) / np.linalg.norm(xo[0])))
+            its.append(int(ito[0]))
+        line["rel_err_vs_fp64_oracle"] = errs
+        line["oracle"] = {"samples": "first sample of the 16^3 and of the 32^3 group at s = 4", "tol": 1e-12,
+                          "iters": its}
+    return line, _Futs(), finish
+
+
+def main_batched(args):
+    res, fut, finish = run_batched(args)
+    finish(fut.result())
+    print(json.dumps(res))
 
 
 # ------------------------------------------------- learned-guess workload
@@ -793,10 +897,12 @@ GUESS_WORKLOAD = ("KL diffusion, 64^3 hex Q1 mesh, M=10: MLP 10-256-256-64 (GELU
                   "coefficients, trained on 4096 solved samples, tested on 1024 fresh samples, CG to 1e-8")
 
 
-def main_guess(args):
+def run_guess(args, compact=False, oracle_jobs=None):
     """Zero-guess ensemble CG vs CG from the learned guess on 1024 fresh
     samples (s = 32), both to ||r|| <= 1e-8 ||b||; training (solves, POD,
-    MLP epochs) timed separately."""
+    MLP epochs) timed separately.  compact: one warm-up and one timed step.
+    Test samples 0 and 1 (solved from the learned guess) are checked against
+    oracle solves (tol 1e-12)."""
     import torch
     import paper_1511_03703_gb300 as E
     from paper_1511_03703_gb300 import inputs
@@ -804,6 +910,10 @@ def main_guess(args):
     dev = torch.device("cuda:0")
     E.lib()
     s = 32
+    steps, warmup = (1, 1) if compact else (args.steps, args.warmup)
+    nref = 2
+    jobs = oracle_jobs or OracleJobs()
+    fut = jobs.solve(N_MESH, inputs.kl_samples(inputs.SEED_GUESS_TEST, 0, nref, M_KL), 1e-12)
     flags = E.CG_GRAPH
     mesh = E.Mesh(N_MESH, M_KL, device=dev)
 
@@ -832,9 +942,11 @@ def main_guess(args):
     vdf = torch.empty(2 * mesh.nnz * s, dtype=torch.float32, device=dev)
     work = torch.empty(E.cg_workspace_size(mesh.n, s), dtype=torch.uint8, device=dev)
 
+    first = {}
+
     def run(learned):
         iters, fb, launches = [], 0, 0
-        for xi in xis:
+        for gi, xi in enumerate(xis):
             mesh.assemble(s, xi, values=vals, b=b, values_df=vdf)
             launches += 2
             if learned:
@@ -850,6 +962,8 @@ def main_guess(args):
             iters += it
             fb += stats.guess_fallbacks
             launches += stats.kernel_launches
+            if gi == 0 and learned:
+                first["x"] = x.view(-1, s)[:, :nref].clone()
         return iters, fb, launches
 
     def timed(learned):
@@ -861,24 +975,25 @@ def main_guess(args):
         torch.cuda.synchronize()
         return e0.elapsed_time(e1) / 1e3, res
 
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         timed(False)
         timed(True)
     tz = tl = 0.0
-    for _ in range(args.steps):
+    for _ in range(steps):
         t, (iz, _, lz) = timed(False)
         tz += t
         t, (il, fb, ll) = timed(True)
         tl += t
+    xg = first["x"].cpu().numpy()
     line = {"metric": "ensemble CG sample-solves/s from the learned initial guess vs from zero, 1 GB300",
-            "value": args.steps * GUESS_TEST / tl, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": 1e3 * tl / args.steps, "higher_is_better": True,
+            "value": steps * GUESS_TEST / tl, "unit": UNIT, "n_gpus": 1, "steps": steps,
+            "warmup": warmup, "ms_per_step": 1e3 * tl / steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64 CG, f32 network", "data": "synthetic",
             "config": {"workload": GUESS_WORKLOAD, "ensemble_size": s, "spmv": "dfv",
                        "step": "assembly + guess + CG of all 1024 test samples",
                        "pod_modes": GUESS_K, "pod_oversampled": GUESS_L, "epochs": GUESS_EPOCHS,
                        "batch": 256},
-            "zero_guess": {"value": args.steps * GUESS_TEST / tz, "unit": UNIT,
+            "zero_guess": {"value": steps * GUESS_TEST / tz, "unit": UNIT,
                            "mean_iterations": float(np.mean(iz)), "max_iterations": int(np.max(iz))},
             "learned_guess": {"mean_iterations": float(np.mean(il)), "max_iterations": int(np.max(il)),
                               "min_iterations": int(np.min(il)), "fallback_rate": fb / GUESS_TEST},
@@ -889,7 +1004,22 @@ def main_guess(args):
                          "loss_first_epoch": float(losses[0]), "loss_last_epoch": float(losses[-1]),
                          "sigma_1": float(sig[0]), "sigma_64_over_sigma_1": float(sig[-1] / sig[0])},
             "gpu_launches": ll}
-    print(json.dumps(line))
+    del vals, b, x, vdf, work, g, mesh
+    torch.cuda.empty_cache()
+
+    def finish(oracle_result):
+        xo, ito, sec = oracle_result
+        line["rel_err_vs_fp64_oracle"] = [float(np.linalg.norm(xg[:, j] - xo[j]) / np.linalg.norm(xo[j]))
+                                          for j in range(nref)]
+        line["oracle"] = {"samples": "test samples 0 and 1 (solved from the learned guess)", "tol": 1e-12,
+                          "iters": [int(v) for v in ito]}
+    return line, fut, finish
+
+
+def main_guess(args):
+    res, fut, finish = run_guess(args)
+    finish(fut.result())
+    print(json.dumps(res))
 
 
 # ------------------------------------------------ coupled CG (Sects. 3.4, 3.7)
@@ -1048,25 +1178,33 @@ MG_WORKLOAD = ("KL diffusion, 64^3 hex Q1 mesh, M=10, 256 samples as 8 ensembles
                "mg_f64: all FP64) vs plain ensemble CG")
 
 
-def main_mg(args):
+def run_mg(args, compact=False, oracle_jobs=None):
     """The paper's solver form (Sect. 3.5): MG-PCG on the nested meshes
     against the plain CG, same samples and tolerance; each step assembles
-    every level of every ensemble and solves."""
+    every level of every ensemble and solves.  compact: 64 samples (2
+    ensembles), one warm-up.  Samples 0 and 1 of the MG-PCG solve (the
+    default, pre-split form) are checked against oracle CG solves (tol 1e-12)."""
     import torch
     import paper_1511_03703_gb300 as E
     from paper_1511_03703_gb300 import inputs
     dev = torch.device("cuda:0")
     E.lib()
     s = 32
+    nsamp = 2 * s if compact else MG_SAMPLES
+    warmup = 1 if compact else args.warmup
+    nref = 2
+    jobs = oracle_jobs or OracleJobs()
+    fut = jobs.solve(N_MESH, inputs.kl_samples(inputs.SEED_SCALE, 0, nref, M_KL), 1e-12)
     t0 = time.perf_counter()
     mg = E.Multigrid(N_MESH, M_KL, device=dev)
     torch.cuda.synchronize()
     t_setup = time.perf_counter() - t0
-    xs = inputs.kl_samples(inputs.SEED_SCALE, 0, MG_SAMPLES, M_KL)
-    xis = [torch.from_numpy(inputs.ensemble_layout(xs[j:j + s])).to(dev) for j in range(0, MG_SAMPLES, s)]
+    xs = inputs.kl_samples(inputs.SEED_SCALE, 0, nsamp, M_KL)
+    xis = [torch.from_numpy(inputs.ensemble_layout(xs[j:j + s])).to(dev) for j in range(0, nsamp, s)]
     starts = [torch.from_numpy(np.stack([inputs.random_vector(600 + 100 * l + e, m.n) for e in range(s)],
                                         axis=1).reshape(-1)).to(dev) for l, m in enumerate(mg.meshes)]
     mesh = mg.meshes[0]
+    first = {}
     vdf = torch.empty(2 * mesh.nnz * s, dtype=torch.float32, device=dev)
     # mg: every level's SpMVs from pre-split values (level 0's buffer shared with cg_dfv)
     vdfs = [vdf] + [torch.empty(2 * m.nnz * s, dtype=torch.float32, device=dev) for m in mg.meshes[1:]]
@@ -1082,7 +1220,7 @@ def main_mg(args):
         its = []
         torch.cuda.synchronize()
         t = time.perf_counter()
-        for xi in xis:
+        for gi, xi in enumerate(xis):
             x.zero_()
             if form in ("mg", "mg_f64", "mg_fp32_vcycle"):
                 # mg: K1 and every level's V-cycle SpMVs from pre-split values;
@@ -1101,26 +1239,48 @@ def main_mg(args):
             if any(st):
                 raise RuntimeError(f"{form}: status {st}")
             its += it
+            if gi == 0 and form == "mg":
+                first["x"] = x.view(-1, s)[:, :nref].clone()
         torch.cuda.synchronize()
         return its, time.perf_counter() - t
 
     out = {}
-    for form in ("cg_f64", "cg_dfv", "mg_f64", "mg", "mg_fp32_vcycle"):
-        for _ in range(args.warmup):
+    forms = ("cg_dfv", "mg", "mg_fp32_vcycle") if compact else ("cg_f64", "cg_dfv", "mg_f64", "mg",
+                                                                 "mg_fp32_vcycle")
+    for form in forms:
+        for _ in range(warmup):
             run(form)
         its, sec = run(form)
         out[form] = {"mean_iterations": float(np.mean(its)), "max_iterations": int(np.max(its)),
-                     "sample_solves_per_s": MG_SAMPLES / sec}
+                     "sample_solves_per_s": nsamp / sec}
+    xg = first["x"].cpu().numpy()
     line = {"metric": "multigrid-preconditioned ensemble CG sample-solves/s vs plain ensemble CG, 1 GB300",
             "value": out["mg"]["sample_solves_per_s"], "unit": UNIT, "n_gpus": 1, "steps": 1,
-            "warmup": args.warmup, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "warmup": warmup, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f64", "data": "synthetic",
-            "config": {"workload": MG_WORKLOAD, "levels": mg.sizes, "smoother": "Chebyshev degree 2 on "
+            "config": {"workload": MG_WORKLOAD if not compact else
+                       MG_WORKLOAD.replace("256 samples as 8 ensembles", "64 samples as 2 ensembles"),
+                       "levels": mg.sizes, "smoother": "Chebyshev degree 2 on "
                        "[lam/5, 1.1 lam], 10 power steps", "mesh_setup_seconds": t_setup,
                        "step": "assembly of every level + solve, per ensemble"},
             "forms": out, "speedup_vs_plain_cg_dfv": out["mg"]["sample_solves_per_s"] /
             out["cg_dfv"]["sample_solves_per_s"]}
-    print(json.dumps(line))
+    del mg, x, vdf, vdfs, wcg, wmg, v32s, starts, xis
+    torch.cuda.empty_cache()
+
+    def finish(oracle_result):
+        xo, ito, sec = oracle_result
+        line["rel_err_vs_fp64_oracle"] = [float(np.linalg.norm(xg[:, j] - xo[j]) / np.linalg.norm(xo[j]))
+                                          for j in range(nref)]
+        line["oracle"] = {"samples": "samples 0 and 1 of the 64^3 workload (MG-PCG, pre-split form)",
+                          "tol": 1e-12, "iters": [int(v) for v in ito]}
+    return line, fut, finish
+
+
+def main_mg(args):
+    res, fut, finish = run_mg(args)
+    finish(fut.result())
+    print(json.dumps(res))
 
 
 # ------------------------------------------ nonlinear advection-diffusion
@@ -1324,7 +1484,10 @@ def main():
                          "alternate entries on each (split), or double-float reading values "
                          "pre-split once per ensemble (dfv)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--quick", action="store_true", help="skip the other-form run and the s sweep")
+    ap.add_argument("--quick", action="store_true", help="skip the other-form run, the s sweep and the "
+                                                          "extension workloads")
+    ap.add_argument("--no-extensions", action="store_true",
+                    help="skip the compact extension workloads (A7, A8, A9, MG-PCG) of the default line")
     ap.add_argument("--workload", default="scale", choices=["scale", "mixed", "batched", "guess", "coupled", "pcg", "mg",
                                                              "nonlinear", "profile-cg", "profile-mg", "profile-nl"],
                     help="scale: 64^3 ensemble CG (default line); mixed: 128^3 mixed precision; "

@@ -44,7 +44,7 @@ typedef enum ens_status {
     ENS_ERR_CUDA = 4,          /* a CUDA runtime call failed */
     ENS_ERR_NOT_CONVERGED = 5, /* CG hit max_iter before the tolerance */
     ENS_ERR_BREAKDOWN = 6,     /* p'Ap <= 0 or not finite (matrix not SPD) */
-    ENS_ERR_NONPOS_COEFF = 7,  /* reserved: coefficient a(x) <= 0 */
+    ENS_ERR_NONPOS_COEFF = 7,  /* a member's coefficient a(x_q) <= 0 at a Gauss point (ens_assemble) */
     ENS_ERR_TIMEOUT = 8,       /* reserved: a bounded device wait gave up */
     ENS_ERR_WORKSPACE = 9      /* workspace smaller than the *_workspace_size value */
 } ens_status;
@@ -125,8 +125,20 @@ int ens_mode_matrices(int N, const ens_graph *graph, int M, const double *kl_tab
  * in the commuted layout: values[entry*s + e], b[node*s + e].  Dirichlet
  * u = 0 by symmetric elimination: boundary rows become identity rows with
  * b = 0; interior rows keep stored zeros in boundary columns.
- * bmask from ens_graph_build; values and b must be 16-byte aligned for s>1. */
-int ens_assemble(const ens_graph *graph, const uint8_t *bmask, int s, int M,
+ * bmask from ens_graph_build; values and b must be 16-byte aligned for s>1.
+ *
+ * Coefficient check (Sect. 4: the KL coefficient must stay positive for the
+ * stiffness matrix to be SPD).  kl_table may be NULL (no check); otherwise it
+ * is the table ens_kl_setup wrote for this mesh and M, and before assembling
+ * the call verifies for every member that a_e(x_q) > 0 at every Gauss point:
+ * first by the bound kappa0 - |sigma| sum_k |xi_k^e| max_q |kappa_k(x_q)|
+ * (exact maxima of the separable table), and for members that bound does not
+ * clear by the exact minimum over all (2N)^3 Gauss coordinates.  With
+ * kl_table the call synchronises `stream` (b, 16-byte aligned, is the check's
+ * scratch before it is written).  If a member fails, values and b are still
+ * written for every member and the call returns ENS_ERR_NONPOS_COEFF (the
+ * message names the member and its minimum); a NaN coefficient fails too. */
+int ens_assemble(const ens_graph *graph, const uint8_t *bmask, int s, int M, const double *kl_table,
                  const double *modes, const double *load, const double *xi, double sigma,
                  double kappa0, double *values, double *b, void *stream);
 
@@ -139,8 +151,9 @@ int ens_assemble(const ens_graph *graph, const uint8_t *bmask, int s, int M,
  * within 1e-14 of their row's diagonal for sigma = 0.1 (measured 4e-15).
  * values_df (float2[nnz*s], may be NULL): also writes the ENS_F64_DF split
  * of values, bitwise what ens_convert_values(..., ENS_F64_DF, ...) would
- * write, for ens_cg_df.  16-byte aligned for s > 1. */
-int ens_assemble_df(const ens_graph *graph, const uint8_t *bmask, int s, int M,
+ * write, for ens_cg_df.  16-byte aligned for s > 1.  kl_table: the
+ * coefficient check of ens_assemble (NULL: none). */
+int ens_assemble_df(const ens_graph *graph, const uint8_t *bmask, int s, int M, const double *kl_table,
                     const double *modes, const double *load, const double *xi, double sigma,
                     double kappa0, double *values, void *values_df, double *b, void *stream);
 
@@ -155,6 +168,18 @@ int ens_assemble_df(const ens_graph *graph, const uint8_t *bmask, int s, int M,
  * every s.  x, y, values 16-byte aligned when s > 1. */
 int ens_spmv(const ens_graph *graph, int s, int dtype, const void *values, const double *x,
              double *y, void *stream);
+
+/* ens_spmv with the values also given pre-split: values_df is their
+ * ENS_F64_DF copy (float2[nnz*s], written by ens_convert_values(...,
+ * ENS_F64_DF, ...) or ens_assemble_df) and values the FP64 originals.  The
+ * products and sums are the double-float terms of ENS_F64_DF without the
+ * per-term split of the values (the arithmetic of ens_cg_df's SpMV), x split
+ * on the fly; a row is bitwise the ENS_F64_DF result.  Rows that meet a value
+ * or an x outside the split range, a non-finite sum, or products below
+ * 2^-96 are recomputed from the FP64 values.  values_df 16-byte aligned
+ * (values, x, y too for s > 1). */
+int ens_spmv_df(const ens_graph *graph, int s, const double *values, const void *values_df,
+                const double *x, double *y, void *stream);
 
 /* ---------------------------------------------------------------- A5 dot */
 /* Per-member inner products (Sect. 3.4: the ensemble inner product computed

@@ -172,6 +172,11 @@ def kl_coeff_qp(N, M, xi, L=1.0, sigma=0.1, kappa0=1.0):
     return out.reshape(N ** 3, 8)
 
 
+def coeff_min(N, M, xi, L=1.0, sigma=0.1, kappa0=1.0):
+    """Smallest coefficient a(x_q) over every Gauss point of the N^3 mesh."""
+    return float(np.min(kl_coeff_qp(N, M, xi, L=L, sigma=sigma, kappa0=kappa0)))
+
+
 # -------------------------------------------------------------- assembly
 def element_matrix(h, a_q):
     a_q = _f64(a_q)
@@ -186,15 +191,26 @@ def element_load(h):
     return f
 
 
-def assemble(N, M, xi, row_map, col_entry, L=1.0, sigma=0.1, kappa0=1.0):
-    """values float64[nnz], b float64[n] of one sample (Algorithm 2)."""
+NONPOS_COEFF = 7   # or_assemble's status for a coefficient <= 0 (the library's ENS_ERR_NONPOS_COEFF)
+
+
+class NonPositiveCoefficient(ValueError):
+    """The sample's coefficient a(x_q) is not positive at some Gauss point."""
+
+
+def assemble(N, M, xi, row_map, col_entry, L=1.0, sigma=0.1, kappa0=1.0, check=True):
+    """values float64[nnz], b float64[n] of one sample (Algorithm 2).
+    check: raise NonPositiveCoefficient when a(x_q) <= 0 at a Gauss point."""
     row_map, col_entry = _i32(row_map), _i32(col_entry)
     xi = _f64(xi) if M > 0 else np.zeros(1)
     vals = np.empty(len(col_entry))
     b = np.empty(len(row_map) - 1)
     rc = lib().or_assemble(N, M, L, sigma, kappa0, _p(xi, _f64p), _p(row_map, _i32p),
                            _p(col_entry, _i32p), _p(vals, _f64p), _p(b, _f64p))
-    if rc:
+    if rc == NONPOS_COEFF:
+        if check:
+            raise NonPositiveCoefficient(f"coefficient not positive at some Gauss point (N={N}, M={M})")
+    elif rc:
         raise RuntimeError(f"or_assemble failed ({rc})")
     return vals, b
 

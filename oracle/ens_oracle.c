@@ -301,6 +301,11 @@ int or_assemble(int N, int M, double L, double sigma, double kappa0, const doubl
     or_node_index(N, ni);
     if (or_elem_graph(N, row_map, col_entry, eg)) { free(ni); free(eg); free(a_qp); free(bm); return 2; }
     or_kl_coeff_qp(N, M, L, sigma, kappa0, xi, a_qp);
+    /* Sect. 4: the diffusion coefficient must be positive for the problem to
+     * be elliptic (and the stiffness matrix SPD); report a(x_q) <= 0 or NaN */
+    int nonpos = 0;
+    for (int64_t i = 0; i < nc * 8; ++i)
+        if (!(a_qp[i] > 0.0)) nonpos = 1;
     or_bmask(N, bm);
     memset(values, 0, sizeof(double) * (size_t)nnz);
     memset(b, 0, sizeof(double) * (size_t)n);
@@ -324,7 +329,7 @@ int or_assemble(int N, int M, double L, double sigma, double kappa0, const doubl
         if (bm[I]) b[I] = 0.0;
     }
     free(ni); free(eg); free(a_qp); free(bm);
-    return 0;
+    return nonpos ? OR_NONPOS_COEFF : 0;
 }
 
 /* --------------------------------------------------------- linear algebra */
@@ -413,8 +418,15 @@ int or_solve_samples(int N, int M, double L, double sigma, double kappa0, int nu
         double *b = (double *)malloc(sizeof(double) * (size_t)n);
         double *x = (double *)calloc((size_t)n, sizeof(double));
         if (!vals || !b || !x) { err |= 1; free(vals); free(b); free(x); continue; }
-        err |= or_assemble(N, M, L, sigma, kappa0, xi + (int64_t)j * M, row_map, col, vals, b);
-        status[j] = or_cg(n, row_map, col, vals, b, x, tol, max_iter, &iters[j], &relres[j]);
+        const int ra = or_assemble(N, M, L, sigma, kappa0, xi + (int64_t)j * M, row_map, col, vals, b);
+        if (ra == OR_NONPOS_COEFF) {   /* not an elliptic problem: no solve */
+            status[j] = OR_NONPOS_COEFF;
+            iters[j] = 0;
+            relres[j] = 0.0;
+        } else {
+            err |= ra;
+            status[j] = or_cg(n, row_map, col, vals, b, x, tol, max_iter, &iters[j], &relres[j]);
+        }
         if (x_out) memcpy(x_out + (int64_t)j * n, x, sizeof(double) * (size_t)n);
         free(vals); free(b); free(x);
     }

@@ -62,7 +62,10 @@ int or_kl_coeff_qp(int N, int M, double L, double sigma, double kappa0,
 void or_element_matrix(double h, const double a_q[8], double K[64]);
 void or_element_load(double h, double f[8]);
 /* full assembly of one sample, Dirichlet u = 0 applied by symmetric
- * elimination; values[num_entries], b[num_rows]; returns 0 */
+ * elimination; values[num_entries], b[num_rows].  Returns 0, or
+ * OR_NONPOS_COEFF when the coefficient is not positive (or NaN) at some
+ * Gauss point (values and b are written all the same). */
+#define OR_NONPOS_COEFF 7
 int or_assemble(int N, int M, double L, double sigma, double kappa0,
                 const double *xi, const int32_t *row_map, const int32_t *col_entry,
                 double *values, double *b);

@@ -107,9 +107,10 @@ def _declare(L):
         "ens_kl_table_size": (I, [I, I, P(i64)]),
         "ens_kl_setup": (I, [I, I, d, vp, vp, vp, vp]),
         "ens_mode_matrices": (I, [I, P(EnsGraphC), I, vp, vp, vp, vp]),
-        "ens_assemble": (I, [P(EnsGraphC), vp, I, I, vp, vp, vp, d, d, vp, vp, vp]),
-        "ens_assemble_df": (I, [P(EnsGraphC), vp, I, I, vp, vp, vp, d, d, vp, vp, vp, vp]),
+        "ens_assemble": (I, [P(EnsGraphC), vp, I, I, vp, vp, vp, vp, d, d, vp, vp, vp]),
+        "ens_assemble_df": (I, [P(EnsGraphC), vp, I, I, vp, vp, vp, vp, d, d, vp, vp, vp, vp]),
         "ens_spmv": (I, [P(EnsGraphC), I, I, vp, vp, vp, vp]),
+        "ens_spmv_df": (I, [P(EnsGraphC), I, vp, vp, vp, vp, vp]),
         "ens_dot_workspace_size": (I, [i64, I, P(sz)]),
         "ens_dot": (I, [i64, I, vp, vp, vp, vp, sz, vp]),
         "ens_dot_static": (I, [i64, I, vp, vp, vp, vp]),
@@ -246,26 +247,35 @@ def mode_matrices(N, graph, M, kl_table, modes, load, stream=None):
 
 
 def assemble(graph, bmask, s, M, modes, load, xi, sigma, kappa0, values, b, stream=None, df=False,
-             values_df=None):
+             values_df=None, kl_table=None):
     """ens_assemble; df=True (or a values_df tensor, 2*nnz*s float32) runs
-    ens_assemble_df, which also writes the pre-split copy into values_df."""
-    _require_cuda(bmask, modes, load, xi, values, b, values_df)
+    ens_assemble_df, which also writes the pre-split copy into values_df.
+    kl_table (the mesh's ens_kl_setup table) turns on the coefficient
+    positivity check: EnsError(7) when a member's a(x_q) <= 0 somewhere (the
+    values are still written)."""
+    _require_cuda(bmask, modes, load, xi, values, b, values_df, kl_table)
     if df or values_df is not None:
-        _check(lib().ens_assemble_df(graph.ref(), _ptr(bmask), s, M, _ptr(modes), _ptr(load), _ptr(xi),
-                                     sigma, kappa0, _ptr(values), _ptr(values_df), _ptr(b), _stream(stream)))
+        _check(lib().ens_assemble_df(graph.ref(), _ptr(bmask), s, M, _ptr(kl_table), _ptr(modes), _ptr(load),
+                                     _ptr(xi), sigma, kappa0, _ptr(values), _ptr(values_df), _ptr(b),
+                                     _stream(stream)))
     else:
-        _check(lib().ens_assemble(graph.ref(), _ptr(bmask), s, M, _ptr(modes), _ptr(load), _ptr(xi),
-                                  sigma, kappa0, _ptr(values), _ptr(b), _stream(stream)))
+        _check(lib().ens_assemble(graph.ref(), _ptr(bmask), s, M, _ptr(kl_table), _ptr(modes), _ptr(load),
+                                  _ptr(xi), sigma, kappa0, _ptr(values), _ptr(b), _stream(stream)))
 
 
 # ------------------------------------------------------------ linear algebra
 _DT = {"float64": F64, "float32": F32, "bfloat16": BF16}
 
 
-def spmv(graph, s, values, x, y, stream=None, df=False, split=False):
+def spmv(graph, s, values, x, y, stream=None, df=False, split=False, values_df=None):
     """y = A_c x.  float64 values: df=True -> double-float arithmetic (ENS_F64_DF),
-    split=True -> alternate entries FP64 / double-float (ENS_F64_SPLIT)."""
-    _require_cuda(values, x, y)
+    split=True -> alternate entries FP64 / double-float (ENS_F64_SPLIT),
+    values_df (the ENS_F64_DF split copy of values) -> ens_spmv_df."""
+    _require_cuda(values, x, y, values_df)
+    if values_df is not None:
+        _check(lib().ens_spmv_df(graph.ref(), s, _ptr(values), _ptr(values_df), _ptr(x), _ptr(y),
+                                 _stream(stream)))
+        return
     dt = _DT[str(values.dtype).replace("torch.", "")]
     if df or split:
         if dt != F64:
@@ -791,9 +801,10 @@ class Mesh:
         mode_matrices(N, self.graph, M, self.kl_table, self.modes, self.load, stream)
 
     def assemble(self, s, xi_ens, sigma=0.1, kappa0=1.0, values=None, b=None, stream=None, df=False,
-                 values_df=None):
+                 values_df=None, check=True):
         """xi_ens: device float64[M*s] (commuted layout).  Returns (values, b).
-        df / values_df: see assemble()."""
+        df / values_df: see assemble().  check: the coefficient positivity
+        check with this mesh's KL table (synchronises the stream)."""
         import torch
         dev = self.row_map.device
         if values is None:
@@ -801,5 +812,5 @@ class Mesh:
         if b is None:
             b = torch.empty(self.n * s, dtype=torch.float64, device=dev)
         assemble(self.graph, self.bmask, s, self.M, self.modes, self.load, xi_ens, sigma, kappa0,
-                 values, b, stream, df=df, values_df=values_df)
+                 values, b, stream, df=df, values_df=values_df, kl_table=self.kl_table if check else None)
         return values, b

@@ -9,6 +9,9 @@
 // remains per ensemble is M+1 fused multiply-adds per value, with the
 // ensemble dimension contiguous so each mode value is read once per entry and
 // used by all s members, and the output written as packed 16-byte stores.
+#include <math.h>
+#include <string.h>
+
 #include <algorithm>
 
 #include "ens_spmv.cuh"
@@ -260,6 +263,142 @@ static unsigned asm_df_grid() {
     return g;
 }
 
+// ------------------------------------------------ coefficient positivity
+// Member e's coefficient at a Gauss point is
+//     a_e(x_q) = kappa0 + sigma * sum_k xi[k*s + e] * kappa_k(x_q),
+// kappa_k(x_q) = T[0][k][tx] * T[1][k][ty] * T[2][k][tz] (the separable table
+// of ens_kl_setup, T[d][k][t] at kl_table[(d*M + k)*2N + t]).  The stiffness
+// matrix is SPD only if a_e > 0 at every Gauss point (Sect. 4's coefficient
+// is positive by construction for bounded xi and small sigma).
+//   Bound: max_q |kappa_k(x_q)| = prod_d max_t |T[d][k][t]| exactly, so
+//     kappa0 - |sigma| * sum_k |xi_k^e| * max_q |kappa_k|  <=  min_q a_e(x_q).
+//   Exact: for members whose bound is not positive, the minimum of a_e over all
+//     (2N)^3 Gauss coordinates, each evaluated as the sum over k in increasing
+//     k of kappa_k * xi_k, then kappa0 + sigma * sum (no fused operations).
+// One CTA: the bound of every member into out[e].
+__global__ void coeff_bound_kernel(int N, int M, const double *__restrict__ T, int s,
+                                   const double *__restrict__ xi, double sigma, double kappa0,
+                                   double *__restrict__ out) {
+    __shared__ double cmax[64];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int nt = 2 * N;
+    for (int k = warp; k < M; k += nw) {
+        double prod = 1.0;
+        for (int d = 0; d < 3; ++d) {
+            double m = 0.0;
+            for (int t = lane; t < nt; t += 32) {
+                const double v = fabs(T[((int64_t)d * M + k) * nt + t]);
+                m = (v > m || v != v) ? v : m;   // a NaN entry propagates
+            }
+            for (int o = 16; o >= 1; o >>= 1) {
+                const double w = __shfl_xor_sync(0xffffffffu, m, o);
+                m = (w > m || w != w) ? w : m;
+            }
+            prod *= m;
+        }
+        if (lane == 0) cmax[k] = prod;
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < s; e += blockDim.x) {
+        double sum = 0.0;
+        for (int k = 0; k < M; ++k) sum += fabs(xi[(int64_t)k * s + e]) * cmax[k];
+        out[e] = kappa0 - fabs(sigma) * sum;
+    }
+}
+
+// order-preserving key of a double for atomicMin (NaN maps below -inf)
+__device__ __forceinline__ unsigned long long order_key(double v) {
+    if (v != v) return 0ull;
+    const unsigned long long u = (unsigned long long)__double_as_longlong(v);
+    return (u >> 63) ? ~u : (u | 0x8000000000000000ull);
+}
+
+// Exact minimum of a_e over the Gauss points, members with need[e] != 0:
+// thread per Gauss point (grid-stride), warp minimum, then atomicMin on the
+// ordered key in key_out[e] (which the host set to all ones).
+__global__ void __launch_bounds__(256) coeff_min_kernel(int N, int M, const double *__restrict__ T, int s,
+                                                        const double *__restrict__ xi, double sigma,
+                                                        double kappa0, const int *__restrict__ need,
+                                                        unsigned long long *__restrict__ key_out) {
+    const int64_t nt = 2 * N, npts = nt * nt * nt;
+    for (int e = 0; e < s; ++e) {
+        if (!need[e]) continue;
+        unsigned long long best = ~0ull;
+        for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < npts;
+             q += (int64_t)gridDim.x * blockDim.x) {
+            const int64_t tx = q % nt, ty = (q / nt) % nt, tz = q / (nt * nt);
+            double sum = 0.0;
+            for (int k = 0; k < M; ++k) {
+                const double kap = __dmul_rn(__dmul_rn(__ldg(T + (int64_t)k * nt + tx),
+                                                       __ldg(T + ((int64_t)M + k) * nt + ty)),
+                                             __ldg(T + ((int64_t)2 * M + k) * nt + tz));
+                sum = __dadd_rn(sum, __dmul_rn(kap, __ldg(xi + (int64_t)k * s + e)));
+            }
+            const unsigned long long key = order_key(__dadd_rn(kappa0, __dmul_rn(sigma, sum)));
+            best = key < best ? key : best;
+        }
+        for (int o = 16; o >= 1; o >>= 1) {
+            const unsigned long long w = __shfl_xor_sync(0xffffffffu, best, o);
+            best = w < best ? w : best;
+        }
+        if ((threadIdx.x & 31) == 0 && best != ~0ull) atomicMin(key_out + e, best);
+    }
+}
+
+static double key_to_double(unsigned long long k) {
+    if (k == 0ull) return NAN;
+    const unsigned long long u = (k >> 63) ? (k & 0x7fffffffffffffffull) : ~k;
+    double v;
+    memcpy(&v, &u, sizeof v);
+    return v;
+}
+
+// Host: the positivity check of ens_assemble (synchronises the stream).
+// Returns ENS_OK with *bad_member = -1 when every member's coefficient is
+// positive at every Gauss point, else the first failing member and its
+// minimum.  scratch: device memory of at least 16*s bytes (the call's b).
+static int coeff_check(const ens_graph *g, int M, const double *kl_table, int s, const double *xi,
+                       double sigma, double kappa0, void *scratch, int *bad_member, double *bad_min,
+                       cudaStream_t st) {
+    *bad_member = -1;
+    *bad_min = 0.0;
+    const double cn = cbrt((double)g->num_rows);
+    const int N = (int)llround(cn) - 1;
+    if (N < 1 || (int64_t)(N + 1) * (N + 1) * (N + 1) != (int64_t)g->num_rows)
+        return fail(ENS_ERR_ARG, "kl_table given but num_rows=%d is not (N+1)^3", g->num_rows);
+    if (M == 0) {
+        if (!(kappa0 > 0.0)) { *bad_member = 0; *bad_min = kappa0; }
+        return ENS_OK;
+    }
+    double *bound = static_cast<double *>(scratch);
+    coeff_bound_kernel<<<1, 256, 0, st>>>(N, M, kl_table, s, xi, sigma, kappa0, bound);
+    ENS_LAUNCH_CHECK("coeff_bound_kernel");
+    double hb[32];
+    ENS_CUDA_TRY(cudaMemcpyAsync(hb, bound, sizeof(double) * s, cudaMemcpyDeviceToHost, st));
+    ENS_CUDA_TRY(cudaStreamSynchronize(st));
+    int need[32], any = 0;
+    for (int e = 0; e < s; ++e) { need[e] = !(hb[e] > 0.0); any |= need[e]; }
+    if (!any) return ENS_OK;
+    // exact minimum for the members the bound does not clear
+    unsigned long long *keys = static_cast<unsigned long long *>(scratch);
+    int *dneed = reinterpret_cast<int *>(keys + s);
+    ENS_CUDA_TRY(cudaMemsetAsync(keys, 0xff, sizeof(unsigned long long) * s, st));
+    ENS_CUDA_TRY(cudaMemcpyAsync(dneed, need, sizeof(int) * s, cudaMemcpyHostToDevice, st));
+    const int64_t npts = (int64_t)8 * N * N * N;
+    const unsigned grid = (unsigned)std::min<int64_t>((npts + 255) / 256, 152 * 8);
+    coeff_min_kernel<<<grid, 256, 0, st>>>(N, M, kl_table, s, xi, sigma, kappa0, dneed, keys);
+    ENS_LAUNCH_CHECK("coeff_min_kernel");
+    unsigned long long hk[32];
+    ENS_CUDA_TRY(cudaMemcpyAsync(hk, keys, sizeof(unsigned long long) * s, cudaMemcpyDeviceToHost, st));
+    ENS_CUDA_TRY(cudaStreamSynchronize(st));
+    for (int e = 0; e < s; ++e) {
+        if (!need[e]) continue;
+        const double amin = key_to_double(hk[e]);
+        if (!(amin > 0.0)) { *bad_member = e; *bad_min = amin; break; }
+    }
+    return ENS_OK;
+}
+
 template <int S>
 static int assemble_s(const ens_graph *g, const uint8_t *bmask, int M, const double *modes,
                       const double *load, const double *xi, double sigma, double kappa0,
@@ -285,9 +424,9 @@ static int assemble_s(const ens_graph *g, const uint8_t *bmask, int M, const dou
     return ENS_OK;
 }
 
-static int assemble_entry(const ens_graph *graph, const uint8_t *bmask, int s, int M, const double *modes,
-                          const double *load, const double *xi, double sigma, double kappa0, double *values,
-                          double *b, bool df, float2 *vdf, void *stream) {
+static int assemble_entry(const ens_graph *graph, const uint8_t *bmask, int s, int M, const double *kl_table,
+                          const double *modes, const double *load, const double *xi, double sigma,
+                          double kappa0, double *values, double *b, bool df, float2 *vdf, void *stream) {
     int rc = check_graph(graph);
     if (rc) return rc;
     if (!supported_s(s)) return fail(ENS_ERR_UNSUPPORTED, "ensemble size s=%d not in {1,4,8,16,32}", s);
@@ -297,30 +436,42 @@ static int assemble_entry(const ens_graph *graph, const uint8_t *bmask, int s, i
     if (s > 1 && (!aligned16(values) || !aligned16(b) || (vdf && !aligned16(vdf))))
         return fail(ENS_ERR_ALIGN, "values/b/values_df must be 16-byte aligned");
     cudaStream_t st = as_stream(stream);
-    switch (s) {
-        case 1: return assemble_s<1>(graph, bmask, M, modes, load, xi, sigma, kappa0, values, b, df, vdf, st);
-        case 4: return assemble_s<4>(graph, bmask, M, modes, load, xi, sigma, kappa0, values, b, df, vdf, st);
-        case 8: return assemble_s<8>(graph, bmask, M, modes, load, xi, sigma, kappa0, values, b, df, vdf, st);
-        case 16: return assemble_s<16>(graph, bmask, M, modes, load, xi, sigma, kappa0, values, b, df, vdf, st);
-        default: return assemble_s<32>(graph, bmask, M, modes, load, xi, sigma, kappa0, values, b, df, vdf, st);
+    int bad = -1;
+    double bad_min = 0.0;
+    if (kl_table && graph->num_rows > 0) {   // b (n*s doubles, n >= 8) is the check's scratch
+        if (!aligned16(b)) return fail(ENS_ERR_ALIGN, "b must be 16-byte aligned when kl_table is given");
+        if ((rc = coeff_check(graph, M, kl_table, s, xi, sigma, kappa0, b, &bad, &bad_min, st))) return rc;
     }
+    switch (s) {
+        case 1: rc = assemble_s<1>(graph, bmask, M, modes, load, xi, sigma, kappa0, values, b, df, vdf, st); break;
+        case 4: rc = assemble_s<4>(graph, bmask, M, modes, load, xi, sigma, kappa0, values, b, df, vdf, st); break;
+        case 8: rc = assemble_s<8>(graph, bmask, M, modes, load, xi, sigma, kappa0, values, b, df, vdf, st); break;
+        case 16: rc = assemble_s<16>(graph, bmask, M, modes, load, xi, sigma, kappa0, values, b, df, vdf, st); break;
+        default: rc = assemble_s<32>(graph, bmask, M, modes, load, xi, sigma, kappa0, values, b, df, vdf, st); break;
+    }
+    if (rc) return rc;
+    if (bad >= 0)
+        return fail(ENS_ERR_NONPOS_COEFF, "member %d: coefficient a(x_q) = %.17g <= 0 at a Gauss point "
+                    "(values and b written; the matrix is not SPD)", bad, bad_min);
+    return ENS_OK;
 }
 
 }  // namespace ens
 
 using namespace ens;
 
-extern "C" int ens_assemble(const ens_graph *graph, const uint8_t *bmask, int s, int M,
+extern "C" int ens_assemble(const ens_graph *graph, const uint8_t *bmask, int s, int M, const double *kl_table,
                             const double *modes, const double *load, const double *xi,
                             double sigma, double kappa0, double *values, double *b,
                             void *stream) {
-    return assemble_entry(graph, bmask, s, M, modes, load, xi, sigma, kappa0, values, b, false, nullptr, stream);
+    return assemble_entry(graph, bmask, s, M, kl_table, modes, load, xi, sigma, kappa0, values, b, false, nullptr,
+                          stream);
 }
 
-extern "C" int ens_assemble_df(const ens_graph *graph, const uint8_t *bmask, int s, int M,
+extern "C" int ens_assemble_df(const ens_graph *graph, const uint8_t *bmask, int s, int M, const double *kl_table,
                                const double *modes, const double *load, const double *xi,
                                double sigma, double kappa0, double *values, void *values_df, double *b,
                                void *stream) {
-    return assemble_entry(graph, bmask, s, M, modes, load, xi, sigma, kappa0, values, b, true,
+    return assemble_entry(graph, bmask, s, M, kl_table, modes, load, xi, sigma, kappa0, values, b, true,
                           static_cast<float2 *>(values_df), stream);
 }

@@ -398,22 +398,44 @@ __global__ void __launch_bounds__(RowMap<S>::THREADS, K1Occ<S, MODE>::THREADS_PE
 // ------------------------------------------------------------------ K2
 // v*v of an FP64 value as an unevaluated float pair: v split by truncation
 // into hi + lo (47 bits), hi*hi exact by FMA error recovery, 2 hi lo added to
-// the error term (lo*lo, below 2^-46 |v*v|, is dropped); values outside the
-// split range square in FP64 and round to a pair (out of line, so that the
-// FP64 instructions stay off the common path)
-static __device__ __noinline__ float2 df_square_wide(double v) {
-    const double q = v * v;
-    const float qh = (float)q;
-    return make_float2(qh, (float)(q - (double)qh));
-}
-
+// the error term (lo*lo, below 2^-46 |v*v|, is dropped).  Exact and free of
+// FP32 underflow and overflow only for |v| in [2^-50, 2^60): hi*hi is then at
+// least 2^-100 (its error term is a normal float) and a chunk's 32 squares
+// stay below 2^125.  Zero squares to (0, 0); any other v outside that range
+// returns (NaN, 0), which marks its (chunk, member) column for the FP64 sum
+// of k2_chunk_rr_fp64.  Integer and FP32 instructions only.
 __device__ __forceinline__ float2 df_square(double v) {
+    const uint32_t uh = (uint32_t)__double2hiint(v), ul = (uint32_t)__double2loint(v);
+    const uint32_t E = (uh >> 20) & 0x7ffu;
+    if (E - 973u > 109u) {  // biased exponent outside [973, 1082]: |v| outside [2^-50, 2^60)
+        const bool zero = ((uh << 1) | ul) == 0u;
+        return make_float2(zero ? 0.0f : __int_as_float(0x7fc00000), 0.0f);
+    }
     float hi, lo;
-    if (!df_split_trunc(v, hi, lo)) return df_square_wide(v);
+    df_split_trunc(v, hi, lo);
     const float p = __fmul_rn(hi, hi);
     float e = __fmaf_rn(hi, hi, -p);
     e = __fmaf_rn(2.0f * hi, lo, e);
     return make_float2(p, e);
+}
+
+// FP64 r.r of one (chunk, member) column whose float-pair sum was marked
+// (a value outside the float-pair range): the 32 rows' r, squared in FP64 and
+// combined by the same halving tree (v[i] += v[i + h], h = 16..1).  Called by
+// one thread after a barrier that orders the CTA's r stores before it.
+static __device__ __noinline__ double k2_chunk_rr_fp64(const double *r, int64_t n, int64_t chunk, int e, int S) {
+    double v[32];
+#pragma unroll
+    for (int i = 0; i < 32; ++i) {
+        const int64_t R = chunk * 32 + i;
+        const double x = (R < n) ? r[R * S + e] : 0.0;
+        v[i] = x * x;
+    }
+#pragma unroll
+    for (int h = 16; h >= 1; h >>= 1)
+#pragma unroll
+        for (int i = 0; i < h; ++i) v[i] += v[i + h];
+    return v[0];
 }
 
 // (a.x + a.y) + (b.x + b.y) as a float pair: TwoSum of the leading parts,
@@ -479,7 +501,11 @@ __device__ __forceinline__ void k2_body(const CgArgs &a, int cta,
     for (int it = threadIdx.x; it < VM::CPC * S; it += VM::THREADS) {
         const int c = it / S, e = it % S;
         const int64_t ch = first_chunk + c;
-        if (ch < a.t1.count[1]) a.t1.buf[1][ch * S + e] = f2d_exact(sf[c][0][e].x) + f2d_exact(sf[c][0][e].y);
+        if (ch < a.t1.count[1]) {
+            const float2 t = sf[c][0][e];
+            a.t1.buf[1][ch * S + e] = (t.x == t.x) ? f2d_exact(t.x) + f2d_exact(t.y)
+                                                   : k2_chunk_rr_fp64(a.r, a.n, ch, e, S);
+        }
     }
     const int nitems = (int)min((int64_t)VM::CPC, a.t1.count[1] - first_chunk);
     if (!dot_tree_propagate(a.t1, first_chunk, nitems)) return;

@@ -9,9 +9,14 @@
 // ENS_DOT_STATIC_MAX_BYTES bytes instead of a caller workspace.  Every GPU
 // that loads this library holds that array until the process exits.
 //
-// The device address of the array is looked up once per device, on the first
-// call made with that device current (cudaGetSymbolAddress), so that first call
-// should come before any stream capture.  All calls share the one array and it
+// The device address of the array is looked up once per device and context,
+// on the first call made with that device current (cudaGetSymbolAddress), so
+// that first call should come before any stream capture.  The cached address
+// is keyed on the current context's unique ID as well (cuCtxGetId, reached
+// through cudaGetDriverEntryPointByVersion, so the library needs no link
+// against the driver): after a device reset, or any other change of the
+// primary context, the next call looks the address up again instead of using
+// an address of the destroyed context.  All calls share the one array and it
 // keeps the previous call's contents; the call clears the arrival counters it
 // needs before launching, and calls that overlap on the GPU (different
 // streams, or different host threads, at the same time) race on it.
@@ -29,18 +34,48 @@ static __device__ __align__(256) unsigned char g_dot_static_scratch[ENS_DOT_STAT
 constexpr int kMaxDevices = 64;
 static std::mutex g_static_mu;
 static void *g_static_ptr[kMaxDevices] = {};
+static unsigned long long g_static_ctx[kMaxDevices] = {};
 
-// device address of the scratch array on the current device (set up once)
+// unique ID of the calling thread's current context (0 if the driver entry
+// points are not available; the cache is then per device only)
+typedef int (*CtxGetCurrentFn)(void **ctx);
+typedef int (*CtxGetIdFn)(void *ctx, unsigned long long *id);
+static unsigned long long current_context_id() {
+    static CtxGetCurrentFn get_current = nullptr;
+    static CtxGetIdFn get_id = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void *f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_current = reinterpret_cast<CtxGetCurrentFn>(f);
+        f = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_id = reinterpret_cast<CtxGetIdFn>(f);
+    });
+    if (!get_current || !get_id) return 0ull;
+    void *ctx = nullptr;
+    unsigned long long id = 0ull;
+    if (get_current(&ctx) != 0 || !ctx || get_id(ctx, &id) != 0) return 0ull;
+    return id;
+}
+
+// device address of the scratch array on the current device and context
+// (looked up on the first call, and again when the context has changed)
 static int static_scratch(void **out) {
     int dev = -1;
     ENS_CUDA_TRY(cudaGetDevice(&dev));
     if (dev < 0 || dev >= kMaxDevices) return fail(ENS_ERR_UNSUPPORTED, "device ordinal %d", dev);
+    const unsigned long long ctx = current_context_id();
     std::lock_guard<std::mutex> lock(g_static_mu);
-    if (!g_static_ptr[dev]) {
+    if (!g_static_ptr[dev] || ctx == 0ull || g_static_ctx[dev] != ctx) {
         void *p = nullptr;
-        cudaError_t e = cudaGetSymbolAddress(&p, g_dot_static_scratch);
+        cudaError_t e = cudaGetSymbolAddress(&p, g_dot_static_scratch);   // also makes the primary context current
         if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(ens_dot_static scratch)");
         g_static_ptr[dev] = p;
+        g_static_ctx[dev] = ctx ? ctx : current_context_id();
     }
     *out = g_static_ptr[dev];
     return ENS_OK;

@@ -59,6 +59,39 @@ __global__ void __launch_bounds__(RowMap<S>::THREADS, 1024 / RowMap<S>::THREADS)
     }
 }
 
+// pre-split double-float values (ENS_F64_DF copy) with their FP64 originals;
+// x FP64, split on the fly; the value block of each chunk prefetched into L2
+// as in the CG's SpMV
+template <int S>
+__global__ void __launch_bounds__(RowMap<S>::THREADS, 1536 / RowMap<S>::THREADS) spmv_dfv_kernel(
+    int32_t n, const int32_t *__restrict__ row_map, const int32_t *__restrict__ col,
+    const double *__restrict__ vals, const float2 *__restrict__ vdf, uint64_t vdf_bytes,
+    const double *__restrict__ x, double *__restrict__ y) {
+    constexpr int G = RowMap<S>::G;
+    __shared__ ChunkCols cc;
+    const int r = threadIdx.x / G, g = threadIdx.x % G;
+    const int64_t R = (int64_t)blockIdx.x * 32 + r;
+    const bool staged = stage_chunk_pf(cc, row_map, col, blockIdx.x, n, vdf, S * 8u, vdf_bytes, 0xffffffffu);
+    const double2 v = chunk_spmv_dfv<S, XSplit>(cc, staged, col, vdf, vals, x, r, g, R < n);
+    if (R >= n) return;
+    if constexpr (S == 1) {
+        if (g == 0) y[R] = v.x;
+    } else {
+        reinterpret_cast<double2 *>(y)[R * G + g] = v;
+    }
+}
+
+template <int S>
+static int spmv_dfv_s(const ens_graph *g, const double *vals, const float2 *vdf, const double *x, double *y,
+                      cudaStream_t st) {
+    const int64_t chunks = ((int64_t)g->num_rows + 31) / 32;
+    if (chunks == 0) return ENS_OK;
+    spmv_dfv_kernel<S><<<(unsigned)chunks, RowMap<S>::THREADS, 0, st>>>(
+        g->num_rows, g->row_map, g->col_entry, vals, vdf, (uint64_t)g->num_entries * S * 8u, x, y);
+    ENS_LAUNCH_CHECK("spmv_dfv_kernel");
+    return ENS_OK;
+}
+
 template <int S>
 static int spmv_split_s(const ens_graph *g, const double *vals, const double *x, double *y,
                         cudaStream_t st) {
@@ -206,6 +239,26 @@ extern "C" int ens_spmv(const ens_graph *graph, int s, int dtype, const void *va
         case ENS_F64_DF: return spmv_df_dispatch(graph, s, values, x, y, st);
         case ENS_F64_SPLIT: return spmv_split_dispatch(graph, s, values, x, y, st);
         default: return fail(ENS_ERR_UNSUPPORTED, "dtype %d", dtype);
+    }
+}
+
+extern "C" int ens_spmv_df(const ens_graph *graph, int s, const double *values, const void *values_df,
+                           const double *x, double *y, void *stream) {
+    int rc = check_graph(graph);
+    if (rc) return rc;
+    if (!supported_s(s)) return fail(ENS_ERR_UNSUPPORTED, "ensemble size s=%d not in {1,4,8,16,32}", s);
+    if (graph->num_rows > 0 && (!values || !values_df || !x || !y))
+        return fail(ENS_ERR_ARG, "NULL values/values_df/x/y");
+    if (!aligned16(values_df) || (s > 1 && (!aligned16(values) || !aligned16(x) || !aligned16(y))))
+        return fail(ENS_ERR_ALIGN, "values_df (and values/x/y for s > 1) must be 16-byte aligned");
+    const float2 *vdf = static_cast<const float2 *>(values_df);
+    cudaStream_t st = as_stream(stream);
+    switch (s) {
+        case 1: return spmv_dfv_s<1>(graph, values, vdf, x, y, st);
+        case 4: return spmv_dfv_s<4>(graph, values, vdf, x, y, st);
+        case 8: return spmv_dfv_s<8>(graph, values, vdf, x, y, st);
+        case 16: return spmv_dfv_s<16>(graph, values, vdf, x, y, st);
+        default: return spmv_dfv_s<32>(graph, values, vdf, x, y, st);
     }
 }
 

@@ -23,7 +23,12 @@
 //    arithmetic, 1971).  About 27 FP32/INT ops per term on the 128/cycle/SM
 //    pipes; error per term <= ~6*2^-48 |a x|, so a row is within
 //    ~1.2e-13 * sum |a_j x_j| of the exact value.  Values outside
-//    [2^-103, 2^128) and non-finite values take an FP64 FMA instead.
+//    [2^-103, 2^128) and non-finite values take an FP64 FMA instead.  The
+//    float-pair error terms are exact only while the products stay in FP32's
+//    normal range, so each member also tracks max |a_j x_j| (in FP32); a
+//    member whose largest product lies in (0, 2^-96) is recomputed with FP64
+//    FMAs (rows where every product is below 2^-149 return 0, an absolute
+//    error below 27 * 2^-149).
 #pragma once
 #include "ens_internal.cuh"
 
@@ -285,12 +290,30 @@ __device__ __forceinline__ void df_term_pre(DfAcc &A, float ah, float al, float 
     A.c = __fadd_rn(A.c, __fadd_rn(t, e));
 }
 
+// df_term_pre that also keeps mx = max |ah*xh| of the member's terms
+__device__ __forceinline__ void df_term_pm(DfAcc &A, float &mx, float ah, float al, float xh, float xl) {
+    const float p = __fmul_rn(ah, xh);
+    mx = fmaxf(mx, fabsf(p));
+    float e = __fmaf_rn(ah, xh, -p);
+    e = __fmaf_rn(ah, xl, e);
+    e = __fmaf_rn(al, xh, e);
+    float s, t;
+    two_sum(A.s, p, s, t);
+    A.s = s;
+    A.c = __fadd_rn(A.c, __fadd_rn(t, e));
+}
+
+// a member's float-pair products reached below FP32's normal range: its
+// largest |a_j x_j| is positive but under 2^-96 (then every error term may
+// have lost bits to underflow)
+__device__ __forceinline__ bool df_tiny(float mx) { return mx > 0.0f && mx < 0x1p-96f; }
+
 // one term a*(xh + xl) into A; returns false when a needs the FP64 path
 // (the term then contributes nothing here and is added by df_fixup)
-__device__ __forceinline__ bool df_term(DfAcc &A, double a, float xh, float xl) {
+__device__ __forceinline__ bool df_term(DfAcc &A, float &mx, double a, float xh, float xl) {
     float ah, al;
     const bool ok = df_split_trunc(a, ah, al);
-    df_term_pre(A, ah, al, xh, xl);
+    df_term_pm(A, mx, ah, al, xh, xl);
     return ok;
 }
 
@@ -319,20 +342,53 @@ struct XPre {
         return __ldg(reinterpret_cast<const float4 *>(x + i));
     }
     __device__ __forceinline__ static float2 one(ptr x, int64_t i) { return __ldg(x + i); }
+    // hi + lo of element i, exact in FP64
+    __device__ __forceinline__ static double dbl(ptr x, int64_t i) {
+        const float2 h = __ldg(x + i);
+        return (double)h.x + (double)h.y;
+    }
 };
+// An x outside the split range (or not finite) is returned with a NaN leading
+// part, so that its products make the row's sum non-finite and the row falls
+// back to FP64 (row_fp64_member / split_odd_fp64 read the FP64 x).
 struct XSplit {
     using ptr = const double *;
     __device__ __forceinline__ static float4 two(ptr x, int64_t i) {
         const double2 v = ld_x2(x, i);
-        bool ok;
-        const float2 a = df_split_vec(v.x, ok), b = df_split_vec(v.y, ok);
-        return make_float4(a.x, a.y, b.x, b.y);
+        bool ok0, ok1;
+        const float2 a = df_split_vec(v.x, ok0), b = df_split_vec(v.y, ok1);
+        const float qnan = __int_as_float(0x7fc00000);
+        return make_float4(ok0 ? a.x : qnan, a.y, ok1 ? b.x : qnan, b.y);
     }
     __device__ __forceinline__ static float2 one(ptr x, int64_t i) {
         bool ok;
-        return df_split_vec(__ldg(x + i), ok);
+        const float2 a = df_split_vec(__ldg(x + i), ok);
+        return make_float2(ok ? a.x : __int_as_float(0x7fc00000), a.y);
+    }
+    __device__ __forceinline__ static double dbl(ptr x, int64_t i) {
+        bool ok;
+        const float2 h = df_split_vec(__ldg(x + i), ok);
+        return ok ? (double)h.x + (double)h.y : __ldg(x + i);
     }
 };
+
+// FP64 value of member mm of a row with entries [rs, re) against the split x
+// (hi + lo, exact in FP64; FP64 x where the split is out of range): entry j to
+// partial (j - rs) mod 2, each partial in increasing j, row value p0 + p1 --
+// the order of every other form.  Used for members whose float-pair products
+// fell below FP32's normal range (rare).
+template <int S, typename XS, typename CA>
+__device__ __noinline__ double row_fp64_member(CA colf, int rs, int re, const double *__restrict__ vals,
+                                               typename XS::ptr x, int mm) {
+    double p0 = 0.0, p1 = 0.0;
+    for (int j = rs; j < re; ++j) {
+        const double t = ValLoad<double>::one(vals, (int64_t)j * S + mm);
+        const double xv = XS::dbl(x, (int64_t)colf(j) * S + mm);
+        if ((j - rs) & 1) p1 = fma(t, xv, p1);
+        else p0 = fma(t, xv, p0);
+    }
+    return p0 + p1;
+}
 
 // FP64 sum, in entry order, of the terms whose value is outside the split
 // range (rare: run only by rows that met one)
@@ -359,6 +415,7 @@ __device__ __forceinline__ double2 row_spmv2_df(CA colf, int rs, int re,
                                                 const double *__restrict__ vals,
                                                 typename XS::ptr __restrict__ x, int g) {
     DfAcc a0 = df_zero(), a1 = df_zero(), b0 = df_zero(), b1 = df_zero();
+    float ma = 0.0f, mb = 0.0f;  // max |product| of members m, m+1
     bool ok = true;
     const int m = 2 * g;
     int j = rs;
@@ -372,20 +429,25 @@ __device__ __forceinline__ double2 row_spmv2_df(CA colf, int rs, int re,
         const float4 x1 = XS::two(x, (int64_t)c1 * S + m);
         const float4 x2 = XS::two(x, (int64_t)c2 * S + m);
         const float4 x3 = XS::two(x, (int64_t)c3 * S + m);
-        ok &= df_term(a0, v0.x, x0.x, x0.y); ok &= df_term(b0, v0.y, x0.z, x0.w);
-        ok &= df_term(a1, v1.x, x1.x, x1.y); ok &= df_term(b1, v1.y, x1.z, x1.w);
-        ok &= df_term(a0, v2.x, x2.x, x2.y); ok &= df_term(b0, v2.y, x2.z, x2.w);
-        ok &= df_term(a1, v3.x, x3.x, x3.y); ok &= df_term(b1, v3.y, x3.z, x3.w);
+        ok &= df_term(a0, ma, v0.x, x0.x, x0.y); ok &= df_term(b0, mb, v0.y, x0.z, x0.w);
+        ok &= df_term(a1, ma, v1.x, x1.x, x1.y); ok &= df_term(b1, mb, v1.y, x1.z, x1.w);
+        ok &= df_term(a0, ma, v2.x, x2.x, x2.y); ok &= df_term(b0, mb, v2.y, x2.z, x2.w);
+        ok &= df_term(a1, ma, v3.x, x3.x, x3.y); ok &= df_term(b1, mb, v3.y, x3.z, x3.w);
     }
     for (; j < re; ++j) {
         const double2 v = ValLoad<double>::two(vals, (int64_t)j * S + m);
         const float4 xv = XS::two(x, (int64_t)colf(j) * S + m);
-        if ((j - rs) & 1) { ok &= df_term(a1, v.x, xv.x, xv.y); ok &= df_term(b1, v.y, xv.z, xv.w); }
-        else { ok &= df_term(a0, v.x, xv.x, xv.y); ok &= df_term(b0, v.y, xv.z, xv.w); }
+        if ((j - rs) & 1) { ok &= df_term(a1, ma, v.x, xv.x, xv.y); ok &= df_term(b1, mb, v.y, xv.z, xv.w); }
+        else { ok &= df_term(a0, ma, v.x, xv.x, xv.y); ok &= df_term(b0, mb, v.y, xv.z, xv.w); }
     }
     double2 fb = make_double2(0.0, 0.0);
     if (!ok) fb = df_fixup2<S, XS, CA>(colf, rs, re, vals, x, m);
-    return make_double2(df_finish(a0, a1, fb.x), df_finish(b0, b1, fb.y));
+    double2 y = make_double2(df_finish(a0, a1, fb.x), df_finish(b0, b1, fb.y));
+    // FP64 for members with tiny products or a non-finite sum (an x outside
+    // the split range, or non-finite data)
+    if (df_tiny(ma) || !finite_bits(y.x)) y.x = row_fp64_member<S, XS, CA>(colf, rs, re, vals, x, m);
+    if (df_tiny(mb) || !finite_bits(y.y)) y.y = row_fp64_member<S, XS, CA>(colf, rs, re, vals, x, m + 1);
+    return y;
 }
 
 // df form of row_spmv1 (s = 1, 2 threads per row, result on both lanes)
@@ -394,11 +456,12 @@ __device__ __forceinline__ double row_spmv1_df(CA colf, int rs, int re,
                                                const double *__restrict__ vals,
                                                typename XS::ptr __restrict__ x, int g, bool valid) {
     DfAcc a = df_zero();
+    float mx = 0.0f;
     bool ok = true;
     if (valid)
         for (int j = rs + g; j < re; j += 2) {
             const float2 xv = XS::one(x, colf(j));
-            ok &= df_term(a, ValLoad<double>::one(vals, j), xv.x, xv.y);
+            ok &= df_term(a, mx, ValLoad<double>::one(vals, j), xv.x, xv.y);
         }
     double fb = 0.0;
     if (!ok)
@@ -413,7 +476,17 @@ __device__ __forceinline__ double row_spmv1_df(CA colf, int rs, int re,
     o.s = __shfl_xor_sync(0xffffffffu, a.s, 1);
     o.c = __shfl_xor_sync(0xffffffffu, a.c, 1);
     const double ofb = __shfl_xor_sync(0xffffffffu, fb, 1);
-    return (g == 0) ? df_finish(a, o, fb + ofb) : df_finish(o, a, ofb + fb);
+    const double y = (g == 0) ? df_finish(a, o, fb + ofb) : df_finish(o, a, ofb + fb);
+    mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, 1));
+    const bool redo = valid && (df_tiny(mx) || !finite_bits(y));
+    if (!__any_sync(0xffffffffu, redo)) return y;
+    // FP64 partial of this lane's entries, then p0 + p1 (both lanes of a pair agree)
+    double p = 0.0;
+    if (valid)
+        for (int j = rs + g; j < re; j += 2) p = fma(ValLoad<double>::one(vals, j), XS::dbl(x, colf(j)), p);
+    const double po = __shfl_xor_sync(0xffffffffu, p, 1);
+    const double yd = (g == 0) ? p + po : po + p;
+    return redo ? yd : y;
 }
 
 // --------------------------------------------- double-float, pre-split values
@@ -424,17 +497,20 @@ __device__ __forceinline__ double row_spmv1_df(CA colf, int rs, int re,
 // result is finite equals row_spmv2_df bitwise; a non-finite result (a marked
 // value, or a non-finite x or sum) is recomputed by row_spmv2_df from the
 // FP64 values, which keeps the equality in every case.
-template <int S, typename CA>
+template <int S, typename XS, typename CA>
 __device__ __noinline__ double2 row_spmv2_df_redo(CA colf, int rs, int re, const double *__restrict__ vals,
-                                                  const float2 *__restrict__ x, int g) {
-    return row_spmv2_df<S, XPre, CA>(colf, rs, re, vals, x, g);
+                                                  typename XS::ptr x, int g) {
+    return row_spmv2_df<S, XS, CA>(colf, rs, re, vals, x, g);
 }
 
-template <int S, typename CA>
+// XS: the source of the split x (XPre: the CG's split vectors; XSplit: FP64 x
+// split on the fly with the same rounding, as in ens_spmv_df)
+template <int S, typename XS, typename CA>
 __device__ __forceinline__ double2 row_spmv2_dfv(CA colf, int rs, int re, const float2 *__restrict__ vdf,
                                                  const double *__restrict__ vals,
-                                                 const float2 *__restrict__ x, int g) {
+                                                 typename XS::ptr __restrict__ x, int g) {
     DfAcc a0 = df_zero(), a1 = df_zero(), b0 = df_zero(), b1 = df_zero();
+    float ma = 0.0f, mb = 0.0f;  // max |product| of members m, m+1
     const int m = 2 * g;
     int j = rs;
     for (; j + 4 <= re; j += 4) {
@@ -443,45 +519,47 @@ __device__ __forceinline__ double2 row_spmv2_dfv(CA colf, int rs, int re, const 
         const float4 v1 = ld_stream(reinterpret_cast<const float4 *>(vdf + (int64_t)(j + 1) * S + m));
         const float4 v2 = ld_stream(reinterpret_cast<const float4 *>(vdf + (int64_t)(j + 2) * S + m));
         const float4 v3 = ld_stream(reinterpret_cast<const float4 *>(vdf + (int64_t)(j + 3) * S + m));
-        const float4 x0 = XPre::two(x, (int64_t)c0 * S + m);
-        const float4 x1 = XPre::two(x, (int64_t)c1 * S + m);
-        const float4 x2 = XPre::two(x, (int64_t)c2 * S + m);
-        const float4 x3 = XPre::two(x, (int64_t)c3 * S + m);
-        df_term_pre(a0, v0.x, v0.y, x0.x, x0.y); df_term_pre(b0, v0.z, v0.w, x0.z, x0.w);
-        df_term_pre(a1, v1.x, v1.y, x1.x, x1.y); df_term_pre(b1, v1.z, v1.w, x1.z, x1.w);
-        df_term_pre(a0, v2.x, v2.y, x2.x, x2.y); df_term_pre(b0, v2.z, v2.w, x2.z, x2.w);
-        df_term_pre(a1, v3.x, v3.y, x3.x, x3.y); df_term_pre(b1, v3.z, v3.w, x3.z, x3.w);
+        const float4 x0 = XS::two(x, (int64_t)c0 * S + m);
+        const float4 x1 = XS::two(x, (int64_t)c1 * S + m);
+        const float4 x2 = XS::two(x, (int64_t)c2 * S + m);
+        const float4 x3 = XS::two(x, (int64_t)c3 * S + m);
+        df_term_pm(a0, ma, v0.x, v0.y, x0.x, x0.y); df_term_pm(b0, mb, v0.z, v0.w, x0.z, x0.w);
+        df_term_pm(a1, ma, v1.x, v1.y, x1.x, x1.y); df_term_pm(b1, mb, v1.z, v1.w, x1.z, x1.w);
+        df_term_pm(a0, ma, v2.x, v2.y, x2.x, x2.y); df_term_pm(b0, mb, v2.z, v2.w, x2.z, x2.w);
+        df_term_pm(a1, ma, v3.x, v3.y, x3.x, x3.y); df_term_pm(b1, mb, v3.z, v3.w, x3.z, x3.w);
     }
     for (; j < re; ++j) {
         const float4 v = ld_stream(reinterpret_cast<const float4 *>(vdf + (int64_t)j * S + m));
-        const float4 xv = XPre::two(x, (int64_t)colf(j) * S + m);
-        if ((j - rs) & 1) { df_term_pre(a1, v.x, v.y, xv.x, xv.y); df_term_pre(b1, v.z, v.w, xv.z, xv.w); }
-        else { df_term_pre(a0, v.x, v.y, xv.x, xv.y); df_term_pre(b0, v.z, v.w, xv.z, xv.w); }
+        const float4 xv = XS::two(x, (int64_t)colf(j) * S + m);
+        if ((j - rs) & 1) { df_term_pm(a1, ma, v.x, v.y, xv.x, xv.y); df_term_pm(b1, mb, v.z, v.w, xv.z, xv.w); }
+        else { df_term_pm(a0, ma, v.x, v.y, xv.x, xv.y); df_term_pm(b0, mb, v.z, v.w, xv.z, xv.w); }
     }
     const double2 y = make_double2(df_finish(a0, a1, 0.0), df_finish(b0, b1, 0.0));
-    if (finite_bits(y.x) && finite_bits(y.y)) return y;
-    return row_spmv2_df_redo<S, CA>(colf, rs, re, vals, x, g);
+    if (finite_bits(y.x) && finite_bits(y.y) && !df_tiny(ma) && !df_tiny(mb)) return y;
+    return row_spmv2_df_redo<S, XS, CA>(colf, rs, re, vals, x, g);
 }
 
 // s = 1 (2 threads per row, full warps): the recomputation is taken by the
 // whole warp when any of its rows needs it (row_spmv1_df shuffles)
-template <typename CA>
+template <typename XS, typename CA>
 __device__ __forceinline__ double row_spmv1_dfv(CA colf, int rs, int re, const float2 *__restrict__ vdf,
                                                 const double *__restrict__ vals,
-                                                const float2 *__restrict__ x, int g, bool valid) {
+                                                typename XS::ptr __restrict__ x, int g, bool valid) {
     DfAcc a = df_zero();
+    float mx = 0.0f;
     if (valid)
         for (int j = rs + g; j < re; j += 2) {
-            const float2 xv = XPre::one(x, colf(j));
+            const float2 xv = XS::one(x, colf(j));
             const float2 v = ld_stream(vdf + j);
-            df_term_pre(a, v.x, v.y, xv.x, xv.y);
+            df_term_pm(a, mx, v.x, v.y, xv.x, xv.y);
         }
     DfAcc o;
     o.s = __shfl_xor_sync(0xffffffffu, a.s, 1);
     o.c = __shfl_xor_sync(0xffffffffu, a.c, 1);
     const double y = (g == 0) ? df_finish(a, o, 0.0) : df_finish(o, a, 0.0);
-    if (!__any_sync(0xffffffffu, !finite_bits(y))) return y;
-    return row_spmv1_df<XPre, CA>(colf, rs, re, vals, x, g, valid);
+    mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, 1));
+    if (!__any_sync(0xffffffffu, !finite_bits(y) || (valid && df_tiny(mx)))) return y;
+    return row_spmv1_df<XS, CA>(colf, rs, re, vals, x, g, valid);
 }
 
 // ------------------------------------------------- split FP64 / double-float
@@ -490,6 +568,17 @@ __device__ __forceinline__ double row_spmv1_dfv(CA colf, int rs, int re, const f
 // double-float product with x pre-split; row value = p0 + double(p1).
 // GB300 retires 2 DFMA and ~3 double-float terms per cycle per SM, so half of
 // the terms on each pipe keeps the SpMV under the HBM time.
+// FP64 sum, in increasing j, of the odd-position terms of member mm (the
+// split form's double-float partial), used when its products were tiny
+template <int S, typename CA>
+__device__ __noinline__ double split_odd_fp64(CA colf, int rs, int re, const double *__restrict__ vals,
+                                              const double *__restrict__ x, int mm) {
+    double p = 0.0;
+    for (int j = rs + 1; j < re; j += 2)
+        p = fma(ValLoad<double>::one(vals, (int64_t)j * S + mm), __ldg(x + (int64_t)colf(j) * S + mm), p);
+    return p;
+}
+
 template <int S, typename XS, typename CA>
 __device__ __forceinline__ double2 row_spmv2_split(CA colf, int rs, int re,
                                                    const double *__restrict__ vals,
@@ -497,6 +586,7 @@ __device__ __forceinline__ double2 row_spmv2_split(CA colf, int rs, int re,
                                                    typename XS::ptr __restrict__ xdf, int g) {
     double a0 = 0.0, b0 = 0.0;          // FP64 partial, members m, m+1
     DfAcc a1 = df_zero(), b1 = df_zero();  // double-float partial
+    float ma = 0.0f, mb = 0.0f;            // max |product| of the double-float partials
     bool ok = true;
     const int m = 2 * g;
     int j = rs;
@@ -511,16 +601,16 @@ __device__ __forceinline__ double2 row_spmv2_split(CA colf, int rs, int re,
         const double2 x2 = ld_x2(x, (int64_t)c2 * S + m);
         const float4 d3 = XS::two(xdf, (int64_t)c3 * S + m);
         a0 = fma(v0.x, x0.x, a0); b0 = fma(v0.y, x0.y, b0);
-        ok &= df_term(a1, v1.x, d1.x, d1.y); ok &= df_term(b1, v1.y, d1.z, d1.w);
+        ok &= df_term(a1, ma, v1.x, d1.x, d1.y); ok &= df_term(b1, mb, v1.y, d1.z, d1.w);
         a0 = fma(v2.x, x2.x, a0); b0 = fma(v2.y, x2.y, b0);
-        ok &= df_term(a1, v3.x, d3.x, d3.y); ok &= df_term(b1, v3.y, d3.z, d3.w);
+        ok &= df_term(a1, ma, v3.x, d3.x, d3.y); ok &= df_term(b1, mb, v3.y, d3.z, d3.w);
     }
     for (; j < re; ++j) {
         const double2 v = ValLoad<double>::two(vals, (int64_t)j * S + m);
         const int c = colf(j);
         if ((j - rs) & 1) {
             const float4 d = XS::two(xdf, (int64_t)c * S + m);
-            ok &= df_term(a1, v.x, d.x, d.y); ok &= df_term(b1, v.y, d.z, d.w);
+            ok &= df_term(a1, ma, v.x, d.x, d.y); ok &= df_term(b1, mb, v.y, d.z, d.w);
         } else {
             const double2 xv = ld_x2(x, (int64_t)c * S + m);
             a0 = fma(v.x, xv.x, a0); b0 = fma(v.y, xv.y, b0);
@@ -537,8 +627,14 @@ __device__ __forceinline__ double2 row_spmv2_split(CA colf, int rs, int re,
             if (!ok0) f0 = fma(v.x, xv.x, f0);
             if (!ok1) f1 = fma(v.y, xv.y, f1);
         }
-    const double p1a = f2d_exact(a1.s) + f2d_exact(a1.c), p1b = f2d_exact(b1.s) + f2d_exact(b1.c);
-    return make_double2(a0 + ((f0 != 0.0) ? p1a + f0 : p1a), b0 + ((f1 != 0.0) ? p1b + f1 : p1b));
+    double p1a = f2d_exact(a1.s) + f2d_exact(a1.c), p1b = f2d_exact(b1.s) + f2d_exact(b1.c);
+    if (f0 != 0.0) p1a += f0;
+    if (f1 != 0.0) p1b += f1;
+    // odd-position partials whose products fell below FP32's normal range, or
+    // whose sum is not finite (an x outside the split range): FP64
+    if (df_tiny(ma) || !finite_bits(p1a)) p1a = split_odd_fp64<S, CA>(colf, rs, re, vals, x, m);
+    if (df_tiny(mb) || !finite_bits(p1b)) p1b = split_odd_fp64<S, CA>(colf, rs, re, vals, x, m + 1);
+    return make_double2(a0 + p1a, b0 + p1b);
 }
 
 // s = 1: lane g = 0 sums the even positions in FP64, lane 1 the odd ones in
@@ -555,10 +651,11 @@ __device__ __forceinline__ double row_spmv1_split(CA colf, int rs, int re,
             for (int j = rs; j < re; j += 2) p = fma(ValLoad<double>::one(vals, j), __ldg(x + colf(j)), p);
         } else {
             DfAcc a = df_zero();
+            float mx = 0.0f;
             bool ok = true;
             for (int j = rs + 1; j < re; j += 2) {
                 const float2 d = XS::one(xdf, colf(j));
-                ok &= df_term(a, ValLoad<double>::one(vals, j), d.x, d.y);
+                ok &= df_term(a, mx, ValLoad<double>::one(vals, j), d.x, d.y);
             }
             double f = 0.0;
             if (!ok)
@@ -570,6 +667,7 @@ __device__ __forceinline__ double row_spmv1_split(CA colf, int rs, int re,
                 }
             const double p1 = f2d_exact(a.s) + f2d_exact(a.c);
             p = (f != 0.0) ? p1 + f : p1;
+            if (df_tiny(mx) || !finite_bits(p)) p = split_odd_fp64<1, CA>(colf, rs, re, vals, x, 0);
         }
     }
     const double o = __shfl_xor_sync(0xffffffffu, p, 1);
@@ -615,21 +713,21 @@ __device__ __forceinline__ double2 chunk_spmv_df(const ChunkCols &cc, bool stage
     }
 }
 
-template <int S>
+template <int S, typename XS = XPre>
 __device__ __forceinline__ double2 chunk_spmv_dfv(const ChunkCols &cc, bool staged,
                                                   const int32_t *__restrict__ col,
                                                   const float2 *__restrict__ vdf,
                                                   const double *__restrict__ vals,
-                                                  const float2 *__restrict__ x, int r, int g, bool valid) {
+                                                  typename XS::ptr __restrict__ x, int r, int g, bool valid) {
     const int rs = valid ? cc.rm[r] : 0, re = valid ? cc.rm[r + 1] : 0;
     if constexpr (S == 1) {
-        const double v = staged ? row_spmv1_dfv(ColShared{cc.col, cc.rm[0]}, rs, re, vdf, vals, x, g, valid)
-                                : row_spmv1_dfv(ColGlobal{col}, rs, re, vdf, vals, x, g, valid);
+        const double v = staged ? row_spmv1_dfv<XS>(ColShared{cc.col, cc.rm[0]}, rs, re, vdf, vals, x, g, valid)
+                                : row_spmv1_dfv<XS>(ColGlobal{col}, rs, re, vdf, vals, x, g, valid);
         return make_double2(v, 0.0);
     } else {
         if (!valid) return make_double2(0.0, 0.0);
-        return staged ? row_spmv2_dfv<S>(ColShared{cc.col, cc.rm[0]}, rs, re, vdf, vals, x, g)
-                      : row_spmv2_dfv<S>(ColGlobal{col}, rs, re, vdf, vals, x, g);
+        return staged ? row_spmv2_dfv<S, XS>(ColShared{cc.col, cc.rm[0]}, rs, re, vdf, vals, x, g)
+                      : row_spmv2_dfv<S, XS>(ColGlobal{col}, rs, re, vdf, vals, x, g);
     }
 }
 

@@ -40,3 +40,20 @@ def spmv_bound(row_map, col, vals, x, rel=1e-12):
 
 def samples(seed, first, s, M):
     return inputs.kl_samples(seed, first, s, M)
+
+
+def leading_mode_threshold(N, L=1.0, kappa0=1.0):
+    """sigma* at which a(x) = kappa0 - sigma kappa_1(x) (M = 1, xi_1 = -1)
+    first reaches 0 at a Gauss point of the N^3 mesh, from the closed form
+    of the leading KL mode: kappa_1 = sqrt(lambda) phi(x) phi(y) phi(z) with
+    phi(t) = cos(w (t - 1/2)) / sqrt(1/2 + sin(w) / (2 w)), w the root of
+    c - w tan(w/2) = 0 in (0, pi), c = 1/L, lambda = (2c / (w^2 + c^2))^3.
+    phi > 0 on [0, 1], so the minimum of a sits where phi^3 is largest."""
+    from scipy.optimize import brentq
+    c = 1.0 / L
+    w = brentq(lambda t: c - t * np.tan(t / 2), 1e-12, np.pi - 1e-12)
+    lam1 = 2 * c / (w * w + c * c)
+    d = 0.5 / np.sqrt(3.0)
+    g = np.concatenate([(np.arange(N) + 0.5 - d) / N, (np.arange(N) + 0.5 + d) / N])
+    phi = np.cos(w * (g - 0.5)) / np.sqrt(0.5 + np.sin(w) / (2 * w))
+    return kappa0 / (lam1 ** 1.5 * phi.max() ** 3)

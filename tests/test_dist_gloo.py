@@ -43,7 +43,7 @@ def _rank_main(rank, world, port, q):
             "value": 1.0, "unit": bench.UNIT, "cores": 1, "kind": "oracle", "sample": "stub", "seconds": 1.0}
 
         class A:
-            steps, warmup = 1, 0
+            steps, warmup, s, spmv = 1, 0, 32, "dfv"
         ref = bench.main_reference(A())
         dist.barrier()
         dist.destroy_process_group()

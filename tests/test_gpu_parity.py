@@ -19,7 +19,7 @@ import pytest
 import oracle as O
 import paper_1511_03703_gb300 as E
 from paper_1511_03703_gb300 import inputs
-from helpers import gpu, oracle_members, spmv_bound, to_dev, to_np
+from helpers import gpu, leading_mode_threshold, oracle_members, spmv_bound, to_dev, to_np
 
 pytestmark = pytest.mark.gpu
 S_ALL = [1, 4, 8, 16, 32]
@@ -97,10 +97,63 @@ def test_assembly_matches_oracle(torch, N, M, s):
         assert np.max(np.abs(B[:, e] - ob[e])) <= 1e-13 * np.max(np.abs(ob[e]))
 
 
+# --------------------------------------- A3 coefficient positivity (status 7)
+@pytest.mark.parametrize("df", [False, True])
+def test_assemble_nonpositive_coefficient_status(torch, df):
+    """Member 2's KL variables scaled by 40 (|xi| >> 1) make its coefficient
+    negative somewhere: ens_assemble(_df) returns ENS_ERR_NONPOS_COEFF naming
+    that member, as the oracle's assembly reports, and still writes every
+    member's values (the good members against the oracle)."""
+    N, M, s = 6, 10, 4
+    mesh = E.Mesh(N, M)
+    xs = inputs.kl_samples(1800, 0, s, M)
+    xs[2] *= 40.0
+    assert [O.coeff_min(N, M, x) <= 0 for x in xs] == [False, False, True, False]
+    vals = torch.empty(mesh.nnz * s, dtype=torch.float64, device=gpu())
+    b = torch.empty(mesh.n * s, dtype=torch.float64, device=gpu())
+    vdf = torch.empty(2 * mesh.nnz * s, dtype=torch.float32, device=gpu()) if df else None
+    with pytest.raises(E.EnsError) as ei:
+        mesh.assemble(s, to_dev(inputs.ensemble_layout(xs)), values=vals, b=b, df=df, values_df=vdf)
+    assert ei.value.code == 7 and "member 2" in str(ei.value)
+    rm, col = O.graph(N)
+    V = ens_cols(to_np(vals), s)
+    for e in (0, 1, 3):
+        ov, ob = O.assemble(N, M, xs[e], rm, col)
+        assert np.all(np.abs(V[:, e] - ov) <= 1e-13 * np.abs(diag_of(rm, col, ov))), e
+    with pytest.raises(O.NonPositiveCoefficient):
+        O.assemble(N, M, xs[2], rm, col)
+    # the unscaled draws pass the check (the bound alone clears them)
+    mesh.assemble(s, to_dev(inputs.ensemble_layout(inputs.kl_samples(1800, 0, s, M))), df=df)
+
+
+@pytest.mark.parametrize("s", [1, 8])
+def test_assemble_coefficient_check_exact_minimum(torch, s):
+    """M = 1: with xi_1 = +1 a large sigma defeats the bound but the exact
+    minimum over the Gauss points stays positive (no error); with xi_1 = -1
+    the status flips exactly at the closed-form threshold sigma*, on the
+    same side as the oracle."""
+    N = 7
+    mesh = E.Mesh(N, 1)
+    sstar = leading_mode_threshold(N)
+    ones = np.ones((s, 1))
+    mesh.assemble(s, to_dev(inputs.ensemble_layout(ones)), sigma=50 * sstar)      # exact path, positive
+    neg = to_dev(inputs.ensemble_layout(-ones))
+    mesh.assemble(s, neg, sigma=sstar * (1 - 1e-7))
+    with pytest.raises(E.EnsError) as ei:
+        mesh.assemble(s, neg, sigma=sstar * (1 + 1e-7), df=True)
+    assert ei.value.code == 7
+    assert O.coeff_min(N, 1, [-1.0], sigma=sstar * (1 - 1e-7)) > 0 > O.coeff_min(N, 1, [-1.0],
+                                                                                sigma=sstar * (1 + 1e-7))
+    with pytest.raises(E.EnsError) as ei:
+        mesh.assemble(s, neg, sigma=float("nan"))
+    assert ei.value.code == 7
+
+
 # ------------------------------------------------------------------ A4 SpMV
 @pytest.mark.parametrize("N", [3, 8, 13])
 @pytest.mark.parametrize("s", S_ALL)
-@pytest.mark.parametrize("dtype", ["float64", "float64_df", "float64_split", "float32", "bfloat16"])
+@pytest.mark.parametrize("dtype", ["float64", "float64_df", "float64_split", "float64_dfv", "float32",
+                                   "bfloat16"])
 def test_spmv_matches_oracle(torch, N, s, dtype):
     M = 10
     xs = inputs.kl_samples(200 + N, 0, min(s, 4), M)
@@ -108,12 +161,16 @@ def test_spmv_matches_oracle(torch, N, s, dtype):
     ov = [ov[e % len(ov)] for e in range(s)]
     n = len(rm) - 1
     xm = [inputs.random_vector(300 + e, n) for e in range(s)]
-    df, split = dtype == "float64_df", dtype == "float64_split"
-    vt = torch.from_numpy(O.to_ensemble(ov)).to(getattr(torch, "float64" if df or split else dtype))
+    df, split, dfv = dtype == "float64_df", dtype == "float64_split", dtype == "float64_dfv"
+    vt = torch.from_numpy(O.to_ensemble(ov)).to(getattr(torch, "float64" if df or split or dfv else dtype))
     vq = [vt.reshape(-1, s)[:, e].double().numpy() for e in range(s)]   # values as stored
     y = torch.empty(n * s, dtype=torch.float64, device=gpu())
     graph = E.Graph(to_dev(rm), to_dev(col))
-    E.spmv(graph, s, vt.to(gpu()), to_dev(O.to_ensemble(xm)), y, df=df, split=split)
+    vdf = None
+    if dfv:
+        vdf = torch.empty(2 * vt.numel(), dtype=torch.float32, device=gpu())
+        E.convert_values(graph, s, vt.to(gpu()), vdf, dtype=E.F64_DF)
+    E.spmv(graph, s, vt.to(gpu()), to_dev(O.to_ensemble(xm)), y, df=df, split=split, values_df=vdf)
     Y = ens_cols(to_np(y), s)
     for e in range(s):
         ref = O.spmv(rm, col, vq[e], xm[e])
@@ -121,7 +178,7 @@ def test_spmv_matches_oracle(torch, N, s, dtype):
 
 
 @pytest.mark.parametrize("s", [1, 8, 32])
-@pytest.mark.parametrize("form", ["df", "split"])
+@pytest.mark.parametrize("form", ["df", "split", "dfv"])
 def test_spmv_df_extreme_values_take_exact_path(torch, s, form):
     """Values outside the double-float split range ([2^-103, 2^128)), exact
     zeros and mixed magnitudes within a row stay inside the 1e-12 bound."""
@@ -137,12 +194,21 @@ def test_spmv_df_extreme_values_take_exact_path(torch, s, form):
     xm = [inputs.random_vector(330 + e, n, -1e3, 1e3) for e in range(s)]
     y = torch.empty(n * s, dtype=torch.float64, device=gpu())
     graph = E.Graph(to_dev(rm), to_dev(col))
-    E.spmv(graph, s, to_dev(O.to_ensemble(vals)), to_dev(O.to_ensemble(xm)), y,
-           df=form == "df", split=form == "split")
+    spmv_form(torch, graph, s, to_dev(O.to_ensemble(vals)), to_dev(O.to_ensemble(xm)), y, form)
     Y = ens_cols(to_np(y), s)
     for e in range(s):
         ref = O.spmv(rm, col, vals[e], xm[e])
         assert np.all(np.abs(Y[:, e] - ref) <= spmv_bound(rm, col, vals[e], xm[e])), e
+
+
+def spmv_form(torch, graph, s, vals, x, y, form):
+    """ens_spmv in the double-float form `form` (df, split) or ens_spmv_df
+    on the ENS_F64_DF copy of vals (dfv)."""
+    vdf = None
+    if form == "dfv":
+        vdf = torch.empty(2 * vals.numel(), dtype=torch.float32, device=gpu())
+        E.convert_values(graph, s, vals, vdf, dtype=E.F64_DF)
+    E.spmv(graph, s, vals, x, y, df=form == "df", split=form == "split", values_df=vdf)
 
 
 def test_spmv_s_invariant_bitwise(torch):
@@ -408,15 +474,126 @@ def test_scale_64cubed_s32_sampled(torch):
         ref = O.spmv(rm, col, ov[e % 2], xm[e])
         assert np.all(np.abs(Y[:, e] - ref) <= spmv_bound(rm, col, ov[e % 2], xm[e])), e
     # CG of the whole ensemble; two members against oracle solves
+    oracle_sol = [O.cg(rm, col, ov[i], ob[i], tol=1e-8) for i in range(len(picks))]
     for flags, presplit in ((0, False), (E.CG_DF64, False), (E.CG_SPLIT64, False), (0, True)):
         xg, it, rr, st, _ = gpu_solve(mesh, xs, 1e-8, flags=flags, presplit=presplit)
         assert st == [0] * s and max(rr) < 2e-8
-        compare_cg_picked(mesh, xs, picks, rm, col, ov, ob, xg, it)
+        compare_cg_picked(mesh, xs, picks, rm, col, ov, ob, oracle_sol, xg, it, flags, presplit)
 
 
-def compare_cg_picked(mesh, xs, picks, rm, col, ov, ob, xg, it):
+def compare_cg_picked(mesh, xs, picks, rm, col, ov, ob, oracle_sol, xg, it, flags, presplit):
+    """Members `picks` against oracle solves: 1e-8 at equal iteration counts;
+    else both sides re-run for max(counts) iterations and compared at 1e-10."""
     for i, e in enumerate(picks):
-        xo, ito, rro, sto = O.cg(rm, col, ov[i], ob[i], tol=1e-8)
-        assert sto == 0 and abs(it[e] - ito) <= 1
-        err = np.linalg.norm(xg[:, e] - xo) / np.linalg.norm(xo)
-        assert err <= 1e-8 or it[e] != ito, (e, err)
+        xo, ito, rro, sto = oracle_sol[i]
+        assert sto == 0 and abs(it[e] - ito) <= 1, (e, it[e], ito)
+        if it[e] == ito:
+            err = np.linalg.norm(xg[:, e] - xo) / np.linalg.norm(xo)
+            assert err <= 1e-8, (e, err)
+        else:
+            k = max(it[e], ito)
+            xo2, _, _, _ = O.cg(rm, col, ov[i], ob[i], tol=0.0, max_iter=k)
+            xg2, it2, _, _, _ = gpu_solve(mesh, xs, 0.0, max_iter=k, flags=flags, presplit=presplit)
+            assert it2[e] == k
+            assert np.linalg.norm(xg2[:, e] - xo2) <= 1e-10 * np.linalg.norm(xo2), e
+
+
+# ------------------------------------ extreme magnitudes (float-pair ranges)
+@pytest.mark.parametrize("scale", [1e-20, 2.0 ** -100, 1e25, 2.0 ** 90])
+@pytest.mark.parametrize("form", ["f64", "df", "split", "dfv"])
+def test_cg_rhs_scaled_far_outside_fp32_range(torch, scale, form):
+    """CG with b scaled far below and above FP32's range: the float-pair r.r of
+    K2 and the double-float SpMV products leave FP32's normal range, and must
+    fall back to FP64 rather than stop early (underflow) or break down
+    (overflow).  Status, iteration counts and solutions against the oracle's
+    CG on the same scaled system."""
+    N, M, s = 9, 10, 4
+    mesh = E.Mesh(N, M)
+    xs = inputs.kl_samples(1500, 0, s, M)
+    vals, b = mesh.assemble(s, to_dev(inputs.ensemble_layout(xs)))
+    b *= scale
+    vdf = None
+    if form == "dfv":
+        vdf = torch.empty(2 * vals.numel(), dtype=torch.float32, device=gpu())
+        E.convert_values(mesh.graph, s, vals, vdf, dtype=E.F64_DF)
+    flags = {"f64": 0, "df": E.CG_DF64, "split": E.CG_SPLIT64, "dfv": 0}[form]
+    work = torch.empty(E.cg_workspace_size(mesh.n, s), dtype=torch.uint8, device=gpu())
+
+    def run(tol, max_iter):
+        x = torch.zeros(mesh.n * s, dtype=torch.float64, device=gpu())
+        it, rr, st, _ = E.cg(mesh.graph, s, vals, b, x, tol, max_iter, work, flags=flags, values_df=vdf)
+        return ens_cols(to_np(x), s), it, rr, st
+
+    xg, it, rr, st = run(1e-8, 5000)
+    assert st == [0] * s, st
+    rm, col, ov, ob = oracle_members(N, M, xs)
+    for e in range(s):
+        bo = ob[e] * scale
+        xo, ito, rro, sto = O.cg(rm, col, ov[e], bo, tol=1e-8)
+        assert sto == 0 and abs(it[e] - ito) <= 1, (e, it[e], ito)
+        assert rr[e] <= 2e-8, (e, rr[e])
+        if it[e] == ito:
+            assert np.linalg.norm(xg[:, e] - xo) <= 1e-8 * np.linalg.norm(xo), e
+        else:  # stopping decided by rounding: compare at a fixed iteration count
+            k = max(it[e], ito)
+            xo2, _, _, _ = O.cg(rm, col, ov[e], bo, tol=0.0, max_iter=k)
+            xg2, it2, _, _ = run(0.0, k)
+            assert it2[e] == k
+            assert np.linalg.norm(xg2[:, e] - xo2) <= 1e-10 * np.linalg.norm(xo2), e
+
+
+@pytest.mark.parametrize("s", [1, 4, 32])
+@pytest.mark.parametrize("form", ["df", "split", "dfv"])
+@pytest.mark.parametrize("vscale,xscale", [(1.0, 2.0 ** -100), (2.0 ** -30, 2.0 ** -100),
+                                           (2.0 ** -60, 2.0 ** -90), (1.0, 2.0 ** -120)])
+def test_spmv_df_products_below_fp32_normal_range(torch, s, form, vscale, xscale):
+    """Products a_j x_j below 2^-96 (here down to FP32's subnormals and below
+    them) with values and x inside the split range, and x below the split range
+    (2^-120): the double-float forms recompute such members in FP64 and stay
+    inside the 1e-12 componentwise bound; rows of ordinary magnitude in the
+    same launch are unaffected.  Members whose every product is below 2^-149
+    may return 0: the documented absolute floor 27 * 2^-149."""
+    N, M = 5, 10
+    xs = inputs.kl_samples(1510, 0, 1, M)
+    rm, col, ov, _ = oracle_members(N, M, xs)
+    n = len(rm) - 1
+    vals = [ov[0] * (1.0 + 0.01 * e) * vscale for e in range(s)]
+    xm = []
+    for e in range(s):
+        v = inputs.random_vector(1520 + e, n, 0.5, 1.0) * np.where(np.arange(n) % 2, 1.0, -1.0)
+        v[(np.arange(n) % 3) != 0] *= xscale      # two thirds of the entries tiny
+        if e % 2:
+            v *= xscale                            # odd members: every entry tiny
+        xm.append(v)
+    y = torch.empty(n * s, dtype=torch.float64, device=gpu())
+    graph = E.Graph(to_dev(rm), to_dev(col))
+    spmv_form(torch, graph, s, to_dev(O.to_ensemble(vals)), to_dev(O.to_ensemble(xm)), y, form)
+    Y = ens_cols(to_np(y), s)
+    for e in range(s):
+        ref = O.spmv(rm, col, vals[e], xm[e])
+        bound = np.maximum(spmv_bound(rm, col, vals[e], xm[e]), 27 * 2.0 ** -149)
+        assert np.all(np.abs(Y[:, e] - ref) <= bound), e
+        if vscale * xscale >= 2.0 ** -130:   # products above FP32's subnormal floor: the plain bar
+            assert np.all(np.abs(Y[:, e] - ref) <= spmv_bound(rm, col, vals[e], xm[e])), e
+
+
+@pytest.mark.parametrize("s", [1, 4, 32])
+def test_cg_df_tiny_products_bitwise_equals_df64(torch, s):
+    """The pre-split form and the df form take the same FP64 decision for
+    members with tiny products, so ens_cg_df stays bitwise ens_cg with
+    ENS_CG_DF64 (b scaled by 2^-100, fixed iteration count)."""
+    N, M = 7, 10
+    mesh = E.Mesh(N, M)
+    xs = inputs.kl_samples(1530 + s, 0, s, M)
+    vals, b = mesh.assemble(s, to_dev(inputs.ensemble_layout(xs)))
+    b *= 2.0 ** -100
+    vdf = torch.empty(2 * vals.numel(), dtype=torch.float32, device=gpu())
+    E.convert_values(mesh.graph, s, vals, vdf, dtype=E.F64_DF)
+    work = torch.empty(E.cg_workspace_size(mesh.n, s), dtype=torch.uint8, device=gpu())
+    out = []
+    for flags, vd in ((E.CG_DF64, None), (0, vdf)):
+        x = torch.zeros(mesh.n * s, dtype=torch.float64, device=gpu())
+        it, rr, st, _ = E.cg(mesh.graph, s, vals, b, x, 0.0, 40, work, flags=flags, values_df=vd)
+        out.append((to_np(x), it, rr))
+    assert out[0][1] == out[1][1] and out[0][2] == out[1][2]
+    assert np.array_equal(out[0][0], out[1][0])

@@ -164,8 +164,8 @@ def test_assemble_df_s_invariant_and_fp64_fallback(torch):
         assert np.array_equal(v0, ref), s
     # coefficients outside the split range: the FP64 combination, bitwise
     xi = to_dev(inputs.ensemble_layout(xs[:4]))
-    vd, _ = mesh.assemble(4, xi, sigma=1e200, df=True)
-    v64, _ = mesh.assemble(4, xi, sigma=1e200)
+    vd, _ = mesh.assemble(4, xi, sigma=1e200, df=True, check=False)
+    v64, _ = mesh.assemble(4, xi, sigma=1e200, check=False)
     assert torch.equal(vd, v64)
 
 

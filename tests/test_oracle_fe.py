@@ -13,6 +13,7 @@ import pytest
 import scipy.sparse as sp
 
 import oracle as O
+from helpers import leading_mode_threshold
 
 
 def dense(row_map, col, vals):
@@ -150,3 +151,34 @@ def test_pde_centre_value_converges_second_order():
         errs.append(abs(x[c + (N + 1) * (c + (N + 1) * c)] - exact))
     r1, r2 = errs[0] / errs[1], errs[1] / errs[2]
     assert 3.5 < r1 < 4.5 and 3.7 < r2 < 4.3, errs
+
+
+@pytest.mark.parametrize("N", [3, 4, 7])
+def test_assembly_reports_a_nonpositive_coefficient_at_the_closed_form_threshold(N):
+    """Sect. 4's coefficient must be positive for an elliptic problem: the
+    oracle's assembly reports a(x_q) <= 0 exactly past the threshold the
+    closed-form leading mode gives, and a positive mode never trips it."""
+    rm, col = O.graph(N)
+    sstar = leading_mode_threshold(N)
+    O.assemble(N, 1, [-1.0], rm, col, sigma=sstar * (1 - 1e-9))
+    assert O.coeff_min(N, 1, [-1.0], sigma=sstar * (1 - 1e-9)) > 0
+    with pytest.raises(O.NonPositiveCoefficient):
+        O.assemble(N, 1, [-1.0], rm, col, sigma=sstar * (1 + 1e-9))
+    assert O.coeff_min(N, 1, [-1.0], sigma=sstar * (1 + 1e-9)) < 0
+    O.assemble(N, 1, [1.0], rm, col, sigma=50 * sstar)          # kappa_1 > 0: a > kappa0
+    with pytest.raises(O.NonPositiveCoefficient):
+        O.assemble(N, 1, [1.0], rm, col, sigma=float("nan"))   # NaN is not positive
+    # unchecked: the values are still those of the assembly
+    v, b = O.assemble(N, 1, [-1.0], rm, col, sigma=2 * sstar, check=False)
+    assert np.all(np.isfinite(v)) and np.all(np.isfinite(b))
+
+
+def test_workload_coefficient_stays_positive():
+    """The workloads' KL variables lie in [-1, 1] with sigma = 0.1 and M = 10:
+    the coefficient stays well above zero (about 0.7 at worst)."""
+    from paper_1511_03703_gb300 import inputs
+    xs = inputs.kl_samples(1002, 0, 64, 10)
+    amin = min(O.coeff_min(8, 10, x) for x in xs)
+    assert 0.5 < amin < 1.0
+    # the same draws with sigma large enough make the problem indefinite
+    assert min(O.coeff_min(8, 10, x, sigma=2.0) for x in xs) < 0
