@@ -783,8 +783,10 @@ def run_batched(args, compact=False, oracle_jobs=None):
             g += 1
     t0 = time.perf_counter()
     # every item carries its pre-split values (written by the double-float
-    # assembly), so all four SpMV forms are candidates
-    forms = {(N, s): autotune.best_form(meshes[N], s) for N in BAT_MESHES for s in BAT_WIDTHS}
+    # assembly), so all four SpMV forms are candidates; each (mesh, s) gets its
+    # own (form, chunks per SpMV CTA) for the separate launches
+    mappings = {(N, s): autotune.best_mapping(meshes[N], s) for N in BAT_MESHES for s in BAT_WIDTHS}
+    forms = {key: m["form"] for key, m in mappings.items()}
     works = {}
     for it in items:
         key = (it["N"], it["s"])
@@ -796,10 +798,11 @@ def run_batched(args, compact=False, oracle_jobs=None):
         f = forms[(it["N"], it["s"])]
         votes[f] = votes.get(f, 0) + meshes[it["N"]].nnz * it["s"]
     bform = max(votes, key=votes.get)
-    bflags = autotune.FORMS[bform]
     batch = E.Batch([(meshes[it["N"]].graph, it["s"], it["vals"], it["b"], it["x"])
                      + ((it["vdf"],) if bform == "dfv" else ()) for it in items])
     bwork = torch.empty(batch.workspace_size(), dtype=torch.uint8, device=dev)
+    bflags = autotune.FORMS[bform] | autotune.best_batch_k1(batch, bwork, autotune.FORMS[bform],
+                                                            tag=f"batched-16^3-64^3-{bform}")
     ce = autotune.best_check_every(batch, bwork, bflags, tag=f"batched-16^3-64^3-{bform}")
     tune_s = time.perf_counter() - t0
 
@@ -817,10 +820,10 @@ def run_batched(args, compact=False, oracle_jobs=None):
         iters = []
         for it in items:
             mesh = meshes[it["N"]]
-            f = forms[(it["N"], it["s"])]
+            m = mappings[(it["N"], it["s"])]
             i, r, st, _ = E.cg(mesh.graph, it["s"], it["vals"], it["b"], it["x"], TOL, 10000,
-                               works[(it["N"], it["s"])], flags=autotune.FORMS[f], check_every=16,
-                               values_df=it["vdf"] if f == "dfv" else None)
+                               works[(it["N"], it["s"])], flags=autotune.mapping_flags(m), check_every=16,
+                               values_df=it["vdf"] if m["form"] == "dfv" else None)
             iters.append(i)
         return iters
 
@@ -861,7 +864,10 @@ def run_batched(args, compact=False, oracle_jobs=None):
             "dtype": "f64", "data": "synthetic",
             "config": {"workload": BAT_WORKLOAD, "ensembles": len(items), "samples": total,
                        "batch_spmv_form": bform, "graph_check_every": ce,
-                       "per_group_forms": {f"{N}^3,s={s}": forms[(N, s)] for (N, s) in groups},
+                       "batch_spmv_cta_threads": 1024 if bflags & E.CG_BATCH_K1_WIDE else 512,
+                       "per_group_mapping": {f"{N}^3,s={s}": {"form": mappings[(N, s)]["form"],
+                                                              "k1_chunks_per_cta": mappings[(N, s)]["k1_chunks"]}
+                                             for (N, s) in groups},
                        "tuning_seconds": tune_s, "step": "mesh set-up + assembly of every ensemble + solve"},
             "separate_launches": {"value": steps * total / ts, "unit": UNIT},
             "speedup_batched_vs_separate": ts / tb,

@@ -245,6 +245,20 @@ enum {
                                 bitwise, as computing b - A*0) */
 };
 
+/* Launch mapping of the CG's SpMV (a tuning knob; not in the paper): rows per
+ * CTA of the SpMV kernel.  ENS_CG_K1_CHUNKS(k) in the flags of ens_cg /
+ * ens_cg_df asks for 2^k chunks of 32 rows per CTA (k = 0..3), each chunk on
+ * 32 * max(s/2, 2) threads; a CTA holds at most 1024 threads, so k <= 1 at
+ * s = 32 and k <= 2 at s = 16 (ENS_ERR_ARG beyond).  Without the field the
+ * library's default for s is used.  Every sum is ordered by row index, so
+ * the mapping never changes a result bit.  Bits 16..18 of flags. */
+#define ENS_CG_K1_CHUNKS_SHIFT 16
+#define ENS_CG_K1_CHUNKS(k) (((k) + 1) << ENS_CG_K1_CHUNKS_SHIFT)
+/* The batched SpMV's mapping (ens_cg_batched): CTAs of 512 threads (default)
+ * or, with this flag, 1024, i.e. 512 / (32 max(s/2, 2)) chunks of 32 rows of
+ * an item per CTA, or twice that; no effect on results either. */
+#define ENS_CG_BATCH_K1_WIDE (1 << 19)
+
 /* Unpreconditioned CG (Hestenes-Stiefel) on each member of the ensemble
  * system, with per-member dots (default) or the paper's coupled form.
  * Member e stops when ||r_e|| <= tol*||b_e|| (recursive residual) and is

@@ -46,6 +46,43 @@ static uint32_t l2_prefetch_cap(int mode) {
     return mode == 3 ? 0xffffffffu : 0u;
 }
 
+// K2 prefetches each CTA's r and q blocks into L2 before its passes; the
+// ENS_K2_PREFETCH environment variable (0 or 1) overrides the default
+static int k2_prefetch() {
+    static const int v = [] {
+        const char *e = getenv("ENS_K2_PREFETCH");
+        return e ? (atoi(e) != 0) : 1;
+    }();
+    return v;
+}
+
+// K1 rows per CTA: the largest mapping a CTA of 1024 threads holds, and the
+// default (measured on the 64^3 mesh; every mapping gives the same bits)
+int k1_max_nsub_rt(int s) {
+    switch (s) {
+        case 1: return k1_max_nsub<1>();
+        case 4: return k1_max_nsub<4>();
+        case 8: return k1_max_nsub<8>();
+        case 16: return k1_max_nsub<16>();
+        default: return k1_max_nsub<32>();
+    }
+}
+
+int k1_default_nsub(int s, int mode) {
+    (void)mode;
+    (void)s;
+    return 1;   // one chunk per CTA measured fastest, or within 1 %, at every s (64^3 mesh)
+}
+
+// chunks per K1 CTA from the ENS_CG_K1_CHUNKS field of flags (0: default);
+// -1 when the field asks for more than a 1024-thread CTA holds
+static int k1_nsub_from_flags(int flags, int s, int mode) {
+    const int f = (flags >> ENS_CG_K1_CHUNKS_SHIFT) & 7;
+    if (f == 0) return k1_default_nsub(s, mode);
+    const int nsub = 1 << (f - 1);
+    return (f <= 4 && nsub <= k1_max_nsub_rt(s)) ? nsub : -1;
+}
+
 static size_t cg_bytes(int64_t n, int s) {
     return align256(sizeof(CgState)) + 4 * align256(sizeof(double) * (size_t)n * s) +
            dot_tree_bytes(n, s) + dot_tree_bytes(n, 2 * s);
@@ -60,13 +97,11 @@ struct CgKernels {
         cg_init_kernel<S, MODE><<<grid, RowMap<S>::THREADS, 0, st>>>(a);
         cg_zero_kernel<S, MODE><<<152 * 2, 256, 0, st>>>(a);
     }
-    static void spmv(const CgArgs &a, unsigned grid, cudaStream_t st) {
-        cg_spmv_kernel<S, MODE><<<grid, RowMap<S>::THREADS, 0, st>>>(a);
-    }
-    static void resid(const CgArgs &a, unsigned, cudaStream_t st) {
+    static void spmv(const CgArgs &a, int nsub, cudaStream_t st) { k1_launch<S, MODE>(a, nsub, st); }
+    static void resid(const CgArgs &a, cudaStream_t st) {
         cg_resid_kernel<S><<<vec_grid(a), VecMap<S>::THREADS, 0, st>>>(a);
     }
-    static void update(const CgArgs &a, unsigned, cudaStream_t st) {
+    static void update(const CgArgs &a, cudaStream_t st) {
         cg_update_kernel<S, MODE><<<vec_grid(a), VecMap<S>::THREADS, 0, st>>>(a);
     }
     static void final_(const CgArgs &a, unsigned grid, cudaStream_t st) {
@@ -112,7 +147,9 @@ static int cg_run(const ens_graph *g, const double *vals, const float2 *vdf, con
     a.x0_zero = (flags & ENS_CG_X0_ZERO) ? 1 : 0;
     a.pf_cap = l2_prefetch_cap(MODE);
     a.val_bytes = (uint64_t)g->num_entries * S * 8u;
+    a.k2_pf = k2_prefetch();
     const unsigned grid = (unsigned)a.t1.count[1];
+    const int nsub = k1_nsub_from_flags(flags, S, MODE);
     int rc;
     if ((rc = dot_tree_clear(a.t1, st))) return rc;
     if ((rc = dot_tree_clear(a.t2, st))) return rc;
@@ -146,11 +183,11 @@ static int cg_run(const ens_graph *g, const double *vals, const float2 *vdf, con
         if (ce == cudaSuccess) {
             for (int i = 0; i < check_every; ++i) {
                 if (timing && ce == cudaSuccess) ce = cudaEventRecordWithFlags(ev[2 * i], cap, cudaEventRecordExternal);
-                K::spmv(a, grid, cap);
+                K::spmv(a, nsub, cap);
                 if (timing && ce == cudaSuccess)
                     ce = cudaEventRecordWithFlags(ev[2 * i + 1], cap, cudaEventRecordExternal);
-                K::resid(a, grid, cap);
-                K::update(a, grid, cap);
+                K::resid(a, cap);
+                K::update(a, cap);
             }
             const cudaError_t ce2 = cudaStreamEndCapture(cap, &graph);
             if (ce == cudaSuccess) ce = ce2;
@@ -180,10 +217,10 @@ static int cg_run(const ens_graph *g, const double *vals, const float2 *vdf, con
         } else {
             for (int i = 0; i < check_every; ++i) {
                 if (timing) cudaEventRecord(ev[2 * i], st);
-                K::spmv(a, grid, st);
+                K::spmv(a, nsub, st);
                 if (timing) cudaEventRecord(ev[2 * i + 1], st);
-                K::resid(a, grid, st);
-                K::update(a, grid, st);
+                K::resid(a, st);
+                K::update(a, st);
             }
         }
         launches += 3 * check_every;
@@ -263,17 +300,21 @@ static int cg_dispatch_df(const ens_graph *g, const double *vals, const float2 *
 // (K2, K3) of that ensemble.  Arithmetic is identical to ens_cg.
 constexpr int kBatchThreads = 512;
 
-template <int S>
+// batched K1 CTA: TH threads (512, or 1024 with ENS_CG_BATCH_K1_WIDE), i.e.
+// TH / (32 * RowMap<S>::G) chunks of an ensemble of size S per CTA
+template <int S, int TH>
 struct BatchK1 {
-    static constexpr int NSUB = kBatchThreads / RowMap<S>::THREADS;
+    static constexpr int NSUB = TH / RowMap<S>::THREADS;
     using Smem = K1Smem<S, NSUB>;
 };
 
 constexpr size_t cmax(size_t a, size_t b) { return a > b ? a : b; }
-constexpr size_t kBatchK1Smem =
-    cmax(cmax(cmax(sizeof(BatchK1<1>::Smem), sizeof(BatchK1<4>::Smem)),
-              cmax(sizeof(BatchK1<8>::Smem), sizeof(BatchK1<16>::Smem))),
-         sizeof(BatchK1<32>::Smem));
+template <int TH>
+constexpr size_t batch_k1_smem() {
+    return cmax(cmax(cmax(sizeof(typename BatchK1<1, TH>::Smem), sizeof(typename BatchK1<4, TH>::Smem)),
+                     cmax(sizeof(typename BatchK1<8, TH>::Smem), sizeof(typename BatchK1<16, TH>::Smem))),
+                sizeof(typename BatchK1<32, TH>::Smem));
+}
 template <int S>
 constexpr size_t batch_k2_smem() { return sizeof(double) * VecMap<S, kBatchThreads>::CPC * 32 * (S + 1); }
 constexpr size_t kBatchK2Smem = cmax(cmax(cmax(batch_k2_smem<1>(), batch_k2_smem<4>()),
@@ -292,18 +333,21 @@ struct BatchTables {
     const int *v_map;   // CTA -> item for K2 / K3 launches
 };
 
-template <int MODE>
-__global__ void __launch_bounds__(kBatchThreads, 2) cg_spmv_batched(BatchTables bt) {
-    __shared__ __align__(16) unsigned char raw[kBatchK1Smem];
+template <int MODE, int TH>
+__global__ void __launch_bounds__(TH, 1024 / TH) cg_spmv_batched(BatchTables bt) {
+    extern __shared__ __align__(16) unsigned char raw[];   // batch_k1_smem<TH>() bytes
     const BItem &it = bt.items[__ldg(bt.k1_map + blockIdx.x)];
     const int cta = blockIdx.x - it.k1_cta0;
+#define ENS_BK1(SS) \
+    k1_body<SS, MODE, BatchK1<SS, TH>::NSUB>(it.a, cta, *reinterpret_cast<typename BatchK1<SS, TH>::Smem *>(raw))
     switch (it.S) {
-        case 1: k1_body<1, MODE, BatchK1<1>::NSUB>(it.a, cta, *reinterpret_cast<BatchK1<1>::Smem *>(raw)); break;
-        case 4: k1_body<4, MODE, BatchK1<4>::NSUB>(it.a, cta, *reinterpret_cast<BatchK1<4>::Smem *>(raw)); break;
-        case 8: k1_body<8, MODE, BatchK1<8>::NSUB>(it.a, cta, *reinterpret_cast<BatchK1<8>::Smem *>(raw)); break;
-        case 16: k1_body<16, MODE, BatchK1<16>::NSUB>(it.a, cta, *reinterpret_cast<BatchK1<16>::Smem *>(raw)); break;
-        default: k1_body<32, MODE, BatchK1<32>::NSUB>(it.a, cta, *reinterpret_cast<BatchK1<32>::Smem *>(raw)); break;
+        case 1: ENS_BK1(1); break;
+        case 4: ENS_BK1(4); break;
+        case 8: ENS_BK1(8); break;
+        case 16: ENS_BK1(16); break;
+        default: ENS_BK1(32); break;
     }
+#undef ENS_BK1
 }
 
 template <int S>
@@ -311,7 +355,7 @@ __device__ __forceinline__ void k2_batched_s(const CgArgs &a, int cta, unsigned 
     k2_body<S, kBatchThreads>(a, cta, reinterpret_cast<double(*)[32][S + 1]>(raw));
 }
 
-__global__ void __launch_bounds__(kBatchThreads) cg_resid_batched(BatchTables bt) {
+__global__ void __launch_bounds__(kBatchThreads, 2) cg_resid_batched(BatchTables bt) {
     __shared__ __align__(16) unsigned char raw[kBatchK2Smem];
     const BItem &it = bt.items[__ldg(bt.v_map + blockIdx.x)];
     const int cta = blockIdx.x - it.v_cta0;
@@ -379,6 +423,7 @@ static void cg_layout_args(CgArgs &a, const ens_graph *g, int S, const double *v
     a.x0_zero = (flags & ENS_CG_X0_ZERO) ? 1 : 0;
     a.pf_cap = 0;
     a.val_bytes = 0;
+    a.k2_pf = k2_prefetch();
 }
 
 template <int MODE>
@@ -397,8 +442,8 @@ static void launch_single(int which, int S, const CgArgs &a, cudaStream_t st) {
 #undef ENS_ONE
 }
 
-static int64_t batch_k1_ctas(int S, int64_t chunks) {
-    const int nsub = kBatchThreads / (32 * ((S == 1) ? 2 : S / 2));
+static int64_t batch_k1_ctas(int S, int64_t chunks, int th = kBatchThreads) {
+    const int nsub = th / (32 * ((S == 1) ? 2 : S / 2));
     return (chunks + nsub - 1) / nsub;
 }
 static int64_t batch_v_ctas(int S, int64_t chunks) {
@@ -433,11 +478,22 @@ static BatchPlan batch_plan(int n_items, const ens_batch_item *items) {
     return p;
 }
 
+template <int MODE, int TH>
+static void launch_k1_batched(unsigned grid, const BatchTables &bt, cudaStream_t st) {
+    cg_spmv_batched<MODE, TH><<<grid, TH, batch_k1_smem<TH>(), st>>>(bt);
+}
+
 template <int MODE>
 static int batched_run(int n_items, const ens_batch_item *items, double tol, int max_iter,
                        int flags, int check_every, void *work, ens_cg_stats *stats,
                        cudaStream_t st) {
     const BatchPlan plan = batch_plan(n_items, items);
+    // K1 CTA size: the plan's CTA maps are sized for 512 threads, the most CTAs
+    const int th = (flags & ENS_CG_BATCH_K1_WIDE) ? 1024 : kBatchThreads;
+    ENS_CUDA_TRY(cudaFuncSetAttribute(cg_spmv_batched<MODE, 512>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)batch_k1_smem<512>()));
+    ENS_CUDA_TRY(cudaFuncSetAttribute(cg_spmv_batched<MODE, 1024>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)batch_k1_smem<1024>()));
     char *w = static_cast<char *>(work);
     BItem *d_items = reinterpret_cast<BItem *>(w);
     int *d_poll = reinterpret_cast<int *>(w + align256(sizeof(BItem) * n_items));
@@ -455,12 +511,12 @@ static int batched_run(int n_items, const ens_batch_item *items, double tol, int
         if (MODE == 3) {  // pre-split values; a whole-chunk CTA prefetches its value block into L2
             h[i].a.vdf = reinterpret_cast<const float2 *>(it.values_df);
             h[i].a.val_bytes = (uint64_t)it.graph.num_entries * it.s * 8u;
-            h[i].a.pf_cap = (kBatchThreads / (32 * ((it.s == 1) ? 2 : it.s / 2)) == 1) ? l2_prefetch_cap(3) : 0u;
+            h[i].a.pf_cap = l2_prefetch_cap(3);
         }
         wi += cg_bytes(it.graph.num_rows, it.s);
         h[i].S = it.s;
         const int64_t chunks = h[i].a.t1.count[1];
-        const int64_t nk = batch_k1_ctas(it.s, chunks), nv = batch_v_ctas(it.s, chunks);
+        const int64_t nk = batch_k1_ctas(it.s, chunks, th), nv = batch_v_ctas(it.s, chunks);
         h[i].k1_cta0 = (int)k1c;
         h[i].v_cta0 = (int)vc;
         for (int64_t c = 0; c < nk; ++c) k1map[k1c++] = i;
@@ -476,7 +532,7 @@ static int batched_run(int n_items, const ens_batch_item *items, double tol, int
     for (int i = 0; i < n_items; ++i) { launch_single<MODE>(0, h[i].S, h[i].a, st); launches += 2; }
     ENS_LAUNCH_CHECK("batched cg init");
     const BatchTables bt{d_items, d_k1map, d_vmap};
-    const unsigned g1 = (unsigned)plan.k1_total, gv = (unsigned)plan.v_total;
+    const unsigned g1 = (unsigned)k1c, gv = (unsigned)plan.v_total;
     const bool timing = (flags & ENS_CG_TIME_SPMV) != 0;
     const bool use_graph = (flags & ENS_CG_GRAPH) != 0 && !timing;
     std::vector<cudaEvent_t> ev;
@@ -491,7 +547,8 @@ static int batched_run(int n_items, const ens_batch_item *items, double tol, int
     } guard{ev};
     auto iteration = [&](cudaStream_t s2, int i) {
         if (timing) cudaEventRecord(ev[2 * i], s2);
-        cg_spmv_batched<MODE><<<g1, kBatchThreads, 0, s2>>>(bt);
+        if (th == 1024) launch_k1_batched<MODE, 1024>(g1, bt, s2);
+        else launch_k1_batched<MODE, 512>(g1, bt, s2);
         if (timing) cudaEventRecord(ev[2 * i + 1], s2);
         cg_resid_batched<<<gv, kBatchThreads, 0, s2>>>(bt);
         cg_update_batched<MODE><<<gv, kBatchThreads, 0, s2>>>(bt);
@@ -607,6 +664,9 @@ static int cg_entry(const ens_graph *graph, int s, const double *values, const f
         return fail(ENS_ERR_ALIGN, "values/b/x/work must be 16-byte aligned");
     const size_t need = cg_bytes(graph->num_rows, s);
     if (work_bytes < need) return fail(ENS_ERR_WORKSPACE, "cg workspace %zu < %zu bytes", work_bytes, need);
+    if (k1_nsub_from_flags(flags, s, 0) < 0)
+        return fail(ENS_ERR_ARG, "ENS_CG_K1_CHUNKS field %d: at most %d chunks of 32 rows per K1 CTA at s=%d",
+                    (flags >> ENS_CG_K1_CHUNKS_SHIFT) & 7, k1_max_nsub_rt(s), s);
     CgHostOut out{iters_host, relres_host, status_host, stats_host};
     cudaStream_t st = as_stream(stream);
     switch (s) {

@@ -1,0 +1,4 @@
+// ens_cg_k1_s8.cu -- K1 (q = A p, p.q) instantiations for ensemble size 8.
+#include "ens_cg_k1.cuh"
+
+ENS_K1_INSTANTIATE(8)

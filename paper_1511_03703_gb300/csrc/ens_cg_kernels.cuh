@@ -33,6 +33,7 @@ struct CgArgs {
     int x0_zero;   // the caller states x0 = 0: r0 = b without the initial SpMV
     uint32_t pf_cap;       // bytes of each chunk's value block prefetched into L2 by K1
     uint64_t val_bytes;    // size of the value array read by K1 (8 bytes per value in every form)
+    int k2_pf;             // K2 prefetches its CTA's r and q blocks into L2 at its start
 };
 
 // mapping of the streaming vector kernels (K2, K3): a CTA of TH threads owns
@@ -173,25 +174,23 @@ __global__ void cg_zero_kernel(CgArgs a) {
 }
 
 // ------------------------------------------------------------------ K1
-// Body of the batched kernel: NSUB chunks of one ensemble per CTA, each on
-// its own thread group.  Its arithmetic is that of cg_spmv_kernel below (kept
-// as a separate copy because the shared form needs more registers there).
+// q = A p and the per-member p.q for NSUB chunks of one ensemble per CTA,
+// each chunk on its own group of 32 * RowMap<S>::G threads (the standalone
+// kernel and the batched one share this body).  NSUB changes only the launch
+// mapping: every sum is ordered by row index, so results are bitwise the same
+// for every NSUB.
 template <int S, int NSUB>
 struct K1Smem {
     double sm[NSUB][32][S + 1];
     ChunkCols cc[NSUB];
 };
 
+template <int S>
+__device__ __forceinline__ void k1_epilogue(const CgArgs &a);
+
 template <int S, int MODE, int NSUB>
 __device__ __forceinline__ void k1_body(const CgArgs &a, const int cta, K1Smem<S, NSUB> &sh) {
     CgState *st = a.st;
-    if (ld_cg(&st->active_count) == 0) {
-        if (cta == 0 && threadIdx.x == 0 && st->updx_any) {
-            for (int e = 0; e < S; ++e) st->updx[e] = 0;
-            st->updx_any = 0;
-        }
-        return;
-    }
     constexpr int G = RowMap<S>::G, T = RowMap<S>::THREADS;
     const int sub = (NSUB == 1) ? 0 : (int)threadIdx.x / T;
     const int ltid = (NSUB == 1) ? (int)threadIdx.x : (int)threadIdx.x % T;
@@ -199,16 +198,26 @@ __device__ __forceinline__ void k1_body(const CgArgs &a, const int cta, K1Smem<S
 #define K1_CHUNK ((int64_t)cta * NSUB + sub)
     const int64_t chunk = K1_CHUNK;
     const bool valid = chunk * 32 + r < a.n;
-    // the split / double-float forms are used unless a vector element fell outside their range
-    const int mode = (MODE != 0 && ld_cg(&st->df_bad_any) != 0) ? 0 : MODE;
     bool staged;
     if constexpr (NSUB == 1) {
         if (MODE == 3) staged = stage_chunk_pf(sh.cc[0], a.row_map, a.col, chunk, a.n, a.vdf, S * 8u, a.val_bytes,
                                                a.pf_cap);
         else staged = stage_chunk(sh.cc[0], a.row_map, a.col, chunk, a.n);
+    } else if (MODE == 3) {
+        staged = stage_chunk_sub(sh.cc[sub], a.row_map, a.col, chunk, a.n, ltid, T, a.vdf, S * 8u, a.val_bytes,
+                                 a.pf_cap);
     } else {
         staged = stage_chunk_sub(sh.cc[sub], a.row_map, a.col, chunk, a.n, ltid, T);
     }
+    if (ld_cg(&st->active_count) == 0) {   // every member stopped: a launch queued past convergence
+        if (cta == 0 && threadIdx.x == 0 && st->updx_any) {
+            for (int e = 0; e < S; ++e) st->updx[e] = 0;
+            st->updx_any = 0;
+        }
+        return;
+    }
+    // the split / double-float forms are used unless a vector element fell outside their range
+    const int mode = (MODE != 0 && ld_cg(&st->df_bad_any) != 0) ? 0 : MODE;
     double2 apv;
     if (MODE == 1 && mode == 1)
         apv = chunk_spmv_df<S, XPre>(sh.cc[sub], staged, a.col, a.vals, a.pdf, r, g, valid);
@@ -251,7 +260,14 @@ __device__ __forceinline__ void k1_body(const CgArgs &a, const int cta, K1Smem<S
     if (!dot_tree_propagate(a.t1, (int64_t)cta * NSUB, nitems)) return;
 #undef K1_CHUNK
     if (threadIdx.x >= 32) return;
-    // epilogue: one lane per member
+    k1_epilogue<S>(a);
+}
+
+// K1's per-member scalar work, run by warp 0 of the CTA that produced the
+// top of p.q's tree: alpha = rho / p.q, breakdown, the active count
+template <int S>
+__device__ __forceinline__ void k1_epilogue(const CgArgs &a) {
+    CgState *st = a.st;
     const unsigned FULL = 0xffffffffu;
     const int e = threadIdx.x;
     const double *top = a.t1.buf[a.t1.levels];
@@ -286,36 +302,30 @@ __device__ __forceinline__ void k1_body(const CgArgs &a, const int cta, K1Smem<S
     __threadfence();
 }
 
-// single-ensemble K1 (one chunk per CTA); same arithmetic as k1_body
-#ifndef ENS_K1_DFV_THREADS_PER_SM
-#define ENS_K1_DFV_THREADS_PER_SM 1536
-#endif
-template <int S, int MODE>
-struct K1Occ {
-    static constexpr int THREADS_PER_SM = (MODE == 3) ? ENS_K1_DFV_THREADS_PER_SM : 1536;
-};
-
-template <int S, int MODE>
-__global__ void __launch_bounds__(RowMap<S>::THREADS, K1Occ<S, MODE>::THREADS_PER_SM / RowMap<S>::THREADS)
-    cg_spmv_kernel(CgArgs a) {
+// K1 with one chunk per CTA: the arithmetic of k1_body<S, MODE, 1>, written
+// out with fewer live indices so that it keeps to 40 registers (3 CTAs of 512
+// threads per SM at s = 32) with little spilling.  VEC, WARP: column staging
+// with 16-byte loads, chunk tree by warp shuffles.
+template <int S, int MODE, bool VEC, bool WARP>
+__device__ __forceinline__ void k1_single(const CgArgs &a) {
     CgState *st = a.st;
-    if (ld_cg(&st->active_count) == 0) {
+    constexpr int G = RowMap<S>::G;
+    __shared__ double sm[32][S + 1];
+    const int r = threadIdx.x / G, g = threadIdx.x % G;
+    const int64_t R = (int64_t)blockIdx.x * 32 + r;
+    __shared__ ChunkCols cc;
+    const void *vblock = (MODE == 3) ? static_cast<const void *>(a.vdf) : static_cast<const void *>(a.vals);
+    const bool staged = stage_chunk_pf<VEC>(cc, a.row_map, a.col, blockIdx.x, a.n, vblock, S * 8u, a.val_bytes,
+                                            a.pf_cap);
+    if (ld_cg(&st->active_count) == 0) {   // every member stopped: a launch queued past convergence
         if (blockIdx.x == 0 && threadIdx.x == 0 && st->updx_any) {
             for (int e = 0; e < S; ++e) st->updx[e] = 0;
             st->updx_any = 0;
         }
         return;
     }
-    constexpr int G = RowMap<S>::G;
-    __shared__ double sm[32][S + 1];
-    const int r = threadIdx.x / G, g = threadIdx.x % G;
-    const int64_t R = (int64_t)blockIdx.x * 32 + r;
-    // the split form is used unless a vector element fell outside its range
+    // the split / double-float forms are used unless a vector element fell outside their range
     const int mode = (MODE != 0 && ld_cg(&st->df_bad_any) != 0) ? 0 : MODE;
-    __shared__ ChunkCols cc;
-    const void *vblock = (MODE == 3) ? static_cast<const void *>(a.vdf) : static_cast<const void *>(a.vals);
-    const bool staged = stage_chunk_pf(cc, a.row_map, a.col, blockIdx.x, a.n, vblock, S * 8u, a.val_bytes,
-                                       a.pf_cap);
     double2 apv;
     if (MODE == 1 && mode == 1)
         apv = chunk_spmv_df<S, XPre>(cc, staged, a.col, a.vals, a.pdf, r, g, R < a.n);
@@ -326,8 +336,7 @@ __global__ void __launch_bounds__(RowMap<S>::THREADS, K1Occ<S, MODE>::THREADS_PE
     else
         apv = chunk_spmv<S, double>(cc, staged, a.col, a.vals, a.p, r, g, R < a.n);
     // p.q: the double-float forms take p as the SpMV saw it, hi + lo of the
-    // split copy (exact in FP64; the SpMV's neighbours' gathers have usually
-    // brought it into L2), which saves reading the FP64 p
+    // split copy (exact in FP64), which saves reading the FP64 p
     const bool pre = (MODE == 1 || MODE == 3) && mode == MODE;
     double v0 = 0.0, v1 = 0.0;
     if constexpr (S == 1) {
@@ -356,43 +365,51 @@ __global__ void __launch_bounds__(RowMap<S>::THREADS, K1Occ<S, MODE>::THREADS_PE
         v0 = ap.x * pv.x;
         v1 = ap.y * pv.y;
     }
-    chunk_tree<S>(sm, v0, v1, r, g, a.t1, blockIdx.x, 0);
+    chunk_tree<S, WARP>(sm, v0, v1, r, g, a.t1, blockIdx.x, 0);
     if (!dot_tree_propagate(a.t1, blockIdx.x, 1)) return;
     if (threadIdx.x >= 32) return;
-    // epilogue: one lane per member
-    const unsigned FULL = 0xffffffffu;
-    const int e = threadIdx.x;
-    const double *top = a.t1.buf[a.t1.levels];
-    const double pi = (e < S) ? ld_cg(top + e) : 0.0;
-    const double rho = (e < S) ? st->rho[e] : 0.0;
-    int act = (e < S) ? st->active[e] : 0;
-    if (a.coupled) {
-        double pis = 0.0, rhos = 0.0;
-        for (int k = 0; k < S; ++k) {
-            pis += __shfl_sync(FULL, pi, k);
-            rhos += __shfl_sync(FULL, rho, k);
-        }
-        const bool bad = !(pis > 0.0) || !isfinite(pis);
-        if (act) {
-            if (bad) { act = 0; st->status[e] = ENS_ERR_BREAKDOWN; }
-            else st->alpha[e] = rhos / pis;
-        }
-    } else if (act) {
-        if (!(pi > 0.0) || !isfinite(pi)) { act = 0; st->status[e] = ENS_ERR_BREAKDOWN; }
-        else st->alpha[e] = rho / pi;
-    }
-    if (e < S) {
-        st->active[e] = act;
-        st->updx[e] = 0;  // consumed by the previous K3
-    }
-    const int ac = __popc(__ballot_sync(FULL, act));
-    if (e == 0) {
-        st->spmv_real += 1;
-        st->updx_any = 0;
-        st->active_count = ac;
-    }
-    __threadfence();
+    k1_epilogue<S>(a);
 }
+
+// standalone K1: NSUB chunks per CTA (NSUB * 32 * RowMap<S>::G <= 1024
+// threads); one chunk at up to 1536 threads per SM (40 registers), several
+// at up to 1024 (64 registers)
+#ifndef ENS_K1_DFV_THREADS_PER_SM
+#define ENS_K1_DFV_THREADS_PER_SM 1536
+#endif
+// Threads per SM the register budget is sized for: 1536 (40 registers) where
+// the SpMV runs fastest with the most CTAs in flight (s = 1, 16, 32), 1024
+// (64 registers) at s = 4 and 8, where the spilled row-loop state costs more
+// than the lost occupancy (64^3 mesh, pre-split form: s = 4 0.115 -> 0.089
+// ms, s = 8 0.139 -> 0.134 ms).
+template <int S, int MODE, int NSUB>
+struct K1Launch {
+    static constexpr int THREADS = NSUB * RowMap<S>::THREADS;
+    static constexpr int PER_SM = (NSUB > 1 || S == 4 || S == 8) ? 1024
+                                  : (MODE == 3) ? ENS_K1_DFV_THREADS_PER_SM : 1536;
+    static constexpr int MIN_BLOCKS = (PER_SM / THREADS) > 0 ? PER_SM / THREADS : 1;
+};
+
+template <int S, int MODE, int NSUB>
+__global__ void __launch_bounds__(K1Launch<S, MODE, NSUB>::THREADS, K1Launch<S, MODE, NSUB>::MIN_BLOCKS)
+    cg_spmv_kernel(CgArgs a) {
+    if constexpr (NSUB == 1) {
+        k1_single<S, MODE, true, true>(a);
+    } else {
+        __shared__ K1Smem<S, NSUB> sh;
+        k1_body<S, MODE, NSUB>(a, blockIdx.x, sh);
+    }
+}
+
+// Host: chunks of 32 rows per K1 CTA (1, 2, 4 or 8; at most 1024 threads per
+// CTA).  k1_launch launches K1 with that mapping; its instantiations live in
+// ens_cg_k1_s*.cu (one translation unit per ensemble size).
+template <int S>
+constexpr int k1_max_nsub() { return (1024 / RowMap<S>::THREADS) >= 8 ? 8 : 1024 / RowMap<S>::THREADS; }
+int k1_max_nsub_rt(int s);
+int k1_default_nsub(int s, int mode);
+template <int S, int MODE>
+void k1_launch(const CgArgs &a, int nsub, cudaStream_t st);
 
 
 // ------------------------------------------------------------------ K2
@@ -450,8 +467,15 @@ template <int S, int TH>
 __device__ __forceinline__ void k2_body(const CgArgs &a, int cta,
                                         double (*sm)[32][S + 1] /* [CPC][32][S+1] */) {
     using VM = VecMap<S, TH>;
-    if (ld_cg(&a.st->active_count) == 0) return;
     constexpr int VG = VM::VG;
+    const int64_t first_chunk = (int64_t)cta * VM::CPC;
+    if (a.k2_pf && threadIdx.x == 0) {   // the passes below then read r and q from L2
+        const uint64_t b0 = (uint64_t)first_chunk * 32 * S * 8u;
+        const uint64_t b1 = (uint64_t)min((first_chunk + VM::CPC) * 32, (int64_t)a.n) * S * 8u;
+        l2_prefetch_span(a.r, b0, b1);
+        l2_prefetch_span(a.q, b0, b1);
+    }
+    if (ld_cg(&a.st->active_count) == 0) return;
     const int cip = threadIdx.x / VM::CHUNK_T, lt = threadIdx.x % VM::CHUNK_T;
     const int r = lt / VG, g = lt % VG;
     const CgState *cs = a.st;
@@ -460,7 +484,6 @@ __device__ __forceinline__ void k2_body(const CgArgs &a, int cta,
     const bool act1 = (S == 1) ? false : (bool)cs->active[m + 1];
     const double al0 = cs->alpha[m];
     const double al1 = (S == 1) ? 0.0 : cs->alpha[m + 1];
-    const int64_t first_chunk = (int64_t)cta * VM::CPC;
     // r.r: squares and the chunk's 32-row tree in double-float on the FP32
     // pipe (the FP64 pipe keeps only the r update); the chunk sums enter the
     // FP64 dot tree above the chunk
@@ -489,7 +512,8 @@ __device__ __forceinline__ void k2_body(const CgArgs &a, int cta,
         if constexpr (S > 1) sf[c][r][m + 1] = v1;
     }
     __syncthreads();
-    // halving tree over the 32 rows of every chunk, all members packed
+    // halving tree over the 32 rows of every chunk, all members packed (every
+    // thread of the CTA busy at each level)
 #pragma unroll
     for (int h = 16; h >= 1; h >>= 1) {
         for (int it = threadIdx.x; it < VM::CPC * h * S; it += VM::THREADS) {
@@ -599,7 +623,7 @@ __device__ __forceinline__ void k3_body(const CgArgs &a, int cta) {
 }
 
 template <int S>
-__global__ void __launch_bounds__(VecMap<S>::THREADS) cg_resid_kernel(CgArgs a) {
+__global__ void __launch_bounds__(VecMap<S>::THREADS, 1536 / VecMap<S>::THREADS) cg_resid_kernel(CgArgs a) {
     __shared__ double sm[VecMap<S>::CPC][32][S + 1];   // per-row products of every chunk
     k2_body<S, VecMap<S>::THREADS>(a, blockIdx.x, sm);
 }

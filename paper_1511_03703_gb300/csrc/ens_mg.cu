@@ -175,7 +175,7 @@ static int mg_run(int nl, const ens_mg_level *levels, const double *b, double *x
         cudaError_t ce = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
         if (ce == cudaSuccess) {
             for (int i = 0; i < check_every; ++i) {
-                cg_spmv_kernel<S, MODE><<<grid, RowMap<S>::THREADS, 0, cap>>>(c);
+                k1_launch<S, MODE>(c, k1_default_nsub(S, MODE), cap);
                 stage(0, cap);
             }
             ce = cudaStreamEndCapture(cap, &graph);
@@ -195,7 +195,7 @@ static int mg_run(int nl, const ens_mg_level *levels, const double *b, double *x
             if (ce != cudaSuccess) { rc = cuda_fail(ce, "cudaGraphLaunch"); break; }
         } else {
             for (int i = 0; i < check_every; ++i) {
-                cg_spmv_kernel<S, MODE><<<grid, RowMap<S>::THREADS, 0, st>>>(c);
+                k1_launch<S, MODE>(c, k1_default_nsub(S, MODE), st);
                 stage(0, st);
             }
         }

@@ -232,7 +232,7 @@ static int pcg_run(const ens_graph *g, const double *vals, const double *b, doub
         cudaError_t ce = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
         if (ce == cudaSuccess) {
             for (int i = 0; i < check_every; ++i) {
-                cg_spmv_kernel<S, 0><<<grid, RowMap<S>::THREADS, 0, cap>>>(c);
+                k1_launch<S, 0>(c, k1_default_nsub(S, 0), cap);
                 precond(0, cap);
             }
             ce = cudaStreamEndCapture(cap, &graph);
@@ -252,7 +252,7 @@ static int pcg_run(const ens_graph *g, const double *vals, const double *b, doub
             if (ce != cudaSuccess) { rc = cuda_fail(ce, "cudaGraphLaunch"); break; }
         } else {
             for (int i = 0; i < check_every; ++i) {
-                cg_spmv_kernel<S, 0><<<grid, RowMap<S>::THREADS, 0, st>>>(c);
+                k1_launch<S, 0>(c, k1_default_nsub(S, 0), st);
                 precond(0, st);
             }
         }

@@ -30,6 +30,8 @@
 //    FMAs (rows where every product is below 2^-149 return 0, an absolute
 //    error below 27 * 2^-149).
 #pragma once
+#include <stddef.h>
+
 #include "ens_internal.cuh"
 
 namespace ens {
@@ -80,16 +82,21 @@ __device__ __forceinline__ double2 ld_x2(const double *x, int64_t i) {
 
 // ------------------------------------------------------ column staging
 // A CTA stages the row offsets and column indices of its 32-row chunk in
-// shared memory (one coalesced copy), so each x gather waits for one shared
-// load instead of a dependent global load.  Chunks with more than kColCap
-// entries (not produced by the hex mesh, whose rows hold at most 27) read
-// their columns from global memory instead.
+// shared memory, so each x gather waits for one shared load instead of a
+// dependent global load.  The columns are copied with 16-byte loads, every
+// load of a thread issued before its first shared store, starting at the
+// chunk's first entry rounded down to a multiple of 4 (col[base] holds entry
+// `base`).  Chunks with more than kColCap entries (not produced by the hex
+// mesh, whose rows hold at most 27) read their columns from global memory.
 constexpr int kColCap = 1024;
 
-struct ChunkCols {
+struct __align__(16) ChunkCols {
     int rm[33];
+    int base;      // entry index of col[0]: the chunk's first entry rounded down to a multiple of 4
+    int pad[2];
     int col[kColCap];
 };
+static_assert(offsetof(ChunkCols, col) % 16 == 0, "staged columns must be 16-byte aligned");
 
 struct ColShared {
     const int *s;
@@ -101,6 +108,38 @@ struct ColGlobal {
     __device__ __forceinline__ int operator()(int j) const { return __ldg(p + j); }
 };
 
+// columns [e0, e1) into cc.col (threads tid = 0..nthr-1 of the caller's group);
+// reads only whole 16-byte groups inside [base, e1) plus at most 3 single
+// entries before e1, so nothing past the chunk's last entry is touched.
+// VEC = false: one entry per load.
+template <bool VEC = true>
+__device__ __forceinline__ void stage_cols(ChunkCols &cc, const int32_t *__restrict__ col, int e0, int e1,
+                                           int tid, int nthr) {
+    const int base = e0 & ~3;
+    if (!VEC || (reinterpret_cast<uintptr_t>(col) & 15u)) {   // column array not 16-byte aligned: one entry per load
+        for (int i = base + tid; i < e1; i += nthr) cc.col[i - base] = __ldg(col + i);
+        if (tid == 0) cc.base = base;
+        return;
+    }
+    const int v0 = base >> 2, v1 = e1 >> 2;
+    const int nv = v1 - v0;
+    const int4 *c4 = reinterpret_cast<const int4 *>(col) + v0;
+    int4 *d4 = reinterpret_cast<int4 *>(cc.col);
+    for (int k0 = tid; k0 < nv; k0 += 4 * nthr) {
+        int4 t[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+            if (k0 + u * nthr < nv) t[u] = __ldg(c4 + k0 + u * nthr);
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+            if (k0 + u * nthr < nv) d4[k0 + u * nthr] = t[u];
+    }
+    for (int i = 4 * max(v1, v0) + tid; i < e1; i += nthr) cc.col[i - base] = __ldg(col + i);
+    if (tid == 0) cc.base = base;
+}
+
+__device__ __forceinline__ bool chunk_fits(int e0, int e1) { return e1 - (e0 & ~3) <= kColCap; }
+
 // all threads of the CTA; returns true when the columns are staged
 __device__ __forceinline__ bool stage_chunk(ChunkCols &cc, const int32_t *__restrict__ row_map,
                                             const int32_t *__restrict__ col, int64_t chunk,
@@ -109,10 +148,9 @@ __device__ __forceinline__ bool stage_chunk(ChunkCols &cc, const int32_t *__rest
     const int nr = (int)min((int64_t)32, (int64_t)n - r0);
     for (int i = threadIdx.x; i <= nr; i += blockDim.x) cc.rm[i] = __ldg(row_map + r0 + i);
     __syncthreads();
-    const int e0 = cc.rm[0], cnt = cc.rm[nr] - e0;
-    const bool staged = cnt <= kColCap;
-    if (staged)
-        for (int i = threadIdx.x; i < cnt; i += blockDim.x) cc.col[i] = __ldg(col + e0 + i);
+    const int e0 = cc.rm[0], e1 = cc.rm[nr];
+    const bool staged = chunk_fits(e0, e1);
+    if (staged) stage_cols(cc, col, e0, e1, threadIdx.x, blockDim.x);
     __syncthreads();
     return staged;
 }
@@ -135,6 +173,17 @@ __device__ __forceinline__ void l2_prefetch_bulk(const void *base, uint64_t begi
                  :: "l"(p), "r"((uint32_t)(end - begin)), "l"(policy) : "memory");
 }
 
+// L2 prefetch of [begin, end) bytes of an array (rounded inward to 16-byte
+// boundaries; normal eviction priority), for data a kernel reads soon
+__device__ __forceinline__ void l2_prefetch_span(const void *base, uint64_t begin, uint64_t end) {
+    begin = (begin + 15) & ~(uint64_t)15;
+    end &= ~(uint64_t)15;
+    if (end <= begin) return;
+    const char *p = static_cast<const char *>(base) + begin;
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"((uint32_t)(end - begin)) : "memory");
+}
+
+template <bool VEC = true>
 __device__ __forceinline__ bool stage_chunk_pf(ChunkCols &cc, const int32_t *__restrict__ row_map,
                                                const int32_t *__restrict__ col, int64_t chunk, int32_t n,
                                                const void *vbase, uint32_t bytes_per_entry,
@@ -143,23 +192,25 @@ __device__ __forceinline__ bool stage_chunk_pf(ChunkCols &cc, const int32_t *__r
     const int nr = (int)min((int64_t)32, (int64_t)n - r0);
     for (int i = threadIdx.x; i <= nr; i += blockDim.x) cc.rm[i] = __ldg(row_map + r0 + i);
     __syncthreads();
-    const int e0 = cc.rm[0], cnt = cc.rm[nr] - e0;
+    const int e0 = cc.rm[0], e1 = cc.rm[nr];
     if (threadIdx.x == 0 && cap > 0)
-        l2_prefetch_bulk(vbase, (uint64_t)e0 * bytes_per_entry, (uint64_t)cc.rm[nr] * bytes_per_entry,
-                         total_bytes, cap);
-    const bool staged = cnt <= kColCap;
-    if (staged)
-        for (int i = threadIdx.x; i < cnt; i += blockDim.x) cc.col[i] = __ldg(col + e0 + i);
+        l2_prefetch_bulk(vbase, (uint64_t)e0 * bytes_per_entry, (uint64_t)e1 * bytes_per_entry, total_bytes, cap);
+    const bool staged = chunk_fits(e0, e1);
+    if (staged) stage_cols<VEC>(cc, col, e0, e1, threadIdx.x, blockDim.x);
     __syncthreads();
     return staged;
 }
 
 // Subset form used when one CTA works on NSUB chunks at once (nthr threads
 // per chunk, ltid the thread's index inside its chunk): the same copy, with
-// chunks past the end of the matrix left empty.  All threads of the CTA call it.
+// chunks past the end of the matrix left empty, and (cap > 0) each chunk's
+// value block prefetched into L2 as in stage_chunk_pf.  All threads of the
+// CTA call it.
 __device__ __forceinline__ bool stage_chunk_sub(ChunkCols &cc, const int32_t *__restrict__ row_map,
                                                 const int32_t *__restrict__ col, int64_t chunk,
-                                                int32_t n, int ltid, int nthr) {
+                                                int32_t n, int ltid, int nthr, const void *vbase = nullptr,
+                                                uint32_t bytes_per_entry = 0, uint64_t total_bytes = 0,
+                                                uint32_t cap = 0) {
     const int64_t r0 = chunk * 32;
     const int nr = (int)max((int64_t)0, min((int64_t)32, (int64_t)n - r0));
     if (nr > 0)
@@ -167,10 +218,11 @@ __device__ __forceinline__ bool stage_chunk_sub(ChunkCols &cc, const int32_t *__
     else if (ltid == 0)
         cc.rm[0] = 0;
     __syncthreads();
-    const int e0 = cc.rm[0], cnt = (nr > 0) ? cc.rm[nr] - e0 : 0;
-    const bool staged = cnt <= kColCap;
-    if (staged)
-        for (int i = ltid; i < cnt; i += nthr) cc.col[i] = __ldg(col + e0 + i);
+    const int e0 = cc.rm[0], e1 = (nr > 0) ? cc.rm[nr] : e0;
+    if (ltid == 0 && cap > 0 && e1 > e0)
+        l2_prefetch_bulk(vbase, (uint64_t)e0 * bytes_per_entry, (uint64_t)e1 * bytes_per_entry, total_bytes, cap);
+    const bool staged = chunk_fits(e0, e1);
+    if (staged) stage_cols(cc, col, e0, e1, ltid, nthr);
     __syncthreads();
     return staged;
 }
@@ -685,12 +737,12 @@ __device__ __forceinline__ double2 chunk_spmv(const ChunkCols &cc, bool staged,
                                               bool valid) {
     const int rs = valid ? cc.rm[r] : 0, re = valid ? cc.rm[r + 1] : 0;
     if constexpr (S == 1) {
-        const double v = staged ? row_spmv1<V>(ColShared{cc.col, cc.rm[0]}, rs, re, vals, x, g, valid)
+        const double v = staged ? row_spmv1<V>(ColShared{cc.col, cc.base}, rs, re, vals, x, g, valid)
                                 : row_spmv1<V>(ColGlobal{col}, rs, re, vals, x, g, valid);
         return make_double2(v, 0.0);
     } else {
         if (!valid) return make_double2(0.0, 0.0);
-        return staged ? row_spmv2<S, V>(ColShared{cc.col, cc.rm[0]}, rs, re, vals, x, g)
+        return staged ? row_spmv2<S, V>(ColShared{cc.col, cc.base}, rs, re, vals, x, g)
                       : row_spmv2<S, V>(ColGlobal{col}, rs, re, vals, x, g);
     }
 }
@@ -703,12 +755,12 @@ __device__ __forceinline__ double2 chunk_spmv_df(const ChunkCols &cc, bool stage
                                                  bool valid) {
     const int rs = valid ? cc.rm[r] : 0, re = valid ? cc.rm[r + 1] : 0;
     if constexpr (S == 1) {
-        const double v = staged ? row_spmv1_df<XS>(ColShared{cc.col, cc.rm[0]}, rs, re, vals, x, g, valid)
+        const double v = staged ? row_spmv1_df<XS>(ColShared{cc.col, cc.base}, rs, re, vals, x, g, valid)
                                 : row_spmv1_df<XS>(ColGlobal{col}, rs, re, vals, x, g, valid);
         return make_double2(v, 0.0);
     } else {
         if (!valid) return make_double2(0.0, 0.0);
-        return staged ? row_spmv2_df<S, XS>(ColShared{cc.col, cc.rm[0]}, rs, re, vals, x, g)
+        return staged ? row_spmv2_df<S, XS>(ColShared{cc.col, cc.base}, rs, re, vals, x, g)
                       : row_spmv2_df<S, XS>(ColGlobal{col}, rs, re, vals, x, g);
     }
 }
@@ -721,12 +773,12 @@ __device__ __forceinline__ double2 chunk_spmv_dfv(const ChunkCols &cc, bool stag
                                                   typename XS::ptr __restrict__ x, int r, int g, bool valid) {
     const int rs = valid ? cc.rm[r] : 0, re = valid ? cc.rm[r + 1] : 0;
     if constexpr (S == 1) {
-        const double v = staged ? row_spmv1_dfv<XS>(ColShared{cc.col, cc.rm[0]}, rs, re, vdf, vals, x, g, valid)
+        const double v = staged ? row_spmv1_dfv<XS>(ColShared{cc.col, cc.base}, rs, re, vdf, vals, x, g, valid)
                                 : row_spmv1_dfv<XS>(ColGlobal{col}, rs, re, vdf, vals, x, g, valid);
         return make_double2(v, 0.0);
     } else {
         if (!valid) return make_double2(0.0, 0.0);
-        return staged ? row_spmv2_dfv<S, XS>(ColShared{cc.col, cc.rm[0]}, rs, re, vdf, vals, x, g)
+        return staged ? row_spmv2_dfv<S, XS>(ColShared{cc.col, cc.base}, rs, re, vdf, vals, x, g)
                       : row_spmv2_dfv<S, XS>(ColGlobal{col}, rs, re, vdf, vals, x, g);
     }
 }
@@ -740,12 +792,12 @@ __device__ __forceinline__ double2 chunk_spmv_split(const ChunkCols &cc, bool st
                                                     int g, bool valid) {
     const int rs = valid ? cc.rm[r] : 0, re = valid ? cc.rm[r + 1] : 0;
     if constexpr (S == 1) {
-        const double v = staged ? row_spmv1_split<XS>(ColShared{cc.col, cc.rm[0]}, rs, re, vals, x, xdf, g, valid)
+        const double v = staged ? row_spmv1_split<XS>(ColShared{cc.col, cc.base}, rs, re, vals, x, xdf, g, valid)
                                 : row_spmv1_split<XS>(ColGlobal{col}, rs, re, vals, x, xdf, g, valid);
         return make_double2(v, 0.0);
     } else {
         if (!valid) return make_double2(0.0, 0.0);
-        return staged ? row_spmv2_split<S, XS>(ColShared{cc.col, cc.rm[0]}, rs, re, vals, x, xdf, g)
+        return staged ? row_spmv2_split<S, XS>(ColShared{cc.col, cc.base}, rs, re, vals, x, xdf, g)
                       : row_spmv2_split<S, XS>(ColGlobal{col}, rs, re, vals, x, xdf, g);
     }
 }
@@ -753,25 +805,16 @@ __device__ __forceinline__ double2 chunk_spmv_split(const ChunkCols &cc, bool st
 // Level-1 tree step: every thread of the CTA holds the per-row products of its
 // (row r, members 2g, 2g+1) [s >= 2] or (row r) [s = 1, value on both lanes].
 // Writes the chunk's per-member partials to t.buf[1][chunk*width + off + e].
-// The 32 rows are combined by the halving tree v[i] += v[i + h], h = 16..1,
-// which is the butterfly order of warp_tree32 (lane 0's value); the adds of
-// all members are packed into full warps (31*S adds, not 5*32*S), which
-// matters on GB300's 1/64-rate FP64 pipe.
-template <int S>
-__device__ __forceinline__ void halving_tree(double (*sm)[S + 1], int nthreads) {
-#pragma unroll
-    for (int h = 16; h >= 1; h >>= 1) {
-        for (int it = threadIdx.x; it < h * S; it += nthreads) {
-            const int i = it / S, e = it % S;
-            sm[i][e] += sm[i + h][e];
-        }
-        __syncthreads();
-    }
-}
-
-template <int S>
-__device__ __forceinline__ void chunk_tree(double (*sm)[S + 1], double v0, double v1, int r,
-                                           int g, const DotTree &t, int64_t chunk, int off) {
+// The 32 rows are combined in the butterfly order of warp_tree32 (lane 0's
+// value), which is the halving tree v[i] += v[i + h], h = 16..1, operand for
+// operand: after one shared-memory transpose (row r of member e to lane r of
+// a warp) every member column is reduced by one warp with shuffles, so the
+// step costs two CTA barriers instead of one per tree level.
+// WARP = false: the same sums by the halving tree in shared memory, one
+// barrier per level, the adds of all members packed into full warps
+template <int S, bool WARP = true>
+__device__ __forceinline__ void chunk_tree(double (*sm)[S + 1], double v0, double v1, int r, int g,
+                                           const DotTree &t, int64_t chunk, int off) {
     if constexpr (S == 1) {
         if (g == 0) sm[r][0] = v0;
     } else {
@@ -779,14 +822,29 @@ __device__ __forceinline__ void chunk_tree(double (*sm)[S + 1], double v0, doubl
         sm[r][2 * g + 1] = v1;
     }
     __syncthreads();
-    halving_tree<S>(sm, blockDim.x);
-    for (int e = threadIdx.x; e < S; e += blockDim.x) t.buf[1][chunk * t.width + off + e] = sm[0][e];
+    if constexpr (WARP) {
+        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+        for (int e = warp; e < S; e += nw) {
+            const double v = warp_tree32<double>(sm[lane][e]);
+            if (lane == 0) t.buf[1][chunk * t.width + off + e] = v;
+        }
+    } else {
+#pragma unroll
+        for (int h = 16; h >= 1; h >>= 1) {
+            for (int it = threadIdx.x; it < h * S; it += blockDim.x) {
+                const int i = it / S, e = it % S;
+                sm[i][e] += sm[i + h][e];
+            }
+            __syncthreads();
+        }
+        for (int e = threadIdx.x; e < S; e += blockDim.x) t.buf[1][chunk * t.width + off + e] = sm[0][e];
+    }
     __syncthreads();
 }
 
-// Subset form of chunk_tree: the chunk's threads are [ltid = 0, nthr); all
-// threads of the CTA call it (its barriers are CTA-wide); writes only when
-// the chunk exists.
+// Subset form of chunk_tree: the chunk's threads are [ltid = 0, nthr), a whole
+// number of warps; all threads of the CTA call it (its barriers are
+// CTA-wide); writes only when the chunk exists.
 template <int S>
 __device__ __forceinline__ void chunk_tree_sub(double (*sm)[S + 1], double v0, double v1, int r,
                                                int g, const DotTree &t, int64_t chunk, int off,
@@ -798,16 +856,12 @@ __device__ __forceinline__ void chunk_tree_sub(double (*sm)[S + 1], double v0, d
         sm[r][2 * g + 1] = v1;
     }
     __syncthreads();
-#pragma unroll
-    for (int h = 16; h >= 1; h >>= 1) {
-        for (int it = ltid; it < h * S; it += nthr) {
-            const int i = it / S, e = it % S;
-            sm[i][e] += sm[i + h][e];
-        }
-        __syncthreads();
-    }
+    const int lane = ltid & 31, warp = ltid >> 5, nw = nthr >> 5;
     if (chunk < t.count[1])
-        for (int e = ltid; e < S; e += nthr) t.buf[1][chunk * t.width + off + e] = sm[0][e];
+        for (int e = warp; e < S; e += nw) {
+            const double v = warp_tree32<double>(sm[lane][e]);
+            if (lane == 0) t.buf[1][chunk * t.width + off + e] = v;
+        }
     __syncthreads();
 }
 

@@ -132,13 +132,13 @@ __device__ __forceinline__ float2 chunk_spmv_f32(const ChunkCols &cc, bool stage
     const int rs = valid ? cc.rm[r] : 0, re = valid ? cc.rm[r + 1] : 0;
     float2 y;
     if constexpr (S == 1) {
-        const float v = staged ? row_spmv1_f32<V>(ColShared{cc.col, cc.rm[0]}, rs, re, vals, x, g, valid)
+        const float v = staged ? row_spmv1_f32<V>(ColShared{cc.col, cc.base}, rs, re, vals, x, g, valid)
                                : row_spmv1_f32<V>(ColGlobal{col}, rs, re, vals, x, g, valid);
         y = make_float2(v, 0.f);
         if (diag && valid) y.x = __fmaf_rn(diag[R], x[R], y.x);
     } else {
         if (!valid) return make_float2(0.f, 0.f);
-        y = staged ? row_spmv2_f32<S, V>(ColShared{cc.col, cc.rm[0]}, rs, re, vals, x, g)
+        y = staged ? row_spmv2_f32<S, V>(ColShared{cc.col, cc.base}, rs, re, vals, x, g)
                    : row_spmv2_f32<S, V>(ColGlobal{col}, rs, re, vals, x, g);
         if (diag) {
             const float2 d = reinterpret_cast<const float2 *>(diag)[R * (S / 2) + g];
@@ -161,7 +161,7 @@ __device__ __forceinline__ float4 chunk_spmv4_f32(const ChunkCols &cc, bool stag
     static_assert(S % 4 == 0, "4 members per thread");
     if (!valid) return make_float4(0.f, 0.f, 0.f, 0.f);
     const int rs = cc.rm[r], re = cc.rm[r + 1];
-    float4 y = staged ? row_spmv4_f32<S, V>(ColShared{cc.col, cc.rm[0]}, rs, re, vals, x, g)
+    float4 y = staged ? row_spmv4_f32<S, V>(ColShared{cc.col, cc.base}, rs, re, vals, x, g)
                       : row_spmv4_f32<S, V>(ColGlobal{col}, rs, re, vals, x, g);
     if (diag) {
         const float4 d = reinterpret_cast<const float4 *>(diag)[R * (S / 4) + g];

@@ -38,7 +38,8 @@ def make_items(torch, spec, seed=500):
 SPEC = [(5, 4), (9, 32), (7, 1), (12, 8), (9, 16), (5, 32), (3, 4)]
 
 
-@pytest.mark.parametrize("flags", [0, E.CG_SPLIT64, E.CG_DF64 | E.CG_GRAPH, E.CG_GRAPH])
+@pytest.mark.parametrize("flags", [0, E.CG_SPLIT64, E.CG_DF64 | E.CG_GRAPH, E.CG_GRAPH,
+                                   E.CG_BATCH_K1_WIDE, E.CG_SPLIT64 | E.CG_BATCH_K1_WIDE | E.CG_GRAPH])
 def test_batched_equals_separate_solves_bitwise(torch, flags):
     items, meta = make_items(torch, SPEC)
     batch = E.Batch(items)
@@ -49,7 +50,7 @@ def test_batched_equals_separate_solves_bitwise(torch, flags):
         assert st_b[i] == [0] * s
         x2 = torch.zeros_like(x)
         w2 = torch.empty(E.cg_workspace_size(graph.num_rows, s), dtype=torch.uint8, device=gpu())
-        it, rr, st, _ = E.cg(graph, s, vals, b, x2, 1e-9, 2000, w2, flags=flags & ~E.CG_GRAPH)
+        it, rr, st, _ = E.cg(graph, s, vals, b, x2, 1e-9, 2000, w2, flags=flags & ~(E.CG_GRAPH | E.CG_BATCH_K1_WIDE))
         assert it == it_b[i] and rr == rr_b[i]
         assert torch.equal(x, x2), i
 
@@ -119,7 +120,8 @@ def test_autotuner_picks_and_caches(torch, tmp_path, monkeypatch):
     assert autotune.best_form(mesh, 8) == form          # served from the cache
     import json
     db = json.loads((tmp_path / "tune.json").read_text())
-    assert any("|form|12|10|8|" in k for k in db)
+    key = next(k for k in db if "|mapping|12|10|8|" in k)
+    assert db[key]["form"] == form and db[key]["k1_chunks"] in autotune.k1_chunk_choices(8)
     s, f = autotune.best_width(mesh)
     assert s in autotune.WIDTHS and f in autotune.FORMS
     items, _ = make_items(torch, [(6, 4), (8, 8)])

@@ -323,6 +323,28 @@ def test_cg_matches_oracle_ragged_mesh(torch, s, flags):
     compare_cg(mesh, xs, 1e-8, xg, it, flags)
 
 
+@pytest.mark.parametrize("s", S_ALL)
+@pytest.mark.parametrize("form", ["f64", "df", "split", "dfv"])
+def test_cg_spmv_mapping_knob_is_bitwise_neutral(torch, s, form):
+    """Every chunks-per-CTA mapping of the CG's SpMV (ENS_CG_K1_CHUNKS) gives
+    bitwise the default's solution, iteration counts and residuals: all sums
+    are ordered by row index.  13^3 cells: 86 chunks, so the wider mappings
+    end with a partly filled CTA; a mapping beyond 1024 threads is refused."""
+    from paper_1511_03703_gb300 import autotune
+    mesh = E.Mesh(13, 10)
+    xs = inputs.kl_samples(910, 0, s, 10)
+    flags = {"f64": 0, "df": E.CG_DF64, "split": E.CG_SPLIT64, "dfv": 0}[form]
+    ref = gpu_solve(mesh, xs, 1e-9, flags=flags | E.CG_GRAPH, presplit=form == "dfv")
+    for c in autotune.k1_chunk_choices(s):
+        got = gpu_solve(mesh, xs, 1e-9, flags=flags | E.CG_GRAPH | E.cg_k1_chunks(c), presplit=form == "dfv")
+        assert got[1] == ref[1] and got[2] == ref[2] and np.array_equal(got[0], ref[0]), c
+    too_wide = 2 * max(autotune.k1_chunk_choices(s))
+    if too_wide <= 8:
+        with pytest.raises(E.EnsError) as ei:
+            gpu_solve(mesh, xs, 1e-9, flags=flags | E.cg_k1_chunks(too_wide))
+        assert ei.value.code == 1
+
+
 def test_cg_identical_members_bitwise(torch):
     mesh = E.Mesh(7, 10)
     xs = np.repeat(inputs.kl_samples(77, 3, 1, 10), 8, axis=0)
