@@ -44,16 +44,20 @@ def spmv_bytes(n, nnz, s, vbytes=8):
 
 
 def kernel_source_hash():
+    """Hash of the sources the CG's SpMV kernel is built from: a committed
+    DRAM-traffic figure is used only while it still describes this kernel."""
     h = hashlib.sha256()
-    for f in ("ens_spmv.cuh", "ens_cg_kernels.cuh", "ens_cg.cu", "ens_internal.cuh"):
+    for f in ("ens_spmv.cuh", "ens_cg_kernels.cuh", "ens_cg.cu", "ens_internal.cuh", "ens_cg_k1.cuh",
+              "ens_cg_k1_s32.cu"):
         h.update(open(os.path.join(ROOT, "paper_1511_03703_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
 
 
 def profiled_traffic(s, mode="f64"):
-    """DRAM bytes per launch of the CG SpMV from the committed ncu summary, if
-    that summary was taken on the current kernel source; else None."""
-    path = os.path.join(ROOT, "profiles", "cg_spmv_64cubed.txt")
+    """DRAM bytes per launch of the CG SpMV from the committed ncu summary (a
+    48^3 capture scaled to the 64^3 launch by its algorithmic bytes), if that
+    summary was taken on the current kernel source; else None."""
+    path = os.path.join(ROOT, "profiles", "cg_spmv_dram_48cubed_s32.txt")
     if not os.path.exists(path):
         return None
     txt = open(path).read()
@@ -70,34 +74,28 @@ def fp64_alu_peak_tflops(sm_mhz=2070.0):
 
 
 def spmv_sweep(torch, device, s_list=(1, 4, 8, 16, 32), iters=24):
-    """CG SpMV (K1) launch time per ensemble size and arithmetic form, from a
-    fixed-iteration CG (tol 0) on the 64^3 mesh with CUDA events per launch."""
+    """CG SpMV (K1) launch time per ensemble size and arithmetic form, from
+    fixed-iteration CGs (tol 0) on the 64^3 mesh with CUDA events per launch:
+    each form at its fastest chunks-per-CTA mapping (`chunks`), with the
+    one-chunk mapping's time beside it."""
     import paper_1511_03703_gb300 as E
-    from paper_1511_03703_gb300 import inputs
+    from paper_1511_03703_gb300 import autotune, inputs
     mesh = E.Mesh(N_MESH, M_KL, device=device)
     peak, _ = measured_peaks()
     out = {}
     for s in s_list:
         xs = inputs.kl_samples(inputs.SEED_SCALE, 0, s, M_KL)
         vals, b = mesh.assemble(s, torch.from_numpy(inputs.ensemble_layout(xs)).to(device))
-        work = torch.empty(E.cg_workspace_size(mesh.n, s), dtype=torch.uint8, device=device)
+        t = autotune.time_spmv_mappings(mesh, s, iters=iters, vals=vals, b=b)
         row = {}
-        vdf = torch.empty(2 * mesh.nnz * s, dtype=torch.float32, device=device)
-        E.convert_values(mesh.graph, s, vals, vdf, dtype=E.F64_DF)
         for name in FORMS:
-            fl = form_flag(name)
-            vd = vdf if name == "dfv" else None
-            x = torch.zeros(mesh.n * s, dtype=torch.float64, device=device)
-            E.cg(mesh.graph, s, vals, b, x, 0.0, 4, work, flags=fl, check_every=4, values_df=vd)  # warm-up
-            x.zero_()
-            _, _, _, st = E.cg(mesh.graph, s, vals, b, x, 0.0, iters, work,
-                               flags=fl | E.CG_TIME_SPMV, check_every=iters, values_df=vd)
-            ms = st.spmv_ms / max(st.spmv_launches, 1)
+            c, ms = min(((c, v) for (f, c), v in t.items() if f == name), key=lambda cv: cv[1])
             gbs = spmv_bytes(mesh.n, mesh.nnz, s) / (ms * 1e-3) / 1e9
-            row[name] = {"ms": ms, "gbs": gbs, "hbm_frac": gbs / peak,
+            row[name] = {"ms": ms, "gbs": gbs, "hbm_frac": gbs / peak, "chunks": c,
+                         "ms_one_chunk": t[(name, 1)],
                          "fp64_tflops": 2 * mesh.nnz * s / (ms * 1e-3) / 1e12}
         out[str(s)] = row
-        del vals, b, work, vdf
+        del vals, b
     return out
 
 
@@ -205,9 +203,10 @@ def make_batch(rank, s, batch):
 
 
 class Runner:
-    """Holds device buffers for one batch; run_step() is one timed step."""
+    """Holds device buffers for one batch; run_step() is one timed step.
+    k1_chunks: the SpMV's chunks of 32 rows per CTA (None: the default)."""
 
-    def __init__(self, torch, s, batch, device, time_spmv=True, df="f64"):
+    def __init__(self, torch, s, batch, device, time_spmv=True, df="f64", k1_chunks=None):
         import paper_1511_03703_gb300 as E
         from paper_1511_03703_gb300 import inputs
         self.torch, self.E, self.s, self.batch = torch, E, s, batch
@@ -215,6 +214,7 @@ class Runner:
         self.nens = batch // s
         self.time_spmv = time_spmv
         self.df = df
+        self.k1_flags = E.cg_k1_chunks(k1_chunks)
         n, nnz, _ = E.mesh_sizes(N_MESH)
         self.n, self.nnz = n, nnz
         T = torch
@@ -257,7 +257,8 @@ class Runner:
                    values_df=self.vdf, kl_table=self.kl)
         x = self.x[g]
         x.zero_()
-        flags = (E.CG_TIME_SPMV if self.time_spmv else 0) | form_flag(self.df) | E.CG_X0_ZERO | E.CG_GRAPH
+        flags = ((E.CG_TIME_SPMV if self.time_spmv else 0) | form_flag(self.df) | E.CG_X0_ZERO | E.CG_GRAPH
+                 | self.k1_flags)
         it, rr, st, stats = E.cg(self.graph, self.s, self.values, self.b, x, TOL, 10000, self.work,
                                  flags=flags, check_every=8, values_df=self.vdf)
         self.launches += 2 + stats.kernel_launches
@@ -275,17 +276,22 @@ class Runner:
 
 def per_sample_baseline(torch, device, nsamp=32, df="f64"):
     """The s = 1 path (samples one after another), as in the paper's speed-up
-    (s * T1 / Ts, Sect. 4); every SpMV form is timed and the fastest reported."""
+    (s * T1 / Ts, Sect. 4): every SpMV form at its autotuned mapping is timed
+    and the fastest reported."""
+    import paper_1511_03703_gb300 as E
+    from paper_1511_03703_gb300 import autotune
+    mesh = E.Mesh(N_MESH, M_KL, device=device)
     best = None
     for form in FORMS:
-        res = _per_sample_form(torch, device, nsamp, form)
+        c = autotune.best_mapping(mesh, 1, candidates=(form,))["k1_chunks"]
+        res = _per_sample_form(torch, device, nsamp, form, c)
         if best is None or res["value"] > best["value"]:
             best = res
     return best
 
 
-def _per_sample_form(torch, device, nsamp, df):
-    r = Runner(torch, 1, nsamp, device, time_spmv=True, df=df)
+def _per_sample_form(torch, device, nsamp, df, k1_chunks=None):
+    r = Runner(torch, 1, nsamp, device, time_spmv=True, df=df, k1_chunks=k1_chunks)
     r.setup_mesh()
     r.solve_ensemble(0)  # warm-up
     r.reset_stats()
@@ -295,7 +301,7 @@ def _per_sample_form(torch, device, nsamp, df):
         r.solve_ensemble(g)
     torch.cuda.synchronize()
     dt = time.perf_counter() - t0
-    return {"value": nsamp / dt, "unit": UNIT, "samples": nsamp, "spmv": df,
+    return {"value": nsamp / dt, "unit": UNIT, "samples": nsamp, "spmv": df, "k1_chunks_per_cta": k1_chunks,
             "mean_iters": float(np.mean(r.iters)),
             "spmv_gbs": spmv_bytes(r.n, r.nnz, 1) * r.spmv_launches / (r.spmv_ms * 1e-3) / 1e9
             if r.spmv_ms > 0 else None}
@@ -303,11 +309,17 @@ def _per_sample_form(torch, device, nsamp, df):
 
 def ensemble_size_sweep(torch, device, nsamp=128):
     """Sample-solves/s (assembly + CG) at the smaller ensemble sizes on the
-    64^3 workload: nsamp samples each, in the SpMV form the s sweep finds
-    fastest at that size (the s = 32 figure is the headline's value)."""
+    64^3 workload: nsamp samples each, in the SpMV form and mapping the
+    autotuner finds fastest at that size (the s = 32 figure is the headline's
+    value)."""
+    import paper_1511_03703_gb300 as E
+    from paper_1511_03703_gb300 import autotune
+    mesh = E.Mesh(N_MESH, M_KL, device=device)
     out = {}
-    for s, form in ((4, "f64"), (8, "split"), (16, "dfv")):
-        r = Runner(torch, s, nsamp, device, time_spmv=False, df=form)
+    for s in (4, 8, 16):
+        m = autotune.best_mapping(mesh, s)
+        form = m["form"]
+        r = Runner(torch, s, nsamp, device, time_spmv=False, df=form, k1_chunks=m["k1_chunks"])
         r.setup_mesh()
         r.solve_ensemble(0)  # warm-up
         r.reset_stats()
@@ -318,6 +330,7 @@ def ensemble_size_sweep(torch, device, nsamp=128):
         torch.cuda.synchronize()
         dt = time.perf_counter() - t0
         out[str(s)] = {"value": nsamp / dt, "unit": UNIT, "samples": nsamp, "spmv": form,
+                       "k1_chunks_per_cta": m["k1_chunks"],
                        "mean_iters": float(np.mean(r.iters)), "failed_members": r.status_bad}
         del r
     return out
@@ -1390,7 +1403,8 @@ def main_profile_cg(args):
     vals, b = mesh.assemble(s, xi, values_df=vdf)
     x = torch.zeros(mesh.n * s, dtype=torch.float64, device=dev)
     work = torch.empty(E.cg_workspace_size(mesh.n, s), dtype=torch.uint8, device=dev)
-    it, rr, st, stats = E.cg(mesh.graph, s, vals, b, x, 0.0, iters, work, flags=form_flag(form),
+    it, rr, st, stats = E.cg(mesh.graph, s, vals, b, x, 0.0, iters, work,
+                             flags=form_flag(form) | E.cg_k1_chunks(args.k1_chunks),
                              check_every=iters, values_df=vdf)
     torch.cuda.synchronize()
     print("N", N, "s", s, "iters", it[:2], "status", st[:2], "nnz", mesh.nnz, "rows", mesh.n)
@@ -1504,6 +1518,8 @@ def main():
                          "an --N mesh for ncu captures (no JSON line)")
     ap.add_argument("--N", type=int, default=64, help="profile-*: cells per side")
     ap.add_argument("--iters", type=int, default=8, help="profile-cg: fixed CG iteration count")
+    ap.add_argument("--k1-chunks", type=int, default=0, choices=[0, 1, 2, 4, 8],
+                    help="profile-cg: chunks of 32 rows per SpMV CTA (0: the library's default)")
     ap.add_argument("--reps", type=int, default=2, help="profile-mg / profile-nl: repetitions")
     ap.add_argument("--mode", default="presplit", choices=["", "presplit", "f32"],
                     help="profile-mg: which levels are pre-split / FP32")

@@ -99,7 +99,9 @@ struct CgKernels {
     }
     static void spmv(const CgArgs &a, int nsub, cudaStream_t st) { k1_launch<S, MODE>(a, nsub, st); }
     static void resid(const CgArgs &a, cudaStream_t st) {
-        cg_resid_kernel<S><<<vec_grid(a), VecMap<S>::THREADS, 0, st>>>(a);
+        using L = K2Launch<S, 2>;
+        const unsigned grid = (unsigned)((a.t1.count[1] + L::Map::CPC - 1) / L::Map::CPC);
+        cg_resid_kernel<S, 2><<<grid, L::TH, 0, st>>>(a);
     }
     static void update(const CgArgs &a, cudaStream_t st) {
         cg_update_kernel<S, MODE><<<vec_grid(a), VecMap<S>::THREADS, 0, st>>>(a);

@@ -463,11 +463,27 @@ __device__ __forceinline__ float2 df_add(float2 a, float2 b) {
     return make_float2(s, __fadd_rn(__fadd_rn(a.y, b.y), t));
 }
 
-template <int S, int TH>
+// K2's mapping: MPT members per thread (16-byte loads of r and q, MPT/2 of
+// each per row), S/MPT threads per row; a CTA of TH threads owns CPC chunks,
+// CPP of them per pass.  With more members per thread every load of the CTA's
+// chunks can be in flight before its first store (one pass).
+template <int S, int TH, int MPT>
+struct K2Map {
+    static constexpr int M = (S == 1) ? 1 : (MPT < S ? MPT : S);   // members per thread
+    static constexpr int VG = S / M;                                // threads per row
+    static constexpr int CHUNK_T = 32 * VG;
+    static constexpr int THREADS = TH;
+    static constexpr int CPP = THREADS / CHUNK_T;
+    static constexpr int CPC0 = (S >= 16) ? 4 : 8;
+    static constexpr int CPC = (CPC0 > CPP) ? CPC0 : CPP;
+    static constexpr int PASSES = CPC / CPP;
+};
+
+template <int S, int TH, int MPT = 2>
 __device__ __forceinline__ void k2_body(const CgArgs &a, int cta,
                                         double (*sm)[32][S + 1] /* [CPC][32][S+1] */) {
-    using VM = VecMap<S, TH>;
-    constexpr int VG = VM::VG;
+    using VM = K2Map<S, TH, MPT>;
+    constexpr int VG = VM::VG, MM = VM::M;
     const int64_t first_chunk = (int64_t)cta * VM::CPC;
     if (a.k2_pf && threadIdx.x == 0) {   // the passes below then read r and q from L2
         const uint64_t b0 = (uint64_t)first_chunk * 32 * S * 8u;
@@ -479,11 +495,14 @@ __device__ __forceinline__ void k2_body(const CgArgs &a, int cta,
     const int cip = threadIdx.x / VM::CHUNK_T, lt = threadIdx.x % VM::CHUNK_T;
     const int r = lt / VG, g = lt % VG;
     const CgState *cs = a.st;
-    const int m = (S == 1) ? 0 : 2 * g;
-    const bool act0 = cs->active[m];
-    const bool act1 = (S == 1) ? false : (bool)cs->active[m + 1];
-    const double al0 = cs->alpha[m];
-    const double al1 = (S == 1) ? 0.0 : cs->alpha[m + 1];
+    const int m = g * MM;   // first member of the thread
+    bool act_m[MM];
+    double al[MM];
+#pragma unroll
+    for (int k = 0; k < MM; ++k) {
+        act_m[k] = cs->active[m + k];
+        al[k] = cs->alpha[m + k];
+    }
     // r.r: squares and the chunk's 32-row tree in double-float on the FP32
     // pipe (the FP64 pipe keeps only the r update); the chunk sums enter the
     // FP64 dot tree above the chunk
@@ -492,24 +511,38 @@ __device__ __forceinline__ void k2_body(const CgArgs &a, int cta,
     for (int pass = 0; pass < VM::PASSES; ++pass) {
         const int c = pass * VM::CPP + cip;
         const int64_t R = (first_chunk + c) * 32 + r;
-        float2 v0 = make_float2(0.f, 0.f), v1 = make_float2(0.f, 0.f);
-        if (R < a.n) {
-            if constexpr (S == 1) {
+        if constexpr (S == 1) {
+            float2 v0 = make_float2(0.f, 0.f);
+            if (R < a.n) {
                 double rv = a.r[R];
-                if (act0) { rv = fma(-al0, a.q[R], rv); a.r[R] = rv; }
+                if (act_m[0]) { rv = fma(-al[0], a.q[R], rv); a.r[R] = rv; }
                 v0 = df_square(rv);
+            }
+            sf[c][r][0] = v0;
+        } else {
+            constexpr int H = MM / 2;
+            double2 rv[H], qv[H];
+            if (R < a.n) {
+                const double2 *r2 = reinterpret_cast<const double2 *>(a.r) + (R * S + m) / 2;
+                const double2 *q2 = reinterpret_cast<const double2 *>(a.q) + (R * S + m) / 2;
+#pragma unroll
+                for (int h = 0; h < H; ++h) { rv[h] = r2[h]; qv[h] = q2[h]; }
+#pragma unroll
+                for (int h = 0; h < H; ++h) {
+                    if (act_m[2 * h]) rv[h].x = fma(-al[2 * h], qv[h].x, rv[h].x);
+                    if (act_m[2 * h + 1]) rv[h].y = fma(-al[2 * h + 1], qv[h].y, rv[h].y);
+                    if (act_m[2 * h] || act_m[2 * h + 1]) reinterpret_cast<double2 *>(a.r)[(R * S + m) / 2 + h] = rv[h];
+                }
             } else {
-                double2 rv = reinterpret_cast<const double2 *>(a.r)[R * VG + g];
-                const double2 qv = reinterpret_cast<const double2 *>(a.q)[R * VG + g];
-                if (act0) rv.x = fma(-al0, qv.x, rv.x);
-                if (act1) rv.y = fma(-al1, qv.y, rv.y);
-                if (act0 || act1) reinterpret_cast<double2 *>(a.r)[R * VG + g] = rv;
-                v0 = df_square(rv.x);
-                v1 = df_square(rv.y);
+#pragma unroll
+                for (int h = 0; h < H; ++h) rv[h] = make_double2(0.0, 0.0);
+            }
+#pragma unroll
+            for (int h = 0; h < H; ++h) {
+                sf[c][r][m + 2 * h] = df_square(rv[h].x);
+                sf[c][r][m + 2 * h + 1] = df_square(rv[h].y);
             }
         }
-        sf[c][r][m] = v0;
-        if constexpr (S > 1) sf[c][r][m + 1] = v1;
     }
     __syncthreads();
     // halving tree over the 32 rows of every chunk, all members packed (every
@@ -622,10 +655,22 @@ __device__ __forceinline__ void k3_body(const CgArgs &a, int cta) {
     }
 }
 
-template <int S>
-__global__ void __launch_bounds__(VecMap<S>::THREADS, 1536 / VecMap<S>::THREADS) cg_resid_kernel(CgArgs a) {
-    __shared__ double sm[VecMap<S>::CPC][32][S + 1];   // per-row products of every chunk
-    k2_body<S, VecMap<S>::THREADS>(a, blockIdx.x, sm);
+// MPT members per thread; CTAs of 512 threads (2 per SM, 64 registers) when
+// a thread holds 8 members' r and q, else VecMap's CTA (3 per SM at s = 32).
+// The library launches MPT = 2: on the 64^3 mesh, s = 32, K2 took 52.6 us with
+// 2 members per thread, 57.4 us with 4 and 76.3 us with 8 (all loads of a CTA
+// in flight at once, but fewer CTAs per SM).
+template <int S, int MPT>
+struct K2Launch {
+    static constexpr int TH = (MPT >= 8) ? 512 : VecMap<S>::THREADS;
+    static constexpr int MIN_BLOCKS = (MPT >= 8) ? 2 : 1536 / VecMap<S>::THREADS;
+    using Map = K2Map<S, TH, MPT>;
+};
+
+template <int S, int MPT>
+__global__ void __launch_bounds__(K2Launch<S, MPT>::TH, K2Launch<S, MPT>::MIN_BLOCKS) cg_resid_kernel(CgArgs a) {
+    __shared__ double sm[K2Launch<S, MPT>::Map::CPC][32][S + 1];   // per-row products of every chunk
+    k2_body<S, K2Launch<S, MPT>::TH, MPT>(a, blockIdx.x, sm);
 }
 
 template <int S, int MODE>
