@@ -91,7 +91,7 @@ def spmv_sweep(torch, device, s_list=(1, 4, 8, 16, 32), iters=24):
         for name in FORMS:
             c, ms = min(((c, v) for (f, c), v in t.items() if f == name), key=lambda cv: cv[1])
             gbs = spmv_bytes(mesh.n, mesh.nnz, s) / (ms * 1e-3) / 1e9
-            row[name] = {"ms": ms, "gbs": gbs, "hbm_frac": gbs / peak, "chunks": c,
+            row[name] = {"ms": ms, "gbs": gbs, "hbm_frac": gbs / peak, "k1_mapping": c,
                          "ms_one_chunk": t[(name, 1)],
                          "fp64_tflops": 2 * mesh.nnz * s / (ms * 1e-3) / 1e12}
         out[str(s)] = row
@@ -301,7 +301,7 @@ def _per_sample_form(torch, device, nsamp, df, k1_chunks=None):
         r.solve_ensemble(g)
     torch.cuda.synchronize()
     dt = time.perf_counter() - t0
-    return {"value": nsamp / dt, "unit": UNIT, "samples": nsamp, "spmv": df, "k1_chunks_per_cta": k1_chunks,
+    return {"value": nsamp / dt, "unit": UNIT, "samples": nsamp, "spmv": df, "k1_mapping": k1_chunks,
             "mean_iters": float(np.mean(r.iters)),
             "spmv_gbs": spmv_bytes(r.n, r.nnz, 1) * r.spmv_launches / (r.spmv_ms * 1e-3) / 1e9
             if r.spmv_ms > 0 else None}
@@ -330,7 +330,7 @@ def ensemble_size_sweep(torch, device, nsamp=128):
         torch.cuda.synchronize()
         dt = time.perf_counter() - t0
         out[str(s)] = {"value": nsamp / dt, "unit": UNIT, "samples": nsamp, "spmv": form,
-                       "k1_chunks_per_cta": m["k1_chunks"],
+                       "k1_mapping": m["k1_chunks"],
                        "mean_iters": float(np.mean(r.iters)), "failed_members": r.status_bad}
         del r
     return out
@@ -879,7 +879,7 @@ def run_batched(args, compact=False, oracle_jobs=None):
                        "batch_spmv_form": bform, "graph_check_every": ce,
                        "batch_spmv_cta_threads": 1024 if bflags & E.CG_BATCH_K1_WIDE else 512,
                        "per_group_mapping": {f"{N}^3,s={s}": {"form": mappings[(N, s)]["form"],
-                                                              "k1_chunks_per_cta": mappings[(N, s)]["k1_chunks"]}
+                                                              "k1_mapping": mappings[(N, s)]["k1_chunks"]}
                                              for (N, s) in groups},
                        "tuning_seconds": tune_s, "step": "mesh set-up + assembly of every ensemble + solve"},
             "separate_launches": {"value": steps * total / ts, "unit": UNIT},

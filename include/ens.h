@@ -258,6 +258,12 @@ enum {
  * or, with this flag, 1024, i.e. 512 / (32 max(s/2, 2)) chunks of 32 rows of
  * an item per CTA, or twice that; no effect on results either. */
 #define ENS_CG_BATCH_K1_WIDE (1 << 19)
+/* ens_cg / ens_cg_df: the SpMV's CTAs (one chunk each) write only their
+ * chunks' partial p.q, and a second, small kernel reduces the upper levels of
+ * the same tree, in the same order, so no SpMV CTA waits on the tree's fence
+ * and arrival counter; pays off at small s, where a CTA's own work is short.
+ * Results bitwise those of the default. */
+#define ENS_CG_K1_DEFER (1 << 20)
 
 /* Unpreconditioned CG (Hestenes-Stiefel) on each member of the ensemble
  * system, with per-member dots (default) or the paper's coupled form.

@@ -24,13 +24,18 @@ F64, F32, BF16, F64_DF, F64_SPLIT = 0, 1, 2, 3, 4
 CG_COUPLED, CG_GRAPH, CG_TIME_SPMV, CG_DF64, CG_SPLIT64, CG_GUESS_FALLBACK, CG_X0_ZERO = 1, 2, 4, 8, 16, 32, 64
 CG_K1_CHUNKS_SHIFT = 16
 CG_BATCH_K1_WIDE = 1 << 19
+CG_K1_DEFER = 1 << 20
 
 
 def cg_k1_chunks(chunks):
-    """ens_cg flags field for `chunks` (1, 2, 4 or 8) chunks of 32 rows per CTA of
-    the CG's SpMV (ENS_CG_K1_CHUNKS); 0 leaves the library's default."""
+    """ens_cg flags for the CG SpMV's mapping: `chunks` (1, 2, 4 or 8) chunks of
+    32 rows per CTA (ENS_CG_K1_CHUNKS), or "defer" for one chunk per CTA with
+    the upper levels of p.q's tree in a second kernel (ENS_CG_K1_DEFER); 0 or
+    None leaves the library's default."""
     if not chunks:
         return 0
+    if chunks == "defer":
+        return CG_K1_DEFER
     k = {1: 0, 2: 1, 4: 2, 8: 3}[chunks]
     return (k + 1) << CG_K1_CHUNKS_SHIFT
 MLP_DIMS = (10, 256, 256, 64)

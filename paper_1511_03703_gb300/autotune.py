@@ -7,8 +7,10 @@ Knobs, all exposed through the C ABI:
     GB300's 1/64-rate FP64 makes the best form depend on s and mesh size;
   - SpMV mapping per (mesh, s, form): chunks of 32 rows per CTA
     (ENS_CG_K1_CHUNKS: 1, 2, 4 or 8, at most 1024 threads per CTA, each row on
-    max(s/2, 2) threads), tuned jointly with the form; for a batch, the CTA
-    size of the batched SpMV (ens_cg_batched, ENS_CG_BATCH_K1_WIDE);
+    max(s/2, 2) threads), or one chunk per CTA with the upper levels of p.q's
+    tree in a second kernel ("defer", ENS_CG_K1_DEFER), tuned jointly with the
+    form; for a batch, the CTA size of the batched SpMV (ens_cg_batched,
+    ENS_CG_BATCH_K1_WIDE);
   - graph length (check_every): iterations replayed per CUDA graph launch
     between host polls of the convergence word;
   - ensemble width s for a group of samples on one mesh (when the caller
@@ -34,6 +36,11 @@ def k1_chunk_choices(s):
     """Chunks of 32 rows per SpMV CTA that fit a 1024-thread CTA at width s."""
     threads_per_chunk = 32 * max(s // 2, 2)
     return tuple(c for c in K1_CHUNKS if c * threads_per_chunk <= 1024)
+
+
+def k1_mapping_choices(s):
+    """Every SpMV mapping at width s: the chunk counts and "defer"."""
+    return k1_chunk_choices(s) + ("defer",)
 
 
 def mapping_flags(mapping):
@@ -94,7 +101,7 @@ def time_spmv_mappings(mesh, s, iters=24, vals=None, b=None, candidates=tuple(FO
     E.convert_values(mesh.graph, s, vals, vdf, dtype=E.F64_DF)
     out = {}
     for name in candidates:
-        for c in (chunks or k1_chunk_choices(s)):
+        for c in (chunks or k1_mapping_choices(s)):
             fl = FORMS[name] | E.cg_k1_chunks(c)
             vd = vdf if name == "dfv" else None
             x = torch.zeros(mesh.n * s, dtype=torch.float64, device=dev)

@@ -75,9 +75,11 @@ int k1_default_nsub(int s, int mode) {
 }
 
 // chunks per K1 CTA from the ENS_CG_K1_CHUNKS field of flags (0: default);
-// -1 when the field asks for more than a 1024-thread CTA holds
+// 0 for the deferred tree (ENS_CG_K1_DEFER); -1 when the field asks for more
+// than a 1024-thread CTA holds
 static int k1_nsub_from_flags(int flags, int s, int mode) {
     const int f = (flags >> ENS_CG_K1_CHUNKS_SHIFT) & 7;
+    if (flags & ENS_CG_K1_DEFER) return (f == 0 || f == 1) ? 0 : -1;
     if (f == 0) return k1_default_nsub(s, mode);
     const int nsub = 1 << (f - 1);
     return (f <= 4 && nsub <= k1_max_nsub_rt(s)) ? nsub : -1;
@@ -667,8 +669,8 @@ static int cg_entry(const ens_graph *graph, int s, const double *values, const f
     const size_t need = cg_bytes(graph->num_rows, s);
     if (work_bytes < need) return fail(ENS_ERR_WORKSPACE, "cg workspace %zu < %zu bytes", work_bytes, need);
     if (k1_nsub_from_flags(flags, s, 0) < 0)
-        return fail(ENS_ERR_ARG, "ENS_CG_K1_CHUNKS field %d: at most %d chunks of 32 rows per K1 CTA at s=%d",
-                    (flags >> ENS_CG_K1_CHUNKS_SHIFT) & 7, k1_max_nsub_rt(s), s);
+        return fail(ENS_ERR_ARG, "ENS_CG_K1_CHUNKS field %d: at most %d chunks of 32 rows per K1 CTA at s=%d "
+                    "(one with ENS_CG_K1_DEFER)", (flags >> ENS_CG_K1_CHUNKS_SHIFT) & 7, k1_max_nsub_rt(s), s);
     CgHostOut out{iters_host, relres_host, status_host, stats_host};
     cudaStream_t st = as_stream(stream);
     switch (s) {

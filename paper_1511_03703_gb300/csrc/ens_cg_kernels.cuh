@@ -304,9 +304,12 @@ __device__ __forceinline__ void k1_epilogue(const CgArgs &a) {
 
 // K1 with one chunk per CTA: the arithmetic of k1_body<S, MODE, 1>, written
 // out with fewer live indices so that it keeps to 40 registers (3 CTAs of 512
-// threads per SM at s = 32) with little spilling.  VEC, WARP: column staging
-// with 16-byte loads, chunk tree by warp shuffles.
-template <int S, int MODE, bool VEC, bool WARP>
+// threads per SM at s = 32) with little spilling.  VEC: column staging with
+// 16-byte loads; WARP: chunk tree by warp shuffles (see chunk_tree).
+// DEFER: the CTA writes only its chunk's p.q partials (level 1 of the tree);
+// cg_spmv_reduce_kernel, launched next, does the upper levels in the same
+// order and the epilogue, so no CTA of K1 waits on a fence and an atomic.
+template <int S, int MODE, bool VEC, bool WARP, bool DEFER = false>
 __device__ __forceinline__ void k1_single(const CgArgs &a) {
     CgState *st = a.st;
     constexpr int G = RowMap<S>::G;
@@ -366,6 +369,7 @@ __device__ __forceinline__ void k1_single(const CgArgs &a) {
         v1 = ap.y * pv.y;
     }
     chunk_tree<S, WARP>(sm, v0, v1, r, g, a.t1, blockIdx.x, 0);
+    if (DEFER) return;
     if (!dot_tree_propagate(a.t1, blockIdx.x, 1)) return;
     if (threadIdx.x >= 32) return;
     k1_epilogue<S>(a);
@@ -394,11 +398,33 @@ template <int S, int MODE, int NSUB>
 __global__ void __launch_bounds__(K1Launch<S, MODE, NSUB>::THREADS, K1Launch<S, MODE, NSUB>::MIN_BLOCKS)
     cg_spmv_kernel(CgArgs a) {
     if constexpr (NSUB == 1) {
-        k1_single<S, MODE, true, true>(a);
+        k1_single<S, MODE, true, (S == 1)>(a);
     } else {
         __shared__ K1Smem<S, NSUB> sh;
         k1_body<S, MODE, NSUB>(a, blockIdx.x, sh);
     }
+}
+
+// K1 with the deferred tree (ENS_CG_K1_DEFER): chunk partials only ...
+template <int S, int MODE>
+__global__ void __launch_bounds__(RowMap<S>::THREADS, K1Launch<S, MODE, 1>::MIN_BLOCKS)
+    cg_spmv_partial_kernel(CgArgs a) {
+    k1_single<S, MODE, true, (S == 1), true>(a);
+}
+
+// ... then one CTA per level-1 group: the group's reduction, the upper levels
+// (last arrivers, as in dot_tree_propagate) and K1's epilogue
+template <int S>
+__global__ void __launch_bounds__(256) cg_spmv_reduce_kernel(CgArgs a) {
+    if (ld_cg(&a.st->active_count) == 0) return;   // K1 already cleared the flags
+    if (a.t1.levels == 1) {                         // one chunk: its partials are the top
+        if (threadIdx.x < 32) k1_epilogue<S>(a);
+        return;
+    }
+    dot_tree_reduce_group(a.t1, blockIdx.x);
+    if (!dot_tree_propagate_from(a.t1, 2, blockIdx.x, 1)) return;
+    if (threadIdx.x >= 32) return;
+    k1_epilogue<S>(a);
 }
 
 // Host: chunks of 32 rows per K1 CTA (1, 2, 4 or 8; at most 1024 threads per

@@ -147,14 +147,16 @@ inline int dot_tree_clear(const DotTreeT<T> &t, cudaStream_t st) {
 // CTA's stores before thread 0's gpu-scope fence and arrival atomic (fences
 // are cumulative); acquire: the last arriver fences after its atomic and the
 // barrier orders the other threads' L2 reads after it.
+// dot_tree_propagate_from starts at level `level` (its items [item0,
+// item0 + nitems) written there); dot_tree_propagate is level 1.
 template <typename T>
-__device__ __forceinline__ bool dot_tree_propagate(const DotTreeT<T> &t, int64_t item0, int nitems) {
+__device__ __forceinline__ bool dot_tree_propagate_from(const DotTreeT<T> &t, int level, int64_t item0, int nitems) {
     __shared__ int s_last;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
     int64_t item = item0;
     int add = nitems;
     __syncthreads();
-    for (int l = 1; l < t.levels; ++l) {
+    for (int l = level; l < t.levels; ++l) {
         const int64_t g = item >> 5;
         const int cnt = (int)min((int64_t)32, t.count[l] - (g << 5));
         if (tid == 0) {
@@ -182,6 +184,25 @@ __device__ __forceinline__ bool dot_tree_propagate(const DotTreeT<T> &t, int64_t
     if (tid == 0) __threadfence();
     __syncthreads();
     return true;
+}
+
+template <typename T>
+__device__ __forceinline__ bool dot_tree_propagate(const DotTreeT<T> &t, int64_t item0, int nitems) {
+    return dot_tree_propagate_from(t, 1, item0, nitems);
+}
+
+// Level-1 group g of a tree whose level-1 items are complete (written by an
+// earlier kernel): its 32 items reduced into level-2 item g exactly as the
+// group's last arriver does in dot_tree_propagate; all threads of the CTA.
+template <typename T>
+__device__ __forceinline__ void dot_tree_reduce_group(const DotTreeT<T> &t, int64_t g) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    const int cnt = (int)min((int64_t)32, t.count[1] - (g << 5));
+    for (int w = warp; w < t.width; w += nwarps) {
+        T v = (lane < cnt) ? ld_cg(t.buf[1] + ((g << 5) + lane) * t.width + w) : T(0);
+        v = warp_tree32<T>(v);
+        if (lane == 0) t.buf[2][g * t.width + w] = v;
+    }
 }
 
 }  // namespace ens

@@ -805,14 +805,17 @@ __device__ __forceinline__ double2 chunk_spmv_split(const ChunkCols &cc, bool st
 // Level-1 tree step: every thread of the CTA holds the per-row products of its
 // (row r, members 2g, 2g+1) [s >= 2] or (row r) [s = 1, value on both lanes].
 // Writes the chunk's per-member partials to t.buf[1][chunk*width + off + e].
-// The 32 rows are combined in the butterfly order of warp_tree32 (lane 0's
-// value), which is the halving tree v[i] += v[i + h], h = 16..1, operand for
-// operand: after one shared-memory transpose (row r of member e to lane r of
-// a warp) every member column is reduced by one warp with shuffles, so the
-// step costs two CTA barriers instead of one per tree level.
-// WARP = false: the same sums by the halving tree in shared memory, one
-// barrier per level, the adds of all members packed into full warps
-template <int S, bool WARP = true>
+// The 32 rows are combined by the halving tree v[i] += v[i + h], h = 16..1,
+// in shared memory, the adds of all members packed into full warps (31 S adds
+// per chunk, one barrier per level).  WARP = true: the same sums in the
+// butterfly order of warp_tree32 (lane 0's value, operand for operand the
+// halving tree) after one shared-memory transpose, one warp per member
+// column: two barriers instead of six, but every lane adds at every level,
+// 5 x 32 adds per member where the halving tree issues 31 -- on GB300's FP64
+// pipe (one 32-lane FP64 instruction per 16 cycles per SM) that costs the
+// FP64-bound SpMV forms 13 % at s = 32.  The default takes the butterfly only
+// at s = 1, where both issue the same FP64 instructions.
+template <int S, bool WARP = (S == 1)>
 __device__ __forceinline__ void chunk_tree(double (*sm)[S + 1], double v0, double v1, int r, int g,
                                            const DotTree &t, int64_t chunk, int off) {
     if constexpr (S == 1) {
@@ -842,8 +845,8 @@ __device__ __forceinline__ void chunk_tree(double (*sm)[S + 1], double v0, doubl
     __syncthreads();
 }
 
-// Subset form of chunk_tree: the chunk's threads are [ltid = 0, nthr), a whole
-// number of warps; all threads of the CTA call it (its barriers are
+// Subset form of chunk_tree (halving tree): the chunk's threads are
+// [ltid = 0, nthr); all threads of the CTA call it (its barriers are
 // CTA-wide); writes only when the chunk exists.
 template <int S>
 __device__ __forceinline__ void chunk_tree_sub(double (*sm)[S + 1], double v0, double v1, int r,
@@ -856,12 +859,16 @@ __device__ __forceinline__ void chunk_tree_sub(double (*sm)[S + 1], double v0, d
         sm[r][2 * g + 1] = v1;
     }
     __syncthreads();
-    const int lane = ltid & 31, warp = ltid >> 5, nw = nthr >> 5;
-    if (chunk < t.count[1])
-        for (int e = warp; e < S; e += nw) {
-            const double v = warp_tree32<double>(sm[lane][e]);
-            if (lane == 0) t.buf[1][chunk * t.width + off + e] = v;
+#pragma unroll
+    for (int h = 16; h >= 1; h >>= 1) {
+        for (int it = ltid; it < h * S; it += nthr) {
+            const int i = it / S, e = it % S;
+            sm[i][e] += sm[i + h][e];
         }
+        __syncthreads();
+    }
+    if (chunk < t.count[1])
+        for (int e = ltid; e < S; e += nthr) t.buf[1][chunk * t.width + off + e] = sm[0][e];
     __syncthreads();
 }
 

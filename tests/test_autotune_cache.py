@@ -47,6 +47,8 @@ def test_mapping_choices_and_flags():
     assert A.mapping_flags({"form": "split", "k1_chunks": 8}) == E.CG_SPLIT64 | (4 << 16)
     assert A.mapping_flags({"form": "f64"}) == 0          # no chunks field: the library default
     assert E.cg_k1_chunks(0) == 0 and E.cg_k1_chunks(2) == 2 << 16
+    assert A.k1_mapping_choices(32) == (1, 2, "defer")
+    assert A.mapping_flags({"form": "dfv", "k1_chunks": "defer"}) == E.CG_K1_DEFER == 1 << 20
 
 
 def test_cached_mapping_is_returned_without_tuning(tmp_path, monkeypatch):

@@ -121,7 +121,7 @@ def test_autotuner_picks_and_caches(torch, tmp_path, monkeypatch):
     import json
     db = json.loads((tmp_path / "tune.json").read_text())
     key = next(k for k in db if "|mapping|12|10|8|" in k)
-    assert db[key]["form"] == form and db[key]["k1_chunks"] in autotune.k1_chunk_choices(8)
+    assert db[key]["form"] == form and db[key]["k1_chunks"] in autotune.k1_mapping_choices(8)
     s, f = autotune.best_width(mesh)
     assert s in autotune.WIDTHS and f in autotune.FORMS
     items, _ = make_items(torch, [(6, 4), (8, 8)])

@@ -326,18 +326,25 @@ def test_cg_matches_oracle_ragged_mesh(torch, s, flags):
 @pytest.mark.parametrize("s", S_ALL)
 @pytest.mark.parametrize("form", ["f64", "df", "split", "dfv"])
 def test_cg_spmv_mapping_knob_is_bitwise_neutral(torch, s, form):
-    """Every chunks-per-CTA mapping of the CG's SpMV (ENS_CG_K1_CHUNKS) gives
+    """Every mapping of the CG's SpMV (ENS_CG_K1_CHUNKS, ENS_CG_K1_DEFER) gives
     bitwise the default's solution, iteration counts and residuals: all sums
     are ordered by row index.  13^3 cells: 86 chunks, so the wider mappings
-    end with a partly filled CTA; a mapping beyond 1024 threads is refused."""
+    end with a partly filled CTA and the deferred tree has three level-1
+    groups; a 2^3-cell mesh is one chunk; a mapping beyond 1024 threads is
+    refused."""
     from paper_1511_03703_gb300 import autotune
     mesh = E.Mesh(13, 10)
     xs = inputs.kl_samples(910, 0, s, 10)
     flags = {"f64": 0, "df": E.CG_DF64, "split": E.CG_SPLIT64, "dfv": 0}[form]
     ref = gpu_solve(mesh, xs, 1e-9, flags=flags | E.CG_GRAPH, presplit=form == "dfv")
-    for c in autotune.k1_chunk_choices(s):
+    for c in autotune.k1_mapping_choices(s):
         got = gpu_solve(mesh, xs, 1e-9, flags=flags | E.CG_GRAPH | E.cg_k1_chunks(c), presplit=form == "dfv")
         assert got[1] == ref[1] and got[2] == ref[2] and np.array_equal(got[0], ref[0]), c
+    # the deferred tree on a mesh of one chunk (the top is the chunk's partials)
+    small = E.Mesh(2, 10)
+    a = gpu_solve(small, xs, 1e-9, flags=flags, presplit=form == "dfv")
+    d = gpu_solve(small, xs, 1e-9, flags=flags | E.CG_K1_DEFER, presplit=form == "dfv")
+    assert a[1] == d[1] and a[2] == d[2] and np.array_equal(a[0], d[0])
     too_wide = 2 * max(autotune.k1_chunk_choices(s))
     if too_wide <= 8:
         with pytest.raises(E.EnsError) as ei:
