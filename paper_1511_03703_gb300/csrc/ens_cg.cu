@@ -85,6 +85,69 @@ static int k1_nsub_from_flags(int flags, int s, int mode) {
     return (f <= 4 && nsub <= k1_max_nsub_rt(s)) ? nsub : -1;
 }
 
+// ------------------------------------------------------ device-side loop
+__global__ void loop_ctl_kernel(const int32_t *flags, int32_t *blocks, int max_blocks,
+                                cudaGraphConditionalHandle h) {
+    const int b = *blocks + 1;
+    *blocks = b;
+    const bool more = (flags[0] != 0 || flags[1] != 0) && b < max_blocks;
+    cudaGraphSetConditional(h, more ? 1u : 0u);
+}
+
+bool use_device_loop() {
+    static const bool v = [] {
+        const char *e = getenv("ENS_DEVICE_LOOP");
+        return e ? (atoi(e) != 0) : true;
+    }();
+    return v;
+}
+
+int while_graph(LoopBodyFn body, void *ctx, const int32_t *flags, int32_t *blocks, int max_blocks,
+                cudaGraph_t *graph_out, cudaGraphExec_t *exec_out) {
+    *graph_out = nullptr;
+    *exec_out = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    cudaStream_t cap = nullptr;
+    cudaError_t ce = cudaGraphCreate(&graph, 0);
+    cudaGraphConditionalHandle h = 0;
+    if (ce == cudaSuccess) ce = cudaGraphConditionalHandleCreate(&h, graph, 1u, cudaGraphCondAssignDefault);
+    cudaGraph_t bodyg = nullptr;
+    if (ce == cudaSuccess) {
+        cudaGraphNodeParams np = {};
+        np.type = cudaGraphNodeTypeConditional;
+        np.conditional.handle = h;
+        np.conditional.type = cudaGraphCondTypeWhile;
+        np.conditional.size = 1;
+        cudaGraphNode_t node;
+        ce = cudaGraphAddNode(&node, graph, nullptr, nullptr, 0, &np);
+        if (ce == cudaSuccess) bodyg = np.conditional.phGraph_out[0];
+    }
+    if (ce == cudaSuccess) ce = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking);
+    int rc = ENS_OK;
+    if (ce == cudaSuccess) {
+        ce = cudaStreamBeginCaptureToGraph(cap, bodyg, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+        if (ce == cudaSuccess) {
+            rc = body(ctx, cap);
+            loop_ctl_kernel<<<1, 1, 0, cap>>>(flags, blocks, max_blocks, h);
+            cudaGraph_t got = nullptr;
+            const cudaError_t ce2 = cudaStreamEndCapture(cap, &got);
+            if (ce == cudaSuccess) ce = cudaGetLastError();
+            if (ce == cudaSuccess) ce = ce2;
+        }
+    }
+    if (cap) cudaStreamDestroy(cap);
+    if (ce == cudaSuccess && rc == ENS_OK) ce = cudaGraphInstantiate(&exec, graph, 0);
+    if (ce != cudaSuccess || rc != ENS_OK) {
+        if (graph) cudaGraphDestroy(graph);
+        cudaGetLastError();   // graph API errors are not sticky: clear for the caller's fallback
+        return rc != ENS_OK ? rc : fail(ENS_ERR_CUDA, "device loop graph: %s", cudaGetErrorString(ce));
+    }
+    *graph_out = graph;
+    *exec_out = exec;
+    return ENS_OK;
+}
+
 static size_t cg_bytes(int64_t n, int s) {
     return align256(sizeof(CgState)) + 4 * align256(sizeof(double) * (size_t)n * s) +
            dot_tree_bytes(n, s) + dot_tree_bytes(n, 2 * s);
@@ -176,7 +239,33 @@ static int cg_run(const ens_graph *g, const double *vals, const float2 *vdf, con
 
     cudaGraphExec_t gexec = nullptr;
     cudaGraph_t graph = nullptr;
-    if (use_graph) {
+    const int max_blocks = max_iter / check_every + 3;
+    // ENS_CG_GRAPH without per-launch timing: the convergence test between
+    // blocks runs on the device (while node); the host waits once
+    bool device_loop = use_graph && !timing && use_device_loop();
+    if (device_loop) {
+        struct Ctx { const CgArgs *a; int nsub, check_every; } ctx{&a, nsub, check_every};
+        LoopBodyFn body = [](void *c, cudaStream_t cap) -> int {
+            const Ctx &x = *static_cast<const Ctx *>(c);
+            for (int i = 0; i < x.check_every; ++i) {
+                K::spmv(*x.a, x.nsub, cap);
+                K::resid(*x.a, cap);
+                K::update(*x.a, cap);
+            }
+            return ENS_OK;
+        };
+        device_loop = while_graph(body, &ctx, &a.st->active_count, &a.st->loop_blocks, max_blocks, &graph,
+                                  &gexec) == ENS_OK;
+        if (device_loop) {
+            const cudaError_t ce = cudaGraphLaunch(gexec, st);
+            cudaGraphExecDestroy(gexec);
+            cudaGraphDestroy(graph);
+            gexec = nullptr;
+            graph = nullptr;
+            if (ce != cudaSuccess) { destroy_events(); return cuda_fail(ce, "device loop graph launch"); }
+        }
+    }
+    if (use_graph && !device_loop) {
         // capture on a private stream (the legacy default stream cannot be
         // captured); the graph is then launched on the caller's stream.  With
         // ENS_CG_TIME_SPMV the events around each SpMV become event-record
@@ -212,9 +301,8 @@ static int cg_run(const ens_graph *g, const double *vals, const float2 *vdf, con
 
     int32_t flags_h[2];
     int iter_blocks = 0;
-    const int max_blocks = max_iter / check_every + 3;
     rc = ENS_OK;
-    while (iter_blocks < max_blocks) {
+    while (!device_loop && iter_blocks < max_blocks) {
         if (use_graph) {
             cudaError_t ce = cudaGraphLaunch(gexec, st);
             if (ce != cudaSuccess) { rc = cuda_fail(ce, "cudaGraphLaunch"); break; }
@@ -255,6 +343,7 @@ static int cg_run(const ens_graph *g, const double *vals, const float2 *vdf, con
     ENS_CUDA_TRY(cudaMemcpyAsync(&hs, a.st, sizeof(CgState), cudaMemcpyDeviceToHost, st));
     ENS_CUDA_TRY(cudaStreamSynchronize(st));
     destroy_events();
+    if (device_loop) launches += (3 * check_every + 1) * hs.loop_blocks;
     int maxit = 0, first_bad = ENS_OK;
     for (int e = 0; e < S; ++e) {
         if (out.iters) out.iters[e] = hs.iters[e];
@@ -559,7 +648,24 @@ static int batched_run(int n_items, const ens_batch_item *items, double tol, int
     };
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t gexec = nullptr;
-    if (use_graph) {
+    const int max_blocks = max_iter / check_every + 3;
+    // graph replay without timing: the convergence test between blocks on the
+    // device (while node; d_poll[2] counts the blocks)
+    bool device_loop = use_graph && !timing && use_device_loop();
+    if (device_loop) {
+        ENS_CUDA_TRY(cudaMemsetAsync(d_poll + 2, 0, sizeof(int), st));
+        auto body = [&](cudaStream_t cap) {
+            for (int i = 0; i < check_every; ++i) iteration(cap, i);
+            batch_poll_kernel<<<1, 64, 0, cap>>>(d_items, n_items, d_poll);
+        };
+        device_loop = while_graph_fn(body, d_poll, d_poll + 2, max_blocks, &graph, &gexec) == ENS_OK;
+        if (device_loop) {
+            if ((rc = launch_while_graph(graph, gexec, st))) return rc;
+            graph = nullptr;
+            gexec = nullptr;
+        }
+    }
+    if (use_graph && !device_loop) {
         cudaStream_t cap;
         ENS_CUDA_TRY(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
         cudaError_t ce = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
@@ -574,9 +680,8 @@ static int batched_run(int n_items, const ens_batch_item *items, double tol, int
         if (ce != cudaSuccess) { cudaGraphDestroy(graph); return cuda_fail(ce, "cudaGraphInstantiate"); }
     }
     int32_t hp[2];
-    const int max_blocks = max_iter / check_every + 3;
     rc = ENS_OK;
-    for (int blk = 0; blk < max_blocks; ++blk) {
+    for (int blk = 0; !device_loop && blk < max_blocks; ++blk) {
         if (use_graph) {
             cudaError_t ce = cudaGraphLaunch(gexec, st);
             if (ce != cudaSuccess) { rc = cuda_fail(ce, "cudaGraphLaunch"); break; }
@@ -606,7 +711,10 @@ static int batched_run(int n_items, const ens_batch_item *items, double tol, int
     std::vector<CgState> hs(n_items);
     for (int i = 0; i < n_items; ++i)
         ENS_CUDA_TRY(cudaMemcpyAsync(&hs[i], h[i].a.st, sizeof(CgState), cudaMemcpyDeviceToHost, st));
+    int32_t loop_blocks = 0;
+    if (device_loop) ENS_CUDA_TRY(cudaMemcpyAsync(&loop_blocks, d_poll + 2, sizeof(int), cudaMemcpyDeviceToHost, st));
     ENS_CUDA_TRY(cudaStreamSynchronize(st));
+    if (device_loop) launches += (3 * check_every + 2) * loop_blocks;
     int first_bad = ENS_OK, maxit = 0, real = 0, nfb = 0;
     for (int i = 0; i < n_items; ++i) {
         nfb += hs[i].fb_count;

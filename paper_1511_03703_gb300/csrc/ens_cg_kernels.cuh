@@ -10,7 +10,7 @@ struct CgState {
     double rho[32], alpha[32], beta[32], bnorm[32], relres[32];
     int active[32], updx[32], zerox[32], iters[32], status[32], fb[32];
     int active_count, updx_any, zero_any, spmv_real;
-    int df_bad_any, fb_count, pad1, pad2;
+    int df_bad_any, fb_count, loop_blocks, pad2;   // loop_blocks: blocks run by the device loop
     double bnorm_all;
 };
 
@@ -204,10 +204,10 @@ __device__ __forceinline__ void k1_body(const CgArgs &a, const int cta, K1Smem<S
                                                a.pf_cap);
         else staged = stage_chunk(sh.cc[0], a.row_map, a.col, chunk, a.n);
     } else if (MODE == 3) {
-        staged = stage_chunk_sub(sh.cc[sub], a.row_map, a.col, chunk, a.n, ltid, T, a.vdf, S * 8u, a.val_bytes,
-                                 a.pf_cap);
+        staged = stage_chunk_sub<stage_unroll(T)>(sh.cc[sub], a.row_map, a.col, chunk, a.n, ltid, T, a.vdf, S * 8u,
+                                                  a.val_bytes, a.pf_cap);
     } else {
-        staged = stage_chunk_sub(sh.cc[sub], a.row_map, a.col, chunk, a.n, ltid, T);
+        staged = stage_chunk_sub<stage_unroll(T)>(sh.cc[sub], a.row_map, a.col, chunk, a.n, ltid, T);
     }
     if (ld_cg(&st->active_count) == 0) {   // every member stopped: a launch queued past convergence
         if (cta == 0 && threadIdx.x == 0 && st->updx_any) {
@@ -318,7 +318,8 @@ __device__ __forceinline__ void k1_single(const CgArgs &a) {
     const int64_t R = (int64_t)blockIdx.x * 32 + r;
     __shared__ ChunkCols cc;
     const void *vblock = (MODE == 3) ? static_cast<const void *>(a.vdf) : static_cast<const void *>(a.vals);
-    const bool staged = stage_chunk_pf<VEC>(cc, a.row_map, a.col, blockIdx.x, a.n, vblock, S * 8u, a.val_bytes,
+    const bool staged = stage_chunk_pf<VEC, stage_unroll(RowMap<S>::THREADS)>(cc, a.row_map, a.col, blockIdx.x, a.n,
+                                                                            vblock, S * 8u, a.val_bytes,
                                             a.pf_cap);
     if (ld_cg(&st->active_count) == 0) {   // every member stopped: a launch queued past convergence
         if (blockIdx.x == 0 && threadIdx.x == 0 && st->updx_any) {

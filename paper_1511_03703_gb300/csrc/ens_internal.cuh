@@ -32,6 +32,38 @@ inline bool supported_s(int s) { return s == 1 || s == 4 || s == 8 || s == 16 ||
 
 int check_graph(const ens_graph *g);
 
+// Device-side convergence loop of the Krylov solvers: an instantiated CUDA
+// graph whose while node replays a body (the caller's capture callback, run
+// on a capture stream: one block of iterations) followed by a one-thread
+// control kernel.  The control kernel counts blocks in *blocks and continues
+// while (flags[0] | flags[1]) != 0 and fewer than max_blocks blocks ran, so
+// the host synchronises once per solve instead of once per block.  The body
+// runs at least once.  Returns ENS_OK, or an error (graph objects released;
+// callers then fall back to the host-polled loop).  use_device_loop(): the
+// ENS_DEVICE_LOOP environment variable (0 or 1, default 1).
+using LoopBodyFn = int (*)(void *ctx, cudaStream_t cap);
+int while_graph(LoopBodyFn body, void *ctx, const int32_t *flags, int32_t *blocks, int max_blocks,
+                cudaGraph_t *graph_out, cudaGraphExec_t *exec_out);
+bool use_device_loop();
+// while_graph with a callable body(cudaStream_t cap) (a lambda with captures)
+template <typename F>
+inline int while_graph_fn(F &body, const int32_t *flags, int32_t *blocks, int max_blocks, cudaGraph_t *graph_out,
+                          cudaGraphExec_t *exec_out) {
+    LoopBodyFn fn = [](void *c, cudaStream_t cap) -> int {
+        (*static_cast<F *>(c))(cap);
+        return ENS_OK;
+    };
+    return while_graph(fn, &body, flags, blocks, max_blocks, graph_out, exec_out);
+}
+// launch an instantiated device-loop graph on st and release it (it stays
+// alive until its replay completes)
+inline int launch_while_graph(cudaGraph_t graph, cudaGraphExec_t exec, cudaStream_t st) {
+    const cudaError_t ce = cudaGraphLaunch(exec, st);
+    cudaGraphExecDestroy(exec);
+    cudaGraphDestroy(graph);
+    return ce == cudaSuccess ? ENS_OK : cuda_fail(ce, "device loop graph launch");
+}
+
 // -------------------------------------------------------- cache-hinted loads
 // streaming loads for data read exactly once (matrix values): evict-first
 __device__ __forceinline__ double2 ld_stream(const double2 *p) {

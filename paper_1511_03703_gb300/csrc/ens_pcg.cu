@@ -226,7 +226,25 @@ static int pcg_run(const ens_graph *g, const double *vals, const double *b, doub
     const bool use_graph = (flags & ENS_CG_GRAPH) != 0;
     cudaGraphExec_t gexec = nullptr;
     cudaGraph_t graph = nullptr;
-    if (use_graph) {
+    const int max_blocks = max_iter / check_every + 3;
+    // graph replay: the convergence test between blocks on the device (while node)
+    bool device_loop = use_graph && use_device_loop();
+    if (device_loop) {
+        auto body = [&](cudaStream_t cap) {
+            for (int i = 0; i < check_every; ++i) {
+                k1_launch<S, 0>(c, k1_default_nsub(S, 0), cap);
+                precond(0, cap);
+            }
+        };
+        device_loop = while_graph_fn(body, &c.st->active_count, &c.st->loop_blocks, max_blocks, &graph, &gexec) ==
+                      ENS_OK;
+        if (device_loop) {
+            if ((rc = launch_while_graph(graph, gexec, st))) return rc;
+            graph = nullptr;
+            gexec = nullptr;
+        }
+    }
+    if (use_graph && !device_loop) {
         cudaStream_t cap;
         ENS_CUDA_TRY(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
         cudaError_t ce = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
@@ -244,9 +262,8 @@ static int pcg_run(const ens_graph *g, const double *vals, const double *b, doub
     }
     int32_t hflag[2];
     int polls = 0;
-    const int max_blocks = max_iter / check_every + 3;
     rc = ENS_OK;
-    for (int blk = 0; blk < max_blocks; ++blk) {
+    for (int blk = 0; !device_loop && blk < max_blocks; ++blk) {
         if (use_graph) {
             cudaError_t ce = cudaGraphLaunch(gexec, st);
             if (ce != cudaSuccess) { rc = cuda_fail(ce, "cudaGraphLaunch"); break; }
@@ -276,6 +293,7 @@ static int pcg_run(const ens_graph *g, const double *vals, const double *b, doub
     ENS_CUDA_TRY(cudaMemcpyAsync(&hs, c.st, sizeof(CgState), cudaMemcpyDeviceToHost, st));
     ENS_CUDA_TRY(cudaMemcpyAsync(&hp, a.ps, sizeof(PcgState), cudaMemcpyDeviceToHost, st));
     ENS_CUDA_TRY(cudaStreamSynchronize(st));
+    if (device_loop) launches += (per_iter * check_every + 1) * hs.loop_blocks;
     int maxit = 0, first_bad = ENS_OK;
     for (int e = 0; e < S; ++e) {
         if (out.iters) out.iters[e] = hs.iters[e];

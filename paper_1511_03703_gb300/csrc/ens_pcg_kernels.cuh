@@ -45,9 +45,9 @@ struct PcgArgs {
 template <int S, int MODE>
 __device__ __forceinline__ double2 pc_setup_spmv(const PcgArgs &a, ChunkCols &cc, int r, int g, bool valid) {
     const CgArgs &c = a.c;
-    if constexpr (MODE == 4) {
-        const bool staged = stage_chunk_pf(cc, c.row_map, c.col, blockIdx.x, c.n, a.vals32, S * 4u, a.vals32_bytes,
-                                           0xffffffffu);
+    if constexpr (MODE == 4) {   // one column per load: 40 registers, 3 CTAs of 512 threads per SM at s = 32
+        const bool staged = stage_chunk_pf<false>(cc, c.row_map, c.col, blockIdx.x, c.n, a.vals32, S * 4u,
+                                                  a.vals32_bytes, 0xffffffffu);
         const int64_t R = (int64_t)blockIdx.x * 32 + r;
         const float2 y = chunk_spmv_f32<S, float>(cc, staged, c.col, a.vals32, nullptr, a.v32, r, g, R, valid);
         return make_double2((double)y.x, (double)y.y);

@@ -111,8 +111,12 @@ struct ColGlobal {
 // columns [e0, e1) into cc.col (threads tid = 0..nthr-1 of the caller's group);
 // reads only whole 16-byte groups inside [base, e1) plus at most 3 single
 // entries before e1, so nothing past the chunk's last entry is touched.
-// VEC = false: one entry per load.
-template <bool VEC = true>
+// VEC = false: one entry per load.  U: 16-byte loads a thread issues before
+// its first store -- 4 for groups of at most 128 threads (a hex-mesh chunk has
+// up to 216 groups of 16 bytes), 1 for groups of 256 or more, where one pass
+// covers the chunk and 4 in flight would only hold 16 more registers (the FP32
+// power step went from 40 to 62 registers and 3 to 2 CTAs per SM with it).
+template <bool VEC = true, int U = 1>
 __device__ __forceinline__ void stage_cols(ChunkCols &cc, const int32_t *__restrict__ col, int e0, int e1,
                                            int tid, int nthr) {
     const int base = e0 & ~3;
@@ -125,13 +129,13 @@ __device__ __forceinline__ void stage_cols(ChunkCols &cc, const int32_t *__restr
     const int nv = v1 - v0;
     const int4 *c4 = reinterpret_cast<const int4 *>(col) + v0;
     int4 *d4 = reinterpret_cast<int4 *>(cc.col);
-    for (int k0 = tid; k0 < nv; k0 += 4 * nthr) {
-        int4 t[4];
+    for (int k0 = tid; k0 < nv; k0 += U * nthr) {
+        int4 t[U];
 #pragma unroll
-        for (int u = 0; u < 4; ++u)
+        for (int u = 0; u < U; ++u)
             if (k0 + u * nthr < nv) t[u] = __ldg(c4 + k0 + u * nthr);
 #pragma unroll
-        for (int u = 0; u < 4; ++u)
+        for (int u = 0; u < U; ++u)
             if (k0 + u * nthr < nv) d4[k0 + u * nthr] = t[u];
     }
     for (int i = 4 * max(v1, v0) + tid; i < e1; i += nthr) cc.col[i - base] = __ldg(col + i);
@@ -139,6 +143,9 @@ __device__ __forceinline__ void stage_cols(ChunkCols &cc, const int32_t *__restr
 }
 
 __device__ __forceinline__ bool chunk_fits(int e0, int e1) { return e1 - (e0 & ~3) <= kColCap; }
+
+// stage_cols' loads in flight per thread for a group of `threads` threads per chunk
+constexpr int stage_unroll(int threads) { return threads <= 128 ? 4 : 1; }
 
 // all threads of the CTA; returns true when the columns are staged
 __device__ __forceinline__ bool stage_chunk(ChunkCols &cc, const int32_t *__restrict__ row_map,
@@ -183,7 +190,7 @@ __device__ __forceinline__ void l2_prefetch_span(const void *base, uint64_t begi
     asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"((uint32_t)(end - begin)) : "memory");
 }
 
-template <bool VEC = true>
+template <bool VEC = true, int U = 1>
 __device__ __forceinline__ bool stage_chunk_pf(ChunkCols &cc, const int32_t *__restrict__ row_map,
                                                const int32_t *__restrict__ col, int64_t chunk, int32_t n,
                                                const void *vbase, uint32_t bytes_per_entry,
@@ -196,7 +203,7 @@ __device__ __forceinline__ bool stage_chunk_pf(ChunkCols &cc, const int32_t *__r
     if (threadIdx.x == 0 && cap > 0)
         l2_prefetch_bulk(vbase, (uint64_t)e0 * bytes_per_entry, (uint64_t)e1 * bytes_per_entry, total_bytes, cap);
     const bool staged = chunk_fits(e0, e1);
-    if (staged) stage_cols<VEC>(cc, col, e0, e1, threadIdx.x, blockDim.x);
+    if (staged) stage_cols<VEC, U>(cc, col, e0, e1, threadIdx.x, blockDim.x);
     __syncthreads();
     return staged;
 }
@@ -205,7 +212,8 @@ __device__ __forceinline__ bool stage_chunk_pf(ChunkCols &cc, const int32_t *__r
 // per chunk, ltid the thread's index inside its chunk): the same copy, with
 // chunks past the end of the matrix left empty, and (cap > 0) each chunk's
 // value block prefetched into L2 as in stage_chunk_pf.  All threads of the
-// CTA call it.
+// CTA call it.  U: see stage_cols.
+template <int U = 1>
 __device__ __forceinline__ bool stage_chunk_sub(ChunkCols &cc, const int32_t *__restrict__ row_map,
                                                 const int32_t *__restrict__ col, int64_t chunk,
                                                 int32_t n, int ltid, int nthr, const void *vbase = nullptr,
@@ -222,7 +230,7 @@ __device__ __forceinline__ bool stage_chunk_sub(ChunkCols &cc, const int32_t *__
     if (ltid == 0 && cap > 0 && e1 > e0)
         l2_prefetch_bulk(vbase, (uint64_t)e0 * bytes_per_entry, (uint64_t)e1 * bytes_per_entry, total_bytes, cap);
     const bool staged = chunk_fits(e0, e1);
-    if (staged) stage_cols(cc, col, e0, e1, ltid, nthr);
+    if (staged) stage_cols<true, U>(cc, col, e0, e1, ltid, nthr);
     __syncthreads();
     return staged;
 }

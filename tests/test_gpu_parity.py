@@ -390,6 +390,31 @@ def test_cg_graph_replay_matches_direct_launches(torch):
         assert d[4].spmv_launches == max(d[1])
 
 
+@pytest.mark.parametrize("s,flags,presplit", [(4, 0, False), (32, E.CG_DF64, False), (32, 0, True),
+                                              (8, E.CG_COUPLED, False), (16, E.cg_k1_chunks("defer"), True)])
+def test_cg_device_loop_matches_host_polled_loop(torch, s, flags, presplit):
+    """ENS_CG_GRAPH without timing runs the convergence test between blocks on
+    the device (a graph while node); with ENS_CG_TIME_SPMV the host polls after
+    every replay.  Both run the same number of blocks: identical bits,
+    iterations and statuses, and the device loop polls nothing."""
+    mesh = E.Mesh(10, 10)
+    xs = inputs.kl_samples(97, 0, s, 10)
+    for ce in (1, 5, 8):
+        a = gpu_solve(mesh, xs, 1e-10, flags=flags | E.CG_GRAPH, check_every=ce, presplit=presplit)
+        b = gpu_solve(mesh, xs, 1e-10, flags=flags | E.CG_GRAPH | E.CG_TIME_SPMV, check_every=ce,
+                      presplit=presplit)
+        assert np.array_equal(a[0], b[0]) and a[1] == b[1] and a[2] == b[2] and a[3] == b[3], ce
+        assert a[4].host_checks == 0 and b[4].host_checks >= 1
+        blocks = b[4].host_checks
+        assert a[4].kernel_launches == b[4].kernel_launches + blocks  # one control kernel per block
+    # max_iter reached inside the device loop: the same bounded result as the host loop
+    a = gpu_solve(mesh, xs, 0.0, max_iter=13, flags=flags | E.CG_GRAPH, check_every=4, presplit=presplit)
+    b = gpu_solve(mesh, xs, 0.0, max_iter=13, flags=flags | E.CG_GRAPH | E.CG_TIME_SPMV, check_every=4,
+                  presplit=presplit)
+    assert np.array_equal(a[0], b[0]) and a[1] == b[1] and max(a[1]) == 13
+    assert all(v == 5 for v in a[3])   # ENS_ERR_NOT_CONVERGED for every member
+
+
 def test_cg_member_edge_cases(torch):
     mesh = E.Mesh(6, 10)
     s = 4
