@@ -135,7 +135,12 @@ int ens_mode_matrices(int N, const ens_graph *graph, int M, const double *kl_tab
  * (exact maxima of the separable table), and for members that bound does not
  * clear by the exact minimum over all (2N)^3 Gauss coordinates.  With
  * kl_table the call synchronises `stream` (b, 16-byte aligned, is the check's
- * scratch before it is written).  If a member fails, values and b are still
+ * scratch before it is written).  The bounds reach the host through pinned,
+ * device-mapped host memory that the kernel writes directly, so the wait is
+ * not held up by copies on other streams; the library allocates that memory
+ * once per device and CUDA context (64 slots of 256 bytes, released with the
+ * context) and reads the bounds by a copy when no slot is free.  Thread-safe
+ * across host threads and streams.  If a member fails, values and b are still
  * written for every member and the call returns ENS_ERR_NONPOS_COEFF (the
  * message names the member and its minimum); a NaN coefficient fails too. */
 int ens_assemble(const ens_graph *graph, const uint8_t *bmask, int s, int M, const double *kl_table,

@@ -13,6 +13,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <mutex>
 
 #include "ens_spmv.cuh"
 
@@ -353,6 +354,100 @@ static double key_to_double(unsigned long long k) {
     return v;
 }
 
+// Pinned, device-mapped host slots for the check's bounds: the bound kernel
+// stores its s values straight into host memory, and the host reads them
+// after synchronising the stream, with no copy-engine transfer.  A small
+// device-to-host copy would queue behind any large copy in flight on another
+// stream (a solution read back while the next ensemble assembles) and leave
+// the GPU idle for its length.  One block of kSlots slots per device and CUDA
+// context, allocated on first use and never freed: a context that is
+// destroyed (cudaDeviceReset) releases it, and the next context gets a new
+// block.  A slot is held for one check; with none free, or without the
+// driver's context id, the check reads its bounds by a copy instead.
+constexpr int kSlotDevices = 64, kSlots = 64, kSlotDoubles = 32;
+struct SlotBlock {
+    double *host;
+    double *dev;
+    unsigned long long ctx;
+    uint64_t used;
+};
+static std::mutex g_slot_mu;
+static SlotBlock g_slot[kSlotDevices];
+
+typedef int (*CtxGetCurrentFn)(void **ctx);
+typedef int (*CtxGetIdFn)(void *ctx, unsigned long long *id);
+static unsigned long long context_id() {   // 0 when the driver entry points are unavailable
+    static CtxGetCurrentFn get_current = nullptr;
+    static CtxGetIdFn get_id = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void *f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_current = reinterpret_cast<CtxGetCurrentFn>(f);
+        f = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_id = reinterpret_cast<CtxGetIdFn>(f);
+    });
+    cudaGetLastError();
+    if (!get_current || !get_id) return 0ull;
+    void *ctx = nullptr;
+    unsigned long long id = 0ull;
+    if (get_current(&ctx) != 0 || !ctx || get_id(ctx, &id) != 0) return 0ull;
+    return id;
+}
+
+struct Slot {
+    int dev = -1, idx = -1;
+    unsigned long long ctx = 0ull;
+    double *host = nullptr, *devp = nullptr;
+};
+
+static Slot acquire_slot() {
+    Slot sl;
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kSlotDevices) { cudaGetLastError(); return sl; }
+    cudaFree(nullptr);   // the device's primary context current before its id is read
+    cudaGetLastError();
+    const unsigned long long ctx = context_id();
+    if (ctx == 0ull) return sl;
+    std::lock_guard<std::mutex> lock(g_slot_mu);
+    SlotBlock &b = g_slot[dev];
+    if (!b.host || b.ctx != ctx) {   // first use, or the block's context was destroyed
+        void *h = nullptr, *d = nullptr;
+        if (cudaHostAlloc(&h, sizeof(double) * kSlots * kSlotDoubles, cudaHostAllocMapped) != cudaSuccess ||
+            cudaHostGetDevicePointer(&d, h, 0) != cudaSuccess) {
+            if (h) cudaFreeHost(h);
+            cudaGetLastError();
+            return sl;
+        }
+        b.host = static_cast<double *>(h);
+        b.dev = static_cast<double *>(d);
+        b.ctx = ctx;
+        b.used = 0;
+    }
+    for (int i = 0; i < kSlots; ++i)
+        if (!(b.used & (1ull << i))) {
+            b.used |= 1ull << i;
+            sl.dev = dev;
+            sl.idx = i;
+            sl.ctx = ctx;
+            sl.host = b.host + (size_t)i * kSlotDoubles;
+            sl.devp = b.dev + (size_t)i * kSlotDoubles;
+            return sl;
+        }
+    return sl;
+}
+
+static void release_slot(const Slot &sl) {
+    if (sl.idx < 0) return;
+    std::lock_guard<std::mutex> lock(g_slot_mu);
+    SlotBlock &b = g_slot[sl.dev];
+    if (b.ctx == sl.ctx) b.used &= ~(1ull << sl.idx);
+}
+
 // Host: the positivity check of ens_assemble (synchronises the stream).
 // Returns ENS_OK with *bad_member = -1 when every member's coefficient is
 // positive at every Gauss point, else the first failing member and its
@@ -370,12 +465,16 @@ static int coeff_check(const ens_graph *g, int M, const double *kl_table, int s,
         if (!(kappa0 > 0.0)) { *bad_member = 0; *bad_min = kappa0; }
         return ENS_OK;
     }
-    double *bound = static_cast<double *>(scratch);
-    coeff_bound_kernel<<<1, 256, 0, st>>>(N, M, kl_table, s, xi, sigma, kappa0, bound);
-    ENS_LAUNCH_CHECK("coeff_bound_kernel");
     double hb[32];
-    ENS_CUDA_TRY(cudaMemcpyAsync(hb, bound, sizeof(double) * s, cudaMemcpyDeviceToHost, st));
-    ENS_CUDA_TRY(cudaStreamSynchronize(st));
+    const Slot sl = acquire_slot();
+    double *bound = sl.devp ? sl.devp : static_cast<double *>(scratch);
+    coeff_bound_kernel<<<1, 256, 0, st>>>(N, M, kl_table, s, xi, sigma, kappa0, bound);
+    cudaError_t ce = cudaGetLastError();
+    if (ce == cudaSuccess && !sl.devp) ce = cudaMemcpyAsync(hb, bound, sizeof(double) * s, cudaMemcpyDeviceToHost, st);
+    if (ce == cudaSuccess) ce = cudaStreamSynchronize(st);
+    if (ce == cudaSuccess && sl.devp) memcpy(hb, sl.host, sizeof(double) * s);
+    release_slot(sl);
+    if (ce != cudaSuccess) return cuda_fail(ce, "coefficient bound");
     int need[32], any = 0;
     for (int e = 0; e < s; ++e) { need[e] = !(hb[e] > 0.0); any |= need[e]; }
     if (!any) return ENS_OK;

@@ -149,6 +149,61 @@ def test_assemble_coefficient_check_exact_minimum(torch, s):
     assert ei.value.code == 7
 
 
+def test_assemble_coefficient_check_concurrent_threads(torch):
+    """Eight host threads check coefficients at once, each on its own stream
+    (the bounds come back through pinned slots shared per device), while a
+    large device-to-host copy is in flight on another stream: every thread gets
+    its own members' verdict, and the good ensembles' values equal a serial
+    assembly bitwise."""
+    import threading
+    N, M, s = 8, 10, 8
+    mesh = E.Mesh(N, M)
+    cases = []
+    for t in range(8):
+        xs = inputs.kl_samples(2400 + t, 0, s, M)
+        if t % 3 == 1:
+            xs[t % s] *= 40.0   # member t % s has a negative coefficient
+        cases.append(xs)
+    ref = []
+    for xs in cases:
+        bad = [O.coeff_min(N, M, x) <= 0 for x in xs]
+        v = torch.empty(mesh.nnz * s, dtype=torch.float64, device=gpu())
+        b = torch.empty(mesh.n * s, dtype=torch.float64, device=gpu())
+        mesh.assemble(s, to_dev(inputs.ensemble_layout(xs)), values=v, b=b, check=False)
+        ref.append((bad.index(True) if any(bad) else -1, to_np(v)))
+    big = torch.ones(64 << 20, dtype=torch.float64, device=gpu())
+    host = torch.empty(big.shape, dtype=torch.float64).pin_memory()
+    side = torch.cuda.Stream()
+    torch.cuda.synchronize()
+    with torch.cuda.stream(side):
+        host.copy_(big, non_blocking=True)   # 512 MB in flight while the checks run
+    out = [None] * len(cases)
+
+    def work(t):
+        st = torch.cuda.Stream()
+        with torch.cuda.stream(st):
+            v = torch.empty(mesh.nnz * s, dtype=torch.float64, device=gpu())
+            b = torch.empty(mesh.n * s, dtype=torch.float64, device=gpu())
+            xi = to_dev(inputs.ensemble_layout(cases[t]))
+            st.synchronize()
+            try:
+                mesh.assemble(s, xi, values=v, b=b, stream=st)
+                out[t] = (-1, to_np(v))
+            except E.EnsError as err:
+                out[t] = (int(str(err).split("member ")[1].split(":")[0]) if err.code == 7 else -99, None)
+
+    threads = [threading.Thread(target=work, args=(t,)) for t in range(len(cases))]
+    for th in threads:
+        th.start()
+    for th in threads:
+        th.join()
+    side.synchronize()
+    for t, (got, want) in enumerate(zip(out, ref)):
+        assert got is not None and got[0] == want[0], t
+        if want[0] < 0:
+            assert np.array_equal(got[1], want[1]), t
+
+
 # ------------------------------------------------------------------ A4 SpMV
 @pytest.mark.parametrize("N", [3, 8, 13])
 @pytest.mark.parametrize("s", S_ALL)
