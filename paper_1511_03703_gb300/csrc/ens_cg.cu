@@ -432,7 +432,7 @@ __global__ void __launch_bounds__(TH, 1024 / TH) cg_spmv_batched(BatchTables bt)
     const BItem &it = bt.items[__ldg(bt.k1_map + blockIdx.x)];
     const int cta = blockIdx.x - it.k1_cta0;
 #define ENS_BK1(SS) \
-    k1_body<SS, MODE, BatchK1<SS, TH>::NSUB>(it.a, cta, *reinterpret_cast<typename BatchK1<SS, TH>::Smem *>(raw))
+    k1_body<SS, MODE, BatchK1<SS, TH>::NSUB, true>(it.a, cta, *reinterpret_cast<typename BatchK1<SS, TH>::Smem *>(raw))
     switch (it.S) {
         case 1: ENS_BK1(1); break;
         case 4: ENS_BK1(4); break;
@@ -445,7 +445,7 @@ __global__ void __launch_bounds__(TH, 1024 / TH) cg_spmv_batched(BatchTables bt)
 
 template <int S>
 __device__ __forceinline__ void k2_batched_s(const CgArgs &a, int cta, unsigned char *raw) {
-    k2_body<S, kBatchThreads>(a, cta, reinterpret_cast<double(*)[32][S + 1]>(raw));
+    k2_body<S, kBatchThreads, 2, true>(a, cta, reinterpret_cast<double(*)[32][S + 1]>(raw));
 }
 
 // 32 registers, 4 CTAs per SM (with 64 registers and 2 CTAs per SM the 2048-sample
