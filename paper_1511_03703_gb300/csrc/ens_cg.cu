@@ -19,8 +19,10 @@
 // K3 3 reads + 2 writes (10 vector passes; +1 write of the split p in df mode).
 // The per-member scalar work runs in the CTA that completes each kernel's
 // deterministic dot tree.  K2/K3 stream tiles of 4-8 tree chunks per CTA.
-// Flag protocol: K2 sets updx_e for members active in its iteration, K3 reads
-// them, and the next K1 clears them (also when it exits early).
+// Flag protocol: K1's epilogue sets updx_e for the members still active after
+// its breakdown test, K3 reads them (before it waits for K2, when it is
+// launched with a programmatic dependency on K2), and a K1 that exits early
+// clears them.
 #include <stdlib.h>
 
 #include <vector>
@@ -92,6 +94,14 @@ __global__ void loop_ctl_kernel(const int32_t *flags, int32_t *blocks, int max_b
     *blocks = b;
     const bool more = (flags[0] != 0 || flags[1] != 0) && b < max_blocks;
     cudaGraphSetConditional(h, more ? 1u : 0u);
+}
+
+static bool use_cg_pdl() {
+    static const bool v = [] {
+        const char *e = getenv("ENS_CG_PDL");
+        return e ? (atoi(e) != 0) : true;
+    }();
+    return v;
 }
 
 bool use_device_loop() {
@@ -168,8 +178,24 @@ struct CgKernels {
         const unsigned grid = (unsigned)((a.t1.count[1] + L::Map::CPC - 1) / L::Map::CPC);
         cg_resid_kernel<S, 2><<<grid, L::TH, 0, st>>>(a);
     }
+    // K3 with a programmatic dependency on K2 (ENS_CG_PDL, default on): its
+    // first CTAs start their x update as K2's last wave leaves SMs idle
     static void update(const CgArgs &a, cudaStream_t st) {
-        cg_update_kernel<S, MODE><<<vec_grid(a), VecMap<S>::THREADS, 0, st>>>(a);
+        if (use_cg_pdl()) {
+            cudaLaunchConfig_t cfg = {};
+            cfg.gridDim = dim3(vec_grid(a));
+            cfg.blockDim = dim3(VecMap<S>::THREADS);
+            cfg.dynamicSmemBytes = 0;
+            cfg.stream = st;
+            cudaLaunchAttribute at[1];
+            at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+            at[0].val.programmaticStreamSerializationAllowed = 1;
+            cfg.attrs = at;
+            cfg.numAttrs = 1;
+            cudaLaunchKernelEx(&cfg, cg_update_kernel<S, MODE>, a);
+        } else {
+            cg_update_kernel<S, MODE><<<vec_grid(a), VecMap<S>::THREADS, 0, st>>>(a);
+        }
     }
     static void final_(const CgArgs &a, unsigned grid, cudaStream_t st) {
         cg_final_kernel<S><<<grid, RowMap<S>::THREADS, 0, st>>>(a);
@@ -464,7 +490,7 @@ __global__ void __launch_bounds__(kBatchThreads, 4) cg_resid_batched(BatchTables
 }
 
 template <int MODE>
-__global__ void __launch_bounds__(kBatchThreads) cg_update_batched(BatchTables bt) {
+__global__ void __launch_bounds__(kBatchThreads, 3) cg_update_batched(BatchTables bt) {
     const BItem &it = bt.items[__ldg(bt.v_map + blockIdx.x)];
     const int cta = blockIdx.x - it.v_cta0;
     switch (it.S) {

@@ -304,12 +304,12 @@ __device__ __forceinline__ void k1_epilogue(const CgArgs &a) {
     }
     if (e < S) {
         st->active[e] = act;
-        st->updx[e] = 0;  // consumed by the previous K3
+        st->updx[e] = act;  // this iteration's K3 updates x of every member still active here
     }
     const int ac = __popc(__ballot_sync(FULL, act));
     if (e == 0) {
         st->spmv_real += 1;
-        st->updx_any = 0;
+        st->updx_any = ac;
         st->active_count = ac;
     }
     __threadfence();
@@ -639,18 +639,26 @@ __device__ __forceinline__ void k2_body(const CgArgs &a, int cta,
     if (e < S) {
         if (a.coupled || ux) st->rho[e] = rn;
         st->iters[e] = it;
-        st->updx[e] = ux;
         st->active[e] = act;
     }
-    const int ac = __popc(__ballot_sync(FULL, act)), uany = __popc(__ballot_sync(FULL, ux));
-    if (e == 0) {
-        st->active_count = ac;
-        st->updx_any = uany;
-    }
+    // the x-update flags of this iteration were set by K1's epilogue (K3 may
+    // read them while this kernel is still running)
+    const int ac = __popc(__ballot_sync(FULL, act));
+    if (e == 0) st->active_count = ac;
     __threadfence();
 }
 
 // ------------------------------------------------------------------ K3
+// griddepcontrol: the dependent grid may launch (K2), and wait for the
+// prerequisite grid's completion and memory (K3); both are no-ops for a
+// launch without a programmatic dependency
+__device__ __forceinline__ void pdl_launch_dependents() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
+// K3: x += alpha p for the members K1 left active (the flags and alpha are
+// K1's, so this part may run while K2 still runs, when K3 is launched with a
+// programmatic dependency on K2), then, after K2 has completed, p = r + beta p
+// for the members K2 left active.
 template <int S, int MODE, int TH>
 __device__ __forceinline__ void k3_body(const CgArgs &a, int cta) {
     using VM = VecMap<S, TH>;
@@ -660,40 +668,64 @@ __device__ __forceinline__ void k3_body(const CgArgs &a, int cta) {
     const int cip = threadIdx.x / VM::CHUNK_T, lt = threadIdx.x % VM::CHUNK_T;
     const int r = lt / VG, g = lt % VG;
     const int m = (S == 1) ? 0 : 2 * g;
-    const bool ux0 = st->updx[m], ac0 = st->active[m];
+    const bool ux0 = st->updx[m];
     const bool ux1 = (S == 1) ? false : (bool)st->updx[m + 1];
-    const bool ac1 = (S == 1) ? false : (bool)st->active[m + 1];
-    const double al0 = st->alpha[m], be0 = st->beta[m];
-    const double al1 = (S == 1) ? 0.0 : st->alpha[m + 1], be1 = (S == 1) ? 0.0 : st->beta[m + 1];
+    const double al0 = st->alpha[m];
+    const double al1 = (S == 1) ? 0.0 : st->alpha[m + 1];
     const int64_t first_chunk = (int64_t)cta * VM::CPC;
-#pragma unroll 2
-    for (int pass = 0; pass < VM::PASSES; ++pass) {
-        const int64_t R = (first_chunk + pass * VM::CPP + cip) * 32 + r;
-        if (R >= a.n) continue;
-        if constexpr (S == 1) {
-            const double pv = a.p[R];
-            if (ux0) a.x[R] = fma(al0, pv, a.x[R]);
-            if (ac0) {
-                const double pn = fma(be0, pv, a.r[R]);
-                a.p[R] = pn;
-                if (MODE != 0) store_split1(a.pdf, R, pn, &st->df_bad_any);
+    if constexpr (S == 1) {
+        double pv[VM::PASSES];
+#pragma unroll
+        for (int pass = 0; pass < VM::PASSES; ++pass) {
+            const int64_t R = (first_chunk + pass * VM::CPP + cip) * 32 + r;
+            pv[pass] = 0.0;
+            if (R < a.n) {
+                pv[pass] = a.p[R];
+                if (ux0) a.x[R] = fma(al0, pv[pass], a.x[R]);
             }
-        } else {
-            const double2 pv = reinterpret_cast<const double2 *>(a.p)[R * VG + g];
-            if (ux0 || ux1) {
-                double2 xv = reinterpret_cast<const double2 *>(a.x)[R * VG + g];
-                if (ux0) xv.x = fma(al0, pv.x, xv.x);
-                if (ux1) xv.y = fma(al1, pv.y, xv.y);
-                reinterpret_cast<double2 *>(a.x)[R * VG + g] = xv;
+        }
+        pdl_wait();
+        const bool ac0 = ld_cg(&st->active[m]) != 0;
+        const double be0 = ld_cg(&st->beta[m]);
+        if (!ac0) return;
+#pragma unroll
+        for (int pass = 0; pass < VM::PASSES; ++pass) {
+            const int64_t R = (first_chunk + pass * VM::CPP + cip) * 32 + r;
+            if (R >= a.n) continue;
+            const double pn = fma(be0, pv[pass], a.r[R]);
+            a.p[R] = pn;
+            if (MODE != 0) store_split1(a.pdf, R, pn, &st->df_bad_any);
+        }
+    } else {
+        double2 pv[VM::PASSES];
+#pragma unroll
+        for (int pass = 0; pass < VM::PASSES; ++pass) {
+            const int64_t R = (first_chunk + pass * VM::CPP + cip) * 32 + r;
+            pv[pass] = make_double2(0.0, 0.0);
+            if (R < a.n) {
+                pv[pass] = reinterpret_cast<const double2 *>(a.p)[R * VG + g];
+                if (ux0 || ux1) {
+                    double2 xv = reinterpret_cast<const double2 *>(a.x)[R * VG + g];
+                    if (ux0) xv.x = fma(al0, pv[pass].x, xv.x);
+                    if (ux1) xv.y = fma(al1, pv[pass].y, xv.y);
+                    reinterpret_cast<double2 *>(a.x)[R * VG + g] = xv;
+                }
             }
-            if (ac0 || ac1) {
-                const double2 rv = reinterpret_cast<const double2 *>(a.r)[R * VG + g];
-                double2 pn = pv;
-                if (ac0) pn.x = fma(be0, pv.x, rv.x);
-                if (ac1) pn.y = fma(be1, pv.y, rv.y);
-                reinterpret_cast<double2 *>(a.p)[R * VG + g] = pn;
-                if (MODE != 0) store_split(a.pdf, R * S + m, pn.x, pn.y, &st->df_bad_any);
-            }
+        }
+        pdl_wait();
+        const bool ac0 = ld_cg(&st->active[m]) != 0, ac1 = ld_cg(&st->active[m + 1]) != 0;
+        const double be0 = ld_cg(&st->beta[m]), be1 = ld_cg(&st->beta[m + 1]);
+        if (!(ac0 || ac1)) return;
+#pragma unroll
+        for (int pass = 0; pass < VM::PASSES; ++pass) {
+            const int64_t R = (first_chunk + pass * VM::CPP + cip) * 32 + r;
+            if (R >= a.n) continue;
+            const double2 rv = reinterpret_cast<const double2 *>(a.r)[R * VG + g];
+            double2 pn = pv[pass];
+            if (ac0) pn.x = fma(be0, pv[pass].x, rv.x);
+            if (ac1) pn.y = fma(be1, pv[pass].y, rv.y);
+            reinterpret_cast<double2 *>(a.p)[R * VG + g] = pn;
+            if (MODE != 0) store_split(a.pdf, R * S + m, pn.x, pn.y, &st->df_bad_any);
         }
     }
 }
@@ -712,12 +744,13 @@ struct K2Launch {
 
 template <int S, int MPT>
 __global__ void __launch_bounds__(K2Launch<S, MPT>::TH, K2Launch<S, MPT>::MIN_BLOCKS) cg_resid_kernel(CgArgs a) {
+    pdl_launch_dependents();   // K3 may start its x update on the SMs this grid leaves idle
     __shared__ double sm[K2Launch<S, MPT>::Map::CPC][32][S + 1];   // per-row products of every chunk
     k2_body<S, K2Launch<S, MPT>::TH, MPT>(a, blockIdx.x, sm);
 }
 
 template <int S, int MODE>
-__global__ void __launch_bounds__(VecMap<S>::THREADS) cg_update_kernel(CgArgs a) {
+__global__ void __launch_bounds__(VecMap<S>::THREADS, 1536 / VecMap<S>::THREADS) cg_update_kernel(CgArgs a) {
     k3_body<S, MODE, VecMap<S>::THREADS>(a, blockIdx.x);
 }
 
