@@ -174,9 +174,9 @@ struct CgKernels {
     }
     static void spmv(const CgArgs &a, int nsub, cudaStream_t st) { k1_launch<S, MODE>(a, nsub, st); }
     static void resid(const CgArgs &a, cudaStream_t st) {
-        using L = K2Launch<S, 2>;
-        const unsigned grid = (unsigned)((a.t1.count[1] + L::Map::CPC - 1) / L::Map::CPC);
-        cg_resid_kernel<S, 2><<<grid, L::TH, 0, st>>>(a);
+        using L = K2Launch<S>;
+        const unsigned grid = (unsigned)((a.t1.count[1] + L::CPC - 1) / L::CPC);
+        cg_resid_kernel<S><<<grid, L::TH, 0, st>>>(a);
     }
     // K3 with a programmatic dependency on K2 (ENS_CG_PDL, default on): its
     // first CTAs start their x update as K2's last wave leaves SMs idle
@@ -435,7 +435,11 @@ constexpr size_t batch_k1_smem() {
                 sizeof(typename BatchK1<32, TH>::Smem));
 }
 template <int S>
-constexpr size_t batch_k2_smem() { return sizeof(double) * VecMap<S, kBatchThreads>::CPC * 32 * (S + 1); }
+struct BatchK2 {   // the batched K2's chunks per CTA: a (chunk, slice) unit per S threads, one level-2 group at most
+    static constexpr int CPC = (kBatchThreads / (kK2Slices * S) < 32) ? kBatchThreads / (kK2Slices * S) : 32;
+};
+template <int S>
+constexpr size_t batch_k2_smem() { return sizeof(float2) * BatchK2<S>::CPC * kK2Slices * S; }
 constexpr size_t kBatchK2Smem = cmax(cmax(cmax(batch_k2_smem<1>(), batch_k2_smem<4>()),
                                           cmax(batch_k2_smem<8>(), batch_k2_smem<16>())),
                                      batch_k2_smem<32>());
@@ -443,13 +447,14 @@ constexpr size_t kBatchK2Smem = cmax(cmax(cmax(batch_k2_smem<1>(), batch_k2_smem
 struct BItem {
     CgArgs a;
     int S;
-    int k1_cta0, v_cta0;
+    int k1_cta0, v_cta0, r_cta0;
 };
 
 struct BatchTables {
     const BItem *items;
     const int *k1_map;  // CTA -> item for K1 launches
-    const int *v_map;   // CTA -> item for K2 / K3 launches
+    const int *v_map;   // CTA -> item for K3 launches
+    const int *r_map;   // CTA -> item for K2 launches
 };
 
 template <int MODE, int TH>
@@ -471,15 +476,15 @@ __global__ void __launch_bounds__(TH, 1024 / TH) cg_spmv_batched(BatchTables bt)
 
 template <int S>
 __device__ __forceinline__ void k2_batched_s(const CgArgs &a, int cta, unsigned char *raw) {
-    k2_body<S, kBatchThreads, 2, true>(a, cta, reinterpret_cast<double(*)[32][S + 1]>(raw));
+    k2_body<S, kBatchThreads, BatchK2<S>::CPC, true>(a, cta, reinterpret_cast<float2(*)[kK2Slices][S]>(raw));
 }
 
-// 32 registers, 4 CTAs per SM (with 64 registers and 2 CTAs per SM the 2048-sample
-// batch of 16^3-64^3 meshes ran at 814 instead of 906 sample-solves/s)
-__global__ void __launch_bounds__(kBatchThreads, 4) cg_resid_batched(BatchTables bt) {
+// 64 registers (a slice's 16 loads in flight per thread), 2 CTAs per SM, as
+// the single-ensemble K2
+__global__ void __launch_bounds__(kBatchThreads, 2) cg_resid_batched(BatchTables bt) {
     __shared__ __align__(16) unsigned char raw[kBatchK2Smem];
-    const BItem &it = bt.items[__ldg(bt.v_map + blockIdx.x)];
-    const int cta = blockIdx.x - it.v_cta0;
+    const BItem &it = bt.items[__ldg(bt.r_map + blockIdx.x)];
+    const int cta = blockIdx.x - it.r_cta0;
     switch (it.S) {
         case 1: k2_batched_s<1>(it.a, cta, raw); break;
         case 4: k2_batched_s<4>(it.a, cta, raw); break;
@@ -579,9 +584,21 @@ static int64_t batch_v_ctas(int S, int64_t chunks) {
     return (chunks + cpc - 1) / cpc;
 }
 
+static int64_t batch_r_ctas(int S, int64_t chunks) {
+    int cpc = 0;
+    switch (S) {
+        case 1: cpc = BatchK2<1>::CPC; break;
+        case 4: cpc = BatchK2<4>::CPC; break;
+        case 8: cpc = BatchK2<8>::CPC; break;
+        case 16: cpc = BatchK2<16>::CPC; break;
+        default: cpc = BatchK2<32>::CPC; break;
+    }
+    return (chunks + cpc - 1) / cpc;
+}
+
 struct BatchPlan {
     size_t head;           // items + poll words + CTA maps
-    int64_t k1_total, v_total;
+    int64_t k1_total, v_total, r_total;
     size_t total;
 };
 
@@ -591,9 +608,10 @@ static BatchPlan batch_plan(int n_items, const ens_batch_item *items) {
         const int64_t chunks = ((int64_t)items[i].graph.num_rows + 31) / 32;
         p.k1_total += batch_k1_ctas(items[i].s, chunks);
         p.v_total += batch_v_ctas(items[i].s, chunks);
+        p.r_total += batch_r_ctas(items[i].s, chunks);
     }
     p.head = align256(sizeof(BItem) * n_items) + 256 + align256(sizeof(int) * (size_t)p.k1_total) +
-             align256(sizeof(int) * (size_t)p.v_total);
+             align256(sizeof(int) * (size_t)p.v_total) + align256(sizeof(int) * (size_t)p.r_total);
     p.total = p.head;
     for (int i = 0; i < n_items; ++i) p.total += cg_bytes(items[i].graph.num_rows, items[i].s);
     return p;
@@ -620,10 +638,11 @@ static int batched_run(int n_items, const ens_batch_item *items, double tol, int
     int *d_poll = reinterpret_cast<int *>(w + align256(sizeof(BItem) * n_items));
     int *d_k1map = reinterpret_cast<int *>(w + align256(sizeof(BItem) * n_items) + 256);
     int *d_vmap = d_k1map + align256(sizeof(int) * (size_t)plan.k1_total) / sizeof(int);
+    int *d_rmap = d_vmap + align256(sizeof(int) * (size_t)plan.v_total) / sizeof(int);
     char *wi = w + plan.head;
     std::vector<BItem> h(n_items);
-    std::vector<int> k1map((size_t)plan.k1_total), vmap((size_t)plan.v_total);
-    int64_t k1c = 0, vc = 0;
+    std::vector<int> k1map((size_t)plan.k1_total), vmap((size_t)plan.v_total), rmap((size_t)plan.r_total);
+    int64_t k1c = 0, vc = 0, rcn = 0;
     int rc;
     for (int i = 0; i < n_items; ++i) {
         const ens_batch_item &it = items[i];
@@ -637,11 +656,14 @@ static int batched_run(int n_items, const ens_batch_item *items, double tol, int
         wi += cg_bytes(it.graph.num_rows, it.s);
         h[i].S = it.s;
         const int64_t chunks = h[i].a.t1.count[1];
-        const int64_t nk = batch_k1_ctas(it.s, chunks, th), nv = batch_v_ctas(it.s, chunks);
+        const int64_t nk = batch_k1_ctas(it.s, chunks, th), nv = batch_v_ctas(it.s, chunks),
+                      nr = batch_r_ctas(it.s, chunks);
         h[i].k1_cta0 = (int)k1c;
         h[i].v_cta0 = (int)vc;
+        h[i].r_cta0 = (int)rcn;
         for (int64_t c = 0; c < nk; ++c) k1map[k1c++] = i;
         for (int64_t c = 0; c < nv; ++c) vmap[vc++] = i;
+        for (int64_t c = 0; c < nr; ++c) rmap[rcn++] = i;
         if ((rc = dot_tree_clear(h[i].a.t1, st))) return rc;
         if ((rc = dot_tree_clear(h[i].a.t2, st))) return rc;
         ENS_CUDA_TRY(cudaMemsetAsync(h[i].a.st, 0, sizeof(CgState), st));
@@ -649,11 +671,12 @@ static int batched_run(int n_items, const ens_batch_item *items, double tol, int
     ENS_CUDA_TRY(cudaMemcpyAsync(d_items, h.data(), sizeof(BItem) * n_items, cudaMemcpyHostToDevice, st));
     ENS_CUDA_TRY(cudaMemcpyAsync(d_k1map, k1map.data(), sizeof(int) * k1map.size(), cudaMemcpyHostToDevice, st));
     ENS_CUDA_TRY(cudaMemcpyAsync(d_vmap, vmap.data(), sizeof(int) * vmap.size(), cudaMemcpyHostToDevice, st));
+    ENS_CUDA_TRY(cudaMemcpyAsync(d_rmap, rmap.data(), sizeof(int) * rmap.size(), cudaMemcpyHostToDevice, st));
     int launches = 0, polls = 0;
     for (int i = 0; i < n_items; ++i) { launch_single<MODE>(0, h[i].S, h[i].a, st); launches += 2; }
     ENS_LAUNCH_CHECK("batched cg init");
-    const BatchTables bt{d_items, d_k1map, d_vmap};
-    const unsigned g1 = (unsigned)k1c, gv = (unsigned)plan.v_total;
+    const BatchTables bt{d_items, d_k1map, d_vmap, d_rmap};
+    const unsigned g1 = (unsigned)k1c, gv = (unsigned)plan.v_total, gr = (unsigned)plan.r_total;
     const bool timing = (flags & ENS_CG_TIME_SPMV) != 0;
     const bool use_graph = (flags & ENS_CG_GRAPH) != 0 && !timing;
     std::vector<cudaEvent_t> ev;
@@ -671,7 +694,7 @@ static int batched_run(int n_items, const ens_batch_item *items, double tol, int
         if (th == 1024) launch_k1_batched<MODE, 1024>(g1, bt, s2);
         else launch_k1_batched<MODE, 512>(g1, bt, s2);
         if (timing) cudaEventRecord(ev[2 * i + 1], s2);
-        cg_resid_batched<<<gv, kBatchThreads, 0, s2>>>(bt);
+        cg_resid_batched<<<gr, kBatchThreads, 0, s2>>>(bt);
         cg_update_batched<MODE><<<gv, kBatchThreads, 0, s2>>>(bt);
     };
     cudaGraph_t graph = nullptr;

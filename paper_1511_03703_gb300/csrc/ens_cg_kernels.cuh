@@ -476,25 +476,6 @@ __device__ __forceinline__ float2 df_square(double v) {
     return make_float2(p, e);
 }
 
-// FP64 r.r of one (chunk, member) column whose float-pair sum was marked
-// (a value outside the float-pair range): the 32 rows' r, squared in FP64 and
-// combined by the same halving tree (v[i] += v[i + h], h = 16..1).  Called by
-// one thread after a barrier that orders the CTA's r stores before it.
-static __device__ __noinline__ double k2_chunk_rr_fp64(const double *r, int64_t n, int64_t chunk, int e, int S) {
-    double v[32];
-#pragma unroll
-    for (int i = 0; i < 32; ++i) {
-        const int64_t R = chunk * 32 + i;
-        const double x = (R < n) ? r[R * S + e] : 0.0;
-        v[i] = x * x;
-    }
-#pragma unroll
-    for (int h = 16; h >= 1; h >>= 1)
-#pragma unroll
-        for (int i = 0; i < h; ++i) v[i] += v[i + h];
-    return v[0];
-}
-
 // (a.x + a.y) + (b.x + b.y) as a float pair: TwoSum of the leading parts,
 // the trailing parts and the rounding error summed
 __device__ __forceinline__ float2 df_add(float2 a, float2 b) {
@@ -503,114 +484,10 @@ __device__ __forceinline__ float2 df_add(float2 a, float2 b) {
     return make_float2(s, __fadd_rn(__fadd_rn(a.y, b.y), t));
 }
 
-// K2's mapping: MPT members per thread (16-byte loads of r and q, MPT/2 of
-// each per row), S/MPT threads per row; a CTA of TH threads owns CPC chunks,
-// CPP of them per pass.  With more members per thread every load of the CTA's
-// chunks can be in flight before its first store (one pass).
-template <int S, int TH, int MPT>
-struct K2Map {
-    static constexpr int M = (S == 1) ? 1 : (MPT < S ? MPT : S);   // members per thread
-    static constexpr int VG = S / M;                                // threads per row
-    static constexpr int CHUNK_T = 32 * VG;
-    static constexpr int THREADS = TH;
-    static constexpr int CPP = THREADS / CHUNK_T;
-    static constexpr int CPC0 = (S >= 16) ? 4 : 8;
-    static constexpr int CPC = (CPC0 > CPP) ? CPC0 : CPP;
-    static constexpr int PASSES = CPC / CPP;
-};
-
-// EXIT_FIRST: as for k1_body (the batched kernel tests for a stopped ensemble
-// before prefetching its r and q blocks)
-template <int S, int TH, int MPT = 2, bool EXIT_FIRST = false>
-__device__ __forceinline__ void k2_body(const CgArgs &a, int cta,
-                                        double (*sm)[32][S + 1] /* [CPC][32][S+1] */) {
-    using VM = K2Map<S, TH, MPT>;
-    constexpr int VG = VM::VG, MM = VM::M;
-    const int64_t first_chunk = (int64_t)cta * VM::CPC;
-    if (EXIT_FIRST && ld_cg(&a.st->active_count) == 0) return;
-    if (a.k2_pf && threadIdx.x == 0) {   // the passes below then read r and q from L2
-        const uint64_t b0 = (uint64_t)first_chunk * 32 * S * 8u;
-        const uint64_t b1 = (uint64_t)min((first_chunk + VM::CPC) * 32, (int64_t)a.n) * S * 8u;
-        l2_prefetch_span(a.r, b0, b1);
-        l2_prefetch_span(a.q, b0, b1);
-    }
-    if (ld_cg(&a.st->active_count) == 0) return;
-    const int cip = threadIdx.x / VM::CHUNK_T, lt = threadIdx.x % VM::CHUNK_T;
-    const int r = lt / VG, g = lt % VG;
-    const CgState *cs = a.st;
-    const int m = g * MM;   // first member of the thread
-    bool act_m[MM];
-    double al[MM];
-#pragma unroll
-    for (int k = 0; k < MM; ++k) {
-        act_m[k] = cs->active[m + k];
-        al[k] = cs->alpha[m + k];
-    }
-    // r.r: squares and the chunk's 32-row tree in double-float on the FP32
-    // pipe (the FP64 pipe keeps only the r update); the chunk sums enter the
-    // FP64 dot tree above the chunk
-    float2(*sf)[32][S + 1] = reinterpret_cast<float2(*)[32][S + 1]>(sm);
-#pragma unroll
-    for (int pass = 0; pass < VM::PASSES; ++pass) {
-        const int c = pass * VM::CPP + cip;
-        const int64_t R = (first_chunk + c) * 32 + r;
-        if constexpr (S == 1) {
-            float2 v0 = make_float2(0.f, 0.f);
-            if (R < a.n) {
-                double rv = a.r[R];
-                if (act_m[0]) { rv = fma(-al[0], a.q[R], rv); a.r[R] = rv; }
-                v0 = df_square(rv);
-            }
-            sf[c][r][0] = v0;
-        } else {
-            constexpr int H = MM / 2;
-            double2 rv[H], qv[H];
-            if (R < a.n) {
-                const double2 *r2 = reinterpret_cast<const double2 *>(a.r) + (R * S + m) / 2;
-                const double2 *q2 = reinterpret_cast<const double2 *>(a.q) + (R * S + m) / 2;
-#pragma unroll
-                for (int h = 0; h < H; ++h) { rv[h] = r2[h]; qv[h] = q2[h]; }
-#pragma unroll
-                for (int h = 0; h < H; ++h) {
-                    if (act_m[2 * h]) rv[h].x = fma(-al[2 * h], qv[h].x, rv[h].x);
-                    if (act_m[2 * h + 1]) rv[h].y = fma(-al[2 * h + 1], qv[h].y, rv[h].y);
-                    if (act_m[2 * h] || act_m[2 * h + 1]) reinterpret_cast<double2 *>(a.r)[(R * S + m) / 2 + h] = rv[h];
-                }
-            } else {
-#pragma unroll
-                for (int h = 0; h < H; ++h) rv[h] = make_double2(0.0, 0.0);
-            }
-#pragma unroll
-            for (int h = 0; h < H; ++h) {
-                sf[c][r][m + 2 * h] = df_square(rv[h].x);
-                sf[c][r][m + 2 * h + 1] = df_square(rv[h].y);
-            }
-        }
-    }
-    __syncthreads();
-    // halving tree over the 32 rows of every chunk, all members packed (every
-    // thread of the CTA busy at each level)
-#pragma unroll
-    for (int h = 16; h >= 1; h >>= 1) {
-        for (int it = threadIdx.x; it < VM::CPC * h * S; it += VM::THREADS) {
-            const int c = it / (h * S), rem = it % (h * S), i = rem / S, e = rem % S;
-            sf[c][i][e] = df_add(sf[c][i][e], sf[c][i + h][e]);
-        }
-        __syncthreads();
-    }
-    for (int it = threadIdx.x; it < VM::CPC * S; it += VM::THREADS) {
-        const int c = it / S, e = it % S;
-        const int64_t ch = first_chunk + c;
-        if (ch < a.t1.count[1]) {
-            const float2 t = sf[c][0][e];
-            a.t1.buf[1][ch * S + e] = (t.x == t.x) ? f2d_exact(t.x) + f2d_exact(t.y)
-                                                   : k2_chunk_rr_fp64(a.r, a.n, ch, e, S);
-        }
-    }
-    const int nitems = (int)min((int64_t)VM::CPC, a.t1.count[1] - first_chunk);
-    if (!dot_tree_propagate(a.t1, first_chunk, nitems)) return;
-    if (threadIdx.x >= 32) return;
-    // epilogue: one lane per member
+// K2's epilogue, in the CTA that produced the top of r.r's tree: one lane
+// per member (warp 0) sets the stopping flags and beta
+template <int S>
+__device__ __forceinline__ void k2_epilogue(const CgArgs &a) {
     const unsigned FULL = 0xffffffffu;
     const int e = threadIdx.x;
     const double *top = a.t1.buf[a.t1.levels];
@@ -646,6 +523,111 @@ __device__ __forceinline__ void k2_body(const CgArgs &a, int cta,
     const int ac = __popc(__ballot_sync(FULL, act));
     if (e == 0) st->active_count = ac;
     __threadfence();
+}
+
+
+// K2's order for a chunk's r.r (the level-1 items of its dot tree): the 32
+// rows in 4 slices of 8 consecutive rows, each slice summed row by row in
+// float pairs, then the slices combined as (q0 + q2) + (q1 + q3).  It depends
+// only on the row index, so a member's r.r is bitwise the same at every s
+// and in every launch shape.  Mapping: a (chunk, slice) unit on S threads,
+// one member each (r and q loaded 8 rows at a time, all 16 loads in flight
+// before the first store); a CTA of TH threads owns CPC chunks.
+constexpr int kK2Slices = 4;
+constexpr int kK2SliceRows = 32 / kK2Slices;
+
+template <int S, int TH, int CPC>
+struct K2Map {
+    static_assert(TH % S == 0, "K2: whole units per CTA");
+    static constexpr int UNITS = CPC * kK2Slices;   // (chunk, slice) units of a CTA
+    static constexpr int UPP = TH / S;              // units per pass
+};
+
+// FP64 r.r of one (chunk, member) column whose float-pair sum was marked (a
+// value outside the float-pair range): the same slices and combination
+// order in FP64.  Called by one thread after a barrier that orders the CTA's
+// r stores before it.
+static __device__ __noinline__ double k2_chunk_rr_fp64(const double *r, int64_t n, int64_t chunk, int e, int S) {
+    double q[kK2Slices];
+    for (int k = 0; k < kK2Slices; ++k) {
+        double acc = 0.0;
+        for (int i = 0; i < kK2SliceRows; ++i) {
+            const int64_t R = chunk * 32 + k * kK2SliceRows + i;
+            const double x = (R < n) ? r[R * S + e] : 0.0;
+            acc = (i == 0) ? x * x : acc + x * x;
+        }
+        q[k] = acc;
+    }
+    return (q[0] + q[2]) + (q[1] + q[3]);
+}
+
+// EXIT_FIRST: as for k1_body (the batched kernel tests for a stopped ensemble
+// before prefetching its r and q blocks).  LB: rows of r and q loaded before
+// the first of them is updated (8: a whole slice).  sl: CPC * 4 * S float
+// pairs of shared memory.
+template <int S, int TH, int CPC, bool EXIT_FIRST = false, int LB = kK2SliceRows>
+__device__ __forceinline__ void k2_body(const CgArgs &a, int cta, float2 (*sl)[kK2Slices][S]) {
+    using VM = K2Map<S, TH, CPC>;
+    const int64_t first_chunk = (int64_t)cta * CPC;
+    if (EXIT_FIRST && ld_cg(&a.st->active_count) == 0) return;
+    if (a.k2_pf && threadIdx.x == 0) {   // the loads below then read r and q from L2
+        const uint64_t b0 = (uint64_t)first_chunk * 32 * S * 8u;
+        const uint64_t b1 = (uint64_t)min((first_chunk + CPC) * 32, (int64_t)a.n) * S * 8u;
+        l2_prefetch_span(a.r, b0, b1);
+        l2_prefetch_span(a.q, b0, b1);
+    }
+    if (ld_cg(&a.st->active_count) == 0) return;
+    const CgState *cs = a.st;
+    const int e = threadIdx.x % S;
+    const bool act = cs->active[e];
+    const double al = cs->alpha[e];
+    double *__restrict__ rp = a.r;
+    const double *__restrict__ qp = a.q;
+    // r -= alpha q (FP64 FMA, the only FP64-pipe work), then the squares and
+    // the slice sums as float pairs on the FP32 pipe
+#pragma unroll 1
+    for (int u = threadIdx.x / S; u < VM::UNITS; u += VM::UPP) {
+        const int c = u / kK2Slices, k = u % kK2Slices;
+        const int64_t R0 = (first_chunk + c) * 32 + k * kK2SliceRows;
+        float2 acc = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int i0 = 0; i0 < kK2SliceRows; i0 += LB) {
+            double rv[LB], qv[LB];
+#pragma unroll
+            for (int i = 0; i < LB; ++i) {
+                rv[i] = 0.0;
+                qv[i] = 0.0;
+                if (R0 + i0 + i < a.n) {
+                    rv[i] = rp[(R0 + i0 + i) * S + e];
+                    qv[i] = qp[(R0 + i0 + i) * S + e];
+                }
+            }
+#pragma unroll
+            for (int i = 0; i < LB; ++i) {
+                if (act && R0 + i0 + i < a.n) {
+                    rv[i] = fma(-al, qv[i], rv[i]);
+                    rp[(R0 + i0 + i) * S + e] = rv[i];
+                }
+                const float2 sq = df_square(rv[i]);
+                acc = (i0 + i == 0) ? sq : df_add(acc, sq);
+            }
+        }
+        sl[c][k][e] = acc;
+    }
+    __syncthreads();
+    for (int it = threadIdx.x; it < CPC * S; it += TH) {
+        const int c = it / S, m = it % S;
+        const int64_t ch = first_chunk + c;
+        if (ch < a.t1.count[1]) {
+            const float2 t = df_add(df_add(sl[c][0][m], sl[c][2][m]), df_add(sl[c][1][m], sl[c][3][m]));
+            a.t1.buf[1][ch * S + m] = (t.x == t.x) ? f2d_exact(t.x) + f2d_exact(t.y)
+                                                   : k2_chunk_rr_fp64(a.r, a.n, ch, m, S);
+        }
+    }
+    const int nitems = (int)min((int64_t)CPC, a.t1.count[1] - first_chunk);
+    if (!dot_tree_propagate(a.t1, first_chunk, nitems)) return;
+    if (threadIdx.x >= 32) return;
+    k2_epilogue<S>(a);
 }
 
 // ------------------------------------------------------------------ K3
@@ -730,23 +712,27 @@ __device__ __forceinline__ void k3_body(const CgArgs &a, int cta) {
     }
 }
 
-// MPT members per thread; CTAs of 512 threads (2 per SM, 64 registers) when
-// a thread holds 8 members' r and q, else VecMap's CTA (3 per SM at s = 32).
-// The library launches MPT = 2: on the 64^3 mesh, s = 32, K2 took 52.6 us with
-// 2 members per thread, 57.4 us with 4 and 76.3 us with 8 (all loads of a CTA
-// in flight at once, but fewer CTAs per SM).
-template <int S, int MPT>
+// K2's launch: CTAs of TH threads, a (chunk, slice) unit on S threads, so a
+// CTA owns TH / (4 S) chunks (at most 32: one level-2 group of the dot tree);
+// 3 CTAs per SM (40 registers), a slice's rows loaded 4 at a time.  At 64^3,
+// s = 32 a CG iteration took 0.4739 ms so, 0.4788 ms with 2 CTAs per SM and
+// 8 rows at a time (64 registers), 0.4781 ms with CTAs of 256 threads at 4
+// per SM, and 0.4836 ms with the earlier K2 (two members per thread and a
+// shared-memory halving tree over each chunk's 32 rows).
+template <int S>
 struct K2Launch {
-    static constexpr int TH = (MPT >= 8) ? 512 : VecMap<S>::THREADS;
-    static constexpr int MIN_BLOCKS = (MPT >= 8) ? 2 : 1536 / VecMap<S>::THREADS;
-    using Map = K2Map<S, TH, MPT>;
+    static constexpr int TH = (S == 1) ? 128 : 512;
+    static constexpr int CPC = TH / (kK2Slices * S);
+    static constexpr int MIN_BLOCKS = 3;
+    static constexpr int LB = 4;
+    static_assert(CPC >= 1 && CPC <= 32 && 32 % CPC == 0, "K2: a CTA's chunks lie in one level-2 group");
 };
 
-template <int S, int MPT>
-__global__ void __launch_bounds__(K2Launch<S, MPT>::TH, K2Launch<S, MPT>::MIN_BLOCKS) cg_resid_kernel(CgArgs a) {
+template <int S>
+__global__ void __launch_bounds__(K2Launch<S>::TH, K2Launch<S>::MIN_BLOCKS) cg_resid_kernel(CgArgs a) {
     pdl_launch_dependents();   // K3 may start its x update on the SMs this grid leaves idle
-    __shared__ double sm[K2Launch<S, MPT>::Map::CPC][32][S + 1];   // per-row products of every chunk
-    k2_body<S, K2Launch<S, MPT>::TH, MPT>(a, blockIdx.x, sm);
+    __shared__ float2 sl[K2Launch<S>::CPC][kK2Slices][S];   // slice sums of every chunk
+    k2_body<S, K2Launch<S>::TH, K2Launch<S>::CPC, false, K2Launch<S>::LB>(a, blockIdx.x, sl);
 }
 
 template <int S, int MODE>
