@@ -102,6 +102,15 @@ __device__ __forceinline__ uint16_t ld_stream_u16(const void *p) {
     asm volatile("ld.global.cs.u16 %0, [%1];" : "=h"(v) : "l"(p));
     return v;
 }
+// the same load with the default cache policy (allocates in L1 and L2 at
+// normal priority), for a line that the same warp reads again a few
+// instructions later
+__device__ __forceinline__ float4 ld_normal(const float4 *p) {
+    float4 v;
+    asm volatile("ld.global.v4.f32 {%0, %1, %2, %3}, [%4];"
+                 : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w) : "l"(p));
+    return v;
+}
 // L2-coherent load that bypasses L1 (reads data written by other CTAs of the
 // same kernel after a fence)
 __device__ __forceinline__ double ld_cg(const double *p) {

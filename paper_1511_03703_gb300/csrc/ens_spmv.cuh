@@ -563,6 +563,20 @@ __device__ __noinline__ double2 row_spmv2_df_redo(CA colf, int rs, int re, const
     return row_spmv2_df<S, XS, CA>(colf, rs, re, vals, x, g);
 }
 
+// Value loads of the pre-split SpMV (16 bytes: two members' float pairs of
+// one entry).  From s = 16 the threads of a row read whole 128-byte lines at
+// each entry, once: streaming loads (evict-first).  Below s = 16 a line holds
+// 16 / s consecutive entries of a row, which the same warp reads over as many
+// steps of its row loop: normal loads, so that the line stays in L1 between
+// them.  64^3 mesh: s = 4 90.9 -> 76.2 us, s = 8 140.9 -> 118.1 us per launch;
+// at s = 32 normal loads took 408 us against 351 us.
+template <int S>
+__device__ __forceinline__ float4 ld_vdf4(const float2 *vdf, int64_t i) {
+    const float4 *p = reinterpret_cast<const float4 *>(vdf + i);
+    if constexpr (S >= 16) return ld_stream(p);
+    else return ld_normal(p);
+}
+
 // XS: the source of the split x (XPre: the CG's split vectors; XSplit: FP64 x
 // split on the fly with the same rounding, as in ens_spmv_df)
 template <int S, typename XS, typename CA>
@@ -575,10 +589,10 @@ __device__ __forceinline__ double2 row_spmv2_dfv(CA colf, int rs, int re, const 
     int j = rs;
     for (; j + 4 <= re; j += 4) {
         const int c0 = colf(j), c1 = colf(j + 1), c2 = colf(j + 2), c3 = colf(j + 3);
-        const float4 v0 = ld_stream(reinterpret_cast<const float4 *>(vdf + (int64_t)j * S + m));
-        const float4 v1 = ld_stream(reinterpret_cast<const float4 *>(vdf + (int64_t)(j + 1) * S + m));
-        const float4 v2 = ld_stream(reinterpret_cast<const float4 *>(vdf + (int64_t)(j + 2) * S + m));
-        const float4 v3 = ld_stream(reinterpret_cast<const float4 *>(vdf + (int64_t)(j + 3) * S + m));
+        const float4 v0 = ld_vdf4<S>(vdf, (int64_t)j * S + m);
+        const float4 v1 = ld_vdf4<S>(vdf, (int64_t)(j + 1) * S + m);
+        const float4 v2 = ld_vdf4<S>(vdf, (int64_t)(j + 2) * S + m);
+        const float4 v3 = ld_vdf4<S>(vdf, (int64_t)(j + 3) * S + m);
         const float4 x0 = XS::two(x, (int64_t)c0 * S + m);
         const float4 x1 = XS::two(x, (int64_t)c1 * S + m);
         const float4 x2 = XS::two(x, (int64_t)c2 * S + m);
@@ -589,7 +603,7 @@ __device__ __forceinline__ double2 row_spmv2_dfv(CA colf, int rs, int re, const 
         df_term_pm(a1, ma, v3.x, v3.y, x3.x, x3.y); df_term_pm(b1, mb, v3.z, v3.w, x3.z, x3.w);
     }
     for (; j < re; ++j) {
-        const float4 v = ld_stream(reinterpret_cast<const float4 *>(vdf + (int64_t)j * S + m));
+        const float4 v = ld_vdf4<S>(vdf, (int64_t)j * S + m);
         const float4 xv = XS::two(x, (int64_t)colf(j) * S + m);
         if ((j - rs) & 1) { df_term_pm(a1, ma, v.x, v.y, xv.x, xv.y); df_term_pm(b1, mb, v.z, v.w, xv.z, xv.w); }
         else { df_term_pm(a0, ma, v.x, v.y, xv.x, xv.y); df_term_pm(b0, mb, v.z, v.w, xv.z, xv.w); }
