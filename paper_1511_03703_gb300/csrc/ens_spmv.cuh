@@ -867,6 +867,41 @@ __device__ __forceinline__ void chunk_tree(double (*sm)[S + 1], double v0, doubl
     __syncthreads();
 }
 
+// Level-1 step of the CG's p.q (K1), in the order of K2's r.r: the chunk's
+// per-row products in shared memory, then the 32 rows in 4 slices of 8 rows,
+// each summed row by row, and the slices combined as (q0 + q2) + (q1 + q3)
+// by two shuffles among the 4 lanes (4e .. 4e+3) that hold member e's
+// slices.  One barrier instead of the halving tree's six; the same number of
+// FP64 adds.  The chunk's threads are [ltid = 0, nthr) with nthr >= 4 S and
+// a multiple of 32; every thread of the CTA calls it (its barrier is
+// CTA-wide).  Writes t.buf[1][chunk*width + off + e] when the chunk exists;
+// TRAIL: a closing barrier (for a caller that reuses sm).
+template <int S, bool TRAIL>
+__device__ __forceinline__ void chunk_slices(double (*sm)[S + 1], double v0, double v1, int r, int g,
+                                             const DotTree &t, int64_t chunk, int off, int ltid, bool exists) {
+    if constexpr (S == 1) {
+        if (g == 0) sm[r][0] = v0;
+    } else {
+        sm[r][2 * g] = v0;
+        sm[r][2 * g + 1] = v1;
+    }
+    __syncthreads();
+    constexpr int NT = (4 * S < 32) ? 32 : 4 * S;   // whole warps take part in the shuffles
+    if (ltid < NT) {
+        const int e = ltid >> 2, k = ltid & 3;
+        double q = 0.0;
+        if (ltid < 4 * S) {
+            q = sm[8 * k][e];
+#pragma unroll
+            for (int i = 1; i < 8; ++i) q += sm[8 * k + i][e];
+        }
+        q += __shfl_xor_sync(0xffffffffu, q, 2);   // lanes k = 0, 1: q0 + q2, q1 + q3
+        q += __shfl_xor_sync(0xffffffffu, q, 1);   // lane k = 0: (q0 + q2) + (q1 + q3)
+        if (k == 0 && ltid < 4 * S && exists) t.buf[1][chunk * t.width + off + e] = q;
+    }
+    if (TRAIL) __syncthreads();
+}
+
 // Subset form of chunk_tree (halving tree): the chunk's threads are
 // [ltid = 0, nthr); all threads of the CTA call it (its barriers are
 // CTA-wide); writes only when the chunk exists.
