@@ -267,7 +267,8 @@ __device__ __forceinline__ void k1_body(const CgArgs &a, const int cta, K1Smem<S
         v0 = apv.x * pv.x;
         v1 = apv.y * pv.y;
     }
-    chunk_slices<S, false>(sh.sm[sub], v0, v1, r, g, a.t1, K1_CHUNK, 0, ltid, K1_CHUNK < a.t1.count[1]);
+    if constexpr (NSUB == 1) chunk_tree<S>(sh.sm[0], v0, v1, r, g, a.t1, K1_CHUNK, 0);
+    else chunk_tree_sub<S>(sh.sm[sub], v0, v1, r, g, a.t1, K1_CHUNK, 0, ltid, T);
     const int nitems = (NSUB == 1) ? 1 : (int)min((int64_t)NSUB, a.t1.count[1] - (int64_t)cta * NSUB);
     if (!dot_tree_propagate(a.t1, (int64_t)cta * NSUB, nitems)) return;
 #undef K1_CHUNK
@@ -317,11 +318,11 @@ __device__ __forceinline__ void k1_epilogue(const CgArgs &a) {
 // K1 with one chunk per CTA: the arithmetic of k1_body<S, MODE, 1>, written
 // out with fewer live indices so that it keeps to 40 registers (3 CTAs of 512
 // threads per SM at s = 32) with little spilling.  VEC: column staging with
-// 16-byte loads.  p.q's chunk level in the slice order (chunk_slices).
+// 16-byte loads; WARP: chunk tree by warp shuffles (see chunk_tree).
 // DEFER: the CTA writes only its chunk's p.q partials (level 1 of the tree);
 // cg_spmv_reduce_kernel, launched next, does the upper levels in the same
 // order and the epilogue, so no CTA of K1 waits on a fence and an atomic.
-template <int S, int MODE, bool VEC, bool DEFER = false>
+template <int S, int MODE, bool VEC, bool WARP, bool DEFER = false>
 __device__ __forceinline__ void k1_single(const CgArgs &a) {
     CgState *st = a.st;
     constexpr int G = RowMap<S>::G;
@@ -381,7 +382,7 @@ __device__ __forceinline__ void k1_single(const CgArgs &a) {
         v0 = ap.x * pv.x;
         v1 = ap.y * pv.y;
     }
-    chunk_slices<S, false>(sm, v0, v1, r, g, a.t1, blockIdx.x, 0, threadIdx.x, true);
+    chunk_tree<S, WARP>(sm, v0, v1, r, g, a.t1, blockIdx.x, 0);
     if (DEFER) return;
     if (!dot_tree_propagate(a.t1, blockIdx.x, 1)) return;
     if (threadIdx.x >= 32) return;
@@ -411,7 +412,7 @@ template <int S, int MODE, int NSUB>
 __global__ void __launch_bounds__(K1Launch<S, MODE, NSUB>::THREADS, K1Launch<S, MODE, NSUB>::MIN_BLOCKS)
     cg_spmv_kernel(CgArgs a) {
     if constexpr (NSUB == 1) {
-        k1_single<S, MODE, true>(a);
+        k1_single<S, MODE, true, (S == 1)>(a);
     } else {
         __shared__ K1Smem<S, NSUB> sh;
         k1_body<S, MODE, NSUB>(a, blockIdx.x, sh);
@@ -422,7 +423,7 @@ __global__ void __launch_bounds__(K1Launch<S, MODE, NSUB>::THREADS, K1Launch<S, 
 template <int S, int MODE>
 __global__ void __launch_bounds__(RowMap<S>::THREADS, K1Launch<S, MODE, 1>::MIN_BLOCKS)
     cg_spmv_partial_kernel(CgArgs a) {
-    k1_single<S, MODE, true, true>(a);
+    k1_single<S, MODE, true, (S == 1), true>(a);
 }
 
 // ... then one CTA per level-1 group: the group's reduction, the upper levels

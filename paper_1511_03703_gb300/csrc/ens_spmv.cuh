@@ -563,20 +563,6 @@ __device__ __noinline__ double2 row_spmv2_df_redo(CA colf, int rs, int re, const
     return row_spmv2_df<S, XS, CA>(colf, rs, re, vals, x, g);
 }
 
-// Value loads of the pre-split SpMV (16 bytes: two members' float pairs of
-// one entry).  From s = 16 the threads of a row read whole 128-byte lines at
-// each entry, once: streaming loads (evict-first).  Below s = 16 a line holds
-// 16 / s consecutive entries of a row, which the same warp reads over as many
-// steps of its row loop: normal loads, so that the line stays in L1 between
-// them.  64^3 mesh: s = 4 90.9 -> 76.2 us, s = 8 140.9 -> 118.1 us per launch;
-// at s = 32 normal loads took 408 us against 351 us.
-template <int S>
-__device__ __forceinline__ float4 ld_vdf4(const float2 *vdf, int64_t i) {
-    const float4 *p = reinterpret_cast<const float4 *>(vdf + i);
-    if constexpr (S >= 16) return ld_stream(p);
-    else return ld_normal(p);
-}
-
 // XS: the source of the split x (XPre: the CG's split vectors; XSplit: FP64 x
 // split on the fly with the same rounding, as in ens_spmv_df)
 template <int S, typename XS, typename CA>
@@ -589,10 +575,10 @@ __device__ __forceinline__ double2 row_spmv2_dfv(CA colf, int rs, int re, const 
     int j = rs;
     for (; j + 4 <= re; j += 4) {
         const int c0 = colf(j), c1 = colf(j + 1), c2 = colf(j + 2), c3 = colf(j + 3);
-        const float4 v0 = ld_vdf4<S>(vdf, (int64_t)j * S + m);
-        const float4 v1 = ld_vdf4<S>(vdf, (int64_t)(j + 1) * S + m);
-        const float4 v2 = ld_vdf4<S>(vdf, (int64_t)(j + 2) * S + m);
-        const float4 v3 = ld_vdf4<S>(vdf, (int64_t)(j + 3) * S + m);
+        const float4 v0 = ld_stream(reinterpret_cast<const float4 *>(vdf + (int64_t)j * S + m));
+        const float4 v1 = ld_stream(reinterpret_cast<const float4 *>(vdf + (int64_t)(j + 1) * S + m));
+        const float4 v2 = ld_stream(reinterpret_cast<const float4 *>(vdf + (int64_t)(j + 2) * S + m));
+        const float4 v3 = ld_stream(reinterpret_cast<const float4 *>(vdf + (int64_t)(j + 3) * S + m));
         const float4 x0 = XS::two(x, (int64_t)c0 * S + m);
         const float4 x1 = XS::two(x, (int64_t)c1 * S + m);
         const float4 x2 = XS::two(x, (int64_t)c2 * S + m);
@@ -603,7 +589,51 @@ __device__ __forceinline__ double2 row_spmv2_dfv(CA colf, int rs, int re, const 
         df_term_pm(a1, ma, v3.x, v3.y, x3.x, x3.y); df_term_pm(b1, mb, v3.z, v3.w, x3.z, x3.w);
     }
     for (; j < re; ++j) {
-        const float4 v = ld_vdf4<S>(vdf, (int64_t)j * S + m);
+        const float4 v = ld_stream(reinterpret_cast<const float4 *>(vdf + (int64_t)j * S + m));
+        const float4 xv = XS::two(x, (int64_t)colf(j) * S + m);
+        if ((j - rs) & 1) { df_term_pm(a1, ma, v.x, v.y, xv.x, xv.y); df_term_pm(b1, mb, v.z, v.w, xv.z, xv.w); }
+        else { df_term_pm(a0, ma, v.x, v.y, xv.x, xv.y); df_term_pm(b0, mb, v.z, v.w, xv.z, xv.w); }
+    }
+    const double2 y = make_double2(df_finish(a0, a1, 0.0), df_finish(b0, b1, 0.0));
+    if (finite_bits(y.x) && finite_bits(y.y) && !df_tiny(ma) && !df_tiny(mb)) return y;
+    return row_spmv2_df_redo<S, XS, CA>(colf, rs, re, vals, x, g);
+}
+
+// row_spmv2_dfv with the value loads in the default cache policy, for s < 16.
+// From s = 16 the threads of a row read whole 128-byte lines of values at each
+// entry, once: streaming loads (evict-first, row_spmv2_dfv).  Below s = 16 a
+// line holds 16 / s consecutive entries of a row, which the same warp reads
+// over as many steps of its row loop: normal loads keep the line in L1 between
+// them (64^3 mesh: s = 8 140.9 -> 115.9 us, s = 4 90.9 -> 79 us per launch;
+// at s = 16 streaming loads are faster, 205.5 against 219.4 us).  A separate
+// function rather than a load chosen by s inside row_spmv2_dfv: routing the
+// s = 32 loads through a shared helper changed that kernel's register
+// allocation and cost 6 % (354.5 -> 376.9 us per launch).
+template <int S, typename XS, typename CA>
+__device__ __forceinline__ double2 row_spmv2_dfv_l1(CA colf, int rs, int re, const float2 *__restrict__ vdf,
+                                                 const double *__restrict__ vals,
+                                                 typename XS::ptr __restrict__ x, int g) {
+    DfAcc a0 = df_zero(), a1 = df_zero(), b0 = df_zero(), b1 = df_zero();
+    float ma = 0.0f, mb = 0.0f;  // max |product| of members m, m+1
+    const int m = 2 * g;
+    int j = rs;
+    for (; j + 4 <= re; j += 4) {
+        const int c0 = colf(j), c1 = colf(j + 1), c2 = colf(j + 2), c3 = colf(j + 3);
+        const float4 v0 = ld_normal(reinterpret_cast<const float4 *>(vdf + (int64_t)j * S + m));
+        const float4 v1 = ld_normal(reinterpret_cast<const float4 *>(vdf + (int64_t)(j + 1) * S + m));
+        const float4 v2 = ld_normal(reinterpret_cast<const float4 *>(vdf + (int64_t)(j + 2) * S + m));
+        const float4 v3 = ld_normal(reinterpret_cast<const float4 *>(vdf + (int64_t)(j + 3) * S + m));
+        const float4 x0 = XS::two(x, (int64_t)c0 * S + m);
+        const float4 x1 = XS::two(x, (int64_t)c1 * S + m);
+        const float4 x2 = XS::two(x, (int64_t)c2 * S + m);
+        const float4 x3 = XS::two(x, (int64_t)c3 * S + m);
+        df_term_pm(a0, ma, v0.x, v0.y, x0.x, x0.y); df_term_pm(b0, mb, v0.z, v0.w, x0.z, x0.w);
+        df_term_pm(a1, ma, v1.x, v1.y, x1.x, x1.y); df_term_pm(b1, mb, v1.z, v1.w, x1.z, x1.w);
+        df_term_pm(a0, ma, v2.x, v2.y, x2.x, x2.y); df_term_pm(b0, mb, v2.z, v2.w, x2.z, x2.w);
+        df_term_pm(a1, ma, v3.x, v3.y, x3.x, x3.y); df_term_pm(b1, mb, v3.z, v3.w, x3.z, x3.w);
+    }
+    for (; j < re; ++j) {
+        const float4 v = ld_normal(reinterpret_cast<const float4 *>(vdf + (int64_t)j * S + m));
         const float4 xv = XS::two(x, (int64_t)colf(j) * S + m);
         if ((j - rs) & 1) { df_term_pm(a1, ma, v.x, v.y, xv.x, xv.y); df_term_pm(b1, mb, v.z, v.w, xv.z, xv.w); }
         else { df_term_pm(a0, ma, v.x, v.y, xv.x, xv.y); df_term_pm(b0, mb, v.z, v.w, xv.z, xv.w); }
@@ -800,8 +830,12 @@ __device__ __forceinline__ double2 chunk_spmv_dfv(const ChunkCols &cc, bool stag
         return make_double2(v, 0.0);
     } else {
         if (!valid) return make_double2(0.0, 0.0);
-        return staged ? row_spmv2_dfv<S, XS>(ColShared{cc.col, cc.base}, rs, re, vdf, vals, x, g)
-                      : row_spmv2_dfv<S, XS>(ColGlobal{col}, rs, re, vdf, vals, x, g);
+        if constexpr (S >= 16)
+            return staged ? row_spmv2_dfv<S, XS>(ColShared{cc.col, cc.base}, rs, re, vdf, vals, x, g)
+                          : row_spmv2_dfv<S, XS>(ColGlobal{col}, rs, re, vdf, vals, x, g);
+        else
+            return staged ? row_spmv2_dfv_l1<S, XS>(ColShared{cc.col, cc.base}, rs, re, vdf, vals, x, g)
+                          : row_spmv2_dfv_l1<S, XS>(ColGlobal{col}, rs, re, vdf, vals, x, g);
     }
 }
 
@@ -865,41 +899,6 @@ __device__ __forceinline__ void chunk_tree(double (*sm)[S + 1], double v0, doubl
         for (int e = threadIdx.x; e < S; e += blockDim.x) t.buf[1][chunk * t.width + off + e] = sm[0][e];
     }
     __syncthreads();
-}
-
-// Level-1 step of the CG's p.q (K1), in the order of K2's r.r: the chunk's
-// per-row products in shared memory, then the 32 rows in 4 slices of 8 rows,
-// each summed row by row, and the slices combined as (q0 + q2) + (q1 + q3)
-// by two shuffles among the 4 lanes (4e .. 4e+3) that hold member e's
-// slices.  One barrier instead of the halving tree's six; the same number of
-// FP64 adds.  The chunk's threads are [ltid = 0, nthr) with nthr >= 4 S and
-// a multiple of 32; every thread of the CTA calls it (its barrier is
-// CTA-wide).  Writes t.buf[1][chunk*width + off + e] when the chunk exists;
-// TRAIL: a closing barrier (for a caller that reuses sm).
-template <int S, bool TRAIL>
-__device__ __forceinline__ void chunk_slices(double (*sm)[S + 1], double v0, double v1, int r, int g,
-                                             const DotTree &t, int64_t chunk, int off, int ltid, bool exists) {
-    if constexpr (S == 1) {
-        if (g == 0) sm[r][0] = v0;
-    } else {
-        sm[r][2 * g] = v0;
-        sm[r][2 * g + 1] = v1;
-    }
-    __syncthreads();
-    constexpr int NT = (4 * S < 32) ? 32 : 4 * S;   // whole warps take part in the shuffles
-    if (ltid < NT) {
-        const int e = ltid >> 2, k = ltid & 3;
-        double q = 0.0;
-        if (ltid < 4 * S) {
-            q = sm[8 * k][e];
-#pragma unroll
-            for (int i = 1; i < 8; ++i) q += sm[8 * k + i][e];
-        }
-        q += __shfl_xor_sync(0xffffffffu, q, 2);   // lanes k = 0, 1: q0 + q2, q1 + q3
-        q += __shfl_xor_sync(0xffffffffu, q, 1);   // lane k = 0: (q0 + q2) + (q1 + q3)
-        if (k == 0 && ltid < 4 * S && exists) t.buf[1][chunk * t.width + off + e] = q;
-    }
-    if (TRAIL) __syncthreads();
 }
 
 // Subset form of chunk_tree (halving tree): the chunk's threads are
