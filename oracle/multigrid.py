@@ -18,7 +18,8 @@ This oracle states the geometric version on the nested hex meshes:
             boundary nodes are left out.  R_l = P_l^T.
   smoother  S(b, x) = x + p(D^-1 A) D^-1 (b - A x), p the Chebyshev polynomial
             of `degree` steps on [lam/ratio, lam], lam = boost x the power
-            estimate of the largest eigenvalue of D^-1 A (oracle.precond);
+            estimate of the largest eigenvalue of D^-1 A (oracle.precond), or
+            with lanczos=True its Lanczos estimate from as many steps;
             ratio 5 by default: a smoother only has to damp the upper part
             of the spectrum, which factor-2 coarsening cannot represent.
   V-cycle   V_L(b) = A_L^-1 b (dense solve);
@@ -74,12 +75,15 @@ def _parents(i, Nc):
 
 
 class Level:
-    def __init__(self, N, M, xi, v0, power_iters, boost, ratio, sigma=0.1, kappa0=1.0, L=1.0):
+    def __init__(self, N, M, xi, v0, power_iters, boost, ratio, sigma=0.1, kappa0=1.0, L=1.0, lanczos=False):
         self.N = N
         self.rm, self.col = O.graph(N)
         self.vals, self.load = O.assemble(N, M, xi, self.rm, self.col, L=L, sigma=sigma, kappa0=kappa0)
         self.d = P.diagonal(self.rm, self.col, self.vals)
-        self.lam = P.lam_max(self.rm, self.col, self.vals, v0, power_iters)
+        if lanczos:   # power_iters Lanczos steps instead of power steps
+            self.lam = P.lam_max_lanczos(self.rm, self.col, self.vals, v0, power_iters)
+        else:
+            self.lam = P.lam_max(self.rm, self.col, self.vals, v0, power_iters)
         self.lmax = boost * self.lam
         self.ratio = ratio
 
@@ -91,7 +95,8 @@ class Level:
 
 
 def hierarchy(N, M, xi, starts, power_iters=10, boost=1.1, ratio=5.0, **kw):
-    """Levels for one sample; starts[l] = power-iteration start vector of level l."""
+    """Levels for one sample; starts[l] = start vector of level l's eigenvalue
+    estimate (power iteration, or Lanczos with lanczos=True)."""
     return [Level(n, M, xi, starts[l], power_iters, boost, ratio, **kw) for l, n in enumerate(level_sizes(N))]
 
 

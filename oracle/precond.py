@@ -13,6 +13,18 @@ SpMV-based preconditioners used on their own, per sample, in textbook form:
             vector v_0, v_{k+1} = D^-1 A v_k / ||D^-1 A v_k||, and after
             `iters` steps the generalized Rayleigh quotient
             (v.A v) / (v.D v) of the last vector.
+  lam_max_lanczos
+            the same bound from `steps` Lanczos steps on D^-1 A, which is
+            self-adjoint in the D inner product <x, y> = x.D y (Lanczos 1950;
+            Saad, Iterative Methods, Sect. 6.6): q_1 = v_0 / ||v_0||_D,
+            beta_0 = 0, and for j = 1 .. steps
+              y = A q_j,  alpha_j = q_j.y,
+              u = D^-1 y - alpha_j q_j - beta_{j-1} q_{j-1},
+              beta_j = ||u||_D,  q_{j+1} = u / beta_j (0 when beta_j = 0);
+            the estimate is the largest eigenvalue of the tridiagonal T with
+            diagonal alpha_1..alpha_steps and off-diagonal beta_1..beta_{steps-1}
+            (a Ritz value: a lower bound that no power estimate from the same
+            start with fewer matrix products exceeds).
   Chebyshev z = p(D^-1 A) D^-1 r: `degree` steps of Chebyshev iteration for
             A z = r from z = 0 on the interval [lam_max / ratio, lam_max]
             (theta = centre, delta = half width, sigma = theta / delta):
@@ -50,6 +62,26 @@ def lam_max(row_map, col, values, v0, iters):
         v = y / np.linalg.norm(y)
     av = O.spmv(row_map, col, values, v)
     return float(np.dot(v, av) / np.dot(v, d * v))
+
+
+def lam_max_lanczos(row_map, col, values, v0, steps):
+    """Lanczos estimate of the largest eigenvalue of D^-1 A (largest Ritz value)."""
+    d = diagonal(row_map, col, values)
+    v = np.asarray(v0, dtype=np.float64)
+    q = v / np.sqrt(np.dot(v, d * v))
+    q_prev = np.zeros_like(q)
+    beta = 0.0
+    alphas, betas = [], []
+    for _ in range(steps):
+        y = O.spmv(row_map, col, values, q)
+        alpha = float(np.dot(q, y))
+        u = y / d - alpha * q - beta * q_prev
+        beta = float(np.sqrt(np.dot(u, d * u)))
+        alphas.append(alpha)
+        betas.append(beta)
+        q_prev, q = q, (u / beta if beta > 0.0 else np.zeros_like(u))
+    T = np.diag(alphas) + np.diag(betas[:-1], 1) + np.diag(betas[:-1], -1)
+    return float(np.linalg.eigvalsh(T)[-1])
 
 
 def chebyshev(row_map, col, values, r, lmax, ratio, degree):

@@ -1,4 +1,4 @@
-"""Pins for the preconditioned-CG oracle (Jacobi, Chebyshev, power iteration).
+"""Pins for the preconditioned-CG oracle (Jacobi, Chebyshev, power iteration, Lanczos).
 
 The Chebyshev preconditioner against its closed form through the Chebyshev
 polynomials T_k of the scaled spectrum (Saad, Sect. 12.3: the error after k
@@ -109,3 +109,55 @@ def test_pcg_identity_is_the_plain_cg_and_jacobi_terminates():
     bA = inputs.random_vector(17, n)
     x, it, rr, st = P.pcg(rmA, colA, vA, bA, lambda r: r / np.diag(A), tol=1e-12)
     assert st == 0 and it <= 2 and np.linalg.norm(A @ x - bA) <= 1e-11 * np.linalg.norm(bA)
+
+
+def tridiag_laplacian(n):
+    """1D tridiag(-1, 2, -1) as CSR: D = 2 I, and the eigenvalues of D^-1 A are
+    1 - cos(k pi / (n + 1)), k = 1..n (closed form)."""
+    rm, col, v = [0], [], []
+    for i in range(n):
+        for j, a in ((i - 1, -1.0), (i, 2.0), (i + 1, -1.0)):
+            if 0 <= j < n:
+                col.append(j)
+                v.append(a)
+        rm.append(len(col))
+    return np.array(rm, np.int32), np.array(col, np.int32), np.array(v)
+
+
+def test_lanczos_is_exact_on_the_whole_krylov_space():
+    # n steps span the whole space: the largest Ritz value is the largest
+    # eigenvalue, here the closed form 1 + cos(pi / (n + 1))
+    n = 12
+    rm, col, v = tridiag_laplacian(n)
+    est = P.lam_max_lanczos(rm, col, v, inputs.random_vector(3, n), n)
+    assert abs(est - (1.0 + np.cos(np.pi / (n + 1)))) <= 1e-12
+
+
+def test_lanczos_terminates_after_the_distinct_eigenvalues():
+    # D^-1 A with five distinct eigenvalues (two decoupled 2x2 blocks of one
+    # kind, one of another, an isolated row): exact after 5 steps (finite
+    # termination), and the repeated block adds no step
+    rm = np.array([0, 2, 4, 6, 8, 10, 12, 13], np.int32)
+    col = np.array([0, 1, 0, 1, 2, 3, 2, 3, 4, 5, 4, 5, 6], np.int32)
+    v = np.array([2.0, -1.0, -1.0, 2.0, 2.0, -1.0, -1.0, 2.0, 4.0, 1.0, 1.0, 4.0, 3.0])
+    # block [[2,-1],[-1,2]]/2: 1/2, 3/2; block [[4,1],[1,4]]/4: 3/4, 5/4; row: 1
+    est = P.lam_max_lanczos(rm, col, v, inputs.random_vector(4, 7), 5)
+    assert abs(est - 1.5) <= 1e-12
+
+
+def test_lanczos_bounds_the_power_estimate_from_below_and_above():
+    rm, col, v, _ = system(3)
+    A, dh, lam, V = scaled_eig(rm, col, v)
+    v0 = inputs.random_vector(7, len(rm) - 1)
+    prev = 0.0
+    for k in range(1, 9):
+        est = P.lam_max_lanczos(rm, col, v, v0, k)
+        # a Ritz value: never above the largest eigenvalue, never decreasing
+        # with k, and never below the power estimate that uses k - 1 products
+        # of the same start (its vector lies in the same Krylov space)
+        assert est <= lam[-1] * (1 + 1e-13)
+        assert est >= prev - 1e-13 * lam[-1]
+        if k >= 2:
+            assert est >= P.lam_max(rm, col, v, v0, k - 1) - 1e-13 * lam[-1]
+        prev = est
+    assert abs(P.lam_max_lanczos(rm, col, v, v0, 30) - lam[-1]) <= 1e-9 * lam[-1]
