@@ -1198,6 +1198,7 @@ def main_pcg(args):
 
 # ----------------------------------- multigrid-preconditioned CG (NEXT-3)
 MG_SAMPLES = 256
+MG_LANCZOS_STEPS = 5   # the *_lanczos forms' steps (ENS_PC_LANCZOS)
 MG_WORKLOAD = ("KL diffusion, 64^3 hex Q1 mesh, M=10, 256 samples as 8 ensembles of s=32, CG to 1e-8: "
                "multigrid-preconditioned ensemble CG (V-cycle over 64^3..4^3, Chebyshev-2 smoothers, "
                "direct coarse solve; mg: the SpMVs in double-float from pre-split values on every level, "
@@ -1242,7 +1243,11 @@ def run_mg(args, compact=False, oracle_jobs=None):
                           mg.workspace_size(s, vals0, starts, [vdf], v32s)), dtype=torch.uint8, device=dev)
     del vals0
 
-    def run(form):
+    def run(form_name):
+        # *_lanczos: the smoothers' eigenvalue bound from MG_LANCZOS_STEPS Lanczos steps
+        lanczos = form_name.endswith("_lanczos")
+        form = form_name[:-len("_lanczos")] if lanczos else form_name
+        eig = dict(flags=E.PC_LANCZOS, power_iters=MG_LANCZOS_STEPS) if lanczos else dict(flags=0, power_iters=10)
         its = []
         torch.cuda.synchronize()
         t = time.perf_counter()
@@ -1255,8 +1260,10 @@ def run_mg(args, compact=False, oracle_jobs=None):
                 # (mg_fp32_vcycle: K1 pre-split; the V-cycle and its eigenvalue bound in FP32)
                 vals, b = mg.assemble(s, xi, df=True, values_df=pre)
                 v32 = mg.to_f32(s, vals, out=v32s) if form == "mg_fp32_vcycle" else None
-                it, rr, st, _ = mg.solve(s, vals, b, x, TOL, 500, wmg, starts, flags=E.CG_GRAPH | E.CG_X0_ZERO,
-                                         check_every=4, values_df=pre, values_f32=v32)
+                it, rr, st, _ = mg.solve(s, vals, b, x, TOL, 500, wmg, starts,
+                                         flags=E.CG_GRAPH | E.CG_X0_ZERO | eig["flags"],
+                                         power_iters=eig["power_iters"], check_every=4, values_df=pre,
+                                         values_f32=v32)
             else:
                 vals, b = mesh.assemble(s, xi, values_df=vdf if form == "cg_dfv" else None)
                 it, rr, st, _ = E.cg(mesh.graph, s, vals, b, x, TOL, 10000, wcg,
@@ -1265,14 +1272,14 @@ def run_mg(args, compact=False, oracle_jobs=None):
             if any(st):
                 raise RuntimeError(f"{form}: status {st}")
             its += it
-            if gi == 0 and form == "mg":
+            if gi == 0 and form_name == "mg":
                 first["x"] = x.view(-1, s)[:, :nref].clone()
         torch.cuda.synchronize()
         return its, time.perf_counter() - t
 
     out = {}
-    forms = ("cg_dfv", "mg", "mg_fp32_vcycle") if compact else ("cg_f64", "cg_dfv", "mg_f64", "mg",
-                                                                 "mg_fp32_vcycle")
+    forms = ("cg_dfv", "mg", "mg_lanczos", "mg_fp32_vcycle") if compact else (
+        "cg_f64", "cg_dfv", "mg_f64", "mg", "mg_lanczos", "mg_fp32_vcycle", "mg_fp32_vcycle_lanczos")
     for form in forms:
         for _ in range(warmup):
             run(form)
@@ -1287,7 +1294,8 @@ def run_mg(args, compact=False, oracle_jobs=None):
             "config": {"workload": MG_WORKLOAD if not compact else
                        MG_WORKLOAD.replace("256 samples as 8 ensembles", "64 samples as 2 ensembles"),
                        "levels": mg.sizes, "smoother": "Chebyshev degree 2 on "
-                       "[lam/5, 1.1 lam], 10 power steps", "mesh_setup_seconds": t_setup,
+                       "[lam/5, 1.1 lam], 10 power steps (*_lanczos forms: %d Lanczos steps)" % MG_LANCZOS_STEPS,
+                       "mesh_setup_seconds": t_setup,
                        "step": "assembly of every level + solve, per ensemble"},
             "forms": out, "speedup_vs_plain_cg_dfv": out["mg"]["sample_solves_per_s"] /
             out["cg_dfv"]["sample_solves_per_s"]}

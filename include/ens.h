@@ -311,12 +311,17 @@ int ens_cg_df(const ens_graph *graph, int s, const double *values, const void *v
  *                     (Saad, Iterative Methods, Sect. 12.3), lam = boost x an
  *                     estimate of the largest eigenvalue of D^-1 A: power_iters
  *                     steps v <- D^-1 A v / ||D^-1 A v|| from power_start (device,
- *                     commuted layout n*s) and the quotient v.Av / v.Dv.
+ *                     commuted layout n*s) and the quotient v.Av / v.Dv; with
+ *                     ENS_PC_LANCZOS in flags the Lanczos estimate from
+ *                     power_iters (1..32) steps instead (see ens_mg_pcg).
  * FP64 values and arithmetic (the ENS_F64 SpMV).  flags: ENS_CG_GRAPH,
- * ENS_CG_X0_ZERO.  lam_host[s] (may be NULL) receives the estimates (0 for
+ * ENS_CG_X0_ZERO, ENS_PC_LANCZOS.  lam_host[s] (may be NULL) receives the estimates (0 for
  * Jacobi).  Other arguments and outputs as ens_cg; work:
  * ens_pcg_workspace_size bytes.  Synchronises `stream`. */
 enum { ENS_PC_JACOBI = 1, ENS_PC_CHEBYSHEV = 2 };
+/* flag of ens_pcg and ens_mg_pcg: the smoothers' eigenvalue bound by Lanczos
+ * (not in the paper: its smoothers take MueLu's power iteration) */
+#define ENS_PC_LANCZOS (1 << 24)
 int ens_pcg_workspace_size(int32_t num_rows, int s, size_t *bytes);
 int ens_pcg(const ens_graph *graph, int s, const double *values, const double *b, double *x, double tol,
             int max_iter, int precond, int degree, double ratio, double boost, int power_iters,
@@ -334,12 +339,20 @@ int ens_pcg(const ens_graph *graph, int s, const double *values, const double *b
  *        i+1, weight 1/2 each, per axis; boundary nodes left out), R_l = P_l^T;
  *   S_l  Chebyshev smoother x += p(D^-1 A) D^-1 (b - A x): `degree` steps on
  *        [lam/ratio, lam], lam = boost x the power estimate of ens_pcg
- *        (power_iters steps from the level's power_start);
+ *        (power_iters steps from the level's power_start), or with
+ *        ENS_PC_LANCZOS in flags the Lanczos estimate from power_iters
+ *        (1..32) steps from the same start: the largest eigenvalue of the
+ *        tridiagonal T_k of Lanczos in the D inner product (Lanczos 1950;
+ *        Saad, Iterative Methods, Sect. 6.6), never below the power estimate
+ *        from the same start with as many matrix products (5 Lanczos steps
+ *        on the 64^3 Q1 levels: about 0.925 of the largest eigenvalue, 10
+ *        power steps 0.91); not in the paper, whose smoothers take MueLu's
+ *        power iteration;
  *   V_L  x = A_L^-1 b (inverse of the coarsest matrix, Gauss-Jordan once per
  *        call; at most 125 rows);
  *   V_l  x = S(b, 0); r = b - A x; x += P V_{l+1}(R r); x = S(b, x).
  * CG as ens_cg with rho = r.z; FP64 throughout.  flags: ENS_CG_GRAPH,
- * ENS_CG_X0_ZERO.  b, x: level-0 vectors (commuted layout).  Returns
+ * ENS_CG_X0_ZERO, ENS_PC_LANCZOS.  b, x: level-0 vectors (commuted layout).  Returns
  * ENS_ERR_BREAKDOWN if the coarsest matrix is not positive definite.
  * Synchronises `stream`. */
 typedef struct ens_mg_level {

@@ -18,7 +18,7 @@ __all__ = ["EnsError", "lib", "Graph", "Mesh", "mesh_sizes", "graph_build", "kl_
            "snapshots_put", "pod", "pod_workspace_size", "pod_targets", "to_f32", "mlp_param_count",
            "mlp_init", "mlp_workspace_size", "mlp_forward", "mlp_grad", "mlp_adam", "mlp_train",
            "guess", "guess_workspace_size", "MLP_DIMS", "pcg", "pcg_workspace_size", "PC_JACOBI",
-           "PC_CHEBYSHEV", "Multigrid", "mg_level_sizes"]
+           "PC_CHEBYSHEV", "PC_LANCZOS", "Multigrid", "mg_level_sizes"]
 
 F64, F32, BF16, F64_DF, F64_SPLIT = 0, 1, 2, 3, 4
 CG_COUPLED, CG_GRAPH, CG_TIME_SPMV, CG_DF64, CG_SPLIT64, CG_GUESS_FALLBACK, CG_X0_ZERO = 1, 2, 4, 8, 16, 32, 64
@@ -349,6 +349,7 @@ def cg(graph, s, values, b, x, tol, max_iter, work, flags=0, check_every=8, stre
 
 # ------------------------------------------------------ preconditioned CG
 PC_JACOBI, PC_CHEBYSHEV = 1, 2
+PC_LANCZOS = 1 << 24   # flags of pcg and Multigrid.solve: the eigenvalue bound by Lanczos steps
 
 
 def pcg_workspace_size(n, s):

@@ -138,7 +138,8 @@ static int mg_run(int nl, const ens_mg_level *levels, const double *b, double *x
     pa0.c = c;
     int launches = 0, rc;
     ENS_CUDA_TRY(cudaMemsetAsync(c.st, 0, sizeof(CgState), st));
-    if ((rc = mg.setup(levels, ratio, boost, power_iters, bad, st, &launches))) return rc;
+    if ((rc = mg.setup(levels, ratio, boost, power_iters, bad, st, &launches, (flags & ENS_PC_LANCZOS) != 0)))
+        return rc;
     pa0.ps = mg.lv[0].pa.ps;
     ENS_LAUNCH_CHECK("ens_mg_pcg set-up");
     // the PCG trees of level 0 (the set-up reused them; clear again)
@@ -273,7 +274,8 @@ extern "C" int ens_mg_pcg(int nlevels, const ens_mg_level *levels, int s, const 
     if (rc) return rc;
     if (!b || !x || !work) return fail(ENS_ERR_ARG, "NULL b/x/work");
     if (!(tol >= 0.0) || max_iter < 0 || check_every < 1 || degree < 1 || degree > kPcMaxDegree ||
-        !(ratio > 1.0) || !(boost >= 1.0) || power_iters < 1 || power_iters > 1000)
+        !(ratio > 1.0) || !(boost >= 1.0) || power_iters < 1 || power_iters > 1000 ||
+        ((flags & ENS_PC_LANCZOS) && power_iters > kLzMaxSteps))
         return fail(ENS_ERR_ARG, "ens_mg_pcg: bad tol/max_iter/check_every/degree/ratio/boost/power_iters");
     for (int l = 0; l < nlevels; ++l)
         if (!levels[l].power_start) return fail(ENS_ERR_ARG, "ens_mg_pcg: level %d: NULL power_start", l);

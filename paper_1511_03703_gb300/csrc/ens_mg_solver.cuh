@@ -649,7 +649,7 @@ struct MgSolver {
     // definite; the caller reads it).  All asynchronous on st.
     // the set-up of level l on stream st (diagonal, eigenvalue bound, Chebyshev parameters)
     int setup_level(int l, const ens_mg_level *levels, double ratio, double boost, int power_iters,
-                    cudaStream_t st, int *launches) {
+                    bool lanczos, cudaStream_t st, int *launches) {
         MgLevel &m = lv[l];
         PcgArgs &a = m.pa;
         int rc;
@@ -666,7 +666,11 @@ struct MgSolver {
         if (f32) mg32_to_f32_kernel<<<152 * 4, 256, 0, st>>>(nt, a.dinv, m.dinv32);
         ENS_CUDA_TRY(cudaMemcpyAsync(a.v, levels[l].power_start, sizeof(double) * (size_t)nt,
                                      cudaMemcpyDeviceToDevice, st));
-        if (f32) {  // the FP32 V-cycle's bound: power iteration on its FP32 values
+        if (lanczos) {   // the level's r holds q_{j-1} (the set-up runs before any V-cycle)
+            if (f32) *launches += lanczos_bound<S, 4>(a, m.r, chunks(m.n), power_iters, st);
+            else if (m.vdf) *launches += lanczos_bound<S, 3>(a, m.r, chunks(m.n), power_iters, st);
+            else *launches += lanczos_bound<S, 0>(a, m.r, chunks(m.n), power_iters, st);
+        } else if (f32) {  // the FP32 V-cycle's bound: power iteration on its FP32 values
             mg32_to_f32_kernel<<<152 * 4, 256, 0, st>>>(nt, a.v, a.v32);
             for (int k = 0; k < power_iters; ++k) {
                 pc_power_kernel<S, 4><<<chunks(m.n), RowMap<S>::THREADS, 0, st>>>(a);
@@ -700,7 +704,7 @@ struct MgSolver {
     // (short, latency-bound launches) and the coarsest inverse (one CTA per
     // member) on two forked streams that st then waits for.  Asynchronous.
     int setup(const ens_mg_level *levels, double ratio, double boost, int power_iters, int *bad,
-              cudaStream_t st, int *launches) {
+              cudaStream_t st, int *launches, bool lanczos = false) {
         const int nl = (int)lv.size();
         int rc = ENS_OK;
         ENS_CUDA_TRY(cudaMemsetAsync(bad, 0, sizeof(int), st));
@@ -720,7 +724,7 @@ struct MgSolver {
         for (int i = 0; i < 2 && ce == cudaSuccess; ++i) ce = cudaStreamWaitEvent(side[i], fork, 0);
         if (ce == cudaSuccess) {
             for (int l = 0; l < nl && rc == ENS_OK; ++l)
-                rc = setup_level(l, levels, ratio, boost, power_iters, l == 0 ? st : side[0], launches);
+                rc = setup_level(l, levels, ratio, boost, power_iters, lanczos, l == 0 ? st : side[0], launches);
             mg_coarse_inverse_kernel<S><<<S, 512, smem, side[1]>>>(mc.n, mc.row_map, mc.col, mc.vals, inv, bad);
             ++*launches;
             for (int i = 0; i < 2 && ce == cudaSuccess; ++i) {

@@ -199,13 +199,17 @@ static int pcg_run(const ens_graph *g, const double *vals, const double *b, doub
     ++launches;
     if (degree >= 1) {  // largest eigenvalue of D^-1 A, then the Chebyshev parameters
         ENS_CUDA_TRY(cudaMemcpyAsync(a.v, v0, sizeof(double) * (size_t)nt, cudaMemcpyDeviceToDevice, st));
-        for (int k = 0; k < power_iters; ++k) {
-            pc_power_kernel<S><<<grid, RowMap<S>::THREADS, 0, st>>>(a);
-            pc_scale_kernel<S><<<152 * 4, 256, 0, st>>>(a);
-            launches += 2;
+        if (flags & ENS_PC_LANCZOS) {   // c.q holds q_{j-1} (the CG has not started)
+            launches += lanczos_bound<S, 0>(a, c.q, grid, power_iters, st);
+        } else {
+            for (int k = 0; k < power_iters; ++k) {
+                pc_power_kernel<S><<<grid, RowMap<S>::THREADS, 0, st>>>(a);
+                pc_scale_kernel<S><<<152 * 4, 256, 0, st>>>(a);
+                launches += 2;
+            }
+            pc_rayleigh_kernel<S><<<grid, RowMap<S>::THREADS, 0, st>>>(a);
+            ++launches;
         }
-        pc_rayleigh_kernel<S><<<grid, RowMap<S>::THREADS, 0, st>>>(a);
-        ++launches;
     }
     ENS_LAUNCH_CHECK("ens_pcg set-up");
     // final z buffer of the preconditioner stage (K3 reads it as "r")
@@ -341,9 +345,9 @@ extern "C" int ens_pcg(const ens_graph *graph, int s, const double *values, cons
     int deg = 0;
     if (precond == ENS_PC_CHEBYSHEV) {
         if (degree < 1 || degree > kPcMaxDegree || !(ratio > 1.0) || !(boost >= 1.0) || power_iters < 1 ||
-            power_iters > 1000 || !power_start)
-            return fail(ENS_ERR_ARG, "chebyshev: 1 <= degree <= %d, ratio > 1, boost >= 1, 1 <= power_iters <= 1000, "
-                        "power_start given", kPcMaxDegree);
+            power_iters > 1000 || ((flags & ENS_PC_LANCZOS) && power_iters > kLzMaxSteps) || !power_start)
+            return fail(ENS_ERR_ARG, "chebyshev: 1 <= degree <= %d, ratio > 1, boost >= 1, 1 <= power_iters <= 1000 "
+                        "(<= %d Lanczos steps), power_start given", kPcMaxDegree, kLzMaxSteps);
         deg = degree;
     } else if (precond != ENS_PC_JACOBI) {
         return fail(ENS_ERR_UNSUPPORTED, "precond %d (ENS_PC_JACOBI or ENS_PC_CHEBYSHEV)", precond);

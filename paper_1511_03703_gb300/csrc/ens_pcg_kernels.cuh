@@ -1,14 +1,16 @@
 // ens_pcg_kernels.cuh -- device pieces shared by the preconditioned CG
 // (ens_pcg.cu) and the multigrid-preconditioned CG (ens_mg.cu): per-member
-// Chebyshev parameters, the diagonal, the power-iteration eigenvalue bound and
-// the epilogue of the preconditioner stage.
+// Chebyshev parameters, the diagonal, the eigenvalue bound (power iteration or
+// Lanczos) and the epilogue of the preconditioner stage.
 #pragma once
+#include <cfloat>
 #include "ens_cg_kernels.cuh"
 #include "ens_spmv_f32.cuh"
 
 namespace ens {
 
 constexpr int kPcMaxDegree = 8;
+constexpr int kLzMaxSteps = 32;   // Lanczos steps of the eigenvalue bound
 
 struct PcgState {
     double lam[32];                    // power-iteration estimate (before the boost)
@@ -21,6 +23,8 @@ struct PcgState {
     double inv_nrm[32];                // 1 / ||y||
     double inv_theta[32];              // 1 / theta
     double c2[kPcMaxDegree][32];       // 2 rho_k / delta
+    double lz_a[kLzMaxSteps][32];      // Lanczos: alpha_j (diagonal of T)
+    double lz_b[kLzMaxSteps][32];      // Lanczos: beta_j (off-diagonal of T)
 };
 
 struct PcgArgs {
@@ -29,7 +33,9 @@ struct PcgArgs {
     const double *dg, *dinv;  // diagonal and its inverse, commuted layout
     double *zk[2];            // Chebyshev iterates (ping-pong); zk[0] is z for Jacobi
     double *d;                // Chebyshev direction
-    double *v, *y;            // power iteration
+    double *v, *y;            // power iteration; Lanczos: q_j and y = A q_j, then u
+    double *vprev;            // Lanczos: q_{j-1} (NULL at the first step)
+    int lz_step;              // Lanczos: j (0-based), or the step count for the finish
     int degree;               // 0: Jacobi, >= 1: Chebyshev steps
     double boost, ratio;
     int *split_bad;           // MODE 3 set-up kernels: a split copy met a value out of range
@@ -135,6 +141,26 @@ __global__ void pc_split_kernel(PcgArgs a) {
         store_split1(a.c.pdf, t, a.v[t], a.split_bad);
 }
 
+// member e's eigenvalue estimate lam and its Chebyshev parameters: the
+// interval [lmax / ratio, lmax], lmax = boost * lam (Saad, Sect. 12.3)
+__device__ __forceinline__ void pc_set_chebyshev(const PcgArgs &a, int e, double lam) {
+    PcgState *ps = a.ps;
+    ps->lam[e] = lam;
+    const double lmax = a.boost * lam, lmin = lmax / a.ratio;
+    const double theta = 0.5 * (lmax + lmin), delta = 0.5 * (lmax - lmin), sigma = theta / delta;
+    ps->theta[e] = theta;
+    ps->delta[e] = delta;
+    ps->inv_theta[e] = 1.0 / theta;
+    double rho = 1.0 / sigma;
+    ps->rhoc[0][e] = rho;
+    ps->c2[0][e] = 2.0 * rho / delta;
+    for (int k = 1; k < kPcMaxDegree; ++k) {
+        rho = 1.0 / (2.0 * sigma - rho);
+        ps->rhoc[k][e] = rho;
+        ps->c2[k][e] = 2.0 * rho / delta;
+    }
+}
+
 // lam_e = (v.Av) / (v.Dv) and the Chebyshev parameters of member e
 template <int S, int MODE = 0>
 __global__ void __launch_bounds__(RowMap<S>::THREADS, 1024 / RowMap<S>::THREADS) pc_rayleigh_kernel(PcgArgs a) {
@@ -164,24 +190,217 @@ __global__ void __launch_bounds__(RowMap<S>::THREADS, 1024 / RowMap<S>::THREADS)
     const int e = threadIdx.x;
     if (e < S) {
         const double *top = c.t2.buf[c.t2.levels];
-        const double lam = ld_cg(top + e) / ld_cg(top + S + e);
-        PcgState *ps = a.ps;
-        ps->lam[e] = lam;
-        const double lmax = a.boost * lam, lmin = lmax / a.ratio;
-        const double theta = 0.5 * (lmax + lmin), delta = 0.5 * (lmax - lmin), sigma = theta / delta;
-        ps->theta[e] = theta;
-        ps->delta[e] = delta;
-        ps->inv_theta[e] = 1.0 / theta;
-        double rho = 1.0 / sigma;
-        ps->rhoc[0][e] = rho;
-        ps->c2[0][e] = 2.0 * rho / delta;
-        for (int k = 1; k < kPcMaxDegree; ++k) {
-            rho = 1.0 / (2.0 * sigma - rho);
-            ps->rhoc[k][e] = rho;
-            ps->c2[k][e] = 2.0 * rho / delta;
-        }
+        pc_set_chebyshev(a, e, ld_cg(top + e) / ld_cg(top + S + e));
     }
     __threadfence();
+}
+
+// ----------------------------------------------- Lanczos eigenvalue bound
+// The largest eigenvalue of D^-1 A by Lanczos steps in the D inner product
+// <x, y> = x.D y, in which D^-1 A is self-adjoint (Lanczos 1950; Saad,
+// Iterative Methods, Sect. 6.6): q_1 = v / ||v||_D; for j = 1, 2, ...
+//   y = A q_j, alpha_j = q_j.y, u = D^-1 y - alpha_j q_j - beta_{j-1} q_{j-1},
+//   beta_j = ||u||_D, q_{j+1} = u / beta_j (0 when beta_j = 0);
+// then the largest eigenvalue of the tridiagonal T_k(alpha, beta).  One
+// kernel per dot (each with the canonical tree); the scaling is
+// pc_scale_kernel (with inv_nrm = 1 / beta_j), which also writes the split or
+// FP32 copy of q_{j+1} that the next SpMV reads.
+
+// ||v||_D of the start vector v: inv_nrm = 1 / ||v||_D (0 for v = 0)
+template <int S>
+__global__ void __launch_bounds__(RowMap<S>::THREADS, 1024 / RowMap<S>::THREADS) pc_lz_dnorm_kernel(PcgArgs a) {
+    constexpr int G = RowMap<S>::G;
+    __shared__ double sm[32][S + 1];
+    const CgArgs &c = a.c;
+    const int r = threadIdx.x / G, g = threadIdx.x % G;
+    const int64_t R = (int64_t)blockIdx.x * 32 + r;
+    double v0 = 0.0, v1 = 0.0;
+    if (R < c.n) {
+        if constexpr (S == 1) {
+            const double vv = a.v[R];
+            v0 = vv * (a.dg[R] * vv);
+        } else {
+            const double2 vv = reinterpret_cast<const double2 *>(a.v)[R * G + g];
+            const double2 dd = reinterpret_cast<const double2 *>(a.dg)[R * G + g];
+            v0 = vv.x * (dd.x * vv.x);
+            v1 = vv.y * (dd.y * vv.y);
+        }
+    }
+    chunk_tree<S>(sm, v0, v1, r, g, c.t1, blockIdx.x, 0);
+    if (!dot_tree_propagate(c.t1, blockIdx.x, 1)) return;
+    const int e = threadIdx.x;
+    if (e < S) {
+        const double nv = sqrt(ld_cg(c.t1.buf[c.t1.levels] + e));
+        a.ps->nrm[e] = nv;
+        a.ps->inv_nrm[e] = (nv > 0.0) ? 1.0 / nv : 0.0;
+    }
+    __threadfence();
+}
+
+// step j: y = A q_j (the SpMV of MODE, as the power iteration's) and
+// alpha_j = q_j.y into lz_a[j]
+template <int S, int MODE = 0>
+__global__ void __launch_bounds__(RowMap<S>::THREADS, 1024 / RowMap<S>::THREADS) pc_lz_spmv_kernel(PcgArgs a) {
+    constexpr int G = RowMap<S>::G;
+    __shared__ double sm[32][S + 1];
+    __shared__ ChunkCols cc;
+    const CgArgs &c = a.c;
+    const int r = threadIdx.x / G, g = threadIdx.x % G;
+    const int64_t R = (int64_t)blockIdx.x * 32 + r;
+    const double2 av = pc_setup_spmv<S, MODE>(a, cc, r, g, R < c.n);
+    double v0 = 0.0, v1 = 0.0;
+    if (R < c.n) {
+        if constexpr (S == 1) {
+            if (g == 0) a.y[R] = av.x;
+            v0 = a.v[R] * av.x;
+        } else {
+            reinterpret_cast<double2 *>(a.y)[R * G + g] = av;
+            const double2 qv = reinterpret_cast<const double2 *>(a.v)[R * G + g];
+            v0 = qv.x * av.x;
+            v1 = qv.y * av.y;
+        }
+    }
+    chunk_tree<S>(sm, v0, v1, r, g, c.t1, blockIdx.x, 0);
+    if (!dot_tree_propagate(c.t1, blockIdx.x, 1)) return;
+    const int e = threadIdx.x;
+    if (e < S) a.ps->lz_a[a.lz_step][e] = ld_cg(c.t1.buf[c.t1.levels] + e);
+    __threadfence();
+}
+
+// step j: u = D^-1 y - alpha_j q_j - beta_{j-1} q_{j-1} (in place of y) and
+// beta_j = ||u||_D into lz_b[j], inv_nrm = 1 / beta_j (0 when beta_j = 0)
+template <int S>
+__global__ void __launch_bounds__(RowMap<S>::THREADS, 1024 / RowMap<S>::THREADS) pc_lz_update_kernel(PcgArgs a) {
+    constexpr int G = RowMap<S>::G;
+    __shared__ double sm[32][S + 1];
+    const CgArgs &c = a.c;
+    const PcgState *ps = a.ps;
+    const int j = a.lz_step;
+    const int r = threadIdx.x / G, g = threadIdx.x % G;
+    const int m = (S == 1) ? 0 : 2 * g;
+    const int64_t R = (int64_t)blockIdx.x * 32 + r;
+    const double al0 = ps->lz_a[j][m], al1 = (S == 1) ? 0.0 : ps->lz_a[j][m + 1];
+    const double be0 = (j > 0) ? ps->lz_b[j - 1][m] : 0.0;
+    const double be1 = (j > 0 && S > 1) ? ps->lz_b[j - 1][m + 1] : 0.0;
+    double v0 = 0.0, v1 = 0.0;
+    if (R < c.n) {
+        if constexpr (S == 1) {
+            double u = a.y[R] * a.dinv[R] - al0 * a.v[R];
+            if (j > 0) u -= be0 * a.vprev[R];
+            if (g == 0) a.y[R] = u;
+            v0 = u * (a.dg[R] * u);
+        } else {
+            const int64_t i = R * G + g;
+            const double2 yv = reinterpret_cast<const double2 *>(a.y)[i];
+            const double2 di = reinterpret_cast<const double2 *>(a.dinv)[i];
+            const double2 qv = reinterpret_cast<const double2 *>(a.v)[i];
+            double2 u = make_double2(yv.x * di.x - al0 * qv.x, yv.y * di.y - al1 * qv.y);
+            if (j > 0) {
+                const double2 pv = reinterpret_cast<const double2 *>(a.vprev)[i];
+                u.x -= be0 * pv.x;
+                u.y -= be1 * pv.y;
+            }
+            reinterpret_cast<double2 *>(a.y)[i] = u;
+            const double2 dd = reinterpret_cast<const double2 *>(a.dg)[i];
+            v0 = u.x * (dd.x * u.x);
+            v1 = u.y * (dd.y * u.y);
+        }
+    }
+    chunk_tree<S>(sm, v0, v1, r, g, c.t1, blockIdx.x, 0);
+    if (!dot_tree_propagate(c.t1, blockIdx.x, 1)) return;
+    const int e = threadIdx.x;
+    if (e < S) {
+        const double be = sqrt(ld_cg(c.t1.buf[c.t1.levels] + e));
+        a.ps->lz_b[j][e] = be;
+        a.ps->nrm[e] = be;
+        a.ps->inv_nrm[e] = (be > 0.0) ? 1.0 / be : 0.0;
+    }
+    __threadfence();
+}
+
+// Number of eigenvalues of the k x k symmetric tridiagonal T(al, be) below x,
+// by the signs of the pivots of the LDL^T factorisation of T - x I (Sturm
+// sequence count; Golub and Van Loan, Matrix Computations, Sect. 8.4.1); a
+// pivot of magnitude below pivmin is replaced by -pivmin, as in LAPACK's
+// bisection.
+__device__ __forceinline__ int lz_sturm_count(const double *al, const double *be2, int k, double x,
+                                              double pivmin) {
+    int cnt = 0;
+    double d = 1.0;
+    for (int i = 0; i < k; ++i) {
+        d = (al[i] - x) - ((i > 0) ? be2[i - 1] / d : 0.0);
+        if (fabs(d) < pivmin) d = -pivmin;
+        if (d < 0.0) ++cnt;
+    }
+    return cnt;
+}
+
+// after k = lz_step steps: lam = the largest eigenvalue of T_k by bisection
+// between Gershgorin bounds to the last bit, then the Chebyshev parameters;
+// one warp, lane e for member e
+template <int S>
+__global__ void pc_lz_finish_kernel(PcgArgs a) {
+    const int e = threadIdx.x;
+    if (e >= S) return;
+    const int k = a.lz_step;
+    double al[kLzMaxSteps], be2[kLzMaxSteps];
+    double lo = 0.0, hi = 0.0, bmax2 = 1.0;
+    for (int i = 0; i < k; ++i) {
+        al[i] = a.ps->lz_a[i][e];
+        const double b = (i + 1 < k) ? a.ps->lz_b[i][e] : 0.0;
+        be2[i] = b * b;
+        bmax2 = fmax(bmax2, be2[i]);
+    }
+    for (int i = 0; i < k; ++i) {
+        const double rad = ((i > 0) ? sqrt(be2[i - 1]) : 0.0) + sqrt(be2[i]);
+        lo = (i == 0) ? al[i] - rad : fmin(lo, al[i] - rad);
+        hi = (i == 0) ? al[i] + rad : fmax(hi, al[i] + rad);
+    }
+    const double pivmin = DBL_MIN * bmax2;
+    // every eigenvalue lies in the Gershgorin interval; widened a little, the
+    // count is k at hi and below k at lo, which the bisection keeps
+    lo -= 1e-300 + fabs(lo) * 1e-15;
+    hi += 1e-300 + fabs(hi) * 1e-15;
+    for (int it = 0; it < 200; ++it) {
+        const double mid = 0.5 * (lo + hi);
+        if (mid <= lo || mid >= hi) break;   // the interval is down to adjacent doubles
+        if (lz_sturm_count(al, be2, k, mid, pivmin) == k) hi = mid;
+        else lo = mid;
+    }
+    pc_set_chebyshev(a, e, 0.5 * (lo + hi));
+    __threadfence();
+}
+
+// Host: the Lanczos bound of the level or system in a (start vector in a.v,
+// overwritten) with `steps` steps and the SpMV of MODE, on st; qp is a third
+// vector of n*s doubles for q_{j-1}.  Returns the launches issued.
+template <int S, int MODE>
+static int lanczos_bound(const PcgArgs &a, double *qp, unsigned chunks, int steps, cudaStream_t st) {
+    double *q = a.v, *u = a.y;
+    pc_lz_dnorm_kernel<S><<<chunks, RowMap<S>::THREADS, 0, st>>>(a);
+    PcgArgs b = a;
+    b.y = q;   // q_1 = v / ||v||_D in place, with its split or FP32 copy
+    pc_scale_kernel<S, MODE><<<152 * 4, 256, 0, st>>>(b);
+    for (int j = 0; j < steps; ++j) {
+        b = a;
+        b.v = q;
+        b.y = u;
+        b.vprev = (j > 0) ? qp : nullptr;
+        b.lz_step = j;
+        pc_lz_spmv_kernel<S, MODE><<<chunks, RowMap<S>::THREADS, 0, st>>>(b);
+        pc_lz_update_kernel<S><<<chunks, RowMap<S>::THREADS, 0, st>>>(b);
+        if (j + 1 < steps) {   // q_{j+1} = u / beta_j over q_{j-1}
+            b.v = qp;
+            pc_scale_kernel<S, MODE><<<152 * 4, 256, 0, st>>>(b);
+            double *t = qp;
+            qp = q;
+            q = t;
+        }
+    }
+    b = a;
+    b.lz_step = steps;
+    pc_lz_finish_kernel<S><<<1, 32, 0, st>>>(b);
+    return 3 + 3 * steps;
 }
 
 // ------------------------------------------------------------ CG kernels

@@ -28,7 +28,8 @@ def start(l, e, n):
     return inputs.random_vector(600 + 100 * l + e, n)
 
 
-def gpu_mg(torch, mg, xs, tol=1e-10, flags=0, degree=2, ratio=5.0, check_every=4, presplit=False, f32=False):
+def gpu_mg(torch, mg, xs, tol=1e-10, flags=0, degree=2, ratio=5.0, check_every=4, presplit=False, f32=False,
+           power_iters=10):
     """presplit: level 0 assembled in double-float with its pre-split copy, so
     that the level-0 SpMVs (K1 and the V-cycle's) run in double-float."""
     s = xs.shape[0]
@@ -43,7 +44,7 @@ def gpu_mg(torch, mg, xs, tol=1e-10, flags=0, degree=2, ratio=5.0, check_every=4
     v32 = mg.to_f32(s, vals) if f32 else None
     work = torch.empty(mg.workspace_size(s, vals, starts, vdf, v32), dtype=torch.uint8, device=gpu())
     it, rr, st, stats = mg.solve(s, vals, b, x, tol, 200, work, starts, degree=degree, ratio=ratio, flags=flags,
-                                 check_every=check_every, values_df=vdf, values_f32=v32)
+                                 check_every=check_every, values_df=vdf, values_f32=v32, power_iters=power_iters)
     return to_np(x).reshape(-1, s), it, rr, st
 
 
@@ -151,3 +152,39 @@ def test_mg_fp32_vcycle_member_independent_of_s_and_graph(torch):
     Xg, itg, _, _ = gpu_mg(torch, mg, xs[:8], flags=E.CG_GRAPH, f32=True)
     Xd, itd, _, _ = gpu_mg(torch, mg, xs[:8], f32=True)
     assert itg == itd and np.array_equal(Xg, Xd)
+
+
+@pytest.mark.parametrize("presplit", [False, "all"])
+@pytest.mark.parametrize("s", [1, 4, 32])
+def test_mg_pcg_lanczos_matches_oracle(torch, s, presplit):
+    """ENS_PC_LANCZOS: every level's smoother bound from 5 Lanczos steps (FP64
+    or pre-split SpMVs) against the oracle's MG-PCG on the hierarchy with the
+    same Lanczos estimates: iterations within one, solutions to 1e-8."""
+    N, M = 16, 10
+    mg = E.Multigrid(N, M)
+    xs = inputs.kl_samples(850 + s, 0, s, M)
+    X, it, rr, st = gpu_mg(torch, mg, xs, presplit=presplit, flags=E.PC_LANCZOS, power_iters=5)
+    assert st == [0] * s and max(rr) <= 1.01e-10
+    for e in ([0, s - 1] if s > 2 else range(s)):
+        starts = [start(l, e, (n + 1) ** 3) for l, n in enumerate(G.level_sizes(N))]
+        lv = G.hierarchy(N, M, xs[e], starts, power_iters=5, lanczos=True)
+        xo, ito, rro, sto = G.mg_pcg(lv, lv[0].load, tol=1e-10)
+        assert sto == 0 and abs(it[e] - ito) <= 1, (e, it[e], ito)
+        assert np.linalg.norm(X[:, e] - xo) <= 1e-8 * np.linalg.norm(xo), e
+
+
+def test_mg_lanczos_member_independent_of_s_and_fp32_converges(torch):
+    mg = E.Multigrid(8, 10)
+    xs = inputs.kl_samples(860, 0, 32, 10)
+    ref = None
+    for s in (1, 4, 32):
+        X, it, rr, st = gpu_mg(torch, mg, xs[:s], presplit="all", flags=E.PC_LANCZOS, power_iters=5)
+        cur = (X[:, 0].copy(), it[0])
+        ref = cur if ref is None else ref
+        assert np.array_equal(cur[0], ref[0]) and cur[1] == ref[1], s
+    # the FP32 V-cycle with its Lanczos bound on the FP32 values: converges
+    # to the same FP64 tolerance, close to the FP64 hierarchy's count
+    X32, it32, rr32, st32 = gpu_mg(torch, mg, xs[:4], f32=True, flags=E.PC_LANCZOS, power_iters=5)
+    X64, it64, rr64, st64 = gpu_mg(torch, mg, xs[:4], flags=E.PC_LANCZOS, power_iters=5)
+    assert st32 == [0] * 4 and max(rr32) <= 1.01e-10
+    assert max(abs(a - b) for a, b in zip(it32, it64)) <= 1

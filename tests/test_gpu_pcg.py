@@ -98,3 +98,36 @@ def test_pcg_saves_iterations_and_rejects_bad_arguments(torch):
         with pytest.raises(E.EnsError) as ei:
             E.pcg(mesh.graph, 4, vals, b, x, 1e-8, 100, pw, **kw)
         assert ei.value.code == code
+
+
+@pytest.mark.parametrize("s", [1, 4, 32])
+@pytest.mark.parametrize("steps", [5, 8, 12])
+def test_pcg_lanczos_bound_matches_oracle(torch, s, steps):
+    """ENS_PC_LANCZOS: the Lanczos estimate of the largest eigenvalue of D^-1 A
+    (largest Ritz value of the tridiagonal, by bisection on the device) against
+    the oracle's (LAPACK on the same tridiagonal) to 1e-10, and the Chebyshev
+    PCG built on it against the oracle's.  (One step gives only the start
+    vector's Rayleigh quotient, about 2/3 of the largest eigenvalue: the
+    Chebyshev polynomial is then not positive on the spectrum and PCG breaks
+    down, as it does with too few power steps.)"""
+    N, M, deg = 13, 10, 2
+    mesh = E.Mesh(N, M)
+    xs = inputs.kl_samples(760 + s, 0, s, M)
+    X, it, rr, st, lam = gpu_pcg(torch, mesh, xs, E.PC_CHEBYSHEV, degree=deg, iters=steps, flags=E.PC_LANCZOS)
+    assert st == [0] * s and max(rr) <= 1.01e-10
+    rm, col, ov, ob = oracle_members(N, M, xs)
+    v0 = starts(mesh.n, s)
+    for e in ([0, s - 1] if s > 2 else range(s)):
+        lo = P.lam_max_lanczos(rm, col, ov[e], v0[e], steps)
+        assert abs(lam[e] - lo) <= 1e-10 * lo, (e, lam[e], lo)
+        pre = lambda r, v=ov[e], lo=lo: P.chebyshev(rm, col, v, r, 1.1 * lo, 30.0, deg)
+        xo, ito, rro, sto = P.pcg(rm, col, ov[e], ob[e], pre, tol=1e-10)
+        assert sto == 0 and abs(it[e] - ito) <= 1, (e, it[e], ito)
+        assert np.linalg.norm(X[:, e] - xo) <= 1e-8 * np.linalg.norm(xo), e
+
+
+def test_pcg_lanczos_steps_limit(torch):
+    mesh = E.Mesh(5, 10)
+    xs = inputs.kl_samples(770, 0, 4, 10)
+    with pytest.raises(E.EnsError):
+        gpu_pcg(torch, mesh, xs, E.PC_CHEBYSHEV, iters=33, flags=E.PC_LANCZOS)
