@@ -1346,6 +1346,9 @@ def main_nonlinear(args):
     starts = [torch.from_numpy(np.stack([inputs.random_vector(600 + 100 * l + e, m.n) for e in range(s)],
                                         axis=1).reshape(-1)).to(dev) for l, m in enumerate(nl.meshes)]
     p = nl.params(NL_ALPHA, NL_BETA, tol=NL_TOL, lin_tol=NL_LIN_TOL, restart=30, max_lin=300, max_newton=20)
+    # the V-cycle's eigenvalue bounds by Lanczos steps (ENS_PC_LANCZOS)
+    p_lz = nl.params(NL_ALPHA, NL_BETA, tol=NL_TOL, lin_tol=NL_LIN_TOL, restart=30, max_lin=300, max_newton=20,
+                     power_iters=MG_LANCZOS_STEPS, flags=E.PC_LANCZOS)
     u = torch.empty(nl.mesh.n * s, dtype=torch.float64, device=dev)
     # every level pre-split (the V-cycle's SpMVs; level 0's also makes the GMRES SpMV pre-split)
     vdf = [torch.empty(2 * m.nnz * s, dtype=torch.float32, device=dev) for m in nl.meshes]
@@ -1355,8 +1358,9 @@ def main_nonlinear(args):
     work32 = torch.empty(nl.workspace_size(s, vals0, starts, p, vdf, v32), dtype=torch.uint8, device=dev)
     del vals0
 
-    def run(f32=False):
+    def run(f32=False, lanczos=False):
         newton, lin, launches = [], [], 0
+        pp = p_lz if lanczos else p
         torch.cuda.synchronize()
         t = time.perf_counter()
         for xi in xis:
@@ -1364,9 +1368,9 @@ def main_nonlinear(args):
             vals, b = nl.assemble(s, xi, values_df=vdf)
             if f32:  # the V-cycle in FP32 (mixed-precision preconditioner; flexible GMRES)
                 nl.mg.to_f32(s, vals, out=v32)
-                ni, li, rr, st, stats = nl.solve(s, vals, b, u, work32, starts, p, values_df=vdf, values_f32=v32)
+                ni, li, rr, st, stats = nl.solve(s, vals, b, u, work32, starts, pp, values_df=vdf, values_f32=v32)
             else:
-                ni, li, rr, st, stats = nl.solve(s, vals, b, u, work, starts, p, values_df=vdf)
+                ni, li, rr, st, stats = nl.solve(s, vals, b, u, work, starts, pp, values_df=vdf)
             if any(st):
                 raise RuntimeError(f"nonlinear: status {st}")
             newton += ni
@@ -1378,8 +1382,10 @@ def main_nonlinear(args):
     for _ in range(args.warmup):
         run()
         run(True)
+        run(lanczos=True)
     newton, lin, launches, sec = run()
     newton32, lin32, _, sec32 = run(True)
+    newton_lz, lin_lz, _, sec_lz = run(lanczos=True)
     line = {"metric": "nonlinear advection-diffusion Newton-GMRES sample-solves/s, 1 GB300",
             "value": NL_SAMPLES / sec, "unit": UNIT, "n_gpus": 1, "steps": 1, "warmup": args.warmup,
             "ms_per_step": 1e3 * sec, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -1393,6 +1399,9 @@ def main_nonlinear(args):
             "fp32_vcycle": {"sample_solves_per_s": NL_SAMPLES / sec32,
                             "newton_steps_mean": float(np.mean(newton32)),
                             "gmres_steps_per_solve_mean": float(np.mean(lin32))},
+            "lanczos_bound": {"sample_solves_per_s": NL_SAMPLES / sec_lz, "steps": MG_LANCZOS_STEPS,
+                              "newton_steps_mean": float(np.mean(newton_lz)),
+                              "gmres_steps_per_solve_mean": float(np.mean(lin_lz))},
             "gpu_launches": launches}
     print(json.dumps(line))
 

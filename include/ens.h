@@ -601,9 +601,10 @@ typedef struct ens_newton_params {
     int32_t max_lin;        /* GMRES steps per Newton step at most */
     int32_t precond;        /* ENS_NL_PRECOND_NONE / _MG */
     int32_t degree;         /* V-cycle: Chebyshev smoother degree */
-    int32_t power_iters;    /* V-cycle: power steps of the eigenvalue estimate */
+    int32_t power_iters;    /* V-cycle: power steps of the eigenvalue estimate (Lanczos steps with
+                               ENS_PC_LANCZOS) */
     int32_t check_every;    /* GMRES steps between host polls */
-    int32_t reserved;
+    int32_t flags;          /* 0, or ENS_PC_LANCZOS: the V-cycle's eigenvalue bounds by Lanczos */
     double ratio, boost;    /* V-cycle: smoother interval [lam/ratio, lam], lam = boost x estimate */
 } ens_newton_params;
 

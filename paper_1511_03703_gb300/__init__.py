@@ -76,7 +76,7 @@ class NewtonParamsC(ctypes.Structure):
     _fields_ = [("alpha", ctypes.c_double), ("beta", ctypes.c_double), ("tol", ctypes.c_double),
                 ("lin_tol", ctypes.c_double), ("max_newton", ctypes.c_int32), ("restart", ctypes.c_int32),
                 ("max_lin", ctypes.c_int32), ("precond", ctypes.c_int32), ("degree", ctypes.c_int32),
-                ("power_iters", ctypes.c_int32), ("check_every", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("power_iters", ctypes.c_int32), ("check_every", ctypes.c_int32), ("flags", ctypes.c_int32),
                 ("ratio", ctypes.c_double), ("boost", ctypes.c_double)]
 
 
@@ -544,11 +544,12 @@ class Nonlinear:
         return c
 
     def params(self, alpha, beta, tol=1e-8, lin_tol=1e-10, max_newton=20, restart=30, max_lin=500, degree=2,
-               ratio=5.0, boost=1.1, power_iters=10, check_every=4):
+               ratio=5.0, boost=1.1, power_iters=10, check_every=4, flags=0):
+        """flags: 0 or PC_LANCZOS (the V-cycle's eigenvalue bounds by power_iters Lanczos steps)."""
         p = NewtonParamsC()
         p.alpha, p.beta, p.tol, p.lin_tol = alpha, beta, tol, lin_tol
         p.max_newton, p.restart, p.max_lin, p.precond = max_newton, restart, max_lin, self.precond
-        p.degree, p.power_iters, p.check_every = degree, power_iters, check_every
+        p.degree, p.power_iters, p.check_every, p.flags = degree, power_iters, check_every, flags
         p.ratio, p.boost = ratio, boost
         return p
 

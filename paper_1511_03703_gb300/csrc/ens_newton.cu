@@ -695,8 +695,9 @@ struct NlSolver {
     }
     int *mg_bad = nullptr;
 
-    int setup_mg(const ens_mg_level *lv, double ratio, double boost, int power_iters, cudaStream_t st) {
-        int rc = mg.setup(lv, ratio, boost, power_iters, mg_bad, st, &launches);
+    int setup_mg(const ens_mg_level *lv, double ratio, double boost, int power_iters, cudaStream_t st,
+                 bool lanczos = false) {
+        int rc = mg.setup(lv, ratio, boost, power_iters, mg_bad, st, &launches, lanczos);
         if (rc) return rc;
         int hbad = 0;
         ENS_CUDA_TRY(cudaMemcpyAsync(&hbad, mg_bad, sizeof(int), cudaMemcpyDeviceToHost, st));
@@ -833,7 +834,9 @@ static int newton_run(int nlevels, const ens_mg_level *lv, const double *C, cons
                      static_cast<char *>(work), &bufs, st);
     if (rc) return rc;
     sv.check_every = p->check_every;
-    if (sv.precond && (rc = sv.setup_mg(lv, p->ratio, p->boost, p->power_iters, st))) return rc;
+    if (sv.precond && (rc = sv.setup_mg(lv, p->ratio, p->boost, p->power_iters, st,
+                                        (p->flags & ENS_PC_LANCZOS) != 0)))
+        return rc;
     GmArgs &a = sv.a;
     a.vals = bufs.J;
     if (bufs.Js) {  // the GMRES SpMV reads J pre-split and z split by the V-cycle
@@ -1032,6 +1035,8 @@ extern "C" int ens_newton(int nlevels, const ens_mg_level *levels, int s, const 
                         p->power_iters, p->check_every, p->lin_tol);
     if (rc) return rc;
     if (!(p->tol >= 0.0) || p->max_newton < 0) return fail(ENS_ERR_ARG, "ens_newton: tol >= 0, max_newton >= 0");
+    if ((p->flags & ~ENS_PC_LANCZOS) != 0 || ((p->flags & ENS_PC_LANCZOS) && p->power_iters > kLzMaxSteps))
+        return fail(ENS_ERR_ARG, "ens_newton: flags 0 or ENS_PC_LANCZOS (with at most %d steps)", kLzMaxSteps);
     if (!levels[0].values || !C || !b || !u || !work) return fail(ENS_ERR_ARG, "NULL values/C/b/u/work");
     if (!aligned16(work) || (s > 1 && (!aligned16(b) || !aligned16(u) || !aligned16(levels[0].values))))
         return fail(ENS_ERR_ALIGN, "values/b/u/work must be 16-byte aligned");

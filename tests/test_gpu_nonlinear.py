@@ -166,6 +166,24 @@ def test_newton_matches_oracle(torch, s, presplit):
         assert np.linalg.norm(U[:, e] - uo) <= 1e-8 * np.linalg.norm(uo), e
 
 
+@pytest.mark.parametrize("s,presplit", [(4, False), (32, "all")])
+def test_newton_lanczos_bound_matches_oracle(torch, s, presplit):
+    """ENS_PC_LANCZOS in the Newton parameters: the V-cycle's eigenvalue bounds
+    by 5 Lanczos steps; against the oracle's Newton with the same hierarchy."""
+    N, alpha, beta, tol, lin_tol = 8, 1.0, 10.0, 1e-10, 1e-11
+    xs, U, ni, li, rr, st = newton_case(torch, s, N, alpha, beta, tol=tol, lin_tol=lin_tol, presplit=presplit,
+                                        power_iters=5, flags=E.PC_LANCZOS)
+    assert st == [0] * s and max(rr) <= tol
+    for e in ([0, s - 1] if s > 2 else range(s)):
+        prob = NL.Problem(N, 10, xs[e], alpha, beta, v=V)
+        lv = G.hierarchy(N, 10, xs[e], [start(l, e, (n + 1) ** 3) for l, n in enumerate(G.level_sizes(N))],
+                         power_iters=5, lanczos=True)
+        uo, ko, lino, hist, sto = NL.newton(prob, tol=tol, lin_tol=lin_tol, precond=lambda r, lv=lv: G.vcycle(lv, r))
+        assert sto == 0 and ni[e] == ko, (e, ni[e], ko)
+        assert abs(li[e] - sum(lino)) <= ko, (e, li[e], lino)
+        assert np.linalg.norm(U[:, e] - uo) <= 1e-8 * np.linalg.norm(uo), e
+
+
 def test_newton_member_independent_of_s(torch):
     ref = None
     for s in (1, 4, 32):
