@@ -1448,7 +1448,8 @@ def main_profile_mg(args):
     --mode presplit: every level also writes its pre-split values (the
     V-cycle's SpMVs in double-float, as in the benchmark); --mode f32: the
     finest level writes its pre-split values and every level an FP32 copy for
-    the FP32 V-cycle."""
+    the FP32 V-cycle.  --lanczos: the smoothers' eigenvalue bounds by
+    MG_LANCZOS_STEPS Lanczos steps instead of 10 power steps."""
     import torch
     import paper_1511_03703_gb300 as E
     from paper_1511_03703_gb300 import inputs
@@ -1474,7 +1475,10 @@ def main_profile_mg(args):
             mg.to_f32(s, vals, out=v32)
         torch.cuda.synchronize()
         t1 = time.perf_counter()
-        it, rr, st, stats = mg.solve(s, vals, b, x, 1e-8, 500, work, starts, flags=E.CG_GRAPH | E.CG_X0_ZERO,
+        eig = dict(flags=E.PC_LANCZOS, power_iters=MG_LANCZOS_STEPS) if args.lanczos else dict(flags=0,
+                                                                                             power_iters=10)
+        it, rr, st, stats = mg.solve(s, vals, b, x, 1e-8, 500, work, starts,
+                                     flags=E.CG_GRAPH | E.CG_X0_ZERO | eig["flags"], power_iters=eig["power_iters"],
                                      check_every=4, values_df=pre, values_f32=v32)
         torch.cuda.synchronize()
         t2 = time.perf_counter()
@@ -1545,6 +1549,7 @@ def main():
     ap.add_argument("--k1-chunks", type=int, default=0, choices=[0, 1, 2, 4, 8],
                     help="profile-cg: chunks of 32 rows per SpMV CTA (0: the library's default)")
     ap.add_argument("--reps", type=int, default=2, help="profile-mg / profile-nl: repetitions")
+    ap.add_argument("--lanczos", action="store_true", help="profile-mg: eigenvalue bounds by Lanczos steps")
     ap.add_argument("--mode", default="presplit", choices=["", "presplit", "f32"],
                     help="profile-mg: which levels are pre-split / FP32")
     args = ap.parse_args()
