@@ -63,3 +63,26 @@ def test_product_path_has_no_oracle_or_cpu_fallback():
                 src = open(os.path.join(dirpath, f)).read()
                 assert "import oracle" not in src and "from oracle" not in src, f
                 assert "ens_oracle" not in src, f
+
+
+def test_binding_constants_match_the_header():
+    """Every status code, dtype, flag and enum value the binding names has the
+    value include/ens.h gives it (a drifted flag would select another path)."""
+    import re
+    import paper_1511_03703_gb300 as E
+    txt = open(os.path.join(ROOT, "include", "ens.h")).read()
+    consts = {}
+    for name, expr in re.findall(r"#define\s+ENS_([A-Z0-9_]+)\s+\(?([0-9u <]+)\)?\s*$", txt, re.M):
+        consts[name] = eval(expr.replace("u", ""))
+    for name, val in re.findall(r"\bENS_([A-Z0-9_]+)\s*=\s*(\d+)", txt):
+        consts[name] = int(val)
+    checked = 0
+    for name, val in consts.items():
+        if hasattr(E, name):
+            assert getattr(E, name) == val, (name, getattr(E, name), val)
+            checked += 1
+    # the binding's flags and codes are all among them
+    for name in ("CG_X0_ZERO", "CG_K1_DEFER", "CG_BATCH_K1_WIDE", "PC_LANCZOS", "PC_CHEBYSHEV", "F64_DF",
+                 "ERR_WORKSPACE", "NL_PRECOND_MG"):
+        assert name in consts and hasattr(E, name), name
+    assert checked >= 20, checked
