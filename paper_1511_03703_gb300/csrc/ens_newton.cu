@@ -940,9 +940,8 @@ extern "C" int ens_nl_jacobian(const ens_graph *gp, int32_t N, int s, const doub
     float m2h, m2l;
     nl_m2_split(beta, N, &m2h, &m2l);
 #define NL_JAC(SS)                                                                                             \
-    (nl_jacobian_kernel<SS><<<grid, 256, 0, st>>>(g.num_rows, N, g.row_map, g.col_entry, A, C, alpha, m2h, m2l, \
-                                                  b, u, J, nullptr, F, ns),                                    \
-     ENS_OK)
+    nl_jacobian_kernel<SS><<<grid, 256, 0, st>>>(g.num_rows, N, g.row_map, g.col_entry, A, C, alpha, m2h, m2l,  \
+                                                 b, u, J, nullptr, F, ns)
     switch (s) {
         case 1: NL_JAC(1); break;
         case 4: NL_JAC(4); break;
